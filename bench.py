@@ -1,0 +1,342 @@
+#!/usr/bin/env python3
+"""Benchmark: SES grid points/s (labels + edge intersections) on one GB300.
+
+Workload: the 5,000-atom synthetic globule (C-alpha walk compacted to 0.0125
+atoms/A^3), r_p 1.4 A, h 0.25 A, margin 0.8 A -- 44.7 M grid points.  A step
+is one eses_run: cell binning, patch construction, classification of every
+point, crossing edges, roots and normals, area and volume.
+
+  value      points/s with the atoms resident in HBM (CUDA events around
+             eses_run on the library's stream; L2 flushed between steps)
+  e2e        points/s through the public C ABI with host buffers: create from
+             pinned host atoms, run, copy labels and intersections back
+  plain_fp64 the same step with every stage in FP64 (the plain GPU form)
+  roofline   the classification kernel against the FP32 ALU peak, with the
+             algorithmic flops of the oracle-counted flop model
+  cpu_baseline  the FP64 CPU oracle on a seeded sample of blocks, all cores
+
+--impl reference times the oracle (the reference arm of this build) on the
+same workload.  Under torchrun every rank computes its own molecule (weak
+scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SES grid points/s (labels+edge intersections)"
+UNIT = "points/s"
+N_SM = 152
+FP32_LANES = 128  # FP32 FMA lanes per SM
+WORKLOAD = 2
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        idx = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+        if not idx.isdigit():
+            idx = "0"
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", idx, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                    power.append(float(p[3]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, p[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_sample(xyz, rad, wl, seed, n_blocks=None, block_pts=32):
+    """Oracle on a seeded sample of block_pts^3 blocks: (points, seconds, cores)."""
+    import numpy as np
+
+    import oracle
+    cores = oracle.num_threads()
+    dims, _ = oracle.grid(xyz, rad, wl.h, wl.margin)
+    nb = [oracle.block_count(int(d), block_pts) for d in dims]
+    total = nb[0] * nb[1] * nb[2]
+    n_blocks = n_blocks or 2 * cores
+    rng = np.random.default_rng(seed)
+    ids = rng.choice(total, size=min(n_blocks, total), replace=False)
+    t0 = time.perf_counter()
+    res = oracle.run(xyz, rad, wl.r_p, wl.h, wl.margin, block_pts=block_pts, block_ids=ids, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return res.n_points, dt, cores, len(ids)
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    from paper_1809_04352_gb300 import inputs
+    wl = inputs.WORKLOADS[WORKLOAD]
+    xyz, rad = inputs.workload_atoms(WORKLOAD)
+    for w in range(args.warmup):
+        cpu_sample(xyz, rad, wl, seed=100 + w, n_blocks=args.ref_blocks)
+    pts, secs = 0, 0.0
+    cores = blocks = 0
+    for k in range(args.steps):
+        p, dt, cores, blocks = cpu_sample(xyz, rad, wl, seed=200 + k, n_blocks=args.ref_blocks)
+        pts += p
+        secs += dt
+    value = pts / secs
+    sample = f"{blocks} seeded 32^3-point blocks of {wl.name} per step, {args.steps} steps"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(wl, xyz, None),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def config_of(wl, xyz, npts):
+    return {"workload": f"{wl.name}: synthetic C-alpha-walk globule, {xyz.shape[0]} atoms, "
+                        f"r_p {wl.r_p} A, h {wl.h} A, margin {wl.margin} A",
+            "n_atoms": int(xyz.shape[0]), "r_p": wl.r_p, "h": wl.h, "margin": wl.margin,
+            "grid_points": npts, "precision": "fp32-filtered, fp64 band and roots",
+            "l2": "flushed between steps (256 MiB device write)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-blocks", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    from paper_1809_04352_gb300 import build as libbuild
+    from paper_1809_04352_gb300 import eses, inputs
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl")
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    if rank == 0:
+        libbuild.build()
+    barrier()
+    libbuild.build()
+    eses.load()
+    wl = inputs.WORKLOADS[WORKLOAD]
+    xyz, rad = inputs.workload_atoms(WORKLOAD, molecule=rank)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def timed_runs(ctx, k):
+        times, stages = [], []
+        for _ in range(k):
+            flush.zero_()
+            s = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            eses.eses_run(ctx)
+            e.record(stream)
+            e.synchronize()
+            times.append(s.elapsed_time(e))
+            stages.append(eses.eses_stage_times(ctx))
+        return times, stages
+
+    # ---- device-resident step (value) --------------------------------------
+    ctx = eses.eses_create(xyz, rad, wl.r_p, wl.h, wl.margin)
+    eses.eses_set_option(ctx, eses.ESES_OPT_STREAM, stream.cuda_stream)
+    eses.eses_set_option(ctx, eses.ESES_OPT_PROFILE, 1)
+    for _ in range(args.warmup):
+        eses.eses_run(ctx)
+    dims, _ = eses.eses_grid(ctx)
+    npts = int(np.prod(dims))
+    torch.cuda.synchronize()
+    barrier()
+    clocks = Clocks()
+    clocks.start()
+    times, stages = timed_runs(ctx, args.steps)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    st = eses.eses_stats(ctx)
+    total_s = sum(times) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+        n = torch.tensor([float(npts)], device="cuda")
+        torch.distributed.all_reduce(n)
+        all_pts = float(n.item())
+    else:
+        all_pts = float(npts)
+    value = all_pts * args.steps / total_s
+    stage_ms = {k: statistics.mean(s[k] for s in stages) for k in stages[0]}
+
+    # ---- plain FP64 form (same step, every stage FP64) ----------------------
+    eses.eses_set_option(ctx, eses.ESES_OPT_PRECISION, eses.ESES_PREC_FP64)
+    eses.eses_run(ctx)
+    t64, s64 = timed_runs(ctx, max(2, min(args.steps, 5)))
+    plain_ms = statistics.mean(t64)
+    eses.eses_set_option(ctx, eses.ESES_OPT_PRECISION, eses.ESES_PREC_FP32_FILTERED)
+    eses.eses_destroy(ctx)
+
+    # ---- end to end through the C ABI with host buffers ---------------------
+    xyz_pin = torch.from_numpy(np.ascontiguousarray(xyz)).pin_memory()
+    rad_pin = torch.from_numpy(np.ascontiguousarray(rad)).pin_memory()
+    lab_pin = torch.empty(npts, dtype=torch.int8).pin_memory()
+    caps = [0, 0, 0]
+    bufs = None
+    h2d = xyz.nbytes + rad.nbytes
+    d2h = 0
+    e2e_times = []
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c2 = eses.eses_create(xyz_pin.numpy(), rad_pin.numpy(), wl.r_p, wl.h, wl.margin)
+        eses.eses_run(c2)
+        eses.eses_labels(c2, lab_pin.numpy().reshape(tuple(int(v) for v in dims)))
+        ne = [eses.eses_num_intersections(c2, a) for a in range(3)]
+        if bufs is None or any(ne[a] > caps[a] for a in range(3)):
+            caps = [int(v * 1.2) + 16 for v in ne]
+            bufs = [(torch.empty(c, dtype=torch.int64).pin_memory(), torch.empty(c, dtype=torch.float64).pin_memory(),
+                     torch.empty(3 * c, dtype=torch.float64).pin_memory()) for c in caps]
+        lib = eses.load()
+        for a in range(3):
+            lib.eses_intersections(c2, a, bufs[a][0].data_ptr(), bufs[a][1].data_ptr(), bufs[a][2].data_ptr(), None,
+                                   None)
+        area_vol = eses.eses_area_volume(c2)
+        eses.eses_destroy(c2)
+        t1 = time.perf_counter()
+        if k >= args.warmup:
+            e2e_times.append(t1 - t0)
+        d2h = npts + sum(ne) * (8 + 8 + 24) + 16
+    e2e_s = sum(e2e_times)
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = all_pts * args.steps / e2e_s
+
+    # ---- roofline of the dominant kernel ------------------------------------
+    peaks, psrc = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = N_SM * FP32_LANES * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    with open(os.path.join(ROOT, "tests", "golden", "flop_model.json")) as f:
+        fm = json.load(f)[wl.name]
+    flops = fm["flops_per_point"] * npts
+    t_cls = stage_ms["classify"] / 1e3
+    achieved = flops / t_cls / 1e12
+    roofline = {"bound": "alu", "kernel": "k_classify<float,true> (FP32-filtered classification)",
+                "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                "traffic": None,
+                "peak_source": f"derived: {N_SM} SMs x {FP32_LANES} FP32 lanes x 2 flops x {sm_max:.0f} MHz "
+                               f"(sm_max_mhz {psrc})",
+                "flops_per_point": fm["flops_per_point"], "kernel_ms": stage_ms["classify"]}
+
+    # ---- CPU baseline (rank 0, N = 1) ---------------------------------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pts, secs, cores, nblk = cpu_sample(xyz, rad, wl, seed=7)
+        cpu = {"value": pts / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{nblk} seeded 32^3-point blocks of {wl.name} ({pts} points, {secs:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": config_of(wl, xyz, npts),
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                        "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s / args.steps},
+                "gpu_launches": int(st["kernel_launches"]) * args.steps,
+                "roofline": roofline,
+                "cpu_baseline": cpu,
+                "clocks": clk,
+                "plain_fp64": {"value": all_pts / (plain_ms / 1e3), "unit": UNIT, "ms_per_step": plain_ms,
+                               "stages_ms": {k: statistics.mean(s[k] for s in s64) for k in s64[0]}},
+                "stages_ms": stage_ms,
+                "stats": {k: st[k] for k in ("crossing_edges", "inside_points", "circle_pairs", "free_vertices",
+                                             "root_failures")},
+                "area_A2": area_vol[0], "volume_A3": area_vol[1]}
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

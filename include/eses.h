@@ -1,0 +1,148 @@
+/*
+ * eses.h -- C ABI of the GB300 ESES library (libeses.so).
+ *
+ * Eulerian solvent excluded surface: given atoms (centres c_i, van der Waals
+ * radii r_i; Eq. 1), a probe radius r_p, a grid spacing h and a margin, the
+ * library labels every point of a Cartesian grid as inside or outside the
+ * solvent excluded surface (Eq. 2), computes the intersection of every grid
+ * edge whose end labels differ with the surface (Eq. 3-4) together with the
+ * surface normal there, and the surface area and enclosed volume.
+ *
+ * The SES is the boundary of the union of all probe balls of radius r_p whose
+ * centres are at distance >= r_i + r_p from every atom (§1).  A grid point x
+ * is inside (label 1) iff dist(x, free probe centres) >= r_p.
+ *
+ * Grid (Eq. 2, §2.3): point (i,j,k) sits at origin + h*(i,j,k) with
+ *   origin_a = min_i(c_ia - r_i) - margin,
+ *   dims_a   = ceil((max_i(c_ia + r_i) + margin - origin_a) / h) + 1.
+ * Labels are stored C order, k fastest: index = (i*dims[1] + j)*dims[2] + k.
+ *
+ * Intersections (Eq. 3-4): for each axis a, one record per edge
+ * (p, p + e_a) with different labels: lower point linear index, tau in
+ * [0,1] such that the surface point is p + tau*h*e_a (the paper's lambda is
+ * 1 - tau), and the unit normal pointing into the solvent.  When an edge
+ * holds several roots the first one from the lower point is reported.
+ * Records are ordered by tile (8x8x8-point tiles in C order of the tile
+ * index), then by lower index within the tile; the order is deterministic.
+ *
+ * Area  = h^2 * sum over all crossing edges of |n_a| (a = the edge's axis).
+ * Volume = h^2/3 * sum over the three axes of the inside length along grid
+ * lines (an edge with both ends inside counts h; a crossing edge counts the
+ * part on the inside end's side of the root).
+ *
+ * Blocks (§2.3-2.5, Algorithm 1): work is grouped in cubic blocks of B
+ * points per edge sharing faces (B-1 cells, ownership half-open per Eq. 5);
+ * results do not depend on B.
+ *
+ * Conventions for every function below:
+ *   - return value 0 on success, a negative ESES_E* code on failure; on
+ *     failure eses_last_error() describes the cause;
+ *   - no exception crosses the ABI; no call aborts the process;
+ *   - pointers documented "host" must be host memory, "device" must be
+ *     memory of the context's device; all sizes are element counts;
+ *   - a context is used by one host thread at a time.
+ */
+#ifndef ESES_H
+#define ESES_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct eses_ctx eses_ctx;
+
+#define ESES_OK 0
+#define ESES_EINVAL (-1)    /* invalid argument (sizes, non-finite input, r <= 0, r_p < 0, h <= 0, margin < h) */
+#define ESES_ENOMEM (-2)    /* host or device allocation failed */
+#define ESES_ECUDA (-3)     /* a CUDA call failed */
+#define ESES_ETIMEOUT (-4)  /* a bounded device wait expired */
+#define ESES_ECAPACITY (-5) /* a per-tile list exceeded its capacity */
+#define ESES_ESTATE (-6)    /* call out of order (e.g. results before eses_run) */
+#define ESES_EROOT (-7)     /* a crossing edge had no surface root (numerical failure) */
+
+/* option keys for eses_set_option */
+#define ESES_OPT_BLOCK_PTS 1   /* points per block edge, >= 9 (default 64) */
+#define ESES_OPT_PRECISION 2   /* ESES_PREC_* (default ESES_PREC_FP32_FILTERED) */
+#define ESES_OPT_STREAM 3      /* cudaStream_t cast to int64 (0 = the context's own stream) */
+#define ESES_OPT_SYNC 4        /* 1 (default): eses_run waits for the device; 0: returns after enqueueing */
+#define ESES_OPT_PROFILE 5     /* 1: time every stage of eses_run with CUDA events (eses_stage_times) */
+
+#define ESES_PREC_FP64 0           /* every step in FP64 */
+#define ESES_PREC_FP32_FILTERED 1  /* FP32 with a forward-error filter, FP64 inside the filter band */
+
+/* Create a context for one molecule.  xyz: host, n_atoms*3 doubles (x,y,z per
+ * atom, Angstrom); radii: host, n_atoms doubles.  Both are copied; the caller
+ * keeps ownership.  Uses the current CUDA device.  *out receives the context
+ * (NULL on failure). */
+int eses_create(const double *xyz, const double *radii, int64_t n_atoms, double r_p, double h, double margin,
+                eses_ctx **out);
+
+/* As eses_create, with xyz and radii in device memory (copied on the device). */
+int eses_create_device(const double *xyz, const double *radii, int64_t n_atoms, double r_p, double h, double margin,
+                       eses_ctx **out);
+
+/* Set an option (ESES_OPT_*).  Takes effect at the next eses_run. */
+int eses_set_option(eses_ctx *ctx, int key, int64_t value);
+
+/* Run the whole path: cell binning, patch construction, classification,
+ * crossing edges, root solve, area and volume.  Results stay in device memory
+ * owned by the context until the next eses_run or eses_destroy. */
+int eses_run(eses_ctx *ctx);
+
+/* Grid dimensions and origin (host outputs, 3 values each). */
+int eses_grid(const eses_ctx *ctx, int64_t dims[3], double origin[3]);
+
+/* Copy the labels (int8, dims[0]*dims[1]*dims[2], C order) to host memory. */
+int eses_labels(const eses_ctx *ctx, int8_t *out);
+
+/* Borrow the device pointer of the labels; valid until the next eses_run or
+ * eses_destroy. */
+int eses_labels_device(const eses_ctx *ctx, const int8_t **dptr);
+
+/* Number of crossing edges along axis (0,1,2). */
+int eses_num_intersections(const eses_ctx *ctx, int axis, int64_t *n);
+
+/* Copy the intersections of one axis to host memory.  Every output is
+ * caller-allocated for eses_num_intersections() records and may be NULL:
+ * lower_idx (int64), tau (double), normal (3 doubles per record), tau32 and
+ * normal32 (the same in float). */
+int eses_intersections(const eses_ctx *ctx, int axis, int64_t *lower_idx, double *tau, double *normal,
+                       float *tau32, float *normal32);
+
+/* Borrow the device pointers of one axis' intersections (valid until the next
+ * eses_run or eses_destroy); any output pointer may be NULL. */
+int eses_intersections_device(const eses_ctx *ctx, int axis, const int64_t **lower_idx, const double **tau,
+                              const double **normal, const float **tau32, const float **normal32);
+
+/* Surface area (A^2) and enclosed volume (A^3), host outputs. */
+int eses_area_volume(const eses_ctx *ctx, double *area, double *volume);
+
+/* Diagnostics of the last run, host output of up to n int64 values:
+ * [0] points, [1] tiles, [2] tiles with work, [3] circle pairs, [4] pairs
+ * with a free arc, [5] free triple points, [6] points re-evaluated in FP64
+ * (filter band), [7] crossing edges (all axes), [8] edges with a reported
+ * root failure, [9] inside points, [10] kernels launched by the run. */
+int eses_stats(const eses_ctx *ctx, int64_t *out, int n);
+
+/* Device time in milliseconds of every stage of the last eses_run, measured
+ * with CUDA events on the context's stream (requires ESES_OPT_PROFILE = 1),
+ * host output of up to n values: [0] cell binning, [1] neighbours and circle
+ * pairs, [2] free arcs, triple points and patch bins, [3] classification,
+ * [4] FP64 band re-evaluation, [5] crossing-edge counts and offsets,
+ * [6] root solve and normals, [7] area/volume reduction.  Stages that wait
+ * for a host read of a list total include that wait. */
+int eses_stage_times(const eses_ctx *ctx, double *ms, int n);
+
+/* Last error message of the context (or of the last failed create when ctx
+ * is NULL).  Never NULL. */
+const char *eses_last_error(const eses_ctx *ctx);
+
+/* Release every resource of the context.  NULL is accepted. */
+void eses_destroy(eses_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ESES_H */

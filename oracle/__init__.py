@@ -77,6 +77,8 @@ def _load():
         lib.eo_model_stats.argtypes = [P, P, i64, d, P, P, P, i64]
         lib.eo_model_stats.restype = ctypes.c_int
         lib.eo_num_threads.restype = ctypes.c_int
+        lib.eo_flop_counts.argtypes = [P, P, i64, d, d, d, ctypes.c_int, P]
+        lib.eo_flop_counts.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -207,3 +209,18 @@ def model_stats(xyz, radii, r_p: float, max_vertices: int = 0):
     nv = int(nverts[0])
     verts = buf[: min(nv, max_vertices)] if max_vertices else None
     return int(npairs[0]), nv, verts
+
+
+FLOP_KEYS = ["points", "sum_reach", "shell_points", "sum_face", "sum_face_x_reach", "sum_arc", "sum_vert",
+             "model_flops"]
+
+
+def flop_counts(xyz, radii, r_p: float, h: float, margin: float, nthreads: int = 0) -> dict:
+    """Algorithmic flop model of the classification over the whole grid."""
+    lib = _load()
+    xyz, radii = _atoms(xyz, radii)
+    out = np.zeros(8, np.int64)
+    rc = lib.eo_flop_counts(_ptr(xyz), _ptr(radii), xyz.shape[0], r_p, h, margin, int(nthreads), _ptr(out))
+    if rc != 0:
+        raise ValueError("invalid parameters")
+    return dict(zip(FLOP_KEYS, (int(v) for v in out)))

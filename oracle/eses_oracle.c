@@ -825,3 +825,85 @@ int eo_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------ */
+/* algorithmic flop model (instrumentation)                                  */
+/* ------------------------------------------------------------------------ */
+/* Counts, over every grid point x, the candidate work that the definition of
+ * Eq. 2 implies, with fixed unit costs:
+ *   8  per atom within reach (|x - c| < r + 2 r_p: the atoms that decide x);
+ * and for shell points (inside some expanded ball, outside every van der
+ * Waals ball):
+ *   12 per face candidate (expanded ball containing x) plus 8 per freeness
+ *      test of its projection against each atom within reach,
+ *   30 per saddle candidate (pair circle passing within r_p of x, with x
+ *      inside one of the pair's expanded balls),
+ *   8  per concave candidate (free triple point within r_p of x).
+ * out[0] = points, out[1] = sum n_reach, out[2] = shell points,
+ * out[3] = sum over shell points of n_face, out[4] = sum of n_face * n_reach,
+ * out[5] = sum n_arc, out[6] = sum n_vert, out[7] = total model flops. */
+int eo_flop_counts(const double *xyz, const double *r, int64_t n, double rp, double h, double margin, int nthreads,
+                   int64_t *out)
+{
+    int64_t dims[3];
+    double lo[3];
+    if (eo_grid(xyz, r, n, h, margin, dims, lo) != 0) return -1;
+    Model m;
+    model_build(&m, xyz, r, NULL, (int)n, rp, rp, 0);
+    /* saddle candidates: circles within r_p of x whose pair has a ball that
+     * contains x (the nearest free point of x lies on such a circle's arc
+     * only then: x is in the triangle of the two centres and that point) */
+    int64_t s_reach = 0, s_shell = 0, s_face = 0, s_fr = 0, s_arc = 0, s_vert = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4) reduction(+ : s_reach, s_shell, s_face, s_fr, s_arc, s_vert)
+#endif
+    for (int64_t i = 0; i < dims[0]; ++i)
+        for (int64_t j = 0; j < dims[1]; ++j)
+            for (int64_t k = 0; k < dims[2]; ++k) {
+                double x[3] = {lo[0] + h * (double)i, lo[1] + h * (double)j, lo[2] + h * (double)k};
+                long reach = 0, face = 0;
+                int in_vdw = 0;
+                FOR_NEAR(&m, x, m.a_start, m.a_list, m.n, a, {
+                    double d2 = dist2(x, m.c + 3 * a);
+                    double rr = m.r[a] + 2.0 * rp;
+                    if (d2 < rr * rr) reach++;
+                    if (d2 < m.R[a] * m.R[a]) face++;
+                    if (d2 < m.r[a] * m.r[a]) in_vdw = 1;
+                });
+                s_reach += reach;
+                if (face == 0 || in_vdw) continue;
+                s_shell++;
+                s_face += face;
+                s_fr += face * reach;
+                long arc = 0, vert = 0;
+                FOR_NEAR(&m, x, m.p_start, m.p_list, m.np, p, {
+                    const double *o = m.po + 3 * p, *u = m.pu + 3 * p;
+                    double y[3] = {x[0] - o[0], x[1] - o[1], x[2] - o[2]};
+                    double z = dot3(y, u);
+                    double w2 = dot3(y, y) - z * z;
+                    double nw = sqrt(w2 > 0.0 ? w2 : 0.0);
+                    double e = nw - m.prho[p];
+                    if (e * e + z * z < rp * rp) {
+                        int pi_ = m.pi[p], pj_ = m.pj[p];
+                        if (dist2(x, m.c + 3 * pi_) < m.R[pi_] * m.R[pi_] || dist2(x, m.c + 3 * pj_) < m.R[pj_] * m.R[pj_])
+                            arc++;
+                    }
+                });
+                FOR_NEAR(&m, x, m.v_start, m.v_list, m.nv, v, {
+                    if (dist2(x, m.vq + 3 * v) < rp * rp) vert++;
+                });
+                s_arc += arc;
+                s_vert += vert;
+            }
+    model_free(&m);
+    out[0] = dims[0] * dims[1] * dims[2];
+    out[1] = s_reach;
+    out[2] = s_shell;
+    out[3] = s_face;
+    out[4] = s_fr;
+    out[5] = s_arc;
+    out[6] = s_vert;
+    out[7] = 8 * s_reach + 12 * s_face + 8 * s_fr + 30 * s_arc + 8 * s_vert;
+    return 0;
+}

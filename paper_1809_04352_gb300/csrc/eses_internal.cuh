@@ -1,0 +1,84 @@
+// eses_internal.cuh -- data layout shared by the kernels of libeses.
+//
+// Everything lives in device memory owned by one context:
+//   atoms       sorted by cell (counting sort), double4 (x, y, z, r)
+//   cell grid   uniform cells of edge 2*R_max, CSR cell_start
+//   neighbours  CSR: j with |c_i - c_j| < R_i + R_j (R = r + r_p)
+//   pairs       i < j with an intersection circle of the expanded spheres
+//               (saddle patch carrier, §1): centre o, axis u, radius rho,
+//               flag "has a free arc"
+//   vertices    free triple points (concave patch centres, §1)
+//   patch bins  free-arc pairs binned by o, vertices binned by position
+// Tiles of 8x8x8 grid points are the unit of work; every tile stages the
+// atoms, free-arc pairs and free vertices that can influence its points into
+// shared memory (§2.2: the classification of a point depends only on atoms
+// within r_max + 2 r_p).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace eses {
+
+constexpr int TILE = 8;          // points per tile edge
+constexpr int TILE_PTS = TILE * TILE * TILE;
+
+// per-tile staging capacities (shared memory lists)
+constexpr int A_MAX = 320;
+constexpr int P_MAX = 512;
+constexpr int V_MAX = 640;
+
+// device error bits (OR-ed into ctx->d_err)
+enum : int {
+    ERR_CAP_ATOMS = 1,
+    ERR_CAP_PAIRS = 2,
+    ERR_CAP_VERTS = 4,
+    ERR_ROOT = 8,
+    ERR_TIMEOUT = 16,
+    ERR_CAP_EDGES = 32,
+};
+
+// label codes in the label array
+constexpr int8_t LABEL_OUT = 0;
+constexpr int8_t LABEL_IN = 1;
+constexpr int8_t LABEL_BAND = 2;  // FP32 filter undecided: re-evaluated in FP64
+
+struct Model {
+    int n_atoms;
+    const double4 *atom;          // sorted atoms (x, y, z, r)
+    const int *atom_orig;         // original index of each sorted atom
+    const uint8_t *atom_face;     // 1: expanded sphere keeps a free face
+    double clo[3];                // cell grid origin
+    double cell;                  // cell edge
+    int cn[3];                    // cells per axis
+    const int *cell_start;        // ncell + 1
+    const int *nb_start;          // n_atoms + 1
+    const int *nb_list;
+    int n_pairs;
+    const double4 *pair_o;        // o.xyz, rho
+    const double4 *pair_u;        // u.xyz, 0
+    const int2 *pair_ij;          // sorted atom indices i < j
+    const uint8_t *pair_free;     // 1: the circle keeps a free arc
+    const int *pcell_start;       // free-arc pairs binned by o
+    const int *pcell_list;
+    int n_verts;
+    const double4 *vert;          // free triple points (xyz, 0)
+    const int *vcell_start;
+    const int *vcell_list;
+    double rp, rmax, Rmax;
+};
+
+struct Grid {
+    double lo[3];
+    double h;
+    long long dims[3];
+    int tiles[3];
+    long long n_tiles;
+    double rp;
+    double halo;                  // r_max + 2 r_p
+    float d0;                     // FP32 error bound of a staged position difference
+};
+
+__host__ __device__ inline long long ceil_div_ll(long long a, long long b) { return (a + b - 1) / b; }
+
+}  // namespace eses

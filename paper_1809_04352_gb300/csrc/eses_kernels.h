@@ -1,0 +1,57 @@
+// eses_kernels.h -- host-side launchers of the libeses kernels (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "eses_internal.cuh"
+
+namespace eses {
+
+// ---- exclusive scan (eses_scan.cu) ---------------------------------------
+// out[0..n] = exclusive prefix sums of in[0..n-1]; out[n] = total.  `tmp`
+// must hold scan_tmp_ints(n) ints.  in and out may not alias.
+long long scan_tmp_ints(long long n);
+int scan_exclusive(const int *in, int *out, long long n, int *tmp, cudaStream_t st);
+
+// ---- model construction (eses_model.cu) ----------------------------------
+struct ModelBuf;  // owned by the context
+int launch_cell_count(const double *xyz, const double *r, int n, const double clo[3], double cell, const int cn[3],
+                       int *cell_id, int *cell_count, cudaStream_t st);
+int launch_cell_scatter(const double *xyz, const double *r, int n, const int *cell_id, const int *cell_start,
+                         int *cursor, int *sorted_orig, cudaStream_t st);
+int launch_cell_finish(const double *xyz, const double *r, int n, int ncell, const int *cell_start, int *sorted_orig,
+                        double4 *atom, cudaStream_t st);
+int launch_nb_count(const Model &M, int *nb_count, int *circle_count, uint8_t *contained, cudaStream_t st);
+int launch_nb_fill(const Model &M, int *nb_list, cudaStream_t st);
+int launch_pair_count(const Model &M, int *pair_count, cudaStream_t st);
+int launch_pair_fill(const Model &M, const int *pair_start, double4 *pair_o, double4 *pair_u, int2 *pair_ij,
+                      cudaStream_t st);
+int launch_arcs(const Model &M, uint8_t *pair_free, int *vert_count, cudaStream_t st);
+int launch_arcs_emit(const Model &M, const int *vert_start, double4 *vert, cudaStream_t st);
+int launch_faces(const Model &M, const int *circle_count, const uint8_t *contained, uint8_t *face, cudaStream_t st);
+int launch_bin_count(const Model &M, int which, int *count, int *item_cell, cudaStream_t st);
+int launch_bin_scatter(const Model &M, int which, const int *item_cell, const int *start, int *cursor, int *list,
+                        cudaStream_t st);
+
+// ---- classification (eses_classify.cu) -----------------------------------
+int launch_classify(const Model &M, const Grid &G, int precision, int8_t *labels, int *tile_band, int *err,
+                     cudaStream_t st);
+int launch_band(const Model &M, const Grid &G, int8_t *labels, const int *tile_band, int *err, cudaStream_t st);
+
+// ---- crossing edges, roots, area/volume (eses_edges.cu) ------------------
+int launch_edge_count(const Grid &G, const int8_t *labels, int *tile_edges, int *tile_inside_edges,
+                       cudaStream_t st);
+struct EdgeOut {
+    long long *idx[3];
+    double *tau[3];
+    double *nrm[3];
+    float *tau32[3];
+    float *nrm32[3];
+};
+int launch_edge_solve(const Model &M, const Grid &G, const int8_t *labels, const int *edge_start, EdgeOut out,
+                       double *tile_area, double *tile_vol, int *n_fail, int *err, cudaStream_t st);
+int launch_reduce(const Grid &G, const double *tile_area, const double *tile_vol, const int *tile_inside_edges,
+                   const int8_t *labels, double *out2, long long *counts, cudaStream_t st);
+
+}  // namespace eses

@@ -1,0 +1,480 @@
+// eses_model.cu -- analytic patch construction (the first ESES stage, §2.2).
+//
+// From the atoms this builds, in FP64:
+//   1. a counting sort of the atoms into uniform cells (cell edge 2 R_max, so
+//      every overlapping pair of expanded balls sits in adjacent cells);
+//   2. neighbour lists: j with |c_i - c_j| < R_i + R_j;
+//   3. circle pairs: i < j whose expanded spheres meet in a circle
+//      (|R_i - R_j| < D < R_i + R_j), carrier of the saddle (toroidal) patch;
+//   4. for every circle, the arcs covered by the other expanded balls: a ball k
+//      covers the arc where cos(phi - psi_k) > T_k; the circle keeps a free
+//      arc unless one ball covers it whole or every covered-arc end point is
+//      itself covered.  A free end point lies on three expanded spheres and in
+//      no other ball: it is a free triple point (concave patch centre; the
+//      probe-clash test of the north-star is this freeness test, in FP64);
+//   5. a per-atom flag "the expanded sphere keeps a free face";
+//   6. free-arc pairs and free triple points binned into the cells.
+// The paper builds patches from all atom pairs under a distance threshold
+// (§5) -- the same set as step 3.
+#include <math.h>
+
+#include "eses_kernels.h"
+
+namespace eses {
+
+__device__ __forceinline__ int cell_coord(double v, double lo, double cell, int n)
+{
+    int k = (int)floor((v - lo) / cell);
+    return k < 0 ? 0 : (k >= n ? n - 1 : k);
+}
+
+__global__ void k_cell_count(const double *__restrict__ xyz, int n, double clx, double cly, double clz, double cell,
+                             int cn0, int cn1, int cn2, int *__restrict__ cell_id, int *__restrict__ cell_count)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int a = cell_coord(xyz[3 * i + 0], clx, cell, cn0);
+    int b = cell_coord(xyz[3 * i + 1], cly, cell, cn1);
+    int c = cell_coord(xyz[3 * i + 2], clz, cell, cn2);
+    int id = (a * cn1 + b) * cn2 + c;
+    cell_id[i] = id;
+    atomicAdd(&cell_count[id], 1);
+}
+
+int launch_cell_count(const double *xyz, const double *, int n, const double clo[3], double cell, const int cn[3],
+                       int *cell_id, int *cell_count, cudaStream_t st)
+{
+    if (n <= 0) return 0;
+    k_cell_count<<<(n + 255) / 256, 256, 0, st>>>(xyz, n, clo[0], clo[1], clo[2], cell, cn[0], cn[1], cn[2], cell_id,
+                                                  cell_count);
+    return 1;
+}
+
+__global__ void k_cell_scatter(int n, const int *__restrict__ cell_id, const int *__restrict__ cell_start,
+                               int *__restrict__ cursor, int *__restrict__ sorted_orig)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int id = cell_id[i];
+    sorted_orig[cell_start[id] + atomicAdd(&cursor[id], 1)] = i;
+}
+
+int launch_cell_scatter(const double *, const double *, int n, const int *cell_id, const int *cell_start, int *cursor,
+                         int *sorted_orig, cudaStream_t st)
+{
+    if (n <= 0) return 0;
+    k_cell_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, cell_id, cell_start, cursor, sorted_orig);
+    return 1;
+}
+
+// order every cell by original atom index (deterministic layout), then gather
+__global__ void k_cell_finish(const double *__restrict__ xyz, const double *__restrict__ r, int ncell,
+                              const int *__restrict__ cell_start, int *__restrict__ sorted_orig,
+                              double4 *__restrict__ atom)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    int s = cell_start[c], e = cell_start[c + 1];
+    for (int a = s + 1; a < e; ++a) {
+        int v = sorted_orig[a];
+        int b = a - 1;
+        while (b >= s && sorted_orig[b] > v) {
+            sorted_orig[b + 1] = sorted_orig[b];
+            --b;
+        }
+        sorted_orig[b + 1] = v;
+    }
+    for (int a = s; a < e; ++a) {
+        int o = sorted_orig[a];
+        atom[a] = make_double4(xyz[3 * o], xyz[3 * o + 1], xyz[3 * o + 2], r[o]);
+    }
+}
+
+int launch_cell_finish(const double *xyz, const double *r, int, int ncell, const int *cell_start, int *sorted_orig,
+                        double4 *atom, cudaStream_t st)
+{
+    k_cell_finish<<<(ncell + 255) / 256, 256, 0, st>>>(xyz, r, ncell, cell_start, sorted_orig, atom);
+    return 1;
+}
+
+// --------------------------------------------------------------------------
+// neighbour iteration over the 27 cells around a sorted atom
+// --------------------------------------------------------------------------
+#define FOR_NEIGHBOUR_CELLS(M, px, py, pz, j, ...)                                               \
+    do {                                                                                          \
+        int ca_ = cell_coord(px, (M).clo[0], (M).cell, (M).cn[0]);                                \
+        int cb_ = cell_coord(py, (M).clo[1], (M).cell, (M).cn[1]);                                \
+        int cc_ = cell_coord(pz, (M).clo[2], (M).cell, (M).cn[2]);                                \
+        for (int a_ = max(ca_ - 1, 0); a_ <= min(ca_ + 1, (M).cn[0] - 1); ++a_)                   \
+            for (int b_ = max(cb_ - 1, 0); b_ <= min(cb_ + 1, (M).cn[1] - 1); ++b_)               \
+                for (int c_ = max(cc_ - 1, 0); c_ <= min(cc_ + 1, (M).cn[2] - 1); ++c_) {         \
+                    int id_ = (a_ * (M).cn[1] + b_) * (M).cn[2] + c_;                             \
+                    for (int j = (M).cell_start[id_]; j < (M).cell_start[id_ + 1]; ++j) { __VA_ARGS__ } \
+                }                                                                                 \
+    } while (0)
+
+// the circle where expanded spheres (ci, Ri) and (cj, Rj) meet, if any
+__device__ __forceinline__ bool circle_of(double4 ci, double Ri, double4 cj, double Rj, double3 &o, double3 &u,
+                                          double &rho)
+{
+    double dx = cj.x - ci.x, dy = cj.y - ci.y, dz = cj.z - ci.z;
+    double D2 = dx * dx + dy * dy + dz * dz;
+    double S = Ri + Rj;
+    if (!(D2 < S * S)) return false;
+    double D = sqrt(D2);
+    if (!(D > fabs(Ri - Rj))) return false;
+    double a = (D2 + Ri * Ri - Rj * Rj) / (2.0 * D);
+    double rho2 = Ri * Ri - a * a;
+    if (!(rho2 > 0.0)) return false;
+    u = make_double3(dx / D, dy / D, dz / D);
+    o = make_double3(ci.x + a * u.x, ci.y + a * u.y, ci.z + a * u.z);
+    rho = sqrt(rho2);
+    return true;
+}
+
+__global__ void k_nb_count(Model M, int *__restrict__ nb_count, int *__restrict__ circle_count,
+                           uint8_t *__restrict__ contained)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M.n_atoms) return;
+    double4 ci = M.atom[i];
+    double Ri = ci.w + M.rp;
+    int nb = 0, nc = 0;
+    uint8_t inside = 0;
+    FOR_NEIGHBOUR_CELLS(M, ci.x, ci.y, ci.z, j, {
+        if (j != i) {
+            double4 cj = M.atom[j];
+            double Rj = cj.w + M.rp;
+            double dx = cj.x - ci.x, dy = cj.y - ci.y, dz = cj.z - ci.z;
+            double D2 = dx * dx + dy * dy + dz * dz;
+            double S = Ri + Rj;
+            if (D2 < S * S) {
+                ++nb;
+                double3 o, u;
+                double rho;
+                if (circle_of(ci, Ri, cj, Rj, o, u, rho)) ++nc;
+                else if (Rj >= Ri && sqrt(D2) <= Rj - Ri) inside = 1;  // ball i inside ball j
+            }
+        }
+    });
+    nb_count[i] = nb;
+    circle_count[i] = nc;
+    contained[i] = inside;
+}
+
+int launch_nb_count(const Model &M, int *nb_count, int *circle_count, uint8_t *contained, cudaStream_t st)
+{
+    if (M.n_atoms <= 0) return 0;
+    k_nb_count<<<(M.n_atoms + 127) / 128, 128, 0, st>>>(M, nb_count, circle_count, contained);
+    return 1;
+}
+
+__global__ void k_nb_fill(Model M, int *__restrict__ nb_list)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M.n_atoms) return;
+    double4 ci = M.atom[i];
+    double Ri = ci.w + M.rp;
+    int w = M.nb_start[i];
+    FOR_NEIGHBOUR_CELLS(M, ci.x, ci.y, ci.z, j, {
+        if (j != i) {
+            double4 cj = M.atom[j];
+            double Rj = cj.w + M.rp;
+            double dx = cj.x - ci.x, dy = cj.y - ci.y, dz = cj.z - ci.z;
+            double S = Ri + Rj;
+            if (dx * dx + dy * dy + dz * dz < S * S) nb_list[w++] = j;
+        }
+    });
+}
+
+int launch_nb_fill(const Model &M, int *nb_list, cudaStream_t st)
+{
+    if (M.n_atoms <= 0) return 0;
+    k_nb_fill<<<(M.n_atoms + 127) / 128, 128, 0, st>>>(M, nb_list);
+    return 1;
+}
+
+__global__ void k_pair_count(Model M, int *__restrict__ pair_count)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M.n_atoms) return;
+    double4 ci = M.atom[i];
+    double Ri = ci.w + M.rp;
+    int c = 0;
+    for (int t = M.nb_start[i]; t < M.nb_start[i + 1]; ++t) {
+        int j = M.nb_list[t];
+        if (j <= i) continue;
+        double4 cj = M.atom[j];
+        double3 o, u;
+        double rho;
+        if (circle_of(ci, Ri, cj, cj.w + M.rp, o, u, rho)) ++c;
+    }
+    pair_count[i] = c;
+}
+
+int launch_pair_count(const Model &M, int *pair_count, cudaStream_t st)
+{
+    if (M.n_atoms <= 0) return 0;
+    k_pair_count<<<(M.n_atoms + 127) / 128, 128, 0, st>>>(M, pair_count);
+    return 1;
+}
+
+__global__ void k_pair_fill(Model M, const int *__restrict__ pair_start, double4 *__restrict__ pair_o,
+                            double4 *__restrict__ pair_u, int2 *__restrict__ pair_ij)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M.n_atoms) return;
+    double4 ci = M.atom[i];
+    double Ri = ci.w + M.rp;
+    int w = pair_start[i];
+    for (int t = M.nb_start[i]; t < M.nb_start[i + 1]; ++t) {
+        int j = M.nb_list[t];
+        if (j <= i) continue;
+        double4 cj = M.atom[j];
+        double3 o, u;
+        double rho;
+        if (circle_of(ci, Ri, cj, cj.w + M.rp, o, u, rho)) {
+            pair_o[w] = make_double4(o.x, o.y, o.z, rho);
+            pair_u[w] = make_double4(u.x, u.y, u.z, 0.0);
+            pair_ij[w] = make_int2(i, j);
+            ++w;
+        }
+    }
+}
+
+int launch_pair_fill(const Model &M, const int *pair_start, double4 *pair_o, double4 *pair_u, int2 *pair_ij,
+                      cudaStream_t st)
+{
+    if (M.n_atoms <= 0) return 0;
+    k_pair_fill<<<(M.n_atoms + 127) / 128, 128, 0, st>>>(M, pair_start, pair_o, pair_u, pair_ij);
+    return 1;
+}
+
+// --------------------------------------------------------------------------
+// free arcs and free triple points
+// --------------------------------------------------------------------------
+struct CircleFrame {
+    double3 o, u, v1, v2;
+    double rho;
+};
+
+__device__ __forceinline__ CircleFrame frame_of(double4 po, double4 pu)
+{
+    CircleFrame f;
+    f.o = make_double3(po.x, po.y, po.z);
+    f.u = make_double3(pu.x, pu.y, pu.z);
+    f.rho = po.w;
+    // a unit vector normal to u
+    double3 t = fabs(f.u.x) > 0.6 ? make_double3(0.0, 1.0, 0.0) : make_double3(1.0, 0.0, 0.0);
+    double3 v = make_double3(f.u.y * t.z - f.u.z * t.y, f.u.z * t.x - f.u.x * t.z, f.u.x * t.y - f.u.y * t.x);
+    double nv = sqrt(v.x * v.x + v.y * v.y + v.z * v.z);
+    f.v1 = make_double3(v.x / nv, v.y / nv, v.z / nv);
+    f.v2 = make_double3(f.u.y * f.v1.z - f.u.z * f.v1.y, f.u.z * f.v1.x - f.u.x * f.v1.z,
+                        f.u.x * f.v1.y - f.u.y * f.v1.x);
+    return f;
+}
+
+// Coverage of the circle by ball (ck, Rk): 0 none, 1 partial (end points
+// qa, qb returned), 2 the whole circle.
+__device__ __forceinline__ int cover_of(const CircleFrame &f, double4 ck, double Rk, double3 &qa, double3 &qb)
+{
+    double dx = ck.x - f.o.x, dy = ck.y - f.o.y, dz = ck.z - f.o.z;
+    double d1 = dx * f.v1.x + dy * f.v1.y + dz * f.v1.z;
+    double d2 = dx * f.v2.x + dy * f.v2.y + dz * f.v2.z;
+    double dd = dx * dx + dy * dy + dz * dz;
+    double A = sqrt(d1 * d1 + d2 * d2);
+    // |q(phi) - c_k|^2 = rho^2 + |d|^2 - 2 rho A cos(phi - psi); covered iff < R_k^2
+    double num = f.rho * f.rho + dd - Rk * Rk;
+    double den = 2.0 * f.rho * A;
+    if (num >= den) return 0;
+    if (num < -den) return 2;
+    double T = num / den;
+    double s = sqrt(fmax(0.0, 1.0 - T * T));
+    double3 ep = make_double3((d1 * f.v1.x + d2 * f.v2.x) / A, (d1 * f.v1.y + d2 * f.v2.y) / A,
+                              (d1 * f.v1.z + d2 * f.v2.z) / A);
+    double3 en = make_double3(f.u.y * ep.z - f.u.z * ep.y, f.u.z * ep.x - f.u.x * ep.z, f.u.x * ep.y - f.u.y * ep.x);
+    qa = make_double3(f.o.x + f.rho * (T * ep.x + s * en.x), f.o.y + f.rho * (T * ep.y + s * en.y),
+                      f.o.z + f.rho * (T * ep.z + s * en.z));
+    qb = make_double3(f.o.x + f.rho * (T * ep.x - s * en.x), f.o.y + f.rho * (T * ep.y - s * en.y),
+                      f.o.z + f.rho * (T * ep.z - s * en.z));
+    return 1;
+}
+
+__device__ __forceinline__ bool common_nb(const Model &M, int k, int i, int j, double4 cj, double Rj)
+{
+    if (k == i || k == j) return false;
+    double4 ck = M.atom[k];
+    double Rk = ck.w + M.rp;
+    double dx = ck.x - cj.x, dy = ck.y - cj.y, dz = ck.z - cj.z;
+    double S = Rk + Rj;
+    return dx * dx + dy * dy + dz * dz < S * S;
+}
+
+// the end point q (on sphere k) is free iff no other common neighbour covers it
+__device__ __forceinline__ bool endpoint_free(const Model &M, int i, int j, int k, double4 cj, double Rj, double3 q)
+{
+    for (int t = M.nb_start[i]; t < M.nb_start[i + 1]; ++t) {
+        int m = M.nb_list[t];
+        if (m == k || !common_nb(M, m, i, j, cj, Rj)) continue;
+        double4 cm = M.atom[m];
+        double Rm = cm.w + M.rp;
+        double dx = q.x - cm.x, dy = q.y - cm.y, dz = q.z - cm.z;
+        if (dx * dx + dy * dy + dz * dz < Rm * Rm) return false;
+    }
+    return true;
+}
+
+template <bool EMIT>
+__device__ void arcs_of_pair(const Model &M, int p, uint8_t *pair_free, int *vert_count, const int *vert_start,
+                             double4 *vert)
+{
+    int2 ij = M.pair_ij[p];
+    const int i = ij.x, j = ij.y;
+    CircleFrame f = frame_of(M.pair_o[p], M.pair_u[p]);
+    double4 cj = M.atom[j];
+    double Rj = cj.w + M.rp;
+    bool full = false;
+    int n_partial = 0, n_free_end = 0, n_emit = 0;
+    int w = EMIT ? vert_start[p] : 0;
+    for (int t = M.nb_start[i]; t < M.nb_start[i + 1] && !full; ++t) {
+        int k = M.nb_list[t];
+        if (!common_nb(M, k, i, j, cj, Rj)) continue;
+        double4 ck = M.atom[k];
+        double3 qa, qb;
+        int c = cover_of(f, ck, ck.w + M.rp, qa, qb);
+        if (c == 2) {
+            full = true;
+        } else if (c == 1) {
+            ++n_partial;
+            bool fa = endpoint_free(M, i, j, k, cj, Rj, qa);
+            bool fb = endpoint_free(M, i, j, k, cj, Rj, qb);
+            n_free_end += (int)fa + (int)fb;
+            if (k > j) {  // triple i < j < k: emitted once, from the circle (i, j)
+                if (fa) {
+                    if (EMIT) vert[w + n_emit] = make_double4(qa.x, qa.y, qa.z, 0.0);
+                    ++n_emit;
+                }
+                if (fb) {
+                    if (EMIT) vert[w + n_emit] = make_double4(qb.x, qb.y, qb.z, 0.0);
+                    ++n_emit;
+                }
+            }
+        }
+    }
+    if (!EMIT) {
+        bool has_free = !full && (n_partial == 0 || n_free_end > 0);
+        pair_free[p] = has_free ? 1 : 0;
+        vert_count[p] = full ? 0 : n_emit;
+    }
+}
+
+__global__ void k_arcs(Model M, uint8_t *__restrict__ pair_free, int *__restrict__ vert_count)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= M.n_pairs) return;
+    arcs_of_pair<false>(M, p, pair_free, vert_count, nullptr, nullptr);
+}
+
+__global__ void k_arcs_emit(Model M, const int *__restrict__ vert_start, double4 *__restrict__ vert)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= M.n_pairs) return;
+    if (vert_start[p + 1] == vert_start[p]) return;
+    arcs_of_pair<true>(M, p, nullptr, nullptr, vert_start, vert);
+}
+
+int launch_arcs(const Model &M, uint8_t *pair_free, int *vert_count, cudaStream_t st)
+{
+    if (M.n_pairs <= 0) return 0;
+    k_arcs<<<(M.n_pairs + 127) / 128, 128, 0, st>>>(M, pair_free, vert_count);
+    return 1;
+}
+
+int launch_arcs_emit(const Model &M, const int *vert_start, double4 *vert, cudaStream_t st)
+{
+    if (M.n_pairs <= 0) return 0;
+    k_arcs_emit<<<(M.n_pairs + 127) / 128, 128, 0, st>>>(M, vert_start, vert);
+    return 1;
+}
+
+__global__ void k_faces_init(int n, const int *__restrict__ circle_count, const uint8_t *__restrict__ contained,
+                             uint8_t *__restrict__ face)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    face[i] = (circle_count[i] == 0 && !contained[i]) ? 1 : 0;
+}
+
+__global__ void k_faces_pairs(Model M, uint8_t *__restrict__ face)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= M.n_pairs) return;
+    if (M.pair_free[p]) {
+        int2 ij = M.pair_ij[p];
+        face[ij.x] = 1;
+        face[ij.y] = 1;
+    }
+}
+
+int launch_faces(const Model &M, const int *circle_count, const uint8_t *contained, uint8_t *face, cudaStream_t st)
+{
+    int nl = 0;
+    if (M.n_atoms > 0) ++nl, k_faces_init<<<(M.n_atoms + 255) / 256, 256, 0, st>>>(M.n_atoms, circle_count, contained, face);
+    if (M.n_pairs > 0) ++nl, k_faces_pairs<<<(M.n_pairs + 255) / 256, 256, 0, st>>>(M, face);
+    return nl;
+}
+
+// which = 0: free-arc pairs by circle centre; which = 1: free triple points
+__global__ void k_bin_count(Model M, int which, int *__restrict__ count, int *__restrict__ item_cell)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    int n = which == 0 ? M.n_pairs : M.n_verts;
+    if (p >= n) return;
+    double x, y, z;
+    if (which == 0) {
+        if (!M.pair_free[p]) {
+            item_cell[p] = -1;
+            return;
+        }
+        double4 o = M.pair_o[p];
+        x = o.x; y = o.y; z = o.z;
+    } else {
+        double4 v = M.vert[p];
+        x = v.x; y = v.y; z = v.z;
+    }
+    int a = cell_coord(x, M.clo[0], M.cell, M.cn[0]);
+    int b = cell_coord(y, M.clo[1], M.cell, M.cn[1]);
+    int c = cell_coord(z, M.clo[2], M.cell, M.cn[2]);
+    int id = (a * M.cn[1] + b) * M.cn[2] + c;
+    item_cell[p] = id;
+    atomicAdd(&count[id], 1);
+}
+
+__global__ void k_bin_scatter(int n, const int *__restrict__ item_cell, const int *__restrict__ start,
+                              int *__restrict__ cursor, int *__restrict__ list)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int id = item_cell[p];
+    if (id < 0) return;
+    list[start[id] + atomicAdd(&cursor[id], 1)] = p;
+}
+
+int launch_bin_count(const Model &M, int which, int *count, int *item_cell, cudaStream_t st)
+{
+    int n = which == 0 ? M.n_pairs : M.n_verts;
+    if (n <= 0) return 0;
+    k_bin_count<<<(n + 255) / 256, 256, 0, st>>>(M, which, count, item_cell);
+    return 1;
+}
+
+int launch_bin_scatter(const Model &M, int which, const int *item_cell, const int *start, int *cursor, int *list,
+                        cudaStream_t st)
+{
+    int n = which == 0 ? M.n_pairs : M.n_verts;
+    if (n <= 0) return 0;
+    k_bin_scatter<<<(n + 255) / 256, 256, 0, st>>>(n, item_cell, start, cursor, list);
+    return 1;
+}
+
+}  // namespace eses

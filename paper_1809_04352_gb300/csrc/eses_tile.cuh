@@ -1,0 +1,278 @@
+// eses_tile.cuh -- tile staging and point classification (device code).
+//
+// A tile is 8x8x8 grid points.  Its "region" is the box [x0, x0 + 8h]^3,
+// which holds the tile's points and the first points of the next tiles, so
+// the edges leaving the tile in + directions lie inside it.  Staged into
+// shared memory, in coordinates relative to x0 (FP64 differences, then
+// rounded to the working type):
+//   atoms     with dist(c, region) < r + 2 r_p  (§2.2 locality radius; the
+//             paper's r_p + r_max is too small -- an atom within r + 2 r_p
+//             of x can cover a probe centre that would reach x)
+//   pairs     with a free arc and dist(o, region) < rho + r_p
+//   vertices  free triple points with dist(v, region) < r_p
+//
+// Classification of a point x (Eq. 2): x is outside M iff some free probe
+// centre lies at distance < r_p.  The nearest free point, when it is that
+// close, is the radial projection on a containing expanded sphere (convex
+// patch), the nearest point of a pair circle (saddle), or a free triple point
+// (concave); each candidate counts only if it is free.  Inside a van der
+// Waals ball x is always in M; outside every expanded ball x is free.
+//
+// FP32 filtering: every comparison of a computed squared distance with a
+// threshold t^2 is accepted only if it clears an error bound
+//     e = 2 ((2 t + delta) delta + 1e-6 t^2)
+// where delta bounds the error of the compared vector (positions staged in
+// FP32 carry at most d0, derived points carry the propagated error).  A
+// comparison inside the band leaves the point undecided; undecided points
+// are re-evaluated by the same code in FP64.
+#pragma once
+
+#include <math.h>
+
+#include "eses_internal.cuh"
+
+namespace eses {
+
+template <class T>
+struct alignas(16) P4 {
+    T x, y, z, w;
+};
+
+template <class T>
+struct TileS {
+    P4<T> atom[A_MAX];      // centre (tile frame), vdW radius
+    P4<T> po[P_MAX];        // circle centre (tile frame), rho
+    P4<T> pu[P_MAX];        // circle axis
+    P4<T> vq[V_MAX];        // free triple point (tile frame)
+    int agid[A_MAX];        // sorted atom index
+    int2 pij[P_MAX];        // sorted atom indices of the pair
+    uint8_t aface[A_MAX];   // expanded sphere keeps a free face
+    int na, np, nv, flags;
+};
+
+__device__ __forceinline__ int cell_coord_d(double v, double lo, double cell, int n)
+{
+    int k = (int)floor((v - lo) / cell);
+    return k < 0 ? 0 : (k >= n ? n - 1 : k);
+}
+
+__device__ __forceinline__ double box_dist2(double x, double y, double z, const double *b0, const double *b1)
+{
+    double ex = x < b0[0] ? b0[0] - x : (x > b1[0] ? x - b1[0] : 0.0);
+    double ey = y < b0[1] ? b0[1] - y : (y > b1[1] ? y - b1[1] : 0.0);
+    double ez = z < b0[2] ? b0[2] - z : (z > b1[2] ? z - b1[2] : 0.0);
+    return ex * ex + ey * ey + ez * ez;
+}
+
+__device__ __forceinline__ void tile_coords(const Grid &G, long long tile, int t[3])
+{
+    t[2] = (int)(tile % G.tiles[2]);
+    t[1] = (int)((tile / G.tiles[2]) % G.tiles[1]);
+    t[0] = (int)(tile / ((long long)G.tiles[1] * G.tiles[2]));
+}
+
+// Stage the tile's atoms, free-arc pairs and free vertices (whole block).
+template <class T>
+__device__ void stage_tile(const Model &M, const Grid &G, long long tile, TileS<T> &S, double x0[3])
+{
+    int t[3];
+    tile_coords(G, tile, t);
+    double x1[3];
+    for (int a = 0; a < 3; ++a) {
+        x0[a] = G.lo[a] + G.h * (double)(TILE * t[a]);
+        x1[a] = x0[a] + G.h * (double)TILE;
+    }
+    if (threadIdx.x == 0) {
+        S.na = 0;
+        S.np = 0;
+        S.nv = 0;
+        S.flags = 0;
+    }
+    __syncthreads();
+    int c0[3], c1[3], nc[3];
+    for (int a = 0; a < 3; ++a) {
+        c0[a] = cell_coord_d(x0[a] - G.halo, M.clo[a], M.cell, M.cn[a]);
+        c1[a] = cell_coord_d(x1[a] + G.halo, M.clo[a], M.cell, M.cn[a]);
+        nc[a] = c1[a] - c0[a] + 1;
+    }
+    const int ncell = nc[0] * nc[1] * nc[2];
+    const double tol = 1e-6;
+    const double rp = M.rp;
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+        int cz = c % nc[2], cy = (c / nc[2]) % nc[1], cx = c / (nc[1] * nc[2]);
+        int id = ((c0[0] + cx) * M.cn[1] + (c0[1] + cy)) * M.cn[2] + (c0[2] + cz);
+        for (int k = M.cell_start[id]; k < M.cell_start[id + 1]; ++k) {
+            double4 a = M.atom[k];
+            double reach = a.w + 2.0 * rp + tol;
+            if (box_dist2(a.x, a.y, a.z, x0, x1) < reach * reach) {
+                int s = atomicAdd(&S.na, 1);
+                if (s < A_MAX) {
+                    S.atom[s] = P4<T>{(T)(a.x - x0[0]), (T)(a.y - x0[1]), (T)(a.z - x0[2]), (T)a.w};
+                    S.agid[s] = k;
+                    S.aface[s] = M.atom_face[k];
+                }
+            }
+        }
+        for (int k = M.pcell_start[id]; k < M.pcell_start[id + 1]; ++k) {
+            int p = M.pcell_list[k];
+            double4 o = M.pair_o[p];
+            double reach = o.w + rp + tol;
+            if (box_dist2(o.x, o.y, o.z, x0, x1) < reach * reach) {
+                int s = atomicAdd(&S.np, 1);
+                if (s < P_MAX) {
+                    double4 u = M.pair_u[p];
+                    S.po[s] = P4<T>{(T)(o.x - x0[0]), (T)(o.y - x0[1]), (T)(o.z - x0[2]), (T)o.w};
+                    S.pu[s] = P4<T>{(T)u.x, (T)u.y, (T)u.z, (T)0};
+                    S.pij[s] = M.pair_ij[p];
+                }
+            }
+        }
+        for (int k = M.vcell_start[id]; k < M.vcell_start[id + 1]; ++k) {
+            int v = M.vcell_list[k];
+            double4 q = M.vert[v];
+            double reach = rp + tol;
+            if (box_dist2(q.x, q.y, q.z, x0, x1) < reach * reach) {
+                int s = atomicAdd(&S.nv, 1);
+                if (s < V_MAX) S.vq[s] = P4<T>{(T)(q.x - x0[0]), (T)(q.y - x0[1]), (T)(q.z - x0[2]), (T)0};
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (S.na > A_MAX) { S.flags |= ERR_CAP_ATOMS; S.na = A_MAX; }
+        if (S.np > P_MAX) { S.flags |= ERR_CAP_PAIRS; S.np = P_MAX; }
+        if (S.nv > V_MAX) { S.flags |= ERR_CAP_VERTS; S.nv = V_MAX; }
+    }
+    __syncthreads();
+}
+
+// 1: d2 < t2 for certain; 0: d2 >= t2 for certain; -1: undecided (FP32 only).
+// t is the threshold distance, delta the error bound of the compared vector.
+template <bool FILT, class T>
+__device__ __forceinline__ int lt_sq(T d2, T t2, T t, T delta)
+{
+    if (!FILT) return d2 < t2 ? 1 : 0;
+    T e = T(2) * ((T(2) * t + delta) * delta + T(1e-6) * t2);
+    if (d2 < t2 - e) return 1;
+    if (d2 >= t2 + e) return 0;
+    return -1;
+}
+
+// 1: a < b for certain; 0: a >= b for certain; -1 undecided (error bound e).
+template <bool FILT, class T>
+__device__ __forceinline__ int lt_lin(T a, T b, T e)
+{
+    if (!FILT) return a < b ? 1 : 0;
+    if (a < b - T(2) * e) return 1;
+    if (a >= b + T(2) * e) return 0;
+    return -1;
+}
+
+// Freeness of q against every staged atom but e0, e1 (sorted indices of the
+// atoms whose spheres carry q).  1 free, 0 covered, -1 undecided.
+template <class T, bool FILT>
+__device__ __forceinline__ int free_pt(T qx, T qy, T qz, const TileS<T> &S, int e0, int e1, T rp, T delta)
+{
+    int res = 1;
+    for (int k = 0; k < S.na; ++k) {
+        int g = S.agid[k];
+        if (g == e0 || g == e1) continue;
+        P4<T> c = S.atom[k];
+        T dx = qx - c.x, dy = qy - c.y, dz = qz - c.z;
+        T R = c.w + rp;
+        int t = lt_sq<FILT>(dx * dx + dy * dy + dz * dz, R * R, R, delta);
+        if (t == 1) return 0;
+        if (t < 0) res = -1;
+    }
+    return res;
+}
+
+// Label of the point (x,y,z) in the tile frame: 1 if no free probe centre lies
+// at distance < thr (thr = r_p for Eq. 2), 0 otherwise, 2 undecided (FP32).
+template <class T, bool FILT>
+__device__ int classify_pt(T x, T y, T z, const TileS<T> &S, T rp, T thr, T d0)
+{
+    const T thr2 = thr * thr;
+    bool in_sas = false, unsure_sas = false;
+    for (int a = 0; a < S.na; ++a) {
+        P4<T> c = S.atom[a];
+        T dx = x - c.x, dy = y - c.y, dz = z - c.z;
+        T d2 = dx * dx + dy * dy + dz * dz;
+        T r = c.w, R = c.w + rp;
+        if (lt_sq<FILT>(d2, r * r, r, d0) == 1) return 1;  // inside a van der Waals ball
+        int s = lt_sq<FILT>(d2, R * R, R, d0);
+        if (s == 1) in_sas = true;
+        else if (s < 0) unsure_sas = true;
+    }
+    if (!in_sas) return unsure_sas ? 2 : 0;  // free point: dist 0
+    bool unsure = false;
+    // concave: free triple points
+    for (int v = 0; v < S.nv; ++v) {
+        P4<T> q = S.vq[v];
+        T dx = x - q.x, dy = y - q.y, dz = z - q.z;
+        int t = lt_sq<FILT>(dx * dx + dy * dy + dz * dz, thr2, thr, d0);
+        if (t == 1) return 0;
+        if (t < 0) unsure = true;
+    }
+    // convex: radial projection on an expanded sphere that (nearly) contains x
+    for (int a = 0; a < S.na; ++a) {
+        if (!S.aface[a]) continue;
+        P4<T> c = S.atom[a];
+        T dx = x - c.x, dy = y - c.y, dz = z - c.z;
+        T d2 = dx * dx + dy * dy + dz * dz;
+        T R = c.w + rp;
+        if (lt_sq<FILT>(d2, R * R, R, d0) == 0) continue;
+        T d = sqrt(d2);
+        if (d <= T(1e-3)) {
+            if (FILT) unsure = true;
+            continue;  // x at a centre is inside its vdW ball (returned above)
+        }
+        T wd = fabs(R - d);  // distance to the projection
+        int tw = lt_lin<FILT>(wd, thr, d0 + T(1e-6) * R);
+        if (tw == 0) continue;
+        T s = R / d;
+        T qx = c.x + s * dx, qy = c.y + s * dy, qz = c.z + s * dz;
+        T dq = FILT ? d0 * (T(1) + T(2) * R / d) + T(1e-6) * R : T(0);
+        int f = free_pt<T, FILT>(qx, qy, qz, S, S.agid[a], -1, rp, dq + d0);
+        if (f == 1 && tw == 1) return 0;
+        if (f != 0) unsure = true;
+    }
+    // saddle: nearest point of every free-arc circle
+    for (int p = 0; p < S.np; ++p) {
+        P4<T> o = S.po[p];
+        P4<T> u = S.pu[p];
+        T yx = x - o.x, yy = y - o.y, yz = z - o.z;
+        T zc = yx * u.x + yy * u.y + yz * u.z;
+        T wx = yx - zc * u.x, wy = yy - zc * u.y, wz = yz - zc * u.z;
+        T w2 = wx * wx + wy * wy + wz * wz;
+        T nw = sqrt(w2);
+        T e1 = nw - o.w;
+        T dist2 = e1 * e1 + zc * zc;
+        T dw = FILT ? T(2) * d0 + T(2e-6) * (nw + fabs(zc)) : T(0);
+        int t = lt_sq<FILT>(dist2, thr2, thr, T(1.5) * dw + T(1e-6));
+        if (t == 0) continue;
+        if (FILT && nw < T(1e-3)) {
+            unsure = true;  // x near the circle's axis: the nearest point is ill-conditioned
+            continue;
+        }
+        T qx, qy, qz;
+        if (w2 > T(0)) {
+            T k = o.w / nw;
+            qx = o.x + k * wx; qy = o.y + k * wy; qz = o.z + k * wz;
+        } else {
+            // x on the axis: every circle point is nearest; take one
+            T ax = fabs(u.x) > T(0.6) ? T(0) : T(1), ay = fabs(u.x) > T(0.6) ? T(1) : T(0);
+            T vx = u.y * T(0) - u.z * ay, vy = u.z * ax - u.x * T(0), vz = u.x * ay - u.y * ax;
+            T nv = sqrt(vx * vx + vy * vy + vz * vz);
+            qx = o.x + o.w * vx / nv; qy = o.y + o.w * vy / nv; qz = o.z + o.w * vz / nv;
+        }
+        T dq = FILT ? o.w * T(2) * dw / nw + d0 + T(1e-6) * o.w : T(0);
+        int2 ij = S.pij[p];
+        int f = free_pt<T, FILT>(qx, qy, qz, S, ij.x, ij.y, rp, dq + d0);
+        if (f == 1 && t == 1) return 0;
+        if (f != 0) unsure = true;
+    }
+    return unsure ? 2 : 1;
+}
+
+}  // namespace eses

@@ -1,0 +1,259 @@
+"""Thin Python binding of the libeses C ABI (include/eses.h).
+
+Argument marshalling only: every function calls the C entry point of the same
+name, and every step of the surface computation runs in the CUDA kernels of
+libeses.so.  The library must have been built (``paper_1809_04352_gb300.build``);
+loading fails loudly otherwise -- there is no CPU fallback.
+
+Host arrays are numpy arrays; device arrays may be given as raw pointers
+(int) or as objects exposing ``data_ptr()`` (torch CUDA tensors).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ESES_OK = 0
+ESES_EINVAL = -1
+ESES_ENOMEM = -2
+ESES_ECUDA = -3
+ESES_ETIMEOUT = -4
+ESES_ECAPACITY = -5
+ESES_ESTATE = -6
+ESES_EROOT = -7
+
+ESES_OPT_BLOCK_PTS = 1
+ESES_OPT_PRECISION = 2
+ESES_OPT_STREAM = 3
+ESES_OPT_SYNC = 4
+ESES_OPT_PROFILE = 5
+
+ESES_PREC_FP64 = 0
+ESES_PREC_FP32_FILTERED = 1
+
+STAT_NAMES = ["points", "tiles", "work_tiles", "circle_pairs", "free_arc_pairs", "free_vertices", "band_points",
+              "crossing_edges", "root_failures", "inside_points", "kernel_launches"]
+
+# every exported C symbol, as declared in include/eses.h
+SYMBOLS = ["eses_create", "eses_create_device", "eses_set_option", "eses_run", "eses_grid", "eses_labels",
+           "eses_labels_device", "eses_num_intersections", "eses_intersections", "eses_intersections_device",
+           "eses_area_volume", "eses_stats", "eses_stage_times", "eses_last_error", "eses_destroy"]
+STAGE_NAMES = ["binning", "pairs", "arcs", "classify", "band", "edge_count", "edge_solve", "reduce"]
+
+_lib = None
+
+
+class EsesError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libeses error {code}: {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libeses.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                           "(paper_1809_04352_gb300.build.build())")
+    lib = ctypes.CDLL(path)
+    P, i64, d, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    lib.eses_create.argtypes = [P, P, i64, d, d, d, PP]
+    lib.eses_create_device.argtypes = [P, P, i64, d, d, d, PP]
+    lib.eses_set_option.argtypes = [P, ci, i64]
+    lib.eses_run.argtypes = [P]
+    lib.eses_grid.argtypes = [P, P, P]
+    lib.eses_labels.argtypes = [P, P]
+    lib.eses_labels_device.argtypes = [P, PP]
+    lib.eses_num_intersections.argtypes = [P, ci, P]
+    lib.eses_intersections.argtypes = [P, ci, P, P, P, P, P]
+    lib.eses_intersections_device.argtypes = [P, ci, PP, PP, PP, PP, PP]
+    lib.eses_area_volume.argtypes = [P, P, P]
+    lib.eses_stats.argtypes = [P, P, ci]
+    lib.eses_stage_times.argtypes = [P, P, ci]
+    lib.eses_last_error.argtypes = [P]
+    lib.eses_last_error.restype = ctypes.c_char_p
+    lib.eses_destroy.argtypes = [P]
+    lib.eses_destroy.restype = None
+    for name in SYMBOLS:
+        if name not in ("eses_last_error", "eses_destroy"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return ctypes.c_void_p(a)
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc: int, ctx=None):
+    if rc != ESES_OK:
+        raise EsesError(rc, eses_last_error(ctx))
+
+
+def eses_last_error(ctx=None) -> str:
+    msg = load().eses_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+def eses_create(xyz, radii, r_p: float, h: float, margin: float):
+    """Host atoms (n,3) float64 and radii (n,) float64 -> context handle."""
+    lib = load()
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    radii = np.ascontiguousarray(radii, dtype=np.float64).reshape(-1)
+    if xyz.shape[0] != radii.shape[0]:
+        raise ValueError("xyz and radii disagree in length")
+    out = ctypes.c_void_p()
+    _check(lib.eses_create(_ptr(xyz), _ptr(radii), xyz.shape[0], r_p, h, margin, ctypes.byref(out)))
+    return out
+
+
+def eses_create_device(xyz, radii, n_atoms: int, r_p: float, h: float, margin: float):
+    """Device atoms (pointer or CUDA tensor, n*3 float64) and radii -> context handle."""
+    lib = load()
+    out = ctypes.c_void_p()
+    _check(lib.eses_create_device(_ptr(xyz), _ptr(radii), int(n_atoms), r_p, h, margin, ctypes.byref(out)))
+    return out
+
+
+def eses_set_option(ctx, key: int, value: int):
+    _check(load().eses_set_option(ctx, key, int(value)), ctx)
+
+
+def eses_run(ctx):
+    _check(load().eses_run(ctx), ctx)
+
+
+def eses_grid(ctx):
+    dims = np.zeros(3, np.int64)
+    origin = np.zeros(3, np.float64)
+    _check(load().eses_grid(ctx, _ptr(dims), _ptr(origin)), ctx)
+    return dims, origin
+
+
+def eses_labels(ctx, out=None):
+    dims, _ = eses_grid(ctx)
+    if out is None:
+        out = np.empty(tuple(int(v) for v in dims), np.int8)
+    _check(load().eses_labels(ctx, _ptr(out)), ctx)
+    return out
+
+
+def eses_labels_device(ctx) -> int:
+    p = ctypes.c_void_p()
+    _check(load().eses_labels_device(ctx, ctypes.byref(p)), ctx)
+    return int(p.value or 0)
+
+
+def eses_num_intersections(ctx, axis: int) -> int:
+    n = np.zeros(1, np.int64)
+    _check(load().eses_num_intersections(ctx, axis, _ptr(n)), ctx)
+    return int(n[0])
+
+
+def eses_intersections(ctx, axis: int, fp32: bool = True):
+    """Host copies of one axis' intersections: dict of numpy arrays."""
+    n = eses_num_intersections(ctx, axis)
+    idx = np.empty(n, np.int64)
+    tau = np.empty(n, np.float64)
+    nrm = np.empty((n, 3), np.float64)
+    t32 = np.empty(n, np.float32) if fp32 else None
+    n32 = np.empty((n, 3), np.float32) if fp32 else None
+    if n:
+        _check(load().eses_intersections(ctx, axis, _ptr(idx), _ptr(tau), _ptr(nrm), _ptr(t32), _ptr(n32)), ctx)
+    out = {"idx": idx, "tau": tau, "normal": nrm}
+    if fp32:
+        out["tau32"] = t32
+        out["normal32"] = n32
+    return out
+
+
+def eses_intersections_device(ctx, axis: int):
+    ps = [ctypes.c_void_p() for _ in range(5)]
+    _check(load().eses_intersections_device(ctx, axis, *[ctypes.byref(p) for p in ps]), ctx)
+    return tuple(int(p.value or 0) for p in ps)
+
+
+def eses_area_volume(ctx):
+    a = np.zeros(1, np.float64)
+    v = np.zeros(1, np.float64)
+    _check(load().eses_area_volume(ctx, _ptr(a), _ptr(v)), ctx)
+    return float(a[0]), float(v[0])
+
+
+def eses_stats(ctx) -> dict:
+    out = np.zeros(len(STAT_NAMES), np.int64)
+    _check(load().eses_stats(ctx, _ptr(out), len(STAT_NAMES)), ctx)
+    return dict(zip(STAT_NAMES, (int(v) for v in out)))
+
+
+def eses_stage_times(ctx) -> dict:
+    out = np.zeros(len(STAGE_NAMES), np.float64)
+    _check(load().eses_stage_times(ctx, _ptr(out), len(STAGE_NAMES)), ctx)
+    return dict(zip(STAGE_NAMES, (float(v) for v in out)))
+
+
+def eses_destroy(ctx):
+    if ctx:
+        load().eses_destroy(ctx)
+
+
+class Surface:
+    """Convenience wrapper: one molecule, one context."""
+
+    def __init__(self, xyz, radii, r_p=1.4, h=0.5, margin=1.0, precision=ESES_PREC_FP32_FILTERED):
+        self.ctx = eses_create(xyz, radii, r_p, h, margin)
+        eses_set_option(self.ctx, ESES_OPT_PRECISION, precision)
+
+    def run(self):
+        eses_run(self.ctx)
+        return self
+
+    def grid(self):
+        return eses_grid(self.ctx)
+
+    def labels(self):
+        return eses_labels(self.ctx)
+
+    def intersections(self, axis):
+        return eses_intersections(self.ctx, axis)
+
+    def area_volume(self):
+        return eses_area_volume(self.ctx)
+
+    def stats(self):
+        return eses_stats(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            eses_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,208 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Bar: labels bit-exact; every crossing edge present on both sides; the
+intersection point within 1e-6 A (tau * h); normals within 1e-6; area and
+volume to 1e-9 relative (the same sums in another order).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1809_04352_gb300 import build as libbuild
+from paper_1809_04352_gb300 import eses, inputs
+
+pytestmark = pytest.mark.gpu
+
+TAU_TOL_A = 1e-6
+NRM_TOL = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    libbuild.build()
+    return eses.load()
+
+
+def gpu_run(xyz, rad, rp, h, margin, precision=eses.ESES_PREC_FP32_FILTERED, profile=False):
+    ctx = eses.eses_create(xyz, rad, rp, h, margin)
+    try:
+        eses.eses_set_option(ctx, eses.ESES_OPT_PRECISION, precision)
+        if profile:
+            eses.eses_set_option(ctx, eses.ESES_OPT_PROFILE, 1)
+        eses.eses_run(ctx)
+        dims, lo = eses.eses_grid(ctx)
+        out = dict(dims=dims, lo=lo, labels=eses.eses_labels(ctx), stats=eses.eses_stats(ctx))
+        out["area"], out["volume"] = eses.eses_area_volume(ctx)
+        out["axes"] = [eses.eses_intersections(ctx, a) for a in range(3)]
+        if profile:
+            out["stages"] = eses.eses_stage_times(ctx)
+        return out
+    finally:
+        eses.eses_destroy(ctx)
+
+
+def compare(g, o, h, check_area=True):
+    assert np.array_equal(g["dims"], o.dims)
+    assert np.array_equal(g["lo"], o.lo)
+    assert g["stats"]["root_failures"] == 0
+    L = g["labels"]
+    assert L.dtype == np.int8
+    mism = np.argwhere(L != o.labels)
+    assert mism.shape[0] == 0, f"{mism.shape[0]} label mismatches, first {mism[:5].tolist()}"
+    for a in range(3):
+        ga = g["axes"][a]
+        order = np.argsort(ga["idx"], kind="stable")
+        gi, gt, gn = ga["idx"][order], ga["tau"][order], ga["normal"][order]
+        assert np.array_equal(gi, o.idx[a])
+        if len(gi):
+            assert np.abs(gt - o.tau[a]).max() * h < TAU_TOL_A
+            assert np.abs(gn - o.normal[a]).max() < NRM_TOL
+            # FP32 copies agree with the FP64 outputs to FP32 rounding
+            assert np.abs(ga["tau32"][order] - gt).max() < 1e-6
+            assert np.abs(ga["normal32"][order] - gn).max() < 1e-6
+    if check_area:
+        assert abs(g["area"] - o.area) <= 1e-9 * max(o.area, 1.0)
+        assert abs(g["volume"] - o.volume) <= 1e-9 * max(o.volume, 1.0)
+
+
+def _cluster(n, seed):
+    rng = np.random.default_rng(seed)
+    xyz = [np.zeros(3)]
+    while len(xyz) < n:
+        base = xyz[rng.integers(len(xyz))]
+        v = rng.standard_normal(3)
+        v /= np.linalg.norm(v)
+        cand = base + v * rng.uniform(2.2, 3.4)
+        if min(np.linalg.norm(cand - p) for p in xyz) > 1.8:
+            xyz.append(cand)
+    rad = inputs.RADII[rng.choice(4, size=n, p=inputs.FREQS)]
+    return np.array(xyz), rad
+
+
+SMALL = {
+    "one-atom": (np.array([[0.3, -0.2, 0.11]]), np.array([1.7]), 1.4, 0.25, 1.0),
+    "two-atoms": (np.array([[0.0, 0, 0], [2.1, 2.4, 0.9]]), np.array([1.7, 1.55]), 1.4, 0.2, 1.0),
+    "two-spindle": (np.array([[0.1, 0, 0], [4.0, 3.9, 1.3]]), np.array([1.52, 1.8]), 1.4, 0.2, 1.0),
+    "cluster-4": _cluster(4, 2) + (1.4, 0.25, 1.0),
+    "cluster-10": _cluster(10, 4) + (1.4, 0.2, 0.8),
+    "far-apart": (np.array([[0.0, 0, 0], [20.0, 0, 0], [0, 15.0, 3.0]]), np.array([1.7, 1.5, 1.8]), 1.4, 0.5, 0.5),
+    "probe-zero": _cluster(6, 5) + (0.0, 0.25, 1.0),
+    "big-probe": _cluster(8, 6) + (3.0, 0.3, 1.0),
+}
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+@pytest.mark.parametrize("precision", [eses.ESES_PREC_FP64, eses.ESES_PREC_FP32_FILTERED])
+def test_small_cases_match_oracle(name, precision):
+    xyz, rad, rp, h, margin = SMALL[name]
+    o = oracle.run(xyz, rad, rp, h, margin)
+    g = gpu_run(xyz, rad, rp, h, margin, precision)
+    compare(g, o, h)
+
+
+@pytest.mark.parametrize("precision", [eses.ESES_PREC_FP64, eses.ESES_PREC_FP32_FILTERED])
+def test_plain_200_atoms_matches_oracle(precision):
+    """200-atom free C-alpha walk, r_p 1.4, h 0.5, margin 4 (several tiles, ragged tail)."""
+    wl = inputs.WORKLOADS[1]
+    xyz, rad = inputs.workload_atoms(1)
+    o = oracle.run(xyz, rad, wl.r_p, wl.h, wl.margin, block_pts=64)
+    g = gpu_run(xyz, rad, wl.r_p, wl.h, wl.margin, precision)
+    compare(g, o, wl.h)
+    assert sum(len(x) for x in o.idx) > 1000
+
+
+@pytest.mark.parametrize("h", [0.3, 0.37])
+def test_ragged_grid_matches_oracle(h):
+    xyz, rad = inputs.protein_like(120, 77, inputs.PROTEIN_DENSITY)
+    o = oracle.run(xyz, rad, 1.4, h, 0.8)
+    g = gpu_run(xyz, rad, 1.4, h, 0.8)
+    assert any(int(d) % 8 for d in g["dims"])
+    compare(g, o, h)
+
+
+def test_globule_5000_fp32_equals_fp64_and_sampled_blocks_match_oracle():
+    """The 5,000-atom globule at h = 0.25 (full size, the benchmark's launch
+    configuration): FP32-filtered labels equal the FP64 form's everywhere, and
+    six seeded 64-point blocks match the oracle."""
+    wl = inputs.WORKLOADS[2]
+    xyz, rad = inputs.workload_atoms(2)
+    g32 = gpu_run(xyz, rad, wl.r_p, wl.h, wl.margin, eses.ESES_PREC_FP32_FILTERED)
+    g64 = gpu_run(xyz, rad, wl.r_p, wl.h, wl.margin, eses.ESES_PREC_FP64)
+    assert np.array_equal(g32["labels"], g64["labels"])
+    for a in range(3):
+        o32 = np.argsort(g32["axes"][a]["idx"], kind="stable")
+        o64 = np.argsort(g64["axes"][a]["idx"], kind="stable")
+        assert np.array_equal(g32["axes"][a]["idx"][o32], g64["axes"][a]["idx"][o64])
+        assert np.abs(g32["axes"][a]["tau"][o32] - g64["axes"][a]["tau"][o64]).max() * wl.h < TAU_TOL_A
+    dims = g32["dims"]
+    nb = [oracle.block_count(int(d), 64) for d in dims]
+    rng = np.random.default_rng(2024)
+    # blocks that hold surface: pick among blocks whose centre is within the globule
+    ids = []
+    while len(ids) < 6:
+        b = [int(rng.integers(n)) for n in nb]
+        bid = (b[0] * nb[1] + b[1]) * nb[2] + b[2]
+        lo = np.array(b) * 63
+        sl = g32["labels"][lo[0]:lo[0] + 63, lo[1]:lo[1] + 63, lo[2]:lo[2] + 63]
+        if 0.02 < sl.mean() < 0.9 and bid not in ids:
+            ids.append(bid)
+    o = oracle.run(xyz, rad, wl.r_p, wl.h, wl.margin, block_pts=64, block_ids=ids)
+    m = o.labels >= 0
+    assert m.sum() > 6 * 60 ** 3
+    assert np.array_equal(g32["labels"][m], o.labels[m])
+    for a in range(3):
+        gi = g32["axes"][a]["idx"]
+        sel = m.reshape(-1)[gi]
+        order = np.argsort(gi[sel], kind="stable")
+        assert np.array_equal(gi[sel][order], o.idx[a])
+        assert np.abs(g32["axes"][a]["tau"][sel][order] - o.tau[a]).max() * wl.h < TAU_TOL_A
+        assert np.abs(g32["axes"][a]["normal"][sel][order] - o.normal[a]).max() < NRM_TOL
+
+
+def test_device_pointer_create_matches_host_create():
+    import torch
+    xyz, rad = inputs.protein_like(60, 3)
+    ctx_h = eses.eses_create(xyz, rad, 1.4, 0.4, 1.0)
+    dx = torch.from_numpy(xyz).cuda()
+    dr = torch.from_numpy(rad).cuda()
+    ctx_d = eses.eses_create_device(dx, dr, xyz.shape[0], 1.4, 0.4, 1.0)
+    try:
+        eses.eses_run(ctx_h)
+        eses.eses_run(ctx_d)
+        assert np.array_equal(eses.eses_labels(ctx_h), eses.eses_labels(ctx_d))
+        assert eses.eses_area_volume(ctx_h) == eses.eses_area_volume(ctx_d)
+        # borrowed device pointer holds the same labels
+        p = eses.eses_labels_device(ctx_d)
+        assert p != 0
+    finally:
+        eses.eses_destroy(ctx_h)
+        eses.eses_destroy(ctx_d)
+
+
+def test_repeated_runs_are_deterministic():
+    xyz, rad = inputs.protein_like(200, 8, inputs.PROTEIN_DENSITY)
+    ctx = eses.eses_create(xyz, rad, 1.4, 0.3, 1.0)
+    try:
+        res = []
+        for _ in range(3):
+            eses.eses_run(ctx)
+            res.append((eses.eses_labels(ctx).copy(), [eses.eses_intersections(ctx, a) for a in range(3)],
+                        eses.eses_area_volume(ctx)))
+        for r in res[1:]:
+            assert np.array_equal(r[0], res[0][0])
+            for a in range(3):
+                for k in ("idx", "tau", "normal"):
+                    assert np.array_equal(r[1][a][k], res[0][1][a][k])
+            assert r[2] == res[0][2]
+    finally:
+        eses.eses_destroy(ctx)
+
+
+def test_stage_times_reported():
+    xyz, rad = inputs.protein_like(100, 9)
+    g = gpu_run(xyz, rad, 1.4, 0.5, 1.0, profile=True)
+    st = g["stages"]
+    assert set(st) == set(eses.STAGE_NAMES)
+    assert all(v >= 0.0 for v in st.values()) and st["classify"] > 0.0
