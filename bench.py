@@ -172,6 +172,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-blocks", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="only the warm-up and device-resident steps (for ncu captures); prints stage times")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -235,6 +237,12 @@ def main():
     barrier()
     clk = clocks.stop()
     st = eses.eses_stats(ctx)
+    if args.profile_only:
+        print(json.dumps({"profile_only": True, "ms_per_step": statistics.mean(times),
+                          "stages_ms": {k: statistics.mean(s[k] for s in stages) for k in stages[0]},
+                          "kernel_launches_per_step": st["kernel_launches"], "points": npts}))
+        eses.eses_destroy(ctx)
+        return
     total_s = sum(times) / 1e3
     if world > 1:
         t = torch.tensor([total_s], device="cuda")

@@ -10,7 +10,9 @@
  *
  * The SES is the boundary of the union of all probe balls of radius r_p whose
  * centres are at distance >= r_i + r_p from every atom (§1).  A grid point x
- * is inside (label 1) iff dist(x, free probe centres) >= r_p.
+ * is inside (label 1) iff dist(x, free probe centres) >= r_p.  r_p must be
+ * > 0: at r_p = 0 that set is the whole space and the surface degenerates to
+ * the van der Waals surface.
  *
  * Grid (Eq. 2, §2.3): point (i,j,k) sits at origin + h*(i,j,k) with
  *   origin_a = min_i(c_ia - r_i) - margin,
@@ -54,7 +56,7 @@ extern "C" {
 typedef struct eses_ctx eses_ctx;
 
 #define ESES_OK 0
-#define ESES_EINVAL (-1)    /* invalid argument (sizes, non-finite input, r <= 0, r_p < 0, h <= 0, margin < h) */
+#define ESES_EINVAL (-1)    /* invalid argument (sizes, non-finite input, r <= 0, r_p <= 0, h <= 0, margin < h) */
 #define ESES_ENOMEM (-2)    /* host or device allocation failed */
 #define ESES_ECUDA (-3)     /* a CUDA call failed */
 #define ESES_ETIMEOUT (-4)  /* a bounded device wait expired */
@@ -134,6 +136,30 @@ int eses_stats(const eses_ctx *ctx, int64_t *out, int n);
  * [6] root solve and normals, [7] area/volume reduction.  Stages that wait
  * for a host read of a list total include that wait. */
 int eses_stage_times(const eses_ctx *ctx, double *ms, int n);
+
+/* Records of crossing edges whose root solve failed in the last run (at most
+ * 8 are kept), host output of max_records * 24 int64: [0] axis, [1..3] lower
+ * point (i,j,k), [4] label of the lower point, [5..7] staged atoms, circle
+ * pairs and triple points of its tile, [8..23] solver counters (sphere
+ * roots, covered sphere witnesses, probe-sphere roots, tori tested, quartic
+ * roots, far-branch roots, covered torus witnesses, candidates, candidates
+ * rejected by the first-root test, then the first candidates' tau*h*1e9).
+ * *n_out receives the number of records copied. */
+int eses_root_failures(const eses_ctx *ctx, int64_t *records, int max_records, int *n_out);
+
+/* Patch model of the last run (§1: saddle patches lie on the circles where
+ * two expanded spheres meet, concave patches are centred on free triple
+ * points): number of circle pairs, of pairs whose circle keeps a free arc,
+ * and of free triple points (host outputs). */
+int eses_patch_counts(const eses_ctx *ctx, int64_t *n_pairs, int64_t *n_free_pairs, int64_t *n_vertices);
+
+/* Copy the patch model to host memory; every output may be NULL and is sized
+ * from eses_patch_counts: pair_atoms (2 int32 per pair, original atom
+ * indices, first < second in the library's sorted order), pair_free (1 per
+ * pair), pair_circle (7 doubles per pair: centre, unit axis from the first
+ * to the second atom, radius), vertices (3 doubles per free triple point). */
+int eses_patch_data(const eses_ctx *ctx, int32_t *pair_atoms, uint8_t *pair_free, double *pair_circle,
+                    double *vertices);
 
 /* Last error message of the context (or of the last failed create when ctx
  * is NULL).  Never NULL. */

@@ -74,7 +74,7 @@ def _load():
         lib.eo_distance_points.restype = ctypes.c_int
         lib.eo_label_points.argtypes = [P, P, i64, d, P, i64, ctypes.c_int, P]
         lib.eo_label_points.restype = ctypes.c_int
-        lib.eo_model_stats.argtypes = [P, P, i64, d, P, P, P, i64]
+        lib.eo_model_stats.argtypes = [P, P, i64, d, P, P, P, i64, P, i64]
         lib.eo_model_stats.restype = ctypes.c_int
         lib.eo_num_threads.restype = ctypes.c_int
         lib.eo_flop_counts.argtypes = [P, P, i64, d, d, d, ctypes.c_int, P]
@@ -198,29 +198,21 @@ def label_points(xyz, radii, r_p: float, pts, brute: bool = False) -> np.ndarray
     return out
 
 
-def model_stats(xyz, radii, r_p: float, max_vertices: int = 0):
+def model_stats(xyz, radii, r_p: float, max_vertices: int = 0, max_pairs: int = 0):
+    """Circle pairs and free triple points of the whole molecule.
+
+    Returns (n_pairs, n_free_vertices, vertices (<= max_vertices, 3) or None,
+    pairs (<= max_pairs, 2) original atom indices or None)."""
     lib = _load()
     xyz, radii = _atoms(xyz, radii)
     npairs = np.zeros(1, np.int64)
     nverts = np.zeros(1, np.int64)
     buf = np.empty((max(max_vertices, 1), 3), np.float64)
+    pbuf = np.empty((max(max_pairs, 1), 2), np.int64)
     lib.eo_model_stats(_ptr(xyz), _ptr(radii), xyz.shape[0], r_p, _ptr(npairs), _ptr(nverts),
-                       _ptr(buf) if max_vertices else None, max_vertices)
+                       _ptr(buf) if max_vertices else None, max_vertices, _ptr(pbuf) if max_pairs else None, max_pairs)
     nv = int(nverts[0])
+    npr = int(npairs[0])
     verts = buf[: min(nv, max_vertices)] if max_vertices else None
-    return int(npairs[0]), nv, verts
-
-
-FLOP_KEYS = ["points", "sum_reach", "shell_points", "sum_face", "sum_face_x_reach", "sum_arc", "sum_vert",
-             "model_flops"]
-
-
-def flop_counts(xyz, radii, r_p: float, h: float, margin: float, nthreads: int = 0) -> dict:
-    """Algorithmic flop model of the classification over the whole grid."""
-    lib = _load()
-    xyz, radii = _atoms(xyz, radii)
-    out = np.zeros(8, np.int64)
-    rc = lib.eo_flop_counts(_ptr(xyz), _ptr(radii), xyz.shape[0], r_p, h, margin, int(nthreads), _ptr(out))
-    if rc != 0:
-        raise ValueError("invalid parameters")
-    return dict(zip(FLOP_KEYS, (int(v) for v in out)))
+    pairs = pbuf[: min(npr, max_pairs)] if max_pairs else None
+    return npr, nv, verts, pairs

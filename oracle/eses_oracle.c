@@ -513,7 +513,7 @@ int eo_label_points(const double *xyz, const double *r, int64_t n, double rp, co
 
 /* model statistics: number of circle pairs and free triple points */
 int eo_model_stats(const double *xyz, const double *r, int64_t n, double rp, int64_t *n_pairs, int64_t *n_free_vertices,
-                   double *vertices_out, int64_t cap_vertices)
+                   double *vertices_out, int64_t cap_vertices, int64_t *pairs_out, int64_t cap_pairs)
 {
     Model m;
     model_build(&m, xyz, r, NULL, (int)n, rp, rp, 0);
@@ -521,6 +521,9 @@ int eo_model_stats(const double *xyz, const double *r, int64_t n, double rp, int
     *n_free_vertices = m.nv;
     if (vertices_out) {
         for (int v = 0; v < m.nv && v < cap_vertices; ++v) memcpy(vertices_out + 3 * v, m.vq + 3 * v, 3 * sizeof(double));
+    }
+    if (pairs_out) {
+        for (int p = 0; p < m.np && p < cap_pairs; ++p) { pairs_out[2 * p] = m.pi[p]; pairs_out[2 * p + 1] = m.pj[p]; }
     }
     model_free(&m);
     return 0;
@@ -693,6 +696,7 @@ static int cmp_i64(const void *a, const void *b)
 eo_result *eo_run(const double *xyz, const double *r, int64_t n, double rp, double h, double margin, int64_t block_pts,
                   int nthreads, int brute, int instrument, const int64_t *block_ids, int64_t n_block_ids)
 {
+    if (!(rp > 0.0)) return NULL; /* at r_p = 0 the closed set M is the whole space */
     eo_result *res = (eo_result *)calloc(1, sizeof(eo_result));
     if (eo_grid(xyz, r, n, h, margin, res->dims, res->lo) != 0) { free(res); return NULL; }
     res->h = h; res->rp = rp;

@@ -87,6 +87,7 @@ struct eses_ctx {
     DBuf labels, tile_band, tile_edges, edge_start, tile_inside, tile_area, tile_vol;
     DBuf out_idx[3], out_tau[3], out_nrm[3], out_tau32[3], out_nrm32[3];
     DBuf scan_tmp, misc;  // misc: err, n_fail, area/vol, counts
+    DBuf fail_log;
     // results
     bool ran = false;
     long long n_edges[3] = {0, 0, 0};
@@ -125,7 +126,7 @@ int read_total(eses_ctx *c, const int *start, long long n)
 int validate(const double *xyz, const double *r, int64_t n, double rp, double h, double margin, std::string &msg)
 {
     if (n < 1 || n > (int64_t)1 << 30) { msg = "n_atoms must be in [1, 2^30]"; return ESES_EINVAL; }
-    if (!(rp >= 0.0) || !isfinite(rp)) { msg = "r_p must be finite and >= 0"; return ESES_EINVAL; }
+    if (!(rp > 0.0) || !isfinite(rp)) { msg = "r_p must be finite and > 0"; return ESES_EINVAL; }
     if (!(h > 0.0) || !isfinite(h)) { msg = "h must be finite and > 0"; return ESES_EINVAL; }
     if (!(margin >= h) || !isfinite(margin)) { msg = "margin must be finite and >= h"; return ESES_EINVAL; }
     for (int64_t i = 0; i < n; ++i) {
@@ -402,7 +403,8 @@ int run_impl(eses_ctx *c)
     double *tile_area = ensure<double>(c->tile_area, nt);
     double *tile_vol = ensure<double>(c->tile_vol, nt);
     mark(c, ST_EDGE_SOLVE);
-    nl += launch_edge_solve(M, G, labels, edge_start, eo, tile_area, tile_vol, d_fail, d_err, st);
+    long long *fail_log = ensure<long long>(c->fail_log, FAIL_LOG * FAIL_REC);
+    nl += launch_edge_solve(M, G, labels, edge_start, eo, tile_area, tile_vol, d_fail, d_err, fail_log, st);
     mark(c, ST_REDUCE);
     nl += launch_reduce(G, tile_area, tile_vol, tile_inside, labels, d_av, d_counts, st);
     mark(c, NSTAGE);
@@ -424,7 +426,7 @@ int run_impl(eses_ctx *c)
     c->stats[1] = nt;
     c->stats[2] = 0;
     c->stats[3] = np;
-    c->stats[4] = 0;
+    c->stats[4] = -1;  // filled on demand by eses_patch_counts
     c->stats[5] = nv;
     c->stats[6] = 0;
     c->stats[7] = c->n_edges[0] + c->n_edges[1] + c->n_edges[2];
@@ -600,6 +602,78 @@ int eses_stats(const eses_ctx *cc, int64_t *out, int n)
     return ESES_OK;
 }
 
+int eses_root_failures(const eses_ctx *cc, int64_t *records, int max_records, int *n_out)
+{
+    eses_ctx *c = const_cast<eses_ctx *>(cc);
+    if (!c || !n_out || max_records < 0 || (max_records > 0 && !records)) return fail(c, ESES_EINVAL, "bad argument");
+    if (!c->ran) return fail(c, ESES_ESTATE, "no results: call eses_run first");
+    int nf = (int)c->stats[8];
+    int n = std::min(std::min(nf, FAIL_LOG), max_records);
+    *n_out = n;
+    if (n > 0 &&
+        cudaMemcpy(records, c->fail_log.p, sizeof(int64_t) * FAIL_REC * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(c, ESES_ECUDA, "failure log copy failed");
+    return ESES_OK;
+}
+
+int eses_patch_counts(const eses_ctx *cc, int64_t *n_pairs, int64_t *n_free_pairs, int64_t *n_vertices)
+{
+    eses_ctx *c = const_cast<eses_ctx *>(cc);
+    if (!c || !n_pairs || !n_free_pairs || !n_vertices) return fail(c, ESES_EINVAL, "NULL argument");
+    if (!c->ran) return fail(c, ESES_ESTATE, "no results: call eses_run first");
+    const int np = c->M.n_pairs;
+    std::vector<uint8_t> fr((size_t)std::max(np, 1));
+    if (np > 0 && cudaMemcpy(fr.data(), c->pair_free.p, np, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(c, ESES_ECUDA, "copy failed");
+    long long nf = 0;
+    for (int p = 0; p < np; ++p) nf += fr[p] ? 1 : 0;
+    *n_pairs = np;
+    *n_free_pairs = nf;
+    *n_vertices = c->M.n_verts;
+    c->stats[4] = nf;
+    return ESES_OK;
+}
+
+int eses_patch_data(const eses_ctx *cc, int32_t *pair_atoms, uint8_t *pair_free, double *pair_circle,
+                    double *vertices)
+{
+    eses_ctx *c = const_cast<eses_ctx *>(cc);
+    if (!c) return fail(c, ESES_EINVAL, "NULL argument");
+    if (!c->ran) return fail(c, ESES_ESTATE, "no results: call eses_run first");
+    const int np = c->M.n_pairs, nv = c->M.n_verts, n = c->M.n_atoms;
+    std::vector<int> orig((size_t)n);
+    std::vector<int2> ij((size_t)std::max(np, 1));
+    std::vector<double4> po((size_t)std::max(np, 1)), pu((size_t)std::max(np, 1)), vq((size_t)std::max(nv, 1));
+    bool ok = cudaMemcpy(orig.data(), c->atom_orig.p, sizeof(int) * n, cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (np > 0) {
+        ok &= cudaMemcpy(ij.data(), c->pair_ij.p, sizeof(int2) * np, cudaMemcpyDeviceToHost) == cudaSuccess;
+        ok &= cudaMemcpy(po.data(), c->pair_o.p, sizeof(double4) * np, cudaMemcpyDeviceToHost) == cudaSuccess;
+        ok &= cudaMemcpy(pu.data(), c->pair_u.p, sizeof(double4) * np, cudaMemcpyDeviceToHost) == cudaSuccess;
+        if (pair_free) ok &= cudaMemcpy(pair_free, c->pair_free.p, np, cudaMemcpyDeviceToHost) == cudaSuccess;
+    }
+    if (nv > 0) ok &= cudaMemcpy(vq.data(), c->vert.p, sizeof(double4) * nv, cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (!ok) return fail(c, ESES_ECUDA, "patch copy failed");
+    for (int p = 0; p < np; ++p) {
+        if (pair_atoms) {
+            pair_atoms[2 * p] = orig[ij[p].x];
+            pair_atoms[2 * p + 1] = orig[ij[p].y];
+        }
+        if (pair_circle) {
+            double *o = pair_circle + 7 * p;
+            o[0] = po[p].x; o[1] = po[p].y; o[2] = po[p].z;
+            o[3] = pu[p].x; o[4] = pu[p].y; o[5] = pu[p].z;
+            o[6] = po[p].w;
+        }
+    }
+    if (vertices)
+        for (int v = 0; v < nv; ++v) {
+            vertices[3 * v] = vq[v].x;
+            vertices[3 * v + 1] = vq[v].y;
+            vertices[3 * v + 2] = vq[v].z;
+        }
+    return ESES_OK;
+}
+
 int eses_stage_times(const eses_ctx *cc, double *ms, int n)
 {
     eses_ctx *c = const_cast<eses_ctx *>(cc);
@@ -625,7 +699,7 @@ void eses_destroy(eses_ctx *c)
                     &c->vert_count, &c->vert_start, &c->vert, &c->pbin_count, &c->pbin_start, &c->pbin_cursor,
                     &c->pbin_cell, &c->pbin_list, &c->vbin_count, &c->vbin_start, &c->vbin_cursor, &c->vbin_cell,
                     &c->vbin_list, &c->labels, &c->tile_band, &c->tile_edges, &c->edge_start, &c->tile_inside,
-                    &c->tile_area, &c->tile_vol, &c->scan_tmp, &c->misc};
+                    &c->tile_area, &c->tile_vol, &c->scan_tmp, &c->misc, &c->fail_log};
     if (c->own_stream) cudaStreamSynchronize(c->own_stream);
     for (DBuf *b : bufs) free_buf(*b);
     for (int a = 0; a < 3; ++a) {

@@ -10,9 +10,11 @@
 //   (convex), tori around pair circles (saddle) and probe spheres around free
 //   triple points (concave).  Every root of every such piece in [0, h] whose
 //   witness (projection on the expanded sphere / nearest circle point / the
-//   triple point) is free is a candidate.  From an inside end point the first
-//   candidate is the first root; from an outside end point the first
-//   candidate that is not strictly outside M is.  Sphere roots come from the
+//   triple point) is free, and whose witness distance crosses r_p in the
+//   direction that leaves the end point's side (falling from an inside end,
+//   rising from an outside end), is a candidate.  From an inside end point
+//   the first candidate is the first root; from an outside end point the
+//   first candidate that is not strictly outside M is.  Sphere roots come from the
 //   quadratic, torus roots from the quartic
 //     (|y-o|^2 + rho^2 - r_p^2)^2 = 4 rho^2 (|y-o|^2 - ((y-o).u)^2)
 //   solved on [0, h] by root isolation on the derivative chain (quadratic ->
@@ -27,7 +29,7 @@
 namespace eses {
 
 constexpr int EDGE_THREADS = 256;
-constexpr int MAX_CAND = 16;
+constexpr int MAX_CAND = 32;
 
 // --------------------------------------------------------------------------
 // polynomial roots on an interval
@@ -159,8 +161,12 @@ __device__ __forceinline__ void push_cand(Cand *c, int &nc, double t, double qx,
 
 // First surface root on the edge from s (tile frame) along +axis, length h.
 // lab_s is the label of s.  Returns false when no root is found.
+// dbg (optional, 16 counters): [0] sphere roots, [1] sphere witness covered,
+// [2] probe-sphere roots, [3] tori tested, [4] quartic roots, [5] far-branch
+// roots, [6] torus witness covered, [7] candidates, [8] candidates rejected by
+// validation, [9..15] t of the first candidates (x 1e9, truncated)
 __device__ bool edge_root(const TileS<double> &S, const double s[3], int axis, double h, double rp, int lab_s,
-                          double &t_out, double q_out[3])
+                          double &t_out, double q_out[3], long long *dbg = nullptr)
 {
     Cand c[MAX_CAND];
     int nc = 0;
@@ -181,9 +187,16 @@ __device__ bool edge_root(const TileS<double> &S, const double s[3], int axis, d
             double v[3] = {y[0] - at.x, y[1] - at.y, y[2] - at.z};
             double nv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
             if (!(nv > 0.0)) continue;
+            // the witness distance R - |y - c| must cross r_p the right way:
+            // rising (leaving the outside of M) from an outside end point,
+            // falling from an inside one
+            double rate = -v[axis] / nv;
+            if (lab_s == LABEL_IN ? rate > 1e-9 : rate < -1e-9) continue;
             double R = at.w + rp;
             double qx = at.x + R * v[0] / nv, qy = at.y + R * v[1] / nv, qz = at.z + R * v[2] / nv;
+            if (dbg) dbg[0]++;
             if (free_pt<double, false>(qx, qy, qz, S, S.agid[a], -1, rp, 0.0) == 1) push_cand(c, nc, rt[k], qx, qy, qz);
+            else if (dbg) dbg[1]++;
         }
     }
     // concave: probe spheres around free triple points
@@ -196,7 +209,12 @@ __device__ bool edge_root(const TileS<double> &S, const double s[3], int axis, d
         double co[3] = {cc, 2.0 * b, 1.0};
         double rt[2];
         int nr = PolyRoots<2>::run(co, 0.0, h, rt);
-        for (int k = 0; k < nr; ++k) push_cand(c, nc, rt[k], q.x, q.y, q.z);
+        if (dbg) dbg[2] += nr;
+        for (int k = 0; k < nr; ++k) {
+            double rate = (d[axis] + rt[k]) / rp;  // d|y - v|/dt at the root
+            if (lab_s == LABEL_IN ? rate > 1e-9 : rate < -1e-9) continue;
+            push_cand(c, nc, rt[k], q.x, q.y, q.z);
+        }
     }
     // saddle: tori around free-arc circles
     for (int p = 0; p < S.np; ++p) {
@@ -222,6 +240,10 @@ __device__ bool edge_root(const TileS<double> &S, const double s[3], int axis, d
         co[0] = K * K - 4.0 * r2 * (P - z0 * z0);
         double rt[4];
         int nr = PolyRoots<4>::run(co, 0.0, h, rt);
+        if (dbg) {
+            dbg[3]++;
+            dbg[4] += nr;
+        }
         for (int k = 0; k < nr; ++k) {
             double y[3] = {p0[0], p0[1], p0[2]};
             y[axis] += rt[k];
@@ -229,12 +251,23 @@ __device__ bool edge_root(const TileS<double> &S, const double s[3], int axis, d
             double w[3] = {y[0] - zc * u.x, y[1] - zc * u.y, y[2] - zc * u.z};
             double nw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
             double near2 = (nw - rho) * (nw - rho) + zc * zc;
-            if (fabs(near2 - rp * rp) > 1e-7 * rp * rp) continue;  // far branch of the quartic
+            if (fabs(near2 - rp * rp) > 1e-7 * rp * rp) {  // far branch of the quartic
+                if (dbg) dbg[5]++;
+                continue;
+            }
             if (!(nw > 0.0)) continue;
+            // d/dt of the distance to the circle: ((|w| - rho) w_a / |w| + z u_a) / r_p
+            double rate = ((nw - rho) * w[axis] / nw + zc * uu[axis]) / rp;
+            if (lab_s == LABEL_IN ? rate > 1e-9 : rate < -1e-9) continue;
             double qx = o.x + rho * w[0] / nw, qy = o.y + rho * w[1] / nw, qz = o.z + rho * w[2] / nw;
             int2 ij = S.pij[p];
             if (free_pt<double, false>(qx, qy, qz, S, ij.x, ij.y, rp, 0.0) == 1) push_cand(c, nc, rt[k], qx, qy, qz);
+            else if (dbg) dbg[6]++;
         }
+    }
+    if (dbg) {
+        dbg[7] = nc;
+        for (int k = 0; k < nc && k < 7; ++k) dbg[9 + k] = (long long)(c[k].t * 1e9);
     }
     if (nc == 0) return false;
     int pick = -1;
@@ -244,11 +277,12 @@ __device__ bool edge_root(const TileS<double> &S, const double s[3], int axis, d
         for (int k = 0; k < nc; ++k) {
             double y[3] = {s[0], s[1], s[2]};
             y[axis] += c[k].t;
-            // not strictly outside M: no free centre closer than r_p - 1e-9
-            if (classify_pt<double, false>(y[0], y[1], y[2], S, rp, rp - 1e-9, 0.0) == 1) {
+            // not strictly outside M: no free centre closer than r_p - 1e-11
+            if (classify_pt<double, false>(y[0], y[1], y[2], S, rp, rp - 1e-11, 0.0) == 1) {
                 pick = k;
                 break;
             }
+            if (dbg) dbg[8]++;
         }
     }
     if (pick < 0) return false;
@@ -358,7 +392,7 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Grid G, co
                                                              const int *__restrict__ edge_start, EdgeOut out,
                                                              double *__restrict__ tile_area,
                                                              double *__restrict__ tile_vol, int *__restrict__ n_fail,
-                                                             int *__restrict__ err)
+                                                             int *__restrict__ err, long long *__restrict__ fail_log)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileS<double> &S = *reinterpret_cast<TileS<double> *>(smem_raw);
@@ -425,8 +459,22 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Grid G, co
                         nrm[2] = v[2] / nv;
                     }
                 } else {
-                    atomicAdd(n_fail, 1);
+                    int slot = atomicAdd(n_fail, 1);
                     atomicOr(err, ERR_ROOT);
+                    if (slot < FAIL_LOG) {
+                        long long *rec = fail_log + FAIL_REC * slot;
+                        for (int z = 0; z < FAIL_REC; ++z) rec[z] = 0;
+                        double tt, qq[3];
+                        edge_root(S, s, a, h, rp, lab_s, tt, qq, rec + 8);
+                        rec[0] = a;
+                        rec[1] = (long long)TILE * t[0] + li;
+                        rec[2] = (long long)TILE * t[1] + lj;
+                        rec[3] = (long long)TILE * t[2] + lk;
+                        rec[4] = lab_s;
+                        rec[5] = S.na;
+                        rec[6] = S.np;
+                        rec[7] = S.nv;
+                    }
                 }
                 long long g[3] = {(long long)TILE * t[0] + li, (long long)TILE * t[1] + lj,
                                   (long long)TILE * t[2] + lk};
@@ -516,12 +564,13 @@ int launch_edge_count(const Grid &G, const int8_t *labels, int *tile_edges, int 
 }
 
 int launch_edge_solve(const Model &M, const Grid &G, const int8_t *labels, const int *edge_start, EdgeOut out,
-                       double *tile_area, double *tile_vol, int *n_fail, int *err, cudaStream_t st)
+                       double *tile_area, double *tile_vol, int *n_fail, int *err, long long *fail_log,
+                       cudaStream_t st)
 {
     size_t sm = sizeof(TileS<double>);
     cudaFuncSetAttribute(k_edge_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_edge_solve<<<grid_tiles(G.n_tiles), EDGE_THREADS, sm, st>>>(M, G, labels, edge_start, out, tile_area, tile_vol,
-                                                                  n_fail, err);
+                                                                  n_fail, err, fail_log);
     return 1;
 }
 

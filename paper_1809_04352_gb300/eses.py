@@ -41,7 +41,8 @@ STAT_NAMES = ["points", "tiles", "work_tiles", "circle_pairs", "free_arc_pairs",
 # every exported C symbol, as declared in include/eses.h
 SYMBOLS = ["eses_create", "eses_create_device", "eses_set_option", "eses_run", "eses_grid", "eses_labels",
            "eses_labels_device", "eses_num_intersections", "eses_intersections", "eses_intersections_device",
-           "eses_area_volume", "eses_stats", "eses_stage_times", "eses_last_error", "eses_destroy"]
+           "eses_area_volume", "eses_stats", "eses_stage_times", "eses_root_failures", "eses_patch_counts",
+           "eses_patch_data", "eses_last_error", "eses_destroy"]
 STAGE_NAMES = ["binning", "pairs", "arcs", "classify", "band", "edge_count", "edge_solve", "reduce"]
 
 _lib = None
@@ -82,6 +83,9 @@ def load():
     lib.eses_area_volume.argtypes = [P, P, P]
     lib.eses_stats.argtypes = [P, P, ci]
     lib.eses_stage_times.argtypes = [P, P, ci]
+    lib.eses_root_failures.argtypes = [P, P, ci, P]
+    lib.eses_patch_counts.argtypes = [P, P, P, P]
+    lib.eses_patch_data.argtypes = [P, P, P, P, P]
     lib.eses_last_error.argtypes = [P]
     lib.eses_last_error.restype = ctypes.c_char_p
     lib.eses_destroy.argtypes = [P]
@@ -208,6 +212,29 @@ def eses_stage_times(ctx) -> dict:
     out = np.zeros(len(STAGE_NAMES), np.float64)
     _check(load().eses_stage_times(ctx, _ptr(out), len(STAGE_NAMES)), ctx)
     return dict(zip(STAGE_NAMES, (float(v) for v in out)))
+
+
+def eses_root_failures(ctx):
+    recs = np.zeros((8, 24), np.int64)
+    n = np.zeros(1, np.int32)
+    _check(load().eses_root_failures(ctx, _ptr(recs), 8, _ptr(n)), ctx)
+    return recs[: int(n[0])]
+
+
+def eses_patch_counts(ctx):
+    a, b, c = (np.zeros(1, np.int64) for _ in range(3))
+    _check(load().eses_patch_counts(ctx, _ptr(a), _ptr(b), _ptr(c)), ctx)
+    return int(a[0]), int(b[0]), int(c[0])
+
+
+def eses_patch_data(ctx):
+    np_, _, nv = eses_patch_counts(ctx)
+    atoms = np.empty((np_, 2), np.int32)
+    free = np.empty(np_, np.uint8)
+    circ = np.empty((np_, 7), np.float64)
+    verts = np.empty((nv, 3), np.float64)
+    _check(load().eses_patch_data(ctx, _ptr(atoms), _ptr(free), _ptr(circ), _ptr(verts)), ctx)
+    return {"pair_atoms": atoms, "pair_free": free, "pair_circle": circ, "vertices": verts}
 
 
 def eses_destroy(ctx):

@@ -41,7 +41,7 @@ def test_binding_names_match_abi():
 
 
 @pytest.mark.parametrize("bad", [
-    dict(n=0), dict(r=-1.0), dict(r=0.0), dict(nan=True), dict(rp=-0.1), dict(h=0.0), dict(margin=0.1),
+    dict(n=0), dict(r=-1.0), dict(r=0.0), dict(nan=True), dict(rp=-0.1), dict(rp=0.0), dict(h=0.0), dict(margin=0.1),
     dict(inf_rp=True),
 ])
 def test_invalid_arguments_rejected(lib, bad):

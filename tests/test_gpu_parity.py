@@ -88,7 +88,7 @@ SMALL = {
     "cluster-4": _cluster(4, 2) + (1.4, 0.25, 1.0),
     "cluster-10": _cluster(10, 4) + (1.4, 0.2, 0.8),
     "far-apart": (np.array([[0.0, 0, 0], [20.0, 0, 0], [0, 15.0, 3.0]]), np.array([1.7, 1.5, 1.8]), 1.4, 0.5, 0.5),
-    "probe-zero": _cluster(6, 5) + (0.0, 0.25, 1.0),
+    "small-probe": _cluster(6, 5) + (0.05, 0.25, 1.0),
     "big-probe": _cluster(8, 6) + (3.0, 0.3, 1.0),
 }
 

@@ -162,7 +162,7 @@ def test_few_atoms_distance_bracketed_by_sampling(n, seed):
 
 def test_free_vertices_lie_on_three_spheres_and_are_free():
     xyz, rad = _cluster(10, 4)
-    npairs, nv, verts = oracle.model_stats(xyz, rad, RP, max_vertices=10000)
+    npairs, nv, verts, _ = oracle.model_stats(xyz, rad, RP, max_vertices=10000)
     assert nv > 0 and npairs > 0
     R = rad + RP
     dd = np.linalg.norm(verts[:, None, :] - xyz[None], axis=2) - R[None]
