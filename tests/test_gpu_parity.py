@@ -43,7 +43,33 @@ def gpu_run(xyz, rad, rp, h, margin, precision=eses.ESES_PREC_FP32_FILTERED, pro
         eses.eses_destroy(ctx)
 
 
-def compare(g, o, h, check_area=True):
+def normal_error(xyz, rad, rp, g_idx, g_tau, g_nrm, o_nrm, dims, lo, h, axis):
+    """Per edge: the smaller of |n_gpu - n_oracle| and |n_gpu - n at the GPU's
+    own root point| (the oracle's witness there).  The second form removes the
+    curvature amplification of a position difference far below the 1e-6 A
+    intersection tolerance (near a spindle or a seam the normal turns fast)."""
+    e = np.abs(g_nrm - o_nrm).max(1)
+    bad = np.where(e >= NRM_TOL)[0]
+    if len(bad):
+        i = g_idx[bad] // (dims[1] * dims[2])
+        j = (g_idx[bad] // dims[2]) % dims[1]
+        k = g_idx[bad] % dims[2]
+        p = lo[None, :] + h * np.stack([i, j, k], 1).astype(np.float64)
+        p[:, axis] += g_tau[bad] * h
+        d, q, t, _ = oracle.distance(xyz, rad, rp, p, rp + 1.0)
+        n_at = (q - p) / np.linalg.norm(q - p, axis=1, keepdims=True)
+        e[bad] = np.minimum(e[bad], np.abs(g_nrm[bad] - n_at).max(1))
+        # at a crease several free probe centres lie at distance r_p from the
+        # surface point and each gives a valid normal: accept the GPU's when
+        # its witness p + r_p n is free and p is on the surface
+        qg = p + rp * g_nrm[bad]
+        margin = (np.linalg.norm(qg[:, None, :] - np.asarray(xyz)[None], axis=2) - (np.asarray(rad) + rp)[None]).min(1)
+        ok = (margin >= -1e-8) & (np.abs(d - rp) <= 1e-9)
+        e[bad[ok]] = 0.0
+    return e
+
+
+def compare(g, o, h, check_area=True, atoms=None):
     assert np.array_equal(g["dims"], o.dims)
     assert np.array_equal(g["lo"], o.lo)
     assert g["stats"]["root_failures"] == 0
@@ -58,7 +84,11 @@ def compare(g, o, h, check_area=True):
         assert np.array_equal(gi, o.idx[a])
         if len(gi):
             assert np.abs(gt - o.tau[a]).max() * h < TAU_TOL_A
-            assert np.abs(gn - o.normal[a]).max() < NRM_TOL
+            if atoms is None:
+                assert np.abs(gn - o.normal[a]).max() < NRM_TOL
+            else:
+                xyz, rad, rp = atoms
+                assert normal_error(xyz, rad, rp, gi, gt, gn, o.normal[a], o.dims, o.lo, h, a).max() < NRM_TOL
             # FP32 copies agree with the FP64 outputs to FP32 rounding
             assert np.abs(ga["tau32"][order] - gt).max() < 1e-6
             assert np.abs(ga["normal32"][order] - gn).max() < 1e-6
@@ -99,7 +129,7 @@ def test_small_cases_match_oracle(name, precision):
     xyz, rad, rp, h, margin = SMALL[name]
     o = oracle.run(xyz, rad, rp, h, margin)
     g = gpu_run(xyz, rad, rp, h, margin, precision)
-    compare(g, o, h)
+    compare(g, o, h, atoms=(xyz, rad, rp))
 
 
 @pytest.mark.parametrize("precision", [eses.ESES_PREC_FP64, eses.ESES_PREC_FP32_FILTERED])
@@ -109,7 +139,7 @@ def test_plain_200_atoms_matches_oracle(precision):
     xyz, rad = inputs.workload_atoms(1)
     o = oracle.run(xyz, rad, wl.r_p, wl.h, wl.margin, block_pts=64)
     g = gpu_run(xyz, rad, wl.r_p, wl.h, wl.margin, precision)
-    compare(g, o, wl.h)
+    compare(g, o, wl.h, atoms=(xyz, rad, wl.r_p))
     assert sum(len(x) for x in o.idx) > 1000
 
 
@@ -119,7 +149,7 @@ def test_ragged_grid_matches_oracle(h):
     o = oracle.run(xyz, rad, 1.4, h, 0.8)
     g = gpu_run(xyz, rad, 1.4, h, 0.8)
     assert any(int(d) % 8 for d in g["dims"])
-    compare(g, o, h)
+    compare(g, o, h, atoms=(xyz, rad, 1.4))
 
 
 def test_globule_5000_fp32_equals_fp64_and_sampled_blocks_match_oracle():
@@ -158,7 +188,9 @@ def test_globule_5000_fp32_equals_fp64_and_sampled_blocks_match_oracle():
         order = np.argsort(gi[sel], kind="stable")
         assert np.array_equal(gi[sel][order], o.idx[a])
         assert np.abs(g32["axes"][a]["tau"][sel][order] - o.tau[a]).max() * wl.h < TAU_TOL_A
-        assert np.abs(g32["axes"][a]["normal"][sel][order] - o.normal[a]).max() < NRM_TOL
+        en = normal_error(xyz, rad, wl.r_p, gi[sel][order], g32["axes"][a]["tau"][sel][order],
+                          g32["axes"][a]["normal"][sel][order], o.normal[a], o.dims, o.lo, wl.h, a)
+        assert en.max() < NRM_TOL
 
 
 def test_device_pointer_create_matches_host_create():
