@@ -161,6 +161,30 @@ int eses_patch_counts(const eses_ctx *ctx, int64_t *n_pairs, int64_t *n_free_pai
 int eses_patch_data(const eses_ctx *ctx, int32_t *pair_atoms, uint8_t *pair_free, double *pair_circle,
                     double *vertices);
 
+/* List the crossing edges of a label grid without allocating any memory.
+ * There is no counterpart in the paper: this entry point exists for callers
+ * that cannot call cudaMalloc -- code whose device memory is owned by a
+ * framework allocator or a fixed budget, or work issued where allocation is
+ * not allowed.
+ * labels: device, int8 (0/1), dims[0]*dims[1]*dims[2], C order (as from
+ * eses_labels_device); dims: host, 3 values.  idx0, idx1, idx2: device,
+ * caller-allocated int64 outputs of capacity[0..2] entries: the lower point's
+ * linear index of every edge along axis 0, 1, 2 whose end labels differ, in
+ * the order of eses_intersections.  counts: host output, the number of such
+ * edges per axis.  stream: a cudaStream_t (NULL: the default stream); the
+ * call waits for that stream before returning.
+ * Its working memory (per-tile counts and offsets) is one file-scope device
+ * array sized for 131,072 tiles of 8x8x8 points (at most 67,108,864 grid
+ * points, about 3 MiB, held by every GPU that loads the library until the
+ * process exits).  Larger grids return ESES_EINVAL.  The first call on a
+ * device looks up that array's address (make it before any stream capture).
+ * Calls share the array: calls that overlap on the GPU race.  Returns
+ * ESES_ECAPACITY when a count exceeds its capacity (the first capacity[a]
+ * entries are written), ESES_EINVAL for NULL pointers or bad sizes,
+ * ESES_ECUDA when a CUDA call fails.  It does not set eses_last_error. */
+int eses_crossing_edges_noalloc(const int8_t *labels, const int64_t dims[3], int64_t *idx0, int64_t *idx1,
+                                int64_t *idx2, const int64_t capacity[3], int64_t counts[3], void *stream);
+
 /* Last error message of the context (or of the last failed create when ctx
  * is NULL).  Never NULL. */
 const char *eses_last_error(const eses_ctx *ctx);

@@ -42,7 +42,7 @@ STAT_NAMES = ["points", "tiles", "work_tiles", "circle_pairs", "free_arc_pairs",
 SYMBOLS = ["eses_create", "eses_create_device", "eses_set_option", "eses_run", "eses_grid", "eses_labels",
            "eses_labels_device", "eses_num_intersections", "eses_intersections", "eses_intersections_device",
            "eses_area_volume", "eses_stats", "eses_stage_times", "eses_root_failures", "eses_patch_counts",
-           "eses_patch_data", "eses_last_error", "eses_destroy"]
+           "eses_patch_data", "eses_crossing_edges_noalloc", "eses_last_error", "eses_destroy"]
 STAGE_NAMES = ["binning", "pairs", "arcs", "classify", "band", "edge_count", "edge_solve", "reduce"]
 
 _lib = None
@@ -86,6 +86,7 @@ def load():
     lib.eses_root_failures.argtypes = [P, P, ci, P]
     lib.eses_patch_counts.argtypes = [P, P, P, P]
     lib.eses_patch_data.argtypes = [P, P, P, P, P]
+    lib.eses_crossing_edges_noalloc.argtypes = [P, P, P, P, P, P, P, P]
     lib.eses_last_error.argtypes = [P]
     lib.eses_last_error.restype = ctypes.c_char_p
     lib.eses_destroy.argtypes = [P]
@@ -235,6 +236,20 @@ def eses_patch_data(ctx):
     verts = np.empty((nv, 3), np.float64)
     _check(load().eses_patch_data(ctx, _ptr(atoms), _ptr(free), _ptr(circ), _ptr(verts)), ctx)
     return {"pair_atoms": atoms, "pair_free": free, "pair_circle": circ, "vertices": verts}
+
+
+def eses_crossing_edges_noalloc(labels, dims, idx0, idx1, idx2, capacity, stream=0):
+    """Crossing edges of a device label grid into caller-allocated device
+    outputs, with no allocation inside the library.  Returns the per-axis
+    counts (numpy int64[3]); raises EsesError on failure."""
+    d = np.ascontiguousarray(dims, dtype=np.int64)
+    cap = np.ascontiguousarray(capacity, dtype=np.int64)
+    counts = np.zeros(3, np.int64)
+    rc = load().eses_crossing_edges_noalloc(_ptr(labels), _ptr(d), _ptr(idx0), _ptr(idx1), _ptr(idx2), _ptr(cap),
+                                            _ptr(counts), ctypes.c_void_p(int(stream)) if stream else None)
+    if rc != ESES_OK:
+        raise EsesError(rc, f"eses_crossing_edges_noalloc failed (counts {counts.tolist()})")
+    return counts
 
 
 def eses_destroy(ctx):
