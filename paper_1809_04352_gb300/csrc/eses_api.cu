@@ -404,7 +404,8 @@ int run_impl(eses_ctx *c)
     double *tile_vol = ensure<double>(c->tile_vol, nt);
     mark(c, ST_EDGE_SOLVE);
     long long *fail_log = ensure<long long>(c->fail_log, FAIL_LOG * FAIL_REC);
-    nl += launch_edge_solve(M, G, labels, edge_start, eo, tile_area, tile_vol, d_fail, d_err, fail_log, st);
+    nl += launch_edge_solve(M, G, c->precision, labels, edge_start, eo, tile_area, tile_vol, d_fail, d_err, fail_log,
+                            st);
     mark(c, ST_REDUCE);
     nl += launch_reduce(G, tile_area, tile_vol, tile_inside, labels, d_av, d_counts, st);
     mark(c, NSTAGE);
@@ -435,9 +436,10 @@ int run_impl(eses_ctx *c)
     c->stats[10] = nl;
     c->ran = true;
     int derr = hmisc[0];
-    if (derr & (ERR_CAP_ATOMS | ERR_CAP_PAIRS | ERR_CAP_VERTS)) {
+    if (derr & (ERR_CAP_ATOMS | ERR_CAP_PAIRS | ERR_CAP_VERTS | ERR_CAP_CAND)) {
         c->ran = false;
-        return fail(c, ESES_ECAPACITY, "a tile's staged list exceeded its shared-memory capacity");
+        return fail(c, ESES_ECAPACITY, (derr & ERR_CAP_CAND) ? "an edge had more candidate roots than its buffer holds"
+                                                             : "a tile's staged list exceeded its shared-memory capacity");
     }
     if (hmisc[1] > 0)
         return fail(c, ESES_EROOT, std::to_string(hmisc[1]) + " crossing edges had no surface root");

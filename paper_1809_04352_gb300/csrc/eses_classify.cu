@@ -1,19 +1,162 @@
 // eses_classify.cu -- grid-point classification kernels (the second ESES
 // stage, Eq. 2), one CTA per 8x8x8 tile.
 //
-// k_classify<T, FILT>: stages the tile's atoms and patches in shared memory
-// and labels its 512 points.  T = double, FILT = false is the plain FP64
-// form; T = float, FILT = true is the filtered form, whose undecided points
-// get LABEL_BAND and are counted per tile.  Warp-uniform early outs: a warp
-// whose points all lie in no expanded ball, or all inside one van der Waals
-// ball, never enters the patch loops.
-// k_band: re-labels the undecided points of the tiles that have any, in FP64.
+// k_classify<T, FILT>:
+//   1. stages the tile's atoms, free-arc pairs and free triple points in
+//      shared memory (tile frame) and lists, for every staged atom, the staged
+//      pairs it belongs to;
+//   2. splits the tile into 16 bricks of 2x4x4 points, one warp per brick:
+//      the lanes test the staged atoms against the brick's box and a ballot
+//      compacts the atoms whose expanded ball reaches the brick.  A warp with
+//      an empty list labels its 32 points outside at once; otherwise every
+//      lane tests its point against the short list: inside a van der Waals
+//      ball -> 1, in no expanded ball -> 0, else a shell point;
+//   3. shell points go to a per-tile queue and the whole CTA works through it:
+//      free triple points within r_p, convex witnesses of the containing
+//      balls, saddle witnesses of the pairs of the containing balls.
+//   T = double, FILT = false is the plain FP64 form; T = float, FILT = true
+//   is the filtered form, whose undecided points get LABEL_BAND and are
+//   counted per tile.
+// k_band: re-labels the undecided points of the tiles that have any, in FP64,
+//   with the same per-point code over every staged item.
 #include "eses_kernels.h"
 #include "eses_tile.cuh"
 
 namespace eses {
 
 constexpr int CLS_THREADS = 256;
+constexpr int NBRICK = 16;     // 2x4x4-point bricks per tile
+constexpr int HASH = 1024;     // staged-atom lookup (power of two > 2 A_MAX)
+constexpr int INC_MAX = 2 * P_MAX;
+
+struct ClsSmem {
+    int hkey[HASH];
+    short hval[HASH];
+    short2 pslot[P_MAX];           // staged slots of each pair's atoms (-1: not staged)
+    int inc_start[A_MAX + 1];      // incident pairs per staged atom (CSR)
+    int inc_fill[A_MAX];
+    short inc[INC_MAX];
+    short blist[NBRICK][A_MAX];    // per-brick atom lists
+    int bcount[NBRICK];
+    short queue[TILE_PTS];         // shell points
+    int nq, band;
+};
+
+__device__ __forceinline__ void brick_point(int brick, int lane, int &li, int &lj, int &lk)
+{
+    int bi = brick >> 2, bj = (brick >> 1) & 1, bk = brick & 1;
+    li = bi * 2 + (lane >> 4);
+    lj = bj * 4 + ((lane >> 2) & 3);
+    lk = bk * 4 + (lane & 3);
+}
+
+__device__ __forceinline__ unsigned hash_of(int key) { return ((unsigned)key * 2654435761u) & (HASH - 1); }
+
+// per-atom incident pair lists (whole block)
+template <class T>
+__device__ void build_incidence(const TileS<T> &S, ClsSmem &C)
+{
+    for (int k = threadIdx.x; k < HASH; k += blockDim.x) C.hkey[k] = -1;
+    for (int a = threadIdx.x; a < A_MAX + 1; a += blockDim.x) C.inc_start[a] = 0;
+    __syncthreads();
+    for (int a = threadIdx.x; a < S.na; a += blockDim.x) {
+        int key = S.agid[a];
+        unsigned h = hash_of(key);
+        while (true) {
+            int prev = atomicCAS(&C.hkey[h], -1, key);
+            if (prev == -1 || prev == key) {
+                C.hval[h] = (short)a;
+                break;
+            }
+            h = (h + 1) & (HASH - 1);
+        }
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < S.np; p += blockDim.x) {
+        int2 ij = S.pij[p];
+        short si = -1, sj = -1;
+        for (unsigned h = hash_of(ij.x);; h = (h + 1) & (HASH - 1)) {
+            int k = C.hkey[h];
+            if (k == ij.x) { si = C.hval[h]; break; }
+            if (k == -1) break;
+        }
+        for (unsigned h = hash_of(ij.y);; h = (h + 1) & (HASH - 1)) {
+            int k = C.hkey[h];
+            if (k == ij.y) { sj = C.hval[h]; break; }
+            if (k == -1) break;
+        }
+        C.pslot[p] = make_short2(si, sj);
+        if (si >= 0 && sj >= 0) {
+            atomicAdd(&C.inc_start[si + 1], 1);
+            atomicAdd(&C.inc_start[sj + 1], 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {  // inclusive scan of inc_start[1..A_MAX] by one warp
+        const int lane = threadIdx.x;
+        const int per = (A_MAX + 31) / 32;
+        const int base = 1 + lane * per;
+        int s = 0;
+        for (int k = 0; k < per; ++k)
+            if (base + k <= A_MAX) s += C.inc_start[base + k];
+        int inc = s;
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        int run = inc - s;
+        for (int k = 0; k < per; ++k)
+            if (base + k <= A_MAX) {
+                run += C.inc_start[base + k];
+                C.inc_start[base + k] = run;
+            }
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < A_MAX; a += blockDim.x) C.inc_fill[a] = C.inc_start[a];
+    __syncthreads();
+    for (int p = threadIdx.x; p < S.np; p += blockDim.x) {
+        short2 sl = C.pslot[p];
+        if (sl.x >= 0 && sl.y >= 0) {
+            C.inc[atomicAdd(&C.inc_fill[sl.x], 1)] = (short)p;
+            C.inc[atomicAdd(&C.inc_fill[sl.y], 1)] = (short)p;
+        }
+    }
+    __syncthreads();
+}
+
+// shell point: witnesses among free triple points, the containing balls and
+// their pairs.  1 inside, 0 outside, 2 undecided.
+template <bool FILT, class T>
+__device__ int shell_label(const TileS<T> &S, const ClsSmem &C, int brick, T x, T y, T z, T rp, T d0)
+{
+    SmemAcc<T> A(S);
+    bool unsure = false;
+    const T thr = rp, thr2 = rp * rp;
+    for (int v = 0; v < S.nv; ++v) {
+        P4<T> q = S.vq[v];
+        T dx = x - q.x, dy = y - q.y, dz = z - q.z;
+        int t = lt_sq<FILT>(dx * dx + dy * dy + dz * dz, thr2, thr, d0);
+        if (t == 1) return 0;
+        if (t < 0) unsure = true;
+    }
+    const int nb = C.bcount[brick];
+    for (int m = 0; m < nb; ++m) {
+        int a = C.blist[brick][m];
+        P4<T> c = S.atom[a];
+        T dx = x - c.x, dy = y - c.y, dz = z - c.z;
+        T R = c.w + rp;
+        if (lt_sq<FILT>(dx * dx + dy * dy + dz * dz, R * R, R, d0) == 0) continue;  // ball does not hold x
+        int w = face_witness<FILT>(A, a, x, y, z, rp, thr, d0);
+        if (w == 1) return 0;
+        if (w < 0) unsure = true;
+        for (int k = C.inc_start[a]; k < C.inc_start[a + 1]; ++k) {
+            int ws = saddle_witness<FILT>(A, (int)C.inc[k], x, y, z, rp, thr, d0);
+            if (ws == 1) return 0;
+            if (ws < 0) unsure = true;
+        }
+    }
+    return unsure ? 2 : 1;
+}
 
 template <class T, bool FILT>
 __global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Grid G, int8_t *__restrict__ labels,
@@ -21,31 +164,108 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Grid G, int8_
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileS<T> &S = *reinterpret_cast<TileS<T> *>(smem_raw);
-    __shared__ int band;
+    ClsSmem &C = *reinterpret_cast<ClsSmem *>(smem_raw + ((sizeof(TileS<T>) + 15) & ~(size_t)15));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const T rp = (T)M.rp;
+    const T d0 = FILT ? (T)G.d0 : T(0);
+    const T h = (T)G.h;
     for (long long tile = blockIdx.x; tile < G.n_tiles; tile += gridDim.x) {
         double x0[3];
         stage_tile<T>(M, G, tile, S, x0);
         if (threadIdx.x == 0) {
-            band = 0;
+            C.nq = 0;
+            C.band = 0;
             if (S.flags) atomicOr(err, S.flags);
         }
-        __syncthreads();
         int t[3];
         tile_coords(G, tile, t);
-        const T rp = (T)M.rp;
-        const T d0 = FILT ? (T)G.d0 : T(0);
-        for (int p = threadIdx.x; p < TILE_PTS; p += CLS_THREADS) {
-            int li = p >> 6, lj = (p >> 3) & 7, lk = p & 7;
+        if (S.na == 0) {  // no atom within reach: every point is free
+            for (int p = threadIdx.x; p < TILE_PTS; p += CLS_THREADS) {
+                int li = p >> 6, lj = (p >> 3) & 7, lk = p & 7;
+                long long gi = (long long)TILE * t[0] + li, gj = (long long)TILE * t[1] + lj,
+                          gk = (long long)TILE * t[2] + lk;
+                if (gi < G.dims[0] && gj < G.dims[1] && gk < G.dims[2])
+                    labels[(gi * G.dims[1] + gj) * G.dims[2] + gk] = LABEL_OUT;
+            }
+            if (threadIdx.x == 0 && tile_band) tile_band[tile] = 0;
+            __syncthreads();
+            continue;
+        }
+        build_incidence<T>(S, C);
+        // phase 1: bricks
+        for (int brick = warp; brick < NBRICK; brick += CLS_THREADS / 32) {
+            int li, lj, lk;
+            brick_point(brick, 0, li, lj, lk);
+            const T b0x = (T)li * h, b0y = (T)lj * h, b0z = (T)lk * h;
+            const T b1x = b0x + h, b1y = b0y + T(3) * h, b1z = b0z + T(3) * h;
+            int cnt = 0;
+            for (int base = 0; base < S.na; base += 32) {
+                int a = base + lane;
+                bool hit = false;
+                if (a < S.na) {
+                    P4<T> c = S.atom[a];
+                    T ex = c.x < b0x ? b0x - c.x : (c.x > b1x ? c.x - b1x : T(0));
+                    T ey = c.y < b0y ? b0y - c.y : (c.y > b1y ? c.y - b1y : T(0));
+                    T ez = c.z < b0z ? b0z - c.z : (c.z > b1z ? c.z - b1z : T(0));
+                    T reach = c.w + rp + T(1e-3);
+                    hit = ex * ex + ey * ey + ez * ez < reach * reach;
+                }
+                unsigned m = __ballot_sync(0xffffffffu, hit);
+                if (hit) C.blist[brick][cnt + __popc(m & ((1u << lane) - 1))] = (short)a;
+                cnt += __popc(m);
+            }
+            if (lane == 0) C.bcount[brick] = cnt;
+            __syncwarp();
+            brick_point(brick, lane, li, lj, lk);
             long long gi = (long long)TILE * t[0] + li, gj = (long long)TILE * t[1] + lj,
                       gk = (long long)TILE * t[2] + lk;
-            if (gi >= G.dims[0] || gj >= G.dims[1] || gk >= G.dims[2]) continue;
-            T x = (T)((double)li * G.h), y = (T)((double)lj * G.h), z = (T)((double)lk * G.h);
-            int lab = classify_pt<T, FILT>(x, y, z, S, rp, rp, d0);
-            labels[(gi * G.dims[1] + gj) * G.dims[2] + gk] = (int8_t)lab;
-            if (FILT && lab == LABEL_BAND) atomicAdd(&band, 1);
+            bool valid = gi < G.dims[0] && gj < G.dims[1] && gk < G.dims[2];
+            int lab = LABEL_OUT;
+            if (cnt > 0) {
+                T x = (T)((double)li * G.h), y = (T)((double)lj * G.h), z = (T)((double)lk * G.h);
+                bool vdw = false, sas = false, sas_u = false;
+                for (int m2 = 0; m2 < cnt; ++m2) {
+                    P4<T> c = S.atom[C.blist[brick][m2]];
+                    T dx = x - c.x, dy = y - c.y, dz = z - c.z;
+                    T d2 = dx * dx + dy * dy + dz * dz;
+                    T r = c.w, R = c.w + rp;
+                    if (lt_sq<FILT>(d2, r * r, r, d0) == 1) {
+                        vdw = true;
+                        break;
+                    }
+                    int s = lt_sq<FILT>(d2, R * R, R, d0);
+                    if (s == 1) sas = true;
+                    else if (s < 0) sas_u = true;
+                }
+                if (vdw) lab = LABEL_IN;
+                else if (!sas) lab = sas_u ? LABEL_BAND : LABEL_OUT;
+                else lab = -1;  // shell point
+            }
+            if (valid) {
+                if (lab == -1) {
+                    C.queue[atomicAdd(&C.nq, 1)] = (short)((li << 6) | (lj << 3) | lk | (brick << 9));
+                } else {
+                    labels[(gi * G.dims[1] + gj) * G.dims[2] + gk] = (int8_t)lab;
+                    if (FILT && lab == LABEL_BAND) atomicAdd(&C.band, 1);
+                }
+            }
         }
         __syncthreads();
-        if (threadIdx.x == 0 && tile_band) tile_band[tile] = band;
+        // phase 2: shell points, the whole block
+        const int nq = C.nq;
+        for (int k = threadIdx.x; k < nq; k += CLS_THREADS) {
+            int code = C.queue[k];
+            int brick = (code >> 9) & 15;
+            int li = (code >> 6) & 7, lj = (code >> 3) & 7, lk = code & 7;
+            long long gi = (long long)TILE * t[0] + li, gj = (long long)TILE * t[1] + lj,
+                      gk = (long long)TILE * t[2] + lk;
+            T x = (T)((double)li * G.h), y = (T)((double)lj * G.h), z = (T)((double)lk * G.h);
+            int lab = shell_label<FILT>(S, C, brick, x, y, z, rp, d0);
+            labels[(gi * G.dims[1] + gj) * G.dims[2] + gk] = (int8_t)lab;
+            if (FILT && lab == LABEL_BAND) atomicAdd(&C.band, 1);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && tile_band) tile_band[tile] = C.band;
         __syncthreads();
     }
 }
@@ -62,6 +282,7 @@ __global__ void __launch_bounds__(CLS_THREADS) k_band(Model M, Grid G, int8_t *_
         if (threadIdx.x == 0 && S.flags) atomicOr(err, S.flags);
         int t[3];
         tile_coords(G, tile, t);
+        SmemAcc<double> A(S);
         for (int p = threadIdx.x; p < TILE_PTS; p += CLS_THREADS) {
             int li = p >> 6, lj = (p >> 3) & 7, lk = p & 7;
             long long gi = (long long)TILE * t[0] + li, gj = (long long)TILE * t[1] + lj,
@@ -69,8 +290,7 @@ __global__ void __launch_bounds__(CLS_THREADS) k_band(Model M, Grid G, int8_t *_
             if (gi >= G.dims[0] || gj >= G.dims[1] || gk >= G.dims[2]) continue;
             long long idx = (gi * G.dims[1] + gj) * G.dims[2] + gk;
             if (labels[idx] != LABEL_BAND) continue;
-            int lab = classify_pt<double, false>((double)li * G.h, (double)lj * G.h, (double)lk * G.h, S, M.rp, M.rp,
-                                                 0.0);
+            int lab = classify_pt<false>(A, (double)li * G.h, (double)lj * G.h, (double)lk * G.h, M.rp, M.rp, 0.0);
             labels[idx] = (int8_t)lab;
         }
         __syncthreads();
@@ -83,15 +303,21 @@ static int grid_size(long long n_tiles)
     return (int)(g > 2147483647LL ? 2147483647LL : g);
 }
 
+template <class T>
+static size_t cls_smem()
+{
+    return ((sizeof(TileS<T>) + 15) & ~(size_t)15) + sizeof(ClsSmem);
+}
+
 int launch_classify(const Model &M, const Grid &G, int precision, int8_t *labels, int *tile_band, int *err,
-                     cudaStream_t st)
+                    cudaStream_t st)
 {
     if (precision == 0) {
-        size_t sm = sizeof(TileS<double>);
+        size_t sm = cls_smem<double>();
         cudaFuncSetAttribute(k_classify<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k_classify<double, false><<<grid_size(G.n_tiles), CLS_THREADS, sm, st>>>(M, G, labels, tile_band, err);
     } else {
-        size_t sm = sizeof(TileS<float>);
+        size_t sm = cls_smem<float>();
         cudaFuncSetAttribute(k_classify<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k_classify<float, true><<<grid_size(G.n_tiles), CLS_THREADS, sm, st>>>(M, G, labels, tile_band, err);
     }

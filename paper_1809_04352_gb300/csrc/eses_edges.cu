@@ -29,7 +29,6 @@
 namespace eses {
 
 constexpr int EDGE_THREADS = 256;
-constexpr int MAX_CAND = 32;
 
 // --------------------------------------------------------------------------
 // polynomial roots on an interval
@@ -139,158 +138,226 @@ struct PolyRoots<2> {
 // --------------------------------------------------------------------------
 // edge root
 // --------------------------------------------------------------------------
-struct Cand {
+// --------------------------------------------------------------------------
+// edge root, one warp per edge
+// --------------------------------------------------------------------------
+constexpr int EDGE_WARPS = EDGE_THREADS / 32;
+constexpr int WCAND = 64;  // candidate roots per warp
+
+struct WCand {
     double t, qx, qy, qz;
+    int kind, id;  // kind 0: van der Waals sphere (atom slot), 1: torus (pair slot), 2: probe sphere (vertex slot)
 };
 
-__device__ __forceinline__ void push_cand(Cand *c, int &nc, double t, double qx, double qy, double qz)
+struct EdgeSmem {
+    int8_t lab[9 * 9 * 9];
+    short eptr[3 * TILE_PTS];  // crossing edges of the tile (local point), grouped by axis
+    int estart[4];
+    long long ebase[3];
+    int sh[EDGE_WARPS];
+    double shd[EDGE_WARPS];
+    WCand cand[EDGE_WARPS][WCAND];
+    int ncand[EDGE_WARPS];
+};
+
+__device__ __forceinline__ void warp_push(EdgeSmem &E, int warp, double t, double qx, double qy, double qz, int kind,
+                                          int id)
 {
-    // keep the MAX_CAND smallest t, ascending
-    int k = nc < MAX_CAND ? nc : MAX_CAND - 1;
-    if (nc >= MAX_CAND && t >= c[MAX_CAND - 1].t) return;
-    while (k > 0 && c[k - 1].t > t) {
-        c[k] = c[k - 1];
-        --k;
+    int slot = atomicAdd(&E.ncand[warp], 1);
+    if (slot < WCAND) {
+        WCand &c = E.cand[warp][slot];
+        c.t = t;
+        c.qx = qx;
+        c.qy = qy;
+        c.qz = qz;
+        c.kind = kind;
+        c.id = id;
     }
-    c[k].t = t;
-    c[k].qx = qx;
-    c[k].qy = qy;
-    c[k].qz = qz;
-    if (nc < MAX_CAND) ++nc;
 }
 
-// First surface root on the edge from s (tile frame) along +axis, length h.
-// lab_s is the label of s.  Returns false when no root is found.
-// dbg (optional, 16 counters): [0] sphere roots, [1] sphere witness covered,
-// [2] probe-sphere roots, [3] tori tested, [4] quartic roots, [5] far-branch
-// roots, [6] torus witness covered, [7] candidates, [8] candidates rejected by
-// validation, [9..15] t of the first candidates (x 1e9, truncated)
-__device__ bool edge_root(const TileS<double> &S, const double s[3], int axis, double h, double rp, int lab_s,
-                          double &t_out, double q_out[3], long long *dbg = nullptr)
+// index of the smallest t (ties: smaller index), -1 if every t is +inf
+__device__ __forceinline__ int warp_argmin(const WCand *c, int n)
 {
-    Cand c[MAX_CAND];
-    int nc = 0;
-    // convex: van der Waals spheres, witness = projection on the expanded sphere
-    for (int a = 0; a < S.na; ++a) {
-        P4<double> at = S.atom[a];
-        double d[3] = {s[0] - at.x, s[1] - at.y, s[2] - at.z};
-        double b = d[axis];
-        double cc = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] - at.w * at.w;
-        double disc = b * b - cc;
-        if (disc < 0.0) continue;
-        double co[3] = {cc, 2.0 * b, 1.0};
-        double rt[2];
-        int nr = PolyRoots<2>::run(co, 0.0, h, rt);
-        for (int k = 0; k < nr; ++k) {
-            double y[3] = {s[0], s[1], s[2]};
-            y[axis] += rt[k];
-            double v[3] = {y[0] - at.x, y[1] - at.y, y[2] - at.z};
-            double nv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-            if (!(nv > 0.0)) continue;
-            // the witness distance R - |y - c| must cross r_p the right way:
-            // rising (leaving the outside of M) from an outside end point,
-            // falling from an inside one
-            double rate = -v[axis] / nv;
-            if (lab_s == LABEL_IN ? rate > 1e-9 : rate < -1e-9) continue;
-            double R = at.w + rp;
-            double qx = at.x + R * v[0] / nv, qy = at.y + R * v[1] / nv, qz = at.z + R * v[2] / nv;
-            if (dbg) dbg[0]++;
-            if (free_pt<double, false>(qx, qy, qz, S, S.agid[a], -1, rp, 0.0) == 1) push_cand(c, nc, rt[k], qx, qy, qz);
-            else if (dbg) dbg[1]++;
+    const int lane = threadIdx.x & 31;
+    double bt = INFINITY;
+    int bk = -1;
+    for (int k = lane; k < n; k += 32)
+        if (c[k].t < bt) {
+            bt = c[k].t;
+            bk = k;
+        }
+    for (int o = 16; o > 0; o >>= 1) {
+        double ot = __shfl_xor_sync(0xffffffffu, bt, o);
+        int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+        if (ot < bt || (ot == bt && ok >= 0 && (bk < 0 || ok < bk))) {
+            bt = ot;
+            bk = ok;
         }
     }
-    // concave: probe spheres around free triple points
-    for (int v = 0; v < S.nv; ++v) {
-        P4<double> q = S.vq[v];
-        double d[3] = {s[0] - q.x, s[1] - q.y, s[2] - q.z};
-        double b = d[axis];
-        double cc = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] - rp * rp;
-        if (b * b - cc < 0.0) continue;
-        double co[3] = {cc, 2.0 * b, 1.0};
-        double rt[2];
-        int nr = PolyRoots<2>::run(co, 0.0, h, rt);
-        if (dbg) dbg[2] += nr;
-        for (int k = 0; k < nr; ++k) {
-            double rate = (d[axis] + rt[k]) / rp;  // d|y - v|/dt at the root
-            if (lab_s == LABEL_IN ? rate > 1e-9 : rate < -1e-9) continue;
-            push_cand(c, nc, rt[k], q.x, q.y, q.z);
-        }
-    }
-    // saddle: tori around free-arc circles
-    for (int p = 0; p < S.np; ++p) {
-        P4<double> o = S.po[p];
-        P4<double> u = S.pu[p];
-        const double rho = o.w;
-        double p0[3] = {s[0] - o.x, s[1] - o.y, s[2] - o.z};
-        double uu[3] = {u.x, u.y, u.z};
-        double P = p0[0] * p0[0] + p0[1] * p0[1] + p0[2] * p0[2];
-        double z0 = p0[0] * u.x + p0[1] * u.y + p0[2] * u.z;
-        // quick reject: the tube around the circle must come within reach of the edge
-        double w0 = sqrt(fmax(P - z0 * z0, 0.0));
-        double dmid = sqrt((w0 - rho) * (w0 - rho) + z0 * z0);
-        if (dmid - rp > h + 1e-9 || rp - dmid > h + 1e-9) continue;  // 1-Lipschitz along the edge
-        double pe = p0[axis], eu = uu[axis];
-        double K = P + rho * rho - rp * rp;
-        double r2 = rho * rho;
-        double co[5];
-        co[4] = 1.0;
-        co[3] = 4.0 * pe;
-        co[2] = 4.0 * pe * pe + 2.0 * K - 4.0 * r2 * (1.0 - eu * eu);
-        co[1] = 4.0 * pe * K - 8.0 * r2 * (pe - z0 * eu);
-        co[0] = K * K - 4.0 * r2 * (P - z0 * z0);
-        double rt[4];
-        int nr = PolyRoots<4>::run(co, 0.0, h, rt);
-        if (dbg) {
-            dbg[3]++;
-            dbg[4] += nr;
-        }
-        for (int k = 0; k < nr; ++k) {
-            double y[3] = {p0[0], p0[1], p0[2]};
-            y[axis] += rt[k];
-            double zc = y[0] * u.x + y[1] * u.y + y[2] * u.z;
-            double w[3] = {y[0] - zc * u.x, y[1] - zc * u.y, y[2] - zc * u.z};
-            double nw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-            double near2 = (nw - rho) * (nw - rho) + zc * zc;
-            if (fabs(near2 - rp * rp) > 1e-7 * rp * rp) {  // far branch of the quartic
-                if (dbg) dbg[5]++;
-                continue;
+    return bk;
+}
+
+// Candidate roots of one crossing edge (lower point s, local index p, +axis,
+// length h), then the first root.  Sphere and torus roots are solved in FP64
+// only for the pieces that an FP32 test (with a margin) lets through; the
+// freeness of a witness is decided in FP32 when the filter allows and in FP64
+// otherwise.  From an inside end point the answer is the first candidate; from
+// an outside end point it is the first candidate at which no free probe centre
+// lies strictly closer than r_p (within 1e-11 A).
+template <class T, bool FILT>
+__device__ int warp_edge(const Model &M, const TileS<T> &S, const double *x0, EdgeSmem &E, int warp, int axis, int p,
+                         int lab_s, double h, double rp, T d0, double &t_out, double q_out[3])
+{
+    const int lane = threadIdx.x & 31;
+    const int li = p >> 6, lj = (p >> 3) & 7, lk = p & 7;
+    const double s64[3] = {(double)li * h, (double)lj * h, (double)lk * h};
+    const T s[3] = {(T)s64[0], (T)s64[1], (T)s64[2]};
+    SmemAcc<T> A(S);
+    ExactAcc<T> X(S, M, x0);
+    if (lane == 0) E.ncand[warp] = 0;
+    __syncwarp();
+    const int na = S.na, nv = S.nv, np = S.np;
+    const T hT = (T)h, rpT = (T)rp;
+    const T mg = FILT ? T(2e-3) : T(0);  // margin of the FP32 prefilters (A)
+    const T fd = d0 + T(2e-6);            // error of an FP64 witness rounded into the tile frame
+    const bool inside = lab_s == LABEL_IN;
+    for (int it = lane; it < na + nv + np; it += 32) {
+        if (it < na) {  // convex: van der Waals sphere, witness = projection on the expanded sphere
+            P4<T> c = S.atom[it];
+            T d[3] = {s[0] - c.x, s[1] - c.y, s[2] - c.z};
+            T dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            T reach = c.w + hT + mg;
+            if (dd > reach * reach) continue;
+            T b = d[axis], disc = b * b - (dd - c.w * c.w);
+            if (disc < -mg) continue;
+            T sq = sqrt(fmax(disc, T(0)) + mg);
+            if (-b + sq < -mg || -b - sq > hT + mg) continue;
+            P4<double> ce = X.atom(it);
+            double de[3] = {s64[0] - ce.x, s64[1] - ce.y, s64[2] - ce.z};
+            double co[3] = {de[0] * de[0] + de[1] * de[1] + de[2] * de[2] - ce.w * ce.w, 2.0 * de[axis], 1.0};
+            double rt[2];
+            int nr = PolyRoots<2>::run(co, 0.0, h, rt);
+            for (int k = 0; k < nr; ++k) {
+                double v[3] = {de[0], de[1], de[2]};
+                v[axis] += rt[k];
+                double nvv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+                if (!(nvv > 0.0)) continue;
+                // the witness distance R - |y - c| must fall from an inside end point
+                // and rise from an outside one
+                double rate = -v[axis] / nvv;
+                if (inside ? rate > 1e-9 : rate < -1e-9) continue;
+                double R = ce.w + rp;
+                double q[3] = {ce.x + R * v[0] / nvv, ce.y + R * v[1] / nvv, ce.z + R * v[2] / nvv};
+                int f = FILT ? free_pt<true>(A, (T)q[0], (T)q[1], (T)q[2], S.agid[it], -1, rpT, fd) : -1;
+                if (f < 0) f = free_pt<false>(X, q[0], q[1], q[2], S.agid[it], -1, rp, 0.0);
+                if (f == 1) warp_push(E, warp, rt[k], q[0], q[1], q[2], 0, it);
             }
-            if (!(nw > 0.0)) continue;
-            // d/dt of the distance to the circle: ((|w| - rho) w_a / |w| + z u_a) / r_p
-            double rate = ((nw - rho) * w[axis] / nw + zc * uu[axis]) / rp;
-            if (lab_s == LABEL_IN ? rate > 1e-9 : rate < -1e-9) continue;
-            double qx = o.x + rho * w[0] / nw, qy = o.y + rho * w[1] / nw, qz = o.z + rho * w[2] / nw;
-            int2 ij = S.pij[p];
-            if (free_pt<double, false>(qx, qy, qz, S, ij.x, ij.y, rp, 0.0) == 1) push_cand(c, nc, rt[k], qx, qy, qz);
-            else if (dbg) dbg[6]++;
+        } else if (it < na + nv) {  // concave: probe sphere around a free triple point
+            const int vi = it - na;
+            P4<T> c = S.vq[vi];
+            T d[3] = {s[0] - c.x, s[1] - c.y, s[2] - c.z};
+            T dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            T reach = rpT + hT + mg;
+            if (dd > reach * reach) continue;
+            T b = d[axis], disc = b * b - (dd - rpT * rpT);
+            if (disc < -mg) continue;
+            T sq = sqrt(fmax(disc, T(0)) + mg);
+            if (-b + sq < -mg || -b - sq > hT + mg) continue;
+            P4<double> ce = X.vq(vi);
+            double de[3] = {s64[0] - ce.x, s64[1] - ce.y, s64[2] - ce.z};
+            double co[3] = {de[0] * de[0] + de[1] * de[1] + de[2] * de[2] - rp * rp, 2.0 * de[axis], 1.0};
+            double rt[2];
+            int nr = PolyRoots<2>::run(co, 0.0, h, rt);
+            for (int k = 0; k < nr; ++k) {
+                double rate = (de[axis] + rt[k]) / rp;  // d|y - v|/dt
+                if (inside ? rate > 1e-9 : rate < -1e-9) continue;
+                warp_push(E, warp, rt[k], ce.x, ce.y, ce.z, 2, vi);
+            }
+        } else {  // saddle: torus around a free-arc circle
+            const int pi = it - na - nv;
+            P4<T> o = S.po[pi];
+            P4<T> u = S.pu[pi];
+            // 1-Lipschitz distance to the circle, checked at the edge midpoint
+            T m[3] = {s[0] - o.x, s[1] - o.y, s[2] - o.z};
+            m[axis] += T(0.5) * hT;
+            T zc = m[0] * u.x + m[1] * u.y + m[2] * u.z;
+            T w2 = fmax(m[0] * m[0] + m[1] * m[1] + m[2] * m[2] - zc * zc, T(0));
+            T e1 = sqrt(w2) - o.w;
+            T gm = sqrt(e1 * e1 + zc * zc) - rpT;
+            if (fabs(gm) > T(0.5) * hT + mg) continue;
+            P4<double> oe = X.po(pi);
+            P4<double> ue = X.pu(pi);
+            const double rho = oe.w;
+            double p0[3] = {s64[0] - oe.x, s64[1] - oe.y, s64[2] - oe.z};
+            double uu[3] = {ue.x, ue.y, ue.z};
+            double P = p0[0] * p0[0] + p0[1] * p0[1] + p0[2] * p0[2];
+            double z0 = p0[0] * uu[0] + p0[1] * uu[1] + p0[2] * uu[2];
+            double pe = p0[axis], eu = uu[axis];
+            double K = P + rho * rho - rp * rp;
+            double r2 = rho * rho;
+            double co[5];
+            co[4] = 1.0;
+            co[3] = 4.0 * pe;
+            co[2] = 4.0 * pe * pe + 2.0 * K - 4.0 * r2 * (1.0 - eu * eu);
+            co[1] = 4.0 * pe * K - 8.0 * r2 * (pe - z0 * eu);
+            co[0] = K * K - 4.0 * r2 * (P - z0 * z0);
+            double rt[4];
+            int nr = PolyRoots<4>::run(co, 0.0, h, rt);
+            for (int k = 0; k < nr; ++k) {
+                double y[3] = {p0[0], p0[1], p0[2]};
+                y[axis] += rt[k];
+                double zy = y[0] * uu[0] + y[1] * uu[1] + y[2] * uu[2];
+                double w[3] = {y[0] - zy * uu[0], y[1] - zy * uu[1], y[2] - zy * uu[2]};
+                double nw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+                double near2 = (nw - rho) * (nw - rho) + zy * zy;
+                if (fabs(near2 - rp * rp) > 1e-7 * rp * rp) continue;  // far branch of the quartic
+                if (!(nw > 0.0)) continue;
+                double rate = ((nw - rho) * w[axis] / nw + zy * uu[axis]) / rp;
+                if (inside ? rate > 1e-9 : rate < -1e-9) continue;
+                double q[3] = {oe.x + rho * w[0] / nw, oe.y + rho * w[1] / nw, oe.z + rho * w[2] / nw};
+                int2 ij = S.pij[pi];
+                int f = FILT ? free_pt<true>(A, (T)q[0], (T)q[1], (T)q[2], ij.x, ij.y, rpT, fd) : -1;
+                if (f < 0) f = free_pt<false>(X, q[0], q[1], q[2], ij.x, ij.y, rp, 0.0);
+                if (f == 1) warp_push(E, warp, rt[k], q[0], q[1], q[2], 1, pi);
+            }
         }
     }
-    if (dbg) {
-        dbg[7] = nc;
-        for (int k = 0; k < nc && k < 7; ++k) dbg[9 + k] = (long long)(c[k].t * 1e9);
-    }
-    if (nc == 0) return false;
+    __syncwarp();
+    int n = E.ncand[warp];
+    int status = n > WCAND ? 2 : 0;  // 2: candidate buffer overflow
+    if (n > WCAND) n = WCAND;
+    WCand *c = E.cand[warp];
     int pick = -1;
-    if (lab_s == LABEL_IN) {
-        pick = 0;
+    if (inside) {
+        pick = warp_argmin(c, n);
     } else {
-        for (int k = 0; k < nc; ++k) {
-            double y[3] = {s[0], s[1], s[2]};
+        for (int iter = 0; iter < n; ++iter) {
+            int k = warp_argmin(c, n);
+            if (k < 0) break;
+            double y[3] = {s64[0], s64[1], s64[2]};
             y[axis] += c[k].t;
-            // not strictly outside M: no free centre closer than r_p - 1e-11
-            if (classify_pt<double, false>(y[0], y[1], y[2], S, rp, rp - 1e-11, 0.0) == 1) {
+            int r;
+            if (FILT) {
+                r = warp_witness<true>(A, (T)y[0], (T)y[1], (T)y[2], rpT, rpT, d0, c[k].kind, c[k].id);
+                if (r < 0) r = warp_witness<false>(X, y[0], y[1], y[2], rp, rp - 1e-11, 0.0, -1, -1);
+            } else {
+                r = warp_witness<false>(X, y[0], y[1], y[2], rp, rp - 1e-11, 0.0, -1, -1);
+            }
+            if (r == 0) {
                 pick = k;
                 break;
             }
-            if (dbg) dbg[8]++;
+            __syncwarp();
+            if (lane == 0) c[k].t = INFINITY;  // strictly outside M: not the root
+            __syncwarp();
         }
     }
-    if (pick < 0) return false;
+    if (pick < 0) return 1;
     t_out = c[pick].t;
     q_out[0] = c[pick].qx;
     q_out[1] = c[pick].qy;
     q_out[2] = c[pick].qz;
-    return true;
+    return status;
 }
 
 // --------------------------------------------------------------------------
@@ -382,12 +449,7 @@ __device__ __forceinline__ int block_excl_scan_e(int v, int *sh, int *total)
     return base + inc - v;
 }
 
-struct EdgeSmem {
-    int8_t lab[9 * 9 * 9];
-    int sh[EDGE_THREADS / 32];
-    double shd[EDGE_THREADS / 32];
-};
-
+template <class T, bool FILT>
 __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Grid G, const int8_t *__restrict__ labels,
                                                              const int *__restrict__ edge_start, EdgeOut out,
                                                              double *__restrict__ tile_area,
@@ -395,11 +457,13 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Grid G, co
                                                              int *__restrict__ err, long long *__restrict__ fail_log)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    TileS<double> &S = *reinterpret_cast<TileS<double> *>(smem_raw);
-    __shared__ EdgeSmem E;
+    TileS<T> &S = *reinterpret_cast<TileS<T> *>(smem_raw);
+    EdgeSmem &E = *reinterpret_cast<EdgeSmem *>(smem_raw + ((sizeof(TileS<T>) + 15) & ~(size_t)15));
     const long long nt = G.n_tiles;
     const long long st1 = G.dims[2], st0 = G.dims[1] * G.dims[2];
     const double h = G.h, rp = M.rp;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const T d0 = FILT ? (T)G.d0 : T(0);
     for (long long tile = blockIdx.x; tile < nt; tile += gridDim.x) {
         int tot = 0;
         for (int a = 0; a < 3; ++a) tot += edge_start[a * nt + tile + 1] - edge_start[a * nt + tile];
@@ -411,75 +475,90 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Grid G, co
             continue;
         }
         double x0[3];
-        stage_tile<double>(M, G, tile, S, x0);
+        stage_tile<T>(M, G, tile, S, x0);
         if (threadIdx.x == 0 && S.flags) atomicOr(err, S.flags);
         int t[3];
         tile_coords(G, tile, t);
         // labels of the tile and of the next layer (9^3), -1 outside the grid
-        for (int p = threadIdx.x; p < 729; p += EDGE_THREADS) {
-            int li = p / 81, lj = (p / 9) % 9, lk = p % 9;
+        for (int q = threadIdx.x; q < 729; q += EDGE_THREADS) {
+            int li = q / 81, lj = (q / 9) % 9, lk = q % 9;
             long long g[3] = {(long long)TILE * t[0] + li, (long long)TILE * t[1] + lj, (long long)TILE * t[2] + lk};
             int8_t v = -1;
             if (g[0] < G.dims[0] && g[1] < G.dims[1] && g[2] < G.dims[2]) v = labels[g[0] * st0 + g[1] * st1 + g[2]];
-            E.lab[p] = v;
+            E.lab[q] = v;
         }
+        if (threadIdx.x == 0) E.estart[0] = 0;
         __syncthreads();
-        double area = 0.0, vol = 0.0;
+        // the tile's crossing edges, axis by axis, in point order
         for (int a = 0; a < 3; ++a) {
-            const long long base = (long long)edge_start[a * nt + tile] - edge_start[a * nt];
-            // two consecutive points per thread keep the output in point order
             int flag[2];
             for (int k = 0; k < 2; ++k) {
-                int p = 2 * threadIdx.x + k;
-                int li = p >> 6, lj = (p >> 3) & 7, lk = p & 7;
-                int l[3] = {li, lj, lk};
-                int8_t l0 = E.lab[(li * 9 + lj) * 9 + lk];
+                int q = 2 * threadIdx.x + k;
+                int l[3] = {q >> 6, (q >> 3) & 7, q & 7};
+                int8_t l0 = E.lab[(l[0] * 9 + l[1]) * 9 + l[2]];
                 l[a] += 1;
                 int8_t l1 = E.lab[(l[0] * 9 + l[1]) * 9 + l[2]];
                 flag[k] = (l0 >= 0 && l1 >= 0 && l0 != l1) ? 1 : 0;
             }
             int tsum;
             int rank = block_excl_scan_e(flag[0] + flag[1], E.sh, &tsum);
-            for (int k = 0; k < 2; ++k) {
-                if (!flag[k]) continue;
-                int p = 2 * threadIdx.x + k;
-                int li = p >> 6, lj = (p >> 3) & 7, lk = p & 7;
-                int lab_s = E.lab[(li * 9 + lj) * 9 + lk];
-                double s[3] = {(double)li * h, (double)lj * h, (double)lk * h};
-                double tr = 0.5 * h, q[3] = {0.0, 0.0, 0.0};
+            const int base = E.estart[a];
+            for (int k = 0; k < 2; ++k)
+                if (flag[k]) E.eptr[base + rank++] = (short)(2 * threadIdx.x + k);
+            if (threadIdx.x == 0) {
+                E.estart[a + 1] = base + tsum;
+                E.ebase[a] = (long long)edge_start[a * nt + tile] - edge_start[a * nt];
+            }
+            __syncthreads();
+        }
+        double area = 0.0, vol = 0.0;
+        const int ne = E.estart[3];
+        for (int e = warp; e < ne; e += EDGE_WARPS) {
+            const int a = e < E.estart[1] ? 0 : (e < E.estart[2] ? 1 : 2);
+            const int q = E.eptr[e];
+            const int li = q >> 6, lj = (q >> 3) & 7, lk = q & 7;
+            const int lab_s = E.lab[(li * 9 + lj) * 9 + lk];
+            double tr = 0.5 * h, qq[3] = {0.0, 0.0, 0.0};
+            int status = warp_edge<T, FILT>(M, S, x0, E, warp, a, q, lab_s, h, rp, d0, tr, qq);
+            if (lane == 0) {
                 double nrm[3] = {0.0, 0.0, 0.0};
-                if (edge_root(S, s, a, h, rp, lab_s, tr, q)) {
-                    double y[3] = {s[0], s[1], s[2]};
+                if (status != 1) {
+                    double y[3] = {(double)li * h, (double)lj * h, (double)lk * h};
                     y[a] += tr;
-                    double v[3] = {q[0] - y[0], q[1] - y[1], q[2] - y[2]};
+                    double v[3] = {qq[0] - y[0], qq[1] - y[1], qq[2] - y[2]};
                     double nv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
                     if (nv > 0.0) {
                         nrm[0] = v[0] / nv;
                         nrm[1] = v[1] / nv;
                         nrm[2] = v[2] / nv;
                     }
-                } else {
-                    int slot = atomicAdd(n_fail, 1);
-                    atomicOr(err, ERR_ROOT);
-                    if (slot < FAIL_LOG) {
-                        long long *rec = fail_log + FAIL_REC * slot;
-                        for (int z = 0; z < FAIL_REC; ++z) rec[z] = 0;
-                        double tt, qq[3];
-                        edge_root(S, s, a, h, rp, lab_s, tt, qq, rec + 8);
-                        rec[0] = a;
-                        rec[1] = (long long)TILE * t[0] + li;
-                        rec[2] = (long long)TILE * t[1] + lj;
-                        rec[3] = (long long)TILE * t[2] + lk;
-                        rec[4] = lab_s;
-                        rec[5] = S.na;
-                        rec[6] = S.np;
-                        rec[7] = S.nv;
+                }
+                if (status != 0) {
+                    atomicOr(err, status == 1 ? ERR_ROOT : ERR_CAP_CAND);
+                    if (status == 1) {
+                        int slot = atomicAdd(n_fail, 1);
+                        if (slot < FAIL_LOG) {
+                            long long *rec = fail_log + FAIL_REC * slot;
+                            for (int z = 0; z < FAIL_REC; ++z) rec[z] = 0;
+                            rec[0] = a;
+                            rec[1] = (long long)TILE * t[0] + li;
+                            rec[2] = (long long)TILE * t[1] + lj;
+                            rec[3] = (long long)TILE * t[2] + lk;
+                            rec[4] = lab_s;
+                            rec[5] = S.na;
+                            rec[6] = S.np;
+                            rec[7] = S.nv;
+                            rec[8] = E.ncand[warp];
+                            for (int z = 0; z < 7 && z < E.ncand[warp] && z < WCAND; ++z) {
+                                rec[9 + z] = (long long)(E.cand[warp][z].t * 1e9);
+                                rec[16 + z] = E.cand[warp][z].kind;
+                            }
+                        }
                     }
                 }
-                long long g[3] = {(long long)TILE * t[0] + li, (long long)TILE * t[1] + lj,
-                                  (long long)TILE * t[2] + lk};
-                long long o = base + rank;
-                out.idx[a][o] = g[0] * st0 + g[1] * st1 + g[2];
+                const long long o = E.ebase[a] + (e - E.estart[a]);
+                out.idx[a][o] = (long long)(TILE * t[0] + li) * st0 + (long long)(TILE * t[1] + lj) * st1 +
+                                (TILE * t[2] + lk);
                 out.tau[a][o] = tr / h;
                 out.nrm[a][3 * o + 0] = nrm[0];
                 out.nrm[a][3 * o + 1] = nrm[1];
@@ -490,8 +569,8 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Grid G, co
                 out.nrm32[a][3 * o + 2] = (float)nrm[2];
                 area += h * h * fabs(nrm[a]);
                 vol += lab_s == LABEL_IN ? tr : h - tr;
-                ++rank;
             }
+            __syncwarp();
         }
         double ta = block_sum_double(area, E.shd);
         double tv = block_sum_double(vol, E.shd);
@@ -563,14 +642,25 @@ int launch_edge_count(const Grid &G, const int8_t *labels, int *tile_edges, int 
     return 1;
 }
 
-int launch_edge_solve(const Model &M, const Grid &G, const int8_t *labels, const int *edge_start, EdgeOut out,
-                       double *tile_area, double *tile_vol, int *n_fail, int *err, long long *fail_log,
-                       cudaStream_t st)
+template <class T, bool FILT>
+static void edge_solve_launch(const Model &M, const Grid &G, const int8_t *labels, const int *edge_start, EdgeOut out,
+                              double *tile_area, double *tile_vol, int *n_fail, int *err, long long *fail_log,
+                              cudaStream_t st)
 {
-    size_t sm = sizeof(TileS<double>);
-    cudaFuncSetAttribute(k_edge_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_edge_solve<<<grid_tiles(G.n_tiles), EDGE_THREADS, sm, st>>>(M, G, labels, edge_start, out, tile_area, tile_vol,
-                                                                  n_fail, err, fail_log);
+    size_t sm = ((sizeof(TileS<T>) + 15) & ~(size_t)15) + sizeof(EdgeSmem);
+    cudaFuncSetAttribute(k_edge_solve<T, FILT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_edge_solve<T, FILT><<<grid_tiles(G.n_tiles), EDGE_THREADS, sm, st>>>(M, G, labels, edge_start, out, tile_area,
+                                                                           tile_vol, n_fail, err, fail_log);
+}
+
+int launch_edge_solve(const Model &M, const Grid &G, int precision, const int8_t *labels, const int *edge_start,
+                      EdgeOut out, double *tile_area, double *tile_vol, int *n_fail, int *err, long long *fail_log,
+                      cudaStream_t st)
+{
+    if (precision == 0)
+        edge_solve_launch<double, false>(M, G, labels, edge_start, out, tile_area, tile_vol, n_fail, err, fail_log, st);
+    else
+        edge_solve_launch<float, true>(M, G, labels, edge_start, out, tile_area, tile_vol, n_fail, err, fail_log, st);
     return 1;
 }
 

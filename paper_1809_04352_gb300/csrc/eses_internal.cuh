@@ -36,6 +36,7 @@ enum : int {
     ERR_ROOT = 8,
     ERR_TIMEOUT = 16,
     ERR_CAP_EDGES = 32,
+    ERR_CAP_CAND = 64,
 };
 
 // label codes in the label array

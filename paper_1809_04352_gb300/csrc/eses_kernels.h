@@ -53,9 +53,9 @@ struct EdgeOut {
 // staged atoms/pairs/vertices, then the 16 edge_root debug counters)
 constexpr int FAIL_LOG = 8;
 constexpr int FAIL_REC = 24;
-int launch_edge_solve(const Model &M, const Grid &G, const int8_t *labels, const int *edge_start, EdgeOut out,
-                       double *tile_area, double *tile_vol, int *n_fail, int *err, long long *fail_log,
-                       cudaStream_t st);
+int launch_edge_solve(const Model &M, const Grid &G, int precision, const int8_t *labels, const int *edge_start,
+                      EdgeOut out, double *tile_area, double *tile_vol, int *n_fail, int *err, long long *fail_log,
+                      cudaStream_t st);
 int launch_reduce(const Grid &G, const double *tile_area, const double *tile_vol, const int *tile_inside_edges,
                    const int8_t *labels, double *out2, long long *counts, cudaStream_t st);
 

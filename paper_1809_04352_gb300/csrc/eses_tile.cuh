@@ -10,13 +10,18 @@
 //             of x can cover a probe centre that would reach x)
 //   pairs     with a free arc and dist(o, region) < rho + r_p
 //   vertices  free triple points with dist(v, region) < r_p
+// Every staged item keeps its index in the model, so exact FP64 values in
+// the same tile frame can be fetched from HBM (ExactAcc) when an FP32 test
+// is undecided.
 //
 // Classification of a point x (Eq. 2): x is outside M iff some free probe
 // centre lies at distance < r_p.  The nearest free point, when it is that
 // close, is the radial projection on a containing expanded sphere (convex
-// patch), the nearest point of a pair circle (saddle), or a free triple point
-// (concave); each candidate counts only if it is free.  Inside a van der
-// Waals ball x is always in M; outside every expanded ball x is free.
+// patch), the nearest point of a pair circle (saddle) -- and then x lies in
+// one of the pair's two expanded balls, since x is in the triangle of the two
+// centres and that point -- or a free triple point (concave); each candidate
+// counts only if it is free.  Inside a van der Waals ball x is always in M;
+// outside every expanded ball x is free.
 //
 // FP32 filtering: every comparison of a computed squared distance with a
 // threshold t^2 is accepted only if it clears an error bound
@@ -46,8 +51,65 @@ struct TileS {
     P4<T> vq[V_MAX];        // free triple point (tile frame)
     int agid[A_MAX];        // sorted atom index
     int2 pij[P_MAX];        // sorted atom indices of the pair
+    int pidx[P_MAX];        // pair index in the model
+    int vidx[V_MAX];        // triple point index in the model
     uint8_t aface[A_MAX];   // expanded sphere keeps a free face
     int na, np, nv, flags;
+};
+
+// ---------------------------------------------------------------------------
+// accessors: staged (shared memory) or exact (FP64 from HBM, same tile frame)
+// ---------------------------------------------------------------------------
+template <class T>
+struct SmemAcc {
+    using real = T;
+    const TileS<T> &S;
+    __device__ SmemAcc(const TileS<T> &s) : S(s) {}
+    __device__ int na() const { return S.na; }
+    __device__ int np() const { return S.np; }
+    __device__ int nv() const { return S.nv; }
+    __device__ P4<T> atom(int a) const { return S.atom[a]; }
+    __device__ int agid(int a) const { return S.agid[a]; }
+    __device__ bool face(int a) const { return S.aface[a] != 0; }
+    __device__ P4<T> po(int p) const { return S.po[p]; }
+    __device__ P4<T> pu(int p) const { return S.pu[p]; }
+    __device__ int2 pij(int p) const { return S.pij[p]; }
+    __device__ P4<T> vq(int v) const { return S.vq[v]; }
+};
+
+template <class TS>
+struct ExactAcc {
+    using real = double;
+    const TileS<TS> &S;
+    const Model &M;
+    double x0, y0, z0;
+    __device__ ExactAcc(const TileS<TS> &s, const Model &m, const double *o) : S(s), M(m), x0(o[0]), y0(o[1]), z0(o[2]) {}
+    __device__ int na() const { return S.na; }
+    __device__ int np() const { return S.np; }
+    __device__ int nv() const { return S.nv; }
+    __device__ P4<double> atom(int a) const
+    {
+        double4 g = M.atom[S.agid[a]];
+        return P4<double>{g.x - x0, g.y - y0, g.z - z0, g.w};
+    }
+    __device__ int agid(int a) const { return S.agid[a]; }
+    __device__ bool face(int a) const { return S.aface[a] != 0; }
+    __device__ P4<double> po(int p) const
+    {
+        double4 g = M.pair_o[S.pidx[p]];
+        return P4<double>{g.x - x0, g.y - y0, g.z - z0, g.w};
+    }
+    __device__ P4<double> pu(int p) const
+    {
+        double4 g = M.pair_u[S.pidx[p]];
+        return P4<double>{g.x, g.y, g.z, 0.0};
+    }
+    __device__ int2 pij(int p) const { return S.pij[p]; }
+    __device__ P4<double> vq(int v) const
+    {
+        double4 g = M.vert[S.vidx[v]];
+        return P4<double>{g.x - x0, g.y - y0, g.z - z0, 0.0};
+    }
 };
 
 __device__ __forceinline__ int cell_coord_d(double v, double lo, double cell, int n)
@@ -124,6 +186,7 @@ __device__ void stage_tile(const Model &M, const Grid &G, long long tile, TileS<
                     S.po[s] = P4<T>{(T)(o.x - x0[0]), (T)(o.y - x0[1]), (T)(o.z - x0[2]), (T)o.w};
                     S.pu[s] = P4<T>{(T)u.x, (T)u.y, (T)u.z, (T)0};
                     S.pij[s] = M.pair_ij[p];
+                    S.pidx[s] = p;
                 }
             }
         }
@@ -133,7 +196,10 @@ __device__ void stage_tile(const Model &M, const Grid &G, long long tile, TileS<
             double reach = rp + tol;
             if (box_dist2(q.x, q.y, q.z, x0, x1) < reach * reach) {
                 int s = atomicAdd(&S.nv, 1);
-                if (s < V_MAX) S.vq[s] = P4<T>{(T)(q.x - x0[0]), (T)(q.y - x0[1]), (T)(q.z - x0[2]), (T)0};
+                if (s < V_MAX) {
+                    S.vq[s] = P4<T>{(T)(q.x - x0[0]), (T)(q.y - x0[1]), (T)(q.z - x0[2]), (T)0};
+                    S.vidx[s] = v;
+                }
             }
         }
     }
@@ -170,14 +236,15 @@ __device__ __forceinline__ int lt_lin(T a, T b, T e)
 
 // Freeness of q against every staged atom but e0, e1 (sorted indices of the
 // atoms whose spheres carry q).  1 free, 0 covered, -1 undecided.
-template <class T, bool FILT>
-__device__ __forceinline__ int free_pt(T qx, T qy, T qz, const TileS<T> &S, int e0, int e1, T rp, T delta)
+template <bool FILT, class Acc, class T>
+__device__ __forceinline__ int free_pt(const Acc &A, T qx, T qy, T qz, int e0, int e1, T rp, T delta)
 {
     int res = 1;
-    for (int k = 0; k < S.na; ++k) {
-        int g = S.agid[k];
+    const int na = A.na();
+    for (int k = 0; k < na; ++k) {
+        int g = A.agid(k);
         if (g == e0 || g == e1) continue;
-        P4<T> c = S.atom[k];
+        P4<T> c = A.atom(k);
         T dx = qx - c.x, dy = qy - c.y, dz = qz - c.z;
         T R = c.w + rp;
         int t = lt_sq<FILT>(dx * dx + dy * dy + dz * dz, R * R, R, delta);
@@ -187,15 +254,75 @@ __device__ __forceinline__ int free_pt(T qx, T qy, T qz, const TileS<T> &S, int 
     return res;
 }
 
+// Convex witness of atom a at x: 1 free projection at distance < thr,
+// 0 none, -1 undecided.
+template <bool FILT, class Acc, class T>
+__device__ __forceinline__ int face_witness(const Acc &A, int a, T x, T y, T z, T rp, T thr, T d0)
+{
+    if (!A.face(a)) return 0;
+    P4<T> c = A.atom(a);
+    T dx = x - c.x, dy = y - c.y, dz = z - c.z;
+    T d2 = dx * dx + dy * dy + dz * dz;
+    T R = c.w + rp;
+    if (lt_sq<FILT>(d2, R * R, R, d0) == 0) return 0;
+    T d = sqrt(d2);
+    if (d <= T(1e-3)) return FILT ? -1 : 0;  // x at a centre is inside its vdW ball
+    T wd = fabs(R - d);                        // distance to the projection
+    int tw = lt_lin<FILT>(wd, thr, d0 + T(1e-6) * R);
+    if (tw == 0) return 0;
+    T s = R / d;
+    T dq = FILT ? d0 * (T(1) + T(2) * R / d) + T(1e-6) * R : T(0);
+    int f = free_pt<FILT>(A, c.x + s * dx, c.y + s * dy, c.z + s * dz, A.agid(a), -1, rp, dq + d0);
+    if (f == 1 && tw == 1) return 1;
+    return f == 0 ? 0 : -1;
+}
+
+// Saddle witness of pair p at x: nearest point of its circle.
+template <bool FILT, class Acc, class T>
+__device__ __forceinline__ int saddle_witness(const Acc &A, int p, T x, T y, T z, T rp, T thr, T d0)
+{
+    P4<T> o = A.po(p);
+    P4<T> u = A.pu(p);
+    T yx = x - o.x, yy = y - o.y, yz = z - o.z;
+    T zc = yx * u.x + yy * u.y + yz * u.z;
+    T wx = yx - zc * u.x, wy = yy - zc * u.y, wz = yz - zc * u.z;
+    T w2 = wx * wx + wy * wy + wz * wz;
+    T nw = sqrt(w2);
+    T e1 = nw - o.w;
+    T dist2 = e1 * e1 + zc * zc;
+    T dw = FILT ? T(2) * d0 + T(2e-6) * (nw + fabs(zc)) : T(0);
+    int t = lt_sq<FILT>(dist2, thr * thr, thr, T(1.5) * dw + T(1e-6));
+    if (t == 0) return 0;
+    if (FILT && nw < T(1e-3)) return -1;  // near the circle's axis the nearest point is ill-conditioned
+    T qx, qy, qz;
+    if (w2 > T(0)) {
+        T k = o.w / nw;
+        qx = o.x + k * wx; qy = o.y + k * wy; qz = o.z + k * wz;
+    } else {
+        // x on the axis: every circle point is nearest; take one
+        T ax = fabs(u.x) > T(0.6) ? T(0) : T(1), ay = fabs(u.x) > T(0.6) ? T(1) : T(0);
+        T vx = -u.z * ay, vy = u.z * ax, vz = u.x * ay - u.y * ax;
+        T nv = sqrt(vx * vx + vy * vy + vz * vz);
+        qx = o.x + o.w * vx / nv; qy = o.y + o.w * vy / nv; qz = o.z + o.w * vz / nv;
+    }
+    T dq = FILT ? o.w * T(2) * dw / nw + d0 + T(1e-6) * o.w : T(0);
+    int2 ij = A.pij(p);
+    int f = free_pt<FILT>(A, qx, qy, qz, ij.x, ij.y, rp, dq + d0);
+    if (f == 1 && t == 1) return 1;
+    return f == 0 ? 0 : -1;
+}
+
 // Label of the point (x,y,z) in the tile frame: 1 if no free probe centre lies
 // at distance < thr (thr = r_p for Eq. 2), 0 otherwise, 2 undecided (FP32).
-template <class T, bool FILT>
-__device__ int classify_pt(T x, T y, T z, const TileS<T> &S, T rp, T thr, T d0)
+// Per thread, over all staged items.
+template <bool FILT, class Acc, class T>
+__device__ int classify_pt(const Acc &A, T x, T y, T z, T rp, T thr, T d0)
 {
     const T thr2 = thr * thr;
     bool in_sas = false, unsure_sas = false;
-    for (int a = 0; a < S.na; ++a) {
-        P4<T> c = S.atom[a];
+    const int na = A.na(), np = A.np(), nv = A.nv();
+    for (int a = 0; a < na; ++a) {
+        P4<T> c = A.atom(a);
         T dx = x - c.x, dy = y - c.y, dz = z - c.z;
         T d2 = dx * dx + dy * dy + dz * dz;
         T r = c.w, R = c.w + rp;
@@ -206,73 +333,75 @@ __device__ int classify_pt(T x, T y, T z, const TileS<T> &S, T rp, T thr, T d0)
     }
     if (!in_sas) return unsure_sas ? 2 : 0;  // free point: dist 0
     bool unsure = false;
-    // concave: free triple points
-    for (int v = 0; v < S.nv; ++v) {
-        P4<T> q = S.vq[v];
+    for (int v = 0; v < nv; ++v) {
+        P4<T> q = A.vq(v);
         T dx = x - q.x, dy = y - q.y, dz = z - q.z;
         int t = lt_sq<FILT>(dx * dx + dy * dy + dz * dz, thr2, thr, d0);
         if (t == 1) return 0;
         if (t < 0) unsure = true;
     }
-    // convex: radial projection on an expanded sphere that (nearly) contains x
-    for (int a = 0; a < S.na; ++a) {
-        if (!S.aface[a]) continue;
-        P4<T> c = S.atom[a];
-        T dx = x - c.x, dy = y - c.y, dz = z - c.z;
-        T d2 = dx * dx + dy * dy + dz * dz;
-        T R = c.w + rp;
-        if (lt_sq<FILT>(d2, R * R, R, d0) == 0) continue;
-        T d = sqrt(d2);
-        if (d <= T(1e-3)) {
-            if (FILT) unsure = true;
-            continue;  // x at a centre is inside its vdW ball (returned above)
-        }
-        T wd = fabs(R - d);  // distance to the projection
-        int tw = lt_lin<FILT>(wd, thr, d0 + T(1e-6) * R);
-        if (tw == 0) continue;
-        T s = R / d;
-        T qx = c.x + s * dx, qy = c.y + s * dy, qz = c.z + s * dz;
-        T dq = FILT ? d0 * (T(1) + T(2) * R / d) + T(1e-6) * R : T(0);
-        int f = free_pt<T, FILT>(qx, qy, qz, S, S.agid[a], -1, rp, dq + d0);
-        if (f == 1 && tw == 1) return 0;
-        if (f != 0) unsure = true;
+    for (int a = 0; a < na; ++a) {
+        int w = face_witness<FILT>(A, a, x, y, z, rp, thr, d0);
+        if (w == 1) return 0;
+        if (w < 0) unsure = true;
     }
-    // saddle: nearest point of every free-arc circle
-    for (int p = 0; p < S.np; ++p) {
-        P4<T> o = S.po[p];
-        P4<T> u = S.pu[p];
-        T yx = x - o.x, yy = y - o.y, yz = z - o.z;
-        T zc = yx * u.x + yy * u.y + yz * u.z;
-        T wx = yx - zc * u.x, wy = yy - zc * u.y, wz = yz - zc * u.z;
-        T w2 = wx * wx + wy * wy + wz * wz;
-        T nw = sqrt(w2);
-        T e1 = nw - o.w;
-        T dist2 = e1 * e1 + zc * zc;
-        T dw = FILT ? T(2) * d0 + T(2e-6) * (nw + fabs(zc)) : T(0);
-        int t = lt_sq<FILT>(dist2, thr2, thr, T(1.5) * dw + T(1e-6));
-        if (t == 0) continue;
-        if (FILT && nw < T(1e-3)) {
-            unsure = true;  // x near the circle's axis: the nearest point is ill-conditioned
-            continue;
-        }
-        T qx, qy, qz;
-        if (w2 > T(0)) {
-            T k = o.w / nw;
-            qx = o.x + k * wx; qy = o.y + k * wy; qz = o.z + k * wz;
-        } else {
-            // x on the axis: every circle point is nearest; take one
-            T ax = fabs(u.x) > T(0.6) ? T(0) : T(1), ay = fabs(u.x) > T(0.6) ? T(1) : T(0);
-            T vx = u.y * T(0) - u.z * ay, vy = u.z * ax - u.x * T(0), vz = u.x * ay - u.y * ax;
-            T nv = sqrt(vx * vx + vy * vy + vz * vz);
-            qx = o.x + o.w * vx / nv; qy = o.y + o.w * vy / nv; qz = o.z + o.w * vz / nv;
-        }
-        T dq = FILT ? o.w * T(2) * dw / nw + d0 + T(1e-6) * o.w : T(0);
-        int2 ij = S.pij[p];
-        int f = free_pt<T, FILT>(qx, qy, qz, S, ij.x, ij.y, rp, dq + d0);
-        if (f == 1 && t == 1) return 0;
-        if (f != 0) unsure = true;
+    for (int p = 0; p < np; ++p) {
+        int w = saddle_witness<FILT>(A, p, x, y, z, rp, thr, d0);
+        if (w == 1) return 0;
+        if (w < 0) unsure = true;
     }
     return unsure ? 2 : 1;
+}
+
+// Warp-cooperative witness search at one point (all 32 lanes call it with the
+// same point): 1 if a free probe centre lies at distance < thr (certain),
+// 0 if none does (certain), -1 undecided.  Items (exclude_kind, exclude_id)
+// are skipped: kind 0 atom (convex witness), 1 pair, 2 vertex, -1 none.
+template <bool FILT, class Acc, class T>
+__device__ int warp_witness(const Acc &A, T x, T y, T z, T rp, T thr, T d0, int exclude_kind, int exclude_id)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int na = A.na(), np = A.np(), nv = A.nv();
+    bool vdw = false, sas = false, sas_u = false;
+    for (int a = lane; a < na; a += 32) {
+        P4<T> c = A.atom(a);
+        T dx = x - c.x, dy = y - c.y, dz = z - c.z;
+        T d2 = dx * dx + dy * dy + dz * dz;
+        T r = c.w, R = c.w + rp;
+        if (lt_sq<FILT>(d2, r * r, r, d0) == 1) vdw = true;
+        int s = lt_sq<FILT>(d2, R * R, R, d0);
+        if (s == 1) sas = true;
+        else if (s < 0) sas_u = true;
+    }
+    if (__any_sync(full, vdw)) return 0;
+    if (!__any_sync(full, sas)) return __any_sync(full, sas_u) ? -1 : 1;
+    bool found = false, und = false;
+    const T thr2 = thr * thr;
+    for (int v = lane; v < nv; v += 32) {
+        if (exclude_kind == 2 && v == exclude_id) continue;
+        P4<T> q = A.vq(v);
+        T dx = x - q.x, dy = y - q.y, dz = z - q.z;
+        int t = lt_sq<FILT>(dx * dx + dy * dy + dz * dz, thr2, thr, d0);
+        if (t == 1) found = true;
+        else if (t < 0) und = true;
+    }
+    if (__any_sync(full, found)) return 1;
+    for (int a = lane; a < na; a += 32) {
+        if (exclude_kind == 0 && a == exclude_id) continue;
+        int w = face_witness<FILT>(A, a, x, y, z, rp, thr, d0);
+        if (w == 1) found = true;
+        else if (w < 0) und = true;
+    }
+    if (__any_sync(full, found)) return 1;
+    for (int p = lane; p < np; p += 32) {
+        if (exclude_kind == 1 && p == exclude_id) continue;
+        int w = saddle_witness<FILT>(A, p, x, y, z, rp, thr, d0);
+        if (w == 1) found = true;
+        else if (w < 0) und = true;
+    }
+    if (__any_sync(full, found)) return 1;
+    return __any_sync(full, und) ? -1 : 0;
 }
 
 }  // namespace eses
