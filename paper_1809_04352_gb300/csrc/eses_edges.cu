@@ -33,63 +33,72 @@ constexpr int EDGE_THREADS = 256;
 // --------------------------------------------------------------------------
 // polynomial roots on an interval
 // --------------------------------------------------------------------------
-template <int DEG>
-__device__ __forceinline__ double horner(const double *c, double t)
+template <class R>
+__device__ __forceinline__ R root_eps();
+template <>
+__device__ __forceinline__ double root_eps<double>() { return 1e-15; }
+template <>
+__device__ __forceinline__ float root_eps<float>() { return 2e-7f; }
+
+template <class R, int DEG>
+__device__ __forceinline__ R horner(const R *c, R t)
 {
-    double v = c[DEG];
+    R v = c[DEG];
 #pragma unroll
     for (int k = DEG - 1; k >= 0; --k) v = fma(v, t, c[k]);
     return v;
 }
 
 // root of c on [a, b], where c is monotone and f(a) (= fa) and f(b) differ in sign
-template <int DEG>
-__device__ double mono_root(const double *c, double a, double b, double fa)
+template <class R, int DEG>
+__device__ R mono_root(const R *c, R a, R b, R fa)
 {
-    double dc[DEG];
+    R dc[DEG];
 #pragma unroll
-    for (int k = 0; k < DEG; ++k) dc[k] = (double)(k + 1) * c[k + 1];
-    double t = 0.5 * (a + b);
+    for (int k = 0; k < DEG; ++k) dc[k] = (R)(k + 1) * c[k + 1];
+    R t = R(0.5) * (a + b);
     for (int it = 0; it < 100; ++it) {
-        double f = horner<DEG>(c, t);
-        if (f == 0.0) return t;
-        if ((f < 0.0) == (fa < 0.0)) a = t;
+        R f = horner<R, DEG>(c, t);
+        if (f == R(0)) return t;
+        if ((f < R(0)) == (fa < R(0))) a = t;
         else b = t;
-        double df = horner<DEG - 1>(dc, t);
-        double tn = (df != 0.0) ? t - f / df : 0.5 * (a + b);
-        if (!(tn > a && tn < b)) tn = 0.5 * (a + b);
-        if (fabs(tn - t) <= 1e-15 * fmax(1.0, fabs(t))) return tn;
+        R df = horner<R, DEG - 1>(dc, t);
+        R tn = (df != R(0)) ? t - f / df : R(0.5) * (a + b);
+        if (!(tn > a && tn < b)) tn = R(0.5) * (a + b);
+        if (fabs(tn - t) <= root_eps<R>() * fmax(R(1), fabs(t))) return tn;
         t = tn;
-        if (b - a <= 1e-15 * fmax(1.0, fabs(a))) return 0.5 * (a + b);
+        if (b - a <= root_eps<R>() * fmax(R(1), fabs(a))) return R(0.5) * (a + b);
     }
     return t;
 }
 
-// roots of c[0] + c[1] t + ... + c[DEG] t^DEG in [lo, hi], ascending
-template <int DEG>
+// roots of c[0] + c[1] t + ... + c[DEG] t^DEG in [lo, hi], ascending: the
+// derivative's roots split [lo, hi] into monotone pieces, each holding at most
+// one root, found by safeguarded Newton-bisection
+template <class R, int DEG>
 struct PolyRoots {
-    __device__ static int run(const double *c, double lo, double hi, double *out)
+    __device__ static int run(const R *c, R lo, R hi, R *out)
     {
-        double dc[DEG];
+        R dc[DEG];
 #pragma unroll
-        for (int k = 0; k < DEG; ++k) dc[k] = (double)(k + 1) * c[k + 1];
-        double crit[DEG - 1];
-        int ncr = PolyRoots<DEG - 1>::run(dc, lo, hi, crit);
-        double pts[DEG + 1];
+        for (int k = 0; k < DEG; ++k) dc[k] = (R)(k + 1) * c[k + 1];
+        R crit[DEG - 1];
+        int ncr = PolyRoots<R, DEG - 1>::run(dc, lo, hi, crit);
+        R pts[DEG + 1];
         int np = 0;
         pts[np++] = lo;
         for (int k = 0; k < ncr; ++k)
             if (crit[k] > pts[np - 1] && crit[k] < hi) pts[np++] = crit[k];
         pts[np++] = hi;
         int n = 0;
-        double fprev = horner<DEG>(c, pts[0]);
-        if (fprev == 0.0) out[n++] = pts[0];
+        R fprev = horner<R, DEG>(c, pts[0]);
+        if (fprev == R(0)) out[n++] = pts[0];
         for (int k = 0; k + 1 < np; ++k) {
-            double fnext = horner<DEG>(c, pts[k + 1]);
-            if (fnext == 0.0) {
+            R fnext = horner<R, DEG>(c, pts[k + 1]);
+            if (fnext == R(0)) {
                 if (n == 0 || out[n - 1] != pts[k + 1]) out[n++] = pts[k + 1];
-            } else if (fprev != 0.0 && ((fprev < 0.0) != (fnext < 0.0))) {
-                out[n++] = mono_root<DEG>(c, pts[k], pts[k + 1], fprev);
+            } else if (fprev != R(0) && ((fprev < R(0)) != (fnext < R(0)))) {
+                out[n++] = mono_root<R, DEG>(c, pts[k], pts[k + 1], fprev);
             }
             fprev = fnext;
         }
@@ -97,12 +106,12 @@ struct PolyRoots {
     }
 };
 
-template <>
-struct PolyRoots<1> {
-    __device__ static int run(const double *c, double lo, double hi, double *out)
+template <class R>
+struct PolyRoots<R, 1> {
+    __device__ static int run(const R *c, R lo, R hi, R *out)
     {
-        if (c[1] == 0.0) return 0;
-        double t = -c[0] / c[1];
+        if (c[1] == R(0)) return 0;
+        R t = -c[0] / c[1];
         if (t >= lo && t <= hi) {
             out[0] = t;
             return 1;
@@ -111,20 +120,20 @@ struct PolyRoots<1> {
     }
 };
 
-template <>
-struct PolyRoots<2> {
-    __device__ static int run(const double *c, double lo, double hi, double *out)
+template <class R>
+struct PolyRoots<R, 2> {
+    __device__ static int run(const R *c, R lo, R hi, R *out)
     {
-        double a = c[2], b = c[1], cc = c[0];
-        if (a == 0.0) return PolyRoots<1>::run(c, lo, hi, out);
-        double disc = b * b - 4.0 * a * cc;
-        if (disc < 0.0) return 0;
-        double sq = sqrt(disc);
-        double q = -0.5 * (b + (b >= 0.0 ? sq : -sq));
-        double r1 = q / a;
-        double r2 = (q != 0.0) ? cc / q : r1;
+        R a = c[2], b = c[1], cc = c[0];
+        if (a == R(0)) return PolyRoots<R, 1>::run(c, lo, hi, out);
+        R disc = b * b - R(4) * a * cc;
+        if (disc < R(0)) return 0;
+        R sq = sqrt(disc);
+        R q = R(-0.5) * (b + (b >= R(0) ? sq : -sq));
+        R r1 = q / a;
+        R r2 = (q != R(0)) ? cc / q : r1;
         if (r1 > r2) {
-            double tmp = r1;
+            R tmp = r1;
             r1 = r2;
             r2 = tmp;
         }
@@ -135,9 +144,23 @@ struct PolyRoots<2> {
     }
 };
 
-// --------------------------------------------------------------------------
-// edge root
-// --------------------------------------------------------------------------
+// two FP64 Newton steps on c from t (the step's divisor in FP32: the error of
+// the start point, about 1e-6 of the edge, shrinks below 1e-12 either way)
+template <int DEG>
+__device__ __forceinline__ double polish(const double *c, double t)
+{
+    double dc[DEG];
+#pragma unroll
+    for (int k = 0; k < DEG; ++k) dc[k] = (double)(k + 1) * c[k + 1];
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        double f = horner<double, DEG>(c, t);
+        float df = (float)horner<double, DEG - 1>(dc, t);
+        if (df != 0.0f) t -= f * (double)(1.0f / df);
+    }
+    return t;
+}
+
 // --------------------------------------------------------------------------
 // edge root, one warp per edge
 // --------------------------------------------------------------------------
@@ -198,15 +221,18 @@ __device__ __forceinline__ int warp_argmin(const WCand *c, int n)
 }
 
 // Candidate roots of one crossing edge (lower point s, local index p, +axis,
-// length h), then the first root.  Sphere and torus roots are solved in FP64
-// only for the pieces that an FP32 test (with a margin) lets through; the
-// freeness of a witness is decided in FP32 when the filter allows and in FP64
-// otherwise.  From an inside end point the answer is the first candidate; from
-// an outside end point it is the first candidate at which no free probe centre
-// lies strictly closer than r_p (within 1e-11 A).
+// length h), then the first root.  Every piece the FP32 prefilter lets
+// through has its roots isolated in FP32 on [-m, h + m] (quadratic for the
+// spheres, the torus quartic on its derivative chain) and polished by two FP64
+// Newton steps on the exact FP64 polynomial; the freeness of a witness is
+// decided in FP32 when the filter allows and in FP64 otherwise.  From an
+// inside end point the answer is the first candidate; from an outside end
+// point it is the first candidate at which no free probe centre lies strictly
+// closer than r_p (within 1e-11 A).  On success t_out is the root and n_out
+// the unit normal (FP64); returns 0, 1 (no root) or 2 (candidate overflow).
 template <class T, bool FILT>
 __device__ int warp_edge(const Model &M, const TileS<T> &S, const double *x0, EdgeSmem &E, int warp, int axis, int p,
-                         int lab_s, double h, double rp, T d0, double &t_out, double q_out[3])
+                         int lab_s, double h, double rp, T d0, double &t_out, double n_out[3])
 {
     const int lane = threadIdx.x & 31;
     const int li = p >> 6, lj = (p >> 3) & 7, lk = p & 7;
@@ -219,8 +245,9 @@ __device__ int warp_edge(const Model &M, const TileS<T> &S, const double *x0, Ed
     const int na = S.na, nv = S.nv, np = S.np;
     const T hT = (T)h, rpT = (T)rp;
     const T mg = FILT ? T(2e-3) : T(0);  // margin of the FP32 prefilters (A)
-    const T fd = d0 + T(2e-6);            // error of an FP64 witness rounded into the tile frame
+    const T fd = d0 + T(4e-6);            // error of an FP32 witness built from an FP64 root
     const bool inside = lab_s == LABEL_IN;
+    const T lo = FILT ? T(-1e-4) : T(0), hi = hT + (FILT ? T(1e-4) : T(0));
     for (int it = lane; it < na + nv + np; it += 32) {
         if (it < na) {  // convex: van der Waals sphere, witness = projection on the expanded sphere
             P4<T> c = S.atom[it];
@@ -230,27 +257,38 @@ __device__ int warp_edge(const Model &M, const TileS<T> &S, const double *x0, Ed
             if (dd > reach * reach) continue;
             T b = d[axis], disc = b * b - (dd - c.w * c.w);
             if (disc < -mg) continue;
-            T sq = sqrt(fmax(disc, T(0)) + mg);
-            if (-b + sq < -mg || -b - sq > hT + mg) continue;
+            T co32[3] = {dd - c.w * c.w, T(2) * b, T(1)};
+            T rt32[2];
+            int nr = PolyRoots<T, 2>::run(co32, lo, hi, rt32);
+            if (FILT && nr == 0 && disc < mg) {  // grazing: let FP64 decide
+                rt32[0] = -b;
+                nr = (-b >= lo && -b <= hi) ? 1 : 0;
+            }
+            if (nr == 0) continue;
             P4<double> ce = X.atom(it);
             double de[3] = {s64[0] - ce.x, s64[1] - ce.y, s64[2] - ce.z};
             double co[3] = {de[0] * de[0] + de[1] * de[1] + de[2] * de[2] - ce.w * ce.w, 2.0 * de[axis], 1.0};
-            double rt[2];
-            int nr = PolyRoots<2>::run(co, 0.0, h, rt);
             for (int k = 0; k < nr; ++k) {
+                double t = polish<2>(co, (double)rt32[k]);
+                if (!(t >= 0.0 && t <= h) || fabs(horner<double, 2>(co, t)) > 1e-9 * ce.w) continue;
                 double v[3] = {de[0], de[1], de[2]};
-                v[axis] += rt[k];
-                double nvv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-                if (!(nvv > 0.0)) continue;
+                v[axis] += t;
                 // the witness distance R - |y - c| must fall from an inside end point
-                // and rise from an outside one
-                double rate = -v[axis] / nvv;
-                if (inside ? rate > 1e-9 : rate < -1e-9) continue;
-                double R = ce.w + rp;
-                double q[3] = {ce.x + R * v[0] / nvv, ce.y + R * v[1] / nvv, ce.z + R * v[2] / nvv};
-                int f = FILT ? free_pt<true>(A, (T)q[0], (T)q[1], (T)q[2], S.agid[it], -1, rpT, fd) : -1;
-                if (f < 0) f = free_pt<false>(X, q[0], q[1], q[2], S.agid[it], -1, rp, 0.0);
-                if (f == 1) warp_push(E, warp, rt[k], q[0], q[1], q[2], 0, it);
+                // and rise from an outside one: its rate has the sign of -v_axis
+                if (inside ? -v[axis] > 1e-9 * ce.w : -v[axis] < -1e-9 * ce.w) continue;
+                T v32[3] = {(T)v[0], (T)v[1], (T)v[2]};
+                T R = c.w + rpT;
+                T sc = R / sqrt(v32[0] * v32[0] + v32[1] * v32[1] + v32[2] * v32[2]);
+                int f = FILT ? free_pt<true>(A, c.x + sc * v32[0], c.y + sc * v32[1], c.z + sc * v32[2], S.agid[it], -1,
+                                             rpT, fd)
+                             : -1;
+                if (f < 0) {
+                    double nvv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+                    double R64 = ce.w + rp;
+                    f = free_pt<false>(X, ce.x + R64 * v[0] / nvv, ce.y + R64 * v[1] / nvv, ce.z + R64 * v[2] / nvv,
+                                       S.agid[it], -1, rp, 0.0);
+                }
+                if (f == 1) warp_push(E, warp, t, 0.0, 0.0, 0.0, 0, it);
             }
         } else if (it < na + nv) {  // concave: probe sphere around a free triple point
             const int vi = it - na;
@@ -261,17 +299,23 @@ __device__ int warp_edge(const Model &M, const TileS<T> &S, const double *x0, Ed
             if (dd > reach * reach) continue;
             T b = d[axis], disc = b * b - (dd - rpT * rpT);
             if (disc < -mg) continue;
-            T sq = sqrt(fmax(disc, T(0)) + mg);
-            if (-b + sq < -mg || -b - sq > hT + mg) continue;
+            T co32[3] = {dd - rpT * rpT, T(2) * b, T(1)};
+            T rt32[2];
+            int nr = PolyRoots<T, 2>::run(co32, lo, hi, rt32);
+            if (FILT && nr == 0 && disc < mg) {
+                rt32[0] = -b;
+                nr = (-b >= lo && -b <= hi) ? 1 : 0;
+            }
+            if (nr == 0) continue;
             P4<double> ce = X.vq(vi);
             double de[3] = {s64[0] - ce.x, s64[1] - ce.y, s64[2] - ce.z};
             double co[3] = {de[0] * de[0] + de[1] * de[1] + de[2] * de[2] - rp * rp, 2.0 * de[axis], 1.0};
-            double rt[2];
-            int nr = PolyRoots<2>::run(co, 0.0, h, rt);
             for (int k = 0; k < nr; ++k) {
-                double rate = (de[axis] + rt[k]) / rp;  // d|y - v|/dt
-                if (inside ? rate > 1e-9 : rate < -1e-9) continue;
-                warp_push(E, warp, rt[k], ce.x, ce.y, ce.z, 2, vi);
+                double t = polish<2>(co, (double)rt32[k]);
+                if (!(t >= 0.0 && t <= h) || fabs(horner<double, 2>(co, t)) > 1e-9 * rp) continue;
+                double rate = de[axis] + t;  // sign of d|y - v|/dt
+                if (inside ? rate > 1e-9 * rp : rate < -1e-9 * rp) continue;
+                warp_push(E, warp, t, 0.0, 0.0, 0.0, 2, vi);
             }
         } else {  // saddle: torus around a free-arc circle
             const int pi = it - na - nv;
@@ -285,40 +329,66 @@ __device__ int warp_edge(const Model &M, const TileS<T> &S, const double *x0, Ed
             T e1 = sqrt(w2) - o.w;
             T gm = sqrt(e1 * e1 + zc * zc) - rpT;
             if (fabs(gm) > T(0.5) * hT + mg) continue;
+            // quartic (|y-o|^2 + rho^2 - r_p^2)^2 - 4 rho^2 |w|^2 in t
+            T q0[3] = {s[0] - o.x, s[1] - o.y, s[2] - o.z};
+            T uu32[3] = {u.x, u.y, u.z};
+            T P = q0[0] * q0[0] + q0[1] * q0[1] + q0[2] * q0[2];
+            T z0 = q0[0] * u.x + q0[1] * u.y + q0[2] * u.z;
+            T pe = q0[axis], eu = uu32[axis];
+            T K = P + o.w * o.w - rpT * rpT, r2 = o.w * o.w;
+            T co32[5] = {K * K - T(4) * r2 * (P - z0 * z0), T(4) * pe * K - T(8) * r2 * (pe - z0 * eu),
+                         T(4) * pe * pe + T(2) * K - T(4) * r2 * (T(1) - eu * eu), T(4) * pe, T(1)};
+            T rt32[4];
+            int nr = PolyRoots<T, 4>::run(co32, lo, hi, rt32);
+            if (nr == 0) continue;
             P4<double> oe = X.po(pi);
             P4<double> ue = X.pu(pi);
             const double rho = oe.w;
             double p0[3] = {s64[0] - oe.x, s64[1] - oe.y, s64[2] - oe.z};
             double uu[3] = {ue.x, ue.y, ue.z};
-            double P = p0[0] * p0[0] + p0[1] * p0[1] + p0[2] * p0[2];
-            double z0 = p0[0] * uu[0] + p0[1] * uu[1] + p0[2] * uu[2];
-            double pe = p0[axis], eu = uu[axis];
-            double K = P + rho * rho - rp * rp;
-            double r2 = rho * rho;
+            double Pd = p0[0] * p0[0] + p0[1] * p0[1] + p0[2] * p0[2];
+            double z0d = p0[0] * uu[0] + p0[1] * uu[1] + p0[2] * uu[2];
+            double ped = p0[axis], eud = uu[axis];
+            double Kd = Pd + rho * rho - rp * rp;
+            double r2d = rho * rho;
             double co[5];
             co[4] = 1.0;
-            co[3] = 4.0 * pe;
-            co[2] = 4.0 * pe * pe + 2.0 * K - 4.0 * r2 * (1.0 - eu * eu);
-            co[1] = 4.0 * pe * K - 8.0 * r2 * (pe - z0 * eu);
-            co[0] = K * K - 4.0 * r2 * (P - z0 * z0);
-            double rt[4];
-            int nr = PolyRoots<4>::run(co, 0.0, h, rt);
+            co[3] = 4.0 * ped;
+            co[2] = 4.0 * ped * ped + 2.0 * Kd - 4.0 * r2d * (1.0 - eud * eud);
+            co[1] = 4.0 * ped * Kd - 8.0 * r2d * (ped - z0d * eud);
+            co[0] = Kd * Kd - 4.0 * r2d * (Pd - z0d * z0d);
             for (int k = 0; k < nr; ++k) {
+                double t = polish<4>(co, (double)rt32[k]);
+                if (!(t >= 0.0 && t <= h)) continue;
                 double y[3] = {p0[0], p0[1], p0[2]};
-                y[axis] += rt[k];
+                y[axis] += t;
+                // near branch (|w| - rho)^2 + z^2 = r_p^2  <=>  |y-o|^2 + rho^2 - r_p^2 >= 0
+                double Ay = y[0] * y[0] + y[1] * y[1] + y[2] * y[2] + rho * rho - rp * rp;
+                if (Ay < 0.0) continue;
                 double zy = y[0] * uu[0] + y[1] * uu[1] + y[2] * uu[2];
                 double w[3] = {y[0] - zy * uu[0], y[1] - zy * uu[1], y[2] - zy * uu[2]};
-                double nw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-                double near2 = (nw - rho) * (nw - rho) + zy * zy;
-                if (fabs(near2 - rp * rp) > 1e-7 * rp * rp) continue;  // far branch of the quartic
-                if (!(nw > 0.0)) continue;
-                double rate = ((nw - rho) * w[axis] / nw + zy * uu[axis]) / rp;
-                if (inside ? rate > 1e-9 : rate < -1e-9) continue;
-                double q[3] = {oe.x + rho * w[0] / nw, oe.y + rho * w[1] / nw, oe.z + rho * w[2] / nw};
+                double w2d = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+                if (!(w2d > 0.0)) continue;
+                // rate of the distance to the circle: ((|w| - rho) w_a / |w| + z u_a) / r_p
+                float nwf = sqrtf((float)w2d);
+                float rate = ((nwf - (float)rho) * (float)w[axis] / nwf + (float)(zy * uu[axis])) / (float)rp;
+                if (fabsf(rate) < 1e-4f) {
+                    double nw = sqrt(w2d);
+                    double rd = ((nw - rho) * w[axis] / nw + zy * uu[axis]) / rp;
+                    rate = rd > 1e-9 ? 1.0f : (rd < -1e-9 ? -1.0f : 0.0f);
+                }
+                if (inside ? rate > 0.0f : rate < 0.0f) continue;
+                T kk = (T)(rho / (double)nwf);
                 int2 ij = S.pij[pi];
-                int f = FILT ? free_pt<true>(A, (T)q[0], (T)q[1], (T)q[2], ij.x, ij.y, rpT, fd) : -1;
-                if (f < 0) f = free_pt<false>(X, q[0], q[1], q[2], ij.x, ij.y, rp, 0.0);
-                if (f == 1) warp_push(E, warp, rt[k], q[0], q[1], q[2], 1, pi);
+                int f = FILT ? free_pt<true>(A, o.x + kk * (T)w[0], o.y + kk * (T)w[1], o.z + kk * (T)w[2], ij.x, ij.y,
+                                             rpT, fd)
+                             : -1;
+                if (f < 0) {
+                    double nw = sqrt(w2d);
+                    f = free_pt<false>(X, oe.x + rho * w[0] / nw, oe.y + rho * w[1] / nw, oe.z + rho * w[2] / nw, ij.x,
+                                       ij.y, rp, 0.0);
+                }
+                if (f == 1) warp_push(E, warp, t, 0.0, 0.0, 0.0, 1, pi);
             }
         }
     }
@@ -353,10 +423,33 @@ __device__ int warp_edge(const Model &M, const TileS<T> &S, const double *x0, Ed
         }
     }
     if (pick < 0) return 1;
-    t_out = c[pick].t;
-    q_out[0] = c[pick].qx;
-    q_out[1] = c[pick].qy;
-    q_out[2] = c[pick].qz;
+    // normal at the root: unit vector from the surface point to its witness
+    const double t = c[pick].t;
+    double y[3] = {s64[0], s64[1], s64[2]};
+    y[axis] += t;
+    double v[3];
+    const int kind = c[pick].kind, id = c[pick].id;
+    if (kind == 0) {  // convex: radial, outward
+        P4<double> ce = X.atom(id);
+        v[0] = y[0] - ce.x; v[1] = y[1] - ce.y; v[2] = y[2] - ce.z;
+    } else if (kind == 2) {  // concave: towards the probe centre
+        P4<double> ce = X.vq(id);
+        v[0] = ce.x - y[0]; v[1] = ce.y - y[1]; v[2] = ce.z - y[2];
+    } else {  // saddle: towards the nearest circle point
+        P4<double> oe = X.po(id);
+        P4<double> ue = X.pu(id);
+        double yo[3] = {y[0] - oe.x, y[1] - oe.y, y[2] - oe.z};
+        double zy = yo[0] * ue.x + yo[1] * ue.y + yo[2] * ue.z;
+        double w[3] = {yo[0] - zy * ue.x, yo[1] - zy * ue.y, yo[2] - zy * ue.z};
+        double nw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+        double k2 = oe.w / nw;
+        v[0] = k2 * w[0] - yo[0]; v[1] = k2 * w[1] - yo[1]; v[2] = k2 * w[2] - yo[2];
+    }
+    double vn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    t_out = t;
+    n_out[0] = v[0] / vn;
+    n_out[1] = v[1] / vn;
+    n_out[2] = v[2] / vn;
     return status;
 }
 
@@ -461,7 +554,7 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Grid G, co
     EdgeSmem &E = *reinterpret_cast<EdgeSmem *>(smem_raw + ((sizeof(TileS<T>) + 15) & ~(size_t)15));
     const long long nt = G.n_tiles;
     const long long st1 = G.dims[2], st0 = G.dims[1] * G.dims[2];
-    const double h = G.h, rp = M.rp;
+    const double h = G.h, rp = M.rp, inv_h = 1.0 / G.h;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const T d0 = FILT ? (T)G.d0 : T(0);
     for (long long tile = blockIdx.x; tile < nt; tile += gridDim.x) {
@@ -518,21 +611,10 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Grid G, co
             const int q = E.eptr[e];
             const int li = q >> 6, lj = (q >> 3) & 7, lk = q & 7;
             const int lab_s = E.lab[(li * 9 + lj) * 9 + lk];
-            double tr = 0.5 * h, qq[3] = {0.0, 0.0, 0.0};
-            int status = warp_edge<T, FILT>(M, S, x0, E, warp, a, q, lab_s, h, rp, d0, tr, qq);
+            double tr = 0.5 * h, nrm[3] = {0.0, 0.0, 0.0};
+            int status = warp_edge<T, FILT>(M, S, x0, E, warp, a, q, lab_s, h, rp, d0, tr, nrm);
             if (lane == 0) {
-                double nrm[3] = {0.0, 0.0, 0.0};
-                if (status != 1) {
-                    double y[3] = {(double)li * h, (double)lj * h, (double)lk * h};
-                    y[a] += tr;
-                    double v[3] = {qq[0] - y[0], qq[1] - y[1], qq[2] - y[2]};
-                    double nv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-                    if (nv > 0.0) {
-                        nrm[0] = v[0] / nv;
-                        nrm[1] = v[1] / nv;
-                        nrm[2] = v[2] / nv;
-                    }
-                }
+                if (status == 1) nrm[0] = nrm[1] = nrm[2] = 0.0;
                 if (status != 0) {
                     atomicOr(err, status == 1 ? ERR_ROOT : ERR_CAP_CAND);
                     if (status == 1) {
@@ -559,11 +641,11 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Grid G, co
                 const long long o = E.ebase[a] + (e - E.estart[a]);
                 out.idx[a][o] = (long long)(TILE * t[0] + li) * st0 + (long long)(TILE * t[1] + lj) * st1 +
                                 (TILE * t[2] + lk);
-                out.tau[a][o] = tr / h;
+                out.tau[a][o] = tr * inv_h;
                 out.nrm[a][3 * o + 0] = nrm[0];
                 out.nrm[a][3 * o + 1] = nrm[1];
                 out.nrm[a][3 * o + 2] = nrm[2];
-                out.tau32[a][o] = (float)(tr / h);
+                out.tau32[a][o] = (float)(tr * inv_h);
                 out.nrm32[a][3 * o + 0] = (float)nrm[0];
                 out.nrm32[a][3 * o + 1] = (float)nrm[1];
                 out.nrm32[a][3 * o + 2] = (float)nrm[2];

@@ -43,6 +43,8 @@ struct alignas(16) P4 {
     T x, y, z, w;
 };
 
+constexpr int STAGE_CELLS = 128;  // cells staged with item-parallel scan (else one thread per cell)
+
 template <class T>
 struct TileS {
     P4<T> atom[A_MAX];      // centre (tile frame), vdW radius
@@ -54,6 +56,8 @@ struct TileS {
     int pidx[P_MAX];        // pair index in the model
     int vidx[V_MAX];        // triple point index in the model
     uint8_t aface[A_MAX];   // expanded sphere keeps a free face
+    int cid[STAGE_CELLS];           // cells of the staging range
+    int cs[3][STAGE_CELLS + 1];     // prefix of their atoms / pairs / vertices
     int na, np, nv, flags;
 };
 
@@ -133,7 +137,55 @@ __device__ __forceinline__ void tile_coords(const Grid &G, long long tile, int t
     t[0] = (int)(tile / ((long long)G.tiles[1] * G.tiles[2]));
 }
 
+// Test one cell item against the region and append it (atoms, pairs, vertices).
+template <class T>
+__device__ __forceinline__ void stage_item(const Model &M, TileS<T> &S, int list, int k, const double *x0,
+                                           const double *x1)
+{
+    const double tol = 1e-6;
+    const double rp = M.rp;
+    if (list == 0) {
+        double4 a = M.atom[k];
+        double reach = a.w + 2.0 * rp + tol;
+        if (box_dist2(a.x, a.y, a.z, x0, x1) < reach * reach) {
+            int s = atomicAdd(&S.na, 1);
+            if (s < A_MAX) {
+                S.atom[s] = P4<T>{(T)(a.x - x0[0]), (T)(a.y - x0[1]), (T)(a.z - x0[2]), (T)a.w};
+                S.agid[s] = k;
+                S.aface[s] = M.atom_face[k];
+            }
+        }
+    } else if (list == 1) {
+        int p = M.pcell_list[k];
+        double4 o = M.pair_o[p];
+        double reach = o.w + rp + tol;
+        if (box_dist2(o.x, o.y, o.z, x0, x1) < reach * reach) {
+            int s = atomicAdd(&S.np, 1);
+            if (s < P_MAX) {
+                double4 u = M.pair_u[p];
+                S.po[s] = P4<T>{(T)(o.x - x0[0]), (T)(o.y - x0[1]), (T)(o.z - x0[2]), (T)o.w};
+                S.pu[s] = P4<T>{(T)u.x, (T)u.y, (T)u.z, (T)0};
+                S.pij[s] = M.pair_ij[p];
+                S.pidx[s] = p;
+            }
+        }
+    } else {
+        int v = M.vcell_list[k];
+        double4 q = M.vert[v];
+        double reach = rp + tol;
+        if (box_dist2(q.x, q.y, q.z, x0, x1) < reach * reach) {
+            int s = atomicAdd(&S.nv, 1);
+            if (s < V_MAX) {
+                S.vq[s] = P4<T>{(T)(q.x - x0[0]), (T)(q.y - x0[1]), (T)(q.z - x0[2]), (T)0};
+                S.vidx[s] = v;
+            }
+        }
+    }
+}
+
 // Stage the tile's atoms, free-arc pairs and free vertices (whole block).
+// The items of every cell in range are numbered by a prefix over the cells
+// and tested one per thread, so all threads share the work.
 template <class T>
 __device__ void stage_tile(const Model &M, const Grid &G, long long tile, TileS<T> &S, double x0[3])
 {
@@ -150,7 +202,6 @@ __device__ void stage_tile(const Model &M, const Grid &G, long long tile, TileS<
         S.nv = 0;
         S.flags = 0;
     }
-    __syncthreads();
     int c0[3], c1[3], nc[3];
     for (int a = 0; a < 3; ++a) {
         c0[a] = cell_coord_d(x0[a] - G.halo, M.clo[a], M.cell, M.cn[a]);
@@ -158,49 +209,57 @@ __device__ void stage_tile(const Model &M, const Grid &G, long long tile, TileS<
         nc[a] = c1[a] - c0[a] + 1;
     }
     const int ncell = nc[0] * nc[1] * nc[2];
-    const double tol = 1e-6;
-    const double rp = M.rp;
-    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
-        int cz = c % nc[2], cy = (c / nc[2]) % nc[1], cx = c / (nc[1] * nc[2]);
-        int id = ((c0[0] + cx) * M.cn[1] + (c0[1] + cy)) * M.cn[2] + (c0[2] + cz);
-        for (int k = M.cell_start[id]; k < M.cell_start[id + 1]; ++k) {
-            double4 a = M.atom[k];
-            double reach = a.w + 2.0 * rp + tol;
-            if (box_dist2(a.x, a.y, a.z, x0, x1) < reach * reach) {
-                int s = atomicAdd(&S.na, 1);
-                if (s < A_MAX) {
-                    S.atom[s] = P4<T>{(T)(a.x - x0[0]), (T)(a.y - x0[1]), (T)(a.z - x0[2]), (T)a.w};
-                    S.agid[s] = k;
-                    S.aface[s] = M.atom_face[k];
+    if (ncell <= STAGE_CELLS) {
+        for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+            int cz = c % nc[2], cy = (c / nc[2]) % nc[1], cx = c / (nc[1] * nc[2]);
+            int id = ((c0[0] + cx) * M.cn[1] + (c0[1] + cy)) * M.cn[2] + (c0[2] + cz);
+            S.cid[c] = id;
+            S.cs[0][c + 1] = M.cell_start[id + 1] - M.cell_start[id];
+            S.cs[1][c + 1] = M.pcell_start[id + 1] - M.pcell_start[id];
+            S.cs[2][c + 1] = M.vcell_start[id + 1] - M.vcell_start[id];
+        }
+        __syncthreads();
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (warp < 3) {  // inclusive scan of each list's counts
+            int *cs = S.cs[warp];
+            int carry = 0;
+            if (lane == 0) cs[0] = 0;
+            for (int base = 1; base <= ncell; base += 32) {
+                int k = base + lane;
+                int v = k <= ncell ? cs[k] : 0;
+                for (int o = 1; o < 32; o <<= 1) {
+                    int u = __shfl_up_sync(0xffffffffu, v, o);
+                    if (lane >= o) v += u;
                 }
+                if (k <= ncell) cs[k] = v + carry;
+                carry += __shfl_sync(0xffffffffu, v, 31);
             }
         }
-        for (int k = M.pcell_start[id]; k < M.pcell_start[id + 1]; ++k) {
-            int p = M.pcell_list[k];
-            double4 o = M.pair_o[p];
-            double reach = o.w + rp + tol;
-            if (box_dist2(o.x, o.y, o.z, x0, x1) < reach * reach) {
-                int s = atomicAdd(&S.np, 1);
-                if (s < P_MAX) {
-                    double4 u = M.pair_u[p];
-                    S.po[s] = P4<T>{(T)(o.x - x0[0]), (T)(o.y - x0[1]), (T)(o.z - x0[2]), (T)o.w};
-                    S.pu[s] = P4<T>{(T)u.x, (T)u.y, (T)u.z, (T)0};
-                    S.pij[s] = M.pair_ij[p];
-                    S.pidx[s] = p;
-                }
+        __syncthreads();
+        const int n0 = S.cs[0][ncell], n1 = S.cs[1][ncell], n2 = S.cs[2][ncell];
+        for (int it = threadIdx.x; it < n0 + n1 + n2; it += blockDim.x) {
+            int list = it < n0 ? 0 : (it < n0 + n1 ? 1 : 2);
+            int k = it - (list == 0 ? 0 : (list == 1 ? n0 : n0 + n1));
+            const int *cs = S.cs[list];
+            int lo = 0, hi = ncell;
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (cs[mid] <= k) lo = mid;
+                else hi = mid;
             }
+            int id = S.cid[lo];
+            int off = k - cs[lo];
+            int item = list == 0 ? M.cell_start[id] + off : (list == 1 ? M.pcell_start[id] + off : M.vcell_start[id] + off);
+            stage_item<T>(M, S, list, item, x0, x1);
         }
-        for (int k = M.vcell_start[id]; k < M.vcell_start[id + 1]; ++k) {
-            int v = M.vcell_list[k];
-            double4 q = M.vert[v];
-            double reach = rp + tol;
-            if (box_dist2(q.x, q.y, q.z, x0, x1) < reach * reach) {
-                int s = atomicAdd(&S.nv, 1);
-                if (s < V_MAX) {
-                    S.vq[s] = P4<T>{(T)(q.x - x0[0]), (T)(q.y - x0[1]), (T)(q.z - x0[2]), (T)0};
-                    S.vidx[s] = v;
-                }
-            }
+    } else {
+        __syncthreads();
+        for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+            int cz = c % nc[2], cy = (c / nc[2]) % nc[1], cx = c / (nc[1] * nc[2]);
+            int id = ((c0[0] + cx) * M.cn[1] + (c0[1] + cy)) * M.cn[2] + (c0[2] + cz);
+            for (int k = M.cell_start[id]; k < M.cell_start[id + 1]; ++k) stage_item<T>(M, S, 0, k, x0, x1);
+            for (int k = M.pcell_start[id]; k < M.pcell_start[id + 1]; ++k) stage_item<T>(M, S, 1, k, x0, x1);
+            for (int k = M.vcell_start[id]; k < M.vcell_start[id + 1]; ++k) stage_item<T>(M, S, 2, k, x0, x1);
         }
     }
     __syncthreads();
