@@ -85,9 +85,10 @@ struct eses_ctx {
     DBuf pbin_count, pbin_start, pbin_cursor, pbin_cell, pbin_list;
     DBuf vbin_count, vbin_start, vbin_cursor, vbin_cell, vbin_list;
     DBuf labels, tile_band, tile_edges, edge_start, tile_inside, tile_area, tile_vol;
-    DBuf out_idx[3], out_tau[3], out_nrm[3], out_tau32[3], out_nrm32[3];
+    DBuf out_idx[3], out_tau[3], out_nrm[3], out_tau32[3], out_nrm32[3], out_code[3];
     DBuf scan_tmp, misc;  // misc: err, n_fail, area/vol, counts
     DBuf fail_log;
+    DBuf atom_hi, atom_lo, pair_hi, pair_lo, pair_u32, vert_hi, vert_lo;
     // results
     bool ran = false;
     long long n_edges[3] = {0, 0, 0};
@@ -197,7 +198,13 @@ int setup(eses_ctx *c, const double *xyz, const double *r)
     G.rp = c->rp;
     G.halo = c->rmax + 2.0 * c->rp;
     double L = 8.0 * c->h * sqrt(3.0) + G.halo + 1.0;
-    G.d0 = (float)(4.2e-7 * L);
+    // staged FP32 coordinates carry two roundings of at most 2^-24 L each, a grid
+    // point one, a difference of two of them one more: 5 * 2^-24 L per
+    // coordinate, 5.2e-7 L for the vector; d0 rounds that up
+    G.d0 = (float)(6e-7 * L);
+    for (int k = 0; k <= TILE; ++k) G.hl[k] = (float)((double)k * c->h);
+    G.ht_hi = (float)(TILE * c->h);
+    G.ht_lo = (float)(TILE * c->h - (double)G.ht_hi);
     return ESES_OK;
 }
 
@@ -293,6 +300,10 @@ int run_impl(eses_ctx *c)
     M.atom = atom;
     M.atom_orig = orig;
     M.cell_start = cell_start;
+    float4 *ahi = ensure<float4>(c->atom_hi, n), *alo = ensure<float4>(c->atom_lo, n);
+    nl += launch_model_f32(M, 0, G.lo, ahi, alo, nullptr, st);
+    M.atom_hi = ahi;
+    M.atom_lo = alo;
 
     mark(c, ST_PAIRS);
     // 2. neighbours
@@ -322,6 +333,12 @@ int run_impl(eses_ctx *c)
     M.pair_o = pair_o;
     M.pair_u = pair_u;
     M.pair_ij = pair_ij;
+    float4 *phi = ensure<float4>(c->pair_hi, std::max(np, 1)), *plo = ensure<float4>(c->pair_lo, std::max(np, 1));
+    float4 *pu32 = ensure<float4>(c->pair_u32, std::max(np, 1));
+    nl += launch_model_f32(M, 1, G.lo, phi, plo, pu32, st);
+    M.pair_hi = phi;
+    M.pair_lo = plo;
+    M.pair_u32 = pu32;
 
     mark(c, ST_ARCS);
     // 4. free arcs and free triple points
@@ -337,6 +354,8 @@ int run_impl(eses_ctx *c)
     nl += launch_arcs_emit(M, vert_start, vert, st);
     M.vert = vert;
 
+    if (n >= (1 << 27) || np >= (1 << 27) || nv >= (1 << 27))
+        return fail(c, ESES_EINVAL, "more than 2^27 atoms, circle pairs or triple points");
     // 5. free faces
     uint8_t *face = ensure<uint8_t>(c->face, n);
     nl += launch_faces(M, circle_count, contained, face, st);
@@ -367,6 +386,10 @@ int run_impl(eses_ctx *c)
     M.pcell_list = plist;
     M.vcell_start = vstart;
     M.vcell_list = vlist;
+    float4 *vhi = ensure<float4>(c->vert_hi, std::max(nv, 1)), *vlo = ensure<float4>(c->vert_lo, std::max(nv, 1));
+    nl += launch_model_f32(M, 2, G.lo, vhi, vlo, nullptr, st);
+    M.vert_hi = vhi;
+    M.vert_lo = vlo;
 
     // 7. classification (+ FP64 band re-evaluation)
     const long long npts = G.dims[0] * G.dims[1] * G.dims[2];
@@ -399,15 +422,15 @@ int run_impl(eses_ctx *c)
         eo.nrm[a] = ensure<double>(c->out_nrm[a], 3 * std::max(ne, 1LL));
         eo.tau32[a] = ensure<float>(c->out_tau32[a], std::max(ne, 1LL));
         eo.nrm32[a] = ensure<float>(c->out_nrm32[a], 3 * std::max(ne, 1LL));
+        eo.code[a] = ensure<int2>(c->out_code[a], std::max(ne, 1LL));
     }
-    double *tile_area = ensure<double>(c->tile_area, nt);
-    double *tile_vol = ensure<double>(c->tile_vol, nt);
+    const long long nparts = polish_blocks(c->n_edges[0] + c->n_edges[1] + c->n_edges[2]);
+    double *part = ensure<double>(c->tile_area, 2 * std::max(nparts, 1LL));
     mark(c, ST_EDGE_SOLVE);
     long long *fail_log = ensure<long long>(c->fail_log, FAIL_LOG * FAIL_REC);
-    nl += launch_edge_solve(M, G, c->precision, labels, edge_start, eo, tile_area, tile_vol, d_fail, d_err, fail_log,
-                            st);
+    nl += launch_edge_solve(M, G, c->precision, labels, edge_start, eo, c->n_edges, part, d_fail, d_err, fail_log, st);
     mark(c, ST_REDUCE);
-    nl += launch_reduce(G, tile_area, tile_vol, tile_inside, labels, d_av, d_counts, st);
+    nl += launch_reduce(G, part, nparts, tile_inside, d_av, d_counts, st);
     mark(c, NSTAGE);
     ck(cudaGetLastError(), "kernel launch");
 
@@ -701,7 +724,8 @@ void eses_destroy(eses_ctx *c)
                     &c->vert_count, &c->vert_start, &c->vert, &c->pbin_count, &c->pbin_start, &c->pbin_cursor,
                     &c->pbin_cell, &c->pbin_list, &c->vbin_count, &c->vbin_start, &c->vbin_cursor, &c->vbin_cell,
                     &c->vbin_list, &c->labels, &c->tile_band, &c->tile_edges, &c->edge_start, &c->tile_inside,
-                    &c->tile_area, &c->tile_vol, &c->scan_tmp, &c->misc, &c->fail_log};
+                    &c->tile_area, &c->tile_vol, &c->scan_tmp, &c->misc, &c->fail_log,
+                    &c->atom_hi, &c->atom_lo, &c->pair_hi, &c->pair_lo, &c->pair_u32, &c->vert_hi, &c->vert_lo};
     if (c->own_stream) cudaStreamSynchronize(c->own_stream);
     for (DBuf *b : bufs) free_buf(*b);
     for (int a = 0; a < 3; ++a) {
@@ -710,6 +734,7 @@ void eses_destroy(eses_ctx *c)
         free_buf(c->out_nrm[a]);
         free_buf(c->out_tau32[a]);
         free_buf(c->out_nrm32[a]);
+        free_buf(c->out_code[a]);
     }
     for (int k = 0; k <= NSTAGE; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);

@@ -50,6 +50,14 @@ __device__ __forceinline__ void brick_point(int brick, int lane, int &li, int &l
     lk = bk * 4 + (lane & 3);
 }
 
+// tile-frame coordinate of local point k: FP32 table, or FP64 k * h
+template <class T>
+__device__ __forceinline__ T pt_coord(const Grid &G, int k)
+{
+    if constexpr (sizeof(T) == sizeof(float)) return G.hl[k];
+    else return (double)k * G.h;
+}
+
 __device__ __forceinline__ unsigned hash_of(int key) { return ((unsigned)key * 2654435761u) & (HASH - 1); }
 
 // per-atom incident pair lists (whole block)
@@ -222,7 +230,7 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Grid G, int8_
             bool valid = gi < G.dims[0] && gj < G.dims[1] && gk < G.dims[2];
             int lab = LABEL_OUT;
             if (cnt > 0) {
-                T x = (T)((double)li * G.h), y = (T)((double)lj * G.h), z = (T)((double)lk * G.h);
+                T x = pt_coord<T>(G, li), y = pt_coord<T>(G, lj), z = pt_coord<T>(G, lk);
                 bool vdw = false, sas = false, sas_u = false;
                 for (int m2 = 0; m2 < cnt; ++m2) {
                     P4<T> c = S.atom[C.blist[brick][m2]];
@@ -259,7 +267,7 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Grid G, int8_
             int li = (code >> 6) & 7, lj = (code >> 3) & 7, lk = code & 7;
             long long gi = (long long)TILE * t[0] + li, gj = (long long)TILE * t[1] + lj,
                       gk = (long long)TILE * t[2] + lk;
-            T x = (T)((double)li * G.h), y = (T)((double)lj * G.h), z = (T)((double)lk * G.h);
+            T x = pt_coord<T>(G, li), y = pt_coord<T>(G, lj), z = pt_coord<T>(G, lk);
             int lab = shell_label<FILT>(S, C, brick, x, y, z, rp, d0);
             labels[(gi * G.dims[1] + gj) * G.dims[2] + gk] = (int8_t)lab;
             if (FILT && lab == LABEL_BAND) atomicAdd(&C.band, 1);

@@ -5,7 +5,7 @@
 //   points whose end labels differ, and the edges with both ends inside.
 // (exclusive scan of the counts -> every tile's output offset per axis; the
 //   paper serialises this output step in a critical section, Algorithm 1)
-// k_edge_solve: per tile, stages the patches and solves every crossing edge.
+// k_edge_solve: per tile, stages the patches; one warp per crossing edge.
 //   The surface along an edge is made of pieces of van der Waals spheres
 //   (convex), tori around pair circles (saddle) and probe spheres around free
 //   triple points (concave).  Every root of every such piece in [0, h] whose
@@ -14,12 +14,19 @@
 //   direction that leaves the end point's side (falling from an inside end,
 //   rising from an outside end), is a candidate.  From an inside end point
 //   the first candidate is the first root; from an outside end point the
-//   first candidate that is not strictly outside M is.  Sphere roots come from the
-//   quadratic, torus roots from the quartic
+//   first candidate that is not strictly outside M is.  Sphere roots come from
+//   the quadratic, torus roots from the quartic
 //     (|y-o|^2 + rho^2 - r_p^2)^2 = 4 rho^2 (|y-o|^2 - ((y-o).u)^2)
-//   solved on [0, h] by root isolation on the derivative chain (quadratic ->
-//   cubic -> quartic, monotone pieces) and safeguarded Newton-bisection,
-//   keeping the near branch (|w| - rho)^2 + z^2 = r_p^2.  All in FP64.
+//   isolated on the derivative chain (quadratic -> cubic -> quartic, monotone
+//   pieces) with safeguarded Newton-bisection, keeping the near branch
+//   (|w| - rho)^2 + z^2 = r_p^2.  The warp works in FP32 with an error bound
+//   on every root; a decision that the bound cannot make (grazing piece, root
+//   near an end point, near tie between candidates, witness near another
+//   sphere) is taken on the FP64 root.  The warp records the chosen piece and
+//   its FP32 root.
+// k_edge_polish: one thread per crossing edge (full warps of FP64 work): the
+//   FP64 root of the chosen piece next to the recorded one, the normal, the
+//   outputs and the area/volume terms.
 // k_reduce: area = h^2 sum |n_a|, volume = h^2/3 sum of inside lengths.
 #include <math.h>
 
@@ -29,6 +36,9 @@
 namespace eses {
 
 constexpr int EDGE_THREADS = 256;
+constexpr int EDGE_WARPS = EDGE_THREADS / 32;
+constexpr int WCAND = 64;        // candidate roots per warp
+constexpr int POLISH_THREADS = 256;
 
 // --------------------------------------------------------------------------
 // polynomial roots on an interval
@@ -144,75 +154,144 @@ struct PolyRoots<R, 2> {
     }
 };
 
-// two FP64 Newton steps on c from t (the step's divisor in FP32: the error of
-// the start point, about 1e-6 of the edge, shrinks below 1e-12 either way)
-template <int DEG>
-__device__ __forceinline__ double polish(const double *c, double t)
+// --------------------------------------------------------------------------
+// exact (FP64) roots and normals of one piece, any common frame
+// --------------------------------------------------------------------------
+// root of |s + t e_axis - c| = rad nearest t0 (t0 returned when none is real)
+__device__ __forceinline__ double exact_root_sphere(const double *c, double rad, const double *s, int axis, double t0)
 {
-    double dc[DEG];
+    double d[3] = {s[0] - c[0], s[1] - c[1], s[2] - c[2]};
+    double b = d[axis];
+    double cc = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] - rad * rad;
+    double disc = b * b - cc;
+    if (disc < 0.0) return t0;
+    double sq = sqrt(disc);
+    double q = -(b + (b >= 0.0 ? sq : -sq));
+    double r1 = q, r2 = (q != 0.0) ? cc / q : q;
+    return fabs(r1 - t0) <= fabs(r2 - t0) ? r1 : r2;
+}
+
+__device__ __forceinline__ void torus_coeffs(const double *o, const double *u, double rho, double rp, const double *s,
+                                             int axis, double *co)
+{
+    double p0[3] = {s[0] - o[0], s[1] - o[1], s[2] - o[2]};
+    double P = p0[0] * p0[0] + p0[1] * p0[1] + p0[2] * p0[2];
+    double z0 = p0[0] * u[0] + p0[1] * u[1] + p0[2] * u[2];
+    double pe = p0[axis], eu = u[axis];
+    double K = P + rho * rho - rp * rp;
+    double r2 = rho * rho;
+    co[4] = 1.0;
+    co[3] = 4.0 * pe;
+    co[2] = 4.0 * pe * pe + 2.0 * K - 4.0 * r2 * (1.0 - eu * eu);
+    co[1] = 4.0 * pe * K - 8.0 * r2 * (pe - z0 * eu);
+    co[0] = K * K - 4.0 * r2 * (P - z0 * z0);
+}
+
+// four FP64 Newton steps on the torus quartic from t0 (the FP32 root is within
+// 1e-3 A and the root simple, else the warp solve already took it in FP64)
+__device__ __forceinline__ double exact_root_torus(const double *o, const double *u, double rho, double rp,
+                                                   const double *s, int axis, double t0)
+{
+    double co[5];
+    torus_coeffs(o, u, rho, rp, s, axis, co);
+    double dc[4] = {co[1], 2.0 * co[2], 3.0 * co[3], 4.0};
+    double t = t0;
 #pragma unroll
-    for (int k = 0; k < DEG; ++k) dc[k] = (double)(k + 1) * c[k + 1];
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-        double f = horner<double, DEG>(c, t);
-        float df = (float)horner<double, DEG - 1>(dc, t);
-        if (df != 0.0f) t -= f * (double)(1.0f / df);
+    for (int it = 0; it < 4; ++it) {
+        double f = horner<double, 4>(co, t);
+        double df = horner<double, 3>(dc, t);
+        if (df != 0.0) t -= f / df;
     }
     return t;
 }
 
-// --------------------------------------------------------------------------
-// edge root, one warp per edge
-// --------------------------------------------------------------------------
-constexpr int EDGE_WARPS = EDGE_THREADS / 32;
-constexpr int WCAND = 64;  // candidate roots per warp
+// unit normal at y (towards the witness, i.e. into the solvent)
+__device__ __forceinline__ void exact_normal(int kind, const double *c, const double *u, double rho, const double *y,
+                                             double *n)
+{
+    double v[3];
+    if (kind == 0) {  // convex: radial, outward
+        v[0] = y[0] - c[0]; v[1] = y[1] - c[1]; v[2] = y[2] - c[2];
+    } else if (kind == 2) {  // concave: towards the probe centre
+        v[0] = c[0] - y[0]; v[1] = c[1] - y[1]; v[2] = c[2] - y[2];
+    } else {  // saddle: towards the nearest point of the circle
+        double yo[3] = {y[0] - c[0], y[1] - c[1], y[2] - c[2]};
+        double z = yo[0] * u[0] + yo[1] * u[1] + yo[2] * u[2];
+        double w[3] = {yo[0] - z * u[0], yo[1] - z * u[1], yo[2] - z * u[2]};
+        double nw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+        double k = nw > 0.0 ? rho / nw : 0.0;
+        v[0] = k * w[0] - yo[0]; v[1] = k * w[1] - yo[1]; v[2] = k * w[2] - yo[2];
+    }
+    double vn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    double iv = vn > 0.0 ? 1.0 / vn : 0.0;
+    n[0] = v[0] * iv;
+    n[1] = v[1] * iv;
+    n[2] = v[2] * iv;
+}
 
+// exact root of a staged piece (tile frame, FP64 data from HBM) near t0
+template <class TS>
+__device__ __forceinline__ double staged_exact_root(const ExactAcc<TS> &X, int kind, int slot, const double *s,
+                                                    int axis, double rp, double t0)
+{
+    if (kind == 0) {
+        P4<double> c = X.atom(slot);
+        double cc[3] = {c.x, c.y, c.z};
+        return exact_root_sphere(cc, c.w, s, axis, t0);
+    }
+    if (kind == 2) {
+        P4<double> c = X.vq(slot);
+        double cc[3] = {c.x, c.y, c.z};
+        return exact_root_sphere(cc, rp, s, axis, t0);
+    }
+    P4<double> o = X.po(slot);
+    P4<double> u = X.pu(slot);
+    double oo[3] = {o.x, o.y, o.z}, uu[3] = {u.x, u.y, u.z};
+    return exact_root_torus(oo, uu, o.w, rp, s, axis, t0);
+}
+
+// --------------------------------------------------------------------------
+// one warp per edge
+// --------------------------------------------------------------------------
 struct WCand {
-    double t, qx, qy, qz;
+    double t64;    // exact root once computed (NaN before)
+    float t, err;  // FP32 root and its error bound (A)
     int kind, id;  // kind 0: van der Waals sphere (atom slot), 1: torus (pair slot), 2: probe sphere (vertex slot)
 };
 
 struct EdgeSmem {
+    double hd[TILE + 1];  // k * h, k = 0..8
     int8_t lab[9 * 9 * 9];
     short eptr[3 * TILE_PTS];  // crossing edges of the tile (local point), grouped by axis
     int estart[4];
     long long ebase[3];
     int sh[EDGE_WARPS];
-    double shd[EDGE_WARPS];
     WCand cand[EDGE_WARPS][WCAND];
     int ncand[EDGE_WARPS];
 };
 
-__device__ __forceinline__ void warp_push(EdgeSmem &E, int warp, double t, double qx, double qy, double qz, int kind,
-                                          int id)
+__device__ __forceinline__ void warp_push(EdgeSmem &E, int warp, float t, float err, double t64, int kind, int id)
 {
     int slot = atomicAdd(&E.ncand[warp], 1);
     if (slot < WCAND) {
         WCand &c = E.cand[warp][slot];
         c.t = t;
-        c.qx = qx;
-        c.qy = qy;
-        c.qz = qz;
+        c.err = err;
+        c.t64 = t64;
         c.kind = kind;
         c.id = id;
     }
 }
 
-// index of the smallest t (ties: smaller index), -1 if every t is +inf
-__device__ __forceinline__ int warp_argmin(const WCand *c, int n)
+// index of the smallest key (ties: smaller index), -1 if every key is +inf
+__device__ __forceinline__ int warp_argmin_key(float key, int k)
 {
-    const int lane = threadIdx.x & 31;
-    double bt = INFINITY;
-    int bk = -1;
-    for (int k = lane; k < n; k += 32)
-        if (c[k].t < bt) {
-            bt = c[k].t;
-            bk = k;
-        }
+    float bt = key;
+    int bk = (key < INFINITY) ? k : -1;
     for (int o = 16; o > 0; o >>= 1) {
-        double ot = __shfl_xor_sync(0xffffffffu, bt, o);
+        float ot = __shfl_xor_sync(0xffffffffu, bt, o);
         int ok = __shfl_xor_sync(0xffffffffu, bk, o);
-        if (ot < bt || (ot == bt && ok >= 0 && (bk < 0 || ok < bk))) {
+        if (ok >= 0 && (bk < 0 || ot < bt || (ot == bt && ok < bk))) {
             bt = ot;
             bk = ok;
         }
@@ -220,23 +299,29 @@ __device__ __forceinline__ int warp_argmin(const WCand *c, int n)
     return bk;
 }
 
-// Candidate roots of one crossing edge (lower point s, local index p, +axis,
-// length h), then the first root.  Every piece the FP32 prefilter lets
-// through has its roots isolated in FP32 on [-m, h + m] (quadratic for the
-// spheres, the torus quartic on its derivative chain) and polished by two FP64
-// Newton steps on the exact FP64 polynomial; the freeness of a witness is
-// decided in FP32 when the filter allows and in FP64 otherwise.  From an
-// inside end point the answer is the first candidate; from an outside end
-// point it is the first candidate at which no free probe centre lies strictly
-// closer than r_p (within 1e-11 A).  On success t_out is the root and n_out
-// the unit normal (FP64); returns 0, 1 (no root) or 2 (candidate overflow).
+__device__ __forceinline__ int warp_argmin(const WCand *c, int n)
+{
+    const int lane = threadIdx.x & 31;
+    float bt = INFINITY;
+    int bk = -1;
+    for (int k = lane; k < n; k += 32)
+        if (c[k].t < bt) {
+            bt = c[k].t;
+            bk = k;
+        }
+    return warp_argmin_key(bt, bk);
+}
+
+// Candidates of one crossing edge, then the first root.  Returns 0 with the
+// chosen piece (kind, staged slot) and its FP32 root, 1 when no root is
+// found, 2 when the candidate buffer overflowed (the first WCAND are used).
 template <class T, bool FILT>
 __device__ int warp_edge(const Model &M, const TileS<T> &S, const double *x0, EdgeSmem &E, int warp, int axis, int p,
-                         int lab_s, double h, double rp, T d0, double &t_out, double n_out[3])
+                         int lab_s, double h, double rp, T d0, float &t_out, int &kind_out, int &slot_out)
 {
     const int lane = threadIdx.x & 31;
     const int li = p >> 6, lj = (p >> 3) & 7, lk = p & 7;
-    const double s64[3] = {(double)li * h, (double)lj * h, (double)lk * h};
+    const double s64[3] = {E.hd[li], E.hd[lj], E.hd[lk]};
     const T s[3] = {(T)s64[0], (T)s64[1], (T)s64[2]};
     SmemAcc<T> A(S);
     ExactAcc<T> X(S, M, x0);
@@ -244,78 +329,85 @@ __device__ int warp_edge(const Model &M, const TileS<T> &S, const double *x0, Ed
     __syncwarp();
     const int na = S.na, nv = S.nv, np = S.np;
     const T hT = (T)h, rpT = (T)rp;
-    const T mg = FILT ? T(2e-3) : T(0);  // margin of the FP32 prefilters (A)
-    const T fd = d0 + T(4e-6);            // error of an FP32 witness built from an FP64 root
-    const bool inside = lab_s == LABEL_IN;
+    const T mg = FILT ? T(2e-3) : T(0);        // margin of the FP32 prefilters (A)
     const T lo = FILT ? T(-1e-4) : T(0), hi = hT + (FILT ? T(1e-4) : T(0));
+    const T tmax = T(1e-3);                    // FP32 root error beyond which FP64 decides (grazing pieces)
+    const float tie = 1e-6f * (float)h;         // FP32 rounding of a root
+    const bool inside = lab_s == LABEL_IN;
+    const double NaN = __longlong_as_double(0x7ff8000000000000LL);
     for (int it = lane; it < na + nv + np; it += 32) {
-        if (it < na) {  // convex: van der Waals sphere, witness = projection on the expanded sphere
-            P4<T> c = S.atom[it];
+        if (it < na + nv) {  // spheres: convex (van der Waals, witness = projection) or concave (probe)
+            const bool vdw = it < na;
+            const int slot = vdw ? it : it - na;
+            P4<T> c = vdw ? S.atom[slot] : S.vq[slot];
+            const T rad = vdw ? c.w : rpT;
             T d[3] = {s[0] - c.x, s[1] - c.y, s[2] - c.z};
             T dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-            T reach = c.w + hT + mg;
+            T reach = rad + hT + mg;
             if (dd > reach * reach) continue;
-            T b = d[axis], disc = b * b - (dd - c.w * c.w);
+            T b = d[axis], disc = b * b - (dd - rad * rad);
             if (disc < -mg) continue;
-            T co32[3] = {dd - c.w * c.w, T(2) * b, T(1)};
+            T co32[3] = {dd - rad * rad, T(2) * b, T(1)};
             T rt32[2];
             int nr = PolyRoots<T, 2>::run(co32, lo, hi, rt32);
             if (FILT && nr == 0 && disc < mg) {  // grazing: let FP64 decide
                 rt32[0] = -b;
                 nr = (-b >= lo && -b <= hi) ? 1 : 0;
             }
-            if (nr == 0) continue;
-            P4<double> ce = X.atom(it);
-            double de[3] = {s64[0] - ce.x, s64[1] - ce.y, s64[2] - ce.z};
-            double co[3] = {de[0] * de[0] + de[1] * de[1] + de[2] * de[2] - ce.w * ce.w, 2.0 * de[axis], 1.0};
             for (int k = 0; k < nr; ++k) {
-                double t = polish<2>(co, (double)rt32[k]);
-                if (!(t >= 0.0 && t <= h) || fabs(horner<double, 2>(co, t)) > 1e-9 * ce.w) continue;
-                double v[3] = {de[0], de[1], de[2]};
-                v[axis] += t;
-                // the witness distance R - |y - c| must fall from an inside end point
-                // and rise from an outside one: its rate has the sign of -v_axis
-                if (inside ? -v[axis] > 1e-9 * ce.w : -v[axis] < -1e-9 * ce.w) continue;
-                T v32[3] = {(T)v[0], (T)v[1], (T)v[2]};
-                T R = c.w + rpT;
-                T sc = R / sqrt(v32[0] * v32[0] + v32[1] * v32[1] + v32[2] * v32[2]);
-                int f = FILT ? free_pt<true>(A, c.x + sc * v32[0], c.y + sc * v32[1], c.z + sc * v32[2], S.agid[it], -1,
-                                             rpT, fd)
-                             : -1;
-                if (f < 0) {
-                    double nvv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-                    double R64 = ce.w + rp;
-                    f = free_pt<false>(X, ce.x + R64 * v[0] / nvv, ce.y + R64 * v[1] / nvv, ce.z + R64 * v[2] / nvv,
-                                       S.agid[it], -1, rp, 0.0);
+                T t = rt32[k];
+                T vA = d[axis] + t;  // +-sqrt(disc) at a root: the rate of |y - c|
+                T terr = T(0);
+                if (FILT) {
+                    T derr = T(2) * (fabs(b) + sqrt(dd)) * d0 + T(2e-6) * (dd + rad * rad);
+                    terr = d0 + derr / (T(2) * fmax(fabs(vA), T(1e-20)));
                 }
-                if (f == 1) warp_push(E, warp, t, 0.0, 0.0, 0.0, 0, it);
-            }
-        } else if (it < na + nv) {  // concave: probe sphere around a free triple point
-            const int vi = it - na;
-            P4<T> c = S.vq[vi];
-            T d[3] = {s[0] - c.x, s[1] - c.y, s[2] - c.z};
-            T dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-            T reach = rpT + hT + mg;
-            if (dd > reach * reach) continue;
-            T b = d[axis], disc = b * b - (dd - rpT * rpT);
-            if (disc < -mg) continue;
-            T co32[3] = {dd - rpT * rpT, T(2) * b, T(1)};
-            T rt32[2];
-            int nr = PolyRoots<T, 2>::run(co32, lo, hi, rt32);
-            if (FILT && nr == 0 && disc < mg) {
-                rt32[0] = -b;
-                nr = (-b >= lo && -b <= hi) ? 1 : 0;
-            }
-            if (nr == 0) continue;
-            P4<double> ce = X.vq(vi);
-            double de[3] = {s64[0] - ce.x, s64[1] - ce.y, s64[2] - ce.z};
-            double co[3] = {de[0] * de[0] + de[1] * de[1] + de[2] * de[2] - rp * rp, 2.0 * de[axis], 1.0};
-            for (int k = 0; k < nr; ++k) {
-                double t = polish<2>(co, (double)rt32[k]);
-                if (!(t >= 0.0 && t <= h) || fabs(horner<double, 2>(co, t)) > 1e-9 * rp) continue;
-                double rate = de[axis] + t;  // sign of d|y - v|/dt
-                if (inside ? rate > 1e-9 * rp : rate < -1e-9 * rp) continue;
-                warp_push(E, warp, t, 0.0, 0.0, 0.0, 2, vi);
+                double t64 = NaN;
+                bool exact = FILT && (terr > tmax || t < terr + T(1e-6) || t > hT - terr - T(1e-6));
+                if (exact) {
+                    P4<double> ce = vdw ? X.atom(slot) : X.vq(slot);
+                    double cc[3] = {ce.x, ce.y, ce.z};
+                    double r64 = vdw ? ce.w : rp;
+                    t64 = exact_root_sphere(cc, r64, s64, axis, (double)t);
+                    double dv[3] = {s64[0] - cc[0], s64[1] - cc[1], s64[2] - cc[2]};
+                    dv[axis] += t64;
+                    double f = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2] - r64 * r64;
+                    if (!(t64 >= 0.0 && t64 <= h) || fabs(f) > 1e-9 * r64) continue;
+                    vA = (T)dv[axis];
+                    if (fabs(dv[axis]) <= 1e-9 * r64) vA = T(0);  // tangent: either way
+                    t = (T)t64;
+                    terr = T(0);
+                }
+                // witness distance: R - |y - c| (convex) falls iff vA > 0; |y - v| (concave) rises iff vA > 0
+                const bool rises = vdw ? (vA < T(0)) : (vA > T(0));
+                const bool falls = vdw ? (vA > T(0)) : (vA < T(0));
+                if (inside ? rises : falls) continue;
+                if (vdw) {
+                    T v32[3] = {d[0], d[1], d[2]};
+                    v32[axis] += t;
+                    T nvv = sqrt(v32[0] * v32[0] + v32[1] * v32[1] + v32[2] * v32[2]);
+                    T R = c.w + rpT;
+                    T sc = R / nvv;
+                    int f = -1;
+                    if (FILT) {
+                        T delta = d0 + terr * (T(1) + sc) + T(2e-6);
+                        f = free_pt<true>(A, c.x + sc * v32[0], c.y + sc * v32[1], c.z + sc * v32[2], S.agid[slot], -1,
+                                          rpT, delta);
+                    }
+                    if (f < 0) {
+                        P4<double> ce = X.atom(slot);
+                        double cc[3] = {ce.x, ce.y, ce.z};
+                        if (t64 != t64) t64 = exact_root_sphere(cc, ce.w, s64, axis, (double)t);
+                        double v[3] = {s64[0] - cc[0], s64[1] - cc[1], s64[2] - cc[2]};
+                        v[axis] += t64;
+                        double nv64 = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+                        double R64 = ce.w + rp;
+                        f = free_pt<false>(X, cc[0] + R64 * v[0] / nv64, cc[1] + R64 * v[1] / nv64,
+                                           cc[2] + R64 * v[2] / nv64, S.agid[slot], -1, rp, 0.0);
+                    }
+                    if (f != 1) continue;
+                }
+                warp_push(E, warp, (float)t, (float)terr, t64, vdw ? 0 : 2, slot);
             }
         } else {  // saddle: torus around a free-arc circle
             const int pi = it - na - nv;
@@ -329,133 +421,158 @@ __device__ int warp_edge(const Model &M, const TileS<T> &S, const double *x0, Ed
             T e1 = sqrt(w2) - o.w;
             T gm = sqrt(e1 * e1 + zc * zc) - rpT;
             if (fabs(gm) > T(0.5) * hT + mg) continue;
-            // quartic (|y-o|^2 + rho^2 - r_p^2)^2 - 4 rho^2 |w|^2 in t
             T q0[3] = {s[0] - o.x, s[1] - o.y, s[2] - o.z};
-            T uu32[3] = {u.x, u.y, u.z};
+            T uu[3] = {u.x, u.y, u.z};
             T P = q0[0] * q0[0] + q0[1] * q0[1] + q0[2] * q0[2];
             T z0 = q0[0] * u.x + q0[1] * u.y + q0[2] * u.z;
-            T pe = q0[axis], eu = uu32[axis];
+            T pe = q0[axis], eu = uu[axis];
             T K = P + o.w * o.w - rpT * rpT, r2 = o.w * o.w;
             T co32[5] = {K * K - T(4) * r2 * (P - z0 * z0), T(4) * pe * K - T(8) * r2 * (pe - z0 * eu),
                          T(4) * pe * pe + T(2) * K - T(4) * r2 * (T(1) - eu * eu), T(4) * pe, T(1)};
             T rt32[4];
             int nr = PolyRoots<T, 4>::run(co32, lo, hi, rt32);
-            if (nr == 0) continue;
-            P4<double> oe = X.po(pi);
-            P4<double> ue = X.pu(pi);
-            const double rho = oe.w;
-            double p0[3] = {s64[0] - oe.x, s64[1] - oe.y, s64[2] - oe.z};
-            double uu[3] = {ue.x, ue.y, ue.z};
-            double Pd = p0[0] * p0[0] + p0[1] * p0[1] + p0[2] * p0[2];
-            double z0d = p0[0] * uu[0] + p0[1] * uu[1] + p0[2] * uu[2];
-            double ped = p0[axis], eud = uu[axis];
-            double Kd = Pd + rho * rho - rp * rp;
-            double r2d = rho * rho;
-            double co[5];
-            co[4] = 1.0;
-            co[3] = 4.0 * ped;
-            co[2] = 4.0 * ped * ped + 2.0 * Kd - 4.0 * r2d * (1.0 - eud * eud);
-            co[1] = 4.0 * ped * Kd - 8.0 * r2d * (ped - z0d * eud);
-            co[0] = Kd * Kd - 4.0 * r2d * (Pd - z0d * z0d);
+            // error scale of the FP32 quartic: its terms' sizes
+            const T Sf = fabs(co32[0]) + fabs(co32[1]) * hT + fabs(co32[2]) * hT * hT + T(6) * (P + r2 + rpT * rpT) * d0;
             for (int k = 0; k < nr; ++k) {
-                double t = polish<4>(co, (double)rt32[k]);
-                if (!(t >= 0.0 && t <= h)) continue;
-                double y[3] = {p0[0], p0[1], p0[2]};
+                T t = rt32[k];
+                T y[3] = {q0[0], q0[1], q0[2]};
                 y[axis] += t;
-                // near branch (|w| - rho)^2 + z^2 = r_p^2  <=>  |y-o|^2 + rho^2 - r_p^2 >= 0
-                double Ay = y[0] * y[0] + y[1] * y[1] + y[2] * y[2] + rho * rho - rp * rp;
-                if (Ay < 0.0) continue;
-                double zy = y[0] * uu[0] + y[1] * uu[1] + y[2] * uu[2];
-                double w[3] = {y[0] - zy * uu[0], y[1] - zy * uu[1], y[2] - zy * uu[2]};
-                double w2d = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
-                if (!(w2d > 0.0)) continue;
-                // rate of the distance to the circle: ((|w| - rho) w_a / |w| + z u_a) / r_p
-                float nwf = sqrtf((float)w2d);
-                float rate = ((nwf - (float)rho) * (float)w[axis] / nwf + (float)(zy * uu[axis])) / (float)rp;
-                if (fabsf(rate) < 1e-4f) {
-                    double nw = sqrt(w2d);
-                    double rd = ((nw - rho) * w[axis] / nw + zy * uu[axis]) / rp;
-                    rate = rd > 1e-9 ? 1.0f : (rd < -1e-9 ? -1.0f : 0.0f);
+                T dfd = T(4) * t * t * t + T(3) * co32[3] * t * t + T(2) * co32[2] * t + co32[1];
+                T yy = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
+                T Ay = yy + r2 - rpT * rpT;
+                T zy = y[0] * uu[0] + y[1] * uu[1] + y[2] * uu[2];
+                T w[3] = {y[0] - zy * uu[0], y[1] - zy * uu[1], y[2] - zy * uu[2]};
+                T nw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+                T rate = nw > T(0) ? ((nw - o.w) * w[axis] / nw + zy * uu[axis]) / rpT : T(0);
+                T terr = FILT ? T(8e-7) * Sf / fmax(fabs(dfd), T(1e-20)) + d0 : T(0);
+                double t64 = NaN;
+                bool exact = FILT && (terr > tmax || t < terr + T(1e-6) || t > hT - terr - T(1e-6) ||
+                                      fabs(Ay) < T(1e-3) * (yy + r2 + rpT * rpT) || fabs(rate) < T(1e-3) ||
+                                      nw < T(1e-3));
+                bool near_branch = Ay >= T(0);
+                if (exact) {
+                    P4<double> oe = X.po(pi);
+                    P4<double> ue = X.pu(pi);
+                    double oo[3] = {oe.x, oe.y, oe.z}, u64[3] = {ue.x, ue.y, ue.z};
+                    t64 = exact_root_torus(oo, u64, oe.w, rp, s64, axis, (double)t);
+                    if (!(t64 >= 0.0 && t64 <= h)) continue;
+                    double yd[3] = {s64[0] - oo[0], s64[1] - oo[1], s64[2] - oo[2]};
+                    yd[axis] += t64;
+                    double Ad = yd[0] * yd[0] + yd[1] * yd[1] + yd[2] * yd[2] + oe.w * oe.w - rp * rp;
+                    double zd = yd[0] * u64[0] + yd[1] * u64[1] + yd[2] * u64[2];
+                    double wd[3] = {yd[0] - zd * u64[0], yd[1] - zd * u64[1], yd[2] - zd * u64[2]};
+                    double nwd = sqrt(wd[0] * wd[0] + wd[1] * wd[1] + wd[2] * wd[2]);
+                    double near2 = (nwd - oe.w) * (nwd - oe.w) + zd * zd;
+                    if (fabs(near2 - rp * rp) > 1e-7 * rp * rp || !(nwd > 0.0)) continue;
+                    near_branch = Ad >= 0.0;
+                    double rd = ((nwd - oe.w) * wd[axis] / nwd + zd * u64[axis]) / rp;
+                    rate = (fabs(rd) <= 1e-9) ? T(0) : (T)rd;
+                    for (int z = 0; z < 3; ++z) w[z] = (T)wd[z];
+                    nw = (T)nwd;
+                    t = (T)t64;
+                    terr = T(0);
                 }
-                if (inside ? rate > 0.0f : rate < 0.0f) continue;
-                T kk = (T)(rho / (double)nwf);
+                if (!near_branch) continue;  // far branch of the quartic
+                if (inside ? rate > T(0) : rate < T(0)) continue;
                 int2 ij = S.pij[pi];
-                int f = FILT ? free_pt<true>(A, o.x + kk * (T)w[0], o.y + kk * (T)w[1], o.z + kk * (T)w[2], ij.x, ij.y,
-                                             rpT, fd)
-                             : -1;
-                if (f < 0) {
-                    double nw = sqrt(w2d);
-                    f = free_pt<false>(X, oe.x + rho * w[0] / nw, oe.y + rho * w[1] / nw, oe.z + rho * w[2] / nw, ij.x,
-                                       ij.y, rp, 0.0);
+                T kk = o.w / nw;
+                int f = -1;
+                if (FILT) {
+                    T delta = d0 + terr * (T(1) + T(2) * o.w / nw) + T(2e-6);
+                    f = free_pt<true>(A, o.x + kk * w[0], o.y + kk * w[1], o.z + kk * w[2], ij.x, ij.y, rpT, delta);
                 }
-                if (f == 1) warp_push(E, warp, t, 0.0, 0.0, 0.0, 1, pi);
+                if (f < 0) {
+                    P4<double> oe = X.po(pi);
+                    P4<double> ue = X.pu(pi);
+                    double oo[3] = {oe.x, oe.y, oe.z}, u64[3] = {ue.x, ue.y, ue.z};
+                    if (t64 != t64) t64 = exact_root_torus(oo, u64, oe.w, rp, s64, axis, (double)t);
+                    double yd[3] = {s64[0] - oo[0], s64[1] - oo[1], s64[2] - oo[2]};
+                    yd[axis] += t64;
+                    double zd = yd[0] * u64[0] + yd[1] * u64[1] + yd[2] * u64[2];
+                    double wd[3] = {yd[0] - zd * u64[0], yd[1] - zd * u64[1], yd[2] - zd * u64[2]};
+                    double nwd = sqrt(wd[0] * wd[0] + wd[1] * wd[1] + wd[2] * wd[2]);
+                    double k64 = oe.w / nwd;
+                    f = free_pt<false>(X, oo[0] + k64 * wd[0], oo[1] + k64 * wd[1], oo[2] + k64 * wd[2], ij.x, ij.y,
+                                       rp, 0.0);
+                }
+                if (f == 1) warp_push(E, warp, (float)t, (float)terr, t64, 1, pi);
             }
         }
     }
     __syncwarp();
     int n = E.ncand[warp];
-    int status = n > WCAND ? 2 : 0;  // 2: candidate buffer overflow
+    int status = n > WCAND ? 2 : 0;
     if (n > WCAND) n = WCAND;
     WCand *c = E.cand[warp];
     int pick = -1;
-    if (inside) {
-        pick = warp_argmin(c, n);
-    } else {
-        for (int iter = 0; iter < n; ++iter) {
-            int k = warp_argmin(c, n);
-            if (k < 0) break;
-            double y[3] = {s64[0], s64[1], s64[2]};
-            y[axis] += c[k].t;
-            int r;
-            if (FILT) {
-                r = warp_witness<true>(A, (T)y[0], (T)y[1], (T)y[2], rpT, rpT, d0, c[k].kind, c[k].id);
-                if (r < 0) r = warp_witness<false>(X, y[0], y[1], y[2], rp, rp - 1e-11, 0.0, -1, -1);
-            } else {
-                r = warp_witness<false>(X, y[0], y[1], y[2], rp, rp - 1e-11, 0.0, -1, -1);
-            }
-            if (r == 0) {
-                pick = k;
-                break;
-            }
+    for (int iter = 0; iter <= n; ++iter) {
+        int k = warp_argmin(c, n);
+        if (k < 0) break;
+        // candidates that the FP32 bounds cannot order against k: settle with FP64 roots
+        const float tk = c[k].t, ek = c[k].err;
+        bool tied = false;
+        for (int j = lane; j < n; j += 32)
+            if (j != k && c[j].t < INFINITY && c[j].t - tk <= c[j].err + ek + tie) tied = true;
+        if (__any_sync(0xffffffffu, tied)) {
+            for (int j = lane; j < n; j += 32)
+                if (c[j].t < INFINITY && c[j].t - tk <= c[j].err + ek + tie && c[j].t64 != c[j].t64)
+                    c[j].t64 = staged_exact_root(X, c[j].kind, c[j].id, s64, axis, rp, (double)c[j].t);
             __syncwarp();
-            if (lane == 0) c[k].t = INFINITY;  // strictly outside M: not the root
-            __syncwarp();
+            double bt = INFINITY;
+            int bk = -1;
+            for (int j = lane; j < n; j += 32)
+                if (c[j].t < INFINITY && c[j].t - tk <= c[j].err + ek + tie && c[j].t64 < bt) {
+                    bt = c[j].t64;
+                    bk = j;
+                }
+            for (int o = 16; o > 0; o >>= 1) {
+                double ot = __shfl_xor_sync(0xffffffffu, bt, o);
+                int ok = __shfl_xor_sync(0xffffffffu, bk, o);
+                if (ok >= 0 && (bk < 0 || ot < bt || (ot == bt && ok < bk))) {
+                    bt = ot;
+                    bk = ok;
+                }
+            }
+            k = bk;
         }
+        if (inside) {
+            pick = k;
+            break;
+        }
+        // outside end point: the root must not be strictly outside M
+        int r;
+        if (FILT && c[k].t64 != c[k].t64) {
+            T y0 = s[0], y1 = s[1], y2 = s[2];
+            T tt = (T)c[k].t;
+            if (axis == 0) y0 += tt;
+            else if (axis == 1) y1 += tt;
+            else y2 += tt;
+            r = warp_witness<true>(A, y0, y1, y2, rpT, rpT, d0 + (T)c[k].err, c[k].kind, c[k].id);
+        } else {
+            r = -1;
+        }
+        if (r < 0) {
+            double t64 = c[k].t64;
+            if (t64 != t64) t64 = staged_exact_root(X, c[k].kind, c[k].id, s64, axis, rp, (double)c[k].t);
+            double y[3] = {s64[0], s64[1], s64[2]};
+            y[axis] += t64;
+            r = warp_witness<false>(X, y[0], y[1], y[2], rp, rp - 1e-11, 0.0, -1, -1);
+        }
+        if (r == 0) {
+            pick = k;
+            break;
+        }
+        __syncwarp();
+        if (lane == 0) c[k].t = INFINITY;  // strictly outside M: not the root
+        __syncwarp();
     }
     if (pick < 0) return 1;
-    // normal at the root: unit vector from the surface point to its witness
-    const double t = c[pick].t;
-    double y[3] = {s64[0], s64[1], s64[2]};
-    y[axis] += t;
-    double v[3];
-    const int kind = c[pick].kind, id = c[pick].id;
-    if (kind == 0) {  // convex: radial, outward
-        P4<double> ce = X.atom(id);
-        v[0] = y[0] - ce.x; v[1] = y[1] - ce.y; v[2] = y[2] - ce.z;
-    } else if (kind == 2) {  // concave: towards the probe centre
-        P4<double> ce = X.vq(id);
-        v[0] = ce.x - y[0]; v[1] = ce.y - y[1]; v[2] = ce.z - y[2];
-    } else {  // saddle: towards the nearest circle point
-        P4<double> oe = X.po(id);
-        P4<double> ue = X.pu(id);
-        double yo[3] = {y[0] - oe.x, y[1] - oe.y, y[2] - oe.z};
-        double zy = yo[0] * ue.x + yo[1] * ue.y + yo[2] * ue.z;
-        double w[3] = {yo[0] - zy * ue.x, yo[1] - zy * ue.y, yo[2] - zy * ue.z};
-        double nw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-        double k2 = oe.w / nw;
-        v[0] = k2 * w[0] - yo[0]; v[1] = k2 * w[1] - yo[1]; v[2] = k2 * w[2] - yo[2];
-    }
-    double vn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-    t_out = t;
-    n_out[0] = v[0] / vn;
-    n_out[1] = v[1] / vn;
-    n_out[2] = v[2] / vn;
+    t_out = c[pick].t64 == c[pick].t64 ? (float)c[pick].t64 : c[pick].t;
+    kind_out = c[pick].kind;
+    slot_out = c[pick].id;
     return status;
 }
 
-// --------------------------------------------------------------------------
-// kernels
-// --------------------------------------------------------------------------
 __device__ __forceinline__ int block_sum_int(int v, int *sh)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -545,28 +662,21 @@ __device__ __forceinline__ int block_excl_scan_e(int v, int *sh, int *total)
 template <class T, bool FILT>
 __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Grid G, const int8_t *__restrict__ labels,
                                                              const int *__restrict__ edge_start, EdgeOut out,
-                                                             double *__restrict__ tile_area,
-                                                             double *__restrict__ tile_vol, int *__restrict__ n_fail,
-                                                             int *__restrict__ err, long long *__restrict__ fail_log)
+                                                             int *__restrict__ n_fail, int *__restrict__ err,
+                                                             long long *__restrict__ fail_log)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileS<T> &S = *reinterpret_cast<TileS<T> *>(smem_raw);
     EdgeSmem &E = *reinterpret_cast<EdgeSmem *>(smem_raw + ((sizeof(TileS<T>) + 15) & ~(size_t)15));
     const long long nt = G.n_tiles;
     const long long st1 = G.dims[2], st0 = G.dims[1] * G.dims[2];
-    const double h = G.h, rp = M.rp, inv_h = 1.0 / G.h;
+    const double h = G.h, rp = M.rp;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const T d0 = FILT ? (T)G.d0 : T(0);
     for (long long tile = blockIdx.x; tile < nt; tile += gridDim.x) {
         int tot = 0;
         for (int a = 0; a < 3; ++a) tot += edge_start[a * nt + tile + 1] - edge_start[a * nt + tile];
-        if (tot == 0) {
-            if (threadIdx.x == 0) {
-                tile_area[tile] = 0.0;
-                tile_vol[tile] = 0.0;
-            }
-            continue;
-        }
+        if (tot == 0) continue;
         double x0[3];
         stage_tile<T>(M, G, tile, S, x0);
         if (threadIdx.x == 0 && S.flags) atomicOr(err, S.flags);
@@ -581,6 +691,7 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Grid G, co
             E.lab[q] = v;
         }
         if (threadIdx.x == 0) E.estart[0] = 0;
+        if (threadIdx.x <= TILE) E.hd[threadIdx.x] = (double)threadIdx.x * h;
         __syncthreads();
         // the tile's crossing edges, axis by axis, in point order
         for (int a = 0; a < 3; ++a) {
@@ -604,23 +715,24 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Grid G, co
             }
             __syncthreads();
         }
-        double area = 0.0, vol = 0.0;
         const int ne = E.estart[3];
         for (int e = warp; e < ne; e += EDGE_WARPS) {
             const int a = e < E.estart[1] ? 0 : (e < E.estart[2] ? 1 : 2);
             const int q = E.eptr[e];
             const int li = q >> 6, lj = (q >> 3) & 7, lk = q & 7;
             const int lab_s = E.lab[(li * 9 + lj) * 9 + lk];
-            double tr = 0.5 * h, nrm[3] = {0.0, 0.0, 0.0};
-            int status = warp_edge<T, FILT>(M, S, x0, E, warp, a, q, lab_s, h, rp, d0, tr, nrm);
+            float tr = 0.5f * (float)h;
+            int kind = 0, slot = 0;
+            int status = warp_edge<T, FILT>(M, S, x0, E, warp, a, q, lab_s, h, rp, d0, tr, kind, slot);
             if (lane == 0) {
-                if (status == 1) nrm[0] = nrm[1] = nrm[2] = 0.0;
+                int mid = 0;
+                if (status != 1) mid = kind == 0 ? S.agid[slot] : (kind == 1 ? S.pidx[slot] : S.vidx[slot]);
                 if (status != 0) {
                     atomicOr(err, status == 1 ? ERR_ROOT : ERR_CAP_CAND);
                     if (status == 1) {
-                        int slot = atomicAdd(n_fail, 1);
-                        if (slot < FAIL_LOG) {
-                            long long *rec = fail_log + FAIL_REC * slot;
+                        int fs = atomicAdd(n_fail, 1);
+                        if (fs < FAIL_LOG) {
+                            long long *rec = fail_log + FAIL_REC * fs;
                             for (int z = 0; z < FAIL_REC; ++z) rec[z] = 0;
                             rec[0] = a;
                             rec[1] = (long long)TILE * t[0] + li;
@@ -632,7 +744,7 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Grid G, co
                             rec[7] = S.nv;
                             rec[8] = E.ncand[warp];
                             for (int z = 0; z < 7 && z < E.ncand[warp] && z < WCAND; ++z) {
-                                rec[9 + z] = (long long)(E.cand[warp][z].t * 1e9);
+                                rec[9 + z] = (long long)((double)E.cand[warp][z].t * 1e9);
                                 rec[16 + z] = E.cand[warp][z].kind;
                             }
                         }
@@ -641,33 +753,97 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Grid G, co
                 const long long o = E.ebase[a] + (e - E.estart[a]);
                 out.idx[a][o] = (long long)(TILE * t[0] + li) * st0 + (long long)(TILE * t[1] + lj) * st1 +
                                 (TILE * t[2] + lk);
-                out.tau[a][o] = tr * inv_h;
-                out.nrm[a][3 * o + 0] = nrm[0];
-                out.nrm[a][3 * o + 1] = nrm[1];
-                out.nrm[a][3 * o + 2] = nrm[2];
-                out.tau32[a][o] = (float)(tr * inv_h);
-                out.nrm32[a][3 * o + 0] = (float)nrm[0];
-                out.nrm32[a][3 * o + 1] = (float)nrm[1];
-                out.nrm32[a][3 * o + 2] = (float)nrm[2];
-                area += h * h * fabs(nrm[a]);
-                vol += lab_s == LABEL_IN ? tr : h - tr;
+                // chosen piece for the FP64 polish: FP32 root, kind, model index, end label, failure
+                out.code[a][o] = make_int2(__float_as_int(tr), (kind << 29) | (lab_s << 28) |
+                                                                    ((status == 1 ? 1 : 0) << 27) | mid);
             }
             __syncwarp();
-        }
-        double ta = block_sum_double(area, E.shd);
-        double tv = block_sum_double(vol, E.shd);
-        if (threadIdx.x == 0) {
-            tile_area[tile] = ta;
-            tile_vol[tile] = tv;
         }
         __syncthreads();
     }
 }
 
+// One thread per crossing edge, over the three axes: FP64 root of the chosen
+// piece next to the recorded FP32 root, normal, outputs, area/volume terms
+// (block partial sums in fixed order).
+__global__ void __launch_bounds__(POLISH_THREADS) k_edge_polish(Model M, Grid G, EdgeOut out, long long n0,
+                                                                long long n1, long long n2,
+                                                                double *__restrict__ part)
+{
+    __shared__ double sha[POLISH_THREADS / 32], shv[POLISH_THREADS / 32];
+    const long long e = (long long)blockIdx.x * POLISH_THREADS + threadIdx.x;
+    const double h = G.h, rp = M.rp;
+    double area = 0.0, vol = 0.0;
+    if (e < n0 + n1 + n2) {
+        const int a = e < n0 ? 0 : (e < n0 + n1 ? 1 : 2);
+        const long long o = e - (a == 0 ? 0 : (a == 1 ? n0 : n0 + n1));
+        const long long idx = out.idx[a][o];
+        const int2 code = out.code[a][o];
+        const float t32 = __int_as_float(code.x);
+        const int kind = (code.y >> 29) & 3, lab_s = (code.y >> 28) & 1, failed = (code.y >> 27) & 1;
+        const int mid = code.y & ((1 << 27) - 1);
+        const long long gi = idx / (G.dims[1] * G.dims[2]), gj = (idx / G.dims[2]) % G.dims[1], gk = idx % G.dims[2];
+        const double s[3] = {G.lo[0] + h * (double)gi, G.lo[1] + h * (double)gj, G.lo[2] + h * (double)gk};
+        double t = 0.5 * h, n[3] = {0.0, 0.0, 0.0};
+        if (!failed) {
+            double c[3], u[3] = {0.0, 0.0, 0.0}, rho = 0.0;
+            if (kind == 0) {
+                double4 g = M.atom[mid];
+                c[0] = g.x; c[1] = g.y; c[2] = g.z;
+                t = exact_root_sphere(c, g.w, s, a, (double)t32);
+            } else if (kind == 2) {
+                double4 g = M.vert[mid];
+                c[0] = g.x; c[1] = g.y; c[2] = g.z;
+                t = exact_root_sphere(c, rp, s, a, (double)t32);
+            } else {
+                double4 g = M.pair_o[mid];
+                double4 q = M.pair_u[mid];
+                c[0] = g.x; c[1] = g.y; c[2] = g.z;
+                u[0] = q.x; u[1] = q.y; u[2] = q.z;
+                rho = g.w;
+                t = exact_root_torus(c, u, rho, rp, s, a, (double)t32);
+            }
+            t = fmin(fmax(t, 0.0), h);
+            double y[3] = {s[0], s[1], s[2]};
+            y[a] += t;
+            exact_normal(kind, c, u, rho, y, n);
+        }
+        const double tau = t * (1.0 / h);
+        out.tau[a][o] = tau;
+        out.nrm[a][3 * o + 0] = n[0];
+        out.nrm[a][3 * o + 1] = n[1];
+        out.nrm[a][3 * o + 2] = n[2];
+        out.tau32[a][o] = (float)tau;
+        out.nrm32[a][3 * o + 0] = (float)n[0];
+        out.nrm32[a][3 * o + 1] = (float)n[1];
+        out.nrm32[a][3 * o + 2] = (float)n[2];
+        area = h * h * fabs(n[a]);
+        vol = lab_s ? t : h - t;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        area += __shfl_down_sync(0xffffffffu, area, off);
+        vol += __shfl_down_sync(0xffffffffu, vol, off);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sha[wid] = area;
+        shv[wid] = vol;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double A = 0.0, V = 0.0;
+        for (int k = 0; k < POLISH_THREADS / 32; ++k) {
+            A += sha[k];
+            V += shv[k];
+        }
+        part[2 * blockIdx.x] = A;
+        part[2 * blockIdx.x + 1] = V;
+    }
+}
+
 // single-block deterministic reduction: out2 = {area, volume};
-// counts = {inside points, inside edges (all axes), crossing edges}
-__global__ void __launch_bounds__(1024) k_reduce(Grid G, const double *__restrict__ tile_area,
-                                                 const double *__restrict__ tile_vol,
+// counts = {inside points, inside edges (all axes)}
+__global__ void __launch_bounds__(1024) k_reduce(Grid G, const double *__restrict__ part, long long nparts,
                                                  const int *__restrict__ tile_inside, double *__restrict__ out2,
                                                  long long *__restrict__ counts)
 {
@@ -676,9 +852,11 @@ __global__ void __launch_bounds__(1024) k_reduce(Grid G, const double *__restric
     const long long nt = G.n_tiles;
     double a = 0.0, v = 0.0;
     long long ie = 0, pin = 0;
+    for (long long k = threadIdx.x; k < nparts; k += blockDim.x) {
+        a += part[2 * k];
+        v += part[2 * k + 1];
+    }
     for (long long k = threadIdx.x; k < nt; k += blockDim.x) {
-        a += tile_area[k];
-        v += tile_vol[k];
         ie += (long long)tile_inside[k] + tile_inside[nt + k] + tile_inside[2 * nt + k];
         pin += tile_inside[3 * nt + k];
     }
@@ -726,30 +904,34 @@ int launch_edge_count(const Grid &G, const int8_t *labels, int *tile_edges, int 
 
 template <class T, bool FILT>
 static void edge_solve_launch(const Model &M, const Grid &G, const int8_t *labels, const int *edge_start, EdgeOut out,
-                              double *tile_area, double *tile_vol, int *n_fail, int *err, long long *fail_log,
-                              cudaStream_t st)
+                              int *n_fail, int *err, long long *fail_log, cudaStream_t st)
 {
     size_t sm = ((sizeof(TileS<T>) + 15) & ~(size_t)15) + sizeof(EdgeSmem);
     cudaFuncSetAttribute(k_edge_solve<T, FILT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_edge_solve<T, FILT><<<grid_tiles(G.n_tiles), EDGE_THREADS, sm, st>>>(M, G, labels, edge_start, out, tile_area,
-                                                                           tile_vol, n_fail, err, fail_log);
+    k_edge_solve<T, FILT><<<grid_tiles(G.n_tiles), EDGE_THREADS, sm, st>>>(M, G, labels, edge_start, out, n_fail, err,
+                                                                           fail_log);
 }
+
+long long polish_blocks(long long n_edges) { return n_edges > 0 ? ceil_div_ll(n_edges, POLISH_THREADS) : 0; }
 
 int launch_edge_solve(const Model &M, const Grid &G, int precision, const int8_t *labels, const int *edge_start,
-                      EdgeOut out, double *tile_area, double *tile_vol, int *n_fail, int *err, long long *fail_log,
-                      cudaStream_t st)
+                      EdgeOut out, const long long n_edges[3], double *part, int *n_fail, int *err,
+                      long long *fail_log, cudaStream_t st)
 {
     if (precision == 0)
-        edge_solve_launch<double, false>(M, G, labels, edge_start, out, tile_area, tile_vol, n_fail, err, fail_log, st);
+        edge_solve_launch<double, false>(M, G, labels, edge_start, out, n_fail, err, fail_log, st);
     else
-        edge_solve_launch<float, true>(M, G, labels, edge_start, out, tile_area, tile_vol, n_fail, err, fail_log, st);
-    return 1;
+        edge_solve_launch<float, true>(M, G, labels, edge_start, out, n_fail, err, fail_log, st);
+    long long nb = polish_blocks(n_edges[0] + n_edges[1] + n_edges[2]);
+    if (nb > 0)
+        k_edge_polish<<<(unsigned)nb, POLISH_THREADS, 0, st>>>(M, G, out, n_edges[0], n_edges[1], n_edges[2], part);
+    return nb > 0 ? 2 : 1;
 }
 
-int launch_reduce(const Grid &G, const double *tile_area, const double *tile_vol, const int *tile_inside,
-                   const int8_t *, double *out2, long long *counts, cudaStream_t st)
+int launch_reduce(const Grid &G, const double *part, long long nparts, const int *tile_inside, double *out2,
+                  long long *counts, cudaStream_t st)
 {
-    k_reduce<<<1, 1024, 0, st>>>(G, tile_area, tile_vol, tile_inside, out2, counts);
+    k_reduce<<<1, 1024, 0, st>>>(G, part, nparts, tile_inside, out2, counts);
     return 1;
 }
 

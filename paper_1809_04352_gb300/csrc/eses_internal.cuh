@@ -67,6 +67,15 @@ struct Model {
     const int *vcell_start;
     const int *vcell_list;
     double rp, rmax, Rmax;
+    // FP32 double-float copies relative to the grid origin (value = hi + lo):
+    // staging in FP32 keeps the FP64 frame's accuracy without FP64 arithmetic
+    const float4 *atom_hi;        // (x, y, z, r)
+    const float4 *atom_lo;        // (x, y, z, 0)
+    const float4 *pair_hi;        // (o, rho)
+    const float4 *pair_lo;        // (o, 0)
+    const float4 *pair_u32;       // (u, 0)
+    const float4 *vert_hi;
+    const float4 *vert_lo;
 };
 
 struct Grid {
@@ -78,6 +87,8 @@ struct Grid {
     double rp;
     double halo;                  // r_max + 2 r_p
     float d0;                     // FP32 error bound of a staged position difference
+    float hl[TILE + 1];           // k * h rounded to FP32, k = 0..8 (tile-frame point coordinates)
+    float ht_hi, ht_lo;           // TILE * h as a double-float
 };
 
 __host__ __device__ inline long long ceil_div_ll(long long a, long long b) { return (a + b - 1) / b; }

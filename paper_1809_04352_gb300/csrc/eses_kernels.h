@@ -31,6 +31,9 @@ int launch_arcs(const Model &M, uint8_t *pair_free, int *vert_count, cudaStream_
 int launch_arcs_emit(const Model &M, const int *vert_start, double4 *vert, cudaStream_t st);
 int launch_faces(const Model &M, const int *circle_count, const uint8_t *contained, uint8_t *face, cudaStream_t st);
 int launch_bin_count(const Model &M, int which, int *count, int *item_cell, cudaStream_t st);
+// FP32 double-float copies: which 0 atoms (hi, lo), 1 circles (hi, lo, axis), 2 triple points (hi, lo)
+int launch_model_f32(const Model &M, int which, const double lo[3], float4 *hi, float4 *lo_, float4 *u32,
+                     cudaStream_t st);
 int launch_bin_scatter(const Model &M, int which, const int *item_cell, const int *start, int *cursor, int *list,
                         cudaStream_t st);
 
@@ -48,15 +51,17 @@ struct EdgeOut {
     double *nrm[3];
     float *tau32[3];
     float *nrm32[3];
+    int2 *code[3];  // chosen piece per edge, from the warp solve to the FP64 polish
 };
 // failed-edge log: FAIL_LOG records of FAIL_REC int64 (axis, i, j, k, label,
 // staged atoms/pairs/vertices, then the 16 edge_root debug counters)
 constexpr int FAIL_LOG = 8;
 constexpr int FAIL_REC = 24;
+long long polish_blocks(long long n_edges);
 int launch_edge_solve(const Model &M, const Grid &G, int precision, const int8_t *labels, const int *edge_start,
-                      EdgeOut out, double *tile_area, double *tile_vol, int *n_fail, int *err, long long *fail_log,
-                      cudaStream_t st);
-int launch_reduce(const Grid &G, const double *tile_area, const double *tile_vol, const int *tile_inside_edges,
-                   const int8_t *labels, double *out2, long long *counts, cudaStream_t st);
+                      EdgeOut out, const long long n_edges[3], double *part, int *n_fail, int *err,
+                      long long *fail_log, cudaStream_t st);
+int launch_reduce(const Grid &G, const double *part, long long nparts, const int *tile_inside, double *out2,
+                  long long *counts, cudaStream_t st);
 
 }  // namespace eses

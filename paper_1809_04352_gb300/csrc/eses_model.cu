@@ -22,6 +22,13 @@
 
 namespace eses {
 
+// double-float split of a grid-frame coordinate
+__device__ __forceinline__ void split_df(double v, float &hi, float &lo)
+{
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
 __device__ __forceinline__ int cell_coord(double v, double lo, double cell, int n)
 {
     int k = (int)floor((v - lo) / cell);
@@ -368,11 +375,190 @@ __device__ void arcs_of_pair(const Model &M, int p, uint8_t *pair_free, int *ver
     }
 }
 
+// FP32-filtered form of arcs_of_pair: the common neighbours are cached in
+// FP32 in the circle's frame (from the double-float copies: two roundings of
+// the offset), and every decision -- common neighbour, no/partial/full cover,
+// end point covered -- is taken in FP32 when it clears its error bound and in
+// FP64 otherwise, so the decisions are those of the FP64 form.  FP32 end
+// points carry a propagated error bound (the FP64 end point is used when that
+// bound exceeds 2e-4 A); emitted triple points are always computed in FP64.
+constexpr int ARC_MAXN = 48;
+
+// 1: d2 < t^2 certain, 0: d2 >= t^2 certain, -1 undecided (delta: error of the vector)
+__device__ __forceinline__ int arc_lt(float d2, float t, float delta)
+{
+    float t2 = t * t;
+    float e = 2.0f * ((2.0f * t + delta) * delta + 1e-6f * t2);
+    if (d2 < t2 - e) return 1;
+    if (d2 >= t2 + e) return 0;
+    return -1;
+}
+
+template <bool EMIT>
+__device__ void arcs_of_pair32(const Model &M, int p, uint8_t *pair_free, int *vert_count, const int *vert_start,
+                               double4 *vert)
+{
+    int2 ij = M.pair_ij[p];
+    const int i = ij.x, j = ij.y;
+    // the circle in FP32: centre from its double-float copy, axis, a frame
+    const float4 oh = M.pair_hi[p], ol = M.pair_lo[p], u4 = M.pair_u32[p];
+    const float rho = oh.w;
+    const float ux = u4.x, uy = u4.y, uz = u4.z;
+    const float tx = fabsf(ux) > 0.6f ? 0.0f : 1.0f, ty = fabsf(ux) > 0.6f ? 1.0f : 0.0f;
+    float v1x = -uz * ty, v1y = uz * tx, v1z = ux * ty - uy * tx;
+    const float iv1 = 1.0f / sqrtf(v1x * v1x + v1y * v1y + v1z * v1z);
+    v1x *= iv1; v1y *= iv1; v1z *= iv1;
+    const float v2x = uy * v1z - uz * v1y, v2y = uz * v1x - ux * v1z, v2z = ux * v1y - uy * v1x;
+    // offsets to the circle centre: (hi - hi) + (lo - lo), two roundings of the result
+    const float dlt = 3e-6f;  // error bound of such an offset vector (|offset| <= 2 R_max)
+    const float4 jh = M.atom_hi[j], jl = M.atom_lo[j];
+    const float djx = (jh.x - oh.x) + (jl.x - ol.x), djy = (jh.y - oh.y) + (jl.y - ol.y),
+                djz = (jh.z - oh.z) + (jl.z - ol.z);
+    const float rpf = (float)M.rp;
+    const float Rj = jh.w + rpf;
+    double4 cj = M.atom[j];
+    const double Rj64 = cj.w + M.rp;
+    float4 nb[ARC_MAXN];
+    int nbk[ARC_MAXN];
+    int n = 0;
+    for (int t = M.nb_start[i]; t < M.nb_start[i + 1]; ++t) {
+        int k = M.nb_list[t];
+        if (k == j) continue;
+        const float4 kh = M.atom_hi[k], kl = M.atom_lo[k];
+        float dx = (kh.x - oh.x) + (kl.x - ol.x), dy = (kh.y - oh.y) + (kl.y - ol.y), dz = (kh.z - oh.z) + (kl.z - ol.z);
+        float Rk = kh.w + rpf;
+        float ex = dx - djx, ey = dy - djy, ez = dz - djz;
+        int c = arc_lt(ex * ex + ey * ey + ez * ez, Rk + Rj, 2.0f * dlt);
+        if (c == 0) continue;
+        if (c < 0 && !common_nb(M, k, i, j, cj, Rj64)) continue;
+        if (n == ARC_MAXN) {  // very crowded circle: the FP64 form
+            arcs_of_pair<EMIT>(M, p, pair_free, vert_count, vert_start, vert);
+            return;
+        }
+        nb[n] = make_float4(dx, dy, dz, Rk);
+        nbk[n] = k;
+        ++n;
+    }
+    bool full = false;
+    bool have64 = false;
+    CircleFrame f;
+    int n_partial = 0, n_free_end = 0, n_emit = 0;
+    int w = EMIT ? vert_start[p] : 0;
+    for (int a = 0; a < n && !full; ++a) {
+        const float4 c = nb[a];
+        const float d1 = c.x * v1x + c.y * v1y + c.z * v1z;
+        const float d2 = c.x * v2x + c.y * v2y + c.z * v2z;
+        const float dd = c.x * c.x + c.y * c.y + c.z * c.z;
+        const float A = sqrtf(d1 * d1 + d2 * d2);
+        const float num = rho * rho + dd - c.w * c.w, den = 2.0f * rho * A;
+        const float dk = sqrtf(dd);
+        // error bounds of num and den (offset error dlt, roundings)
+        const float en = 2.0f * dk * dlt + 2e-6f * (rho * rho + dd + c.w * c.w);
+        const float ed = 2.0f * rho * (dlt + 3e-7f * dk) + 2e-6f * den;
+        const float err = 2.0f * (en + ed);
+        if (num >= den + err) continue;  // no cover
+        if (num < -den - err) {          // the whole circle
+            full = true;
+            break;
+        }
+        double3 qe[2];
+        bool e64 = false;
+        float qf[2][3];
+        float dq = 1.0f;
+        if (num < den - err && num > -den + err) {  // partial for certain: FP32 end points
+            const float T = num / den;
+            const float sT = sqrtf(fmaxf(0.0f, 1.0f - T * T));
+            const float iA = 1.0f / A;
+            const float epx = (d1 * v1x + d2 * v2x) * iA, epy = (d1 * v1y + d2 * v2y) * iA,
+                        epz = (d1 * v1z + d2 * v2z) * iA;
+            const float enx = uy * epz - uz * epy, eny = uz * epx - ux * epz, enz = ux * epy - uy * epx;
+            for (int e = 0; e < 2; ++e) {
+                const float sg = e == 0 ? 1.0f : -1.0f;
+                qf[e][0] = rho * (T * epx + sg * sT * enx);
+                qf[e][1] = rho * (T * epy + sg * sT * eny);
+                qf[e][2] = rho * (T * epz + sg * sT * enz);
+            }
+            const float dT = (en + fabsf(T) * ed) / den;
+            dq = rho * (dT * (1.0f + fabsf(T) / fmaxf(sT, 1e-6f)) + 2.0f * (dlt / fmaxf(A, 1e-6f) + 3e-7f)) + 1e-6f;
+        }
+        if (dq > 2e-4f) {  // undecided cover or loose FP32 end points: FP64
+            if (!have64) {
+                f = frame_of(M.pair_o[p], M.pair_u[p]);
+                have64 = true;
+            }
+            double4 ck = M.atom[nbk[a]];
+            int cov = cover_of(f, ck, ck.w + M.rp, qe[0], qe[1]);
+            if (cov == 2) {
+                full = true;
+                break;
+            }
+            if (cov != 1) continue;
+            for (int e = 0; e < 2; ++e) {
+                qf[e][0] = (float)(qe[e].x - f.o.x);
+                qf[e][1] = (float)(qe[e].y - f.o.y);
+                qf[e][2] = (float)(qe[e].z - f.o.z);
+            }
+            dq = 1e-6f;
+            e64 = true;
+        }
+        ++n_partial;
+        bool fr[2];
+        for (int e = 0; e < 2; ++e) {
+            bool free_ = true;
+            for (int b = 0; b < n && free_; ++b) {
+                if (b == a) continue;
+                const float4 cb = nb[b];
+                float ex = qf[e][0] - cb.x, ey = qf[e][1] - cb.y, ez = qf[e][2] - cb.z;
+                int t = arc_lt(ex * ex + ey * ey + ez * ez, cb.w, dq + dlt);
+                if (t < 0) {  // FP64: the exact end point against the exact ball
+                    if (!e64) {
+                        if (!have64) {
+                            f = frame_of(M.pair_o[p], M.pair_u[p]);
+                            have64 = true;
+                        }
+                        double4 ck = M.atom[nbk[a]];
+                        cover_of(f, ck, ck.w + M.rp, qe[0], qe[1]);
+                        e64 = true;
+                    }
+                    double4 c64 = M.atom[nbk[b]];
+                    double Rb = c64.w + M.rp;
+                    double gx = qe[e].x - c64.x, gy = qe[e].y - c64.y, gz = qe[e].z - c64.z;
+                    t = (gx * gx + gy * gy + gz * gz < Rb * Rb) ? 1 : 0;
+                }
+                if (t == 1) free_ = false;
+            }
+            fr[e] = free_;
+        }
+        n_free_end += (int)fr[0] + (int)fr[1];
+        if (nbk[a] > j && (fr[0] || fr[1])) {  // triple i < j < k: emitted once, from the circle (i, j)
+            if (!e64) {
+                if (!have64) {
+                    f = frame_of(M.pair_o[p], M.pair_u[p]);
+                    have64 = true;
+                }
+                double4 ck = M.atom[nbk[a]];
+                cover_of(f, ck, ck.w + M.rp, qe[0], qe[1]);
+                e64 = true;
+            }
+            for (int e = 0; e < 2; ++e)
+                if (fr[e]) {
+                    if (EMIT) vert[w + n_emit] = make_double4(qe[e].x, qe[e].y, qe[e].z, 0.0);
+                    ++n_emit;
+                }
+        }
+    }
+    if (!EMIT) {
+        bool has_free = !full && (n_partial == 0 || n_free_end > 0);
+        pair_free[p] = has_free ? 1 : 0;
+        vert_count[p] = full ? 0 : n_emit;
+    }
+}
+
 __global__ void k_arcs(Model M, uint8_t *__restrict__ pair_free, int *__restrict__ vert_count)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= M.n_pairs) return;
-    arcs_of_pair<false>(M, p, pair_free, vert_count, nullptr, nullptr);
+    arcs_of_pair32<false>(M, p, pair_free, vert_count, nullptr, nullptr);
 }
 
 __global__ void k_arcs_emit(Model M, const int *__restrict__ vert_start, double4 *__restrict__ vert)
@@ -380,7 +566,7 @@ __global__ void k_arcs_emit(Model M, const int *__restrict__ vert_start, double4
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= M.n_pairs) return;
     if (vert_start[p + 1] == vert_start[p]) return;
-    arcs_of_pair<true>(M, p, nullptr, nullptr, vert_start, vert);
+    arcs_of_pair32<true>(M, p, nullptr, nullptr, vert_start, vert);
 }
 
 int launch_arcs(const Model &M, uint8_t *pair_free, int *vert_count, cudaStream_t st)
@@ -458,6 +644,60 @@ __global__ void k_bin_scatter(int n, const int *__restrict__ item_cell, const in
     int id = item_cell[p];
     if (id < 0) return;
     list[start[id] + atomicAdd(&cursor[id], 1)] = p;
+}
+
+__global__ void k_f32_atoms(Model M, double lx, double ly, double lz, float4 *__restrict__ hi, float4 *__restrict__ lo)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= M.n_atoms) return;
+    float hx, hy, hz, ex, ey, ez;
+    double4 a = M.atom[k];
+    split_df(a.x - lx, hx, ex);
+    split_df(a.y - ly, hy, ey);
+    split_df(a.z - lz, hz, ez);
+    hi[k] = make_float4(hx, hy, hz, (float)a.w);
+    lo[k] = make_float4(ex, ey, ez, 0.0f);
+}
+
+__global__ void k_f32_pairs(Model M, double lx, double ly, double lz, float4 *__restrict__ hi, float4 *__restrict__ lo,
+                            float4 *__restrict__ u32)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= M.n_pairs) return;
+    float hx, hy, hz, ex, ey, ez;
+    double4 o = M.pair_o[k];
+    double4 u = M.pair_u[k];
+    split_df(o.x - lx, hx, ex);
+    split_df(o.y - ly, hy, ey);
+    split_df(o.z - lz, hz, ez);
+    hi[k] = make_float4(hx, hy, hz, (float)o.w);
+    lo[k] = make_float4(ex, ey, ez, 0.0f);
+    u32[k] = make_float4((float)u.x, (float)u.y, (float)u.z, 0.0f);
+}
+
+__global__ void k_f32_verts(Model M, double lx, double ly, double lz, float4 *__restrict__ hi, float4 *__restrict__ lo)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= M.n_verts) return;
+    float hx, hy, hz, ex, ey, ez;
+    double4 v = M.vert[k];
+    split_df(v.x - lx, hx, ex);
+    split_df(v.y - ly, hy, ey);
+    split_df(v.z - lz, hz, ez);
+    hi[k] = make_float4(hx, hy, hz, 0.0f);
+    lo[k] = make_float4(ex, ey, ez, 0.0f);
+}
+
+// which: 0 atoms, 1 circles (centre and axis), 2 triple points
+int launch_model_f32(const Model &M, int which, const double lo[3], float4 *hi, float4 *lo_, float4 *u32,
+                     cudaStream_t st)
+{
+    int n = which == 0 ? M.n_atoms : (which == 1 ? M.n_pairs : M.n_verts);
+    if (n <= 0) return 0;
+    if (which == 0) k_f32_atoms<<<(n + 255) / 256, 256, 0, st>>>(M, lo[0], lo[1], lo[2], hi, lo_);
+    else if (which == 1) k_f32_pairs<<<(n + 255) / 256, 256, 0, st>>>(M, lo[0], lo[1], lo[2], hi, lo_, u32);
+    else k_f32_verts<<<(n + 255) / 256, 256, 0, st>>>(M, lo[0], lo[1], lo[2], hi, lo_);
+    return 1;
 }
 
 int launch_bin_count(const Model &M, int which, int *count, int *item_cell, cudaStream_t st)

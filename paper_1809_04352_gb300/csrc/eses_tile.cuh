@@ -58,6 +58,9 @@ struct TileS {
     uint8_t aface[A_MAX];   // expanded sphere keeps a free face
     int cid[STAGE_CELLS];           // cells of the staging range
     int cs[3][STAGE_CELLS + 1];     // prefix of their atoms / pairs / vertices
+    double fx0[3], fx1[3];          // tile region (absolute), computed once per tile
+    float fh0[3], fl0[3];           // region origin in the grid frame, double-float
+    int fc0[3], fnc[3];             // cell range of the region plus halo
     int na, np, nv, flags;
 };
 
@@ -138,46 +141,111 @@ __device__ __forceinline__ void tile_coords(const Grid &G, long long tile, int t
 }
 
 // Test one cell item against the region and append it (atoms, pairs, vertices).
-template <class T>
-__device__ __forceinline__ void stage_item(const Model &M, TileS<T> &S, int list, int k, const double *x0,
-                                           const double *x1)
+// FP64 staging: FP64 box test, FP64 difference to the tile origin, rounded
+// once.  FP32 staging: the double-float copies (hi + lo, grid frame); the box
+// test uses hi with a 1e-3 A margin, and the tile-frame coordinate is
+// (hi - x0_hi) + (lo - x0_lo), whose error is a rounding of the result only.
+struct StageFrame {
+    double x0[3], x1[3];   // region, absolute (FP64)
+    float h0[3], l0[3];    // region origin, grid frame, double-float
+    float b0[3], b1[3];    // region in the grid frame (hi parts), for FP32 box tests
+};
+
+__device__ __forceinline__ float box_dist2f(float x, float y, float z, const float *b0, const float *b1)
 {
-    const double tol = 1e-6;
+    float ex = x < b0[0] ? b0[0] - x : (x > b1[0] ? x - b1[0] : 0.0f);
+    float ey = y < b0[1] ? b0[1] - y : (y > b1[1] ? y - b1[1] : 0.0f);
+    float ez = z < b0[2] ? b0[2] - z : (z > b1[2] ? z - b1[2] : 0.0f);
+    return ex * ex + ey * ey + ez * ez;
+}
+
+template <class T>
+__device__ __forceinline__ void stage_item(const Model &M, TileS<T> &S, int list, int k, const StageFrame &F)
+{
     const double rp = M.rp;
-    if (list == 0) {
-        double4 a = M.atom[k];
-        double reach = a.w + 2.0 * rp + tol;
-        if (box_dist2(a.x, a.y, a.z, x0, x1) < reach * reach) {
-            int s = atomicAdd(&S.na, 1);
-            if (s < A_MAX) {
-                S.atom[s] = P4<T>{(T)(a.x - x0[0]), (T)(a.y - x0[1]), (T)(a.z - x0[2]), (T)a.w};
-                S.agid[s] = k;
-                S.aface[s] = M.atom_face[k];
+    if constexpr (sizeof(T) == sizeof(float)) {
+        const float rpf = (float)rp, tol = 1e-3f;
+        if (list == 0) {
+            float4 a = M.atom_hi[k];
+            float reach = a.w + 2.0f * rpf + tol;
+            if (box_dist2f(a.x, a.y, a.z, F.b0, F.b1) < reach * reach) {
+                int s = atomicAdd(&S.na, 1);
+                if (s < A_MAX) {
+                    float4 l = M.atom_lo[k];
+                    S.atom[s] = P4<T>{(a.x - F.h0[0]) + (l.x - F.l0[0]), (a.y - F.h0[1]) + (l.y - F.l0[1]),
+                                      (a.z - F.h0[2]) + (l.z - F.l0[2]), a.w};
+                    S.agid[s] = k;
+                    S.aface[s] = M.atom_face[k];
+                }
             }
-        }
-    } else if (list == 1) {
-        int p = M.pcell_list[k];
-        double4 o = M.pair_o[p];
-        double reach = o.w + rp + tol;
-        if (box_dist2(o.x, o.y, o.z, x0, x1) < reach * reach) {
-            int s = atomicAdd(&S.np, 1);
-            if (s < P_MAX) {
-                double4 u = M.pair_u[p];
-                S.po[s] = P4<T>{(T)(o.x - x0[0]), (T)(o.y - x0[1]), (T)(o.z - x0[2]), (T)o.w};
-                S.pu[s] = P4<T>{(T)u.x, (T)u.y, (T)u.z, (T)0};
-                S.pij[s] = M.pair_ij[p];
-                S.pidx[s] = p;
+        } else if (list == 1) {
+            int p = M.pcell_list[k];
+            float4 o = M.pair_hi[p];
+            float reach = o.w + rpf + tol;
+            if (box_dist2f(o.x, o.y, o.z, F.b0, F.b1) < reach * reach) {
+                int s = atomicAdd(&S.np, 1);
+                if (s < P_MAX) {
+                    float4 l = M.pair_lo[p];
+                    float4 u = M.pair_u32[p];
+                    S.po[s] = P4<T>{(o.x - F.h0[0]) + (l.x - F.l0[0]), (o.y - F.h0[1]) + (l.y - F.l0[1]),
+                                    (o.z - F.h0[2]) + (l.z - F.l0[2]), o.w};
+                    S.pu[s] = P4<T>{u.x, u.y, u.z, 0.0f};
+                    S.pij[s] = M.pair_ij[p];
+                    S.pidx[s] = p;
+                }
+            }
+        } else {
+            int v = M.vcell_list[k];
+            float4 q = M.vert_hi[v];
+            float reach = rpf + tol;
+            if (box_dist2f(q.x, q.y, q.z, F.b0, F.b1) < reach * reach) {
+                int s = atomicAdd(&S.nv, 1);
+                if (s < V_MAX) {
+                    float4 l = M.vert_lo[v];
+                    S.vq[s] = P4<T>{(q.x - F.h0[0]) + (l.x - F.l0[0]), (q.y - F.h0[1]) + (l.y - F.l0[1]),
+                                    (q.z - F.h0[2]) + (l.z - F.l0[2]), 0.0f};
+                    S.vidx[s] = v;
+                }
             }
         }
     } else {
-        int v = M.vcell_list[k];
-        double4 q = M.vert[v];
-        double reach = rp + tol;
-        if (box_dist2(q.x, q.y, q.z, x0, x1) < reach * reach) {
-            int s = atomicAdd(&S.nv, 1);
-            if (s < V_MAX) {
-                S.vq[s] = P4<T>{(T)(q.x - x0[0]), (T)(q.y - x0[1]), (T)(q.z - x0[2]), (T)0};
-                S.vidx[s] = v;
+        const double tol = 1e-6;
+        const double *x0 = F.x0, *x1 = F.x1;
+        if (list == 0) {
+            double4 a = M.atom[k];
+            double reach = a.w + 2.0 * rp + tol;
+            if (box_dist2(a.x, a.y, a.z, x0, x1) < reach * reach) {
+                int s = atomicAdd(&S.na, 1);
+                if (s < A_MAX) {
+                    S.atom[s] = P4<T>{(T)(a.x - x0[0]), (T)(a.y - x0[1]), (T)(a.z - x0[2]), (T)a.w};
+                    S.agid[s] = k;
+                    S.aface[s] = M.atom_face[k];
+                }
+            }
+        } else if (list == 1) {
+            int p = M.pcell_list[k];
+            double4 o = M.pair_o[p];
+            double reach = o.w + rp + tol;
+            if (box_dist2(o.x, o.y, o.z, x0, x1) < reach * reach) {
+                int s = atomicAdd(&S.np, 1);
+                if (s < P_MAX) {
+                    double4 u = M.pair_u[p];
+                    S.po[s] = P4<T>{(T)(o.x - x0[0]), (T)(o.y - x0[1]), (T)(o.z - x0[2]), (T)o.w};
+                    S.pu[s] = P4<T>{(T)u.x, (T)u.y, (T)u.z, (T)0};
+                    S.pij[s] = M.pair_ij[p];
+                    S.pidx[s] = p;
+                }
+            }
+        } else {
+            int v = M.vcell_list[k];
+            double4 q = M.vert[v];
+            double reach = rp + tol;
+            if (box_dist2(q.x, q.y, q.z, x0, x1) < reach * reach) {
+                int s = atomicAdd(&S.nv, 1);
+                if (s < V_MAX) {
+                    S.vq[s] = P4<T>{(T)(q.x - x0[0]), (T)(q.y - x0[1]), (T)(q.z - x0[2]), (T)0};
+                    S.vidx[s] = v;
+                }
             }
         }
     }
@@ -189,24 +257,36 @@ __device__ __forceinline__ void stage_item(const Model &M, TileS<T> &S, int list
 template <class T>
 __device__ void stage_tile(const Model &M, const Grid &G, long long tile, TileS<T> &S, double x0[3])
 {
-    int t[3];
-    tile_coords(G, tile, t);
-    double x1[3];
-    for (int a = 0; a < 3; ++a) {
-        x0[a] = G.lo[a] + G.h * (double)(TILE * t[a]);
-        x1[a] = x0[a] + G.h * (double)TILE;
-    }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0) {  // the tile frame, once per tile (FP64 arithmetic is scarce)
+        int t[3];
+        tile_coords(G, tile, t);
+        for (int a = 0; a < 3; ++a) {
+            const double rel = G.h * (double)(TILE * t[a]);  // region origin in the grid frame
+            S.fx0[a] = G.lo[a] + rel;
+            S.fx1[a] = S.fx0[a] + G.h * (double)TILE;
+            S.fh0[a] = (float)rel;
+            S.fl0[a] = (float)(rel - (double)S.fh0[a]);
+            S.fc0[a] = cell_coord_d(S.fx0[a] - G.halo, M.clo[a], M.cell, M.cn[a]);
+            S.fnc[a] = cell_coord_d(S.fx1[a] + G.halo, M.clo[a], M.cell, M.cn[a]) - S.fc0[a] + 1;
+        }
         S.na = 0;
         S.np = 0;
         S.nv = 0;
         S.flags = 0;
     }
-    int c0[3], c1[3], nc[3];
+    __syncthreads();
+    StageFrame F;
+    int c0[3], nc[3];
     for (int a = 0; a < 3; ++a) {
-        c0[a] = cell_coord_d(x0[a] - G.halo, M.clo[a], M.cell, M.cn[a]);
-        c1[a] = cell_coord_d(x1[a] + G.halo, M.clo[a], M.cell, M.cn[a]);
-        nc[a] = c1[a] - c0[a] + 1;
+        x0[a] = S.fx0[a];
+        F.x0[a] = S.fx0[a];
+        F.x1[a] = S.fx1[a];
+        F.h0[a] = S.fh0[a];
+        F.l0[a] = S.fl0[a];
+        F.b0[a] = F.h0[a];
+        F.b1[a] = F.h0[a] + G.ht_hi;
+        c0[a] = S.fc0[a];
+        nc[a] = S.fnc[a];
     }
     const int ncell = nc[0] * nc[1] * nc[2];
     if (ncell <= STAGE_CELLS) {
@@ -250,16 +330,16 @@ __device__ void stage_tile(const Model &M, const Grid &G, long long tile, TileS<
             int id = S.cid[lo];
             int off = k - cs[lo];
             int item = list == 0 ? M.cell_start[id] + off : (list == 1 ? M.pcell_start[id] + off : M.vcell_start[id] + off);
-            stage_item<T>(M, S, list, item, x0, x1);
+            stage_item<T>(M, S, list, item, F);
         }
     } else {
         __syncthreads();
         for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
             int cz = c % nc[2], cy = (c / nc[2]) % nc[1], cx = c / (nc[1] * nc[2]);
             int id = ((c0[0] + cx) * M.cn[1] + (c0[1] + cy)) * M.cn[2] + (c0[2] + cz);
-            for (int k = M.cell_start[id]; k < M.cell_start[id + 1]; ++k) stage_item<T>(M, S, 0, k, x0, x1);
-            for (int k = M.pcell_start[id]; k < M.pcell_start[id + 1]; ++k) stage_item<T>(M, S, 1, k, x0, x1);
-            for (int k = M.vcell_start[id]; k < M.vcell_start[id + 1]; ++k) stage_item<T>(M, S, 2, k, x0, x1);
+            for (int k = M.cell_start[id]; k < M.cell_start[id + 1]; ++k) stage_item<T>(M, S, 0, k, F);
+            for (int k = M.pcell_start[id]; k < M.pcell_start[id + 1]; ++k) stage_item<T>(M, S, 1, k, F);
+            for (int k = M.vcell_start[id]; k < M.vcell_start[id + 1]; ++k) stage_item<T>(M, S, 2, k, F);
         }
     }
     __syncthreads();

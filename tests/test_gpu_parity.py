@@ -238,3 +238,49 @@ def test_stage_times_reported():
     st = g["stages"]
     assert set(st) == set(eses.STAGE_NAMES)
     assert all(v >= 0.0 for v in st.values()) and st["classify"] > 0.0
+
+
+@pytest.mark.parametrize("wl_id", [1, 2])
+def test_patch_model_matches_oracle(wl_id):
+    """Circle pairs (saddle carriers) and free triple points (concave patch
+    centres, after the probe-clash test) equal the oracle's set exactly; the
+    triple points agree to 1e-9 A."""
+    from scipy.spatial import cKDTree
+
+    wl = inputs.WORKLOADS[wl_id]
+    xyz, rad = inputs.workload_atoms(wl_id)
+    ctx = eses.eses_create(xyz, rad, wl.r_p, wl.h, wl.margin)
+    try:
+        eses.eses_run(ctx)
+        pd = eses.eses_patch_data(ctx)
+    finally:
+        eses.eses_destroy(ctx)
+    npo, nvo, vo, po = oracle.model_stats(xyz, rad, wl.r_p, max_vertices=10 ** 6, max_pairs=10 ** 7)
+    gp = set(map(tuple, np.sort(pd["pair_atoms"], 1).tolist()))
+    op = set(map(tuple, np.sort(po, 1).tolist()))
+    assert gp == op
+    assert pd["vertices"].shape[0] == nvo
+    if nvo:
+        d, _ = cKDTree(pd["vertices"]).query(vo)
+        assert d.max() < 1e-9
+        d2, _ = cKDTree(vo).query(pd["vertices"])
+        assert d2.max() < 1e-9
+    # a pair flagged without a free arc has every sampled circle point covered
+    R = rad + wl.r_p
+    rng = np.random.default_rng(0)
+    for p in rng.choice(len(pd["pair_free"]), size=min(300, len(pd["pair_free"])), replace=False):
+        o, u, rho = pd["pair_circle"][p, :3], pd["pair_circle"][p, 3:6], pd["pair_circle"][p, 6]
+        t = np.array([1.0, 0, 0]) if abs(u[0]) < 0.6 else np.array([0, 1.0, 0])
+        v1 = np.cross(u, t)
+        v1 /= np.linalg.norm(v1)
+        v2 = np.cross(u, v1)
+        ph = np.linspace(0, 2 * np.pi, 2048, endpoint=False)
+        q = o + rho * (np.cos(ph)[:, None] * v1 + np.sin(ph)[:, None] * v2)
+        a_, b_ = pd["pair_atoms"][p]
+        near = np.where(np.linalg.norm(xyz - o, axis=1) < rho + R + 0.1)[0]
+        near = near[(near != a_) & (near != b_)]
+        free = np.all(np.linalg.norm(q[:, None, :] - xyz[near][None], axis=2) >= R[near][None], axis=1)
+        if not pd["pair_free"][p]:
+            assert not free.any()
+        elif free.mean() > 0.01:
+            assert pd["pair_free"][p]
