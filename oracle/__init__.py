@@ -79,6 +79,8 @@ def _load():
         lib.eo_num_threads.restype = ctypes.c_int
         lib.eo_flop_counts.argtypes = [P, P, i64, d, d, d, ctypes.c_int, P]
         lib.eo_flop_counts.restype = ctypes.c_int
+        lib.eo_edge_flop_counts.argtypes = [P, P, i64, d, d, d, P, P, ctypes.c_int, P]
+        lib.eo_edge_flop_counts.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -216,3 +218,36 @@ def model_stats(xyz, radii, r_p: float, max_vertices: int = 0, max_pairs: int = 
     verts = buf[: min(nv, max_vertices)] if max_vertices else None
     pairs = pbuf[: min(npr, max_pairs)] if max_pairs else None
     return npr, nv, verts, pairs
+
+
+FLOP_KEYS = ["points", "sum_reach", "shell_points", "sum_face", "sum_face_x_reach", "sum_arc", "sum_vert",
+             "model_flops"]
+
+
+def flop_counts(xyz, radii, r_p: float, h: float, margin: float, nthreads: int = 0) -> dict:
+    """Algorithmic flop model of the classification over the whole grid."""
+    lib = _load()
+    xyz, radii = _atoms(xyz, radii)
+    out = np.zeros(8, np.int64)
+    rc = lib.eo_flop_counts(_ptr(xyz), _ptr(radii), xyz.shape[0], r_p, h, margin, int(nthreads), _ptr(out))
+    if rc != 0:
+        raise ValueError("invalid parameters")
+    return dict(zip(FLOP_KEYS, (int(v) for v in out)))
+
+
+EDGE_FLOP_KEYS = ["edges", "vdw_spheres", "probe_spheres", "tori", "model_flops"]
+
+
+def edge_flop_counts(xyz, radii, r_p: float, h: float, margin: float, idx, nthreads: int = 0) -> dict:
+    """Edge terms of the flop model over the crossing edges idx (3 arrays of lower indices)."""
+    lib = _load()
+    xyz, radii = _atoms(xyz, radii)
+    arrs = [np.ascontiguousarray(a, dtype=np.int64) for a in idx]
+    ne = np.array([a.shape[0] for a in arrs], np.int64)
+    ptrs = (ctypes.c_void_p * 3)(*[a.ctypes.data for a in arrs])
+    out = np.zeros(5, np.int64)
+    rc = lib.eo_edge_flop_counts(_ptr(xyz), _ptr(radii), xyz.shape[0], r_p, h, margin, _ptr(ne),
+                                 ctypes.cast(ptrs, ctypes.c_void_p), int(nthreads), _ptr(out))
+    if rc != 0:
+        raise ValueError("invalid parameters")
+    return dict(zip(EDGE_FLOP_KEYS, (int(v) for v in out)))

@@ -911,3 +911,79 @@ int eo_flop_counts(const double *xyz, const double *r, int64_t n, double rp, dou
     out[7] = 8 * s_reach + 12 * s_face + 8 * s_fr + 30 * s_arc + 8 * s_vert;
     return 0;
 }
+
+/* Edge terms of the flop model, over given crossing edges (lower point
+ * linear index per axis): per edge, 20 flops per sphere-patch candidate (van
+ * der Waals sphere or probe sphere of a free triple point that the edge
+ * segment meets) and 150 per torus candidate (circle whose tube of radius r_p
+ * the segment meets: the distance to the circle takes r_p on the segment,
+ * judged on 33 samples with the 1-Lipschitz slack).
+ * out[0] = edges, out[1] = van der Waals spheres, out[2] = probe spheres,
+ * out[3] = tori, out[4] = model flops. */
+static double seg_dist2(const double *s, int axis, double h, const double *c)
+{
+    double t = c[axis] - s[axis];
+    if (t < 0.0) t = 0.0;
+    if (t > h) t = h;
+    double y[3] = {s[0], s[1], s[2]};
+    y[axis] += t;
+    return dist2(y, c);
+}
+
+int eo_edge_flop_counts(const double *xyz, const double *r, int64_t n, double rp, double h, double margin,
+                        const int64_t *n_edges, const int64_t *const *idx, int nthreads, int64_t *out)
+{
+    int64_t dims[3];
+    double lo[3];
+    if (eo_grid(xyz, r, n, h, margin, dims, lo) != 0) return -1;
+    Model m;
+    model_build(&m, xyz, r, NULL, (int)n, rp, rp + h, 0);
+    int64_t s_e = 0, s_v = 0, s_p = 0, s_t = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    for (int axis = 0; axis < 3; ++axis) {
+        const int64_t ne = n_edges[axis];
+        const int64_t *ix = idx[axis];
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : s_e, s_v, s_p, s_t)
+#endif
+        for (int64_t e = 0; e < ne; ++e) {
+            int64_t g = ix[e];
+            int64_t gi = g / (dims[1] * dims[2]), gj = (g / dims[2]) % dims[1], gk = g % dims[2];
+            double s[3] = {lo[0] + h * (double)gi, lo[1] + h * (double)gj, lo[2] + h * (double)gk};
+            double mid[3] = {s[0], s[1], s[2]};
+            mid[axis] += 0.5 * h;
+            s_e++;
+            FOR_NEAR(&m, mid, m.a_start, m.a_list, m.n, a, {
+                if (seg_dist2(s, axis, h, m.c + 3 * a) < m.r[a] * m.r[a]) s_v++;
+            });
+            FOR_NEAR(&m, mid, m.v_start, m.v_list, m.nv, v, {
+                if (seg_dist2(s, axis, h, m.vq + 3 * v) < rp * rp) s_p++;
+            });
+            FOR_NEAR(&m, mid, m.p_start, m.p_list, m.np, p, {
+                const double *o = m.po + 3 * p, *u = m.pu + 3 * p;
+                double dmin = 1e300, dmax = -1e300;
+                for (int k = 0; k <= 32; ++k) {
+                    double y[3] = {s[0] - o[0], s[1] - o[1], s[2] - o[2]};
+                    y[axis] += h * (double)k / 32.0;
+                    double z = dot3(y, u);
+                    double w2 = dot3(y, y) - z * z;
+                    double ee = sqrt(w2 > 0.0 ? w2 : 0.0) - m.prho[p];
+                    double d = sqrt(ee * ee + z * z);
+                    if (d < dmin) dmin = d;
+                    if (d > dmax) dmax = d;
+                }
+                double slack = h / 64.0;
+                if (dmin - slack <= rp && dmax + slack >= rp) s_t++;
+            });
+        }
+    }
+    model_free(&m);
+    out[0] = s_e;
+    out[1] = s_v;
+    out[2] = s_p;
+    out[3] = s_t;
+    out[4] = 20 * (s_v + s_p) + 150 * s_t;
+    return 0;
+}

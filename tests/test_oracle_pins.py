@@ -260,3 +260,61 @@ def test_appendix_block_counts():
     for g in rows:
         for a in range(3):
             assert oracle.block_count(g[a], 64) == g[3 + a], g
+
+
+def test_flop_model_counts_single_atom_brute_force():
+    """The flop model's counters (the roofline's algorithmic work) on one
+    atom, against brute force over the grid: reach = points within r + 2 r_p,
+    shell = points in r <= |x - c| < r + r_p (one face candidate each, no arc
+    or vertex), and every crossing edge meets exactly the van der Waals
+    sphere (no probe sphere, no torus)."""
+    c = np.array([[0.13, -0.21, 0.07]])
+    r = np.array([1.7])
+    h, margin = 0.25, 0.8
+    fc = oracle.flop_counts(c, r, RP, h, margin)
+    res = oracle.run(c, r, RP, h, margin)
+    d = np.linalg.norm(_all_points(res) - c[0], axis=1)
+    reach = int(np.count_nonzero(d < r[0] + 2 * RP))
+    shell = int(np.count_nonzero((d >= r[0]) & (d < r[0] + RP)))
+    assert fc["points"] == int(np.prod(res.dims))
+    assert fc["sum_reach"] == reach
+    assert fc["shell_points"] == shell and fc["sum_face"] == shell and fc["sum_face_x_reach"] == shell
+    assert fc["sum_arc"] == 0 and fc["sum_vert"] == 0
+    assert fc["model_flops"] == 8 * reach + 12 * shell + 8 * shell
+    ec = oracle.edge_flop_counts(c, r, RP, h, margin, res.idx)
+    ne = sum(int(a.shape[0]) for a in res.idx)
+    assert ne > 0 and ec["edges"] == ne and ec["vdw_spheres"] == ne
+    assert ec["probe_spheres"] == 0 and ec["tori"] == 0 and ec["model_flops"] == 20 * ne
+
+
+def test_flop_model_edge_tori_two_atoms():
+    """Two overlapping atoms: the edges that cross the saddle (torus) part of
+    the surface count the pair's torus; brute force over 257 points of each
+    edge segment decides which edges come within r_p of the circle."""
+    c = np.array([[0.0, 0.0, 0.0], [2.6, 0.3, -0.2]])
+    r = np.array([1.7, 1.52])
+    h, margin = 0.25, 0.8
+    res = oracle.run(c, r, RP, h, margin)
+    ec = oracle.edge_flop_counts(c, r, RP, h, margin, res.idx)
+    R = r + RP
+    D = np.linalg.norm(c[1] - c[0])
+    u = (c[1] - c[0]) / D
+    aa = (D * D + R[0] ** 2 - R[1] ** 2) / (2 * D)
+    o = c[0] + aa * u
+    rho = math.sqrt(R[0] ** 2 - aa * aa)
+    sure = maybe = 0
+    for ax in range(3):
+        p0 = _grid_points(res, res.idx[ax])
+        t = np.linspace(0.0, h, 257)
+        y = p0[:, None, :] + t[None, :, None] * np.eye(3)[ax][None, None, :] - o
+        z = y @ u
+        w = np.sqrt(np.maximum((y * y).sum(-1) - z * z, 0.0))
+        dist = np.sqrt((w - rho) ** 2 + z * z)
+        lo, hi = dist.min(1), dist.max(1)
+        # the counter's sampled meet test with its Lipschitz slack lies
+        # between the edges that surely meet the tube and those that may
+        sure += int(np.count_nonzero((lo <= RP) & (hi >= RP)))
+        maybe += int(np.count_nonzero((lo - h / 64 <= RP) & (hi + h / 64 >= RP)))
+    assert sure > 0
+    assert sure <= ec["tori"] <= maybe
+    assert ec["model_flops"] == 20 * (ec["vdw_spheres"] + ec["probe_spheres"]) + 150 * ec["tori"]
