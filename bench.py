@@ -11,8 +11,9 @@ point, crossing edges, roots and normals, area and volume.
   e2e        points/s through the public C ABI with host buffers: create from
              pinned host atoms, run, copy labels and intersections back
   plain_fp64 the same step with every stage in FP64 (the plain GPU form)
-  roofline   the classification kernel against the FP32 ALU peak, with the
-             algorithmic flops of the oracle-counted flop model
+  roofline   the dominant kernel (by event-timed duration; the other heavy
+             kernel beside it) against the FP32 ALU peak, with the algorithmic
+             flops of the oracle-counted flop model
   cpu_baseline  the FP64 CPU oracle on a seeded sample of blocks, all cores
 
 --impl reference times the oracle (the reference arm of this build) on the
@@ -307,15 +308,26 @@ def main():
     fp32_peak = N_SM * FP32_LANES * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
     with open(os.path.join(ROOT, "tests", "golden", "flop_model.json")) as f:
         fm = json.load(f)[wl.name]
-    flops = fm["flops_per_point"] * npts
-    t_cls = stage_ms["classify"] / 1e3
-    achieved = flops / t_cls / 1e12
-    roofline = {"bound": "alu", "kernel": "k_classify<float,true> (FP32-filtered classification)",
-                "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                "traffic": None,
-                "peak_source": f"derived: {N_SM} SMs x {FP32_LANES} FP32 lanes x 2 flops x {sm_max:.0f} MHz "
-                               f"(sm_max_mhz {psrc})",
-                "flops_per_point": fm["flops_per_point"], "kernel_ms": stage_ms["classify"]}
+    psrc_txt = f"derived: {N_SM} SMs x {FP32_LANES} FP32 lanes x 2 flops x {sm_max:.0f} MHz (sm_max_mhz {psrc})"
+    # algorithmic flops per launch (oracle-counted flop model) and the kernel's
+    # mean event-timed duration over the timed steps
+    kernels = {
+        "classify": ("k_classify<float,true> (FP32-filtered classification, every grid point)",
+                     fm["model_flops"], stage_ms["classify"],
+                     {"flops_per_point": fm["flops_per_point"]}),
+        "edge_solve": ("k_edge_solve<float,true> (first root and its patch, one warp per crossing edge)",
+                       fm["edge_counts"]["model_flops"], stage_ms["edge_solve"],
+                       {"flops_per_edge": fm["edge_flops_per_edge"], "edges": fm["edge_counts"]["edges"]}),
+    }
+    rl = {}
+    for name, (kname, flops, ms, extra) in kernels.items():
+        achieved = flops / (ms / 1e3) / 1e12
+        rl[name] = dict({"bound": "alu", "kernel": kname, "achieved": achieved, "peak": fp32_peak,
+                         "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                         "peak_source": psrc_txt, "flops_per_launch": flops, "kernel_ms": ms}, **extra)
+    dominant = max(rl, key=lambda k: rl[k]["kernel_ms"])
+    roofline = rl[dominant]
+    roofline_others = {k: v for k, v in rl.items() if k != dominant}
 
     # ---- CPU baseline (rank 0, N = 1) ---------------------------------------
     cpu = None
@@ -333,6 +345,7 @@ def main():
                         "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s / args.steps},
                 "gpu_launches": int(st["kernel_launches"]) * args.steps,
                 "roofline": roofline,
+                "roofline_other_kernels": roofline_others,
                 "cpu_baseline": cpu,
                 "clocks": clk,
                 "plain_fp64": {"value": all_pts / (plain_ms / 1e3), "unit": UNIT, "ms_per_step": plain_ms,

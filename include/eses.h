@@ -133,8 +133,9 @@ int eses_stats(const eses_ctx *ctx, int64_t *out, int n);
  * host output of up to n values: [0] cell binning, [1] neighbours and circle
  * pairs, [2] free arcs, triple points and patch bins, [3] classification,
  * [4] FP64 band re-evaluation, [5] crossing-edge counts and offsets,
- * [6] root solve and normals, [7] area/volume reduction.  Stages that wait
- * for a host read of a list total include that wait. */
+ * [6] root solve (first root and its patch per crossing edge), [7] FP64 root
+ * polish, normals and area/volume terms, [8] area/volume reduction.  Stages
+ * that wait for a host read of a list total include that wait. */
 int eses_stage_times(const eses_ctx *ctx, double *ms, int n);
 
 /* Records of crossing edges whose root solve failed in the last run (at most

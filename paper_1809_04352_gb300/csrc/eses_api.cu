@@ -19,7 +19,7 @@ using namespace eses;
 
 // stages timed with CUDA events when ESES_OPT_PROFILE is set
 enum { NSTAT = 11 };
-enum { ST_BIN = 0, ST_PAIRS, ST_ARCS, ST_CLASSIFY, ST_BAND, ST_EDGE_COUNT, ST_EDGE_SOLVE, ST_REDUCE, NSTAGE };
+enum { ST_BIN = 0, ST_PAIRS, ST_ARCS, ST_CLASSIFY, ST_BAND, ST_EDGE_COUNT, ST_EDGE_SOLVE, ST_EDGE_POLISH, ST_REDUCE, NSTAGE };
 
 namespace {
 
@@ -428,7 +428,9 @@ int run_impl(eses_ctx *c)
     double *part = ensure<double>(c->tile_area, 2 * std::max(nparts, 1LL));
     mark(c, ST_EDGE_SOLVE);
     long long *fail_log = ensure<long long>(c->fail_log, FAIL_LOG * FAIL_REC);
-    nl += launch_edge_solve(M, G, c->precision, labels, edge_start, eo, c->n_edges, part, d_fail, d_err, fail_log, st);
+    nl += launch_edge_solve(M, G, c->precision, labels, edge_start, eo, d_fail, d_err, fail_log, st);
+    mark(c, ST_EDGE_POLISH);
+    nl += launch_edge_polish(M, G, eo, c->n_edges, part, st);
     mark(c, ST_REDUCE);
     nl += launch_reduce(G, part, nparts, tile_inside, d_av, d_counts, st);
     mark(c, NSTAGE);

@@ -37,7 +37,10 @@ namespace eses {
 
 constexpr int EDGE_THREADS = 256;
 constexpr int EDGE_WARPS = EDGE_THREADS / 32;
-constexpr int WCAND = 64;        // candidate roots per warp
+constexpr int WCAND = 64;        // candidate roots of one edge in the selection buffer
+constexpr int CHUNK = 64;        // edges per chunk of the pooled root solve
+constexpr int POOL_MAX = 2048;   // (edge, item) pairs of a chunk that pass the prefilter
+constexpr int ROOT_MAX = 512;    // valid roots of a chunk
 constexpr int POLISH_THREADS = 256;
 
 // --------------------------------------------------------------------------
@@ -87,7 +90,7 @@ __device__ R mono_root(const R *c, R a, R b, R fa)
 // one root, found by safeguarded Newton-bisection
 template <class R, int DEG>
 struct PolyRoots {
-    __device__ static int run(const R *c, R lo, R hi, R *out)
+    __device__ static __noinline__ int run(const R *c, R lo, R hi, R *out)
     {
         R dc[DEG];
 #pragma unroll
@@ -189,7 +192,7 @@ __device__ __forceinline__ void torus_coeffs(const double *o, const double *u, d
 
 // four FP64 Newton steps on the torus quartic from t0 (the FP32 root is within
 // 1e-3 A and the root simple, else the warp solve already took it in FP64)
-__device__ __forceinline__ double exact_root_torus(const double *o, const double *u, double rho, double rp,
+__device__ __noinline__ double exact_root_torus(const double *o, const double *u, double rho, double rp,
                                                    const double *s, int axis, double t0)
 {
     double co[5];
@@ -231,7 +234,7 @@ __device__ __forceinline__ void exact_normal(int kind, const double *c, const do
 
 // exact root of a staged piece (tile frame, FP64 data from HBM) near t0
 template <class TS>
-__device__ __forceinline__ double staged_exact_root(const ExactAcc<TS> &X, int kind, int slot, const double *s,
+__device__ __noinline__ double staged_exact_root(const ExactAcc<TS> &X, int kind, int slot, const double *s,
                                                     int axis, double rp, double t0)
 {
     if (kind == 0) {
@@ -251,7 +254,7 @@ __device__ __forceinline__ double staged_exact_root(const ExactAcc<TS> &X, int k
 }
 
 // --------------------------------------------------------------------------
-// one warp per edge
+// root candidates of a tile's crossing edges, pooled over the block
 // --------------------------------------------------------------------------
 struct WCand {
     double t64;    // exact root once computed (NaN before)
@@ -266,21 +269,45 @@ struct EdgeSmem {
     int estart[4];
     long long ebase[3];
     int sh[EDGE_WARPS];
+    // the current chunk of edges [c0, c0 + CHUNK): (edge, item) pairs that pass
+    // the prefilter, then the roots they give (valid pieces only)
+    int npool, nroot;
+    unsigned pool[POOL_MAX];  // (edge << 16) | item
+    WCand root[ROOT_MAX];
+    short redge[ROOT_MAX];
+    short rorder[ROOT_MAX];   // roots grouped by edge
+    int rstart[CHUNK + 1];
+    int rfill[CHUNK];
+    // per-warp selection buffer
     WCand cand[EDGE_WARPS][WCAND];
     int ncand[EDGE_WARPS];
 };
 
-__device__ __forceinline__ void warp_push(EdgeSmem &E, int warp, float t, float err, double t64, int kind, int id)
+__device__ __forceinline__ void pool_push(EdgeSmem &E, int e, float t, float err, double t64, int kind, int id)
 {
-    int slot = atomicAdd(&E.ncand[warp], 1);
-    if (slot < WCAND) {
-        WCand &c = E.cand[warp][slot];
+    int slot = atomicAdd(&E.nroot, 1);
+    if (slot < ROOT_MAX) {
+        WCand &c = E.root[slot];
         c.t = t;
         c.err = err;
         c.t64 = t64;
         c.kind = kind;
         c.id = id;
+        E.redge[slot] = (short)e;
     }
+}
+
+// axis, lower point (local index) and its label of crossing edge e of the tile
+struct EdgeRef {
+    int axis, p, lab;
+};
+__device__ __forceinline__ EdgeRef edge_ref(const EdgeSmem &E, int e)
+{
+    EdgeRef r;
+    r.axis = e < E.estart[1] ? 0 : (e < E.estart[2] ? 1 : 2);
+    r.p = E.eptr[e];
+    r.lab = E.lab[((r.p >> 6) * 9 + ((r.p >> 3) & 7)) * 9 + (r.p & 7)];
+    return r;
 }
 
 // index of the smallest key (ties: smaller index), -1 if every key is +inf
@@ -312,194 +339,353 @@ __device__ __forceinline__ int warp_argmin(const WCand *c, int n)
     return warp_argmin_key(bt, bk);
 }
 
-// Candidates of one crossing edge, then the first root.  Returns 0 with the
-// chosen piece (kind, staged slot) and its FP32 root, 1 when no root is
-// found, 2 when the candidate buffer overflowed (the first WCAND are used).
-template <class T, bool FILT>
-__device__ int warp_edge(const Model &M, const TileS<T> &S, const double *x0, EdgeSmem &E, int warp, int axis, int p,
-                         int lab_s, double h, double rp, T d0, float &t_out, int &kind_out, int &slot_out)
+// --------------------------------------------------------------------------
+// torus pieces: near-branch roots of g(t) = D(t) - r_p, D the distance from
+// y(t) = q0 + t e_axis to the circle (centre at the frame origin, axis u,
+// radius rho).  These are the roots of the quartic whose nearest circle point
+// is the witness.
+// --------------------------------------------------------------------------
+// D, dD/dt, the distance |w| to the circle's axis, |y|^2, z = y.u and w at t
+__device__ __forceinline__ void circle_dist32(const float *q0, const float *u, float rho, int axis, float t, float &D,
+                                              float &dD, float &nw, float &yy, float &z, float *w)
 {
-    const int lane = threadIdx.x & 31;
-    const int li = p >> 6, lj = (p >> 3) & 7, lk = p & 7;
-    const double s64[3] = {E.hd[li], E.hd[lj], E.hd[lk]};
+    float y0 = q0[0], y1 = q0[1], y2 = q0[2];
+    if (axis == 0) y0 += t;
+    else if (axis == 1) y1 += t;
+    else y2 += t;
+    z = y0 * u[0] + y1 * u[1] + y2 * u[2];
+    yy = y0 * y0 + y1 * y1 + y2 * y2;
+    w[0] = y0 - z * u[0];
+    w[1] = y1 - z * u[1];
+    w[2] = y2 - z * u[2];
+    nw = sqrtf(fmaxf(yy - z * z, 0.0f));
+    const float e = nw - rho;
+    D = sqrtf(e * e + z * z);
+    const float wa = axis == 0 ? w[0] : (axis == 1 ? w[1] : w[2]);
+    dD = (nw > 0.0f && D > 0.0f) ? (e * wa / nw + z * u[axis]) / D : 0.0f;
+}
+
+// error bound of the FP32 D: staged positions (d0) and rounding of |y|^2 - z^2
+// (relative 2^-24 per operation, amplified by |y|^2 / |w| in |w|)
+__device__ __forceinline__ float circle_dist_err(float d0, float yy, float nw, float rho, float rp)
+{
+    return 2.0f * d0 + 4e-7f * (yy / fmaxf(nw, 1e-3f) + sqrtf(yy) + rho + rp);
+}
+
+// Certified FP32 isolation of the roots of g on [lo, hi].  g is 1-Lipschitz
+// and |g''| <= C = max(1/D, 1/|w|) (the distance to a circle has Hessian
+// eigenvalues 0 and 1/D in the meridian plane and (dD/d|w|)/|w| around the
+// axis; D and |w| are 1-Lipschitz too, so on a sub-interval of length l they
+// stay above their smaller end value minus l/2).  On 8 sub-intervals: none
+// holds a root when |g| at its ends adds up to more than its length; g' keeps
+// its sign when g' has the same sign at both ends and |g'| there adds up to
+// more than C l, and then the sub-interval holds one root if g changes sign,
+// else none.  Each root is refined by Newton from the secant point inside its
+// bracket.  Returns false when a sign or the monotonicity cannot be decided.
+__device__ __noinline__ bool torus_roots32(const float *q0, const float *u, float rho, float rp, int axis, float lo,
+                                           float hi, float d0, float *rt, int &nr)
+{
+    constexpr int K = 8;
+    const float dl = (hi - lo) / (float)K;
+    float g[K + 1], dg[K + 1], eg[K + 1], mw[K + 1];
+#pragma unroll 1
+    for (int k = 0; k <= K; ++k) {
+        const float t = k == K ? hi : lo + (float)k * dl;
+        float D, dD, nw, yy, z, w[3];
+        circle_dist32(q0, u, rho, axis, t, D, dD, nw, yy, z, w);
+        g[k] = D - rp;
+        dg[k] = dD;
+        eg[k] = circle_dist_err(d0, yy, nw, rho, rp);
+        mw[k] = fminf(D, nw);
+    }
+    nr = 0;
+#pragma unroll 1
+    for (int k = 0; k < K; ++k) {
+        const float ga = g[k], gb = g[k + 1];
+        const bool sc = (ga <= 0.0f) != (gb <= 0.0f);
+        if (!sc && fabsf(ga) + fabsf(gb) > dl + eg[k] + eg[k + 1]) continue;
+        if (fabsf(ga) <= eg[k] || fabsf(gb) <= eg[k + 1]) return false;
+        const float low = fminf(mw[k], mw[k + 1]) - 0.5f * dl;
+        if (!(low > 1e-2f)) return false;
+        const bool mono = (dg[k] > 0.0f) == (dg[k + 1] > 0.0f) && fabsf(dg[k]) + fabsf(dg[k + 1]) > dl / low + 2e-4f;
+        if (!mono) return false;
+        if (!sc) continue;
+        if (nr == 4) return false;
+        float a = lo + (float)k * dl, b = k + 1 == K ? hi : lo + (float)(k + 1) * dl;
+        float t = a + (b - a) * (ga / (ga - gb));
+        for (int itn = 0; itn < 5; ++itn) {  // Newton, bisection when it leaves the bracket
+            float D, dD, nw, yy, z, w[3];
+            circle_dist32(q0, u, rho, axis, t, D, dD, nw, yy, z, w);
+            const float f = D - rp;
+            if (f == 0.0f) break;
+            if ((f <= 0.0f) == (ga <= 0.0f)) a = t;
+            else b = t;
+            float tn = dD != 0.0f ? t - f / dD : 0.5f * (a + b);
+            if (!(tn > a && tn < b)) tn = 0.5f * (a + b);
+            t = tn;
+        }
+        rt[nr++] = t;
+    }
+    return true;
+}
+
+// One FP64 root t64 of a torus piece: kept if it lies on the near branch in
+// [0, h], its witness distance crosses r_p in the direction that leaves the
+// end point's side, and its witness (nearest circle point) is free.
+template <class Acc>
+__device__ __noinline__ void torus_root_exact(const Acc &X, EdgeSmem &E, int e, int pi, const double *s64, int axis,
+                                              double h, double rp, bool inside, double t64)
+{
+    if (!(t64 >= 0.0 && t64 <= h)) return;
+    const P4<double> oe = X.po(pi);
+    const P4<double> ue = X.pu(pi);
+    const double oo[3] = {oe.x, oe.y, oe.z}, u64[3] = {ue.x, ue.y, ue.z};
+    double yd[3] = {s64[0] - oo[0], s64[1] - oo[1], s64[2] - oo[2]};
+    yd[axis] += t64;
+    const double Ad = yd[0] * yd[0] + yd[1] * yd[1] + yd[2] * yd[2] + oe.w * oe.w - rp * rp;
+    const double zd = yd[0] * u64[0] + yd[1] * u64[1] + yd[2] * u64[2];
+    const double wd[3] = {yd[0] - zd * u64[0], yd[1] - zd * u64[1], yd[2] - zd * u64[2]};
+    const double nwd = sqrt(wd[0] * wd[0] + wd[1] * wd[1] + wd[2] * wd[2]);
+    const double near2 = (nwd - oe.w) * (nwd - oe.w) + zd * zd;
+    if (fabs(near2 - rp * rp) > 1e-7 * rp * rp || !(nwd > 0.0) || !(Ad >= 0.0)) return;
+    const double rd = ((nwd - oe.w) * wd[axis] / nwd + zd * u64[axis]) / rp;
+    const double rate = fabs(rd) <= 1e-9 ? 0.0 : rd;
+    if (inside ? rate > 0.0 : rate < 0.0) return;
+    const int2 ij = X.pij(pi);
+    const double k64 = oe.w / nwd;
+    const int f = free_pt<false>(X, oo[0] + k64 * wd[0], oo[1] + k64 * wd[1], oo[2] + k64 * wd[2], ij.x, ij.y, rp, 0.0);
+    if (f == 1) pool_push(E, e, (float)t64, 0.0f, t64, 1, pi);
+}
+
+// Every root of a torus piece in [0, h] from the quartic, each decided in FP64.
+template <class Acc>
+__device__ __noinline__ void torus_piece_exact(const Acc &X, EdgeSmem &E, int e, int pi, const double *s64, int axis,
+                                               double h, double rp, bool inside)
+{
+    const P4<double> oe = X.po(pi);
+    const P4<double> ue = X.pu(pi);
+    const double oo[3] = {oe.x, oe.y, oe.z}, u64[3] = {ue.x, ue.y, ue.z};
+    double co[5], r64[4];
+    torus_coeffs(oo, u64, oe.w, rp, s64, axis, co);
+    const int n = PolyRoots<double, 4>::run(co, 0.0, h, r64);
+    for (int k = 0; k < n; ++k) torus_root_exact(X, E, e, pi, s64, axis, h, rp, inside, r64[k]);
+}
+
+// Can item `it` (staged atom, vertex or pair, in that order) put a root on the
+// edge from s along axis?  Spheres |y - c| = rad: only if the distance from c
+// to the segment takes the value rad (its minimum and maximum over the
+// segment bracket rad); tori: the 1-Lipschitz distance to the circle is
+// within h/2 of r_p at the edge's midpoint.  mg widens both for FP32.
+template <class T>
+__device__ __forceinline__ bool cand_test(const TileS<T> &S, const T *s, int axis, int it, T hT, T rpT, T mg)
+{
+    const int na = S.na, nv = S.nv;
+    if (it < na + nv) {
+        const P4<T> c = it < na ? S.atom[it] : S.vq[it - na];
+        const T rad = it < na ? c.w : rpT;
+        const T d0 = s[0] - c.x, d1 = s[1] - c.y, d2 = s[2] - c.z;
+        const T dd = d0 * d0 + d1 * d1 + d2 * d2;
+        const T da = axis == 0 ? d0 : (axis == 1 ? d1 : d2);
+        const T tc = fmin(fmax(-da, T(0)), hT);         // nearest point of the segment
+        const T dmin2 = dd + tc * (tc + T(2) * da);
+        const T dmax2 = dd + fmax(T(0), hT * (hT + T(2) * da));
+        const T rhi = rad + mg, rlo = fmax(rad - mg, T(0));
+        return dmin2 <= rhi * rhi && dmax2 >= rlo * rlo;
+    }
+    const int pi = it - na - nv;
+    const P4<T> o = S.po[pi];
+    const P4<T> u = S.pu[pi];
+    T m[3] = {s[0] - o.x, s[1] - o.y, s[2] - o.z};
+    m[axis] += T(0.5) * hT;
+    const T zc = m[0] * u.x + m[1] * u.y + m[2] * u.z;
+    const T w2 = fmax(m[0] * m[0] + m[1] * m[1] + m[2] * m[2] - zc * zc, T(0));
+    const T e1 = sqrt(w2) - o.w;
+    const T gm = sqrt(e1 * e1 + zc * zc) - rpT;
+    return fabs(gm) <= T(0.5) * hT + mg;
+}
+
+// Roots of one (edge, item) pair that can be the surface on that edge: every
+// root in [0, h] of the piece whose witness distance crosses r_p in the
+// direction that leaves the end point's side (falling from an inside end,
+// rising from an outside end) and whose witness is free.  FP32 roots carry
+// an error bound; a decision the bound cannot make goes to FP64.
+template <class T, bool FILT>
+__device__ void cand_roots(const Model &M, const TileS<T> &S, const double *x0, EdgeSmem &E, int e, int it, double h,
+                           double rp, T d0)
+{
+    const EdgeRef R = edge_ref(E, e);
+    const int axis = R.axis;
+    const double s64[3] = {E.hd[R.p >> 6], E.hd[(R.p >> 3) & 7], E.hd[R.p & 7]};
     const T s[3] = {(T)s64[0], (T)s64[1], (T)s64[2]};
     SmemAcc<T> A(S);
     ExactAcc<T> X(S, M, x0);
-    if (lane == 0) E.ncand[warp] = 0;
-    __syncwarp();
-    const int na = S.na, nv = S.nv, np = S.np;
+    const int na = S.na, nv = S.nv;
     const T hT = (T)h, rpT = (T)rp;
-    const T mg = FILT ? T(2e-3) : T(0);        // margin of the FP32 prefilters (A)
     const T lo = FILT ? T(-1e-4) : T(0), hi = hT + (FILT ? T(1e-4) : T(0));
-    const T tmax = T(1e-3);                    // FP32 root error beyond which FP64 decides (grazing pieces)
-    const float tie = 1e-6f * (float)h;         // FP32 rounding of a root
-    const bool inside = lab_s == LABEL_IN;
+    const T tmax = T(1e-3);  // FP32 root error beyond which FP64 decides (grazing pieces)
+    const bool inside = R.lab == LABEL_IN;
     const double NaN = __longlong_as_double(0x7ff8000000000000LL);
-    for (int it = lane; it < na + nv + np; it += 32) {
-        if (it < na + nv) {  // spheres: convex (van der Waals, witness = projection) or concave (probe)
-            const bool vdw = it < na;
-            const int slot = vdw ? it : it - na;
-            P4<T> c = vdw ? S.atom[slot] : S.vq[slot];
-            const T rad = vdw ? c.w : rpT;
-            T d[3] = {s[0] - c.x, s[1] - c.y, s[2] - c.z};
-            T dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-            T reach = rad + hT + mg;
-            if (dd > reach * reach) continue;
-            T b = d[axis], disc = b * b - (dd - rad * rad);
-            if (disc < -mg) continue;
-            T co32[3] = {dd - rad * rad, T(2) * b, T(1)};
-            T rt32[2];
-            int nr = PolyRoots<T, 2>::run(co32, lo, hi, rt32);
-            if (FILT && nr == 0 && disc < mg) {  // grazing: let FP64 decide
-                rt32[0] = -b;
-                nr = (-b >= lo && -b <= hi) ? 1 : 0;
+    if (it < na + nv) {  // spheres: convex (van der Waals, witness = projection) or concave (probe)
+        const bool vdw = it < na;
+        const int slot = vdw ? it : it - na;
+        P4<T> c = vdw ? S.atom[slot] : S.vq[slot];
+        const T rad = vdw ? c.w : rpT;
+        T d[3] = {s[0] - c.x, s[1] - c.y, s[2] - c.z};
+        T dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        T b = d[axis], disc = b * b - (dd - rad * rad);
+        T co32[3] = {dd - rad * rad, T(2) * b, T(1)};
+        T rt32[2];
+        int nr = PolyRoots<T, 2>::run(co32, lo, hi, rt32);
+        if (FILT && nr == 0 && disc < T(2e-3)) {  // grazing: let FP64 decide
+            rt32[0] = -b;
+            nr = (-b >= lo && -b <= hi) ? 1 : 0;
+        }
+        for (int k = 0; k < nr; ++k) {
+            T t = rt32[k];
+            T vA = d[axis] + t;  // +-sqrt(disc) at a root: the rate of |y - c|
+            T terr = T(0);
+            if (FILT) {
+                T derr = T(2) * (fabs(b) + sqrt(dd)) * d0 + T(2e-6) * (dd + rad * rad);
+                terr = d0 + derr / (T(2) * fmax(fabs(vA), T(1e-20)));
             }
-            for (int k = 0; k < nr; ++k) {
-                T t = rt32[k];
-                T vA = d[axis] + t;  // +-sqrt(disc) at a root: the rate of |y - c|
-                T terr = T(0);
-                if (FILT) {
-                    T derr = T(2) * (fabs(b) + sqrt(dd)) * d0 + T(2e-6) * (dd + rad * rad);
-                    terr = d0 + derr / (T(2) * fmax(fabs(vA), T(1e-20)));
-                }
-                double t64 = NaN;
-                bool exact = FILT && (terr > tmax || t < terr + T(1e-6) || t > hT - terr - T(1e-6));
-                if (exact) {
-                    P4<double> ce = vdw ? X.atom(slot) : X.vq(slot);
-                    double cc[3] = {ce.x, ce.y, ce.z};
-                    double r64 = vdw ? ce.w : rp;
-                    t64 = exact_root_sphere(cc, r64, s64, axis, (double)t);
-                    double dv[3] = {s64[0] - cc[0], s64[1] - cc[1], s64[2] - cc[2]};
-                    dv[axis] += t64;
-                    double f = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2] - r64 * r64;
-                    if (!(t64 >= 0.0 && t64 <= h) || fabs(f) > 1e-9 * r64) continue;
-                    vA = (T)dv[axis];
-                    if (fabs(dv[axis]) <= 1e-9 * r64) vA = T(0);  // tangent: either way
-                    t = (T)t64;
-                    terr = T(0);
-                }
-                // witness distance: R - |y - c| (convex) falls iff vA > 0; |y - v| (concave) rises iff vA > 0
-                const bool rises = vdw ? (vA < T(0)) : (vA > T(0));
-                const bool falls = vdw ? (vA > T(0)) : (vA < T(0));
-                if (inside ? rises : falls) continue;
-                if (vdw) {
-                    T v32[3] = {d[0], d[1], d[2]};
-                    v32[axis] += t;
-                    T nvv = sqrt(v32[0] * v32[0] + v32[1] * v32[1] + v32[2] * v32[2]);
-                    T R = c.w + rpT;
-                    T sc = R / nvv;
-                    int f = -1;
-                    if (FILT) {
-                        T delta = d0 + terr * (T(1) + sc) + T(2e-6);
-                        f = free_pt<true>(A, c.x + sc * v32[0], c.y + sc * v32[1], c.z + sc * v32[2], S.agid[slot], -1,
-                                          rpT, delta);
-                    }
-                    if (f < 0) {
-                        P4<double> ce = X.atom(slot);
-                        double cc[3] = {ce.x, ce.y, ce.z};
-                        if (t64 != t64) t64 = exact_root_sphere(cc, ce.w, s64, axis, (double)t);
-                        double v[3] = {s64[0] - cc[0], s64[1] - cc[1], s64[2] - cc[2]};
-                        v[axis] += t64;
-                        double nv64 = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-                        double R64 = ce.w + rp;
-                        f = free_pt<false>(X, cc[0] + R64 * v[0] / nv64, cc[1] + R64 * v[1] / nv64,
-                                           cc[2] + R64 * v[2] / nv64, S.agid[slot], -1, rp, 0.0);
-                    }
-                    if (f != 1) continue;
-                }
-                warp_push(E, warp, (float)t, (float)terr, t64, vdw ? 0 : 2, slot);
+            double t64 = NaN;
+            bool exact = FILT && (terr > tmax || t < terr + T(1e-6) || t > hT - terr - T(1e-6));
+            if (exact) {
+                P4<double> ce = vdw ? X.atom(slot) : X.vq(slot);
+                double cc[3] = {ce.x, ce.y, ce.z};
+                double r64 = vdw ? ce.w : rp;
+                t64 = exact_root_sphere(cc, r64, s64, axis, (double)t);
+                double dv[3] = {s64[0] - cc[0], s64[1] - cc[1], s64[2] - cc[2]};
+                dv[axis] += t64;
+                double f = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2] - r64 * r64;
+                if (!(t64 >= 0.0 && t64 <= h) || fabs(f) > 1e-9 * r64) continue;
+                vA = (T)dv[axis];
+                if (fabs(dv[axis]) <= 1e-9 * r64) vA = T(0);  // tangent: either way
+                t = (T)t64;
+                terr = T(0);
             }
-        } else {  // saddle: torus around a free-arc circle
-            const int pi = it - na - nv;
-            P4<T> o = S.po[pi];
-            P4<T> u = S.pu[pi];
-            // 1-Lipschitz distance to the circle, checked at the edge midpoint
-            T m[3] = {s[0] - o.x, s[1] - o.y, s[2] - o.z};
-            m[axis] += T(0.5) * hT;
-            T zc = m[0] * u.x + m[1] * u.y + m[2] * u.z;
-            T w2 = fmax(m[0] * m[0] + m[1] * m[1] + m[2] * m[2] - zc * zc, T(0));
-            T e1 = sqrt(w2) - o.w;
-            T gm = sqrt(e1 * e1 + zc * zc) - rpT;
-            if (fabs(gm) > T(0.5) * hT + mg) continue;
-            T q0[3] = {s[0] - o.x, s[1] - o.y, s[2] - o.z};
-            T uu[3] = {u.x, u.y, u.z};
-            T P = q0[0] * q0[0] + q0[1] * q0[1] + q0[2] * q0[2];
-            T z0 = q0[0] * u.x + q0[1] * u.y + q0[2] * u.z;
-            T pe = q0[axis], eu = uu[axis];
-            T K = P + o.w * o.w - rpT * rpT, r2 = o.w * o.w;
-            T co32[5] = {K * K - T(4) * r2 * (P - z0 * z0), T(4) * pe * K - T(8) * r2 * (pe - z0 * eu),
-                         T(4) * pe * pe + T(2) * K - T(4) * r2 * (T(1) - eu * eu), T(4) * pe, T(1)};
-            T rt32[4];
-            int nr = PolyRoots<T, 4>::run(co32, lo, hi, rt32);
-            // error scale of the FP32 quartic: its terms' sizes
-            const T Sf = fabs(co32[0]) + fabs(co32[1]) * hT + fabs(co32[2]) * hT * hT + T(6) * (P + r2 + rpT * rpT) * d0;
-            for (int k = 0; k < nr; ++k) {
-                T t = rt32[k];
-                T y[3] = {q0[0], q0[1], q0[2]};
-                y[axis] += t;
-                T dfd = T(4) * t * t * t + T(3) * co32[3] * t * t + T(2) * co32[2] * t + co32[1];
-                T yy = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
-                T Ay = yy + r2 - rpT * rpT;
-                T zy = y[0] * uu[0] + y[1] * uu[1] + y[2] * uu[2];
-                T w[3] = {y[0] - zy * uu[0], y[1] - zy * uu[1], y[2] - zy * uu[2]};
-                T nw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-                T rate = nw > T(0) ? ((nw - o.w) * w[axis] / nw + zy * uu[axis]) / rpT : T(0);
-                T terr = FILT ? T(8e-7) * Sf / fmax(fabs(dfd), T(1e-20)) + d0 : T(0);
-                double t64 = NaN;
-                bool exact = FILT && (terr > tmax || t < terr + T(1e-6) || t > hT - terr - T(1e-6) ||
-                                      fabs(Ay) < T(1e-3) * (yy + r2 + rpT * rpT) || fabs(rate) < T(1e-3) ||
-                                      nw < T(1e-3));
-                bool near_branch = Ay >= T(0);
-                if (exact) {
-                    P4<double> oe = X.po(pi);
-                    P4<double> ue = X.pu(pi);
-                    double oo[3] = {oe.x, oe.y, oe.z}, u64[3] = {ue.x, ue.y, ue.z};
-                    t64 = exact_root_torus(oo, u64, oe.w, rp, s64, axis, (double)t);
-                    if (!(t64 >= 0.0 && t64 <= h)) continue;
-                    double yd[3] = {s64[0] - oo[0], s64[1] - oo[1], s64[2] - oo[2]};
-                    yd[axis] += t64;
-                    double Ad = yd[0] * yd[0] + yd[1] * yd[1] + yd[2] * yd[2] + oe.w * oe.w - rp * rp;
-                    double zd = yd[0] * u64[0] + yd[1] * u64[1] + yd[2] * u64[2];
-                    double wd[3] = {yd[0] - zd * u64[0], yd[1] - zd * u64[1], yd[2] - zd * u64[2]};
-                    double nwd = sqrt(wd[0] * wd[0] + wd[1] * wd[1] + wd[2] * wd[2]);
-                    double near2 = (nwd - oe.w) * (nwd - oe.w) + zd * zd;
-                    if (fabs(near2 - rp * rp) > 1e-7 * rp * rp || !(nwd > 0.0)) continue;
-                    near_branch = Ad >= 0.0;
-                    double rd = ((nwd - oe.w) * wd[axis] / nwd + zd * u64[axis]) / rp;
-                    rate = (fabs(rd) <= 1e-9) ? T(0) : (T)rd;
-                    for (int z = 0; z < 3; ++z) w[z] = (T)wd[z];
-                    nw = (T)nwd;
-                    t = (T)t64;
-                    terr = T(0);
-                }
-                if (!near_branch) continue;  // far branch of the quartic
-                if (inside ? rate > T(0) : rate < T(0)) continue;
-                int2 ij = S.pij[pi];
-                T kk = o.w / nw;
+            // witness distance: R - |y - c| (convex) falls iff vA > 0; |y - v| (concave) rises iff vA > 0
+            const bool rises = vdw ? (vA < T(0)) : (vA > T(0));
+            const bool falls = vdw ? (vA > T(0)) : (vA < T(0));
+            if (inside ? rises : falls) continue;
+            if (vdw) {
+                T v32[3] = {d[0], d[1], d[2]};
+                v32[axis] += t;
+                T nvv = sqrt(v32[0] * v32[0] + v32[1] * v32[1] + v32[2] * v32[2]);
+                T Rr = c.w + rpT;
+                T sc = Rr / nvv;
                 int f = -1;
                 if (FILT) {
-                    T delta = d0 + terr * (T(1) + T(2) * o.w / nw) + T(2e-6);
-                    f = free_pt<true>(A, o.x + kk * w[0], o.y + kk * w[1], o.z + kk * w[2], ij.x, ij.y, rpT, delta);
+                    T delta = d0 + terr * (T(1) + sc) + T(2e-6);
+                    f = free_pt<true>(A, c.x + sc * v32[0], c.y + sc * v32[1], c.z + sc * v32[2], S.agid[slot], -1,
+                                      rpT, delta);
                 }
                 if (f < 0) {
-                    P4<double> oe = X.po(pi);
-                    P4<double> ue = X.pu(pi);
-                    double oo[3] = {oe.x, oe.y, oe.z}, u64[3] = {ue.x, ue.y, ue.z};
-                    if (t64 != t64) t64 = exact_root_torus(oo, u64, oe.w, rp, s64, axis, (double)t);
-                    double yd[3] = {s64[0] - oo[0], s64[1] - oo[1], s64[2] - oo[2]};
-                    yd[axis] += t64;
-                    double zd = yd[0] * u64[0] + yd[1] * u64[1] + yd[2] * u64[2];
-                    double wd[3] = {yd[0] - zd * u64[0], yd[1] - zd * u64[1], yd[2] - zd * u64[2]};
-                    double nwd = sqrt(wd[0] * wd[0] + wd[1] * wd[1] + wd[2] * wd[2]);
-                    double k64 = oe.w / nwd;
-                    f = free_pt<false>(X, oo[0] + k64 * wd[0], oo[1] + k64 * wd[1], oo[2] + k64 * wd[2], ij.x, ij.y,
-                                       rp, 0.0);
+                    P4<double> ce = X.atom(slot);
+                    double cc[3] = {ce.x, ce.y, ce.z};
+                    if (t64 != t64) t64 = exact_root_sphere(cc, ce.w, s64, axis, (double)t);
+                    double v[3] = {s64[0] - cc[0], s64[1] - cc[1], s64[2] - cc[2]};
+                    v[axis] += t64;
+                    double nv64 = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+                    double R64 = ce.w + rp;
+                    f = free_pt<false>(X, cc[0] + R64 * v[0] / nv64, cc[1] + R64 * v[1] / nv64,
+                                       cc[2] + R64 * v[2] / nv64, S.agid[slot], -1, rp, 0.0);
                 }
-                if (f == 1) warp_push(E, warp, (float)t, (float)terr, t64, 1, pi);
+                if (f != 1) continue;
+            }
+            pool_push(E, e, (float)t, (float)terr, t64, vdw ? 0 : 2, slot);
+        }
+        return;
+    }
+    // saddle: torus around a free-arc circle
+    const int pi = it - na - nv;
+    if constexpr (!FILT) {
+        torus_piece_exact(A, E, e, pi, s64, axis, h, rp, inside);
+    } else {
+        const P4<T> o = S.po[pi];
+        const P4<T> u = S.pu[pi];
+        const float q0[3] = {s[0] - o.x, s[1] - o.y, s[2] - o.z};
+        const float uu[3] = {u.x, u.y, u.z};
+        float rt[4];
+        int nr = 0;
+        if (!torus_roots32(q0, uu, o.w, rpT, axis, lo, hi, d0, rt, nr)) {
+            // sampling undecided (near-tangent line, or close to the circle's axis): the
+            // quartic's roots on the derivative chain
+            const float P = q0[0] * q0[0] + q0[1] * q0[1] + q0[2] * q0[2];
+            const float z0 = q0[0] * uu[0] + q0[1] * uu[1] + q0[2] * uu[2];
+            const float pe = q0[axis], eu = uu[axis];
+            const float K = P + o.w * o.w - rpT * rpT, r2 = o.w * o.w;
+            const float co32[5] = {K * K - 4.0f * r2 * (P - z0 * z0), 4.0f * pe * K - 8.0f * r2 * (pe - z0 * eu),
+                                   4.0f * pe * pe + 2.0f * K - 4.0f * r2 * (1.0f - eu * eu), 4.0f * pe, 1.0f};
+            float rq[4];
+            const int nq = PolyRoots<float, 4>::run(co32, lo, hi, rq);
+            nr = 0;
+            for (int k = 0; k < nq; ++k) {
+                float D, dD, nw, yy, zy, wv[3];
+                circle_dist32(q0, uu, o.w, axis, rq[k], D, dD, nw, yy, zy, wv);
+                // near branch: A = |y|^2 + rho^2 - r_p^2 >= 0; undecided signs go to FP64
+                const float Ay = yy + r2 - rpT * rpT;
+                if (fabsf(Ay) < 1e-3f * (yy + r2 + rpT * rpT)) nr = -1;
+                else if (Ay > 0.0f && nr >= 0) rt[nr++] = rq[k];
+            }
+            if (nr < 0) {
+                torus_piece_exact(X, E, e, pi, s64, axis, h, rp, inside);
+                return;
+            }
+        }
+        const int2 ij = S.pij[pi];
+        for (int k = 0; k < nr; ++k) {
+            const float t = rt[k];
+            float D, rate, nw, yy, zy, wv[3];
+            circle_dist32(q0, uu, o.w, axis, t, D, rate, nw, yy, zy, wv);
+            // root error: residual plus rounding of g over |g'| (g' varies little within terr)
+            const float terr =
+                (fabsf(D - rpT) + circle_dist_err(d0, yy, nw, o.w, rpT)) / fmax(fabs(rate), 1e-20f) + d0;
+            if (terr > tmax || t < terr + 1e-6f || t > hT - terr - 1e-6f || fabs(rate) < 1e-3f ||
+                nw < 1e-3f) {  // grazing or at an end point: the FP64 root decides
+                const P4<double> oe = X.po(pi);
+                const P4<double> ue = X.pu(pi);
+                const double oo[3] = {oe.x, oe.y, oe.z}, u64[3] = {ue.x, ue.y, ue.z};
+                const double t64 = exact_root_torus(oo, u64, oe.w, rp, s64, axis, (double)t);
+                torus_root_exact(X, E, e, pi, s64, axis, h, rp, inside, t64);
+                continue;
+            }
+            if (inside ? rate > 0.0f : rate < 0.0f) continue;
+            const float kk = o.w / nw;
+            const float delta = d0 + terr * (1.0f + 2.0f * o.w / nw) + 2e-6f;
+            const int f =
+                free_pt<true>(A, o.x + kk * wv[0], o.y + kk * wv[1], o.z + kk * wv[2], ij.x, ij.y, rpT, delta);
+            if (f == 1) {
+                pool_push(E, e, t, terr, NaN, 1, pi);
+            } else if (f < 0) {
+                const P4<double> oe = X.po(pi);
+                const P4<double> ue = X.pu(pi);
+                const double oo[3] = {oe.x, oe.y, oe.z}, u64[3] = {ue.x, ue.y, ue.z};
+                const double t64 = exact_root_torus(oo, u64, oe.w, rp, s64, axis, (double)t);
+                torus_root_exact(X, E, e, pi, s64, axis, h, rp, inside, t64);
             }
         }
     }
-    __syncwarp();
+}
+
+// First root of one crossing edge from its candidates in E.cand[warp] (whole
+// warp).  Returns 0 with the chosen piece (kind, staged slot) and its root, 1
+// when no root is found, 2 when the candidates overflowed the buffer (the
+// first WCAND are used).
+template <class T, bool FILT>
+__device__ int warp_select(const Model &M, const TileS<T> &S, const double *x0, EdgeSmem &E, int warp, int e,
+                           double h, double rp, T d0, float &t_out, int &kind_out, int &slot_out)
+{
+    const int lane = threadIdx.x & 31;
+    const EdgeRef R = edge_ref(E, e);
+    const int axis = R.axis;
+    const double s64[3] = {E.hd[R.p >> 6], E.hd[(R.p >> 3) & 7], E.hd[R.p & 7]};
+    const T s[3] = {(T)s64[0], (T)s64[1], (T)s64[2]};
+    SmemAcc<T> A(S);
+    ExactAcc<T> X(S, M, x0);
+    const T rpT = (T)rp;
+    const float tie = 1e-6f * (float)h;  // FP32 rounding of a root
+    const bool inside = R.lab == LABEL_IN;
     int n = E.ncand[warp];
     int status = n > WCAND ? 2 : 0;
     if (n > WCAND) n = WCAND;
@@ -673,6 +859,7 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Grid G, co
     const double h = G.h, rp = M.rp;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const T d0 = FILT ? (T)G.d0 : T(0);
+    const T hT = (T)h, rpT = (T)rp, mg = FILT ? T(2e-3) : T(0);
     for (long long tile = blockIdx.x; tile < nt; tile += gridDim.x) {
         int tot = 0;
         for (int a = 0; a < 3; ++a) tot += edge_start[a * nt + tile + 1] - edge_start[a * nt + tile];
@@ -716,48 +903,131 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Grid G, co
             __syncthreads();
         }
         const int ne = E.estart[3];
-        for (int e = warp; e < ne; e += EDGE_WARPS) {
-            const int a = e < E.estart[1] ? 0 : (e < E.estart[2] ? 1 : 2);
-            const int q = E.eptr[e];
-            const int li = q >> 6, lj = (q >> 3) & 7, lk = q & 7;
-            const int lab_s = E.lab[(li * 9 + lj) * 9 + lk];
-            float tr = 0.5f * (float)h;
-            int kind = 0, slot = 0;
-            int status = warp_edge<T, FILT>(M, S, x0, E, warp, a, q, lab_s, h, rp, d0, tr, kind, slot);
-            if (lane == 0) {
-                int mid = 0;
-                if (status != 1) mid = kind == 0 ? S.agid[slot] : (kind == 1 ? S.pidx[slot] : S.vidx[slot]);
-                if (status != 0) {
-                    atomicOr(err, status == 1 ? ERR_ROOT : ERR_CAP_CAND);
-                    if (status == 1) {
-                        int fs = atomicAdd(n_fail, 1);
-                        if (fs < FAIL_LOG) {
-                            long long *rec = fail_log + FAIL_REC * fs;
-                            for (int z = 0; z < FAIL_REC; ++z) rec[z] = 0;
-                            rec[0] = a;
-                            rec[1] = (long long)TILE * t[0] + li;
-                            rec[2] = (long long)TILE * t[1] + lj;
-                            rec[3] = (long long)TILE * t[2] + lk;
-                            rec[4] = lab_s;
-                            rec[5] = S.na;
-                            rec[6] = S.np;
-                            rec[7] = S.nv;
-                            rec[8] = E.ncand[warp];
-                            for (int z = 0; z < 7 && z < E.ncand[warp] && z < WCAND; ++z) {
-                                rec[9 + z] = (long long)((double)E.cand[warp][z].t * 1e9);
-                                rec[16 + z] = E.cand[warp][z].kind;
+        const int nitem = S.na + S.nv + S.np;
+        // chunks of edges; a chunk whose candidates or roots overflow the pools
+        // is retried at half the size
+        int c0 = 0, csz = CHUNK;
+        while (c0 < ne) {
+            const int c1 = min(ne, c0 + csz);
+            if (threadIdx.x == 0) {
+                E.npool = 0;
+                E.nroot = 0;
+            }
+            for (int k = threadIdx.x; k < CHUNK; k += EDGE_THREADS) E.rfill[k] = 0;
+            __syncthreads();
+            // 1. (edge, item) pairs that pass the prefilter: one warp per edge, lanes over items
+            for (int e = c0 + warp; e < c1; e += EDGE_WARPS) {
+                const EdgeRef R = edge_ref(E, e);
+                const T s[3] = {(T)E.hd[R.p >> 6], (T)E.hd[(R.p >> 3) & 7], (T)E.hd[R.p & 7]};
+                for (int i0 = 0; i0 < nitem; i0 += 32) {
+                    const int it = i0 + lane;
+                    const bool hit = it < nitem && cand_test<T>(S, s, R.axis, it, hT, rpT, mg);
+                    const unsigned m = __ballot_sync(0xffffffffu, hit);
+                    int base = 0;
+                    if (lane == 0 && m) base = atomicAdd(&E.npool, __popc(m));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    const int pos = base + __popc(m & ((1u << lane) - 1));
+                    if (hit && pos < POOL_MAX) E.pool[pos] = ((unsigned)e << 16) | (unsigned)it;
+                }
+            }
+            __syncthreads();
+            const int npool = E.npool;
+            if (npool > POOL_MAX && csz > 1) {
+                csz = (csz + 1) / 2;
+                __syncthreads();
+                continue;
+            }
+            // 2. roots of every pair, one thread each
+            for (int k = threadIdx.x; k < min(npool, POOL_MAX); k += EDGE_THREADS) {
+                const unsigned v = E.pool[k];
+                cand_roots<T, FILT>(M, S, x0, E, (int)(v >> 16), (int)(v & 0xffffu), h, rp, d0);
+            }
+            __syncthreads();
+            const int nroot = E.nroot;
+            if (nroot > ROOT_MAX && csz > 1) {
+                csz = (csz + 1) / 2;
+                __syncthreads();
+                continue;
+            }
+            const int nr = min(nroot, ROOT_MAX);
+            // 3. roots grouped by edge (counting sort)
+            for (int r = threadIdx.x; r < nr; r += EDGE_THREADS) atomicAdd(&E.rfill[E.redge[r] - c0], 1);
+            __syncthreads();
+            if (warp == 0) {
+                constexpr int PER = CHUNK / 32;
+                int v[PER], s = 0;
+                for (int k = 0; k < PER; ++k) {
+                    v[k] = E.rfill[lane * PER + k];
+                    s += v[k];
+                }
+                int inc = s;
+                for (int o = 1; o < 32; o <<= 1) {
+                    int u = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += u;
+                }
+                int run = inc - s;
+                for (int k = 0; k < PER; ++k) {
+                    E.rstart[lane * PER + k] = run;
+                    E.rfill[lane * PER + k] = run;
+                    run += v[k];
+                }
+                if (lane == 31) E.rstart[CHUNK] = run;
+            }
+            __syncthreads();
+            for (int r = threadIdx.x; r < nr; r += EDGE_THREADS)
+                E.rorder[atomicAdd(&E.rfill[E.redge[r] - c0], 1)] = (short)r;
+            __syncthreads();
+            // 4. first root of every edge: one warp per edge
+            for (int e = c0 + warp; e < c1; e += EDGE_WARPS) {
+                const int b = E.rstart[e - c0], n = E.rstart[e - c0 + 1] - b;
+                for (int k = lane; k < n && k < WCAND; k += 32) E.cand[warp][k] = E.root[E.rorder[b + k]];
+                if (lane == 0) E.ncand[warp] = n;
+                __syncwarp();
+                float tr = 0.5f * (float)h;
+                int kind = 0, slot = 0;
+                int status = warp_select<T, FILT>(M, S, x0, E, warp, e, h, rp, d0, tr, kind, slot);
+                if (nroot > ROOT_MAX || npool > POOL_MAX) status = 2;  // single-edge overflow
+                if (lane == 0) {
+                    const EdgeRef R = edge_ref(E, e);
+                    const int a = R.axis, q = R.p;
+                    const int li = q >> 6, lj = (q >> 3) & 7, lk = q & 7;
+                    int mid = 0;
+                    if (status != 1) mid = kind == 0 ? S.agid[slot] : (kind == 1 ? S.pidx[slot] : S.vidx[slot]);
+                    if (status != 0) {
+                        atomicOr(err, status == 1 ? ERR_ROOT : ERR_CAP_CAND);
+                        if (status == 1) {
+                            int fs = atomicAdd(n_fail, 1);
+                            if (fs < FAIL_LOG) {
+                                long long *rec = fail_log + FAIL_REC * fs;
+                                for (int z = 0; z < FAIL_REC; ++z) rec[z] = 0;
+                                rec[0] = a;
+                                rec[1] = (long long)TILE * t[0] + li;
+                                rec[2] = (long long)TILE * t[1] + lj;
+                                rec[3] = (long long)TILE * t[2] + lk;
+                                rec[4] = R.lab;
+                                rec[5] = S.na;
+                                rec[6] = S.np;
+                                rec[7] = S.nv;
+                                rec[8] = E.ncand[warp];
+                                for (int z = 0; z < 7 && z < E.ncand[warp] && z < WCAND; ++z) {
+                                    rec[9 + z] = (long long)((double)E.cand[warp][z].t * 1e9);
+                                    rec[16 + z] = E.cand[warp][z].kind;
+                                }
                             }
                         }
                     }
+                    const long long o = E.ebase[a] + (e - E.estart[a]);
+                    out.idx[a][o] = (long long)(TILE * t[0] + li) * st0 + (long long)(TILE * t[1] + lj) * st1 +
+                                    (TILE * t[2] + lk);
+                    // chosen piece for the FP64 polish: FP32 root, kind, model index, end label, failure
+                    out.code[a][o] = make_int2(__float_as_int(tr), (kind << 29) | (R.lab << 28) |
+                                                                        ((status == 1 ? 1 : 0) << 27) | mid);
                 }
-                const long long o = E.ebase[a] + (e - E.estart[a]);
-                out.idx[a][o] = (long long)(TILE * t[0] + li) * st0 + (long long)(TILE * t[1] + lj) * st1 +
-                                (TILE * t[2] + lk);
-                // chosen piece for the FP64 polish: FP32 root, kind, model index, end label, failure
-                out.code[a][o] = make_int2(__float_as_int(tr), (kind << 29) | (lab_s << 28) |
-                                                                    ((status == 1 ? 1 : 0) << 27) | mid);
+                __syncwarp();
             }
-            __syncwarp();
+            __syncthreads();
+            c0 = c1;
+            csz = CHUNK;
         }
         __syncthreads();
     }
@@ -915,17 +1185,22 @@ static void edge_solve_launch(const Model &M, const Grid &G, const int8_t *label
 long long polish_blocks(long long n_edges) { return n_edges > 0 ? ceil_div_ll(n_edges, POLISH_THREADS) : 0; }
 
 int launch_edge_solve(const Model &M, const Grid &G, int precision, const int8_t *labels, const int *edge_start,
-                      EdgeOut out, const long long n_edges[3], double *part, int *n_fail, int *err,
-                      long long *fail_log, cudaStream_t st)
+                      EdgeOut out, int *n_fail, int *err, long long *fail_log, cudaStream_t st)
 {
     if (precision == 0)
         edge_solve_launch<double, false>(M, G, labels, edge_start, out, n_fail, err, fail_log, st);
     else
         edge_solve_launch<float, true>(M, G, labels, edge_start, out, n_fail, err, fail_log, st);
+    return 1;
+}
+
+int launch_edge_polish(const Model &M, const Grid &G, EdgeOut out, const long long n_edges[3], double *part,
+                       cudaStream_t st)
+{
     long long nb = polish_blocks(n_edges[0] + n_edges[1] + n_edges[2]);
     if (nb > 0)
         k_edge_polish<<<(unsigned)nb, POLISH_THREADS, 0, st>>>(M, G, out, n_edges[0], n_edges[1], n_edges[2], part);
-    return nb > 0 ? 2 : 1;
+    return nb > 0 ? 1 : 0;
 }
 
 int launch_reduce(const Grid &G, const double *part, long long nparts, const int *tile_inside, double *out2,

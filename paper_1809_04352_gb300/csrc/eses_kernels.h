@@ -59,8 +59,9 @@ constexpr int FAIL_LOG = 8;
 constexpr int FAIL_REC = 24;
 long long polish_blocks(long long n_edges);
 int launch_edge_solve(const Model &M, const Grid &G, int precision, const int8_t *labels, const int *edge_start,
-                      EdgeOut out, const long long n_edges[3], double *part, int *n_fail, int *err,
-                      long long *fail_log, cudaStream_t st);
+                      EdgeOut out, int *n_fail, int *err, long long *fail_log, cudaStream_t st);
+int launch_edge_polish(const Model &M, const Grid &G, EdgeOut out, const long long n_edges[3], double *part,
+                       cudaStream_t st);
 int launch_reduce(const Grid &G, const double *part, long long nparts, const int *tile_inside, double *out2,
                   long long *counts, cudaStream_t st);
 

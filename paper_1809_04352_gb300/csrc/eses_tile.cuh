@@ -376,7 +376,7 @@ __device__ __forceinline__ int lt_lin(T a, T b, T e)
 // Freeness of q against every staged atom but e0, e1 (sorted indices of the
 // atoms whose spheres carry q).  1 free, 0 covered, -1 undecided.
 template <bool FILT, class Acc, class T>
-__device__ __forceinline__ int free_pt(const Acc &A, T qx, T qy, T qz, int e0, int e1, T rp, T delta)
+__device__ __noinline__ int free_pt(const Acc &A, T qx, T qy, T qz, int e0, int e1, T rp, T delta)
 {
     int res = 1;
     const int na = A.na();
@@ -396,7 +396,7 @@ __device__ __forceinline__ int free_pt(const Acc &A, T qx, T qy, T qz, int e0, i
 // Convex witness of atom a at x: 1 free projection at distance < thr,
 // 0 none, -1 undecided.
 template <bool FILT, class Acc, class T>
-__device__ __forceinline__ int face_witness(const Acc &A, int a, T x, T y, T z, T rp, T thr, T d0)
+__device__ __noinline__ int face_witness(const Acc &A, int a, T x, T y, T z, T rp, T thr, T d0)
 {
     if (!A.face(a)) return 0;
     P4<T> c = A.atom(a);
@@ -418,7 +418,7 @@ __device__ __forceinline__ int face_witness(const Acc &A, int a, T x, T y, T z, 
 
 // Saddle witness of pair p at x: nearest point of its circle.
 template <bool FILT, class Acc, class T>
-__device__ __forceinline__ int saddle_witness(const Acc &A, int p, T x, T y, T z, T rp, T thr, T d0)
+__device__ __noinline__ int saddle_witness(const Acc &A, int p, T x, T y, T z, T rp, T thr, T d0)
 {
     P4<T> o = A.po(p);
     P4<T> u = A.pu(p);
@@ -497,7 +497,7 @@ __device__ int classify_pt(const Acc &A, T x, T y, T z, T rp, T thr, T d0)
 // 0 if none does (certain), -1 undecided.  Items (exclude_kind, exclude_id)
 // are skipped: kind 0 atom (convex witness), 1 pair, 2 vertex, -1 none.
 template <bool FILT, class Acc, class T>
-__device__ int warp_witness(const Acc &A, T x, T y, T z, T rp, T thr, T d0, int exclude_kind, int exclude_id)
+__device__ __noinline__ int warp_witness(const Acc &A, T x, T y, T z, T rp, T thr, T d0, int exclude_kind, int exclude_id)
 {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;

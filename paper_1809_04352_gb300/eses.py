@@ -43,7 +43,7 @@ SYMBOLS = ["eses_create", "eses_create_device", "eses_set_option", "eses_run", "
            "eses_labels_device", "eses_num_intersections", "eses_intersections", "eses_intersections_device",
            "eses_area_volume", "eses_stats", "eses_stage_times", "eses_root_failures", "eses_patch_counts",
            "eses_patch_data", "eses_crossing_edges_noalloc", "eses_last_error", "eses_destroy"]
-STAGE_NAMES = ["binning", "pairs", "arcs", "classify", "band", "edge_count", "edge_solve", "reduce"]
+STAGE_NAMES = ["binning", "pairs", "arcs", "classify", "band", "edge_count", "edge_solve", "edge_polish", "reduce"]
 
 _lib = None
 
