@@ -315,7 +315,7 @@ def main():
         "classify": ("k_classify<float,true> (FP32-filtered classification, every grid point)",
                      fm["model_flops"], stage_ms["classify"],
                      {"flops_per_point": fm["flops_per_point"]}),
-        "edge_solve": ("k_edge_solve<float,true> (first root and its patch, one warp per crossing edge)",
+        "edge_solve": ("k_edge_solve<float,true> (first root and its patch of every crossing edge, pooled per tile)",
                        fm["edge_counts"]["model_flops"], stage_ms["edge_solve"],
                        {"flops_per_edge": fm["edge_flops_per_edge"], "edges": fm["edge_counts"]["edges"]}),
     }

@@ -372,6 +372,23 @@ __device__ __forceinline__ float circle_dist_err(float d0, float yy, float nw, f
     return 2.0f * d0 + 4e-7f * (yy / fmaxf(nw, 1e-3f) + sqrtf(yy) + rho + rp);
 }
 
+// g along the edge from its quadratic pieces: |y|^2 = yy0 + 2 qa t + t^2 and
+// z = z0 + ua t (qa, ua the edge-axis components of q0 and u)
+struct LineCircle32 {
+    float yy0, qa, z0, ua, rho, rp;
+    __device__ __forceinline__ void eval(float t, float &g, float &dg, float &nw, float &yy) const
+    {
+        yy = fmaf(t, t + 2.0f * qa, yy0);
+        const float z = fmaf(t, ua, z0);
+        nw = sqrtf(fmaxf(yy - z * z, 0.0f));
+        const float e = nw - rho;
+        const float D = sqrtf(e * e + z * z);
+        g = D - rp;
+        const float wa = qa + t - z * ua;  // edge-axis component of w
+        dg = (nw > 0.0f && D > 0.0f) ? __fdividef(e * __fdividef(wa, nw) + z * ua, D) : 0.0f;
+    }
+};
+
 // Certified FP32 isolation of the roots of g on [lo, hi].  g is 1-Lipschitz
 // and |g''| <= C = max(1/D, 1/|w|) (the distance to a circle has Hessian
 // eigenvalues 0 and 1/D in the meridian plane and (dD/d|w|)/|w| around the
@@ -387,40 +404,55 @@ __device__ __noinline__ bool torus_roots32(const float *q0, const float *u, floa
 {
     constexpr int K = 8;
     const float dl = (hi - lo) / (float)K;
-    float g[K + 1], dg[K + 1], eg[K + 1], mw[K + 1];
-#pragma unroll 1
+    LineCircle32 L;
+    L.yy0 = q0[0] * q0[0] + q0[1] * q0[1] + q0[2] * q0[2];
+    L.qa = q0[axis];
+    L.z0 = q0[0] * u[0] + q0[1] * u[1] + q0[2] * u[2];
+    L.ua = u[axis];
+    L.rho = rho;
+    L.rp = rp;
+    unsigned rootmask = 0;
+    float gp = 0.0f, dgp = 0.0f, egp = 0.0f, mwp = 0.0f;
+#pragma unroll
     for (int k = 0; k <= K; ++k) {
         const float t = k == K ? hi : lo + (float)k * dl;
-        float D, dD, nw, yy, z, w[3];
-        circle_dist32(q0, u, rho, axis, t, D, dD, nw, yy, z, w);
-        g[k] = D - rp;
-        dg[k] = dD;
-        eg[k] = circle_dist_err(d0, yy, nw, rho, rp);
-        mw[k] = fminf(D, nw);
+        float g, dg, nw, yy;
+        L.eval(t, g, dg, nw, yy);
+        const float eg = circle_dist_err(d0, yy, nw, rho, rp);
+        const float mw = fminf(g + rp, nw);
+        if (k > 0) {
+            const bool sc = (gp <= 0.0f) != (g <= 0.0f);
+            if (sc || fabsf(gp) + fabsf(g) <= dl + egp + eg) {
+                if (fabsf(gp) <= egp || fabsf(g) <= eg) return false;
+                const float low = fminf(mwp, mw) - 0.5f * dl;
+                if (!(low > 1e-2f)) return false;
+                if (!((dgp > 0.0f) == (dg > 0.0f) && fabsf(dgp) + fabsf(dg) > dl / low + 2e-4f)) return false;
+                if (sc) rootmask |= 1u << (k - 1);
+            }
+        }
+        gp = g;
+        dgp = dg;
+        egp = eg;
+        mwp = mw;
     }
     nr = 0;
-#pragma unroll 1
-    for (int k = 0; k < K; ++k) {
-        const float ga = g[k], gb = g[k + 1];
-        const bool sc = (ga <= 0.0f) != (gb <= 0.0f);
-        if (!sc && fabsf(ga) + fabsf(gb) > dl + eg[k] + eg[k + 1]) continue;
-        if (fabsf(ga) <= eg[k] || fabsf(gb) <= eg[k + 1]) return false;
-        const float low = fminf(mw[k], mw[k + 1]) - 0.5f * dl;
-        if (!(low > 1e-2f)) return false;
-        const bool mono = (dg[k] > 0.0f) == (dg[k + 1] > 0.0f) && fabsf(dg[k]) + fabsf(dg[k + 1]) > dl / low + 2e-4f;
-        if (!mono) return false;
-        if (!sc) continue;
+    while (rootmask) {
+        const int k = __ffs(rootmask) - 1;
+        rootmask &= rootmask - 1;
         if (nr == 4) return false;
         float a = lo + (float)k * dl, b = k + 1 == K ? hi : lo + (float)(k + 1) * dl;
-        float t = a + (b - a) * (ga / (ga - gb));
+        float ga, gb, dga, dgb, nwa, yya;
+        L.eval(a, ga, dga, nwa, yya);
+        L.eval(b, gb, dgb, nwa, yya);
+        const bool neg_a = ga <= 0.0f;
+        float t = a + (b - a) * __fdividef(ga, ga - gb);
         for (int itn = 0; itn < 5; ++itn) {  // Newton, bisection when it leaves the bracket
-            float D, dD, nw, yy, z, w[3];
-            circle_dist32(q0, u, rho, axis, t, D, dD, nw, yy, z, w);
-            const float f = D - rp;
+            float f, df, nw, yy;
+            L.eval(t, f, df, nw, yy);
             if (f == 0.0f) break;
-            if ((f <= 0.0f) == (ga <= 0.0f)) a = t;
+            if ((f <= 0.0f) == neg_a) a = t;
             else b = t;
-            float tn = dD != 0.0f ? t - f / dD : 0.5f * (a + b);
+            float tn = df != 0.0f ? t - __fdividef(f, df) : 0.5f * (a + b);
             if (!(tn > a && tn < b)) tn = 0.5f * (a + b);
             t = tn;
         }
@@ -725,7 +757,17 @@ __device__ int warp_select(const Model &M, const TileS<T> &S, const double *x0, 
             pick = k;
             break;
         }
-        // outside end point: the root must not be strictly outside M
+        // outside end point: the root must not be strictly outside M.  The
+        // surface crossing is always a candidate (the nearest free point at
+        // it is a piece's free witness) and every candidate before it lies
+        // strictly outside, so the last candidate left needs no test.
+        bool others = false;
+        for (int j = lane; j < n; j += 32)
+            if (j != k && c[j].t < INFINITY) others = true;
+        if (!__any_sync(0xffffffffu, others)) {
+            pick = k;
+            break;
+        }
         int r;
         if (FILT && c[k].t64 != c[k].t64) {
             T y0 = s[0], y1 = s[1], y2 = s[2];

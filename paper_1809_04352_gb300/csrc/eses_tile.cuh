@@ -393,10 +393,15 @@ __device__ __noinline__ int free_pt(const Acc &A, T qx, T qy, T qz, int e0, int 
     return res;
 }
 
-// Convex witness of atom a at x: 1 free projection at distance < thr,
-// 0 none, -1 undecided.
+// Witness proposals.  A convex proposal of atom a at x is the radial
+// projection q of x on a's expanded sphere, a saddle proposal of pair p the
+// nearest point q of p's circle; each counts when q is free and closer than
+// thr.  Return: 0 no proposal (certain), 1 proposal within thr (certain),
+// -1 proposal with the distance test undecided, -2 undecided without a
+// proposal; dq bounds the error of q, e0/e1 are the atoms that carry q.
 template <bool FILT, class Acc, class T>
-__device__ __noinline__ int face_witness(const Acc &A, int a, T x, T y, T z, T rp, T thr, T d0)
+__device__ __forceinline__ int face_proposal(const Acc &A, int a, T x, T y, T z, T rp, T thr, T d0, T &qx, T &qy,
+                                             T &qz, T &dq, int &e0, int &e1)
 {
     if (!A.face(a)) return 0;
     P4<T> c = A.atom(a);
@@ -405,20 +410,23 @@ __device__ __noinline__ int face_witness(const Acc &A, int a, T x, T y, T z, T r
     T R = c.w + rp;
     if (lt_sq<FILT>(d2, R * R, R, d0) == 0) return 0;
     T d = sqrt(d2);
-    if (d <= T(1e-3)) return FILT ? -1 : 0;  // x at a centre is inside its vdW ball
+    if (d <= T(1e-3)) return FILT ? -2 : 0;  // x at a centre is inside its vdW ball
     T wd = fabs(R - d);                        // distance to the projection
     int tw = lt_lin<FILT>(wd, thr, d0 + T(1e-6) * R);
     if (tw == 0) return 0;
     T s = R / d;
-    T dq = FILT ? d0 * (T(1) + T(2) * R / d) + T(1e-6) * R : T(0);
-    int f = free_pt<FILT>(A, c.x + s * dx, c.y + s * dy, c.z + s * dz, A.agid(a), -1, rp, dq + d0);
-    if (f == 1 && tw == 1) return 1;
-    return f == 0 ? 0 : -1;
+    qx = c.x + s * dx;
+    qy = c.y + s * dy;
+    qz = c.z + s * dz;
+    dq = FILT ? d0 * (T(1) + T(2) * R / d) + T(1e-6) * R : T(0);
+    e0 = A.agid(a);
+    e1 = -1;
+    return tw;
 }
 
-// Saddle witness of pair p at x: nearest point of its circle.
 template <bool FILT, class Acc, class T>
-__device__ __noinline__ int saddle_witness(const Acc &A, int p, T x, T y, T z, T rp, T thr, T d0)
+__device__ __forceinline__ int saddle_proposal(const Acc &A, int p, T x, T y, T z, T rp, T thr, T d0, T &qx, T &qy,
+                                               T &qz, T &dq, int &e0, int &e1)
 {
     P4<T> o = A.po(p);
     P4<T> u = A.pu(p);
@@ -427,13 +435,12 @@ __device__ __noinline__ int saddle_witness(const Acc &A, int p, T x, T y, T z, T
     T wx = yx - zc * u.x, wy = yy - zc * u.y, wz = yz - zc * u.z;
     T w2 = wx * wx + wy * wy + wz * wz;
     T nw = sqrt(w2);
-    T e1 = nw - o.w;
-    T dist2 = e1 * e1 + zc * zc;
+    T e1d = nw - o.w;
+    T dist2 = e1d * e1d + zc * zc;
     T dw = FILT ? T(2) * d0 + T(2e-6) * (nw + fabs(zc)) : T(0);
     int t = lt_sq<FILT>(dist2, thr * thr, thr, T(1.5) * dw + T(1e-6));
     if (t == 0) return 0;
-    if (FILT && nw < T(1e-3)) return -1;  // near the circle's axis the nearest point is ill-conditioned
-    T qx, qy, qz;
+    if (FILT && nw < T(1e-3)) return -2;  // near the circle's axis the nearest point is ill-conditioned
     if (w2 > T(0)) {
         T k = o.w / nw;
         qx = o.x + k * wx; qy = o.y + k * wy; qz = o.z + k * wz;
@@ -444,11 +451,87 @@ __device__ __noinline__ int saddle_witness(const Acc &A, int p, T x, T y, T z, T
         T nv = sqrt(vx * vx + vy * vy + vz * vz);
         qx = o.x + o.w * vx / nv; qy = o.y + o.w * vy / nv; qz = o.z + o.w * vz / nv;
     }
-    T dq = FILT ? o.w * T(2) * dw / nw + d0 + T(1e-6) * o.w : T(0);
+    dq = FILT ? o.w * T(2) * dw / nw + d0 + T(1e-6) * o.w : T(0);
     int2 ij = A.pij(p);
-    int f = free_pt<FILT>(A, qx, qy, qz, ij.x, ij.y, rp, dq + d0);
+    e0 = ij.x;
+    e1 = ij.y;
+    return t;
+}
+
+// Convex witness of atom a at x: 1 free projection at distance < thr,
+// 0 none, -1 undecided.
+template <bool FILT, class Acc, class T>
+__device__ __noinline__ int face_witness(const Acc &A, int a, T x, T y, T z, T rp, T thr, T d0)
+{
+    T qx, qy, qz, dq;
+    int e0, e1;
+    const int tw = face_proposal<FILT>(A, a, x, y, z, rp, thr, d0, qx, qy, qz, dq, e0, e1);
+    if (tw == 0) return 0;
+    if (tw == -2) return -1;
+    int f = free_pt<FILT>(A, qx, qy, qz, e0, e1, rp, dq + d0);
+    if (f == 1 && tw == 1) return 1;
+    return f == 0 ? 0 : -1;
+}
+
+// Saddle witness of pair p at x: nearest point of its circle.
+template <bool FILT, class Acc, class T>
+__device__ __noinline__ int saddle_witness(const Acc &A, int p, T x, T y, T z, T rp, T thr, T d0)
+{
+    T qx, qy, qz, dq;
+    int e0, e1;
+    const int t = saddle_proposal<FILT>(A, p, x, y, z, rp, thr, d0, qx, qy, qz, dq, e0, e1);
+    if (t == 0) return 0;
+    if (t == -2) return -1;
+    int f = free_pt<FILT>(A, qx, qy, qz, e0, e1, rp, dq + d0);
     if (f == 1 && t == 1) return 1;
     return f == 0 ? 0 : -1;
+}
+
+// Freeness of q (the same on every lane) against every staged atom but e0,
+// e1, lanes over the atoms: 1 free, 0 covered, -1 undecided.
+template <bool FILT, class Acc, class T>
+__device__ __forceinline__ int warp_free(const Acc &A, T qx, T qy, T qz, int e0, int e1, T rp, T delta)
+{
+    const unsigned full = 0xffffffffu;
+    bool cov = false, und = false;
+    for (int k = threadIdx.x & 31; k < A.na(); k += 32) {
+        int g = A.agid(k);
+        if (g == e0 || g == e1) continue;
+        P4<T> c = A.atom(k);
+        T dx = qx - c.x, dy = qy - c.y, dz = qz - c.z;
+        T R = c.w + rp;
+        int t = lt_sq<FILT>(dx * dx + dy * dy + dz * dz, R * R, R, delta);
+        if (t == 1) cov = true;
+        else if (t < 0) und = true;
+    }
+    if (__any_sync(full, cov)) return 0;
+    return __any_sync(full, und) ? -1 : 1;
+}
+
+// Proposals held by the lanes in `mask`, tested one after the other by the
+// whole warp: 1 as soon as one is free and certainly within thr; else
+// und is set when one could be.
+template <bool FILT, class Acc, class T>
+__device__ __forceinline__ int warp_test_proposals(const Acc &A, unsigned mask, int tw, T qx, T qy, T qz, T dq, int e0,
+                                                   int e1, T rp, T d0, bool &und)
+{
+    const unsigned full = 0xffffffffu;
+    while (mask) {
+        const int b = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const int btw = __shfl_sync(full, tw, b);
+        if (btw == -2) {
+            und = true;
+            continue;
+        }
+        const T bx = __shfl_sync(full, qx, b), by = __shfl_sync(full, qy, b), bz = __shfl_sync(full, qz, b);
+        const T bd = __shfl_sync(full, dq, b);
+        const int b0 = __shfl_sync(full, e0, b), b1 = __shfl_sync(full, e1, b);
+        const int f = warp_free<FILT>(A, bx, by, bz, b0, b1, rp, bd + d0);
+        if (f == 1 && btw == 1) return 1;
+        if (f != 0) und = true;
+    }
+    return 0;
 }
 
 // Label of the point (x,y,z) in the tile frame: 1 if no free probe centre lies
@@ -526,21 +609,23 @@ __device__ __noinline__ int warp_witness(const Acc &A, T x, T y, T z, T rp, T th
         else if (t < 0) und = true;
     }
     if (__any_sync(full, found)) return 1;
-    for (int a = lane; a < na; a += 32) {
-        if (exclude_kind == 0 && a == exclude_id) continue;
-        int w = face_witness<FILT>(A, a, x, y, z, rp, thr, d0);
-        if (w == 1) found = true;
-        else if (w < 0) und = true;
+    und = __any_sync(full, und);
+    // convex and saddle proposals: lanes propose, the warp tests freeness
+    for (int i0 = 0; i0 < na + np; i0 += 32) {
+        const int i = i0 + lane;
+        T qx = T(0), qy = T(0), qz = T(0), dq = T(0);
+        int e0 = -1, e1 = -1, tw = 0;
+        if (i < na) {
+            if (!(exclude_kind == 0 && i == exclude_id))
+                tw = face_proposal<FILT>(A, i, x, y, z, rp, thr, d0, qx, qy, qz, dq, e0, e1);
+        } else if (i < na + np) {
+            if (!(exclude_kind == 1 && i - na == exclude_id))
+                tw = saddle_proposal<FILT>(A, i - na, x, y, z, rp, thr, d0, qx, qy, qz, dq, e0, e1);
+        }
+        const unsigned m = __ballot_sync(full, tw != 0);
+        if (warp_test_proposals<FILT>(A, m, tw, qx, qy, qz, dq, e0, e1, rp, d0, und) == 1) return 1;
     }
-    if (__any_sync(full, found)) return 1;
-    for (int p = lane; p < np; p += 32) {
-        if (exclude_kind == 1 && p == exclude_id) continue;
-        int w = saddle_witness<FILT>(A, p, x, y, z, rp, thr, d0);
-        if (w == 1) found = true;
-        else if (w < 0) und = true;
-    }
-    if (__any_sync(full, found)) return 1;
-    return __any_sync(full, und) ? -1 : 0;
+    return und ? -1 : 0;
 }
 
 }  // namespace eses
