@@ -14,6 +14,9 @@ point, crossing edges, roots and normals, area and volume.
   roofline   the dominant kernel (by event-timed duration; the other heavy
              kernel beside it) against the FP32 ALU peak, with the algorithmic
              flops of the oracle-counted flop model
+  batch      the 256-molecule workload (log-uniform 300-20,000 atoms, h 0.5)
+             in one batched context: persistent tile kernels with a device
+             work queue, replayed as one CUDA graph, autotuned launch shapes
   cpu_baseline  the FP64 CPU oracle on a seeded sample of blocks, all cores
 
 --impl reference times the oracle (the reference arm of this build) on the
@@ -175,6 +178,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-only", action="store_true",
                     help="only the warm-up and device-resident steps (for ncu captures); prints stage times")
+    ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of the autotuner's")
+    ap.add_argument("--no-graph", action="store_true", help="eager launches instead of CUDA-graph replay")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 256-molecule batched workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -225,6 +231,15 @@ def main():
     ctx = eses.eses_create(xyz, rad, wl.r_p, wl.h, wl.margin)
     eses.eses_set_option(ctx, eses.ESES_OPT_STREAM, stream.cuda_stream)
     eses.eses_set_option(ctx, eses.ESES_OPT_PROFILE, 1)
+    use_graph = not args.no_graph
+    eses.eses_set_option(ctx, eses.ESES_OPT_GRAPH, 1 if use_graph else 0)
+    tuned = None
+    if not args.no_autotune and not args.profile_only:
+        cls_ms, edge_ms = eses.eses_autotune(ctx, 3)
+        tuned = {k: eses.eses_get_option(ctx, v) for k, v in (
+            ("cls_ctas_per_sm", eses.ESES_OPT_CLS_CTAS), ("cls_tiles_per_pop", eses.ESES_OPT_CLS_TILES),
+            ("edge_ctas_per_sm", eses.ESES_OPT_EDGE_CTAS), ("edge_tiles_per_pop", eses.ESES_OPT_EDGE_TILES),
+            ("edge_chunk", eses.ESES_OPT_EDGE_CHUNK))}
     for _ in range(args.warmup):
         eses.eses_run(ctx)
     dims, _ = eses.eses_grid(ctx)
@@ -329,6 +344,48 @@ def main():
     roofline = rl[dominant]
     roofline_others = {k: v for k, v in rl.items() if k != dominant}
 
+    # ---- batched workload: 256 molecules in one context ---------------------
+    batch = None
+    if not args.no_batch:
+        bwl = inputs.WORKLOADS[3]
+        mols = [inputs.workload_atoms(3, molecule=m) for m in range(len(inputs.batch_sizes()))]
+        bctx = eses.eses_create_batch(mols, bwl.r_p, bwl.h, bwl.margin)
+        eses.eses_set_option(bctx, eses.ESES_OPT_STREAM, stream.cuda_stream)
+        eses.eses_set_option(bctx, eses.ESES_OPT_GRAPH, 1 if use_graph else 0)
+        if not args.no_autotune:
+            eses.eses_autotune(bctx, 2)
+        for _ in range(args.warmup):
+            eses.eses_run(bctx)
+        bpts = eses.eses_stats(bctx)["points"]
+        torch.cuda.synchronize()
+        barrier()
+        bt = []
+        for _ in range(args.steps):
+            flush.zero_()
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            eses.eses_run(bctx)
+            s1.record(stream)
+            s1.synchronize()
+            bt.append(s0.elapsed_time(s1))
+        torch.cuda.synchronize()
+        barrier()
+        bst = eses.eses_stats(bctx)
+        btot = sum(bt) / 1e3
+        if world > 1:
+            t = torch.tensor([btot], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            btot = float(t.item())
+        batch = {"workload": f"{bwl.name}: {len(mols)} synthetic globules, atom counts log-uniform in [300, 20000] "
+                             f"({sum(len(r) for _, r in mols)} atoms), r_p {bwl.r_p} A, h {bwl.h} A, "
+                             f"margin {bwl.margin} A, one context",
+                 "value": world * bpts * args.steps / btot, "unit": UNIT, "ms_per_step": 1e3 * btot / args.steps,
+                 "points": int(bpts), "crossing_edges": int(bst["crossing_edges"]),
+                 "root_failures": int(bst["root_failures"]), "kernel_launches_per_step": int(bst["kernel_launches"]),
+                 "graph": use_graph}
+        eses.eses_destroy(bctx)
+
     # ---- CPU baseline (rank 0, N = 1) ---------------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -346,6 +403,8 @@ def main():
                 "gpu_launches": int(st["kernel_launches"]) * args.steps,
                 "roofline": roofline,
                 "roofline_other_kernels": roofline_others,
+                "launch": {"cuda_graph": use_graph, "autotuned": tuned},
+                "batch": batch,
                 "cpu_baseline": cpu,
                 "clocks": clk,
                 "plain_fp64": {"value": all_pts / (plain_ms / 1e3), "unit": UNIT, "ms_per_step": plain_ms,

@@ -70,6 +70,15 @@ typedef struct eses_ctx eses_ctx;
 #define ESES_OPT_STREAM 3      /* cudaStream_t cast to int64 (0 = the context's own stream) */
 #define ESES_OPT_SYNC 4        /* 1 (default): eses_run waits for the device; 0: returns after enqueueing */
 #define ESES_OPT_PROFILE 5     /* 1: time every stage of eses_run with CUDA events (eses_stage_times) */
+#define ESES_OPT_GRAPH 6       /* 1: after the first (planning) run, capture the device path in one CUDA graph
+                                  and replay it on every later eses_run (default 0) */
+#define ESES_OPT_QUEUE 7       /* 1 (default): persistent tile kernels take tiles from a device work queue;
+                                  0: fixed grid-stride order */
+#define ESES_OPT_CLS_CTAS 8    /* classification CTAs per SM (0 = occupancy limit, default) */
+#define ESES_OPT_CLS_TILES 9   /* classification tiles per queue pop (default 4) */
+#define ESES_OPT_EDGE_CTAS 10  /* root-solve CTAs per SM (0 = occupancy limit, default) */
+#define ESES_OPT_EDGE_TILES 11 /* root-solve tiles per queue pop (default 4) */
+#define ESES_OPT_EDGE_CHUNK 12 /* root-solve edges per pooled chunk (0 = the maximum, 64; default) */
 
 #define ESES_PREC_FP64 0           /* every step in FP64 */
 #define ESES_PREC_FP32_FILTERED 1  /* FP32 with a forward-error filter, FP64 inside the filter band */
@@ -85,8 +94,55 @@ int eses_create(const double *xyz, const double *radii, int64_t n_atoms, double 
 int eses_create_device(const double *xyz, const double *radii, int64_t n_atoms, double r_p, double h, double margin,
                        eses_ctx **out);
 
+/* Create a context for a batch of n_mol molecules that share r_p, h and
+ * margin.  xyz: host, 3 doubles per atom, the molecules' atoms one after the
+ * other; radii: host, one double per atom, same order; n_atoms: host, n_mol
+ * counts (each >= 1).  Every molecule gets its own grid (Eq. 2 on its own
+ * atoms) and its own results, equal to what eses_create on that molecule
+ * alone gives; a run processes all molecules together (one launch per stage,
+ * persistent tile kernels with a device work queue).  Results are read with
+ * the eses_mol_* functions (the single-molecule accessors below return
+ * ESES_EINVAL on a context with more than one molecule).  This batching has
+ * no counterpart in the paper, which runs one molecule at a time. */
+int eses_create_batch(const double *xyz, const double *radii, const int64_t *n_atoms, int n_mol, double r_p,
+                      double h, double margin, eses_ctx **out);
+
+/* Create a batch context from one host array per molecule (xyz[m]: 3 *
+ * n_atoms[m] doubles, radii[m]: n_atoms[m] doubles; copied) and run it once.
+ * On failure *out is NULL and eses_last_error(NULL) describes the cause. */
+int eses_run_batch(int n_mol, const double *const *xyz, const double *const *radii, const int64_t *n_atoms,
+                   double r_p, double h, double margin, eses_ctx **out);
+
 /* Set an option (ESES_OPT_*).  Takes effect at the next eses_run. */
 int eses_set_option(eses_ctx *ctx, int key, int64_t value);
+
+/* Read an option's current value (host output). */
+int eses_get_option(const eses_ctx *ctx, int key, int64_t *value);
+
+/* Autotuner: runs the context once, then times the persistent kernels
+ * (classification; root solve) over their launch shapes -- CTAs per SM from 1
+ * to the occupancy limit, tiles per queue pop, root-solve chunk size -- on
+ * the context's own workload, `reps` timed launches each (1..100), keeps the
+ * fastest (readable with eses_get_option) and runs once more with it.
+ * ms_out (host, 2 doubles, may be NULL): mean milliseconds of the chosen
+ * classification and root-solve launches. */
+int eses_autotune(eses_ctx *ctx, int reps, double *ms_out);
+
+/* Number of molecules of the context (host output). */
+int eses_num_molecules(const eses_ctx *ctx, int *n);
+
+/* Per-molecule results of a batch context (molecule m in [0, n_mol)); the
+ * same layout and semantics as the single-molecule functions below. */
+int eses_mol_grid(const eses_ctx *ctx, int m, int64_t dims[3], double origin[3]);
+int eses_mol_labels(const eses_ctx *ctx, int m, int8_t *out);
+int eses_mol_labels_device(const eses_ctx *ctx, int m, const int8_t **dptr);
+int eses_mol_num_intersections(const eses_ctx *ctx, int m, int axis, int64_t *n);
+int eses_mol_intersections(const eses_ctx *ctx, int m, int axis, int64_t *lower_idx, double *tau, double *normal,
+                           float *tau32, float *normal32);
+int eses_mol_intersections_device(const eses_ctx *ctx, int m, int axis, const int64_t **lower_idx,
+                                  const double **tau, const double **normal, const float **tau32,
+                                  const float **normal32);
+int eses_mol_area_volume(const eses_ctx *ctx, int m, double *area, double *volume);
 
 /* Run the whole path: cell binning, patch construction, classification,
  * crossing edges, root solve, area and volume.  Results stay in device memory
@@ -141,11 +197,10 @@ int eses_stage_times(const eses_ctx *ctx, double *ms, int n);
 /* Records of crossing edges whose root solve failed in the last run (at most
  * 8 are kept), host output of max_records * 24 int64: [0] axis, [1..3] lower
  * point (i,j,k), [4] label of the lower point, [5..7] staged atoms, circle
- * pairs and triple points of its tile, [8..23] solver counters (sphere
- * roots, covered sphere witnesses, probe-sphere roots, tori tested, quartic
- * roots, far-branch roots, covered torus witnesses, candidates, candidates
- * rejected by the first-root test, then the first candidates' tau*h*1e9).
- * *n_out receives the number of records copied. */
+ * pairs and triple points of its tile, [8] candidate roots of the edge,
+ * [9..15] the first candidates' root distance from the lower point in 1e-9 A,
+ * [16..22] their patch kinds (0 convex, 1 saddle, 2 concave), [23] the
+ * molecule.  *n_out receives the number of records copied. */
 int eses_root_failures(const eses_ctx *ctx, int64_t *records, int max_records, int *n_out);
 
 /* Patch model of the last run (§1: saddle patches lie on the circles where

@@ -1,8 +1,18 @@
 // eses_api.cu -- the C ABI (include/eses.h) and the host orchestration of one
-// run: cell binning -> neighbours -> circle pairs -> free arcs and triple
-// points -> patch bins -> classification (+ FP64 band) -> crossing edges ->
-// roots -> area/volume.  Every step runs on the device; the host only sizes
-// buffers (it reads four list totals per run) and launches.
+// run over a batch of molecules (one molecule is a batch of one):
+// cell binning -> neighbours -> circle pairs -> free arcs and triple points ->
+// patch bins -> classification (+ FP64 band) -> crossing edges -> roots ->
+// area/volume.  Every step runs on the device over all molecules at once:
+// the model lists are built in one pass (each molecule keeps its own cells),
+// and the tile kernels are persistent, taking tiles of every molecule from a
+// device work queue.
+//
+// The first run of a context plans it: the host reads four list totals to
+// size the buffers.  With ESES_OPT_GRAPH the next run captures the whole
+// device path, with those sizes, in one CUDA graph, and every later run
+// replays it (the inputs of a context never change, so neither do the sizes).
+// eses_autotune times the persistent kernels' launch shapes on the context's
+// own workload and keeps the fastest.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -38,11 +48,16 @@ void ck(cudaError_t e, const char *what)
     if (e != cudaSuccess) throw CudaError{e, what};
 }
 
+struct CaptureGrow {};  // a buffer would have to grow during graph capture
+
+thread_local bool g_capturing = false;
+
 template <class T>
 T *ensure(DBuf &b, size_t count)
 {
     size_t bytes = std::max<size_t>(count * sizeof(T), 16);
     if (b.cap < bytes) {
+        if (g_capturing) throw CaptureGrow{};
         if (b.p) cudaFree(b.p);
         b.p = nullptr;
         b.cap = 0;
@@ -60,41 +75,74 @@ T *ensure(DBuf &b, size_t count)
 
 thread_local std::string g_create_error;
 
+struct MolInfo {
+    long long atom0 = 0, n_atoms = 0;  // range in the batch input
+    double lo[3] = {0, 0, 0};
+    long long dims[3] = {0, 0, 0};
+    double rmax = 0;
+    double amin[3] = {0, 0, 0}, amax[3] = {0, 0, 0};
+};
+
+// launch shape of a persistent tile kernel
+struct Shape {
+    int ctas_per_sm = 0;  // 0: the occupancy limit
+    int tiles_per_pop = 4;
+    int chunk = 0;        // root solve: edges per pooled chunk (0: the maximum)
+};
+
 }  // namespace
 
 struct eses_ctx {
     int device = 0;
+    int n_sm = 1;
     cudaStream_t own_stream = nullptr;
     cudaStream_t stream = nullptr;
     bool sync = true;
     int precision = ESES_PREC_FP32_FILTERED;
     int block_pts = 64;
-    long long n_atoms = 0;
+    int n_mol = 1;
+    long long n_atoms = 0;  // all molecules
     double rp = 0, h = 0, margin = 0;
-    double lo[3] = {0, 0, 0};
-    long long dims[3] = {0, 0, 0};
     double rmax = 0, Rmax = 0;
-    double amin[3], amax[3];
+    std::vector<MolInfo> mol;
+    std::vector<Grid> grids;
+    std::vector<CellGrid> cgs;
+    std::vector<long long> tile_off;
+    long long n_tiles = 0, n_points = 0, ncell = 0;
     Model M{};
-    Grid G{};
+    Batch B{};
     // device buffers
-    DBuf xyz, rad, cell_id, cell_count, cell_start, cursor, atom_orig, atom;
+    DBuf xyz, rad, in_mol, grid_d, cg_d, tile_off_d, atom_mol, vert_mol, medge, term, queue;
+    DBuf cell_id, cell_count, cell_start, cursor, atom_orig, atom;
     DBuf nb_count, nb_start, nb_list, circle_count, contained, face;
     DBuf pair_count, pair_start, pair_o, pair_u, pair_ij, pair_free;
     DBuf vert_count, vert_start, vert;
     DBuf pbin_count, pbin_start, pbin_cursor, pbin_cell, pbin_list;
     DBuf vbin_count, vbin_start, vbin_cursor, vbin_cell, vbin_list;
-    DBuf labels, tile_band, tile_edges, edge_start, tile_inside, tile_area, tile_vol;
+    DBuf labels, tile_band, tile_edges, edge_start, tile_inside;
     DBuf out_idx[3], out_tau[3], out_nrm[3], out_tau32[3], out_nrm32[3], out_code[3];
-    DBuf scan_tmp, misc;  // misc: err, n_fail, area/vol, counts
+    DBuf scan_tmp, misc, av, counts, red_d, red_i;  // misc: err, n_fail
     DBuf fail_log;
     DBuf atom_hi, atom_lo, pair_hi, pair_lo, pair_u32, vert_hi, vert_lo;
+    // plan: list sizes of the first run (the inputs never change)
+    bool planned = false;
+    int plan_precision = -1;
+    int n_nb = 0, n_pairs = 0, n_verts = 0;
+    long long n_edges[3] = {0, 0, 0};
     // results
     bool ran = false;
-    long long n_edges[3] = {0, 0, 0};
-    double area = 0, volume = 0;
+    std::vector<long long> medge_h;  // 3 * (n_mol + 1)
+    std::vector<double> av_h;        // 2 per molecule
+    std::vector<long long> cnt_h;    // 2 per molecule
     long long stats[NSTAT] = {0};
     std::string err;
+    // launch shapes (eses_autotune, ESES_OPT_*)
+    Shape cls, edge;
+    bool use_queue = true;
+    // CUDA graph of the device path
+    bool graph_on = false;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_launches = 0;  // kernels in the graph
     // stage timing (ESES_OPT_PROFILE)
     bool profile = false;
     cudaEvent_t ev[NSTAGE + 1] = {};
@@ -110,17 +158,26 @@ int fail(eses_ctx *c, int code, const std::string &msg)
     return code;
 }
 
+void drop_graph(eses_ctx *c)
+{
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+}
+
 int scan(eses_ctx *c, const int *in, int *out, long long n)
 {
     int *tmp = ensure<int>(c->scan_tmp, (size_t)scan_tmp_ints(n));
     return scan_exclusive(in, out, n, tmp, c->stream);
 }
 
-int read_total(eses_ctx *c, const int *start, long long n)
+// list total at start[n]: read when planning, the planned value when capturing
+int list_total(eses_ctx *c, const int *start, long long n, int &planned)
 {
+    if (g_capturing) return planned;
     int v = 0;
     ck(cudaMemcpyAsync(&v, start + n, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read list total");
     ck(cudaStreamSynchronize(c->stream), "synchronize");
+    planned = v;
     return v;
 }
 
@@ -143,105 +200,168 @@ int validate(const double *xyz, const double *r, int64_t n, double rp, double h,
     return ESES_OK;
 }
 
-// grid of Eq. 2 and the cell/tile layout; xyz/r on the host
-int setup(eses_ctx *c, const double *xyz, const double *r)
+// Grids of Eq. 2, cell grids and the tile layout of every molecule; xyz/r on the host
+int setup(eses_ctx *c, const double *xyz, const double *r, const int64_t *counts)
 {
-    const long long n = c->n_atoms;
+    const int nm = c->n_mol;
+    c->mol.assign(nm, MolInfo());
     c->rmax = 0.0;
-    for (int a = 0; a < 3; ++a) {
-        double mn = xyz[a] - r[0], mx = xyz[a] + r[0];
-        c->amin[a] = xyz[a];
-        c->amax[a] = xyz[a];
-        for (long long i = 1; i < n; ++i) {
-            double v0 = xyz[3 * i + a] - r[i], v1 = xyz[3 * i + a] + r[i];
-            if (v0 < mn) mn = v0;
-            if (v1 > mx) mx = v1;
-            c->amin[a] = std::min(c->amin[a], xyz[3 * i + a]);
-            c->amax[a] = std::max(c->amax[a], xyz[3 * i + a]);
+    long long a0 = 0;
+    for (int m = 0; m < nm; ++m) {
+        MolInfo &I = c->mol[m];
+        I.atom0 = a0;
+        I.n_atoms = counts[m];
+        a0 += counts[m];
+        const double *X = xyz + 3 * I.atom0;
+        const double *R = r + I.atom0;
+        for (int a = 0; a < 3; ++a) {
+            double mn = X[a] - R[0], mx = X[a] + R[0];
+            I.amin[a] = X[a];
+            I.amax[a] = X[a];
+            for (long long i = 1; i < I.n_atoms; ++i) {
+                double v0 = X[3 * i + a] - R[i], v1 = X[3 * i + a] + R[i];
+                if (v0 < mn) mn = v0;
+                if (v1 > mx) mx = v1;
+                I.amin[a] = std::min(I.amin[a], X[3 * i + a]);
+                I.amax[a] = std::max(I.amax[a], X[3 * i + a]);
+            }
+            I.lo[a] = mn - c->margin;
+            I.dims[a] = (long long)ceil((mx + c->margin - I.lo[a]) / c->h) + 1;
         }
-        c->lo[a] = mn - c->margin;
-        c->dims[a] = (long long)ceil((mx + c->margin - c->lo[a]) / c->h) + 1;
+        I.rmax = 0.0;
+        for (long long i = 0; i < I.n_atoms; ++i) I.rmax = std::max(I.rmax, R[i]);
+        c->rmax = std::max(c->rmax, I.rmax);
+        if (I.dims[0] > (1LL << 30) || I.dims[1] > (1LL << 30) || I.dims[2] > (1LL << 30) ||
+            I.dims[0] * I.dims[1] * I.dims[2] > (1LL << 40))
+            return fail(c, ESES_EINVAL, "grid too large (molecule " + std::to_string(m) + ")");
     }
-    for (long long i = 0; i < n; ++i) c->rmax = std::max(c->rmax, r[i]);
     c->Rmax = c->rmax + c->rp;
-    long long npts = c->dims[0] * c->dims[1] * c->dims[2];
-    if (c->dims[0] > (1LL << 30) || c->dims[1] > (1LL << 30) || c->dims[2] > (1LL << 30) || npts > (1LL << 40))
-        return fail(c, ESES_EINVAL, "grid too large");
     Model &M = c->M;
-    M.n_atoms = (int)n;
+    M.n_atoms = (int)c->n_atoms;
+    M.n_mol = nm;
     M.rp = c->rp;
     M.rmax = c->rmax;
     M.Rmax = c->Rmax;
     // cubic cells of edge >= 2 R_max: overlapping expanded balls sit in adjacent cells
     M.cell = std::max(2.0 * c->Rmax, 1e-3);
-    for (int a = 0; a < 3; ++a) M.clo[a] = c->amin[a] - 1e-6;
-    long long ncell = 0;
+    c->cgs.assign(nm, CellGrid());
     for (int it = 0; it < 200; ++it) {
-        ncell = 1;
-        for (int a = 0; a < 3; ++a) {
-            long long k = (long long)floor((c->amax[a] - M.clo[a]) / M.cell) + 1;
-            M.cn[a] = (int)std::min(k, 1LL << 20);
-            ncell *= k;
+        long long total = 0;
+        bool ok = true;
+        for (int m = 0; m < nm; ++m) {
+            CellGrid &g = c->cgs[m];
+            long long n = 1;
+            for (int a = 0; a < 3; ++a) {
+                g.clo[a] = c->mol[m].amin[a] - 1e-6;
+                long long k = (long long)floor((c->mol[m].amax[a] - g.clo[a]) / M.cell) + 1;
+                if (k > (1LL << 20)) ok = false;
+                g.cn[a] = (int)std::min(k, 1LL << 20);
+                n *= k;
+            }
+            g.coff = (int)std::min(total, (long long)INT32_MAX);
+            total += n;
         }
-        if (ncell <= (1LL << 26)) break;
+        c->ncell = total;
+        if (ok && total <= (1LL << 26)) break;
         M.cell *= 1.25;  // very sparse extents: coarser cells stay correct
     }
-    if (ncell > (1LL << 26)) return fail(c, ESES_EINVAL, "cell grid too large");
-    Grid &G = c->G;
-    for (int a = 0; a < 3; ++a) {
-        G.lo[a] = c->lo[a];
-        G.dims[a] = c->dims[a];
-        G.tiles[a] = (int)ceil_div_ll(c->dims[a], TILE);
+    if (c->ncell > (1LL << 26)) return fail(c, ESES_EINVAL, "cell grid too large");
+    c->grids.assign(nm, Grid());
+    c->tile_off.assign(nm + 1, 0);
+    long long lab0 = 0;
+    for (int m = 0; m < nm; ++m) {
+        Grid &G = c->grids[m];
+        const MolInfo &I = c->mol[m];
+        for (int a = 0; a < 3; ++a) {
+            G.lo[a] = I.lo[a];
+            G.dims[a] = I.dims[a];
+            G.tiles[a] = (int)ceil_div_ll(I.dims[a], TILE);
+        }
+        G.h = c->h;
+        G.n_tiles = (long long)G.tiles[0] * G.tiles[1] * G.tiles[2];
+        G.tile0 = c->tile_off[m];
+        G.lab0 = lab0;
+        c->tile_off[m + 1] = c->tile_off[m] + G.n_tiles;
+        lab0 += I.dims[0] * I.dims[1] * I.dims[2];
+        G.rp = c->rp;
+        G.halo = I.rmax + 2.0 * c->rp;
+        double L = 8.0 * c->h * sqrt(3.0) + G.halo + 1.0;
+        // staged FP32 coordinates carry two roundings of at most 2^-24 L each, a grid
+        // point one, a difference of two of them one more: 5 * 2^-24 L per
+        // coordinate, 5.2e-7 L for the vector; d0 rounds that up
+        G.d0 = (float)(6e-7 * L);
+        for (int k = 0; k <= TILE; ++k) G.hl[k] = (float)((double)k * c->h);
+        G.ht_hi = (float)(TILE * c->h);
+        G.ht_lo = (float)(TILE * c->h - (double)G.ht_hi);
     }
-    G.h = c->h;
-    G.n_tiles = (long long)G.tiles[0] * G.tiles[1] * G.tiles[2];
-    G.rp = c->rp;
-    G.halo = c->rmax + 2.0 * c->rp;
-    double L = 8.0 * c->h * sqrt(3.0) + G.halo + 1.0;
-    // staged FP32 coordinates carry two roundings of at most 2^-24 L each, a grid
-    // point one, a difference of two of them one more: 5 * 2^-24 L per
-    // coordinate, 5.2e-7 L for the vector; d0 rounds that up
-    G.d0 = (float)(6e-7 * L);
-    for (int k = 0; k <= TILE; ++k) G.hl[k] = (float)((double)k * c->h);
-    G.ht_hi = (float)(TILE * c->h);
-    G.ht_lo = (float)(TILE * c->h - (double)G.ht_hi);
+    c->n_tiles = c->tile_off[nm];
+    c->n_points = lab0;
+    if (c->n_tiles >= (1LL << 31) / 4) return fail(c, ESES_EINVAL, "too many tiles");
     return ESES_OK;
 }
 
-int create_common(const double *hxyz, const double *hr, int64_t n, double rp, double h, double margin,
-                  const double *dxyz, const double *dr, eses_ctx **out)
+int create_common(const double *hxyz, const double *hr, const int64_t *counts, int n_mol, double rp, double h,
+                  double margin, const double *dxyz, const double *dr, eses_ctx **out)
 {
     if (!out) return fail(nullptr, ESES_EINVAL, "out is NULL");
     *out = nullptr;
+    if (n_mol < 1 || n_mol > (1 << 20)) return fail(nullptr, ESES_EINVAL, "n_mol must be in [1, 2^20]");
+    long long total = 0;
+    for (int m = 0; m < n_mol; ++m) {
+        if (counts[m] < 1) return fail(nullptr, ESES_EINVAL, "every molecule needs at least one atom");
+        total += counts[m];
+    }
     std::string msg;
-    int rc = validate(hxyz, hr, n, rp, h, margin, msg);
+    int rc = validate(hxyz, hr, total, rp, h, margin, msg);
     if (rc) return fail(nullptr, rc, msg);
     eses_ctx *c = new (std::nothrow) eses_ctx();
     if (!c) return fail(nullptr, ESES_ENOMEM, "host allocation failed");
-    c->n_atoms = n;
+    c->n_atoms = total;
+    c->n_mol = n_mol;
     c->rp = rp;
     c->h = h;
     c->margin = margin;
     try {
         ck(cudaGetDevice(&c->device), "cudaGetDevice");
+        ck(cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device), "device attribute");
+        classify_init();
+        edges_init();
+        ck(cudaGetLastError(), "kernel attributes");
         ck(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking), "cudaStreamCreate");
         c->stream = c->own_stream;
-        rc = setup(c, hxyz, hr);
+        rc = setup(c, hxyz, hr, counts);
         if (rc) {
             g_create_error = c->err;
             eses_destroy(c);
             return rc;
         }
-        double *x = ensure<double>(c->xyz, 3 * (size_t)n);
-        double *r = ensure<double>(c->rad, (size_t)n);
+        double *x = ensure<double>(c->xyz, 3 * (size_t)total);
+        double *r = ensure<double>(c->rad, (size_t)total);
         if (dxyz) {
-            ck(cudaMemcpyAsync(x, dxyz, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, c->stream), "copy atoms");
-            ck(cudaMemcpyAsync(r, dr, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream), "copy radii");
+            ck(cudaMemcpyAsync(x, dxyz, sizeof(double) * 3 * total, cudaMemcpyDeviceToDevice, c->stream), "copy atoms");
+            ck(cudaMemcpyAsync(r, dr, sizeof(double) * total, cudaMemcpyDeviceToDevice, c->stream), "copy radii");
         } else {
-            ck(cudaMemcpyAsync(x, hxyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream), "copy atoms");
-            ck(cudaMemcpyAsync(r, hr, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream), "copy radii");
+            ck(cudaMemcpyAsync(x, hxyz, sizeof(double) * 3 * total, cudaMemcpyHostToDevice, c->stream), "copy atoms");
+            ck(cudaMemcpyAsync(r, hr, sizeof(double) * total, cudaMemcpyHostToDevice, c->stream), "copy radii");
         }
+        std::vector<int> im((size_t)total);
+        for (int m = 0; m < n_mol; ++m)
+            for (long long i = 0; i < c->mol[m].n_atoms; ++i) im[(size_t)(c->mol[m].atom0 + i)] = m;
+        int *imd = ensure<int>(c->in_mol, (size_t)total);
+        Grid *gd = ensure<Grid>(c->grid_d, (size_t)n_mol);
+        CellGrid *cgd = ensure<CellGrid>(c->cg_d, (size_t)n_mol);
+        long long *tod = ensure<long long>(c->tile_off_d, (size_t)n_mol + 1);
+        ck(cudaMemcpyAsync(imd, im.data(), sizeof(int) * total, cudaMemcpyHostToDevice, c->stream), "copy");
+        ck(cudaMemcpyAsync(gd, c->grids.data(), sizeof(Grid) * n_mol, cudaMemcpyHostToDevice, c->stream), "copy");
+        ck(cudaMemcpyAsync(cgd, c->cgs.data(), sizeof(CellGrid) * n_mol, cudaMemcpyHostToDevice, c->stream), "copy");
+        ck(cudaMemcpyAsync(tod, c->tile_off.data(), sizeof(long long) * (n_mol + 1), cudaMemcpyHostToDevice, c->stream),
+           "copy");
         ck(cudaStreamSynchronize(c->stream), "synchronize");
+        c->M.cg = cgd;
+        c->B.n_mol = n_mol;
+        c->B.n_tiles = c->n_tiles;
+        c->B.grid = gd;
+        c->B.tile_off = tod;
     } catch (const CudaError &e) {
         std::string m = std::string(e.what) + ": " + cudaGetErrorString(e.e);
         eses_destroy(c);
@@ -263,24 +383,45 @@ void free_buf(DBuf &b)
 
 void mark(eses_ctx *c, int k)
 {
-    if (c->profile) ck(cudaEventRecord(c->ev[k], c->stream), "cudaEventRecord");
+    if (!c->profile) return;
+    // under capture an external record becomes a node of the graph, replayed every launch
+    if (g_capturing) ck(cudaEventRecordWithFlags(c->ev[k], c->stream, cudaEventRecordExternal), "cudaEventRecord");
+    else ck(cudaEventRecord(c->ev[k], c->stream), "cudaEventRecord");
 }
 
-int run_impl(eses_ctx *c)
+int grid_of(const eses_ctx *c, const Shape &s, int max_per_sm)
+{
+    int k = s.ctas_per_sm > 0 ? std::min(s.ctas_per_sm, max_per_sm) : max_per_sm;
+    long long g = (long long)std::max(k, 1) * c->n_sm;
+    long long need = ceil_div_ll(std::max(c->n_tiles, 1LL), std::max(s.tiles_per_pop, 1));
+    return (int)std::max(1LL, std::min(g, need));
+}
+
+TileSched sched_of(eses_ctx *c, const Shape &s, int which)
+{
+    TileSched q;
+    q.head = c->use_queue ? (unsigned long long *)c->queue.p + which : nullptr;
+    q.per = std::max(s.tiles_per_pop, 1);
+    return q;
+}
+
+// The device path of one run.  Planning (not capturing): reads list totals
+// and sizes every buffer; capturing: uses the planned sizes and touches no
+// host memory.  Returns the number of kernels launched.
+int run_device(eses_ctx *c)
 {
     cudaStream_t st = c->stream;
-    int nl = 0;  // kernels launched by this run
-    if (c->profile && !c->ev[0])
-        for (int k = 0; k <= NSTAGE; ++k) ck(cudaEventCreate(&c->ev[k]), "cudaEventCreate");
+    int nl = 0;
     Model &M = c->M;
-    Grid &G = c->G;
+    Batch &B = c->B;
     const int n = M.n_atoms;
-    const long long ncell = (long long)M.cn[0] * M.cn[1] * M.cn[2];
+    const long long ncell = c->ncell;
+    const long long nt = c->n_tiles;
     int *misc = ensure<int>(c->misc, 64);
     int *d_err = misc, *d_fail = misc + 1;
-    double *d_av = (double *)(misc + 8);
-    long long *d_counts = (long long *)(misc + 16);
+    unsigned long long *queue = ensure<unsigned long long>(c->queue, 4);
     ck(cudaMemsetAsync(misc, 0, 64 * sizeof(int), st), "memset");
+    ck(cudaMemsetAsync(queue, 0, 4 * sizeof(unsigned long long), st), "memset");
 
     mark(c, ST_BIN);
     // 1. cell binning (counting sort, deterministic within a cell)
@@ -290,18 +431,21 @@ int run_impl(eses_ctx *c)
     int *cursor = ensure<int>(c->cursor, ncell);
     int *orig = ensure<int>(c->atom_orig, n);
     double4 *atom = ensure<double4>(c->atom, n);
+    int *atom_mol = ensure<int>(c->atom_mol, n);
     ck(cudaMemsetAsync(cell_count, 0, sizeof(int) * ncell, st), "memset");
     ck(cudaMemsetAsync(cursor, 0, sizeof(int) * ncell, st), "memset");
-    nl += launch_cell_count((const double *)c->xyz.p, (const double *)c->rad.p, n, M.clo, M.cell, M.cn, cell_id, cell_count,
-                      st);
+    nl += launch_cell_count((const double *)c->xyz.p, (const int *)c->in_mol.p, n, M.cg, M.cell, cell_id, cell_count,
+                            st);
     nl += scan(c, cell_count, cell_start, ncell);
     nl += launch_cell_scatter(nullptr, nullptr, n, cell_id, cell_start, cursor, orig, st);
-    nl += launch_cell_finish((const double *)c->xyz.p, (const double *)c->rad.p, n, (int)ncell, cell_start, orig, atom, st);
+    nl += launch_cell_finish((const double *)c->xyz.p, (const double *)c->rad.p, (const int *)c->in_mol.p, (int)ncell,
+                             cell_start, orig, atom, atom_mol, st);
     M.atom = atom;
     M.atom_orig = orig;
+    M.atom_mol = atom_mol;
     M.cell_start = cell_start;
     float4 *ahi = ensure<float4>(c->atom_hi, n), *alo = ensure<float4>(c->atom_lo, n);
-    nl += launch_model_f32(M, 0, G.lo, ahi, alo, nullptr, st);
+    nl += launch_model_f32(M, 0, B.grid, ahi, alo, nullptr, st);
     M.atom_hi = ahi;
     M.atom_lo = alo;
 
@@ -313,7 +457,7 @@ int run_impl(eses_ctx *c)
     int *nb_start = ensure<int>(c->nb_start, n + 1);
     nl += launch_nb_count(M, nb_count, circle_count, contained, st);
     nl += scan(c, nb_count, nb_start, n);
-    int n_nb = read_total(c, nb_start, n);
+    const int n_nb = list_total(c, nb_start, n, c->n_nb);
     int *nb_list = ensure<int>(c->nb_list, std::max(n_nb, 1));
     M.nb_start = nb_start;
     M.nb_list = nb_list;
@@ -324,7 +468,7 @@ int run_impl(eses_ctx *c)
     int *pair_start = ensure<int>(c->pair_start, n + 1);
     nl += launch_pair_count(M, pair_count, st);
     nl += scan(c, pair_count, pair_start, n);
-    int np = read_total(c, pair_start, n);
+    const int np = list_total(c, pair_start, n, c->n_pairs);
     M.n_pairs = np;
     double4 *pair_o = ensure<double4>(c->pair_o, std::max(np, 1));
     double4 *pair_u = ensure<double4>(c->pair_u, std::max(np, 1));
@@ -335,7 +479,7 @@ int run_impl(eses_ctx *c)
     M.pair_ij = pair_ij;
     float4 *phi = ensure<float4>(c->pair_hi, std::max(np, 1)), *plo = ensure<float4>(c->pair_lo, std::max(np, 1));
     float4 *pu32 = ensure<float4>(c->pair_u32, std::max(np, 1));
-    nl += launch_model_f32(M, 1, G.lo, phi, plo, pu32, st);
+    nl += launch_model_f32(M, 1, B.grid, phi, plo, pu32, st);
     M.pair_hi = phi;
     M.pair_lo = plo;
     M.pair_u32 = pu32;
@@ -348,14 +492,16 @@ int run_impl(eses_ctx *c)
     nl += launch_arcs(M, pair_free, vert_count, st);
     M.pair_free = pair_free;
     nl += scan(c, vert_count, vert_start, np);
-    int nv = read_total(c, vert_start, np);
+    const int nv = list_total(c, vert_start, np, c->n_verts);
     M.n_verts = nv;
     double4 *vert = ensure<double4>(c->vert, std::max(nv, 1));
-    nl += launch_arcs_emit(M, vert_start, vert, st);
+    int *vert_mol = ensure<int>(c->vert_mol, std::max(nv, 1));
+    nl += launch_arcs_emit(M, vert_start, vert, vert_mol, st);
     M.vert = vert;
+    M.vert_mol = vert_mol;
 
     if (n >= (1 << 27) || np >= (1 << 27) || nv >= (1 << 27))
-        return fail(c, ESES_EINVAL, "more than 2^27 atoms, circle pairs or triple points");
+        throw std::string("more than 2^27 atoms, circle pairs or triple points");
     // 5. free faces
     uint8_t *face = ensure<uint8_t>(c->face, n);
     nl += launch_faces(M, circle_count, contained, face, st);
@@ -387,36 +533,40 @@ int run_impl(eses_ctx *c)
     M.vcell_start = vstart;
     M.vcell_list = vlist;
     float4 *vhi = ensure<float4>(c->vert_hi, std::max(nv, 1)), *vlo = ensure<float4>(c->vert_lo, std::max(nv, 1));
-    nl += launch_model_f32(M, 2, G.lo, vhi, vlo, nullptr, st);
+    nl += launch_model_f32(M, 2, B.grid, vhi, vlo, nullptr, st);
     M.vert_hi = vhi;
     M.vert_lo = vlo;
 
-    // 7. classification (+ FP64 band re-evaluation)
-    const long long npts = G.dims[0] * G.dims[1] * G.dims[2];
-    const long long nt = G.n_tiles;
-    int8_t *labels = ensure<int8_t>(c->labels, npts);
+    // 7. classification (+ FP64 band re-evaluation), persistent over all tiles
+    int8_t *labels = ensure<int8_t>(c->labels, c->n_points);
     int *tile_band = ensure<int>(c->tile_band, nt);
     mark(c, ST_CLASSIFY);
-    nl += launch_classify(M, G, c->precision, labels, c->precision == ESES_PREC_FP64 ? nullptr : tile_band, d_err, st);
+    nl += launch_classify(M, B, c->precision, sched_of(c, c->cls, 0),
+                          grid_of(c, c->cls, classify_ctas_per_sm(c->precision)), labels,
+                          c->precision == ESES_PREC_FP64 ? nullptr : tile_band, d_err, st);
     mark(c, ST_BAND);
-    if (c->precision != ESES_PREC_FP64) nl += launch_band(M, G, labels, tile_band, d_err, st);
+    if (c->precision != ESES_PREC_FP64) nl += launch_band(M, B, labels, tile_band, d_err, st);
 
     // 8. crossing edges, roots, area and volume
     int *tile_edges = ensure<int>(c->tile_edges, 3 * nt);
     int *edge_start = ensure<int>(c->edge_start, 3 * nt + 1);
     int *tile_inside = ensure<int>(c->tile_inside, 4 * nt);
+    long long *medge = ensure<long long>(c->medge, 3 * ((size_t)c->n_mol + 1));
     mark(c, ST_EDGE_COUNT);
-    nl += launch_edge_count(G, labels, tile_edges, tile_inside, st);
+    nl += launch_edge_count(B, labels, tile_edges, tile_inside, st);
     nl += scan(c, tile_edges, edge_start, 3 * nt);
-    std::vector<int> tot(4);
-    for (int a = 0; a < 3; ++a)
-        ck(cudaMemcpyAsync(&tot[a], edge_start + a * nt, sizeof(int), cudaMemcpyDeviceToHost, st), "read");
-    ck(cudaMemcpyAsync(&tot[3], edge_start + 3 * nt, sizeof(int), cudaMemcpyDeviceToHost, st), "read");
-    ck(cudaStreamSynchronize(st), "synchronize");
+    nl += launch_mol_edges(B, edge_start, medge, st);
+    if (!g_capturing) {
+        std::vector<int> tot(4);
+        for (int a = 0; a < 3; ++a)
+            ck(cudaMemcpyAsync(&tot[a], edge_start + a * nt, sizeof(int), cudaMemcpyDeviceToHost, st), "read");
+        ck(cudaMemcpyAsync(&tot[3], edge_start + 3 * nt, sizeof(int), cudaMemcpyDeviceToHost, st), "read");
+        ck(cudaStreamSynchronize(st), "synchronize");
+        for (int a = 0; a < 3; ++a) c->n_edges[a] = (long long)tot[a + 1] - tot[a];
+    }
     EdgeOut eo;
     for (int a = 0; a < 3; ++a) {
-        long long ne = (long long)tot[a + 1] - tot[a];
-        c->n_edges[a] = ne;
+        const long long ne = c->n_edges[a];
         eo.idx[a] = ensure<long long>(c->out_idx[a], std::max(ne, 1LL));
         eo.tau[a] = ensure<double>(c->out_tau[a], std::max(ne, 1LL));
         eo.nrm[a] = ensure<double>(c->out_nrm[a], 3 * std::max(ne, 1LL));
@@ -424,40 +574,58 @@ int run_impl(eses_ctx *c)
         eo.nrm32[a] = ensure<float>(c->out_nrm32[a], 3 * std::max(ne, 1LL));
         eo.code[a] = ensure<int2>(c->out_code[a], std::max(ne, 1LL));
     }
-    const long long nparts = polish_blocks(c->n_edges[0] + c->n_edges[1] + c->n_edges[2]);
-    double *part = ensure<double>(c->tile_area, 2 * std::max(nparts, 1LL));
-    mark(c, ST_EDGE_SOLVE);
+    const long long ne_all = c->n_edges[0] + c->n_edges[1] + c->n_edges[2];
+    double2 *term = ensure<double2>(c->term, std::max(ne_all, 1LL));
+    double *av = ensure<double>(c->av, 2 * (size_t)c->n_mol);
+    long long *cnt = ensure<long long>(c->counts, 2 * (size_t)c->n_mol);
     long long *fail_log = ensure<long long>(c->fail_log, FAIL_LOG * FAIL_REC);
-    nl += launch_edge_solve(M, G, c->precision, labels, edge_start, eo, d_fail, d_err, fail_log, st);
+    mark(c, ST_EDGE_SOLVE);
+    const int chunk = c->edge.chunk > 0 ? c->edge.chunk : edge_chunk_max();
+    nl += launch_edge_solve(M, B, c->precision, sched_of(c, c->edge, 1),
+                            grid_of(c, c->edge, edge_ctas_per_sm(c->precision)), chunk, labels, edge_start, eo, d_fail,
+                            d_err, fail_log, st);
     mark(c, ST_EDGE_POLISH);
-    nl += launch_edge_polish(M, G, eo, c->n_edges, part, st);
+    nl += launch_edge_polish(M, B, eo, ne_all, medge, term, st);
     mark(c, ST_REDUCE);
-    nl += launch_reduce(G, part, nparts, tile_inside, d_av, d_counts, st);
+    double *part_d = ensure<double>(c->red_d, (size_t)reduce_scratch(c->n_mol));
+    long long *part_i = ensure<long long>(c->red_i, (size_t)reduce_scratch(c->n_mol));
+    nl += launch_reduce(B, term, medge, tile_inside, part_d, part_i, av, cnt, st);
     mark(c, NSTAGE);
     ck(cudaGetLastError(), "kernel launch");
+    return nl;
+}
 
-    // results
+// results of the run just enqueued (host reads; waits for the device)
+int finish(eses_ctx *c, int nl)
+{
+    cudaStream_t st = c->stream;
+    const int nm = c->n_mol;
     int hmisc[64];
-    ck(cudaMemcpyAsync(hmisc, misc, sizeof(hmisc), cudaMemcpyDeviceToHost, st), "read results");
+    c->medge_h.assign(3 * ((size_t)nm + 1), 0);
+    c->av_h.assign(2 * (size_t)nm, 0.0);
+    c->cnt_h.assign(2 * (size_t)nm, 0);
+    ck(cudaMemcpyAsync(hmisc, c->misc.p, sizeof(hmisc), cudaMemcpyDeviceToHost, st), "read results");
+    ck(cudaMemcpyAsync(c->medge_h.data(), c->medge.p, sizeof(long long) * c->medge_h.size(), cudaMemcpyDeviceToHost, st),
+       "read results");
+    ck(cudaMemcpyAsync(c->av_h.data(), c->av.p, sizeof(double) * c->av_h.size(), cudaMemcpyDeviceToHost, st),
+       "read results");
+    ck(cudaMemcpyAsync(c->cnt_h.data(), c->counts.p, sizeof(long long) * c->cnt_h.size(), cudaMemcpyDeviceToHost, st),
+       "read results");
     ck(cudaStreamSynchronize(st), "synchronize");
     if (c->profile)
         for (int k = 0; k < NSTAGE; ++k) ck(cudaEventElapsedTime(&c->stage_ms[k], c->ev[k], c->ev[k + 1]), "elapsed");
-    double av[2];
-    memcpy(av, hmisc + 8, sizeof(av));
-    long long cnt[2];
-    memcpy(cnt, hmisc + 16, sizeof(cnt));
-    c->area = av[0];
-    c->volume = av[1];
-    c->stats[0] = npts;
-    c->stats[1] = nt;
+    long long inside = 0;
+    for (int m = 0; m < nm; ++m) inside += c->cnt_h[2 * m];
+    c->stats[0] = c->n_points;
+    c->stats[1] = c->n_tiles;
     c->stats[2] = 0;
-    c->stats[3] = np;
+    c->stats[3] = c->n_pairs;
     c->stats[4] = -1;  // filled on demand by eses_patch_counts
-    c->stats[5] = nv;
+    c->stats[5] = c->n_verts;
     c->stats[6] = 0;
     c->stats[7] = c->n_edges[0] + c->n_edges[1] + c->n_edges[2];
     c->stats[8] = hmisc[1];
-    c->stats[9] = cnt[0];
+    c->stats[9] = inside;
     c->stats[10] = nl;
     c->ran = true;
     int derr = hmisc[0];
@@ -471,6 +639,84 @@ int run_impl(eses_ctx *c)
     return ESES_OK;
 }
 
+int run_impl(eses_ctx *c)
+{
+    if (c->profile && !c->ev[0])
+        for (int k = 0; k <= NSTAGE; ++k) ck(cudaEventCreate(&c->ev[k]), "cudaEventCreate");
+    const bool replay = c->graph_on && c->planned && c->plan_precision == c->precision;
+    if (!replay) {
+        drop_graph(c);
+        const int nl = run_device(c);
+        c->planned = true;
+        c->plan_precision = c->precision;
+        return finish(c, nl);
+    }
+    if (!c->gexec) {
+        cudaGraph_t g = nullptr;
+        ck(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        g_capturing = true;
+        int nl = 0;
+        try {
+            nl = run_device(c);
+        } catch (...) {
+            g_capturing = false;
+            cudaStreamEndCapture(c->stream, &g);
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            throw;
+        }
+        g_capturing = false;
+        ck(cudaStreamEndCapture(c->stream, &g), "end capture");
+        cudaError_t e = cudaGraphInstantiate(&c->gexec, g, 0);
+        cudaGraphDestroy(g);
+        ck(e, "graph instantiate");
+        c->graph_launches = nl;
+    }
+    ck(cudaGraphLaunch(c->gexec, c->stream), "graph launch");
+    return finish(c, c->graph_launches);
+}
+
+int run_guarded(eses_ctx *c)
+{
+    c->ran = false;
+    try {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        return run_impl(c);
+    } catch (const CudaError &e) {
+        return fail(c, ESES_ECUDA, std::string(e.what) + ": " + cudaGetErrorString(e.e));
+    } catch (const std::bad_alloc &) {
+        return fail(c, ESES_ENOMEM, "device allocation failed");
+    } catch (const CaptureGrow &) {
+        drop_graph(c);
+        c->planned = false;
+        return fail(c, ESES_ESTATE, "buffer sizes changed under graph capture; run again to re-plan");
+    } catch (const std::string &m) {
+        return fail(c, ESES_EINVAL, m);
+    }
+}
+
+bool mol_ok(const eses_ctx *c, int m) { return c && m >= 0 && m < c->n_mol; }
+
+long long mol_points(const eses_ctx *c, int m)
+{
+    const MolInfo &I = c->mol[m];
+    return I.dims[0] * I.dims[1] * I.dims[2];
+}
+
+// first record and count of molecule m in axis a's output
+void mol_range(const eses_ctx *c, int m, int a, long long &off, long long &n)
+{
+    const long long *me = c->medge_h.data() + a * (c->n_mol + 1);
+    off = me[m];
+    n = me[m + 1] - me[m];
+}
+
+int single(eses_ctx *c)
+{
+    if (c && c->n_mol != 1) return fail(c, ESES_EINVAL, "batch context: use the eses_mol_* accessors");
+    return ESES_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -479,7 +725,8 @@ int eses_create(const double *xyz, const double *radii, int64_t n_atoms, double 
                 eses_ctx **out)
 {
     if (!xyz || !radii) return fail(nullptr, ESES_EINVAL, "xyz or radii is NULL");
-    return create_common(xyz, radii, n_atoms, r_p, h, margin, nullptr, nullptr, out);
+    if (n_atoms < 1 || n_atoms > (int64_t)1 << 30) return fail(nullptr, ESES_EINVAL, "n_atoms must be in [1, 2^30]");
+    return create_common(xyz, radii, &n_atoms, 1, r_p, h, margin, nullptr, nullptr, out);
 }
 
 int eses_create_device(const double *xyz, const double *radii, int64_t n_atoms, double r_p, double h, double margin,
@@ -493,7 +740,40 @@ int eses_create_device(const double *xyz, const double *radii, int64_t n_atoms, 
         cudaGetLastError();
         return fail(nullptr, ESES_EINVAL, "xyz/radii are not readable device memory");
     }
-    return create_common(hx.data(), hr.data(), n_atoms, r_p, h, margin, xyz, radii, out);
+    return create_common(hx.data(), hr.data(), &n_atoms, 1, r_p, h, margin, xyz, radii, out);
+}
+
+int eses_create_batch(const double *xyz, const double *radii, const int64_t *n_atoms, int n_mol, double r_p, double h,
+                      double margin, eses_ctx **out)
+{
+    if (!xyz || !radii || !n_atoms) return fail(nullptr, ESES_EINVAL, "xyz, radii or n_atoms is NULL");
+    return create_common(xyz, radii, n_atoms, n_mol, r_p, h, margin, nullptr, nullptr, out);
+}
+
+int eses_run_batch(int n_mol, const double *const *xyz, const double *const *radii, const int64_t *n_atoms,
+                   double r_p, double h, double margin, eses_ctx **out)
+{
+    if (!out) return fail(nullptr, ESES_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!xyz || !radii || !n_atoms || n_mol < 1) return fail(nullptr, ESES_EINVAL, "bad argument");
+    std::vector<double> X, R;
+    for (int m = 0; m < n_mol; ++m) {
+        if (!xyz[m] || !radii[m] || n_atoms[m] < 1)
+            return fail(nullptr, ESES_EINVAL, "bad molecule " + std::to_string(m));
+        X.insert(X.end(), xyz[m], xyz[m] + 3 * n_atoms[m]);
+        R.insert(R.end(), radii[m], radii[m] + n_atoms[m]);
+    }
+    eses_ctx *c = nullptr;
+    int rc = eses_create_batch(X.data(), R.data(), n_atoms, n_mol, r_p, h, margin, &c);
+    if (rc) return rc;
+    rc = run_guarded(c);
+    if (rc) {
+        g_create_error = c->err;
+        eses_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return ESES_OK;
 }
 
 int eses_set_option(eses_ctx *c, int key, int64_t value)
@@ -509,71 +789,306 @@ int eses_set_option(eses_ctx *c, int key, int64_t value)
         c->precision = (int)value;
         return ESES_OK;
     case ESES_OPT_STREAM:
+        drop_graph(c);
         c->stream = value ? (cudaStream_t)(intptr_t)value : c->own_stream;
         return ESES_OK;
     case ESES_OPT_SYNC:
         c->sync = value != 0;
         return ESES_OK;
     case ESES_OPT_PROFILE:
+        drop_graph(c);
         c->profile = value != 0;
+        return ESES_OK;
+    case ESES_OPT_GRAPH:
+        drop_graph(c);
+        c->graph_on = value != 0;
+        return ESES_OK;
+    case ESES_OPT_QUEUE:
+        drop_graph(c);
+        c->use_queue = value != 0;
+        return ESES_OK;
+    case ESES_OPT_CLS_CTAS:
+    case ESES_OPT_EDGE_CTAS:
+        if (value < 0 || value > 64) return fail(c, ESES_EINVAL, "CTAs per SM must be in [0, 64]");
+        drop_graph(c);
+        (key == ESES_OPT_CLS_CTAS ? c->cls : c->edge).ctas_per_sm = (int)value;
+        return ESES_OK;
+    case ESES_OPT_CLS_TILES:
+    case ESES_OPT_EDGE_TILES:
+        if (value < 1 || value > 64) return fail(c, ESES_EINVAL, "tiles per pop must be in [1, 64]");
+        drop_graph(c);
+        (key == ESES_OPT_CLS_TILES ? c->cls : c->edge).tiles_per_pop = (int)value;
+        return ESES_OK;
+    case ESES_OPT_EDGE_CHUNK:
+        if (value < 0 || value > edge_chunk_max())
+            return fail(c, ESES_EINVAL, "edge chunk must be in [0, " + std::to_string(edge_chunk_max()) + "]");
+        drop_graph(c);
+        c->edge.chunk = (int)value;
         return ESES_OK;
     default:
         return fail(c, ESES_EINVAL, "unknown option key " + std::to_string(key));
     }
 }
 
-int eses_run(eses_ctx *c)
+int eses_get_option(const eses_ctx *cc, int key, int64_t *value)
 {
-    if (!c) return fail(nullptr, ESES_EINVAL, "ctx is NULL");
-    c->ran = false;
-    try {
-        ck(cudaSetDevice(c->device), "cudaSetDevice");
-        return run_impl(c);
-    } catch (const CudaError &e) {
-        return fail(c, ESES_ECUDA, std::string(e.what) + ": " + cudaGetErrorString(e.e));
-    } catch (const std::bad_alloc &) {
-        return fail(c, ESES_ENOMEM, "device allocation failed");
+    eses_ctx *c = const_cast<eses_ctx *>(cc);
+    if (!c || !value) return fail(c, ESES_EINVAL, "NULL argument");
+    switch (key) {
+    case ESES_OPT_BLOCK_PTS: *value = c->block_pts; return ESES_OK;
+    case ESES_OPT_PRECISION: *value = c->precision; return ESES_OK;
+    case ESES_OPT_STREAM: *value = (int64_t)(intptr_t)c->stream; return ESES_OK;
+    case ESES_OPT_SYNC: *value = c->sync ? 1 : 0; return ESES_OK;
+    case ESES_OPT_PROFILE: *value = c->profile ? 1 : 0; return ESES_OK;
+    case ESES_OPT_GRAPH: *value = c->graph_on ? 1 : 0; return ESES_OK;
+    case ESES_OPT_QUEUE: *value = c->use_queue ? 1 : 0; return ESES_OK;
+    case ESES_OPT_CLS_CTAS: *value = c->cls.ctas_per_sm; return ESES_OK;
+    case ESES_OPT_EDGE_CTAS: *value = c->edge.ctas_per_sm; return ESES_OK;
+    case ESES_OPT_CLS_TILES: *value = c->cls.tiles_per_pop; return ESES_OK;
+    case ESES_OPT_EDGE_TILES: *value = c->edge.tiles_per_pop; return ESES_OK;
+    case ESES_OPT_EDGE_CHUNK: *value = c->edge.chunk; return ESES_OK;
+    default: return fail(c, ESES_EINVAL, "unknown option key " + std::to_string(key));
     }
 }
 
-int eses_grid(const eses_ctx *c, int64_t dims[3], double origin[3])
+int eses_run(eses_ctx *c)
 {
-    if (!c || !dims || !origin) return fail(nullptr, ESES_EINVAL, "NULL argument");
+    if (!c) return fail(nullptr, ESES_EINVAL, "ctx is NULL");
+    return run_guarded(c);
+}
+
+int eses_autotune(eses_ctx *c, int reps, double *ms_out)
+{
+    if (!c) return fail(nullptr, ESES_EINVAL, "ctx is NULL");
+    if (reps < 1 || reps > 100) return fail(c, ESES_EINVAL, "reps must be in [1, 100]");
+    const bool graph = c->graph_on;
+    c->graph_on = false;
+    drop_graph(c);
+    int rc = run_guarded(c);  // plans and leaves valid inputs for every stage
+    if (rc) {
+        c->graph_on = graph;
+        return rc;
+    }
+    try {
+        cudaStream_t st = c->stream;
+        cudaEvent_t e0, e1;
+        ck(cudaEventCreate(&e0), "event");
+        ck(cudaEventCreate(&e1), "event");
+        Model &M = c->M;
+        Batch &B = c->B;
+        int *misc = (int *)c->misc.p;
+        int8_t *labels = (int8_t *)c->labels.p;
+        int *tile_band = (int *)c->tile_band.p;
+        auto time_it = [&](auto &&launch) {
+            launch();
+            ck(cudaEventRecord(e0, st), "record");
+            for (int r = 0; r < reps; ++r) launch();
+            ck(cudaEventRecord(e1, st), "record");
+            ck(cudaEventSynchronize(e1), "sync");
+            float ms = 0.0f;
+            ck(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+            return ms / reps;
+        };
+        const int cls_max = classify_ctas_per_sm(c->precision), edge_max = edge_ctas_per_sm(c->precision);
+        // classification: CTAs per SM x tiles per pop (labels are rewritten identically)
+        Shape best_cls = c->cls;
+        float best_cls_ms = INFINITY;
+        for (int k = 1; k <= cls_max; ++k)
+            for (int per : {1, 4, 16}) {
+                Shape s;
+                s.ctas_per_sm = k;
+                s.tiles_per_pop = per;
+                float ms = time_it([&] {
+                    ck(cudaMemsetAsync(c->queue.p, 0, 4 * sizeof(unsigned long long), st), "memset");
+                    launch_classify(M, B, c->precision, sched_of(c, s, 0), grid_of(c, s, cls_max), labels,
+                                    c->precision == ESES_PREC_FP64 ? nullptr : tile_band, misc, st);
+                });
+                if (ms < best_cls_ms) best_cls_ms = ms, best_cls = s;
+            }
+        if (c->precision != ESES_PREC_FP64) launch_band(M, B, labels, tile_band, misc, st);
+        // root solve: CTAs per SM x tiles per pop x chunk
+        Shape best_edge = c->edge;
+        float best_edge_ms = INFINITY;
+        EdgeOut eo;
+        for (int a = 0; a < 3; ++a) {
+            eo.idx[a] = (long long *)c->out_idx[a].p;
+            eo.tau[a] = (double *)c->out_tau[a].p;
+            eo.nrm[a] = (double *)c->out_nrm[a].p;
+            eo.tau32[a] = (float *)c->out_tau32[a].p;
+            eo.nrm32[a] = (float *)c->out_nrm32[a].p;
+            eo.code[a] = (int2 *)c->out_code[a].p;
+        }
+        for (int k = 1; k <= edge_max; ++k)
+            for (int per : {1, 4})
+                for (int chunk : {16, 32, edge_chunk_max()}) {
+                    Shape s;
+                    s.ctas_per_sm = k;
+                    s.tiles_per_pop = per;
+                    s.chunk = chunk;
+                    float ms = time_it([&] {
+                        ck(cudaMemsetAsync(c->queue.p, 0, 4 * sizeof(unsigned long long), st), "memset");
+                        launch_edge_solve(M, B, c->precision, sched_of(c, s, 1), grid_of(c, s, edge_max), chunk,
+                                          labels, (const int *)c->edge_start.p, eo, misc + 1, misc,
+                                          (long long *)c->fail_log.p, st);
+                    });
+                    if (ms < best_edge_ms) best_edge_ms = ms, best_edge = s;
+                }
+        ck(cudaGetLastError(), "autotune launch");
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        c->cls = best_cls;
+        c->edge = best_edge;
+        if (ms_out) {
+            ms_out[0] = best_cls_ms;
+            ms_out[1] = best_edge_ms;
+        }
+    } catch (const CudaError &e) {
+        c->graph_on = graph;
+        return fail(c, ESES_ECUDA, std::string(e.what) + ": " + cudaGetErrorString(e.e));
+    }
+    c->graph_on = graph;
+    return run_guarded(c);  // fresh results with the chosen shapes
+}
+
+int eses_num_molecules(const eses_ctx *c, int *n)
+{
+    if (!c || !n) return fail(const_cast<eses_ctx *>(c), ESES_EINVAL, "NULL argument");
+    *n = c->n_mol;
+    return ESES_OK;
+}
+
+int eses_mol_grid(const eses_ctx *cc, int m, int64_t dims[3], double origin[3])
+{
+    eses_ctx *c = const_cast<eses_ctx *>(cc);
+    if (!mol_ok(c, m) || !dims || !origin) return fail(c, ESES_EINVAL, "bad argument");
     for (int a = 0; a < 3; ++a) {
-        dims[a] = c->dims[a];
-        origin[a] = c->lo[a];
+        dims[a] = c->mol[m].dims[a];
+        origin[a] = c->mol[m].lo[a];
     }
     return ESES_OK;
+}
+
+int eses_mol_labels(const eses_ctx *cc, int m, int8_t *out)
+{
+    eses_ctx *c = const_cast<eses_ctx *>(cc);
+    if (!mol_ok(c, m) || !out) return fail(c, ESES_EINVAL, "bad argument");
+    if (!c->ran) return fail(c, ESES_ESTATE, "no results: call eses_run first");
+    const size_t n = (size_t)mol_points(c, m);
+    if (cudaMemcpyAsync(out, (const int8_t *)c->labels.p + c->grids[m].lab0, n, cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return fail(c, ESES_ECUDA, "label copy failed");
+    return ESES_OK;
+}
+
+int eses_mol_labels_device(const eses_ctx *cc, int m, const int8_t **dptr)
+{
+    eses_ctx *c = const_cast<eses_ctx *>(cc);
+    if (!mol_ok(c, m) || !dptr) return fail(c, ESES_EINVAL, "bad argument");
+    if (!c->ran) return fail(c, ESES_ESTATE, "no results: call eses_run first");
+    *dptr = (const int8_t *)c->labels.p + c->grids[m].lab0;
+    return ESES_OK;
+}
+
+int eses_mol_num_intersections(const eses_ctx *cc, int m, int axis, int64_t *n)
+{
+    eses_ctx *c = const_cast<eses_ctx *>(cc);
+    if (!mol_ok(c, m) || !n || axis < 0 || axis > 2) return fail(c, ESES_EINVAL, "bad argument");
+    if (!c->ran) return fail(c, ESES_ESTATE, "no results: call eses_run first");
+    long long off, cnt;
+    mol_range(c, m, axis, off, cnt);
+    *n = cnt;
+    return ESES_OK;
+}
+
+int eses_mol_intersections(const eses_ctx *cc, int m, int axis, int64_t *lower_idx, double *tau, double *normal,
+                           float *tau32, float *normal32)
+{
+    eses_ctx *c = const_cast<eses_ctx *>(cc);
+    if (!mol_ok(c, m) || axis < 0 || axis > 2) return fail(c, ESES_EINVAL, "bad argument");
+    if (!c->ran) return fail(c, ESES_ESTATE, "no results: call eses_run first");
+    long long off, cnt;
+    mol_range(c, m, axis, off, cnt);
+    const size_t ne = (size_t)cnt;
+    if (ne == 0) return ESES_OK;
+    cudaStream_t st = c->stream;
+    bool ok = true;
+    if (lower_idx)
+        ok &= cudaMemcpyAsync(lower_idx, (const long long *)c->out_idx[axis].p + off, ne * 8, cudaMemcpyDeviceToHost,
+                              st) == cudaSuccess;
+    if (tau)
+        ok &= cudaMemcpyAsync(tau, (const double *)c->out_tau[axis].p + off, ne * 8, cudaMemcpyDeviceToHost, st) ==
+              cudaSuccess;
+    if (normal)
+        ok &= cudaMemcpyAsync(normal, (const double *)c->out_nrm[axis].p + 3 * off, ne * 24, cudaMemcpyDeviceToHost,
+                              st) == cudaSuccess;
+    if (tau32)
+        ok &= cudaMemcpyAsync(tau32, (const float *)c->out_tau32[axis].p + off, ne * 4, cudaMemcpyDeviceToHost, st) ==
+              cudaSuccess;
+    if (normal32)
+        ok &= cudaMemcpyAsync(normal32, (const float *)c->out_nrm32[axis].p + 3 * off, ne * 12,
+                              cudaMemcpyDeviceToHost, st) == cudaSuccess;
+    ok &= cudaStreamSynchronize(st) == cudaSuccess;
+    if (!ok) return fail(c, ESES_ECUDA, "intersection copy failed");
+    return ESES_OK;
+}
+
+int eses_mol_intersections_device(const eses_ctx *cc, int m, int axis, const int64_t **lower_idx, const double **tau,
+                                  const double **normal, const float **tau32, const float **normal32)
+{
+    eses_ctx *c = const_cast<eses_ctx *>(cc);
+    if (!mol_ok(c, m) || axis < 0 || axis > 2) return fail(c, ESES_EINVAL, "bad argument");
+    if (!c->ran) return fail(c, ESES_ESTATE, "no results: call eses_run first");
+    long long off, cnt;
+    mol_range(c, m, axis, off, cnt);
+    if (lower_idx) *lower_idx = (const int64_t *)c->out_idx[axis].p + off;
+    if (tau) *tau = (const double *)c->out_tau[axis].p + off;
+    if (normal) *normal = (const double *)c->out_nrm[axis].p + 3 * off;
+    if (tau32) *tau32 = (const float *)c->out_tau32[axis].p + off;
+    if (normal32) *normal32 = (const float *)c->out_nrm32[axis].p + 3 * off;
+    return ESES_OK;
+}
+
+int eses_mol_area_volume(const eses_ctx *cc, int m, double *area, double *volume)
+{
+    eses_ctx *c = const_cast<eses_ctx *>(cc);
+    if (!mol_ok(c, m) || !area || !volume) return fail(c, ESES_EINVAL, "bad argument");
+    if (!c->ran) return fail(c, ESES_ESTATE, "no results: call eses_run first");
+    *area = c->av_h[2 * m];
+    *volume = c->av_h[2 * m + 1];
+    return ESES_OK;
+}
+
+int eses_grid(const eses_ctx *cc, int64_t dims[3], double origin[3])
+{
+    eses_ctx *c = const_cast<eses_ctx *>(cc);
+    if (!c || !dims || !origin) return fail(c, ESES_EINVAL, "NULL argument");
+    if (int rc = single(c)) return rc;
+    return eses_mol_grid(c, 0, dims, origin);
 }
 
 int eses_labels(const eses_ctx *cc, int8_t *out)
 {
     eses_ctx *c = const_cast<eses_ctx *>(cc);
     if (!c || !out) return fail(c, ESES_EINVAL, "NULL argument");
-    if (!c->ran) return fail(c, ESES_ESTATE, "no results: call eses_run first");
-    size_t n = (size_t)(c->dims[0] * c->dims[1] * c->dims[2]);
-    if (cudaMemcpyAsync(out, c->labels.p, n, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
-        cudaStreamSynchronize(c->stream) != cudaSuccess)
-        return fail(c, ESES_ECUDA, "label copy failed");
-    return ESES_OK;
+    if (int rc = single(c)) return rc;
+    return eses_mol_labels(c, 0, out);
 }
 
 int eses_labels_device(const eses_ctx *cc, const int8_t **dptr)
 {
     eses_ctx *c = const_cast<eses_ctx *>(cc);
     if (!c || !dptr) return fail(c, ESES_EINVAL, "NULL argument");
-    if (!c->ran) return fail(c, ESES_ESTATE, "no results: call eses_run first");
-    *dptr = (const int8_t *)c->labels.p;
-    return ESES_OK;
+    if (int rc = single(c)) return rc;
+    return eses_mol_labels_device(c, 0, dptr);
 }
 
 int eses_num_intersections(const eses_ctx *cc, int axis, int64_t *n)
 {
     eses_ctx *c = const_cast<eses_ctx *>(cc);
     if (!c || !n || axis < 0 || axis > 2) return fail(c, ESES_EINVAL, "bad argument");
-    if (!c->ran) return fail(c, ESES_ESTATE, "no results: call eses_run first");
-    *n = c->n_edges[axis];
-    return ESES_OK;
+    if (int rc = single(c)) return rc;
+    return eses_mol_num_intersections(c, 0, axis, n);
 }
 
 int eses_intersections(const eses_ctx *cc, int axis, int64_t *lower_idx, double *tau, double *normal, float *tau32,
@@ -581,20 +1096,8 @@ int eses_intersections(const eses_ctx *cc, int axis, int64_t *lower_idx, double 
 {
     eses_ctx *c = const_cast<eses_ctx *>(cc);
     if (!c || axis < 0 || axis > 2) return fail(c, ESES_EINVAL, "bad argument");
-    if (!c->ran) return fail(c, ESES_ESTATE, "no results: call eses_run first");
-    size_t ne = (size_t)c->n_edges[axis];
-    if (ne == 0) return ESES_OK;
-    cudaStream_t st = c->stream;
-    bool ok = true;
-    if (lower_idx) ok &= cudaMemcpyAsync(lower_idx, c->out_idx[axis].p, ne * 8, cudaMemcpyDeviceToHost, st) == cudaSuccess;
-    if (tau) ok &= cudaMemcpyAsync(tau, c->out_tau[axis].p, ne * 8, cudaMemcpyDeviceToHost, st) == cudaSuccess;
-    if (normal) ok &= cudaMemcpyAsync(normal, c->out_nrm[axis].p, ne * 24, cudaMemcpyDeviceToHost, st) == cudaSuccess;
-    if (tau32) ok &= cudaMemcpyAsync(tau32, c->out_tau32[axis].p, ne * 4, cudaMemcpyDeviceToHost, st) == cudaSuccess;
-    if (normal32)
-        ok &= cudaMemcpyAsync(normal32, c->out_nrm32[axis].p, ne * 12, cudaMemcpyDeviceToHost, st) == cudaSuccess;
-    ok &= cudaStreamSynchronize(st) == cudaSuccess;
-    if (!ok) return fail(c, ESES_ECUDA, "intersection copy failed");
-    return ESES_OK;
+    if (int rc = single(c)) return rc;
+    return eses_mol_intersections(c, 0, axis, lower_idx, tau, normal, tau32, normal32);
 }
 
 int eses_intersections_device(const eses_ctx *cc, int axis, const int64_t **lower_idx, const double **tau,
@@ -602,23 +1105,16 @@ int eses_intersections_device(const eses_ctx *cc, int axis, const int64_t **lowe
 {
     eses_ctx *c = const_cast<eses_ctx *>(cc);
     if (!c || axis < 0 || axis > 2) return fail(c, ESES_EINVAL, "bad argument");
-    if (!c->ran) return fail(c, ESES_ESTATE, "no results: call eses_run first");
-    if (lower_idx) *lower_idx = (const int64_t *)c->out_idx[axis].p;
-    if (tau) *tau = (const double *)c->out_tau[axis].p;
-    if (normal) *normal = (const double *)c->out_nrm[axis].p;
-    if (tau32) *tau32 = (const float *)c->out_tau32[axis].p;
-    if (normal32) *normal32 = (const float *)c->out_nrm32[axis].p;
-    return ESES_OK;
+    if (int rc = single(c)) return rc;
+    return eses_mol_intersections_device(c, 0, axis, lower_idx, tau, normal, tau32, normal32);
 }
 
 int eses_area_volume(const eses_ctx *cc, double *area, double *volume)
 {
     eses_ctx *c = const_cast<eses_ctx *>(cc);
     if (!c || !area || !volume) return fail(c, ESES_EINVAL, "NULL argument");
-    if (!c->ran) return fail(c, ESES_ESTATE, "no results: call eses_run first");
-    *area = c->area;
-    *volume = c->volume;
-    return ESES_OK;
+    if (int rc = single(c)) return rc;
+    return eses_mol_area_volume(c, 0, area, volume);
 }
 
 int eses_stats(const eses_ctx *cc, int64_t *out, int n)
@@ -720,15 +1216,17 @@ const char *eses_last_error(const eses_ctx *c)
 void eses_destroy(eses_ctx *c)
 {
     if (!c) return;
-    DBuf *bufs[] = {&c->xyz, &c->rad, &c->cell_id, &c->cell_count, &c->cell_start, &c->cursor, &c->atom_orig,
-                    &c->atom, &c->nb_count, &c->nb_start, &c->nb_list, &c->circle_count, &c->contained, &c->face,
-                    &c->pair_count, &c->pair_start, &c->pair_o, &c->pair_u, &c->pair_ij, &c->pair_free,
-                    &c->vert_count, &c->vert_start, &c->vert, &c->pbin_count, &c->pbin_start, &c->pbin_cursor,
-                    &c->pbin_cell, &c->pbin_list, &c->vbin_count, &c->vbin_start, &c->vbin_cursor, &c->vbin_cell,
-                    &c->vbin_list, &c->labels, &c->tile_band, &c->tile_edges, &c->edge_start, &c->tile_inside,
-                    &c->tile_area, &c->tile_vol, &c->scan_tmp, &c->misc, &c->fail_log,
-                    &c->atom_hi, &c->atom_lo, &c->pair_hi, &c->pair_lo, &c->pair_u32, &c->vert_hi, &c->vert_lo};
+    DBuf *bufs[] = {&c->xyz, &c->rad, &c->in_mol, &c->grid_d, &c->cg_d, &c->tile_off_d, &c->atom_mol, &c->vert_mol,
+                    &c->medge, &c->term, &c->queue, &c->cell_id, &c->cell_count, &c->cell_start, &c->cursor,
+                    &c->atom_orig, &c->atom, &c->nb_count, &c->nb_start, &c->nb_list, &c->circle_count,
+                    &c->contained, &c->face, &c->pair_count, &c->pair_start, &c->pair_o, &c->pair_u, &c->pair_ij,
+                    &c->pair_free, &c->vert_count, &c->vert_start, &c->vert, &c->pbin_count, &c->pbin_start,
+                    &c->pbin_cursor, &c->pbin_cell, &c->pbin_list, &c->vbin_count, &c->vbin_start, &c->vbin_cursor,
+                    &c->vbin_cell, &c->vbin_list, &c->labels, &c->tile_band, &c->tile_edges, &c->edge_start,
+                    &c->tile_inside, &c->scan_tmp, &c->misc, &c->av, &c->counts, &c->red_d, &c->red_i, &c->fail_log, &c->atom_hi,
+                    &c->atom_lo, &c->pair_hi, &c->pair_lo, &c->pair_u32, &c->vert_hi, &c->vert_lo};
     if (c->own_stream) cudaStreamSynchronize(c->own_stream);
+    drop_graph(c);
     for (DBuf *b : bufs) free_buf(*b);
     for (int a = 0; a < 3; ++a) {
         free_buf(c->out_idx[a]);

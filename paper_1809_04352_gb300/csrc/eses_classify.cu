@@ -167,19 +167,31 @@ __device__ int shell_label(const TileS<T> &S, const ClsSmem &C, int brick, T x, 
 }
 
 template <class T, bool FILT>
-__global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Grid G, int8_t *__restrict__ labels,
+__global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Batch B, TileSched Q, int8_t *__restrict__ labels_all,
                                                           int *__restrict__ tile_band, int *__restrict__ err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileS<T> &S = *reinterpret_cast<TileS<T> *>(smem_raw);
     ClsSmem &C = *reinterpret_cast<ClsSmem *>(smem_raw + ((sizeof(TileS<T>) + 15) & ~(size_t)15));
+    __shared__ long long q_base;
+    __shared__ Grid sG;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const T rp = (T)M.rp;
-    const T d0 = FILT ? (T)G.d0 : T(0);
-    const T h = (T)G.h;
-    for (long long tile = blockIdx.x; tile < G.n_tiles; tile += gridDim.x) {
+    long long iter = 0;
+    for (;;) {
+      const long long base = next_tiles(Q, iter, &q_base);
+      if (base >= B.n_tiles) break;
+      const long long bend = min(base + (long long)Q.per, B.n_tiles);
+      for (long long gt = base; gt < bend; ++gt) {
+        const int mol = mol_of_tile(B, gt);
+        load_grid(B, mol, sG);
+        const Grid &G = sG;
+        const long long tile = gt - G.tile0;
+        int8_t *__restrict__ labels = labels_all + G.lab0;
+        const T d0 = FILT ? (T)G.d0 : T(0);
+        const T h = (T)G.h;
         double x0[3];
-        stage_tile<T>(M, G, tile, S, x0);
+        stage_tile<T>(M, G, mol, tile, S, x0);
         if (threadIdx.x == 0) {
             C.nq = 0;
             C.band = 0;
@@ -195,7 +207,7 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Grid G, int8_
                 if (gi < G.dims[0] && gj < G.dims[1] && gk < G.dims[2])
                     labels[(gi * G.dims[1] + gj) * G.dims[2] + gk] = LABEL_OUT;
             }
-            if (threadIdx.x == 0 && tile_band) tile_band[tile] = 0;
+            if (threadIdx.x == 0 && tile_band) tile_band[gt] = 0;
             __syncthreads();
             continue;
         }
@@ -273,20 +285,27 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Grid G, int8_
             if (FILT && lab == LABEL_BAND) atomicAdd(&C.band, 1);
         }
         __syncthreads();
-        if (threadIdx.x == 0 && tile_band) tile_band[tile] = C.band;
+        if (threadIdx.x == 0 && tile_band) tile_band[gt] = C.band;
         __syncthreads();
+      }
     }
 }
 
-__global__ void __launch_bounds__(CLS_THREADS) k_band(Model M, Grid G, int8_t *__restrict__ labels,
+__global__ void __launch_bounds__(CLS_THREADS) k_band(Model M, Batch B, int8_t *__restrict__ labels_all,
                                                       const int *__restrict__ tile_band, int *__restrict__ err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileS<double> &S = *reinterpret_cast<TileS<double> *>(smem_raw);
-    for (long long tile = blockIdx.x; tile < G.n_tiles; tile += gridDim.x) {
-        if (tile_band[tile] == 0) continue;  // uniform across the block
+    __shared__ Grid sG;
+    for (long long gt = blockIdx.x; gt < B.n_tiles; gt += gridDim.x) {
+        if (tile_band[gt] == 0) continue;  // uniform across the block
+        const int mol = mol_of_tile(B, gt);
+        load_grid(B, mol, sG);
+        const Grid &G = sG;
+        const long long tile = gt - G.tile0;
+        int8_t *__restrict__ labels = labels_all + G.lab0;
         double x0[3];
-        stage_tile<double>(M, G, tile, S, x0);
+        stage_tile<double>(M, G, mol, tile, S, x0);
         if (threadIdx.x == 0 && S.flags) atomicOr(err, S.flags);
         int t[3];
         tile_coords(G, tile, t);
@@ -317,26 +336,43 @@ static size_t cls_smem()
     return ((sizeof(TileS<T>) + 15) & ~(size_t)15) + sizeof(ClsSmem);
 }
 
-int launch_classify(const Model &M, const Grid &G, int precision, int8_t *labels, int *tile_band, int *err,
-                    cudaStream_t st)
+// dynamic shared memory limits (once per device, before any launch or capture)
+void classify_init()
 {
+    cudaFuncSetAttribute(k_classify<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cls_smem<double>());
+    cudaFuncSetAttribute(k_classify<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cls_smem<float>());
+    cudaFuncSetAttribute(k_band, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileS<double>));
+}
+
+int classify_ctas_per_sm(int precision)
+{
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    if (precision == 0)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_classify<double, false>, CLS_THREADS, cls_smem<double>());
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_classify<float, true>, CLS_THREADS, cls_smem<float>());
+    return n > 0 ? n : 1;
+}
+
+int launch_classify(const Model &M, const Batch &B, int precision, const TileSched &Q, int grid, int8_t *labels,
+                    int *tile_band, int *err, cudaStream_t st)
+{
+    if (grid < 1) grid = 1;
     if (precision == 0) {
         size_t sm = cls_smem<double>();
-        cudaFuncSetAttribute(k_classify<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_classify<double, false><<<grid_size(G.n_tiles), CLS_THREADS, sm, st>>>(M, G, labels, tile_band, err);
+        k_classify<double, false><<<grid, CLS_THREADS, sm, st>>>(M, B, Q, labels, tile_band, err);
     } else {
         size_t sm = cls_smem<float>();
-        cudaFuncSetAttribute(k_classify<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_classify<float, true><<<grid_size(G.n_tiles), CLS_THREADS, sm, st>>>(M, G, labels, tile_band, err);
+        k_classify<float, true><<<grid, CLS_THREADS, sm, st>>>(M, B, Q, labels, tile_band, err);
     }
     return 1;
 }
 
-int launch_band(const Model &M, const Grid &G, int8_t *labels, const int *tile_band, int *err, cudaStream_t st)
+int launch_band(const Model &M, const Batch &B, int8_t *labels, const int *tile_band, int *err, cudaStream_t st)
 {
     size_t sm = sizeof(TileS<double>);
-    cudaFuncSetAttribute(k_band, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_band<<<grid_size(G.n_tiles), CLS_THREADS, sm, st>>>(M, G, labels, tile_band, err);
+    k_band<<<grid_size(B.n_tiles), CLS_THREADS, sm, st>>>(M, B, labels, tile_band, err);
     return 1;
 }
 

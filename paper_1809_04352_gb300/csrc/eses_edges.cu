@@ -27,7 +27,9 @@
 // k_edge_polish: one thread per crossing edge (full warps of FP64 work): the
 //   FP64 root of the chosen piece next to the recorded one, the normal, the
 //   outputs and the area/volume terms.
-// k_reduce: area = h^2 sum |n_a|, volume = h^2/3 sum of inside lengths.
+// k_reduce: per molecule, area = h^2 sum |n_a|, volume = h^2/3 sum of
+//   inside lengths.
+// Every tile kernel runs over the tiles of all molecules of a batch.
 #include <math.h>
 
 #include "eses_kernels.h"
@@ -827,14 +829,19 @@ __device__ __forceinline__ double block_sum_double(double v, double *sh)
     return tot;
 }
 
-__global__ void __launch_bounds__(EDGE_THREADS) k_edge_count(Grid G, const int8_t *__restrict__ labels,
+__global__ void __launch_bounds__(EDGE_THREADS) k_edge_count(Batch B, const int8_t *__restrict__ labels_all,
                                                              int *__restrict__ tile_edges,
                                                              int *__restrict__ tile_inside)
 {
     __shared__ int sh[EDGE_THREADS / 32];
-    const long long nt = G.n_tiles;
-    const long long st1 = G.dims[2], st0 = G.dims[1] * G.dims[2];
-    for (long long tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    __shared__ Grid sG;
+    const long long nt = B.n_tiles;
+    for (long long gt = blockIdx.x; gt < nt; gt += gridDim.x) {
+        load_grid(B, mol_of_tile(B, gt), sG);
+        const Grid &G = sG;
+        const long long tile = gt - G.tile0;
+        const int8_t *__restrict__ labels = labels_all + G.lab0;
+        const long long st1 = G.dims[2], st0 = G.dims[1] * G.dims[2];
         int t[3];
         tile_coords(G, tile, t);
         int ce[3] = {0, 0, 0}, ci[3] = {0, 0, 0}, npin = 0;
@@ -857,13 +864,24 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_count(Grid G, const int8_
             int e = block_sum_int(ce[a], sh);
             int i = block_sum_int(ci[a], sh);
             if (threadIdx.x == 0) {
-                tile_edges[a * nt + tile] = e;
-                tile_inside[a * nt + tile] = i;
+                tile_edges[a * nt + gt] = e;
+                tile_inside[a * nt + gt] = i;
             }
         }
         int pin = block_sum_int(npin, sh);
-        if (threadIdx.x == 0) tile_inside[3 * nt + tile] = pin;
+        if (threadIdx.x == 0) tile_inside[3 * nt + gt] = pin;
     }
+}
+
+// per axis, the first crossing edge of every molecule in the axis' output
+// (medge[a * (n_mol + 1) + m]; m = n_mol gives the axis total)
+__global__ void k_mol_edges(Batch B, const int *__restrict__ edge_start, long long *__restrict__ medge)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 3 * (B.n_mol + 1)) return;
+    const int a = k / (B.n_mol + 1), m = k % (B.n_mol + 1);
+    const long long nt = B.n_tiles;
+    medge[k] = (long long)edge_start[a * nt + B.tile_off[m]] - edge_start[a * nt];
 }
 
 __device__ __forceinline__ int block_excl_scan_e(int v, int *sh, int *total)
@@ -888,7 +906,8 @@ __device__ __forceinline__ int block_excl_scan_e(int v, int *sh, int *total)
 }
 
 template <class T, bool FILT>
-__global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Grid G, const int8_t *__restrict__ labels,
+__global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Batch B, TileSched Q, int chunk0,
+                                                             const int8_t *__restrict__ labels_all,
                                                              const int *__restrict__ edge_start, EdgeOut out,
                                                              int *__restrict__ n_fail, int *__restrict__ err,
                                                              long long *__restrict__ fail_log)
@@ -896,18 +915,32 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Grid G, co
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileS<T> &S = *reinterpret_cast<TileS<T> *>(smem_raw);
     EdgeSmem &E = *reinterpret_cast<EdgeSmem *>(smem_raw + ((sizeof(TileS<T>) + 15) & ~(size_t)15));
-    const long long nt = G.n_tiles;
-    const long long st1 = G.dims[2], st0 = G.dims[1] * G.dims[2];
-    const double h = G.h, rp = M.rp;
+    __shared__ long long q_base;
+    __shared__ Grid sG;
+    const long long nt = B.n_tiles;
+    const double rp = M.rp;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const T d0 = FILT ? (T)G.d0 : T(0);
-    const T hT = (T)h, rpT = (T)rp, mg = FILT ? T(2e-3) : T(0);
-    for (long long tile = blockIdx.x; tile < nt; tile += gridDim.x) {
+    const T rpT = (T)rp, mg = FILT ? T(2e-3) : T(0);
+    long long iter = 0;
+    for (;;) {
+      const long long base = next_tiles(Q, iter, &q_base);
+      if (base >= nt) break;
+      const long long bend = min(base + (long long)Q.per, nt);
+      for (long long gt = base; gt < bend; ++gt) {
         int tot = 0;
-        for (int a = 0; a < 3; ++a) tot += edge_start[a * nt + tile + 1] - edge_start[a * nt + tile];
+        for (int a = 0; a < 3; ++a) tot += edge_start[a * nt + gt + 1] - edge_start[a * nt + gt];
         if (tot == 0) continue;
+        const int mol = mol_of_tile(B, gt);
+        load_grid(B, mol, sG);
+        const Grid &G = sG;
+        const long long tile = gt - G.tile0;
+        const int8_t *__restrict__ labels = labels_all + G.lab0;
+        const long long st1 = G.dims[2], st0 = G.dims[1] * G.dims[2];
+        const double h = G.h;
+        const T d0 = FILT ? (T)G.d0 : T(0);
+        const T hT = (T)h;
         double x0[3];
-        stage_tile<T>(M, G, tile, S, x0);
+        stage_tile<T>(M, G, mol, tile, S, x0);
         if (threadIdx.x == 0 && S.flags) atomicOr(err, S.flags);
         int t[3];
         tile_coords(G, tile, t);
@@ -940,7 +973,7 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Grid G, co
                 if (flag[k]) E.eptr[base + rank++] = (short)(2 * threadIdx.x + k);
             if (threadIdx.x == 0) {
                 E.estart[a + 1] = base + tsum;
-                E.ebase[a] = (long long)edge_start[a * nt + tile] - edge_start[a * nt];
+                E.ebase[a] = (long long)edge_start[a * nt + gt] - edge_start[a * nt];
             }
             __syncthreads();
         }
@@ -948,7 +981,7 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Grid G, co
         const int nitem = S.na + S.nv + S.np;
         // chunks of edges; a chunk whose candidates or roots overflow the pools
         // is retried at half the size
-        int c0 = 0, csz = CHUNK;
+        int c0 = 0, csz = chunk0;
         while (c0 < ne) {
             const int c1 = min(ne, c0 + csz);
             if (threadIdx.x == 0) {
@@ -1051,6 +1084,7 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Grid G, co
                                 rec[6] = S.np;
                                 rec[7] = S.nv;
                                 rec[8] = E.ncand[warp];
+                                rec[23] = mol;
                                 for (int z = 0; z < 7 && z < E.ncand[warp] && z < WCAND; ++z) {
                                     rec[9 + z] = (long long)((double)E.cand[warp][z].t * 1e9);
                                     rec[16 + z] = E.cand[warp][z].kind;
@@ -1069,26 +1103,37 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Grid G, co
             }
             __syncthreads();
             c0 = c1;
-            csz = CHUNK;
+            csz = chunk0;
         }
         __syncthreads();
+      }
     }
 }
 
 // One thread per crossing edge, over the three axes: FP64 root of the chosen
 // piece next to the recorded FP32 root, normal, outputs, area/volume terms
 // (block partial sums in fixed order).
-__global__ void __launch_bounds__(POLISH_THREADS) k_edge_polish(Model M, Grid G, EdgeOut out, long long n0,
-                                                                long long n1, long long n2,
-                                                                double *__restrict__ part)
+__global__ void __launch_bounds__(POLISH_THREADS) k_edge_polish(Model M, Batch B, EdgeOut out,
+                                                                const long long *__restrict__ medge,
+                                                                double2 *__restrict__ term)
 {
-    __shared__ double sha[POLISH_THREADS / 32], shv[POLISH_THREADS / 32];
     const long long e = (long long)blockIdx.x * POLISH_THREADS + threadIdx.x;
-    const double h = G.h, rp = M.rp;
-    double area = 0.0, vol = 0.0;
+    const int nm = B.n_mol;
+    const long long n0 = medge[nm], n1 = medge[2 * nm + 1], n2 = medge[3 * nm + 2];
+    const double rp = M.rp;
     if (e < n0 + n1 + n2) {
         const int a = e < n0 ? 0 : (e < n0 + n1 ? 1 : 2);
         const long long o = e - (a == 0 ? 0 : (a == 1 ? n0 : n0 + n1));
+        // molecule of the edge: its axis output is molecule-major
+        const long long *me = medge + a * (nm + 1);
+        int lo = 0, hi = nm;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (me[mid] <= o) lo = mid;
+            else hi = mid;
+        }
+        const Grid &G = B.grid[lo];
+        const double h = G.h;
         const long long idx = out.idx[a][o];
         const int2 code = out.code[a][o];
         const float t32 = __int_as_float(code.x);
@@ -1129,46 +1174,43 @@ __global__ void __launch_bounds__(POLISH_THREADS) k_edge_polish(Model M, Grid G,
         out.nrm32[a][3 * o + 0] = (float)n[0];
         out.nrm32[a][3 * o + 1] = (float)n[1];
         out.nrm32[a][3 * o + 2] = (float)n[2];
-        area = h * h * fabs(n[a]);
-        vol = lab_s ? t : h - t;
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-        area += __shfl_down_sync(0xffffffffu, area, off);
-        vol += __shfl_down_sync(0xffffffffu, vol, off);
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) {
-        sha[wid] = area;
-        shv[wid] = vol;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double A = 0.0, V = 0.0;
-        for (int k = 0; k < POLISH_THREADS / 32; ++k) {
-            A += sha[k];
-            V += shv[k];
-        }
-        part[2 * blockIdx.x] = A;
-        part[2 * blockIdx.x + 1] = V;
+        // Crofton area term and the inside length of the edge (C9)
+        term[e] = make_double2(h * h * fabs(n[a]), lab_s ? t : h - t);
     }
 }
 
-// single-block deterministic reduction: out2 = {area, volume};
-// counts = {inside points, inside edges (all axes)}
-__global__ void __launch_bounds__(1024) k_reduce(Grid G, const double *__restrict__ part, long long nparts,
-                                                 const int *__restrict__ tile_inside, double *__restrict__ out2,
-                                                 long long *__restrict__ counts)
+// Area/volume reduction in two fixed-order levels (deterministic): block
+// (m, g) of k_reduce_part sums the terms of molecule m whose index within the
+// molecule's range is g (mod RED_PARTS * blockDim), in a fixed tree;
+// k_reduce_final adds the RED_PARTS partials of each molecule in order.
+constexpr int RED_PARTS = 16;
+constexpr int RED_THREADS = 512;
+
+__global__ void __launch_bounds__(RED_THREADS) k_reduce_part(Batch B, const double2 *__restrict__ term,
+                                                             const long long *__restrict__ medge,
+                                                             const int *__restrict__ tile_inside,
+                                                             double *__restrict__ part_d,
+                                                             long long *__restrict__ part_i)
 {
     __shared__ double sa[32], sv[32];
     __shared__ long long si[32], sp[32];
-    const long long nt = G.n_tiles;
+    const int m = blockIdx.x / RED_PARTS, g = blockIdx.x % RED_PARTS, nm = B.n_mol;
+    const long long nt = B.n_tiles;
+    const long long stride = (long long)RED_PARTS * RED_THREADS;
+    const long long first = (long long)g * RED_THREADS + threadIdx.x;
     double a = 0.0, v = 0.0;
     long long ie = 0, pin = 0;
-    for (long long k = threadIdx.x; k < nparts; k += blockDim.x) {
-        a += part[2 * k];
-        v += part[2 * k + 1];
+    long long axis_base = 0;
+    for (int ax = 0; ax < 3; ++ax) {
+        const long long *me = medge + ax * (nm + 1);
+        for (long long k = me[m] + first; k < me[m + 1]; k += stride) {
+            const double2 w = term[axis_base + k];
+            a += w.x;
+            v += w.y;
+        }
+        axis_base += me[nm];
     }
-    for (long long k = threadIdx.x; k < nt; k += blockDim.x) {
+    for (long long k = B.tile_off[m] + first; k < B.tile_off[m + 1]; k += stride) {
         ie += (long long)tile_inside[k] + tile_inside[nt + k] + tile_inside[2 * nt + k];
         pin += tile_inside[3 * nt + k];
     }
@@ -1189,17 +1231,39 @@ __global__ void __launch_bounds__(1024) k_reduce(Grid G, const double *__restric
     if (threadIdx.x == 0) {
         double A = 0.0, V = 0.0;
         long long IE = 0, P = 0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+        for (int k = 0; k < RED_THREADS / 32; ++k) {
             A += sa[k];
             V += sv[k];
             IE += si[k];
             P += sp[k];
         }
-        out2[0] = A;
-        out2[1] = G.h * G.h * (V + G.h * (double)IE) / 3.0;
-        counts[0] = P;
-        counts[1] = IE;
+        part_d[2 * blockIdx.x] = A;
+        part_d[2 * blockIdx.x + 1] = V;
+        part_i[2 * blockIdx.x] = P;
+        part_i[2 * blockIdx.x + 1] = IE;
     }
+}
+
+// out2[2m..] = {area, volume}; counts[2m..] = {inside points, inside edges (all axes)}
+__global__ void k_reduce_final(Batch B, const double *__restrict__ part_d, const long long *__restrict__ part_i,
+                               double *__restrict__ out2, long long *__restrict__ counts)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= B.n_mol) return;
+    double A = 0.0, V = 0.0;
+    long long P = 0, IE = 0;
+    for (int g = 0; g < RED_PARTS; ++g) {
+        const int k = m * RED_PARTS + g;
+        A += part_d[2 * k];
+        V += part_d[2 * k + 1];
+        P += part_i[2 * k];
+        IE += part_i[2 * k + 1];
+    }
+    const double h = B.grid[m].h;
+    out2[2 * m] = A;
+    out2[2 * m + 1] = h * h * (V + h * (double)IE) / 3.0;
+    counts[2 * m] = P;
+    counts[2 * m + 1] = IE;
 }
 
 static int grid_tiles(long long n)
@@ -1208,48 +1272,89 @@ static int grid_tiles(long long n)
     return (int)(g > 2147483647LL ? 2147483647LL : g);
 }
 
-int launch_edge_count(const Grid &G, const int8_t *labels, int *tile_edges, int *tile_inside, cudaStream_t st)
+int launch_edge_count(const Batch &B, const int8_t *labels, int *tile_edges, int *tile_inside, cudaStream_t st)
 {
-    k_edge_count<<<grid_tiles(G.n_tiles), EDGE_THREADS, 0, st>>>(G, labels, tile_edges, tile_inside);
+    k_edge_count<<<grid_tiles(B.n_tiles), EDGE_THREADS, 0, st>>>(B, labels, tile_edges, tile_inside);
+    return 1;
+}
+
+int launch_mol_edges(const Batch &B, const int *edge_start, long long *medge, cudaStream_t st)
+{
+    const int n = 3 * (B.n_mol + 1);
+    k_mol_edges<<<(n + 255) / 256, 256, 0, st>>>(B, edge_start, medge);
     return 1;
 }
 
 template <class T, bool FILT>
-static void edge_solve_launch(const Model &M, const Grid &G, const int8_t *labels, const int *edge_start, EdgeOut out,
-                              int *n_fail, int *err, long long *fail_log, cudaStream_t st)
+static size_t edge_smem()
 {
-    size_t sm = ((sizeof(TileS<T>) + 15) & ~(size_t)15) + sizeof(EdgeSmem);
-    cudaFuncSetAttribute(k_edge_solve<T, FILT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_edge_solve<T, FILT><<<grid_tiles(G.n_tiles), EDGE_THREADS, sm, st>>>(M, G, labels, edge_start, out, n_fail, err,
-                                                                           fail_log);
+    return ((sizeof(TileS<T>) + 15) & ~(size_t)15) + sizeof(EdgeSmem);
+}
+
+// dynamic shared memory limits (once per device, before any launch or capture)
+void edges_init()
+{
+    cudaFuncSetAttribute(k_edge_solve<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)edge_smem<double, false>());
+    cudaFuncSetAttribute(k_edge_solve<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)edge_smem<float, true>());
+}
+
+int edge_ctas_per_sm(int precision)
+{
+    int n = 0;
+    if (precision == 0)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_edge_solve<double, false>, EDGE_THREADS,
+                                                      edge_smem<double, false>());
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_edge_solve<float, true>, EDGE_THREADS,
+                                                      edge_smem<float, true>());
+    return n > 0 ? n : 1;
+}
+
+int edge_chunk_max() { return CHUNK; }
+
+template <class T, bool FILT>
+static void edge_solve_launch(const Model &M, const Batch &B, const TileSched &Q, int grid, int chunk,
+                              const int8_t *labels, const int *edge_start, EdgeOut out, int *n_fail, int *err,
+                              long long *fail_log, cudaStream_t st)
+{
+    size_t sm = edge_smem<T, FILT>();
+    k_edge_solve<T, FILT><<<grid, EDGE_THREADS, sm, st>>>(M, B, Q, chunk, labels, edge_start, out, n_fail, err,
+                                                           fail_log);
 }
 
 long long polish_blocks(long long n_edges) { return n_edges > 0 ? ceil_div_ll(n_edges, POLISH_THREADS) : 0; }
 
-int launch_edge_solve(const Model &M, const Grid &G, int precision, const int8_t *labels, const int *edge_start,
-                      EdgeOut out, int *n_fail, int *err, long long *fail_log, cudaStream_t st)
+int launch_edge_solve(const Model &M, const Batch &B, int precision, const TileSched &Q, int grid, int chunk,
+                      const int8_t *labels, const int *edge_start, EdgeOut out, int *n_fail, int *err,
+                      long long *fail_log, cudaStream_t st)
 {
+    if (grid < 1) grid = 1;
+    chunk = chunk < 1 ? 1 : (chunk > CHUNK ? CHUNK : chunk);
     if (precision == 0)
-        edge_solve_launch<double, false>(M, G, labels, edge_start, out, n_fail, err, fail_log, st);
+        edge_solve_launch<double, false>(M, B, Q, grid, chunk, labels, edge_start, out, n_fail, err, fail_log, st);
     else
-        edge_solve_launch<float, true>(M, G, labels, edge_start, out, n_fail, err, fail_log, st);
+        edge_solve_launch<float, true>(M, B, Q, grid, chunk, labels, edge_start, out, n_fail, err, fail_log, st);
     return 1;
 }
 
-int launch_edge_polish(const Model &M, const Grid &G, EdgeOut out, const long long n_edges[3], double *part,
-                       cudaStream_t st)
+int launch_edge_polish(const Model &M, const Batch &B, EdgeOut out, long long n_edges_total,
+                       const long long *medge, double2 *term, cudaStream_t st)
 {
-    long long nb = polish_blocks(n_edges[0] + n_edges[1] + n_edges[2]);
-    if (nb > 0)
-        k_edge_polish<<<(unsigned)nb, POLISH_THREADS, 0, st>>>(M, G, out, n_edges[0], n_edges[1], n_edges[2], part);
+    long long nb = polish_blocks(n_edges_total);
+    if (nb > 0) k_edge_polish<<<(unsigned)nb, POLISH_THREADS, 0, st>>>(M, B, out, medge, term);
     return nb > 0 ? 1 : 0;
 }
 
-int launch_reduce(const Grid &G, const double *part, long long nparts, const int *tile_inside, double *out2,
-                  long long *counts, cudaStream_t st)
+long long reduce_scratch(int n_mol) { return 2LL * RED_PARTS * n_mol; }
+
+int launch_reduce(const Batch &B, const double2 *term, const long long *medge, const int *tile_inside, double *part_d,
+                  long long *part_i, double *out2, long long *counts, cudaStream_t st)
 {
-    k_reduce<<<1, 1024, 0, st>>>(G, part, nparts, tile_inside, out2, counts);
-    return 1;
+    k_reduce_part<<<B.n_mol * RED_PARTS, RED_THREADS, 0, st>>>(B, term, medge, tile_inside, part_d, part_i);
+    k_reduce_final<<<(B.n_mol + 127) / 128, 128, 0, st>>>(B, part_d, part_i, out2, counts);
+    return 2;
 }
 
 }  // namespace eses

@@ -44,14 +44,27 @@ constexpr int8_t LABEL_OUT = 0;
 constexpr int8_t LABEL_IN = 1;
 constexpr int8_t LABEL_BAND = 2;  // FP32 filter undecided: re-evaluated in FP64
 
-struct Model {
-    int n_atoms;
-    const double4 *atom;          // sorted atoms (x, y, z, r)
-    const int *atom_orig;         // original index of each sorted atom
-    const uint8_t *atom_face;     // 1: expanded sphere keeps a free face
+// Cell grid of one molecule: its cells hold ids coff .. coff + cn0*cn1*cn2 - 1
+// of the cell arrays shared by all molecules of a batch.
+struct CellGrid {
     double clo[3];                // cell grid origin
-    double cell;                  // cell edge
     int cn[3];                    // cells per axis
+    int coff;                     // first cell id
+};
+
+// The patch model of every molecule of a batch.  Items of different molecules
+// never interact: every cell-list query stays in the item's own molecule's
+// cells, so all lists (neighbours, pairs, triple points) are built in one
+// pass over the whole batch.
+struct Model {
+    int n_atoms;                  // all molecules
+    int n_mol;
+    const CellGrid *cg;           // per molecule
+    const int *atom_mol;          // molecule of each sorted atom
+    const double4 *atom;          // sorted atoms (x, y, z, r)
+    const int *atom_orig;         // original index of each sorted atom (in the batch)
+    const uint8_t *atom_face;     // 1: expanded sphere keeps a free face
+    double cell;                  // cell edge (all molecules)
     const int *cell_start;        // ncell + 1
     const int *nb_start;          // n_atoms + 1
     const int *nb_list;
@@ -64,6 +77,7 @@ struct Model {
     const int *pcell_list;
     int n_verts;
     const double4 *vert;          // free triple points (xyz, 0)
+    const int *vert_mol;          // molecule of each triple point
     const int *vcell_start;
     const int *vcell_list;
     double rp, rmax, Rmax;
@@ -78,12 +92,15 @@ struct Model {
     const float4 *vert_lo;
 };
 
+// The grid of one molecule (Eq. 2 with the origin of its reading).
 struct Grid {
     double lo[3];
     double h;
     long long dims[3];
     int tiles[3];
     long long n_tiles;
+    long long tile0;              // index of its first tile in the batch
+    long long lab0;               // offset of its labels in the batch's label array
     double rp;
     double halo;                  // r_max + 2 r_p
     float d0;                     // FP32 error bound of a staged position difference
@@ -91,6 +108,61 @@ struct Grid {
     float ht_hi, ht_lo;           // TILE * h as a double-float
 };
 
+// The tiles of a batch: molecule m owns global tiles tile_off[m] .. tile_off[m+1]-1.
+struct Batch {
+    int n_mol;
+    long long n_tiles;            // all molecules
+    const Grid *grid;             // per molecule
+    const long long *tile_off;    // n_mol + 1
+};
+
 __host__ __device__ inline long long ceil_div_ll(long long a, long long b) { return (a + b - 1) / b; }
+
+// Order in which a persistent kernel's CTAs take tiles: `per` consecutive
+// global tiles at a time, popped from the device counter `head` (dynamic load
+// balance over molecules and tiles of uneven cost), or in grid-stride order
+// when head is null.
+struct TileSched {
+    unsigned long long *head;
+    int per;
+};
+
+// first global tile of the CTA's next batch of Q.per tiles (whole block)
+__device__ __forceinline__ long long next_tiles(const TileSched &Q, long long &iter, long long *sh)
+{
+    if (threadIdx.x == 0)
+        *sh = Q.head ? (long long)atomicAdd(Q.head, (unsigned long long)Q.per)
+                     : ((long long)blockIdx.x + iter * (long long)gridDim.x) * Q.per;
+    __syncthreads();
+    const long long b = *sh;
+    __syncthreads();
+    ++iter;
+    return b;
+}
+
+// The molecule's grid into shared memory, for a whole block working on one of
+// its tiles (uniform, cheap reads instead of a struct in registers).  Ends
+// with a barrier.
+__device__ __forceinline__ void load_grid(const Batch &B, int mol, Grid &sG)
+{
+    static_assert(sizeof(Grid) % 4 == 0, "Grid copied as words");
+    constexpr int W = (int)(sizeof(Grid) / 4);
+    const int *src = reinterpret_cast<const int *>(B.grid + mol);
+    int *dst = reinterpret_cast<int *>(&sG);
+    for (int k = threadIdx.x; k < W; k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+}
+
+// molecule owning global tile gt (binary search of the tile offsets)
+__device__ __forceinline__ int mol_of_tile(const Batch &B, long long gt)
+{
+    int lo = 0, hi = B.n_mol;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (B.tile_off[mid] <= gt) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
 
 }  // namespace eses

@@ -16,35 +16,40 @@ int scan_exclusive(const int *in, int *out, long long n, int *tmp, cudaStream_t 
 
 // ---- model construction (eses_model.cu) ----------------------------------
 struct ModelBuf;  // owned by the context
-int launch_cell_count(const double *xyz, const double *r, int n, const double clo[3], double cell, const int cn[3],
-                       int *cell_id, int *cell_count, cudaStream_t st);
+int launch_cell_count(const double *xyz, const int *in_mol, int n, const CellGrid *cg, double cell, int *cell_id,
+                      int *cell_count, cudaStream_t st);
 int launch_cell_scatter(const double *xyz, const double *r, int n, const int *cell_id, const int *cell_start,
                          int *cursor, int *sorted_orig, cudaStream_t st);
-int launch_cell_finish(const double *xyz, const double *r, int n, int ncell, const int *cell_start, int *sorted_orig,
-                        double4 *atom, cudaStream_t st);
+int launch_cell_finish(const double *xyz, const double *r, const int *in_mol, int ncell, const int *cell_start,
+                       int *sorted_orig, double4 *atom, int *atom_mol, cudaStream_t st);
 int launch_nb_count(const Model &M, int *nb_count, int *circle_count, uint8_t *contained, cudaStream_t st);
 int launch_nb_fill(const Model &M, int *nb_list, cudaStream_t st);
 int launch_pair_count(const Model &M, int *pair_count, cudaStream_t st);
 int launch_pair_fill(const Model &M, const int *pair_start, double4 *pair_o, double4 *pair_u, int2 *pair_ij,
                       cudaStream_t st);
 int launch_arcs(const Model &M, uint8_t *pair_free, int *vert_count, cudaStream_t st);
-int launch_arcs_emit(const Model &M, const int *vert_start, double4 *vert, cudaStream_t st);
+int launch_arcs_emit(const Model &M, const int *vert_start, double4 *vert, int *vert_mol, cudaStream_t st);
 int launch_faces(const Model &M, const int *circle_count, const uint8_t *contained, uint8_t *face, cudaStream_t st);
 int launch_bin_count(const Model &M, int which, int *count, int *item_cell, cudaStream_t st);
 // FP32 double-float copies: which 0 atoms (hi, lo), 1 circles (hi, lo, axis), 2 triple points (hi, lo)
-int launch_model_f32(const Model &M, int which, const double lo[3], float4 *hi, float4 *lo_, float4 *u32,
+int launch_model_f32(const Model &M, int which, const Grid *grids, float4 *hi, float4 *lo_, float4 *u32,
                      cudaStream_t st);
 int launch_bin_scatter(const Model &M, int which, const int *item_cell, const int *start, int *cursor, int *list,
                         cudaStream_t st);
 
 // ---- classification (eses_classify.cu) -----------------------------------
-int launch_classify(const Model &M, const Grid &G, int precision, int8_t *labels, int *tile_band, int *err,
-                     cudaStream_t st);
-int launch_band(const Model &M, const Grid &G, int8_t *labels, const int *tile_band, int *err, cudaStream_t st);
+// persistent: `grid` CTAs take tiles in the order of Q (labels of the whole batch)
+void classify_init();
+int classify_ctas_per_sm(int precision);
+int launch_classify(const Model &M, const Batch &B, int precision, const TileSched &Q, int grid, int8_t *labels,
+                    int *tile_band, int *err, cudaStream_t st);
+int launch_band(const Model &M, const Batch &B, int8_t *labels, const int *tile_band, int *err, cudaStream_t st);
 
 // ---- crossing edges, roots, area/volume (eses_edges.cu) ------------------
-int launch_edge_count(const Grid &G, const int8_t *labels, int *tile_edges, int *tile_inside_edges,
-                       cudaStream_t st);
+int launch_edge_count(const Batch &B, const int8_t *labels, int *tile_edges, int *tile_inside_edges,
+                      cudaStream_t st);
+// medge[a * (n_mol + 1) + m]: first edge of molecule m in axis a's output
+int launch_mol_edges(const Batch &B, const int *edge_start, long long *medge, cudaStream_t st);
 struct EdgeOut {
     long long *idx[3];
     double *tau[3];
@@ -58,11 +63,18 @@ struct EdgeOut {
 constexpr int FAIL_LOG = 8;
 constexpr int FAIL_REC = 24;
 long long polish_blocks(long long n_edges);
-int launch_edge_solve(const Model &M, const Grid &G, int precision, const int8_t *labels, const int *edge_start,
-                      EdgeOut out, int *n_fail, int *err, long long *fail_log, cudaStream_t st);
-int launch_edge_polish(const Model &M, const Grid &G, EdgeOut out, const long long n_edges[3], double *part,
-                       cudaStream_t st);
-int launch_reduce(const Grid &G, const double *part, long long nparts, const int *tile_inside, double *out2,
-                  long long *counts, cudaStream_t st);
+void edges_init();
+int edge_ctas_per_sm(int precision);
+int edge_chunk_max();
+// persistent: `grid` CTAs take tiles in the order of Q; `chunk` edges per pooled chunk
+int launch_edge_solve(const Model &M, const Batch &B, int precision, const TileSched &Q, int grid, int chunk,
+                      const int8_t *labels, const int *edge_start, EdgeOut out, int *n_fail, int *err,
+                      long long *fail_log, cudaStream_t st);
+int launch_edge_polish(const Model &M, const Batch &B, EdgeOut out, long long n_edges_total, const long long *medge,
+                       double2 *term, cudaStream_t st);
+// part_d / part_i: reduce_scratch(n_mol) doubles / int64 each
+long long reduce_scratch(int n_mol);
+int launch_reduce(const Batch &B, const double2 *term, const long long *medge, const int *tile_inside, double *part_d,
+                  long long *part_i, double *out2, long long *counts, cudaStream_t st);
 
 }  // namespace eses

@@ -35,25 +35,31 @@ __device__ __forceinline__ int cell_coord(double v, double lo, double cell, int 
     return k < 0 ? 0 : (k >= n ? n - 1 : k);
 }
 
-__global__ void k_cell_count(const double *__restrict__ xyz, int n, double clx, double cly, double clz, double cell,
-                             int cn0, int cn1, int cn2, int *__restrict__ cell_id, int *__restrict__ cell_count)
+// cell id of a point of molecule m
+__device__ __forceinline__ int cell_of(const CellGrid &g, double cell, double x, double y, double z)
+{
+    int a = cell_coord(x, g.clo[0], cell, g.cn[0]);
+    int b = cell_coord(y, g.clo[1], cell, g.cn[1]);
+    int c = cell_coord(z, g.clo[2], cell, g.cn[2]);
+    return g.coff + (a * g.cn[1] + b) * g.cn[2] + c;
+}
+
+__global__ void k_cell_count(const double *__restrict__ xyz, const int *__restrict__ in_mol, int n,
+                             const CellGrid *__restrict__ cg, double cell, int *__restrict__ cell_id,
+                             int *__restrict__ cell_count)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int a = cell_coord(xyz[3 * i + 0], clx, cell, cn0);
-    int b = cell_coord(xyz[3 * i + 1], cly, cell, cn1);
-    int c = cell_coord(xyz[3 * i + 2], clz, cell, cn2);
-    int id = (a * cn1 + b) * cn2 + c;
+    int id = cell_of(cg[in_mol[i]], cell, xyz[3 * i + 0], xyz[3 * i + 1], xyz[3 * i + 2]);
     cell_id[i] = id;
     atomicAdd(&cell_count[id], 1);
 }
 
-int launch_cell_count(const double *xyz, const double *, int n, const double clo[3], double cell, const int cn[3],
-                       int *cell_id, int *cell_count, cudaStream_t st)
+int launch_cell_count(const double *xyz, const int *in_mol, int n, const CellGrid *cg, double cell, int *cell_id,
+                      int *cell_count, cudaStream_t st)
 {
     if (n <= 0) return 0;
-    k_cell_count<<<(n + 255) / 256, 256, 0, st>>>(xyz, n, clo[0], clo[1], clo[2], cell, cn[0], cn[1], cn[2], cell_id,
-                                                  cell_count);
+    k_cell_count<<<(n + 255) / 256, 256, 0, st>>>(xyz, in_mol, n, cg, cell, cell_id, cell_count);
     return 1;
 }
 
@@ -75,9 +81,9 @@ int launch_cell_scatter(const double *, const double *, int n, const int *cell_i
 }
 
 // order every cell by original atom index (deterministic layout), then gather
-__global__ void k_cell_finish(const double *__restrict__ xyz, const double *__restrict__ r, int ncell,
-                              const int *__restrict__ cell_start, int *__restrict__ sorted_orig,
-                              double4 *__restrict__ atom)
+__global__ void k_cell_finish(const double *__restrict__ xyz, const double *__restrict__ r,
+                              const int *__restrict__ in_mol, int ncell, const int *__restrict__ cell_start,
+                              int *__restrict__ sorted_orig, double4 *__restrict__ atom, int *__restrict__ atom_mol)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
@@ -94,28 +100,31 @@ __global__ void k_cell_finish(const double *__restrict__ xyz, const double *__re
     for (int a = s; a < e; ++a) {
         int o = sorted_orig[a];
         atom[a] = make_double4(xyz[3 * o], xyz[3 * o + 1], xyz[3 * o + 2], r[o]);
+        atom_mol[a] = in_mol[o];
     }
 }
 
-int launch_cell_finish(const double *xyz, const double *r, int, int ncell, const int *cell_start, int *sorted_orig,
-                        double4 *atom, cudaStream_t st)
+int launch_cell_finish(const double *xyz, const double *r, const int *in_mol, int ncell, const int *cell_start,
+                       int *sorted_orig, double4 *atom, int *atom_mol, cudaStream_t st)
 {
-    k_cell_finish<<<(ncell + 255) / 256, 256, 0, st>>>(xyz, r, ncell, cell_start, sorted_orig, atom);
+    k_cell_finish<<<(ncell + 255) / 256, 256, 0, st>>>(xyz, r, in_mol, ncell, cell_start, sorted_orig, atom, atom_mol);
     return 1;
 }
 
 // --------------------------------------------------------------------------
-// neighbour iteration over the 27 cells around a sorted atom
+// neighbour iteration over the 27 cells around a sorted atom (in the cells of
+// its own molecule)
 // --------------------------------------------------------------------------
-#define FOR_NEIGHBOUR_CELLS(M, px, py, pz, j, ...)                                               \
+#define FOR_NEIGHBOUR_CELLS(M, mol, px, py, pz, j, ...)                                          \
     do {                                                                                          \
-        int ca_ = cell_coord(px, (M).clo[0], (M).cell, (M).cn[0]);                                \
-        int cb_ = cell_coord(py, (M).clo[1], (M).cell, (M).cn[1]);                                \
-        int cc_ = cell_coord(pz, (M).clo[2], (M).cell, (M).cn[2]);                                \
-        for (int a_ = max(ca_ - 1, 0); a_ <= min(ca_ + 1, (M).cn[0] - 1); ++a_)                   \
-            for (int b_ = max(cb_ - 1, 0); b_ <= min(cb_ + 1, (M).cn[1] - 1); ++b_)               \
-                for (int c_ = max(cc_ - 1, 0); c_ <= min(cc_ + 1, (M).cn[2] - 1); ++c_) {         \
-                    int id_ = (a_ * (M).cn[1] + b_) * (M).cn[2] + c_;                             \
+        const CellGrid g_ = (M).cg[mol];                                                          \
+        int ca_ = cell_coord(px, g_.clo[0], (M).cell, g_.cn[0]);                                  \
+        int cb_ = cell_coord(py, g_.clo[1], (M).cell, g_.cn[1]);                                  \
+        int cc_ = cell_coord(pz, g_.clo[2], (M).cell, g_.cn[2]);                                  \
+        for (int a_ = max(ca_ - 1, 0); a_ <= min(ca_ + 1, g_.cn[0] - 1); ++a_)                    \
+            for (int b_ = max(cb_ - 1, 0); b_ <= min(cb_ + 1, g_.cn[1] - 1); ++b_)                \
+                for (int c_ = max(cc_ - 1, 0); c_ <= min(cc_ + 1, g_.cn[2] - 1); ++c_) {          \
+                    int id_ = g_.coff + (a_ * g_.cn[1] + b_) * g_.cn[2] + c_;                     \
                     for (int j = (M).cell_start[id_]; j < (M).cell_start[id_ + 1]; ++j) { __VA_ARGS__ } \
                 }                                                                                 \
     } while (0)
@@ -148,7 +157,7 @@ __global__ void k_nb_count(Model M, int *__restrict__ nb_count, int *__restrict_
     double Ri = ci.w + M.rp;
     int nb = 0, nc = 0;
     uint8_t inside = 0;
-    FOR_NEIGHBOUR_CELLS(M, ci.x, ci.y, ci.z, j, {
+    FOR_NEIGHBOUR_CELLS(M, M.atom_mol[i], ci.x, ci.y, ci.z, j, {
         if (j != i) {
             double4 cj = M.atom[j];
             double Rj = cj.w + M.rp;
@@ -183,7 +192,7 @@ __global__ void k_nb_fill(Model M, int *__restrict__ nb_list)
     double4 ci = M.atom[i];
     double Ri = ci.w + M.rp;
     int w = M.nb_start[i];
-    FOR_NEIGHBOUR_CELLS(M, ci.x, ci.y, ci.z, j, {
+    FOR_NEIGHBOUR_CELLS(M, M.atom_mol[i], ci.x, ci.y, ci.z, j, {
         if (j != i) {
             double4 cj = M.atom[j];
             double Rj = cj.w + M.rp;
@@ -561,12 +570,15 @@ __global__ void k_arcs(Model M, uint8_t *__restrict__ pair_free, int *__restrict
     arcs_of_pair32<false>(M, p, pair_free, vert_count, nullptr, nullptr);
 }
 
-__global__ void k_arcs_emit(Model M, const int *__restrict__ vert_start, double4 *__restrict__ vert)
+__global__ void k_arcs_emit(Model M, const int *__restrict__ vert_start, double4 *__restrict__ vert,
+                            int *__restrict__ vert_mol)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= M.n_pairs) return;
     if (vert_start[p + 1] == vert_start[p]) return;
     arcs_of_pair32<true>(M, p, nullptr, nullptr, vert_start, vert);
+    const int mol = M.atom_mol[M.pair_ij[p].x];
+    for (int k = vert_start[p]; k < vert_start[p + 1]; ++k) vert_mol[k] = mol;
 }
 
 int launch_arcs(const Model &M, uint8_t *pair_free, int *vert_count, cudaStream_t st)
@@ -576,10 +588,10 @@ int launch_arcs(const Model &M, uint8_t *pair_free, int *vert_count, cudaStream_
     return 1;
 }
 
-int launch_arcs_emit(const Model &M, const int *vert_start, double4 *vert, cudaStream_t st)
+int launch_arcs_emit(const Model &M, const int *vert_start, double4 *vert, int *vert_mol, cudaStream_t st)
 {
     if (M.n_pairs <= 0) return 0;
-    k_arcs_emit<<<(M.n_pairs + 127) / 128, 128, 0, st>>>(M, vert_start, vert);
+    k_arcs_emit<<<(M.n_pairs + 127) / 128, 128, 0, st>>>(M, vert_start, vert, vert_mol);
     return 1;
 }
 
@@ -617,6 +629,7 @@ __global__ void k_bin_count(Model M, int which, int *__restrict__ count, int *__
     int n = which == 0 ? M.n_pairs : M.n_verts;
     if (p >= n) return;
     double x, y, z;
+    int mol;
     if (which == 0) {
         if (!M.pair_free[p]) {
             item_cell[p] = -1;
@@ -624,14 +637,13 @@ __global__ void k_bin_count(Model M, int which, int *__restrict__ count, int *__
         }
         double4 o = M.pair_o[p];
         x = o.x; y = o.y; z = o.z;
+        mol = M.atom_mol[M.pair_ij[p].x];
     } else {
         double4 v = M.vert[p];
         x = v.x; y = v.y; z = v.z;
+        mol = M.vert_mol[p];
     }
-    int a = cell_coord(x, M.clo[0], M.cell, M.cn[0]);
-    int b = cell_coord(y, M.clo[1], M.cell, M.cn[1]);
-    int c = cell_coord(z, M.clo[2], M.cell, M.cn[2]);
-    int id = (a * M.cn[1] + b) * M.cn[2] + c;
+    int id = cell_of(M.cg[mol], M.cell, x, y, z);
     item_cell[p] = id;
     atomicAdd(&count[id], 1);
 }
@@ -646,10 +658,12 @@ __global__ void k_bin_scatter(int n, const int *__restrict__ item_cell, const in
     list[start[id] + atomicAdd(&cursor[id], 1)] = p;
 }
 
-__global__ void k_f32_atoms(Model M, double lx, double ly, double lz, float4 *__restrict__ hi, float4 *__restrict__ lo)
+__global__ void k_f32_atoms(Model M, const Grid *__restrict__ grids, float4 *__restrict__ hi, float4 *__restrict__ lo)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= M.n_atoms) return;
+    const double *L = grids[M.atom_mol[k]].lo;
+    const double lx = L[0], ly = L[1], lz = L[2];
     float hx, hy, hz, ex, ey, ez;
     double4 a = M.atom[k];
     split_df(a.x - lx, hx, ex);
@@ -659,11 +673,13 @@ __global__ void k_f32_atoms(Model M, double lx, double ly, double lz, float4 *__
     lo[k] = make_float4(ex, ey, ez, 0.0f);
 }
 
-__global__ void k_f32_pairs(Model M, double lx, double ly, double lz, float4 *__restrict__ hi, float4 *__restrict__ lo,
+__global__ void k_f32_pairs(Model M, const Grid *__restrict__ grids, float4 *__restrict__ hi, float4 *__restrict__ lo,
                             float4 *__restrict__ u32)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= M.n_pairs) return;
+    const double *L = grids[M.atom_mol[M.pair_ij[k].x]].lo;
+    const double lx = L[0], ly = L[1], lz = L[2];
     float hx, hy, hz, ex, ey, ez;
     double4 o = M.pair_o[k];
     double4 u = M.pair_u[k];
@@ -675,10 +691,12 @@ __global__ void k_f32_pairs(Model M, double lx, double ly, double lz, float4 *__
     u32[k] = make_float4((float)u.x, (float)u.y, (float)u.z, 0.0f);
 }
 
-__global__ void k_f32_verts(Model M, double lx, double ly, double lz, float4 *__restrict__ hi, float4 *__restrict__ lo)
+__global__ void k_f32_verts(Model M, const Grid *__restrict__ grids, float4 *__restrict__ hi, float4 *__restrict__ lo)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= M.n_verts) return;
+    const double *L = grids[M.vert_mol[k]].lo;
+    const double lx = L[0], ly = L[1], lz = L[2];
     float hx, hy, hz, ex, ey, ez;
     double4 v = M.vert[k];
     split_df(v.x - lx, hx, ex);
@@ -688,15 +706,16 @@ __global__ void k_f32_verts(Model M, double lx, double ly, double lz, float4 *__
     lo[k] = make_float4(ex, ey, ez, 0.0f);
 }
 
-// which: 0 atoms, 1 circles (centre and axis), 2 triple points
-int launch_model_f32(const Model &M, int which, const double lo[3], float4 *hi, float4 *lo_, float4 *u32,
+// which: 0 atoms, 1 circles (centre and axis), 2 triple points; relative to
+// the grid origin of each item's molecule
+int launch_model_f32(const Model &M, int which, const Grid *grids, float4 *hi, float4 *lo_, float4 *u32,
                      cudaStream_t st)
 {
     int n = which == 0 ? M.n_atoms : (which == 1 ? M.n_pairs : M.n_verts);
     if (n <= 0) return 0;
-    if (which == 0) k_f32_atoms<<<(n + 255) / 256, 256, 0, st>>>(M, lo[0], lo[1], lo[2], hi, lo_);
-    else if (which == 1) k_f32_pairs<<<(n + 255) / 256, 256, 0, st>>>(M, lo[0], lo[1], lo[2], hi, lo_, u32);
-    else k_f32_verts<<<(n + 255) / 256, 256, 0, st>>>(M, lo[0], lo[1], lo[2], hi, lo_);
+    if (which == 0) k_f32_atoms<<<(n + 255) / 256, 256, 0, st>>>(M, grids, hi, lo_);
+    else if (which == 1) k_f32_pairs<<<(n + 255) / 256, 256, 0, st>>>(M, grids, hi, lo_, u32);
+    else k_f32_verts<<<(n + 255) / 256, 256, 0, st>>>(M, grids, hi, lo_);
     return 1;
 }
 

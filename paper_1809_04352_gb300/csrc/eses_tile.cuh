@@ -255,8 +255,9 @@ __device__ __forceinline__ void stage_item(const Model &M, TileS<T> &S, int list
 // The items of every cell in range are numbered by a prefix over the cells
 // and tested one per thread, so all threads share the work.
 template <class T>
-__device__ void stage_tile(const Model &M, const Grid &G, long long tile, TileS<T> &S, double x0[3])
+__device__ void stage_tile(const Model &M, const Grid &G, int mol, long long tile, TileS<T> &S, double x0[3])
 {
+    const CellGrid &CG = M.cg[mol];
     if (threadIdx.x == 0) {  // the tile frame, once per tile (FP64 arithmetic is scarce)
         int t[3];
         tile_coords(G, tile, t);
@@ -266,8 +267,8 @@ __device__ void stage_tile(const Model &M, const Grid &G, long long tile, TileS<
             S.fx1[a] = S.fx0[a] + G.h * (double)TILE;
             S.fh0[a] = (float)rel;
             S.fl0[a] = (float)(rel - (double)S.fh0[a]);
-            S.fc0[a] = cell_coord_d(S.fx0[a] - G.halo, M.clo[a], M.cell, M.cn[a]);
-            S.fnc[a] = cell_coord_d(S.fx1[a] + G.halo, M.clo[a], M.cell, M.cn[a]) - S.fc0[a] + 1;
+            S.fc0[a] = cell_coord_d(S.fx0[a] - G.halo, CG.clo[a], M.cell, CG.cn[a]);
+            S.fnc[a] = cell_coord_d(S.fx1[a] + G.halo, CG.clo[a], M.cell, CG.cn[a]) - S.fc0[a] + 1;
         }
         S.na = 0;
         S.np = 0;
@@ -292,7 +293,7 @@ __device__ void stage_tile(const Model &M, const Grid &G, long long tile, TileS<
     if (ncell <= STAGE_CELLS) {
         for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
             int cz = c % nc[2], cy = (c / nc[2]) % nc[1], cx = c / (nc[1] * nc[2]);
-            int id = ((c0[0] + cx) * M.cn[1] + (c0[1] + cy)) * M.cn[2] + (c0[2] + cz);
+            int id = CG.coff + ((c0[0] + cx) * CG.cn[1] + (c0[1] + cy)) * CG.cn[2] + (c0[2] + cz);
             S.cid[c] = id;
             S.cs[0][c + 1] = M.cell_start[id + 1] - M.cell_start[id];
             S.cs[1][c + 1] = M.pcell_start[id + 1] - M.pcell_start[id];
@@ -336,7 +337,7 @@ __device__ void stage_tile(const Model &M, const Grid &G, long long tile, TileS<
         __syncthreads();
         for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
             int cz = c % nc[2], cy = (c / nc[2]) % nc[1], cx = c / (nc[1] * nc[2]);
-            int id = ((c0[0] + cx) * M.cn[1] + (c0[1] + cy)) * M.cn[2] + (c0[2] + cz);
+            int id = CG.coff + ((c0[0] + cx) * CG.cn[1] + (c0[1] + cy)) * CG.cn[2] + (c0[2] + cz);
             for (int k = M.cell_start[id]; k < M.cell_start[id + 1]; ++k) stage_item<T>(M, S, 0, k, F);
             for (int k = M.pcell_start[id]; k < M.pcell_start[id + 1]; ++k) stage_item<T>(M, S, 1, k, F);
             for (int k = M.vcell_start[id]; k < M.vcell_start[id + 1]; ++k) stage_item<T>(M, S, 2, k, F);

@@ -31,6 +31,13 @@ ESES_OPT_PRECISION = 2
 ESES_OPT_STREAM = 3
 ESES_OPT_SYNC = 4
 ESES_OPT_PROFILE = 5
+ESES_OPT_GRAPH = 6
+ESES_OPT_QUEUE = 7
+ESES_OPT_CLS_CTAS = 8
+ESES_OPT_CLS_TILES = 9
+ESES_OPT_EDGE_CTAS = 10
+ESES_OPT_EDGE_TILES = 11
+ESES_OPT_EDGE_CHUNK = 12
 
 ESES_PREC_FP64 = 0
 ESES_PREC_FP32_FILTERED = 1
@@ -39,7 +46,10 @@ STAT_NAMES = ["points", "tiles", "work_tiles", "circle_pairs", "free_arc_pairs",
               "crossing_edges", "root_failures", "inside_points", "kernel_launches"]
 
 # every exported C symbol, as declared in include/eses.h
-SYMBOLS = ["eses_create", "eses_create_device", "eses_set_option", "eses_run", "eses_grid", "eses_labels",
+SYMBOLS = ["eses_create", "eses_create_device", "eses_create_batch", "eses_run_batch", "eses_set_option",
+           "eses_get_option", "eses_autotune", "eses_run", "eses_num_molecules", "eses_mol_grid", "eses_mol_labels",
+           "eses_mol_labels_device", "eses_mol_num_intersections", "eses_mol_intersections",
+           "eses_mol_intersections_device", "eses_mol_area_volume", "eses_grid", "eses_labels",
            "eses_labels_device", "eses_num_intersections", "eses_intersections", "eses_intersections_device",
            "eses_area_volume", "eses_stats", "eses_stage_times", "eses_root_failures", "eses_patch_counts",
            "eses_patch_data", "eses_crossing_edges_noalloc", "eses_last_error", "eses_destroy"]
@@ -72,6 +82,18 @@ def load():
     PP = ctypes.POINTER(ctypes.c_void_p)
     lib.eses_create.argtypes = [P, P, i64, d, d, d, PP]
     lib.eses_create_device.argtypes = [P, P, i64, d, d, d, PP]
+    lib.eses_create_batch.argtypes = [P, P, P, ci, d, d, d, PP]
+    lib.eses_run_batch.argtypes = [ci, P, P, P, d, d, d, PP]
+    lib.eses_get_option.argtypes = [P, ci, P]
+    lib.eses_autotune.argtypes = [P, ci, P]
+    lib.eses_num_molecules.argtypes = [P, P]
+    lib.eses_mol_grid.argtypes = [P, ci, P, P]
+    lib.eses_mol_labels.argtypes = [P, ci, P]
+    lib.eses_mol_labels_device.argtypes = [P, ci, PP]
+    lib.eses_mol_num_intersections.argtypes = [P, ci, ci, P]
+    lib.eses_mol_intersections.argtypes = [P, ci, ci, P, P, P, P, P]
+    lib.eses_mol_intersections_device.argtypes = [P, ci, ci, PP, PP, PP, PP, PP]
+    lib.eses_mol_area_volume.argtypes = [P, ci, P, P]
     lib.eses_set_option.argtypes = [P, ci, i64]
     lib.eses_run.argtypes = [P]
     lib.eses_grid.argtypes = [P, P, P]
@@ -138,8 +160,119 @@ def eses_create_device(xyz, radii, n_atoms: int, r_p: float, h: float, margin: f
     return out
 
 
+def _batch_arrays(mols):
+    xyz = [np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3) for x, _ in mols]
+    rad = [np.ascontiguousarray(r, dtype=np.float64).reshape(-1) for _, r in mols]
+    for x, r in zip(xyz, rad):
+        if x.shape[0] != r.shape[0]:
+            raise ValueError("xyz and radii disagree in length")
+    counts = np.array([x.shape[0] for x in xyz], np.int64)
+    return xyz, rad, counts
+
+
+def eses_create_batch(mols, r_p: float, h: float, margin: float):
+    """Molecules [(xyz (n,3), radii (n,)), ...] sharing r_p, h, margin -> context handle."""
+    lib = load()
+    xyz, rad, counts = _batch_arrays(mols)
+    X = np.ascontiguousarray(np.concatenate(xyz, 0))
+    R = np.ascontiguousarray(np.concatenate(rad, 0))
+    out = ctypes.c_void_p()
+    _check(lib.eses_create_batch(_ptr(X), _ptr(R), _ptr(counts), len(xyz), r_p, h, margin, ctypes.byref(out)))
+    return out
+
+
+def eses_run_batch(mols, r_p: float, h: float, margin: float):
+    """Create a batch context from per-molecule arrays and run it once."""
+    lib = load()
+    xyz, rad, counts = _batch_arrays(mols)
+    px = (ctypes.c_void_p * len(xyz))(*[x.ctypes.data for x in xyz])
+    pr = (ctypes.c_void_p * len(rad))(*[r.ctypes.data for r in rad])
+    out = ctypes.c_void_p()
+    _check(lib.eses_run_batch(len(xyz), ctypes.cast(px, ctypes.c_void_p), ctypes.cast(pr, ctypes.c_void_p),
+                              _ptr(counts), r_p, h, margin, ctypes.byref(out)))
+    return out
+
+
 def eses_set_option(ctx, key: int, value: int):
     _check(load().eses_set_option(ctx, key, int(value)), ctx)
+
+
+def eses_get_option(ctx, key: int) -> int:
+    v = np.zeros(1, np.int64)
+    _check(load().eses_get_option(ctx, key, _ptr(v)), ctx)
+    return int(v[0])
+
+
+def eses_autotune(ctx, reps: int = 3):
+    """Time the persistent kernels' launch shapes and keep the fastest; returns
+    (classification ms, root-solve ms) of the chosen shapes."""
+    ms = np.zeros(2, np.float64)
+    _check(load().eses_autotune(ctx, int(reps), _ptr(ms)), ctx)
+    return float(ms[0]), float(ms[1])
+
+
+def eses_num_molecules(ctx) -> int:
+    n = np.zeros(1, np.int32)
+    _check(load().eses_num_molecules(ctx, _ptr(n)), ctx)
+    return int(n[0])
+
+
+def eses_mol_grid(ctx, m: int):
+    dims = np.zeros(3, np.int64)
+    origin = np.zeros(3, np.float64)
+    _check(load().eses_mol_grid(ctx, int(m), _ptr(dims), _ptr(origin)), ctx)
+    return dims, origin
+
+
+def eses_mol_labels(ctx, m: int, out=None):
+    dims, _ = eses_mol_grid(ctx, m)
+    if out is None:
+        out = np.empty(tuple(int(v) for v in dims), np.int8)
+    _check(load().eses_mol_labels(ctx, int(m), _ptr(out)), ctx)
+    return out
+
+
+def eses_mol_labels_device(ctx, m: int) -> int:
+    p = ctypes.c_void_p()
+    _check(load().eses_mol_labels_device(ctx, int(m), ctypes.byref(p)), ctx)
+    return int(p.value or 0)
+
+
+def eses_mol_num_intersections(ctx, m: int, axis: int) -> int:
+    n = np.zeros(1, np.int64)
+    _check(load().eses_mol_num_intersections(ctx, int(m), axis, _ptr(n)), ctx)
+    return int(n[0])
+
+
+def eses_mol_intersections(ctx, m: int, axis: int, fp32: bool = True):
+    """Host copies of molecule m's intersections along one axis."""
+    n = eses_mol_num_intersections(ctx, m, axis)
+    idx = np.empty(n, np.int64)
+    tau = np.empty(n, np.float64)
+    nrm = np.empty((n, 3), np.float64)
+    t32 = np.empty(n, np.float32) if fp32 else None
+    n32 = np.empty((n, 3), np.float32) if fp32 else None
+    if n:
+        _check(load().eses_mol_intersections(ctx, int(m), axis, _ptr(idx), _ptr(tau), _ptr(nrm), _ptr(t32),
+                                             _ptr(n32)), ctx)
+    out = {"idx": idx, "tau": tau, "normal": nrm}
+    if fp32:
+        out["tau32"] = t32
+        out["normal32"] = n32
+    return out
+
+
+def eses_mol_intersections_device(ctx, m: int, axis: int):
+    ps = [ctypes.c_void_p() for _ in range(5)]
+    _check(load().eses_mol_intersections_device(ctx, int(m), axis, *[ctypes.byref(p) for p in ps]), ctx)
+    return tuple(int(p.value or 0) for p in ps)
+
+
+def eses_mol_area_volume(ctx, m: int):
+    a = np.zeros(1, np.float64)
+    v = np.zeros(1, np.float64)
+    _check(load().eses_mol_area_volume(ctx, int(m), _ptr(a), _ptr(v)), ctx)
+    return float(a[0]), float(v[0])
 
 
 def eses_run(ctx):
