@@ -80,6 +80,12 @@ typedef struct eses_ctx eses_ctx;
 #define ESES_OPT_EDGE_TILES 11 /* root-solve tiles per queue pop (default 4) */
 #define ESES_OPT_EDGE_CHUNK 12 /* root-solve edges per pooled chunk (0 = the maximum, 64; default) */
 
+#define ESES_PROPOSER_OFF 0      /* classify every tile (default) */
+#define ESES_PROPOSER_MLP 1      /* the MLP scores tiles; those scored far are certified and filled */
+#define ESES_PROPOSER_CERTIFY 2  /* the certificate on every tile (no network) */
+
+#define ESES_MLP_NPARAM 6337     /* parameters of the proposer MLP (layout at eses_set_proposer) */
+
 #define ESES_PREC_FP64 0           /* every step in FP64 */
 #define ESES_PREC_FP32_FILTERED 1  /* FP32 with a forward-error filter, FP64 inside the filter band */
 
@@ -127,6 +133,44 @@ int eses_get_option(const eses_ctx *ctx, int key, int64_t *value);
  * ms_out (host, 2 doubles, may be NULL): mean milliseconds of the chosen
  * classification and root-solve launches. */
 int eses_autotune(eses_ctx *ctx, int reps, double *ms_out);
+
+/* Learned tile proposer (a GPU-side addition; the paper classifies every
+ * point).  Tiles are 8x8x8 points; a tile is "far" when all its labels are
+ * equal.  mode ESES_PROPOSER_MLP: a multilayer perceptron 32 -> 64 -> 64 -> 1
+ * (ReLU) scores every tile from 32 atom-density features (eses_tile_data) and
+ * a tile whose score sigmoid(z) < p_far is checked by an exact certificate
+ * from nearest-atom distance bounds around the tile centre t (points within
+ * delta of t): all points outside if min_i(|t - c_i| - r_i - r_p) >= delta,
+ * all inside if max_i(r_i - |t - c_i|) > delta.  Certified tiles are filled;
+ * all other tiles are classified exactly, so labels never depend on the
+ * network.  ESES_PROPOSER_CERTIFY applies the certificate to every tile.
+ * params: host, ESES_MLP_NPARAM floats, copied (NULL keeps the previous
+ * ones): W1[32][64] (input-major), b1[64], W2[64][64], b2[64], w3[64], b3.
+ * eses_stats [11] counts the tiles proposed far, [12] the tiles certified. */
+int eses_set_proposer(eses_ctx *ctx, int mode, const float *params, double p_far);
+
+/* Number of 8x8x8-point tiles of the context, all molecules (host output). */
+int eses_num_tiles(const eses_ctx *ctx, int64_t *n);
+
+/* Training data of the proposer from the last run: device outputs, either may
+ * be NULL: features (n_tiles * 32 floats, tile-major, the proposer's
+ * features) and targets (n_tiles bytes, 1 where the tile's labels are not
+ * all equal).  Tiles are numbered molecule by molecule, C order within one. */
+int eses_tile_data(const eses_ctx *ctx, float *features, uint8_t *targets);
+
+/* Training kernels of the proposer MLP (device pointers; stream = cudaStream_t
+ * or NULL; they enqueue and return).  eses_mlp_forward: z[s] = MLP(X[s]) for
+ * n samples of 32 features.  eses_mlp_grad: grad (ESES_MLP_NPARAM floats) and
+ * loss (1 float) of L = sum_s w[s] * BCE(z_s, y[s]) (binary cross entropy on
+ * the logit z); scratch holds eses_mlp_grad_scratch(n) floats; the result is
+ * deterministic.  eses_mlp_adam: one Adam step (beta 0.9, 0.999, eps 1e-8,
+ * step >= 1) on params with moments m, v.  Errors: ESES_EINVAL, ESES_ECUDA
+ * (eses_last_error(NULL)). */
+int eses_mlp_forward(const float *X, int64_t n, const float *params, float *z, void *stream);
+int64_t eses_mlp_grad_scratch(int64_t n);
+int eses_mlp_grad(const float *X, const float *y, const float *w, int64_t n, const float *params, float *grad,
+                  float *loss, float *scratch, void *stream);
+int eses_mlp_adam(float *params, const float *grad, float *m, float *v, int step, float lr, void *stream);
 
 /* Number of molecules of the context (host output). */
 int eses_num_molecules(const eses_ctx *ctx, int *n);
@@ -181,7 +225,8 @@ int eses_area_volume(const eses_ctx *ctx, double *area, double *volume);
  * [0] points, [1] tiles, [2] tiles with work, [3] circle pairs, [4] pairs
  * with a free arc, [5] free triple points, [6] points re-evaluated in FP64
  * (filter band), [7] crossing edges (all axes), [8] edges with a reported
- * root failure, [9] inside points, [10] kernels launched by the run. */
+ * root failure, [9] inside points, [10] kernels launched by the run,
+ * [11] tiles proposed far, [12] tiles certified far (eses_set_proposer). */
 int eses_stats(const eses_ctx *ctx, int64_t *out, int n);
 
 /* Device time in milliseconds of every stage of the last eses_run, measured

@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libeses.so")
-SOURCES = ["eses_api.cu", "eses_scan.cu", "eses_model.cu", "eses_classify.cu", "eses_edges.cu", "eses_noalloc.cu"]
+SOURCES = ["eses_api.cu", "eses_scan.cu", "eses_model.cu", "eses_classify.cu", "eses_edges.cu", "eses_noalloc.cu",
+           "eses_mlp.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -27,8 +27,10 @@
 
 using namespace eses;
 
+static_assert(MLP_NPARAM == ESES_MLP_NPARAM, "proposer parameter count");
+
 // stages timed with CUDA events when ESES_OPT_PROFILE is set
-enum { NSTAT = 11 };
+enum { NSTAT = 13 };
 enum { ST_BIN = 0, ST_PAIRS, ST_ARCS, ST_CLASSIFY, ST_BAND, ST_EDGE_COUNT, ST_EDGE_SOLVE, ST_EDGE_POLISH, ST_REDUCE, NSTAGE };
 
 namespace {
@@ -139,6 +141,11 @@ struct eses_ctx {
     // launch shapes (eses_autotune, ESES_OPT_*)
     Shape cls, edge;
     bool use_queue = true;
+    // learned tile proposer
+    int proposer = 0;  // ESES_PROPOSER_*
+    float z_far = 0.0f;
+    bool have_params = false;
+    DBuf mlp_params, need, need_pos, tile_list, prop_counts, features, targets;
     // CUDA graph of the device path
     bool graph_on = false;
     cudaGraphExec_t gexec = nullptr;
@@ -326,6 +333,7 @@ int create_common(const double *hxyz, const double *hr, const int64_t *counts, i
         ck(cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device), "device attribute");
         classify_init();
         edges_init();
+        mlp_init();
         ck(cudaGetLastError(), "kernel attributes");
         ck(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking), "cudaStreamCreate");
         c->stream = c->own_stream;
@@ -402,6 +410,8 @@ TileSched sched_of(eses_ctx *c, const Shape &s, int which)
     TileSched q;
     q.head = c->use_queue ? (unsigned long long *)c->queue.p + which : nullptr;
     q.per = std::max(s.tiles_per_pop, 1);
+    q.list = nullptr;
+    q.list_n = nullptr;
     return q;
 }
 
@@ -537,12 +547,27 @@ int run_device(eses_ctx *c)
     M.vert_hi = vhi;
     M.vert_lo = vlo;
 
-    // 7. classification (+ FP64 band re-evaluation), persistent over all tiles
+    // 7. classification (+ FP64 band re-evaluation), persistent over all tiles;
+    //    with the proposer, certified far tiles are filled first and only the
+    //    others are classified
     int8_t *labels = ensure<int8_t>(c->labels, c->n_points);
     int *tile_band = ensure<int>(c->tile_band, nt);
+    int *prop_counts = ensure<int>(c->prop_counts, 4);
+    ck(cudaMemsetAsync(prop_counts, 0, 4 * sizeof(int), st), "memset");
     mark(c, ST_CLASSIFY);
-    nl += launch_classify(M, B, c->precision, sched_of(c, c->cls, 0),
-                          grid_of(c, c->cls, classify_ctas_per_sm(c->precision)), labels,
+    TileSched cq = sched_of(c, c->cls, 0);
+    if (c->proposer != ESES_PROPOSER_OFF) {
+        int *need = ensure<int>(c->need, nt);
+        int *pos = ensure<int>(c->need_pos, nt + 1);
+        int *list = ensure<int>(c->tile_list, nt);
+        nl += launch_propose(M, B, c->proposer, (const float *)c->mlp_params.p, c->z_far, labels,
+                             c->precision == ESES_PREC_FP64 ? nullptr : tile_band, need, prop_counts, st);
+        nl += scan(c, need, pos, nt);
+        nl += launch_compact(nt, need, pos, list, st);
+        cq.list = list;
+        cq.list_n = pos + nt;
+    }
+    nl += launch_classify(M, B, c->precision, cq, grid_of(c, c->cls, classify_ctas_per_sm(c->precision)), labels,
                           c->precision == ESES_PREC_FP64 ? nullptr : tile_band, d_err, st);
     mark(c, ST_BAND);
     if (c->precision != ESES_PREC_FP64) nl += launch_band(M, B, labels, tile_band, d_err, st);
@@ -605,6 +630,8 @@ int finish(eses_ctx *c, int nl)
     c->av_h.assign(2 * (size_t)nm, 0.0);
     c->cnt_h.assign(2 * (size_t)nm, 0);
     ck(cudaMemcpyAsync(hmisc, c->misc.p, sizeof(hmisc), cudaMemcpyDeviceToHost, st), "read results");
+    int hprop[4] = {0, 0, 0, 0};
+    ck(cudaMemcpyAsync(hprop, c->prop_counts.p, sizeof(hprop), cudaMemcpyDeviceToHost, st), "read results");
     ck(cudaMemcpyAsync(c->medge_h.data(), c->medge.p, sizeof(long long) * c->medge_h.size(), cudaMemcpyDeviceToHost, st),
        "read results");
     ck(cudaMemcpyAsync(c->av_h.data(), c->av.p, sizeof(double) * c->av_h.size(), cudaMemcpyDeviceToHost, st),
@@ -627,6 +654,8 @@ int finish(eses_ctx *c, int nl)
     c->stats[8] = hmisc[1];
     c->stats[9] = inside;
     c->stats[10] = nl;
+    c->stats[11] = hprop[0];
+    c->stats[12] = hprop[1];
     c->ran = true;
     int derr = hmisc[0];
     if (derr & (ERR_CAP_ATOMS | ERR_CAP_PAIRS | ERR_CAP_VERTS | ERR_CAP_CAND)) {
@@ -950,6 +979,57 @@ int eses_autotune(eses_ctx *c, int reps, double *ms_out)
     return run_guarded(c);  // fresh results with the chosen shapes
 }
 
+int eses_set_proposer(eses_ctx *c, int mode, const float *params, double p_far)
+{
+    if (!c) return fail(nullptr, ESES_EINVAL, "ctx is NULL");
+    if (mode != ESES_PROPOSER_OFF && mode != ESES_PROPOSER_MLP && mode != ESES_PROPOSER_CERTIFY)
+        return fail(c, ESES_EINVAL, "bad proposer mode");
+    if (mode == ESES_PROPOSER_MLP) {
+        if (!(p_far > 0.0 && p_far < 1.0)) return fail(c, ESES_EINVAL, "p_far must be in (0, 1)");
+        if (!params && !c->have_params) return fail(c, ESES_EINVAL, "the MLP proposer needs parameters");
+    }
+    try {
+        if (params) {
+            for (int k = 0; k < MLP_NPARAM; ++k)
+                if (!isfinite(params[k])) return fail(c, ESES_EINVAL, "non-finite proposer parameter");
+            float *d = ensure<float>(c->mlp_params, MLP_NPARAM);
+            ck(cudaMemcpy(d, params, sizeof(float) * MLP_NPARAM, cudaMemcpyHostToDevice), "copy parameters");
+            c->have_params = true;
+        }
+    } catch (const CudaError &e) {
+        return fail(c, ESES_ECUDA, std::string(e.what) + ": " + cudaGetErrorString(e.e));
+    } catch (const std::bad_alloc &) {
+        return fail(c, ESES_ENOMEM, "device allocation failed");
+    }
+    drop_graph(c);
+    c->proposer = mode;
+    if (mode == ESES_PROPOSER_MLP) c->z_far = (float)log(p_far / (1.0 - p_far));
+    return ESES_OK;
+}
+
+int eses_num_tiles(const eses_ctx *c, int64_t *n)
+{
+    if (!c || !n) return fail(const_cast<eses_ctx *>(c), ESES_EINVAL, "NULL argument");
+    *n = c->n_tiles;
+    return ESES_OK;
+}
+
+int eses_tile_data(const eses_ctx *cc, float *features, uint8_t *targets)
+{
+    eses_ctx *c = const_cast<eses_ctx *>(cc);
+    if (!c) return fail(c, ESES_EINVAL, "NULL argument");
+    if (!c->ran) return fail(c, ESES_ESTATE, "no results: call eses_run first");
+    try {
+        if (features) launch_tile_features(c->M, c->B, features, c->stream);
+        if (targets) launch_tile_targets(c->B, (const int8_t *)c->labels.p, targets, c->stream);
+        ck(cudaGetLastError(), "tile data");
+        ck(cudaStreamSynchronize(c->stream), "synchronize");
+    } catch (const CudaError &e) {
+        return fail(c, ESES_ECUDA, std::string(e.what) + ": " + cudaGetErrorString(e.e));
+    }
+    return ESES_OK;
+}
+
 int eses_num_molecules(const eses_ctx *c, int *n)
 {
     if (!c || !n) return fail(const_cast<eses_ctx *>(c), ESES_EINVAL, "NULL argument");
@@ -1207,6 +1287,35 @@ int eses_stage_times(const eses_ctx *cc, double *ms, int n)
     return ESES_OK;
 }
 
+int eses_mlp_forward(const float *X, int64_t n, const float *params, float *z, void *stream)
+{
+    if (!X || !params || !z || n < 0 || n > (1LL << 30)) return fail(nullptr, ESES_EINVAL, "bad argument");
+    launch_mlp_forward(X, (int)n, params, z, (cudaStream_t)stream);
+    if (cudaGetLastError() != cudaSuccess) return fail(nullptr, ESES_ECUDA, "mlp forward launch failed");
+    return ESES_OK;
+}
+
+int64_t eses_mlp_grad_scratch(int64_t n) { return n > 0 && n <= (1LL << 30) ? mlp_grad_scratch((int)n) : 0; }
+
+int eses_mlp_grad(const float *X, const float *y, const float *w, int64_t n, const float *params, float *grad,
+                  float *loss, float *scratch, void *stream)
+{
+    if (!X || !y || !w || !params || !grad || !loss || !scratch || n < 1 || n > (1LL << 30))
+        return fail(nullptr, ESES_EINVAL, "bad argument");
+    mlp_init();
+    launch_mlp_grad(X, y, w, (int)n, params, scratch, grad, loss, (cudaStream_t)stream);
+    if (cudaGetLastError() != cudaSuccess) return fail(nullptr, ESES_ECUDA, "mlp gradient launch failed");
+    return ESES_OK;
+}
+
+int eses_mlp_adam(float *params, const float *grad, float *m, float *v, int step, float lr, void *stream)
+{
+    if (!params || !grad || !m || !v || step < 1 || !(lr > 0.0f)) return fail(nullptr, ESES_EINVAL, "bad argument");
+    launch_adam(params, grad, m, v, step, lr, (cudaStream_t)stream);
+    if (cudaGetLastError() != cudaSuccess) return fail(nullptr, ESES_ECUDA, "adam launch failed");
+    return ESES_OK;
+}
+
 const char *eses_last_error(const eses_ctx *c)
 {
     if (!c) return g_create_error.c_str();
@@ -1224,7 +1333,9 @@ void eses_destroy(eses_ctx *c)
                     &c->pbin_cursor, &c->pbin_cell, &c->pbin_list, &c->vbin_count, &c->vbin_start, &c->vbin_cursor,
                     &c->vbin_cell, &c->vbin_list, &c->labels, &c->tile_band, &c->tile_edges, &c->edge_start,
                     &c->tile_inside, &c->scan_tmp, &c->misc, &c->av, &c->counts, &c->red_d, &c->red_i, &c->fail_log, &c->atom_hi,
-                    &c->atom_lo, &c->pair_hi, &c->pair_lo, &c->pair_u32, &c->vert_hi, &c->vert_lo};
+                    &c->atom_lo, &c->pair_hi, &c->pair_lo, &c->pair_u32, &c->vert_hi, &c->vert_lo,
+                    &c->mlp_params, &c->need, &c->need_pos, &c->tile_list, &c->prop_counts, &c->features,
+                    &c->targets};
     if (c->own_stream) cudaStreamSynchronize(c->own_stream);
     drop_graph(c);
     for (DBuf *b : bufs) free_buf(*b);

@@ -178,11 +178,13 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Batch B, Tile
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const T rp = (T)M.rp;
     long long iter = 0;
+    const long long npos = sched_count(Q, B.n_tiles);
     for (;;) {
       const long long base = next_tiles(Q, iter, &q_base);
-      if (base >= B.n_tiles) break;
-      const long long bend = min(base + (long long)Q.per, B.n_tiles);
-      for (long long gt = base; gt < bend; ++gt) {
+      if (base >= npos) break;
+      const long long bend = min(base + (long long)Q.per, npos);
+      for (long long pos = base; pos < bend; ++pos) {
+        const long long gt = sched_tile(Q, pos);
         const int mol = mol_of_tile(B, gt);
         load_grid(B, mol, sG);
         const Grid &G = sG;

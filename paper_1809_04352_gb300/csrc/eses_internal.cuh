@@ -125,7 +125,19 @@ __host__ __device__ inline long long ceil_div_ll(long long a, long long b) { ret
 struct TileSched {
     unsigned long long *head;
     int per;
+    const int *list;    // optional: the global tiles to process (else every tile)
+    const int *list_n;  // device count of `list`
 };
+
+// number of queue positions and the global tile at a position
+__device__ __forceinline__ long long sched_count(const TileSched &Q, long long n_tiles)
+{
+    return Q.list ? (long long)*Q.list_n : n_tiles;
+}
+__device__ __forceinline__ long long sched_tile(const TileSched &Q, long long pos)
+{
+    return Q.list ? (long long)Q.list[pos] : pos;
+}
 
 // first global tile of the CTA's next batch of Q.per tiles (whole block)
 __device__ __forceinline__ long long next_tiles(const TileSched &Q, long long &iter, long long *sh)

@@ -77,4 +77,29 @@ long long reduce_scratch(int n_mol);
 int launch_reduce(const Batch &B, const double2 *term, const long long *medge, const int *tile_inside, double *part_d,
                   long long *part_i, double *out2, long long *counts, cudaStream_t st);
 
+// ---- learned tile proposer (eses_mlp.cu) ---------------------------------
+// MLP 32 -> 64 -> 64 -> 1 with ReLU; parameters in one float vector:
+// W1[32][64] (in x out), b1[64], W2[64][64], b2[64], w3[64], b3
+constexpr int MLP_IN = 32, MLP_H = 64;
+constexpr int P_W1 = 0;
+constexpr int P_B1 = P_W1 + MLP_IN * MLP_H;
+constexpr int P_W2 = P_B1 + MLP_H;
+constexpr int P_B2 = P_W2 + MLP_H * MLP_H;
+constexpr int P_W3 = P_B2 + MLP_H;
+constexpr int P_B3 = P_W3 + MLP_H;
+constexpr int MLP_NPARAM = P_B3 + 1;
+void mlp_init();
+int launch_mlp_forward(const float *X, int n, const float *P, float *z, cudaStream_t st);
+long long mlp_grad_scratch(int n);  // floats
+int launch_mlp_grad(const float *X, const float *y, const float *w, int n, const float *P, float *part, float *grad,
+                    float *loss, cudaStream_t st);
+int launch_adam(float *P, const float *g, float *m, float *v, int step, float lr, cudaStream_t st);
+int launch_tile_features(const Model &M, const Batch &B, float *feat, cudaStream_t st);
+int launch_tile_targets(const Batch &B, const int8_t *labels, uint8_t *target, cudaStream_t st);
+// mode 1: MLP + certificate, 2: certificate on every tile; need[t] = 1 for
+// tiles left to the exact classification; counts[0..1] += proposed, certified
+int launch_propose(const Model &M, const Batch &B, int mode, const float *P, float z_far, int8_t *labels,
+                   int *tile_band, int *need, int *counts, cudaStream_t st);
+int launch_compact(long long n, const int *need, const int *pos, int *list, cudaStream_t st);
+
 }  // namespace eses

@@ -39,11 +39,17 @@ ESES_OPT_EDGE_CTAS = 10
 ESES_OPT_EDGE_TILES = 11
 ESES_OPT_EDGE_CHUNK = 12
 
+ESES_PROPOSER_OFF = 0
+ESES_PROPOSER_MLP = 1
+ESES_PROPOSER_CERTIFY = 2
+ESES_MLP_NPARAM = 6337
+
 ESES_PREC_FP64 = 0
 ESES_PREC_FP32_FILTERED = 1
 
 STAT_NAMES = ["points", "tiles", "work_tiles", "circle_pairs", "free_arc_pairs", "free_vertices", "band_points",
-              "crossing_edges", "root_failures", "inside_points", "kernel_launches"]
+              "crossing_edges", "root_failures", "inside_points", "kernel_launches", "tiles_proposed_far",
+              "tiles_certified"]
 
 # every exported C symbol, as declared in include/eses.h
 SYMBOLS = ["eses_create", "eses_create_device", "eses_create_batch", "eses_run_batch", "eses_set_option",
@@ -52,7 +58,9 @@ SYMBOLS = ["eses_create", "eses_create_device", "eses_create_batch", "eses_run_b
            "eses_mol_intersections_device", "eses_mol_area_volume", "eses_grid", "eses_labels",
            "eses_labels_device", "eses_num_intersections", "eses_intersections", "eses_intersections_device",
            "eses_area_volume", "eses_stats", "eses_stage_times", "eses_root_failures", "eses_patch_counts",
-           "eses_patch_data", "eses_crossing_edges_noalloc", "eses_last_error", "eses_destroy"]
+           "eses_patch_data", "eses_crossing_edges_noalloc", "eses_set_proposer", "eses_num_tiles",
+           "eses_tile_data", "eses_mlp_forward", "eses_mlp_grad_scratch", "eses_mlp_grad", "eses_mlp_adam",
+           "eses_last_error", "eses_destroy"]
 STAGE_NAMES = ["binning", "pairs", "arcs", "classify", "band", "edge_count", "edge_solve", "edge_polish", "reduce"]
 
 _lib = None
@@ -95,6 +103,13 @@ def load():
     lib.eses_mol_intersections_device.argtypes = [P, ci, ci, PP, PP, PP, PP, PP]
     lib.eses_mol_area_volume.argtypes = [P, ci, P, P]
     lib.eses_set_option.argtypes = [P, ci, i64]
+    lib.eses_set_proposer.argtypes = [P, ci, P, d]
+    lib.eses_num_tiles.argtypes = [P, P]
+    lib.eses_tile_data.argtypes = [P, P, P]
+    lib.eses_mlp_forward.argtypes = [P, i64, P, P, P]
+    lib.eses_mlp_grad_scratch.argtypes = [i64]
+    lib.eses_mlp_grad.argtypes = [P, P, P, i64, P, P, P, P, P]
+    lib.eses_mlp_adam.argtypes = [P, P, P, P, ci, ctypes.c_float, P]
     lib.eses_run.argtypes = [P]
     lib.eses_grid.argtypes = [P, P, P]
     lib.eses_labels.argtypes = [P, P]
@@ -116,6 +131,7 @@ def load():
     for name in SYMBOLS:
         if name not in ("eses_last_error", "eses_destroy"):
             getattr(lib, name).restype = ctypes.c_int
+    lib.eses_mlp_grad_scratch.restype = i64
     _lib = lib
     return lib
 
@@ -209,6 +225,48 @@ def eses_autotune(ctx, reps: int = 3):
     ms = np.zeros(2, np.float64)
     _check(load().eses_autotune(ctx, int(reps), _ptr(ms)), ctx)
     return float(ms[0]), float(ms[1])
+
+
+def eses_set_proposer(ctx, mode: int, params=None, p_far: float = 0.5):
+    """Tile proposer mode (ESES_PROPOSER_*); params: host float32[ESES_MLP_NPARAM] or None."""
+    if params is not None:
+        params = np.ascontiguousarray(params, dtype=np.float32).reshape(-1)
+        if params.shape[0] != ESES_MLP_NPARAM:
+            raise ValueError(f"expected {ESES_MLP_NPARAM} parameters")
+    _check(load().eses_set_proposer(ctx, int(mode), _ptr(params), float(p_far)), ctx)
+
+
+def eses_num_tiles(ctx) -> int:
+    n = np.zeros(1, np.int64)
+    _check(load().eses_num_tiles(ctx, _ptr(n)), ctx)
+    return int(n[0])
+
+
+def eses_tile_data(ctx, features=None, targets=None):
+    """Device outputs (torch CUDA tensors or pointers): features float32[n_tiles, 32], targets uint8[n_tiles]."""
+    _check(load().eses_tile_data(ctx, _ptr(features), _ptr(targets)), ctx)
+
+
+def _stream(stream):
+    return ctypes.c_void_p(int(stream)) if stream else None
+
+
+def eses_mlp_forward(X, n: int, params, z, stream=0):
+    _check(load().eses_mlp_forward(_ptr(X), int(n), _ptr(params), _ptr(z), _stream(stream)))
+
+
+def eses_mlp_grad_scratch(n: int) -> int:
+    return int(load().eses_mlp_grad_scratch(int(n)))
+
+
+def eses_mlp_grad(X, y, w, n: int, params, grad, loss, scratch, stream=0):
+    _check(load().eses_mlp_grad(_ptr(X), _ptr(y), _ptr(w), int(n), _ptr(params), _ptr(grad), _ptr(loss),
+                                _ptr(scratch), _stream(stream)))
+
+
+def eses_mlp_adam(params, grad, m, v, step: int, lr: float, stream=0):
+    _check(load().eses_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(step), ctypes.c_float(lr),
+                                _stream(stream)))
 
 
 def eses_num_molecules(ctx) -> int:
