@@ -168,6 +168,11 @@ int eses_tile_data(const eses_ctx *ctx, float *features, uint8_t *targets);
  * (eses_last_error(NULL)). */
 int eses_mlp_forward(const float *X, int64_t n, const float *params, float *z, void *stream);
 int64_t eses_mlp_grad_scratch(int64_t n);
+/* The proposer's scoring path on n rows: BF16 weights and activations on the
+ * tensor cores (tcgen05.mma, FP32 accumulation in tensor memory); *err
+ * (device int) gets bit 16 when a bounded wait ran out (those rows score
+ * +inf). */
+int eses_mlp_forward_tc(const float *X, int64_t n, const float *params, float *z, int *err, void *stream);
 int eses_mlp_grad(const float *X, const float *y, const float *w, int64_t n, const float *params, float *grad,
                   float *loss, float *scratch, void *stream);
 int eses_mlp_adam(float *params, const float *grad, float *m, float *v, int step, float lr, void *stream);

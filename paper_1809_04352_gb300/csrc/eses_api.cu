@@ -561,7 +561,7 @@ int run_device(eses_ctx *c)
         int *pos = ensure<int>(c->need_pos, nt + 1);
         int *list = ensure<int>(c->tile_list, nt);
         nl += launch_propose(M, B, c->proposer, (const float *)c->mlp_params.p, c->z_far, labels,
-                             c->precision == ESES_PREC_FP64 ? nullptr : tile_band, need, prop_counts, st);
+                             c->precision == ESES_PREC_FP64 ? nullptr : tile_band, need, prop_counts, d_err, st);
         nl += scan(c, need, pos, nt);
         nl += launch_compact(nt, need, pos, list, st);
         cq.list = list;
@@ -665,6 +665,8 @@ int finish(eses_ctx *c, int nl)
     }
     if (hmisc[1] > 0)
         return fail(c, ESES_EROOT, std::to_string(hmisc[1]) + " crossing edges had no surface root");
+    if (derr & ERR_TIMEOUT)
+        return fail(c, ESES_ETIMEOUT, "a bounded device wait ran out (the proposer fell back to the exact path)");
     return ESES_OK;
 }
 
@@ -1292,6 +1294,15 @@ int eses_mlp_forward(const float *X, int64_t n, const float *params, float *z, v
     if (!X || !params || !z || n < 0 || n > (1LL << 30)) return fail(nullptr, ESES_EINVAL, "bad argument");
     launch_mlp_forward(X, (int)n, params, z, (cudaStream_t)stream);
     if (cudaGetLastError() != cudaSuccess) return fail(nullptr, ESES_ECUDA, "mlp forward launch failed");
+    return ESES_OK;
+}
+
+int eses_mlp_forward_tc(const float *X, int64_t n, const float *params, float *z, int *err, void *stream)
+{
+    if (!X || !params || !z || !err || n < 0 || n > (1LL << 30)) return fail(nullptr, ESES_EINVAL, "bad argument");
+    mlp_init();
+    launch_mlp_forward_tc(X, (int)n, params, z, err, (cudaStream_t)stream);
+    if (cudaGetLastError() != cudaSuccess) return fail(nullptr, ESES_ECUDA, "tensor-core mlp launch failed");
     return ESES_OK;
 }
 

@@ -99,7 +99,9 @@ int launch_tile_targets(const Batch &B, const int8_t *labels, uint8_t *target, c
 // mode 1: MLP + certificate, 2: certificate on every tile; need[t] = 1 for
 // tiles left to the exact classification; counts[0..1] += proposed, certified
 int launch_propose(const Model &M, const Batch &B, int mode, const float *P, float z_far, int8_t *labels,
-                   int *tile_band, int *need, int *counts, cudaStream_t st);
+                   int *tile_band, int *need, int *counts, int *err, cudaStream_t st);
+// the proposer's tensor-core MLP on n rows of features (err |= ERR_TIMEOUT on a wait that ran out)
+int launch_mlp_forward_tc(const float *X, int n, const float *P, float *z, int *err, cudaStream_t st);
 int launch_compact(long long n, const int *need, const int *pos, int *list, cudaStream_t st);
 
 }  // namespace eses

@@ -25,6 +25,7 @@
 #include <algorithm>
 
 #include "eses_kernels.h"
+#include "eses_mlp_tc.cuh"
 #include "eses_tile.cuh"
 
 namespace eses {
@@ -318,38 +319,41 @@ __device__ int certify_tile(const Model &M, const Grid &G, int mol, long long ti
     return -1;
 }
 
-// Proposer: features and score per tile (thread per tile), then the
-// certificate for the tiles scored far (warp per tile); certified tiles are
-// filled, the others flagged for the exact classification.
-// mode 1: MLP + certificate; mode 2: certificate on every tile.
+// Proposer: features and tensor-core score per tile (thread per tile, 128
+// tiles per CTA step), then the certificate for the tiles scored far (warp
+// per tile); certified tiles are filled, the others flagged for the exact
+// classification.  mode 1: MLP + certificate; mode 2: certificate on every tile.
 __global__ void __launch_bounds__(PROP_THREADS) k_propose(Model M, Batch B, int mode, const float *__restrict__ Pg,
                                                           float z_far, int8_t *__restrict__ labels_all,
                                                           int *__restrict__ tile_band, int *__restrict__ need,
-                                                          int *__restrict__ counts)
+                                                          int *__restrict__ counts, int *__restrict__ err)
 {
-    __shared__ float P[MLP_NPARAM];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TcSmem &T = *reinterpret_cast<TcSmem *>(smem_raw);
     __shared__ int far_list[PROP_THREADS];
     __shared__ int n_far;
-    if (mode == 1)
-        for (int k = threadIdx.x; k < MLP_NPARAM; k += PROP_THREADS) P[k] = Pg[k];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t phase = 0;
+    if (mode == 1) tc_setup(T, Pg);
     for (long long base = (long long)blockIdx.x * PROP_THREADS; base < B.n_tiles;
          base += (long long)gridDim.x * PROP_THREADS) {
         if (threadIdx.x == 0) n_far = 0;
         __syncthreads();
         const long long gt = base + threadIdx.x;
-        if (gt < B.n_tiles) {
-            bool far = true;
-            if (mode == 1) {
+        const bool valid = gt < B.n_tiles;
+        bool far = valid;
+        if (mode == 1) {
+            float f[MLP_IN];
+            if (valid) {
                 const int mol = mol_of_tile(B, gt);
                 const Grid &G = B.grid[mol];
-                float f[MLP_IN];
                 tile_features(M, G, mol, gt - G.tile0, f);
-                far = mlp_eval(P, f) < z_far;
             }
-            need[gt] = 1;
-            if (far) far_list[atomicAdd(&n_far, 1)] = (int)threadIdx.x;
+            const float zt = tc_score(T, f, valid, phase, err);  // every thread: block-wide barriers inside
+            far = valid && zt < z_far;
         }
+        if (valid) need[gt] = 1;
+        if (far) far_list[atomicAdd(&n_far, 1)] = (int)threadIdx.x;
         __syncthreads();
         const int nf = n_far;
         for (int k = warp; k < nf; k += PROP_THREADS / 32) {
@@ -380,6 +384,29 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose(Model M, Batch B, int 
         }
         __syncthreads();
     }
+    if (mode == 1) tc_teardown(T, phase);
+}
+
+// The tensor-core MLP on arbitrary rows (n x 32 features): z = MLP(X), BF16
+// weights and activations, FP32 accumulation (the proposer's scoring path).
+__global__ void __launch_bounds__(PROP_THREADS) k_mlp_forward_tc(const float *__restrict__ X, int n,
+                                                                 const float *__restrict__ Pg, float *__restrict__ z,
+                                                                 int *__restrict__ err)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TcSmem &T = *reinterpret_cast<TcSmem *>(smem_raw);
+    uint32_t phase = 0;
+    tc_setup(T, Pg);
+    for (long long base = (long long)blockIdx.x * PROP_THREADS; base < n; base += (long long)gridDim.x * PROP_THREADS) {
+        const long long s = base + threadIdx.x;
+        const bool valid = s < n;
+        float x[MLP_IN];
+#pragma unroll
+        for (int i = 0; i < MLP_IN; ++i) x[i] = valid ? X[s * MLP_IN + i] : 0.0f;
+        const float v = tc_score(T, x, valid, phase, err);
+        if (valid) z[s] = v;
+    }
+    tc_teardown(T, phase);
 }
 
 // list of the tiles flagged in `need`, from their exclusive scan
@@ -395,7 +422,12 @@ __global__ void k_compact(long long n, const int *__restrict__ need, const int *
 // ---------------------------------------------------------------------------
 static size_t grad_smem() { return sizeof(GradSmem); }
 
-void mlp_init() { cudaFuncSetAttribute(k_mlp_grad_part, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem()); }
+void mlp_init()
+{
+    cudaFuncSetAttribute(k_mlp_grad_part, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem());
+    cudaFuncSetAttribute(k_propose, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem));
+    cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem));
+}
 
 int launch_mlp_forward(const float *X, int n, const float *P, float *z, cudaStream_t st)
 {
@@ -438,12 +470,28 @@ int launch_tile_targets(const Batch &B, const int8_t *labels, uint8_t *target, c
     return 1;
 }
 
-int launch_propose(const Model &M, const Batch &B, int mode, const float *P, float z_far, int8_t *labels,
-                   int *tile_band, int *need, int *counts, cudaStream_t st)
+// persistent grids: at most 4 CTAs per SM, so every CTA's 128 TMEM columns fit (512 per SM)
+static int tc_grid(long long rows)
 {
-    const long long g = std::min<long long>((B.n_tiles + PROP_THREADS - 1) / PROP_THREADS, 1 << 20);
-    k_propose<<<(unsigned)std::max(g, 1LL), PROP_THREADS, 0, st>>>(M, B, mode, P, z_far, labels, tile_band, need,
-                                                                  counts);
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long long need = (rows + PROP_THREADS - 1) / PROP_THREADS;
+    return (int)std::max(1LL, std::min(need, 4LL * nsm));
+}
+
+int launch_propose(const Model &M, const Batch &B, int mode, const float *P, float z_far, int8_t *labels,
+                   int *tile_band, int *need, int *counts, int *err, cudaStream_t st)
+{
+    k_propose<<<tc_grid(B.n_tiles), PROP_THREADS, sizeof(TcSmem), st>>>(M, B, mode, P, z_far, labels, tile_band, need,
+                                                                       counts, err);
+    return 1;
+}
+
+int launch_mlp_forward_tc(const float *X, int n, const float *P, float *z, int *err, cudaStream_t st)
+{
+    if (n <= 0) return 0;
+    k_mlp_forward_tc<<<tc_grid(n), PROP_THREADS, sizeof(TcSmem), st>>>(X, n, P, z, err);
     return 1;
 }
 

@@ -59,7 +59,7 @@ SYMBOLS = ["eses_create", "eses_create_device", "eses_create_batch", "eses_run_b
            "eses_labels_device", "eses_num_intersections", "eses_intersections", "eses_intersections_device",
            "eses_area_volume", "eses_stats", "eses_stage_times", "eses_root_failures", "eses_patch_counts",
            "eses_patch_data", "eses_crossing_edges_noalloc", "eses_set_proposer", "eses_num_tiles",
-           "eses_tile_data", "eses_mlp_forward", "eses_mlp_grad_scratch", "eses_mlp_grad", "eses_mlp_adam",
+           "eses_tile_data", "eses_mlp_forward", "eses_mlp_forward_tc", "eses_mlp_grad_scratch", "eses_mlp_grad", "eses_mlp_adam",
            "eses_last_error", "eses_destroy"]
 STAGE_NAMES = ["binning", "pairs", "arcs", "classify", "band", "edge_count", "edge_solve", "edge_polish", "reduce"]
 
@@ -107,6 +107,7 @@ def load():
     lib.eses_num_tiles.argtypes = [P, P]
     lib.eses_tile_data.argtypes = [P, P, P]
     lib.eses_mlp_forward.argtypes = [P, i64, P, P, P]
+    lib.eses_mlp_forward_tc.argtypes = [P, i64, P, P, P, P]
     lib.eses_mlp_grad_scratch.argtypes = [i64]
     lib.eses_mlp_grad.argtypes = [P, P, P, i64, P, P, P, P, P]
     lib.eses_mlp_adam.argtypes = [P, P, P, P, ci, ctypes.c_float, P]
@@ -253,6 +254,10 @@ def _stream(stream):
 
 def eses_mlp_forward(X, n: int, params, z, stream=0):
     _check(load().eses_mlp_forward(_ptr(X), int(n), _ptr(params), _ptr(z), _stream(stream)))
+
+
+def eses_mlp_forward_tc(X, n: int, params, z, err, stream=0):
+    _check(load().eses_mlp_forward_tc(_ptr(X), int(n), _ptr(params), _ptr(z), _ptr(err), _stream(stream)))
 
 
 def eses_mlp_grad_scratch(n: int) -> int:

@@ -214,3 +214,41 @@ def test_gpu_training_learns_far_tiles_and_stays_exact(lib):
     r, st = _run(test_mols, 0.3, eses.ESES_PROPOSER_MLP, params, 0.5)
     _same(r, base)
     assert st["tiles_certified"] > 0.3 * st["tiles"]
+
+
+@gpu
+def test_tensor_core_mlp_matches_the_bf16_oracle(lib):
+    """The proposer's tcgen05 path (BF16 operands, FP32 accumulation) against
+    the FP64 oracle evaluated on the same BF16-rounded weights and inputs
+    (hidden activations rounded to BF16 too): agreement to FP32 summation
+    order; against the FP32 forward kernel to BF16 rounding."""
+    import torch
+    from paper_1809_04352_gb300 import eses
+    n = 1000  # several 128-row groups and a ragged last one
+    p, X, _, _ = _data(n, 11)
+    p = p.astype(np.float32)
+    X = X.astype(np.float32)
+
+    def bf16(a):
+        b = np.asarray(a, np.float32).view(np.uint32)
+        r = ((b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+        return r.view(np.float32).astype(np.float64)
+
+    q = mo.unpack(p.astype(np.float64))
+    W1, W2 = bf16(q["W1"].astype(np.float32)), bf16(q["W2"].astype(np.float32))
+    h1 = bf16(np.maximum(bf16(X) @ W1 + q["b1"], 0.0).astype(np.float32))
+    h2 = np.maximum(h1 @ W2 + q["b2"], 0.0)
+    z_ref = h2 @ q["w3"] + q["b3"]
+    dev = torch.device("cuda")
+    Xd = torch.from_numpy(X).to(dev)
+    Pd = torch.from_numpy(p).to(dev)
+    z = torch.empty(n, dtype=torch.float32, device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    eses.eses_mlp_forward_tc(Xd, n, Pd, z, err)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    zt = z.cpu().numpy().astype(np.float64)
+    scale = max(1.0, np.abs(z_ref).max())
+    assert np.abs(zt - z_ref).max() <= 2e-3 * scale
+    z32, _ = mo.forward(p.astype(np.float64), X.astype(np.float64))
+    assert np.abs(zt - z32).max() <= 0.05 * max(1.0, np.abs(z32).max())
