@@ -10,7 +10,10 @@ point, crossing edges, roots and normals, area and volume.
              eses_run on the library's stream; L2 flushed between steps)
   e2e        points/s through the public C ABI with host buffers: create from
              pinned host atoms, run, copy labels and intersections back
-  plain_fp64 the same step with every stage in FP64 (the plain GPU form)
+  plain_fp64 the same step with every stage in FP64 and no proposer (the
+             plain GPU form)
+  proposer_study  the 50,000-atom globule (h 0.2) with the proposer off, the
+             certificate on every tile, and the trained MLP + certificate
   roofline   the dominant kernel (by event-timed duration; the other heavy
              kernel beside it) against the FP32 ALU peak, with the algorithmic
              flops of the oracle-counted flop model
@@ -181,6 +184,10 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of the autotuner's")
     ap.add_argument("--no-graph", action="store_true", help="eager launches instead of CUDA-graph replay")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-molecule batched workload")
+    ap.add_argument("--proposer", default="mlp", choices=["off", "mlp", "certify"],
+                    help="tile proposer of the headline step (default: the trained MLP with the exact certificate)")
+    ap.add_argument("--no-proposer-study", action="store_true",
+                    help="skip the proposer comparison on the 50,000-atom globule")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -228,9 +235,18 @@ def main():
         return times, stages
 
     # ---- device-resident step (value) --------------------------------------
+    from paper_1809_04352_gb300 import proposer as prop
+    prop_modes = {"off": eses.ESES_PROPOSER_OFF, "mlp": eses.ESES_PROPOSER_MLP,
+                  "certify": eses.ESES_PROPOSER_CERTIFY}
+    params = prop.load_params()
+
+    def set_prop(c, mode):
+        eses.eses_set_proposer(c, prop_modes[mode], params if mode == "mlp" else None, 0.5)
+
     ctx = eses.eses_create(xyz, rad, wl.r_p, wl.h, wl.margin)
     eses.eses_set_option(ctx, eses.ESES_OPT_STREAM, stream.cuda_stream)
     eses.eses_set_option(ctx, eses.ESES_OPT_PROFILE, 1)
+    set_prop(ctx, args.proposer)
     use_graph = not args.no_graph
     eses.eses_set_option(ctx, eses.ESES_OPT_GRAPH, 1 if use_graph else 0)
     tuned = None
@@ -274,6 +290,7 @@ def main():
 
     # ---- plain FP64 form (same step, every stage FP64) ----------------------
     eses.eses_set_option(ctx, eses.ESES_OPT_PRECISION, eses.ESES_PREC_FP64)
+    set_prop(ctx, "off")
     eses.eses_run(ctx)
     t64, s64 = timed_runs(ctx, max(2, min(args.steps, 5)))
     plain_ms = statistics.mean(t64)
@@ -286,13 +303,14 @@ def main():
     lab_pin = torch.empty(npts, dtype=torch.int8).pin_memory()
     caps = [0, 0, 0]
     bufs = None
-    h2d = xyz.nbytes + rad.nbytes
+    h2d = xyz.nbytes + rad.nbytes + (params.nbytes if args.proposer == "mlp" else 0)
     d2h = 0
     e2e_times = []
     for k in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         c2 = eses.eses_create(xyz_pin.numpy(), rad_pin.numpy(), wl.r_p, wl.h, wl.margin)
+        set_prop(c2, args.proposer)
         eses.eses_run(c2)
         eses.eses_labels(c2, lab_pin.numpy().reshape(tuple(int(v) for v in dims)))
         ne = [eses.eses_num_intersections(c2, a) for a in range(3)]
@@ -343,6 +361,41 @@ def main():
     dominant = max(rl, key=lambda k: rl[k]["kernel_ms"])
     roofline = rl[dominant]
     roofline_others = {k: v for k, v in rl.items() if k != dominant}
+
+    # ---- proposer study: the 50,000-atom globule, h 0.2, three modes ---------
+    study = None
+    if not args.no_proposer_study:
+        swl = inputs.WORKLOADS[4]
+        sxyz, srad = inputs.workload_atoms(4)
+        sctx = eses.eses_create(sxyz, srad, swl.r_p, swl.h, swl.margin)
+        eses.eses_set_option(sctx, eses.ESES_OPT_STREAM, stream.cuda_stream)
+        eses.eses_set_option(sctx, eses.ESES_OPT_PROFILE, 1)
+        eses.eses_set_option(sctx, eses.ESES_OPT_GRAPH, 1 if use_graph else 0)
+        study = {"workload": f"{swl.name}: synthetic globule, {sxyz.shape[0]} atoms, r_p {swl.r_p} A, h {swl.h} A, "
+                             f"margin {swl.margin} A"}
+        ref_labels = None
+        for mode in ("off", "certify", "mlp"):
+            set_prop(sctx, mode)
+            for _ in range(2):
+                eses.eses_run(sctx)
+            ts, sts = timed_runs(sctx, max(2, min(args.steps, 5)))
+            sst = eses.eses_stats(sctx)
+            # identical labels in every mode (the certificate keeps them exact)
+            same = None
+            cur = eses.eses_labels(sctx).reshape(-1)
+            if ref_labels is None:
+                ref_labels = cur
+            else:
+                same = bool(np.array_equal(cur, ref_labels))
+            study[mode] = {"ms_per_step": statistics.mean(ts),
+                           "classify_ms": statistics.mean(x["classify"] for x in sts),
+                           "points_per_s": sst["points"] / (statistics.mean(ts) / 1e3),
+                           "tiles": int(sst["tiles"]), "tiles_proposed_far": int(sst["tiles_proposed_far"]),
+                           "tiles_certified": int(sst["tiles_certified"]), "labels_equal_off": same}
+        study["points"] = int(sst["points"])
+        study["mlp_gain_vs_off"] = study["off"]["ms_per_step"] / study["mlp"]["ms_per_step"]
+        study["mlp_gain_vs_certify"] = study["certify"]["ms_per_step"] / study["mlp"]["ms_per_step"]
+        eses.eses_destroy(sctx)
 
     # ---- batched workload: 256 molecules in one context ---------------------
     batch = None
@@ -403,7 +456,8 @@ def main():
                 "gpu_launches": int(st["kernel_launches"]) * args.steps,
                 "roofline": roofline,
                 "roofline_other_kernels": roofline_others,
-                "launch": {"cuda_graph": use_graph, "autotuned": tuned},
+                "launch": {"cuda_graph": use_graph, "autotuned": tuned, "proposer": args.proposer},
+                "proposer_study": study,
                 "batch": batch,
                 "cpu_baseline": cpu,
                 "clocks": clk,

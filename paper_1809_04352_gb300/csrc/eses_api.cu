@@ -718,9 +718,10 @@ int run_guarded(eses_ctx *c)
     } catch (const std::bad_alloc &) {
         return fail(c, ESES_ENOMEM, "device allocation failed");
     } catch (const CaptureGrow &) {
+        // a buffer the plan did not size: plan again (eagerly), capture next time
         drop_graph(c);
         c->planned = false;
-        return fail(c, ESES_ESTATE, "buffer sizes changed under graph capture; run again to re-plan");
+        return run_guarded(c);
     } catch (const std::string &m) {
         return fail(c, ESES_EINVAL, m);
     }
@@ -1004,6 +1005,7 @@ int eses_set_proposer(eses_ctx *c, int mode, const float *params, double p_far)
         return fail(c, ESES_ENOMEM, "device allocation failed");
     }
     drop_graph(c);
+    if (mode != c->proposer) c->planned = false;  // its buffers join the plan
     c->proposer = mode;
     if (mode == ESES_PROPOSER_MLP) c->z_far = (float)log(p_far / (1.0 - p_far));
     return ESES_OK;

@@ -283,39 +283,51 @@ __global__ void k_tile_targets(Batch B, const int8_t *__restrict__ labels_all, u
 }
 
 // Certificate of one tile (whole warp): 0 all points outside, 1 all inside,
-// -1 neither proven.
+// -1 neither proven.  FP32 on the double-float atom copies (relative to the
+// grid origin) and squared distances, with the rounding covered: a squared
+// distance carries a relative error below 1e-6, the thresholds get 1e-4 A of
+// slack, so a certified answer is exact.
 __device__ int certify_tile(const Model &M, const Grid &G, int mol, long long tile)
 {
     const int lane = threadIdx.x & 31;
     const CellGrid cg = M.cg[mol];
+    int tc[3];
+    tile_coords(G, tile, tc);
+    float th[3], tl[3];
     double t[3];
-    tile_centre(G, tile, t);
-    const double delta = 0.5 * (TILE - 1) * G.h * sqrt(3.0);
-    const double eps = 1e-9;
+    for (int a = 0; a < 3; ++a) {
+        const double rel = G.h * ((double)(TILE * tc[a]) + 0.5 * (TILE - 1));
+        th[a] = (float)rel;
+        tl[a] = (float)(rel - (double)th[a]);
+        t[a] = G.lo[a] + rel;
+    }
+    const float delta = (float)(0.5 * (TILE - 1) * G.h * sqrt(3.0));
+    const float slack = 1e-4f, rel_lo = 1.0f - 2e-6f, rel_hi = 1.0f + 2e-6f;
+    const float rp = (float)M.rp;
     // every atom that can matter lies within delta + R_max of t
-    const int nc = (int)ceil((delta + M.Rmax + eps) / M.cell);
+    const int nc = (int)ceil(((double)delta + M.Rmax + 1e-3) / M.cell);
     long long ci[3];
     for (int a = 0; a < 3; ++a) ci[a] = floor_ll((t[a] - cg.clo[a]) / M.cell);
-    double out_m = INFINITY, in_m = -INFINITY;
+    bool not_out = false, in = false;
     for (long long a = max(ci[0] - nc, 0LL); a <= min(ci[0] + nc, (long long)cg.cn[0] - 1); ++a)
         for (long long b = max(ci[1] - nc, 0LL); b <= min(ci[1] + nc, (long long)cg.cn[1] - 1); ++b)
             for (long long c = max(ci[2] - nc, 0LL); c <= min(ci[2] + nc, (long long)cg.cn[2] - 1); ++c) {
                 const int id = cg.coff + (int)((a * cg.cn[1] + b) * cg.cn[2] + c);
                 const int e = M.cell_start[id + 1];
                 for (int k = M.cell_start[id] + lane; k < e; k += 32) {
-                    const double4 at = M.atom[k];
-                    const double dx = t[0] - at.x, dy = t[1] - at.y, dz = t[2] - at.z;
-                    const double d = sqrt(dx * dx + dy * dy + dz * dz);
-                    out_m = fmin(out_m, d - (at.w + M.rp));
-                    in_m = fmax(in_m, at.w - d);
+                    const float4 hi = M.atom_hi[k], lo = M.atom_lo[k];
+                    const float dx = (hi.x - th[0]) + (lo.x - tl[0]);
+                    const float dy = (hi.y - th[1]) + (lo.y - tl[1]);
+                    const float dz = (hi.z - th[2]) + (lo.z - tl[2]);
+                    const float d2 = dx * dx + dy * dy + dz * dz;
+                    const float to = hi.w + rp + delta + slack;   // outside needs d >= R + delta
+                    if (d2 * rel_lo < to * to) not_out = true;
+                    const float ti = hi.w - delta - slack;        // inside needs d < r - delta
+                    if (ti > 0.0f && d2 * rel_hi < ti * ti) in = true;
                 }
             }
-    for (int o = 16; o > 0; o >>= 1) {
-        out_m = fmin(out_m, __shfl_xor_sync(0xffffffffu, out_m, o));
-        in_m = fmax(in_m, __shfl_xor_sync(0xffffffffu, in_m, o));
-    }
-    if (out_m >= delta + eps) return 0;
-    if (in_m > delta + eps) return 1;
+    if (!__any_sync(0xffffffffu, not_out)) return 0;
+    if (__any_sync(0xffffffffu, in)) return 1;
     return -1;
 }
 
