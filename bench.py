@@ -48,6 +48,30 @@ FP32_LANES = 128  # FP32 FMA lanes per SM
 WORKLOAD = 2
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of the globule workload (profiles/k_<kernel>_globule-5000.md),
+# reported only while the kernel's sources are the ones that were captured
+TRAFFIC = {
+    "edge_solve": (59_203_840, {"eses_edges.cu": "2a64725508692f7b", "eses_tile.cuh": "8f8fa1997a5f98d1",
+                                "eses_internal.cuh": "7ce4766849297923"}),
+    "classify": (9_506_560, {"eses_classify.cu": "f72620ef3f59bed9", "eses_tile.cuh": "8f8fa1997a5f98d1",
+                             "eses_internal.cuh": "7ce4766849297923"}),
+}
+
+
+def captured_traffic(kernel):
+    import hashlib
+    entry = TRAFFIC.get(kernel)
+    if entry is None:
+        return None
+    nbytes, shas = entry
+    for f, sha in shas.items():
+        with open(os.path.join(ROOT, "paper_1809_04352_gb300", "csrc", f), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest()[:16] != sha:
+                return None
+    return nbytes
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -356,7 +380,7 @@ def main():
     for name, (kname, flops, ms, extra) in kernels.items():
         achieved = flops / (ms / 1e3) / 1e12
         rl[name] = dict({"bound": "alu", "kernel": kname, "achieved": achieved, "peak": fp32_peak,
-                         "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": captured_traffic(name),
                          "peak_source": psrc_txt, "flops_per_launch": flops, "kernel_ms": ms}, **extra)
     dominant = max(rl, key=lambda k: rl[k]["kernel_ms"])
     roofline = rl[dominant]
