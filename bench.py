@@ -137,10 +137,8 @@ class Clocks:
 
 
 def dist_setup():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    from paper_1809_04352_gb300.scaling import rank_env
+    return rank_env()
 
 
 def cpu_sample(xyz, rad, wl, seed, n_blocks=None, block_pts=32):
@@ -222,7 +220,7 @@ def main():
     import torch
 
     from paper_1809_04352_gb300 import build as libbuild
-    from paper_1809_04352_gb300 import eses, inputs
+    from paper_1809_04352_gb300 import eses, inputs, scaling
 
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
@@ -299,17 +297,8 @@ def main():
                           "kernel_launches_per_step": st["kernel_launches"], "points": npts}))
         eses.eses_destroy(ctx)
         return
-    total_s = sum(times) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-        n = torch.tensor([float(npts)], device="cuda")
-        torch.distributed.all_reduce(n)
-        all_pts = float(n.item())
-    else:
-        all_pts = float(npts)
-    value = all_pts * args.steps / total_s
+    total_s, all_pts = scaling.job_totals(sum(times) / 1e3, float(npts), "cuda")
+    value = scaling.throughput(all_pts, args.steps, total_s)
     stage_ms = {k: statistics.mean(s[k] for s in stages) for k in stages[0]}
 
     # ---- plain FP64 form (same step, every stage FP64) ----------------------
@@ -352,12 +341,8 @@ def main():
         if k >= args.warmup:
             e2e_times.append(t1 - t0)
         d2h = npts + sum(ne) * (8 + 8 + 24) + 16
-    e2e_s = sum(e2e_times)
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = all_pts * args.steps / e2e_s
+    e2e_s = scaling.job_max(sum(e2e_times), "cuda")
+    e2e_value = scaling.throughput(all_pts, args.steps, e2e_s)
 
     # ---- roofline of the dominant kernel ------------------------------------
     peaks, psrc = load_peaks()
@@ -449,15 +434,12 @@ def main():
         torch.cuda.synchronize()
         barrier()
         bst = eses.eses_stats(bctx)
-        btot = sum(bt) / 1e3
-        if world > 1:
-            t = torch.tensor([btot], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            btot = float(t.item())
+        btot, bpts_all = scaling.job_totals(sum(bt) / 1e3, float(bpts), "cuda")
         batch = {"workload": f"{bwl.name}: {len(mols)} synthetic globules, atom counts log-uniform in [300, 20000] "
                              f"({sum(len(r) for _, r in mols)} atoms), r_p {bwl.r_p} A, h {bwl.h} A, "
                              f"margin {bwl.margin} A, one context",
-                 "value": world * bpts * args.steps / btot, "unit": UNIT, "ms_per_step": 1e3 * btot / args.steps,
+                 "value": scaling.throughput(bpts_all, args.steps, btot), "unit": UNIT,
+                 "ms_per_step": 1e3 * btot / args.steps,
                  "points": int(bpts), "crossing_edges": int(bst["crossing_edges"]),
                  "root_failures": int(bst["root_failures"]), "kernel_launches_per_step": int(bst["kernel_launches"]),
                  "graph": use_graph}
