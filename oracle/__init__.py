@@ -77,6 +77,11 @@ def _load():
         lib.eo_model_stats.argtypes = [P, P, i64, d, P, P, P, i64, P, i64]
         lib.eo_model_stats.restype = ctypes.c_int
         lib.eo_num_threads.restype = ctypes.c_int
+        lib.eo_run_sparse.argtypes = [P, P, i64, d, d, d, i64, ctypes.c_int, P, i64]
+        lib.eo_run_sparse.restype = ctypes.c_void_p
+        lib.eo_result_block_region.argtypes = [ctypes.c_void_p, i64, P, P]
+        lib.eo_result_block_region.restype = i64
+        lib.eo_result_block_labels.argtypes = [ctypes.c_void_p, i64, P]
         lib.eo_flop_counts.argtypes = [P, P, i64, d, d, d, ctypes.c_int, P]
         lib.eo_flop_counts.restype = ctypes.c_int
         lib.eo_edge_flop_counts.argtypes = [P, P, i64, d, d, d, P, P, ctypes.c_int, P]
@@ -172,6 +177,44 @@ def run(xyz, radii, r_p: float, h: float, margin: float, block_pts: int = 0, nth
     return Result(dims=dims, lo=lo, h=h, labels=labels, idx=idx, tau=tau, normal=nrm, ptype=pt,
                   area=float(st[0]), volume=float(st[1]), volume_count=float(st[2]),
                   near_ties=int(st[3]), slow_edges=int(st[4]), n_points=int(st[11]))
+
+
+def run_blocks(xyz, radii, r_p: float, h: float, margin: float, block_pts: int, block_ids, nthreads: int = 0):
+    """Algorithm 1 over the listed blocks only, keeping only their owned
+    points' labels: returns (dims, lo, blocks, idx, tau, normal) with blocks a
+    list of (own_lo, own_hi, labels of the owned region); idx are global."""
+    lib = _load()
+    xyz, radii = _atoms(xyz, radii)
+    ids = np.ascontiguousarray(block_ids, dtype=np.int64)
+    res = lib.eo_run_sparse(_ptr(xyz), _ptr(radii), xyz.shape[0], r_p, h, margin, int(block_pts), int(nthreads),
+                            _ptr(ids), ids.shape[0])
+    if not res:
+        raise ValueError("invalid parameters")
+    try:
+        dims = np.zeros(3, np.int64)
+        lo = np.zeros(3, np.float64)
+        lib.eo_result_grid(res, _ptr(dims), _ptr(lo))
+        blocks = []
+        for t in range(ids.shape[0]):
+            blo = np.zeros(3, np.int64)
+            bhi = np.zeros(3, np.int64)
+            cnt = lib.eo_result_block_region(res, t, _ptr(blo), _ptr(bhi))
+            lab = np.empty(tuple(int(v) for v in (bhi - blo)), np.int8)
+            assert cnt == lab.size
+            lib.eo_result_block_labels(res, t, _ptr(lab))
+            blocks.append((blo, bhi, lab))
+        idx, tau, nrm = [], [], []
+        for a in range(3):
+            ne = int(lib.eo_result_num_intersections(res, a))
+            i = np.empty(ne, np.int64)
+            t_ = np.empty(ne, np.float64)
+            nn = np.empty((ne, 3), np.float64)
+            if ne:
+                lib.eo_result_intersections(res, a, _ptr(i), _ptr(t_), _ptr(nn), None)
+            idx.append(i); tau.append(t_); nrm.append(nn)
+    finally:
+        lib.eo_result_free(res)
+    return dims, lo, blocks, idx, tau, nrm
 
 
 def distance(xyz, radii, r_p: float, pts, cap: float, brute: bool = False):

@@ -536,6 +536,11 @@ typedef struct {
     int64_t dims[3];
     double lo[3], h, rp;
     int8_t *labels;
+    /* sparse runs: labels hold only the listed blocks' owned points, block
+     * after block, C order within a block */
+    int sparse;
+    int64_t nblk;
+    int64_t *blk_lo, *blk_hi, *blk_off;
     ivec idx[3];
     dvec tau[3], nrm[3];
     ivec ptype[3];
@@ -584,7 +589,7 @@ typedef struct {
 } BlockOut;
 
 static void run_block(const double *xyz, const double *r, int64_t n, double rp, double h, const int64_t *dims,
-                      const double *lo, BlockOut *bo, int8_t *labels, int brute, int instrument)
+                      const double *lo, BlockOut *bo, int8_t *labels, int8_t *own_out, int brute, int instrument)
 {
     const double cap = rp + 2.0 * h; /* enough for the sphere tracing of a crossing edge */
     /* block box in space (computed points) */
@@ -632,7 +637,11 @@ static void run_block(const double *xyz, const double *r, int64_t n, double rp, 
                 int owned = g[0] < bo->own_hi[0] && g[1] < bo->own_hi[1] && g[2] < bo->own_hi[2];
                 if (owned) {
                     bo->near_ties += nt;
-                    labels[(g[0] * dims[1] + g[1]) * dims[2] + g[2]] = (int8_t)lab; /* LocalToGlobal, Eq. 5 */
+                    if (own_out) /* sparse run: the block's own array */
+                        own_out[((g[0] - bo->own_lo[0]) * (bo->own_hi[1] - bo->own_lo[1]) + (g[1] - bo->own_lo[1])) *
+                                    (bo->own_hi[2] - bo->own_lo[2]) + (g[2] - bo->own_lo[2])] = (int8_t)lab;
+                    else
+                        labels[(g[0] * dims[1] + g[1]) * dims[2] + g[2]] = (int8_t)lab; /* LocalToGlobal, Eq. 5 */
                     bo->n_points++;
                     if (lab) bo->vol_count += 1.0;
                 }
@@ -693,17 +702,22 @@ static int cmp_i64(const void *a, const void *b)
 /* Run the whole grid (block_pts == 0: one block) or a subset of blocks
  * (block_ids != NULL: only those blocks, for timing samples; labels of other
  * points are left at -1).  nthreads <= 0: OpenMP default. */
-eo_result *eo_run(const double *xyz, const double *r, int64_t n, double rp, double h, double margin, int64_t block_pts,
-                  int nthreads, int brute, int instrument, const int64_t *block_ids, int64_t n_block_ids)
+static eo_result *run_impl(const double *xyz, const double *r, int64_t n, double rp, double h, double margin,
+                           int64_t block_pts, int nthreads, int brute, int instrument, const int64_t *block_ids,
+                           int64_t n_block_ids, int sparse)
 {
     if (!(rp > 0.0)) return NULL; /* at r_p = 0 the closed set M is the whole space */
+    if (sparse && !block_ids) return NULL;
     eo_result *res = (eo_result *)calloc(1, sizeof(eo_result));
     if (eo_grid(xyz, r, n, h, margin, res->dims, res->lo) != 0) { free(res); return NULL; }
     res->h = h; res->rp = rp;
+    res->sparse = sparse;
     const int64_t *dims = res->dims;
     int64_t npts = dims[0] * dims[1] * dims[2];
-    res->labels = (int8_t *)malloc((size_t)npts);
-    memset(res->labels, 0xff, (size_t)npts);
+    if (!sparse) {
+        res->labels = (int8_t *)malloc((size_t)npts);
+        memset(res->labels, 0xff, (size_t)npts);
+    }
     int64_t cells[3], nb[3];
     for (int a = 0; a < 3; ++a) {
         if (block_pts <= 1) { cells[a] = dims[a]; nb[a] = 1; }
@@ -724,12 +738,30 @@ eo_result *eo_run(const double *xyz, const double *r, int64_t n, double rp, doub
             bo->cmp_hi[a] = bo->own_hi[a] + 1 < dims[a] ? bo->own_hi[a] + 1 : dims[a];
         }
     }
+    if (sparse) {
+        res->nblk = nrun;
+        res->blk_lo = (int64_t *)malloc(sizeof(int64_t) * 3 * (size_t)(nrun > 0 ? nrun : 1));
+        res->blk_hi = (int64_t *)malloc(sizeof(int64_t) * 3 * (size_t)(nrun > 0 ? nrun : 1));
+        res->blk_off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nrun + 1));
+        res->blk_off[0] = 0;
+        for (int64_t t = 0; t < nrun; ++t) {
+            int64_t e = 1;
+            for (int a = 0; a < 3; ++a) {
+                res->blk_lo[3 * t + a] = bos[t].own_lo[a];
+                res->blk_hi[3 * t + a] = bos[t].own_hi[a];
+                e *= bos[t].own_hi[a] - bos[t].own_lo[a];
+            }
+            res->blk_off[t + 1] = res->blk_off[t] + e;
+        }
+        res->labels = (int8_t *)malloc((size_t)(res->blk_off[nrun] > 0 ? res->blk_off[nrun] : 1));
+    }
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 1)
 #endif
     for (int64_t t = 0; t < nrun; ++t)
-        run_block(xyz, r, n, rp, h, dims, res->lo, &bos[t], res->labels, brute, instrument);
+        run_block(xyz, r, n, rp, h, dims, res->lo, &bos[t], res->labels,
+                  sparse ? res->labels + res->blk_off[t] : NULL, brute, instrument);
     /* OutputInfo: concatenate in block order, then order edges by lower index */
     for (int64_t t = 0; t < nrun; ++t) {
         BlockOut *bo = &bos[t];
@@ -784,12 +816,39 @@ eo_result *eo_run(const double *xyz, const double *r, int64_t n, double rp, doub
     return res;
 }
 
+eo_result *eo_run(const double *xyz, const double *r, int64_t n, double rp, double h, double margin, int64_t block_pts,
+                  int nthreads, int brute, int instrument, const int64_t *block_ids, int64_t n_block_ids)
+{
+    return run_impl(xyz, r, n, rp, h, margin, block_pts, nthreads, brute, instrument, block_ids, n_block_ids, 0);
+}
+
+/* As eo_run over the listed blocks only, storing only their owned points'
+ * labels (for grids too large to hold whole on the host). */
+eo_result *eo_run_sparse(const double *xyz, const double *r, int64_t n, double rp, double h, double margin,
+                         int64_t block_pts, int nthreads, const int64_t *block_ids, int64_t n_block_ids)
+{
+    return run_impl(xyz, r, n, rp, h, margin, block_pts, nthreads, 0, 0, block_ids, n_block_ids, 1);
+}
+
+/* sparse runs: owned region [lo, hi) of block t and its label count; labels of block t */
+int64_t eo_result_block_region(const eo_result *res, int64_t t, int64_t lo[3], int64_t hi[3])
+{
+    if (!res->sparse || t < 0 || t >= res->nblk) return -1;
+    for (int a = 0; a < 3; ++a) { lo[a] = res->blk_lo[3 * t + a]; hi[a] = res->blk_hi[3 * t + a]; }
+    return res->blk_off[t + 1] - res->blk_off[t];
+}
+void eo_result_block_labels(const eo_result *res, int64_t t, int8_t *out)
+{
+    memcpy(out, res->labels + res->blk_off[t], (size_t)(res->blk_off[t + 1] - res->blk_off[t]));
+}
+
 void eo_result_grid(const eo_result *res, int64_t dims[3], double lo[3])
 {
     for (int a = 0; a < 3; ++a) { dims[a] = res->dims[a]; lo[a] = res->lo[a]; }
 }
 void eo_result_labels(const eo_result *res, int8_t *out)
 {
+    if (res->sparse) return;
     memcpy(out, res->labels, (size_t)(res->dims[0] * res->dims[1] * res->dims[2]));
 }
 int64_t eo_result_num_intersections(const eo_result *res, int axis) { return res->idx[axis].n; }
@@ -817,6 +876,7 @@ void eo_result_free(eo_result *res)
 {
     if (!res) return;
     free(res->labels);
+    free(res->blk_lo); free(res->blk_hi); free(res->blk_off);
     for (int a = 0; a < 3; ++a) { free(res->idx[a].v); free(res->tau[a].v); free(res->nrm[a].v); free(res->ptype[a].v); }
     free(res);
 }

@@ -318,3 +318,19 @@ def test_flop_model_edge_tori_two_atoms():
     assert sure > 0
     assert sure <= ec["tori"] <= maybe
     assert ec["model_flops"] == 20 * (ec["vdw_spheres"] + ec["probe_spheres"]) + 150 * ec["tori"]
+
+
+def test_sparse_block_run_equals_dense_run():
+    """The sparse oracle run (labels of the listed blocks only, for grids too
+    large to hold on the host) gives the dense run's labels and edges."""
+    xyz, rad = inputs.protein_like(120, 77, inputs.PROTEIN_DENSITY)
+    full = oracle.run(xyz, rad, RP, 0.3, 0.8, block_pts=16)
+    ids = [3, 17, 40]
+    dims, lo, blocks, idx, tau, nrm = oracle.run_blocks(xyz, rad, RP, 0.3, 0.8, 16, ids)
+    part = oracle.run(xyz, rad, RP, 0.3, 0.8, block_pts=16, block_ids=ids)
+    assert np.array_equal(dims, full.dims) and np.array_equal(lo, full.lo)
+    for blo, bhi, lab in blocks:
+        assert np.array_equal(lab, full.labels[blo[0]:bhi[0], blo[1]:bhi[1], blo[2]:bhi[2]])
+    for a in range(3):
+        assert np.array_equal(idx[a], part.idx[a]) and np.array_equal(tau[a], part.tau[a])
+        assert np.array_equal(nrm[a], part.normal[a])
