@@ -563,35 +563,248 @@ __device__ void arcs_of_pair32(const Model &M, int p, uint8_t *pair_free, int *v
     }
 }
 
-__global__ void k_arcs(Model M, uint8_t *__restrict__ pair_free, int *__restrict__ vert_count)
+// Warp-per-circle form of arcs_of_pair32 (same decisions, same emission
+// order): the lanes gather the common neighbours (ballot compaction, list
+// order), then each lane takes candidates a = lane, lane + 32: its cover of
+// the circle, its end points and their freeness against every other
+// candidate.  Emitted triple points keep the order (a, end point).
+constexpr int ARC_WARPS = 4;
+
+struct ArcWarp {
+    float4 nb[ARC_MAXN];
+    int nbk[ARC_MAXN];
+};
+
+template <bool EMIT>
+__device__ void arcs_of_pair_warp(const Model &M, int p, ArcWarp &W, uint8_t *pair_free, int *vert_count,
+                                  const int *vert_start, double4 *vert)
 {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= M.n_pairs) return;
-    arcs_of_pair32<false>(M, p, pair_free, vert_count, nullptr, nullptr);
+    const unsigned full_mask = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    int2 ij = M.pair_ij[p];
+    const int i = ij.x, j = ij.y;
+    const float4 oh = M.pair_hi[p], ol = M.pair_lo[p], u4 = M.pair_u32[p];
+    const float rho = oh.w;
+    const float ux = u4.x, uy = u4.y, uz = u4.z;
+    const float tx = fabsf(ux) > 0.6f ? 0.0f : 1.0f, ty = fabsf(ux) > 0.6f ? 1.0f : 0.0f;
+    float v1x = -uz * ty, v1y = uz * tx, v1z = ux * ty - uy * tx;
+    const float iv1 = 1.0f / sqrtf(v1x * v1x + v1y * v1y + v1z * v1z);
+    v1x *= iv1; v1y *= iv1; v1z *= iv1;
+    const float v2x = uy * v1z - uz * v1y, v2y = uz * v1x - ux * v1z, v2z = ux * v1y - uy * v1x;
+    const float dlt = 3e-6f;
+    const float4 jh = M.atom_hi[j], jl = M.atom_lo[j];
+    const float djx = (jh.x - oh.x) + (jl.x - ol.x), djy = (jh.y - oh.y) + (jl.y - ol.y),
+                djz = (jh.z - oh.z) + (jl.z - ol.z);
+    const float rpf = (float)M.rp;
+    const float Rj = jh.w + rpf;
+    const double4 cj = M.atom[j];
+    const double Rj64 = cj.w + M.rp;
+    // 1. common neighbours, in list order
+    int n = 0;
+    const int t_end = M.nb_start[i + 1];
+    for (int t0 = M.nb_start[i]; t0 < t_end; t0 += 32) {
+        const int t = t0 + lane;
+        bool keep = false;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        int k = -1;
+        if (t < t_end) {
+            k = M.nb_list[t];
+            if (k != j) {
+                const float4 kh = M.atom_hi[k], kl = M.atom_lo[k];
+                const float dx = (kh.x - oh.x) + (kl.x - ol.x), dy = (kh.y - oh.y) + (kl.y - ol.y),
+                            dz = (kh.z - oh.z) + (kl.z - ol.z);
+                const float Rk = kh.w + rpf;
+                const float ex = dx - djx, ey = dy - djy, ez = dz - djz;
+                const int c = arc_lt(ex * ex + ey * ey + ez * ez, Rk + Rj, 2.0f * dlt);
+                keep = c == 1 || (c < 0 && common_nb(M, k, i, j, cj, Rj64));
+                v = make_float4(dx, dy, dz, Rk);
+            }
+        }
+        const unsigned m = __ballot_sync(full_mask, keep);
+        const int pos = n + __popc(m & ((1u << lane) - 1));
+        if (keep && pos < ARC_MAXN) {
+            W.nb[pos] = v;
+            W.nbk[pos] = k;
+        }
+        n += __popc(m);
+    }
+    __syncwarp();
+    if (n > ARC_MAXN) {  // very crowded circle: the FP64 form, one lane
+        if (lane == 0) arcs_of_pair<EMIT>(M, p, pair_free, vert_count, vert_start, vert);
+        __syncwarp();
+        return;
+    }
+    // 2-3. candidates a = lane + 32 r
+    CircleFrame f;
+    bool have64 = false;
+    int n_partial = 0, n_free_end = 0, n_emit_total = 0;
+    bool full = false;
+    const int w0 = EMIT ? vert_start[p] : 0;
+    for (int r = 0; r * 32 < n; ++r) {
+        const int a = r * 32 + lane;
+        int status = 0;  // 0 none, 1 partial, 2 full
+        bool fr[2] = {false, false};
+        double3 qe[2];
+        bool e64 = false;
+        if (a < n) {
+            const float4 c = W.nb[a];
+            const float d1 = c.x * v1x + c.y * v1y + c.z * v1z;
+            const float d2 = c.x * v2x + c.y * v2y + c.z * v2z;
+            const float dd = c.x * c.x + c.y * c.y + c.z * c.z;
+            const float A = sqrtf(d1 * d1 + d2 * d2);
+            const float num = rho * rho + dd - c.w * c.w, den = 2.0f * rho * A;
+            const float dk = sqrtf(dd);
+            const float en = 2.0f * dk * dlt + 2e-6f * (rho * rho + dd + c.w * c.w);
+            const float ed = 2.0f * rho * (dlt + 3e-7f * dk) + 2e-6f * den;
+            const float err = 2.0f * (en + ed);
+            float qf[2][3];
+            float dq = 1.0f;
+            if (num >= den + err) {
+                status = 0;
+            } else if (num < -den - err) {
+                status = 2;
+            } else {
+                status = 1;
+                if (num < den - err && num > -den + err) {  // partial for certain: FP32 end points
+                    const float T = num / den;
+                    const float sT = sqrtf(fmaxf(0.0f, 1.0f - T * T));
+                    const float iA = 1.0f / A;
+                    const float epx = (d1 * v1x + d2 * v2x) * iA, epy = (d1 * v1y + d2 * v2y) * iA,
+                                epz = (d1 * v1z + d2 * v2z) * iA;
+                    const float enx = uy * epz - uz * epy, eny = uz * epx - ux * epz, enz = ux * epy - uy * epx;
+                    for (int e = 0; e < 2; ++e) {
+                        const float sg = e == 0 ? 1.0f : -1.0f;
+                        qf[e][0] = rho * (T * epx + sg * sT * enx);
+                        qf[e][1] = rho * (T * epy + sg * sT * eny);
+                        qf[e][2] = rho * (T * epz + sg * sT * enz);
+                    }
+                    const float dT = (en + fabsf(T) * ed) / den;
+                    dq = rho * (dT * (1.0f + fabsf(T) / fmaxf(sT, 1e-6f)) + 2.0f * (dlt / fmaxf(A, 1e-6f) + 3e-7f)) +
+                         1e-6f;
+                }
+                if (dq > 2e-4f) {  // undecided cover or loose FP32 end points: FP64
+                    if (!have64) {
+                        f = frame_of(M.pair_o[p], M.pair_u[p]);
+                        have64 = true;
+                    }
+                    const double4 ck = M.atom[W.nbk[a]];
+                    const int cov = cover_of(f, ck, ck.w + M.rp, qe[0], qe[1]);
+                    status = cov;
+                    if (cov == 1) {
+                        for (int e = 0; e < 2; ++e) {
+                            qf[e][0] = (float)(qe[e].x - f.o.x);
+                            qf[e][1] = (float)(qe[e].y - f.o.y);
+                            qf[e][2] = (float)(qe[e].z - f.o.z);
+                        }
+                        dq = 1e-6f;
+                        e64 = true;
+                    }
+                }
+            }
+            if (status == 1) {
+                for (int e = 0; e < 2; ++e) {
+                    bool free_ = true;
+                    for (int b = 0; b < n && free_; ++b) {
+                        if (b == a) continue;
+                        const float4 cb = W.nb[b];
+                        const float ex = qf[e][0] - cb.x, ey = qf[e][1] - cb.y, ez = qf[e][2] - cb.z;
+                        int t = arc_lt(ex * ex + ey * ey + ez * ez, cb.w, dq + dlt);
+                        if (t < 0) {  // FP64: the exact end point against the exact ball
+                            if (!e64) {
+                                if (!have64) {
+                                    f = frame_of(M.pair_o[p], M.pair_u[p]);
+                                    have64 = true;
+                                }
+                                const double4 ck = M.atom[W.nbk[a]];
+                                cover_of(f, ck, ck.w + M.rp, qe[0], qe[1]);
+                                e64 = true;
+                            }
+                            const double4 c64 = M.atom[W.nbk[b]];
+                            const double Rb = c64.w + M.rp;
+                            const double gx = qe[e].x - c64.x, gy = qe[e].y - c64.y, gz = qe[e].z - c64.z;
+                            t = (gx * gx + gy * gy + gz * gz < Rb * Rb) ? 1 : 0;
+                        }
+                        if (t == 1) free_ = false;
+                    }
+                    fr[e] = free_;
+                }
+            }
+        }
+        full = full || __any_sync(full_mask, status == 2);
+        if (full) break;  // uniform
+        int np_ = status == 1 ? 1 : 0, nf_ = (int)fr[0] + (int)fr[1];
+        const bool emits = status == 1 && a < n && W.nbk[a] > j;  // triple i < j < k: emitted once, here
+        int ne_ = emits ? nf_ : 0;
+        // inclusive scan of ne_ over the lanes (the serial order a = 0, 1, ...)
+        int inc = ne_;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(full_mask, inc, o);
+            if (lane >= o) inc += u;
+        }
+        const int tot = __shfl_sync(full_mask, inc, 31);
+        if (EMIT && ne_ > 0) {
+            if (!e64) {
+                if (!have64) {
+                    f = frame_of(M.pair_o[p], M.pair_u[p]);
+                    have64 = true;
+                }
+                const double4 ck = M.atom[W.nbk[a]];
+                cover_of(f, ck, ck.w + M.rp, qe[0], qe[1]);
+            }
+            int wpos = w0 + n_emit_total + inc - ne_;
+            for (int e = 0; e < 2; ++e)
+                if (fr[e]) vert[wpos++] = make_double4(qe[e].x, qe[e].y, qe[e].z, 0.0);
+        }
+        n_emit_total += tot;
+        for (int o = 16; o > 0; o >>= 1) {
+            np_ += __shfl_xor_sync(full_mask, np_, o);
+            nf_ += __shfl_xor_sync(full_mask, nf_, o);
+        }
+        n_partial += np_;
+        n_free_end += nf_;
+    }
+    if (!EMIT && lane == 0) {
+        const bool has_free = !full && (n_partial == 0 || n_free_end > 0);
+        pair_free[p] = has_free ? 1 : 0;
+        vert_count[p] = full ? 0 : n_emit_total;
+    }
+    __syncwarp();
 }
 
-__global__ void k_arcs_emit(Model M, const int *__restrict__ vert_start, double4 *__restrict__ vert,
-                            int *__restrict__ vert_mol)
+__global__ void __launch_bounds__(ARC_WARPS * 32) k_arcs(Model M, uint8_t *__restrict__ pair_free,
+                                                         int *__restrict__ vert_count)
 {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ ArcWarp W[ARC_WARPS];
+    const int warp = threadIdx.x >> 5;
+    const int p = blockIdx.x * ARC_WARPS + warp;
+    if (p >= M.n_pairs) return;  // uniform per warp
+    arcs_of_pair_warp<false>(M, p, W[warp], pair_free, vert_count, nullptr, nullptr);
+}
+
+__global__ void __launch_bounds__(ARC_WARPS * 32) k_arcs_emit(Model M, const int *__restrict__ vert_start,
+                                                              double4 *__restrict__ vert, int *__restrict__ vert_mol)
+{
+    __shared__ ArcWarp W[ARC_WARPS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int p = blockIdx.x * ARC_WARPS + warp;
     if (p >= M.n_pairs) return;
     if (vert_start[p + 1] == vert_start[p]) return;
-    arcs_of_pair32<true>(M, p, nullptr, nullptr, vert_start, vert);
+    arcs_of_pair_warp<true>(M, p, W[warp], nullptr, nullptr, vert_start, vert);
     const int mol = M.atom_mol[M.pair_ij[p].x];
-    for (int k = vert_start[p]; k < vert_start[p + 1]; ++k) vert_mol[k] = mol;
+    for (int k = vert_start[p] + lane; k < vert_start[p + 1]; k += 32) vert_mol[k] = mol;
 }
 
 int launch_arcs(const Model &M, uint8_t *pair_free, int *vert_count, cudaStream_t st)
 {
     if (M.n_pairs <= 0) return 0;
-    k_arcs<<<(M.n_pairs + 127) / 128, 128, 0, st>>>(M, pair_free, vert_count);
+    k_arcs<<<(M.n_pairs + ARC_WARPS - 1) / ARC_WARPS, ARC_WARPS * 32, 0, st>>>(M, pair_free, vert_count);
     return 1;
 }
 
 int launch_arcs_emit(const Model &M, const int *vert_start, double4 *vert, int *vert_mol, cudaStream_t st)
 {
     if (M.n_pairs <= 0) return 0;
-    k_arcs_emit<<<(M.n_pairs + 127) / 128, 128, 0, st>>>(M, vert_start, vert, vert_mol);
+    k_arcs_emit<<<(M.n_pairs + ARC_WARPS - 1) / ARC_WARPS, ARC_WARPS * 32, 0, st>>>(M, vert_start, vert, vert_mol);
     return 1;
 }
 
