@@ -273,8 +273,8 @@ struct EdgeSmem {
     int sh[EDGE_WARPS];
     // the current chunk of edges [c0, c0 + CHUNK): (edge, item) pairs that pass
     // the prefilter, then the roots they give (valid pieces only)
-    int npool, nroot;
-    unsigned pool[POOL_MAX];  // (edge << 16) | item
+    int npool, npool_t, nroot, next_c, next_e;
+    unsigned pool[POOL_MAX];  // (edge << 16) | item: spheres from the front, tori from the back
     WCand root[ROOT_MAX];
     short redge[ROOT_MAX];
     short rorder[ROOT_MAX];   // roots grouped by edge
@@ -986,7 +986,10 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Batch B, T
             const int c1 = min(ne, c0 + csz);
             if (threadIdx.x == 0) {
                 E.npool = 0;
+                E.npool_t = 0;
                 E.nroot = 0;
+                E.next_c = 0;
+                E.next_e = c0;
             }
             for (int k = threadIdx.x; k < CHUNK; k += EDGE_THREADS) E.rfill[k] = 0;
             __syncthreads();
@@ -994,28 +997,50 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Batch B, T
             for (int e = c0 + warp; e < c1; e += EDGE_WARPS) {
                 const EdgeRef R = edge_ref(E, e);
                 const T s[3] = {(T)E.hd[R.p >> 6], (T)E.hd[(R.p >> 3) & 7], (T)E.hd[R.p & 7]};
+                const int nsph = S.na + S.nv;
                 for (int i0 = 0; i0 < nitem; i0 += 32) {
                     const int it = i0 + lane;
                     const bool hit = it < nitem && cand_test<T>(S, s, R.axis, it, hT, rpT, mg);
-                    const unsigned m = __ballot_sync(0xffffffffu, hit);
-                    int base = 0;
-                    if (lane == 0 && m) base = atomicAdd(&E.npool, __popc(m));
-                    base = __shfl_sync(0xffffffffu, base, 0);
-                    const int pos = base + __popc(m & ((1u << lane) - 1));
-                    if (hit && pos < POOL_MAX) E.pool[pos] = ((unsigned)e << 16) | (unsigned)it;
+                    // spheres and tori in separate runs, so a warp of the root phase does one kind
+                    const bool tor = it >= nsph;
+                    const unsigned ms = __ballot_sync(0xffffffffu, hit && !tor);
+                    const unsigned mt = __ballot_sync(0xffffffffu, hit && tor);
+                    int bs = 0, bt = 0;
+                    if (lane == 0) {
+                        if (ms) bs = atomicAdd(&E.npool, __popc(ms));
+                        if (mt) bt = atomicAdd(&E.npool_t, __popc(mt));
+                    }
+                    bs = __shfl_sync(0xffffffffu, bs, 0);
+                    bt = __shfl_sync(0xffffffffu, bt, 0);
+                    const unsigned below = (1u << lane) - 1;
+                    const int pos = tor ? POOL_MAX - 1 - (bt + __popc(mt & below)) : bs + __popc(ms & below);
+                    const int used = tor ? bt + __popc(mt & below) : bs + __popc(ms & below);
+                    if (hit && used < POOL_MAX) E.pool[pos] = ((unsigned)e << 16) | (unsigned)it;
                 }
             }
             __syncthreads();
-            const int npool = E.npool;
+            const int npool_s = E.npool, npool_t = E.npool_t;
+            const int npool = npool_s + npool_t;
             if (npool > POOL_MAX && csz > 1) {
                 csz = (csz + 1) / 2;
                 __syncthreads();
                 continue;
             }
-            // 2. roots of every pair, one thread each
-            for (int k = threadIdx.x; k < min(npool, POOL_MAX); k += EDGE_THREADS) {
-                const unsigned v = E.pool[k];
-                cand_roots<T, FILT>(M, S, x0, E, (int)(v >> 16), (int)(v & 0xffffu), h, rp, d0);
+            // 2. roots of every pair, one thread each; warps take 32 pairs at a
+            //    time from the block's counter (spheres first, then tori)
+            {
+                const int ns = min(npool_s, POOL_MAX), nt_ = min(npool_t, POOL_MAX - ns);
+                for (;;) {
+                    int base = 0;
+                    if (lane == 0) base = atomicAdd(&E.next_c, 32);
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (base >= ns + nt_) break;
+                    const int k = base + lane;
+                    if (k < ns + nt_) {
+                        const unsigned v = k < ns ? E.pool[k] : E.pool[POOL_MAX - 1 - (k - ns)];
+                        cand_roots<T, FILT>(M, S, x0, E, (int)(v >> 16), (int)(v & 0xffffu), h, rp, d0);
+                    }
+                }
             }
             __syncthreads();
             const int nroot = E.nroot;
@@ -1052,8 +1077,12 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Batch B, T
             for (int r = threadIdx.x; r < nr; r += EDGE_THREADS)
                 E.rorder[atomicAdd(&E.rfill[E.redge[r] - c0], 1)] = (short)r;
             __syncthreads();
-            // 4. first root of every edge: one warp per edge
-            for (int e = c0 + warp; e < c1; e += EDGE_WARPS) {
+            // 4. first root of every edge: one warp per edge, edges taken from the block's counter
+            for (;;) {
+                int e = 0;
+                if (lane == 0) e = atomicAdd(&E.next_e, 1);
+                e = __shfl_sync(0xffffffffu, e, 0);
+                if (e >= c1) break;
                 const int b = E.rstart[e - c0], n = E.rstart[e - c0 + 1] - b;
                 for (int k = lane; k < n && k < WCAND; k += 32) E.cand[warp][k] = E.root[E.rorder[b + k]];
                 if (lane == 0) E.ncand[warp] = n;
