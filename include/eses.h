@@ -78,7 +78,7 @@ typedef struct eses_ctx eses_ctx;
 #define ESES_OPT_CLS_TILES 9   /* classification tiles per queue pop (default 4) */
 #define ESES_OPT_EDGE_CTAS 10  /* root-solve CTAs per SM (0 = occupancy limit, default) */
 #define ESES_OPT_EDGE_TILES 11 /* root-solve tiles per queue pop (default 4) */
-#define ESES_OPT_EDGE_CHUNK 12 /* root-solve edges per pooled chunk (0 = the maximum, 64; default) */
+#define ESES_OPT_EDGE_CHUNK 12 /* root-solve edges per pooled chunk at most (0 = the maximum, 128; default) */
 
 #define ESES_PROPOSER_OFF 0      /* classify every tile (default) */
 #define ESES_PROPOSER_MLP 1      /* the MLP scores tiles; those scored far are certified and filled */

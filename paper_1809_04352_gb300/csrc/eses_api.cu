@@ -952,7 +952,7 @@ int eses_autotune(eses_ctx *c, int reps, double *ms_out)
         }
         for (int k = 1; k <= edge_max; ++k)
             for (int per : {1, 4})
-                for (int chunk : {16, 32, edge_chunk_max()}) {
+                for (int chunk : {32, 64, edge_chunk_max()}) {
                     Shape s;
                     s.ctas_per_sm = k;
                     s.tiles_per_pop = per;

@@ -40,7 +40,7 @@ namespace eses {
 constexpr int EDGE_THREADS = 256;
 constexpr int EDGE_WARPS = EDGE_THREADS / 32;
 constexpr int WCAND = 64;        // candidate roots of one edge in the selection buffer
-constexpr int CHUNK = 64;        // edges per chunk of the pooled root solve
+constexpr int CHUNK = 128;       // edges per chunk of the pooled root solve (at most)
 constexpr int POOL_MAX = 2048;   // (edge, item) pairs of a chunk that pass the prefilter
 constexpr int ROOT_MAX = 512;    // valid roots of a chunk
 constexpr int POLISH_THREADS = 256;
@@ -981,7 +981,10 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Batch B, T
         const int nitem = S.na + S.nv + S.np;
         // chunks of edges; a chunk whose candidates or roots overflow the pools
         // is retried at half the size
-        int c0 = 0, csz = chunk0;
+        // chunks of equal size (at most chunk0 edges), so no small last chunk
+        const int nch = (ne + chunk0 - 1) / chunk0;
+        const int cbal = nch > 0 ? (ne + nch - 1) / nch : chunk0;
+        int c0 = 0, csz = cbal;
         while (c0 < ne) {
             const int c1 = min(ne, c0 + csz);
             if (threadIdx.x == 0) {
@@ -1132,7 +1135,7 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Batch B, T
             }
             __syncthreads();
             c0 = c1;
-            csz = chunk0;
+            csz = cbal;
         }
         __syncthreads();
       }
