@@ -232,8 +232,54 @@ static int is_free(const Model *m, const double *q, int e0, int e1, int e2)
 /* Build the patch model of the given atoms: all pairs with an intersection
  * circle (saddle patches) and all free triple points (concave patches).  The
  * probe-clash test of a triple point is the freeness test above. */
-static void model_build(Model *m, const double *xyz, const double *r, const int64_t *gid, int n, double rp, double cap, int brute)
+/* Coincident atoms (the same centre and radius) are one ball: the union of
+ * balls, hence Omega_free and M (§1), does not change when one is dropped,
+ * and keeping both would make each one's sphere "cover" the other's surface
+ * points in floating point.  keep[i] = 0 for every repeat of an earlier atom. */
+typedef struct { double x, y, z, r; int i; } AtomKey;
+static int cmp_atomkey(const void *a, const void *b)
 {
+    const AtomKey *p = (const AtomKey *)a, *q = (const AtomKey *)b;
+    if (p->x != q->x) return p->x < q->x ? -1 : 1;
+    if (p->y != q->y) return p->y < q->y ? -1 : 1;
+    if (p->z != q->z) return p->z < q->z ? -1 : 1;
+    if (p->r != q->r) return p->r < q->r ? -1 : 1;
+    return (p->i > q->i) - (p->i < q->i);
+}
+static int unique_atoms(const double *xyz, const double *r, int n, char *keep)
+{
+    AtomKey *k = (AtomKey *)malloc(sizeof(AtomKey) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) {
+        k[i].x = xyz[3 * i]; k[i].y = xyz[3 * i + 1]; k[i].z = xyz[3 * i + 2]; k[i].r = r[i]; k[i].i = i;
+        keep[i] = 1;
+    }
+    qsort(k, (size_t)n, sizeof(AtomKey), cmp_atomkey);
+    int kept = n;
+    for (int t = 1; t < n; ++t)
+        if (k[t].x == k[t - 1].x && k[t].y == k[t - 1].y && k[t].z == k[t - 1].z && k[t].r == k[t - 1].r) {
+            keep[k[t].i] = 0;
+            --kept;
+        }
+    free(k);
+    return kept;
+}
+
+static void model_build(Model *m, const double *xyz_in, const double *r_in, const int64_t *gid_in, int n_in,
+                        double rp, double cap, int brute)
+{
+    char *keep = (char *)malloc((size_t)(n_in > 0 ? n_in : 1));
+    const int n = unique_atoms(xyz_in, r_in, n_in, keep);
+    double *xyz = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
+    double *r = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    int64_t *gid = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0, k = 0; i < n_in; ++i) {
+        if (!keep[i]) continue;
+        for (int a = 0; a < 3; ++a) xyz[3 * k + a] = xyz_in[3 * i + a];
+        r[k] = r_in[i];
+        gid[k] = gid_in ? gid_in[i] : i;
+        ++k;
+    }
+    free(keep);
     memset(m, 0, sizeof(*m));
     m->n = n; m->rp = rp; m->brute = brute;
     m->c = (double *)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
@@ -370,6 +416,7 @@ static void model_build(Model *m, const double *xyz, const double *r, const int6
     if (m->nv == 0) m->vq = (double *)malloc(24);
     free(VI.v); free(VJ.v); free(VK.v);
     bin_items(m, m->vq, m->nv, &m->v_start, &m->v_list);
+    free(xyz); free(r); free(gid);
 }
 
 /* ------------------------------------------------------------------------ */

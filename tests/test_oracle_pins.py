@@ -334,3 +334,16 @@ def test_sparse_block_run_equals_dense_run():
     for a in range(3):
         assert np.array_equal(idx[a], part.idx[a]) and np.array_equal(tau[a], part.tau[a])
         assert np.array_equal(nrm[a], part.normal[a])
+
+
+def test_coincident_atoms_are_one_ball():
+    """Repeating an atom (same centre and radius) leaves the union of balls,
+    hence the labels, intersections and area/volume, unchanged."""
+    xyz = np.array([[0.1, 0.2, 0.3], [2.9, 0.4, -0.6], [0.7, 2.3, 0.2]])
+    rad = np.array([1.7, 1.55, 1.52])
+    one = oracle.run(xyz, rad, RP, 0.25, 1.0)
+    rep = oracle.run(np.vstack([xyz, xyz[:1], xyz[2:3]]), np.concatenate([rad, rad[:1], rad[2:3]]), RP, 0.25, 1.0)
+    assert np.array_equal(one.labels, rep.labels)
+    for a in range(3):
+        assert np.array_equal(one.idx[a], rep.idx[a]) and np.array_equal(one.tau[a], rep.tau[a])
+    assert one.area == rep.area and one.volume == rep.volume
