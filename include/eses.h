@@ -92,7 +92,9 @@ typedef struct eses_ctx eses_ctx;
 /* Create a context for one molecule.  xyz: host, n_atoms*3 doubles (x,y,z per
  * atom, Angstrom); radii: host, n_atoms doubles.  Both are copied; the caller
  * keeps ownership.  Uses the current CUDA device.  *out receives the context
- * (NULL on failure). */
+ * (NULL on failure).  Coincident atoms (equal centre and radius) are one
+ * ball: repeats are dropped (the union of balls, hence the surface, is the
+ * same); atom indices reported by the library are input indices. */
 int eses_create(const double *xyz, const double *radii, int64_t n_atoms, double r_p, double h, double margin,
                 eses_ctx **out);
 

@@ -103,7 +103,8 @@ struct eses_ctx {
     int precision = ESES_PREC_FP32_FILTERED;
     int block_pts = 64;
     int n_mol = 1;
-    long long n_atoms = 0;  // all molecules
+    long long n_atoms = 0;  // all molecules, coincident repeats dropped
+    std::vector<int64_t> kept;  // input index of every atom of the model
     double rp = 0, h = 0, margin = 0;
     double rmax = 0, Rmax = 0;
     std::vector<MolInfo> mol;
@@ -321,8 +322,61 @@ int create_common(const double *hxyz, const double *hr, const int64_t *counts, i
     std::string msg;
     int rc = validate(hxyz, hr, total, rp, h, margin, msg);
     if (rc) return fail(nullptr, rc, msg);
+    // Coincident atoms (the same centre and radius, within one molecule) are
+    // one ball: the union of balls (§1) does not change without the repeats,
+    // and keeping them would let each sphere "cover" the other's surface.
+    std::vector<int64_t> kept;  // input index of every atom the model uses
+    std::vector<int64_t> kcounts(counts, counts + n_mol);
+    {
+        kept.reserve((size_t)total);
+        long long a0 = 0;
+        std::vector<int64_t> idx;
+        for (int m = 0; m < n_mol; ++m) {
+            idx.resize((size_t)counts[m]);
+            for (long long i = 0; i < counts[m]; ++i) idx[(size_t)i] = a0 + i;
+            auto key_less = [&](int64_t a, int64_t b) {
+                for (int q = 0; q < 3; ++q)
+                    if (hxyz[3 * a + q] != hxyz[3 * b + q]) return hxyz[3 * a + q] < hxyz[3 * b + q];
+                if (hr[a] != hr[b]) return hr[a] < hr[b];
+                return a < b;
+            };
+            std::sort(idx.begin(), idx.end(), key_less);
+            std::vector<char> keep((size_t)counts[m], 1);
+            for (size_t t = 1; t < idx.size(); ++t) {
+                const int64_t a = idx[t - 1], b = idx[t];
+                if (hxyz[3 * a] == hxyz[3 * b] && hxyz[3 * a + 1] == hxyz[3 * b + 1] &&
+                    hxyz[3 * a + 2] == hxyz[3 * b + 2] && hr[a] == hr[b])
+                    keep[(size_t)(b - a0)] = 0;
+            }
+            int64_t nk = 0;
+            for (long long i = 0; i < counts[m]; ++i)
+                if (keep[(size_t)i]) {
+                    kept.push_back(a0 + i);
+                    ++nk;
+                }
+            kcounts[(size_t)m] = nk;
+            a0 += counts[m];
+        }
+    }
+    const bool has_repeats = (long long)kept.size() != total;
+    std::vector<double> cx, cr;
+    if (has_repeats) {
+        cx.resize(3 * kept.size());
+        cr.resize(kept.size());
+        for (size_t k = 0; k < kept.size(); ++k) {
+            for (int q = 0; q < 3; ++q) cx[3 * k + q] = hxyz[3 * kept[k] + q];
+            cr[k] = hr[kept[k]];
+        }
+        hxyz = cx.data();
+        hr = cr.data();
+        counts = kcounts.data();
+        total = (long long)kept.size();
+        dxyz = nullptr;  // upload the de-duplicated host copy
+        dr = nullptr;
+    }
     eses_ctx *c = new (std::nothrow) eses_ctx();
     if (!c) return fail(nullptr, ESES_ENOMEM, "host allocation failed");
+    c->kept = std::move(kept);
     c->n_atoms = total;
     c->n_mol = n_mol;
     c->rp = rp;
@@ -1262,8 +1316,8 @@ int eses_patch_data(const eses_ctx *cc, int32_t *pair_atoms, uint8_t *pair_free,
     if (!ok) return fail(c, ESES_ECUDA, "patch copy failed");
     for (int p = 0; p < np; ++p) {
         if (pair_atoms) {
-            pair_atoms[2 * p] = orig[ij[p].x];
-            pair_atoms[2 * p + 1] = orig[ij[p].y];
+            pair_atoms[2 * p] = (int32_t)c->kept[(size_t)orig[ij[p].x]];
+            pair_atoms[2 * p + 1] = (int32_t)c->kept[(size_t)orig[ij[p].y]];
         }
         if (pair_circle) {
             double *o = pair_circle + 7 * p;

@@ -18,7 +18,7 @@ class _DevView:
     """A device array (pointer, element count, dtype) for torch.as_tensor."""
 
     def __init__(self, ptr, n, typestr):
-        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr), True),
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr), False),
                                          "version": 3}
 
 

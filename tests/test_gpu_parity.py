@@ -120,6 +120,17 @@ SMALL = {
     "far-apart": (np.array([[0.0, 0, 0], [20.0, 0, 0], [0, 15.0, 3.0]]), np.array([1.7, 1.5, 1.8]), 1.4, 0.5, 0.5),
     "small-probe": _cluster(6, 5) + (0.05, 0.25, 1.0),
     "big-probe": _cluster(8, 6) + (3.0, 0.3, 1.0),
+    # degenerate configurations the method has
+    "duplicate-atom": (np.array([[0.1, 0.2, 0.3], [0.1, 0.2, 0.3], [2.9, 0.4, -0.6]]), np.array([1.7, 1.7, 1.55]),
+                       1.4, 0.25, 1.0),
+    "nested-vdw": (np.array([[0.0, 0.0, 0.0], [0.3, -0.2, 0.1], [3.1, 0.9, 0.2]]), np.array([1.8, 1.0, 1.52]),
+                   1.4, 0.25, 1.0),
+    "tangent-expanded": (np.array([[0.0, 0.0, 0.0], [6.2, 0.0, 0.0]]), np.array([1.7, 1.7]), 1.4, 0.23, 1.0),
+    "tetrahedron": (2.2 * np.array([[1.0, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]]) / np.sqrt(3.0) +
+                    np.array([0.013, -0.021, 0.007]), np.full(4, 1.6), 1.4, 0.2, 1.0),
+    "collinear": (np.array([[0.0, 0, 0], [2.5, 0, 0], [5.0, 0, 0], [7.5, 0, 0]]) + 0.0371, np.array([1.7, 1.52, 1.8, 1.55]),
+                  1.4, 0.25, 1.0),
+    "tiny-and-huge": (np.array([[0.0, 0, 0], [3.5, 0.5, 0], [1.0, 3.0, 0.5]]), np.array([3.0, 0.1, 1.2]), 1.4, 0.25, 1.0),
 }
 
 
