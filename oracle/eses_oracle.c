@@ -479,9 +479,14 @@ static double dist_free(const Model *m, const double *x, double cap, Witness *w)
         double y[3] = {x[0] - o[0], x[1] - o[1], x[2] - o[2]};
         double z = dot3(y, u);
         double wv[3] = {y[0] - z * u[0], y[1] - z * u[1], y[2] - z * u[2]};
+        /* the nearest circle point lies along the part of y normal to the
+         * axis; remove the rounding left along u, so that the direction is
+         * normal to u even when x is (numerically) on the axis */
+        double zr = dot3(wv, u);
+        for (int a = 0; a < 3; ++a) wv[a] -= zr * u[a];
         double nw = sqrt(dot3(wv, wv));
         double q[3];
-        if (nw > 0.0) {
+        if (nw > 1e-12 * (1.0 + sqrt(dot3(y, y)))) {
             for (int a = 0; a < 3; ++a) q[a] = o[a] + m->prho[p] * wv[a] / nw;
         } else {
             for (int a = 0; a < 3; ++a) q[a] = o[a] + m->prho[p] * m->pv1[3 * p + a]; /* x on the axis */
