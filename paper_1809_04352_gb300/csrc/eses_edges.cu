@@ -221,11 +221,9 @@ __device__ __forceinline__ void exact_normal(int kind, const double *c, const do
         v[0] = c[0] - y[0]; v[1] = c[1] - y[1]; v[2] = c[2] - y[2];
     } else {  // saddle: towards the nearest point of the circle
         double yo[3] = {y[0] - c[0], y[1] - c[1], y[2] - c[2]};
-        double z = yo[0] * u[0] + yo[1] * u[1] + yo[2] * u[2];
-        double w[3] = {yo[0] - z * u[0], yo[1] - z * u[1], yo[2] - z * u[2]};
-        double nw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-        double k = nw > 0.0 ? rho / nw : 0.0;
-        v[0] = k * w[0] - yo[0]; v[1] = k * w[1] - yo[1]; v[2] = k * w[2] - yo[2];
+        double w[3];
+        axis_normal(yo, u, w);
+        v[0] = rho * w[0] - yo[0]; v[1] = rho * w[1] - yo[1]; v[2] = rho * w[2] - yo[2];
     }
     double vn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
     double iv = vn > 0.0 ? 1.0 / vn : 0.0;
@@ -478,16 +476,16 @@ __device__ __noinline__ void torus_root_exact(const Acc &X, EdgeSmem &E, int e, 
     yd[axis] += t64;
     const double Ad = yd[0] * yd[0] + yd[1] * yd[1] + yd[2] * yd[2] + oe.w * oe.w - rp * rp;
     const double zd = yd[0] * u64[0] + yd[1] * u64[1] + yd[2] * u64[2];
-    const double wd[3] = {yd[0] - zd * u64[0], yd[1] - zd * u64[1], yd[2] - zd * u64[2]};
-    const double nwd = sqrt(wd[0] * wd[0] + wd[1] * wd[1] + wd[2] * wd[2]);
+    double wd[3];
+    const double nwd = axis_normal(yd, u64, wd);  // unit direction
     const double near2 = (nwd - oe.w) * (nwd - oe.w) + zd * zd;
     if (fabs(near2 - rp * rp) > 1e-7 * rp * rp || !(nwd > 0.0) || !(Ad >= 0.0)) return;
-    const double rd = ((nwd - oe.w) * wd[axis] / nwd + zd * u64[axis]) / rp;
+    const double rd = ((nwd - oe.w) * wd[axis] + zd * u64[axis]) / rp;
     const double rate = fabs(rd) <= 1e-9 ? 0.0 : rd;
     if (inside ? rate > 0.0 : rate < 0.0) return;
     const int2 ij = X.pij(pi);
-    const double k64 = oe.w / nwd;
-    const int f = free_pt<false>(X, oo[0] + k64 * wd[0], oo[1] + k64 * wd[1], oo[2] + k64 * wd[2], ij.x, ij.y, rp, 0.0);
+    const int f = free_pt<false>(X, oo[0] + oe.w * wd[0], oo[1] + oe.w * wd[1], oo[2] + oe.w * wd[2], ij.x, ij.y, rp,
+                                 0.0);
     if (f == 1) pool_push(E, e, (float)t64, 0.0f, t64, 1, pi);
 }
 

@@ -394,6 +394,31 @@ __device__ __noinline__ int free_pt(const Acc &A, T qx, T qy, T qz, int e0, int 
     return res;
 }
 
+// Direction from a circle's axis towards y (y relative to the centre, u the
+// unit axis): the part of y normal to u, with the rounding left along u
+// removed, so it is normal to u even next to the axis; on the axis (to 1e-12
+// relative) any unit normal to u -- every circle point is then nearest.
+// Returns |w| before normalisation (0 on the axis) and w as a unit vector.
+__device__ __forceinline__ double axis_normal(const double *y, const double *u, double *w)
+{
+    const double z = y[0] * u[0] + y[1] * u[1] + y[2] * u[2];
+    for (int a = 0; a < 3; ++a) w[a] = y[a] - z * u[a];
+    const double zr = w[0] * u[0] + w[1] * u[1] + w[2] * u[2];
+    for (int a = 0; a < 3; ++a) w[a] -= zr * u[a];
+    const double nw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    if (nw > 1e-12 * (1.0 + sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]))) {
+        for (int a = 0; a < 3; ++a) w[a] /= nw;
+        return nw;
+    }
+    const double ax = fabs(u[0]) > 0.6 ? 0.0 : 1.0, ay = fabs(u[0]) > 0.6 ? 1.0 : 0.0;
+    w[0] = -u[2] * ay;
+    w[1] = u[2] * ax;
+    w[2] = u[0] * ay - u[1] * ax;
+    const double nv = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+    for (int a = 0; a < 3; ++a) w[a] /= nv;
+    return 0.0;
+}
+
 // Witness proposals.  A convex proposal of atom a at x is the radial
 // projection q of x on a's expanded sphere, a saddle proposal of pair p the
 // nearest point q of p's circle; each counts when q is free and closer than
@@ -442,15 +467,14 @@ __device__ __forceinline__ int saddle_proposal(const Acc &A, int p, T x, T y, T 
     int t = lt_sq<FILT>(dist2, thr * thr, thr, T(1.5) * dw + T(1e-6));
     if (t == 0) return 0;
     if (FILT && nw < T(1e-3)) return -2;  // near the circle's axis the nearest point is ill-conditioned
-    if (w2 > T(0)) {
+    if constexpr (FILT) {
         T k = o.w / nw;
         qx = o.x + k * wx; qy = o.y + k * wy; qz = o.z + k * wz;
     } else {
-        // x on the axis: every circle point is nearest; take one
-        T ax = fabs(u.x) > T(0.6) ? T(0) : T(1), ay = fabs(u.x) > T(0.6) ? T(1) : T(0);
-        T vx = -u.z * ay, vy = u.z * ax, vz = u.x * ay - u.y * ax;
-        T nv = sqrt(vx * vx + vy * vy + vz * vz);
-        qx = o.x + o.w * vx / nv; qy = o.y + o.w * vy / nv; qz = o.z + o.w * vz / nv;
+        const double yv[3] = {(double)yx, (double)yy, (double)yz}, uv[3] = {(double)u.x, (double)u.y, (double)u.z};
+        double wn[3];
+        axis_normal(yv, uv, wn);
+        qx = o.x + o.w * (T)wn[0]; qy = o.y + o.w * (T)wn[1]; qz = o.z + o.w * (T)wn[2];
     }
     dq = FILT ? o.w * T(2) * dw / nw + d0 + T(1e-6) * o.w : T(0);
     int2 ij = A.pij(p);
