@@ -425,6 +425,7 @@ static void model_build(Model *m, const double *xyz_in, const double *r_in, cons
 typedef struct {
     int type;         /* EO_TYPE_F/E/V or NONE (no free point closer than cap) */
     int64_t ids[3];   /* global ids of the generating atoms */
+    int loc;          /* model index of the witness' patch: atom (F), pair (E), triple point (V) */
     double q[3];      /* the witness (nearest free point) */
     /* instrumentation for the flop model (counts of candidate work) */
     long n_reach;     /* atoms with |x - c| < r + 2 r_p */
@@ -463,7 +464,7 @@ static double dist_free(const Model *m, const double *x, double cap, Witness *w)
                 if (w) w->n_face_tests++;
                 if (is_free(m, q, i, -1, -1)) {
                     best = dist;
-                    if (w) { w->type = EO_TYPE_F; w->ids[0] = m->gid[i]; w->ids[1] = w->ids[2] = -1; memcpy(w->q, q, sizeof q); }
+                    if (w) { w->type = EO_TYPE_F; w->loc = i; w->ids[0] = m->gid[i]; w->ids[1] = w->ids[2] = -1; memcpy(w->q, q, sizeof q); }
                 }
             }
         }
@@ -495,7 +496,7 @@ static double dist_free(const Model *m, const double *x, double cap, Witness *w)
         if (dist < cap && w) w->n_arc++;
         if (dist < best && is_free(m, q, m->pi[p], m->pj[p], -1)) {
             best = dist;
-            if (w) { w->type = EO_TYPE_E; w->ids[0] = m->gid[m->pi[p]]; w->ids[1] = m->gid[m->pj[p]]; w->ids[2] = -1; memcpy(w->q, q, sizeof q); }
+            if (w) { w->type = EO_TYPE_E; w->loc = p; w->ids[0] = m->gid[m->pi[p]]; w->ids[1] = m->gid[m->pj[p]]; w->ids[2] = -1; memcpy(w->q, q, sizeof q); }
         }
     });
     /* V: free triple points */
@@ -504,7 +505,7 @@ static double dist_free(const Model *m, const double *x, double cap, Witness *w)
         if (w && dist < cap) w->n_vert++;
         if (dist < best) {
             best = dist;
-            if (w) { w->type = EO_TYPE_V; w->ids[0] = m->gid[m->vi[v]]; w->ids[1] = m->gid[m->vj[v]]; w->ids[2] = m->gid[m->vk[v]]; memcpy(w->q, m->vq + 3 * v, 3 * sizeof(double)); }
+            if (w) { w->type = EO_TYPE_V; w->loc = v; w->ids[0] = m->gid[m->vi[v]]; w->ids[1] = m->gid[m->vj[v]]; w->ids[2] = m->gid[m->vk[v]]; memcpy(w->q, m->vq + 3 * v, 3 * sizeof(double)); }
         }
     });
     return best;
@@ -602,6 +603,45 @@ typedef struct {
     int64_t sum_reach, sum_face, sum_face_tests, sum_arc, sum_vert, n_shell, n_points_done;
 } eo_result;
 
+/* Root of the witness' patch next to tau (in [0, 1] units of h): the van der
+ * Waals sphere |y - c_i| = r_i (F: dist = R_i - |y - c_i|), the probe sphere
+ * |y - q_v| = r_p (V), or the torus (|w| - rho)^2 + z^2 = r_p^2 (E, Newton
+ * from tau).  A grazing sphere (discriminant <= 0) touches at its vertex. */
+static double refine_on_patch(const Model *m, const double *s, int axis, double h, double tau, const Witness *w)
+{
+    if (w->type == EO_TYPE_F || w->type == EO_TYPE_V) {
+        const double *c = w->type == EO_TYPE_F ? m->c + 3 * w->loc : m->vq + 3 * w->loc;
+        const double rad = w->type == EO_TYPE_F ? m->r[w->loc] : m->rp;
+        double d[3] = {s[0] - c[0], s[1] - c[1], s[2] - c[2]};
+        double b = d[axis];
+        double disc = b * b - (dot3(d, d) - rad * rad);
+        double t0 = tau * h;
+        if (disc <= 0.0) return -b / h;
+        double sq = sqrt(disc);
+        double r1 = -b - sq, r2 = -b + sq;
+        return (fabs(r1 - t0) <= fabs(r2 - t0) ? r1 : r2) / h;
+    }
+    /* E: Newton on f(t) = (|w| - rho)^2 + z^2 - r_p^2 along the edge */
+    const double *o = m->po + 3 * w->loc, *u = m->pu + 3 * w->loc;
+    const double rho = m->prho[w->loc], rp = m->rp;
+    double t = tau * h;
+    for (int it = 0; it < 100; ++it) {
+        double y[3] = {s[0] - o[0], s[1] - o[1], s[2] - o[2]};
+        y[axis] += t;
+        double z = dot3(y, u);
+        double wv[3] = {y[0] - z * u[0], y[1] - z * u[1], y[2] - z * u[2]};
+        double nw = sqrt(dot3(wv, wv));
+        if (!(nw > 0.0)) break;
+        double f = (nw - rho) * (nw - rho) + z * z - rp * rp;
+        double df = 2.0 * (nw - rho) * wv[axis] / nw + 2.0 * z * u[axis];
+        if (df == 0.0) break;
+        double step = f / df;
+        t -= step;
+        if (fabs(step) <= 1e-16 * (1.0 + fabs(t))) break;
+    }
+    return t / h;
+}
+
 /* Sphere tracing of g(tau) = min(cap, dist(s + tau h e_a)) - r_p from tau = 0
  * (the lower-index end point): step |g|/h never passes a root of the
  * 1-Lipschitz g, so the sequence converges to the first root (Eq. 3-4 with
@@ -624,7 +664,20 @@ static double first_root(const Model *m, const double *s, int axis, double h, do
     /* witness at the final point */
     y[0] = s[0]; y[1] = s[1]; y[2] = s[2];
     y[axis] = s[axis] + tau * h;
-    dist_free(m, y, cap, w);
+    double g0 = fabs(dist_free(m, y, cap, w) - m->rp);
+    /* |g| <= tol bounds the root's position only by tol / |g'|, which is
+     * large where the edge grazes the surface: finish on the equation of the
+     * witness' own patch (the surface there), solved next to tau */
+    if (w && w->type != EO_TYPE_NONE && w->type != EO_TYPE_FREE) {
+        double t = refine_on_patch(m, s, axis, h, tau, w);
+        if (t >= tau - 1e-7 && t <= 1.0 && fabs(t - tau) <= 1e-3) {
+            Witness w2;
+            double y2[3] = {s[0], s[1], s[2]};
+            y2[axis] = s[axis] + t * h;
+            double g2 = fabs(dist_free(m, y2, cap, &w2) - m->rp);
+            if (g2 <= (g0 > 1e-12 ? g0 : 1e-12)) { tau = t; *w = w2; }
+        }
+    }
     return tau;
 }
 
