@@ -63,6 +63,26 @@ def test_single_atom_labels_roots_normals():
         assert np.all(res.ptype[a] == oracle.TYPE_F)
 
 
+def test_single_atom_tangent_edges():
+    """Grid lines tangent to the sphere at a grid point (centre and radius on
+    the grid, all values exact in binary): the distance to the surface is
+    quadratic in tau there, and the root must still be the closed-form one."""
+    c = np.array([[0.0, 0.0, 0.0]])
+    res = oracle.run(c, np.array([1.5]), RP, 0.25, 0.75)
+    assert np.allclose(res.lo, -2.25)
+    tangent = 0
+    for a in range(3):
+        s = _grid_points(res, res.idx[a])
+        for e in range(len(s)):
+            d = s[e] - c[0]
+            if abs(d[a] ** 2 - (d @ d - 2.25)) < 1e-12:  # discriminant zero
+                tangent += 1
+            t = sphere_first_root(s[e], a, res.h, c[0], 1.5)
+            assert t is not None
+            assert abs(t - res.tau[a][e]) * res.h < 1e-9
+    assert tangent >= 8
+
+
 @pytest.mark.parametrize("h,tol", [(0.2, 6e-3), (0.1, 2e-3)])
 def test_single_atom_area_volume_converge(h, tol):
     r = 1.8
