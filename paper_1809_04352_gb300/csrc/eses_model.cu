@@ -113,21 +113,28 @@ int launch_cell_finish(const double *xyz, const double *r, const int *in_mol, in
 
 // --------------------------------------------------------------------------
 // neighbour iteration over the 27 cells around a sorted atom (in the cells of
-// its own molecule)
+// its own molecule), one warp: f(j, valid) on every lane for 32 consecutive
+// atoms of a cell at a time, so the lanes visit the atoms in cell order and
+// ballots over `valid` keep that order
 // --------------------------------------------------------------------------
-#define FOR_NEIGHBOUR_CELLS(M, mol, px, py, pz, j, ...)                                          \
-    do {                                                                                          \
-        const CellGrid g_ = (M).cg[mol];                                                          \
-        int ca_ = cell_coord(px, g_.clo[0], (M).cell, g_.cn[0]);                                  \
-        int cb_ = cell_coord(py, g_.clo[1], (M).cell, g_.cn[1]);                                  \
-        int cc_ = cell_coord(pz, g_.clo[2], (M).cell, g_.cn[2]);                                  \
-        for (int a_ = max(ca_ - 1, 0); a_ <= min(ca_ + 1, g_.cn[0] - 1); ++a_)                    \
-            for (int b_ = max(cb_ - 1, 0); b_ <= min(cb_ + 1, g_.cn[1] - 1); ++b_)                \
-                for (int c_ = max(cc_ - 1, 0); c_ <= min(cc_ + 1, g_.cn[2] - 1); ++c_) {          \
-                    int id_ = g_.coff + (a_ * g_.cn[1] + b_) * g_.cn[2] + c_;                     \
-                    for (int j = (M).cell_start[id_]; j < (M).cell_start[id_ + 1]; ++j) { __VA_ARGS__ } \
-                }                                                                                 \
-    } while (0)
+template <class F>
+__device__ __forceinline__ void warp_neighbour_cells(const Model &M, int mol, double px, double py, double pz, F f)
+{
+    const int lane = threadIdx.x & 31;
+    const CellGrid g = M.cg[mol];
+    const int ca = cell_coord(px, g.clo[0], M.cell, g.cn[0]);
+    const int cb = cell_coord(py, g.clo[1], M.cell, g.cn[1]);
+    const int cc = cell_coord(pz, g.clo[2], M.cell, g.cn[2]);
+    for (int a = max(ca - 1, 0); a <= min(ca + 1, g.cn[0] - 1); ++a)
+        for (int b = max(cb - 1, 0); b <= min(cb + 1, g.cn[1] - 1); ++b)
+            for (int c = max(cc - 1, 0); c <= min(cc + 1, g.cn[2] - 1); ++c) {
+                const int id = g.coff + (a * g.cn[1] + b) * g.cn[2] + c;
+                const int s0 = M.cell_start[id], s1 = M.cell_start[id + 1];
+                for (int j0 = s0; j0 < s1; j0 += 32) f(j0 + lane, j0 + lane < s1);
+            }
+}
+
+constexpr int NB_WARPS = 4;  // warps (atoms) per block of the neighbour and pair kernels
 
 // the circle where expanded spheres (ci, Ri) and (cj, Rj) meet, if any
 __device__ __forceinline__ bool circle_of(double4 ci, double Ri, double4 cj, double Rj, double3 &o, double3 &u,
@@ -148,113 +155,144 @@ __device__ __forceinline__ bool circle_of(double4 ci, double Ri, double4 cj, dou
     return true;
 }
 
-__global__ void k_nb_count(Model M, int *__restrict__ nb_count, int *__restrict__ circle_count,
-                           uint8_t *__restrict__ contained)
+// One warp per atom: neighbours (expanded spheres that overlap), circles, and
+// whether the expanded ball lies inside another one.
+__global__ void __launch_bounds__(NB_WARPS * 32) k_nb_count(Model M, int *__restrict__ nb_count,
+                                                           int *__restrict__ circle_count,
+                                                           uint8_t *__restrict__ contained)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= M.n_atoms) return;
-    double4 ci = M.atom[i];
-    double Ri = ci.w + M.rp;
+    const int i = blockIdx.x * NB_WARPS + (threadIdx.x >> 5);
+    if (i >= M.n_atoms) return;  // uniform per warp
+    const double4 ci = M.atom[i];
+    const double Ri = ci.w + M.rp;
     int nb = 0, nc = 0;
-    uint8_t inside = 0;
-    FOR_NEIGHBOUR_CELLS(M, M.atom_mol[i], ci.x, ci.y, ci.z, j, {
-        if (j != i) {
-            double4 cj = M.atom[j];
-            double Rj = cj.w + M.rp;
-            double dx = cj.x - ci.x, dy = cj.y - ci.y, dz = cj.z - ci.z;
-            double D2 = dx * dx + dy * dy + dz * dz;
-            double S = Ri + Rj;
-            if (D2 < S * S) {
-                ++nb;
-                double3 o, u;
-                double rho;
-                if (circle_of(ci, Ri, cj, Rj, o, u, rho)) ++nc;
-                else if (Rj >= Ri && sqrt(D2) <= Rj - Ri) inside = 1;  // ball i inside ball j
-            }
+    bool inside = false;
+    warp_neighbour_cells(M, M.atom_mol[i], ci.x, ci.y, ci.z, [&](int j, bool valid) {
+        if (!valid || j == i) return;
+        const double4 cj = M.atom[j];
+        const double Rj = cj.w + M.rp;
+        const double dx = cj.x - ci.x, dy = cj.y - ci.y, dz = cj.z - ci.z;
+        const double D2 = dx * dx + dy * dy + dz * dz;
+        const double S = Ri + Rj;
+        if (D2 < S * S) {
+            ++nb;
+            double3 o, u;
+            double rho;
+            if (circle_of(ci, Ri, cj, Rj, o, u, rho)) ++nc;
+            else if (Rj >= Ri && sqrt(D2) <= Rj - Ri) inside = true;  // ball i inside ball j
         }
     });
-    nb_count[i] = nb;
-    circle_count[i] = nc;
-    contained[i] = inside;
+    for (int o = 16; o > 0; o >>= 1) {
+        nb += __shfl_xor_sync(0xffffffffu, nb, o);
+        nc += __shfl_xor_sync(0xffffffffu, nc, o);
+    }
+    inside = __any_sync(0xffffffffu, inside);
+    if ((threadIdx.x & 31) == 0) {
+        nb_count[i] = nb;
+        circle_count[i] = nc;
+        contained[i] = inside ? 1 : 0;
+    }
 }
 
 int launch_nb_count(const Model &M, int *nb_count, int *circle_count, uint8_t *contained, cudaStream_t st)
 {
     if (M.n_atoms <= 0) return 0;
-    k_nb_count<<<(M.n_atoms + 127) / 128, 128, 0, st>>>(M, nb_count, circle_count, contained);
+    k_nb_count<<<(M.n_atoms + NB_WARPS - 1) / NB_WARPS, NB_WARPS * 32, 0, st>>>(M, nb_count, circle_count, contained);
     return 1;
 }
 
-__global__ void k_nb_fill(Model M, int *__restrict__ nb_list)
+// One warp per atom: the neighbour list in cell order (the same order as a
+// serial walk over the 27 cells).
+__global__ void __launch_bounds__(NB_WARPS * 32) k_nb_fill(Model M, int *__restrict__ nb_list)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.x * NB_WARPS + (threadIdx.x >> 5);
     if (i >= M.n_atoms) return;
-    double4 ci = M.atom[i];
-    double Ri = ci.w + M.rp;
+    const int lane = threadIdx.x & 31;
+    const double4 ci = M.atom[i];
+    const double Ri = ci.w + M.rp;
     int w = M.nb_start[i];
-    FOR_NEIGHBOUR_CELLS(M, M.atom_mol[i], ci.x, ci.y, ci.z, j, {
-        if (j != i) {
-            double4 cj = M.atom[j];
-            double Rj = cj.w + M.rp;
-            double dx = cj.x - ci.x, dy = cj.y - ci.y, dz = cj.z - ci.z;
-            double S = Ri + Rj;
-            if (dx * dx + dy * dy + dz * dz < S * S) nb_list[w++] = j;
+    warp_neighbour_cells(M, M.atom_mol[i], ci.x, ci.y, ci.z, [&](int j, bool valid) {
+        bool keep = false;
+        if (valid && j != i) {
+            const double4 cj = M.atom[j];
+            const double Rj = cj.w + M.rp;
+            const double dx = cj.x - ci.x, dy = cj.y - ci.y, dz = cj.z - ci.z;
+            const double S = Ri + Rj;
+            keep = dx * dx + dy * dy + dz * dz < S * S;
         }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) nb_list[w + __popc(m & ((1u << lane) - 1))] = j;
+        w += __popc(m);
     });
 }
 
 int launch_nb_fill(const Model &M, int *nb_list, cudaStream_t st)
 {
     if (M.n_atoms <= 0) return 0;
-    k_nb_fill<<<(M.n_atoms + 127) / 128, 128, 0, st>>>(M, nb_list);
+    k_nb_fill<<<(M.n_atoms + NB_WARPS - 1) / NB_WARPS, NB_WARPS * 32, 0, st>>>(M, nb_list);
     return 1;
 }
 
-__global__ void k_pair_count(Model M, int *__restrict__ pair_count)
+// One warp per atom i: circles with neighbours j > i.
+__global__ void __launch_bounds__(NB_WARPS * 32) k_pair_count(Model M, int *__restrict__ pair_count)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.x * NB_WARPS + (threadIdx.x >> 5);
     if (i >= M.n_atoms) return;
-    double4 ci = M.atom[i];
-    double Ri = ci.w + M.rp;
+    const double4 ci = M.atom[i];
+    const double Ri = ci.w + M.rp;
     int c = 0;
-    for (int t = M.nb_start[i]; t < M.nb_start[i + 1]; ++t) {
-        int j = M.nb_list[t];
+    for (int t = M.nb_start[i] + (threadIdx.x & 31); t < M.nb_start[i + 1]; t += 32) {
+        const int j = M.nb_list[t];
         if (j <= i) continue;
-        double4 cj = M.atom[j];
+        const double4 cj = M.atom[j];
         double3 o, u;
         double rho;
         if (circle_of(ci, Ri, cj, cj.w + M.rp, o, u, rho)) ++c;
     }
-    pair_count[i] = c;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) pair_count[i] = c;
 }
 
 int launch_pair_count(const Model &M, int *pair_count, cudaStream_t st)
 {
     if (M.n_atoms <= 0) return 0;
-    k_pair_count<<<(M.n_atoms + 127) / 128, 128, 0, st>>>(M, pair_count);
+    k_pair_count<<<(M.n_atoms + NB_WARPS - 1) / NB_WARPS, NB_WARPS * 32, 0, st>>>(M, pair_count);
     return 1;
 }
 
-__global__ void k_pair_fill(Model M, const int *__restrict__ pair_start, double4 *__restrict__ pair_o,
-                            double4 *__restrict__ pair_u, int2 *__restrict__ pair_ij)
+// One warp per atom i: the circles with neighbours j > i, in neighbour-list order.
+__global__ void __launch_bounds__(NB_WARPS * 32) k_pair_fill(Model M, const int *__restrict__ pair_start,
+                                                            double4 *__restrict__ pair_o, double4 *__restrict__ pair_u,
+                                                            int2 *__restrict__ pair_ij)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.x * NB_WARPS + (threadIdx.x >> 5);
     if (i >= M.n_atoms) return;
-    double4 ci = M.atom[i];
-    double Ri = ci.w + M.rp;
+    const int lane = threadIdx.x & 31;
+    const double4 ci = M.atom[i];
+    const double Ri = ci.w + M.rp;
     int w = pair_start[i];
-    for (int t = M.nb_start[i]; t < M.nb_start[i + 1]; ++t) {
-        int j = M.nb_list[t];
-        if (j <= i) continue;
-        double4 cj = M.atom[j];
+    const int t1 = M.nb_start[i + 1];
+    for (int t0 = M.nb_start[i]; t0 < t1; t0 += 32) {
+        const int t = t0 + lane;
+        bool keep = false;
         double3 o, u;
-        double rho;
-        if (circle_of(ci, Ri, cj, cj.w + M.rp, o, u, rho)) {
-            pair_o[w] = make_double4(o.x, o.y, o.z, rho);
-            pair_u[w] = make_double4(u.x, u.y, u.z, 0.0);
-            pair_ij[w] = make_int2(i, j);
-            ++w;
+        double rho = 0.0;
+        int j = -1;
+        if (t < t1) {
+            j = M.nb_list[t];
+            if (j > i) {
+                const double4 cj = M.atom[j];
+                keep = circle_of(ci, Ri, cj, cj.w + M.rp, o, u, rho);
+            }
         }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            const int k = w + __popc(m & ((1u << lane) - 1));
+            pair_o[k] = make_double4(o.x, o.y, o.z, rho);
+            pair_u[k] = make_double4(u.x, u.y, u.z, 0.0);
+            pair_ij[k] = make_int2(i, j);
+        }
+        w += __popc(m);
     }
 }
 
@@ -262,7 +300,8 @@ int launch_pair_fill(const Model &M, const int *pair_start, double4 *pair_o, dou
                       cudaStream_t st)
 {
     if (M.n_atoms <= 0) return 0;
-    k_pair_fill<<<(M.n_atoms + 127) / 128, 128, 0, st>>>(M, pair_start, pair_o, pair_u, pair_ij);
+    k_pair_fill<<<(M.n_atoms + NB_WARPS - 1) / NB_WARPS, NB_WARPS * 32, 0, st>>>(M, pair_start, pair_o, pair_u,
+                                                                               pair_ij);
     return 1;
 }
 
@@ -384,14 +423,14 @@ __device__ void arcs_of_pair(const Model &M, int p, uint8_t *pair_free, int *ver
     }
 }
 
-// FP32-filtered form of arcs_of_pair: the common neighbours are cached in
-// FP32 in the circle's frame (from the double-float copies: two roundings of
-// the offset), and every decision -- common neighbour, no/partial/full cover,
+// FP32-filtered form of arcs_of_pair, one warp per circle: the common
+// neighbours are cached in FP32 in the circle's frame (from the double-float
+// copies: two roundings of the offset), and every decision -- common neighbour, no/partial/full cover,
 // end point covered -- is taken in FP32 when it clears its error bound and in
 // FP64 otherwise, so the decisions are those of the FP64 form.  FP32 end
 // points carry a propagated error bound (the FP64 end point is used when that
 // bound exceeds 2e-4 A); emitted triple points are always computed in FP64.
-constexpr int ARC_MAXN = 48;
+constexpr int ARC_MAXN = 128;
 
 // 1: d2 < t^2 certain, 0: d2 >= t^2 certain, -1 undecided (delta: error of the vector)
 __device__ __forceinline__ int arc_lt(float d2, float t, float delta)
@@ -403,171 +442,10 @@ __device__ __forceinline__ int arc_lt(float d2, float t, float delta)
     return -1;
 }
 
-template <bool EMIT>
-__device__ void arcs_of_pair32(const Model &M, int p, uint8_t *pair_free, int *vert_count, const int *vert_start,
-                               double4 *vert)
-{
-    int2 ij = M.pair_ij[p];
-    const int i = ij.x, j = ij.y;
-    // the circle in FP32: centre from its double-float copy, axis, a frame
-    const float4 oh = M.pair_hi[p], ol = M.pair_lo[p], u4 = M.pair_u32[p];
-    const float rho = oh.w;
-    const float ux = u4.x, uy = u4.y, uz = u4.z;
-    const float tx = fabsf(ux) > 0.6f ? 0.0f : 1.0f, ty = fabsf(ux) > 0.6f ? 1.0f : 0.0f;
-    float v1x = -uz * ty, v1y = uz * tx, v1z = ux * ty - uy * tx;
-    const float iv1 = 1.0f / sqrtf(v1x * v1x + v1y * v1y + v1z * v1z);
-    v1x *= iv1; v1y *= iv1; v1z *= iv1;
-    const float v2x = uy * v1z - uz * v1y, v2y = uz * v1x - ux * v1z, v2z = ux * v1y - uy * v1x;
-    // offsets to the circle centre: (hi - hi) + (lo - lo), two roundings of the result
-    const float dlt = 3e-6f;  // error bound of such an offset vector (|offset| <= 2 R_max)
-    const float4 jh = M.atom_hi[j], jl = M.atom_lo[j];
-    const float djx = (jh.x - oh.x) + (jl.x - ol.x), djy = (jh.y - oh.y) + (jl.y - ol.y),
-                djz = (jh.z - oh.z) + (jl.z - ol.z);
-    const float rpf = (float)M.rp;
-    const float Rj = jh.w + rpf;
-    double4 cj = M.atom[j];
-    const double Rj64 = cj.w + M.rp;
-    float4 nb[ARC_MAXN];
-    int nbk[ARC_MAXN];
-    int n = 0;
-    for (int t = M.nb_start[i]; t < M.nb_start[i + 1]; ++t) {
-        int k = M.nb_list[t];
-        if (k == j) continue;
-        const float4 kh = M.atom_hi[k], kl = M.atom_lo[k];
-        float dx = (kh.x - oh.x) + (kl.x - ol.x), dy = (kh.y - oh.y) + (kl.y - ol.y), dz = (kh.z - oh.z) + (kl.z - ol.z);
-        float Rk = kh.w + rpf;
-        float ex = dx - djx, ey = dy - djy, ez = dz - djz;
-        int c = arc_lt(ex * ex + ey * ey + ez * ez, Rk + Rj, 2.0f * dlt);
-        if (c == 0) continue;
-        if (c < 0 && !common_nb(M, k, i, j, cj, Rj64)) continue;
-        if (n == ARC_MAXN) {  // very crowded circle: the FP64 form
-            arcs_of_pair<EMIT>(M, p, pair_free, vert_count, vert_start, vert);
-            return;
-        }
-        nb[n] = make_float4(dx, dy, dz, Rk);
-        nbk[n] = k;
-        ++n;
-    }
-    bool full = false;
-    bool have64 = false;
-    CircleFrame f;
-    int n_partial = 0, n_free_end = 0, n_emit = 0;
-    int w = EMIT ? vert_start[p] : 0;
-    for (int a = 0; a < n && !full; ++a) {
-        const float4 c = nb[a];
-        const float d1 = c.x * v1x + c.y * v1y + c.z * v1z;
-        const float d2 = c.x * v2x + c.y * v2y + c.z * v2z;
-        const float dd = c.x * c.x + c.y * c.y + c.z * c.z;
-        const float A = sqrtf(d1 * d1 + d2 * d2);
-        const float num = rho * rho + dd - c.w * c.w, den = 2.0f * rho * A;
-        const float dk = sqrtf(dd);
-        // error bounds of num and den (offset error dlt, roundings)
-        const float en = 2.0f * dk * dlt + 2e-6f * (rho * rho + dd + c.w * c.w);
-        const float ed = 2.0f * rho * (dlt + 3e-7f * dk) + 2e-6f * den;
-        const float err = 2.0f * (en + ed);
-        if (num >= den + err) continue;  // no cover
-        if (num < -den - err) {          // the whole circle
-            full = true;
-            break;
-        }
-        double3 qe[2];
-        bool e64 = false;
-        float qf[2][3];
-        float dq = 1.0f;
-        if (num < den - err && num > -den + err) {  // partial for certain: FP32 end points
-            const float T = num / den;
-            const float sT = sqrtf(fmaxf(0.0f, 1.0f - T * T));
-            const float iA = 1.0f / A;
-            const float epx = (d1 * v1x + d2 * v2x) * iA, epy = (d1 * v1y + d2 * v2y) * iA,
-                        epz = (d1 * v1z + d2 * v2z) * iA;
-            const float enx = uy * epz - uz * epy, eny = uz * epx - ux * epz, enz = ux * epy - uy * epx;
-            for (int e = 0; e < 2; ++e) {
-                const float sg = e == 0 ? 1.0f : -1.0f;
-                qf[e][0] = rho * (T * epx + sg * sT * enx);
-                qf[e][1] = rho * (T * epy + sg * sT * eny);
-                qf[e][2] = rho * (T * epz + sg * sT * enz);
-            }
-            const float dT = (en + fabsf(T) * ed) / den;
-            dq = rho * (dT * (1.0f + fabsf(T) / fmaxf(sT, 1e-6f)) + 2.0f * (dlt / fmaxf(A, 1e-6f) + 3e-7f)) + 1e-6f;
-        }
-        if (dq > 2e-4f) {  // undecided cover or loose FP32 end points: FP64
-            if (!have64) {
-                f = frame_of(M.pair_o[p], M.pair_u[p]);
-                have64 = true;
-            }
-            double4 ck = M.atom[nbk[a]];
-            int cov = cover_of(f, ck, ck.w + M.rp, qe[0], qe[1]);
-            if (cov == 2) {
-                full = true;
-                break;
-            }
-            if (cov != 1) continue;
-            for (int e = 0; e < 2; ++e) {
-                qf[e][0] = (float)(qe[e].x - f.o.x);
-                qf[e][1] = (float)(qe[e].y - f.o.y);
-                qf[e][2] = (float)(qe[e].z - f.o.z);
-            }
-            dq = 1e-6f;
-            e64 = true;
-        }
-        ++n_partial;
-        bool fr[2];
-        for (int e = 0; e < 2; ++e) {
-            bool free_ = true;
-            for (int b = 0; b < n && free_; ++b) {
-                if (b == a) continue;
-                const float4 cb = nb[b];
-                float ex = qf[e][0] - cb.x, ey = qf[e][1] - cb.y, ez = qf[e][2] - cb.z;
-                int t = arc_lt(ex * ex + ey * ey + ez * ez, cb.w, dq + dlt);
-                if (t < 0) {  // FP64: the exact end point against the exact ball
-                    if (!e64) {
-                        if (!have64) {
-                            f = frame_of(M.pair_o[p], M.pair_u[p]);
-                            have64 = true;
-                        }
-                        double4 ck = M.atom[nbk[a]];
-                        cover_of(f, ck, ck.w + M.rp, qe[0], qe[1]);
-                        e64 = true;
-                    }
-                    double4 c64 = M.atom[nbk[b]];
-                    double Rb = c64.w + M.rp;
-                    double gx = qe[e].x - c64.x, gy = qe[e].y - c64.y, gz = qe[e].z - c64.z;
-                    t = (gx * gx + gy * gy + gz * gz < Rb * Rb) ? 1 : 0;
-                }
-                if (t == 1) free_ = false;
-            }
-            fr[e] = free_;
-        }
-        n_free_end += (int)fr[0] + (int)fr[1];
-        if (nbk[a] > j && (fr[0] || fr[1])) {  // triple i < j < k: emitted once, from the circle (i, j)
-            if (!e64) {
-                if (!have64) {
-                    f = frame_of(M.pair_o[p], M.pair_u[p]);
-                    have64 = true;
-                }
-                double4 ck = M.atom[nbk[a]];
-                cover_of(f, ck, ck.w + M.rp, qe[0], qe[1]);
-                e64 = true;
-            }
-            for (int e = 0; e < 2; ++e)
-                if (fr[e]) {
-                    if (EMIT) vert[w + n_emit] = make_double4(qe[e].x, qe[e].y, qe[e].z, 0.0);
-                    ++n_emit;
-                }
-        }
-    }
-    if (!EMIT) {
-        bool has_free = !full && (n_partial == 0 || n_free_end > 0);
-        pair_free[p] = has_free ? 1 : 0;
-        vert_count[p] = full ? 0 : n_emit;
-    }
-}
-
-// Warp-per-circle form of arcs_of_pair32 (same decisions, same emission
-// order): the lanes gather the common neighbours (ballot compaction, list
-// order), then each lane takes candidates a = lane, lane + 32: its cover of
-// the circle, its end points and their freeness against every other
-// candidate.  Emitted triple points keep the order (a, end point).
+// The lanes gather the common neighbours (ballot compaction, list order;
+// circles with more than ARC_MAXN take the FP64 form on one lane), then each
+// lane takes candidates a = lane, lane + 32, ...: its cover of the circle, its
+// end points and their freeness against every other candidate.  Emitted triple points keep the order (a, end point).
 constexpr int ARC_WARPS = 4;
 
 struct ArcWarp {
