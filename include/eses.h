@@ -56,7 +56,8 @@ extern "C" {
 typedef struct eses_ctx eses_ctx;
 
 #define ESES_OK 0
-#define ESES_EINVAL (-1)    /* invalid argument (sizes, non-finite input, r <= 0, r_p <= 0, h <= 0, margin < h) */
+#define ESES_EINVAL (-1)    /* invalid argument (sizes, non-finite input, r <= 0, r_p <= 0, h <= 0, margin < h,
+                                a molecule's grid of 2^31 or more 8x8x8-point tiles) */
 #define ESES_ENOMEM (-2)    /* host or device allocation failed */
 #define ESES_ECUDA (-3)     /* a CUDA call failed */
 #define ESES_ETIMEOUT (-4)  /* a bounded device wait expired */

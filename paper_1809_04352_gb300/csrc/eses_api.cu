@@ -287,6 +287,7 @@ int setup(eses_ctx *c, const double *xyz, const double *r, const int64_t *counts
         }
         G.h = c->h;
         G.n_tiles = (long long)G.tiles[0] * G.tiles[1] * G.tiles[2];
+        if (G.n_tiles >= (1LL << 31)) return fail(c, ESES_EINVAL, "grid too large (2^31 tiles in one molecule)");
         G.tile0 = c->tile_off[m];
         G.lab0 = lab0;
         c->tile_off[m + 1] = c->tile_off[m] + G.n_tiles;

@@ -132,15 +132,20 @@ __device__ void build_incidence(const TileS<T> &S, ClsSmem &C)
     __syncthreads();
 }
 
-// shell point: witnesses among free triple points, the containing balls and
-// their pairs.  1 inside, 0 outside, 2 undecided.
+// Shell point: witnesses among free triple points, the containing balls and
+// their pairs.  A group of G lanes (G a power of two) shares one point: the
+// candidates (triple points; per containing ball its face, then its incident
+// pairs) are numbered and lane r of the group tests those numbered r mod G.
+// Returns this lane's part: 0 a free witness within r_p (certain), 2 one is
+// undecided, 1 none; the group's label is 0 if any part is 0, else 2 if any
+// part is 2, else 1 -- the label of one lane testing every candidate.
 template <bool FILT, class T>
-__device__ int shell_label(const TileS<T> &S, const ClsSmem &C, int brick, T x, T y, T z, T rp, T d0)
+__device__ int shell_part(const TileS<T> &S, const ClsSmem &C, int brick, T x, T y, T z, T rp, T d0, int r, int G)
 {
     SmemAcc<T> A(S);
     bool unsure = false;
     const T thr = rp, thr2 = rp * rp;
-    for (int v = 0; v < S.nv; ++v) {
+    for (int v = r; v < S.nv; v += G) {
         P4<T> q = S.vq[v];
         T dx = x - q.x, dy = y - q.y, dz = z - q.z;
         int t = lt_sq<FILT>(dx * dx + dy * dy + dz * dz, thr2, thr, d0);
@@ -148,20 +153,26 @@ __device__ int shell_label(const TileS<T> &S, const ClsSmem &C, int brick, T x, 
         if (t < 0) unsure = true;
     }
     const int nb = C.bcount[brick];
+    int u = 0;  // candidate number
     for (int m = 0; m < nb; ++m) {
         int a = C.blist[brick][m];
         P4<T> c = S.atom[a];
         T dx = x - c.x, dy = y - c.y, dz = z - c.z;
         T R = c.w + rp;
         if (lt_sq<FILT>(dx * dx + dy * dy + dz * dz, R * R, R, d0) == 0) continue;  // ball does not hold x
-        int w = face_witness<FILT>(A, a, x, y, z, rp, thr, d0);
-        if (w == 1) return 0;
-        if (w < 0) unsure = true;
-        for (int k = C.inc_start[a]; k < C.inc_start[a + 1]; ++k) {
+        if ((u & (G - 1)) == r) {
+            int w = face_witness<FILT>(A, a, x, y, z, rp, thr, d0);
+            if (w == 1) return 0;
+            if (w < 0) unsure = true;
+        }
+        ++u;
+        const int k0 = C.inc_start[a], k1 = C.inc_start[a + 1];
+        for (int k = k0 + ((r - u) & (G - 1)); k < k1; k += G) {
             int ws = saddle_witness<FILT>(A, (int)C.inc[k], x, y, z, rp, thr, d0);
             if (ws == 1) return 0;
             if (ws < 0) unsure = true;
         }
+        u += k1 - k0;
     }
     return unsure ? 2 : 1;
 }
@@ -273,18 +284,30 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Batch B, Tile
             }
         }
         __syncthreads();
-        // phase 2: shell points, the whole block
+        // phase 2: shell points, the whole block; with few points, groups of
+        // up to 32 lanes share one (so a tile's last point is not left to one lane)
         const int nq = C.nq;
-        for (int k = threadIdx.x; k < nq; k += CLS_THREADS) {
+        int gs = 1;
+        while (gs < 32 && nq * gs * 2 <= CLS_THREADS) gs <<= 1;
+        const int r = lane & (gs - 1);
+        const unsigned gmask = (gs == 32 ? 0xffffffffu : ((1u << gs) - 1u)) << (lane & ~(gs - 1));
+        for (int k = threadIdx.x / gs; k < nq; k += CLS_THREADS / gs) {
             int code = C.queue[k];
             int brick = (code >> 9) & 15;
             int li = (code >> 6) & 7, lj = (code >> 3) & 7, lk = code & 7;
-            long long gi = (long long)TILE * t[0] + li, gj = (long long)TILE * t[1] + lj,
-                      gk = (long long)TILE * t[2] + lk;
             T x = pt_coord<T>(G, li), y = pt_coord<T>(G, lj), z = pt_coord<T>(G, lk);
-            int lab = shell_label<FILT>(S, C, brick, x, y, z, rp, d0);
-            labels[(gi * G.dims[1] + gj) * G.dims[2] + gk] = (int8_t)lab;
-            if (FILT && lab == LABEL_BAND) atomicAdd(&C.band, 1);
+            int part = shell_part<FILT>(S, C, brick, x, y, z, rp, d0, r, gs);
+            // group label: 0 if any part found a witness, else 2 if any is undecided, else 1
+            for (int o = 1; o < gs; o <<= 1) {
+                const int q = __shfl_xor_sync(gmask, part, o);
+                part = (part == 0 || q == 0) ? 0 : max(part, q);
+            }
+            if (r == 0) {
+                long long gi = (long long)TILE * t[0] + li, gj = (long long)TILE * t[1] + lj,
+                          gk = (long long)TILE * t[2] + lk;
+                labels[(gi * G.dims[1] + gj) * G.dims[2] + gk] = (int8_t)part;
+                if (FILT && part == LABEL_BAND) atomicAdd(&C.band, 1);
+            }
         }
         __syncthreads();
         if (threadIdx.x == 0 && tile_band) tile_band[gt] = C.band;

@@ -60,7 +60,7 @@ struct TileS {
     int cs[3][STAGE_CELLS + 1];     // prefix of their atoms / pairs / vertices
     double fx0[3], fx1[3];          // tile region (absolute), computed once per tile
     float fh0[3], fl0[3];           // region origin in the grid frame, double-float
-    int fc0[3], fnc[3];             // cell range of the region plus halo
+    int fc0[3], fc1[3];             // cell range of the region plus halo
     int na, np, nv, flags;
 };
 
@@ -133,11 +133,15 @@ __device__ __forceinline__ double box_dist2(double x, double y, double z, const 
     return ex * ex + ey * ey + ez * ez;
 }
 
+// tile index within its molecule -> tile coordinates (fewer than 2^31 tiles
+// per molecule, checked at create: 32-bit division)
 __device__ __forceinline__ void tile_coords(const Grid &G, long long tile, int t[3])
 {
-    t[2] = (int)(tile % G.tiles[2]);
-    t[1] = (int)((tile / G.tiles[2]) % G.tiles[1]);
-    t[0] = (int)(tile / ((long long)G.tiles[1] * G.tiles[2]));
+    const unsigned tt = (unsigned)tile, n2 = (unsigned)G.tiles[2], n1 = (unsigned)G.tiles[1];
+    const unsigned q = tt / n2;
+    t[2] = (int)(tt - q * n2);
+    t[1] = (int)(q % n1);
+    t[0] = (int)(q / n1);
 }
 
 // Test one cell item against the region and append it (atoms, pairs, vertices).
@@ -251,25 +255,31 @@ __device__ __forceinline__ void stage_item(const Model &M, TileS<T> &S, int list
     }
 }
 
-// Stage the tile's atoms, free-arc pairs and free vertices (whole block).
+// Stage the tile's atoms, free-arc pairs and free vertices (whole block of at
+// least 96 threads).
 // The items of every cell in range are numbered by a prefix over the cells
 // and tested one per thread, so all threads share the work.
 template <class T>
 __device__ void stage_tile(const Model &M, const Grid &G, int mol, long long tile, TileS<T> &S, double x0[3])
 {
     const CellGrid &CG = M.cg[mol];
-    if (threadIdx.x == 0) {  // the tile frame, once per tile (FP64 arithmetic is scarce)
+    if (threadIdx.x < 6) {  // the tile frame, once per tile: one thread per axis and end
         int t[3];
         tile_coords(G, tile, t);
-        for (int a = 0; a < 3; ++a) {
-            const double rel = G.h * (double)(TILE * t[a]);  // region origin in the grid frame
-            S.fx0[a] = G.lo[a] + rel;
-            S.fx1[a] = S.fx0[a] + G.h * (double)TILE;
+        const int a = threadIdx.x < 3 ? threadIdx.x : threadIdx.x - 3;
+        const double rel = G.h * (double)(TILE * t[a]);  // region origin in the grid frame
+        const double fx0 = G.lo[a] + rel, fx1 = fx0 + G.h * (double)TILE;
+        if (threadIdx.x < 3) {
+            S.fx0[a] = fx0;
+            S.fx1[a] = fx1;
             S.fh0[a] = (float)rel;
             S.fl0[a] = (float)(rel - (double)S.fh0[a]);
-            S.fc0[a] = cell_coord_d(S.fx0[a] - G.halo, CG.clo[a], M.cell, CG.cn[a]);
-            S.fnc[a] = cell_coord_d(S.fx1[a] + G.halo, CG.clo[a], M.cell, CG.cn[a]) - S.fc0[a] + 1;
+            S.fc0[a] = cell_coord_d(fx0 - G.halo, CG.clo[a], M.cell, CG.cn[a]);
+        } else {
+            S.fc1[a] = cell_coord_d(fx1 + G.halo, CG.clo[a], M.cell, CG.cn[a]);
         }
+    }
+    if (threadIdx.x == 32) {
         S.na = 0;
         S.np = 0;
         S.nv = 0;
@@ -287,7 +297,7 @@ __device__ void stage_tile(const Model &M, const Grid &G, int mol, long long til
         F.b0[a] = F.h0[a];
         F.b1[a] = F.h0[a] + G.ht_hi;
         c0[a] = S.fc0[a];
-        nc[a] = S.fnc[a];
+        nc[a] = S.fc1[a] - S.fc0[a] + 1;
     }
     const int ncell = nc[0] * nc[1] * nc[2];
     if (ncell <= STAGE_CELLS) {
