@@ -769,22 +769,56 @@ __device__ int warp_select(const Model &M, const TileS<T> &S, const double *x0, 
             break;
         }
         int r;
-        if (FILT && c[k].t64 != c[k].t64) {
+        unsigned um_prop = 0u, um_vert = 0u;
+        if (FILT) {
+            // FP32 position: the FP32 root and its bound, or the exact root
+            // rounded (its rounding and that of the sum within 2e-7 A)
+            const bool ex = c[k].t64 == c[k].t64;
             T y0 = s[0], y1 = s[1], y2 = s[2];
-            T tt = (T)c[k].t;
+            T tt = ex ? (T)c[k].t64 : (T)c[k].t;
             if (axis == 0) y0 += tt;
             else if (axis == 1) y1 += tt;
             else y2 += tt;
-            r = warp_witness<true>(A, y0, y1, y2, rpT, rpT, d0 + (T)c[k].err, c[k].kind, c[k].id);
+            const T dk = d0 + (ex ? T(2e-7) : (T)c[k].err);
+            // First the witnesses of the other remaining candidates' pieces at
+            // y_k: the crossing is a later candidate, whose witness at y_k is
+            // usually free and closer than r_p (then y_k is strictly outside M).
+            // Only a certain answer counts; otherwise the full search decides.
+            T qx = T(0), qy = T(0), qz = T(0), dq = T(0);
+            int e0 = -1, e1 = -1, tw = 0;
+            bool vnear = false;
+            if (lane < n && lane != k && c[lane].t < INFINITY &&
+                !(c[lane].kind == c[k].kind && c[lane].id == c[k].id)) {
+                const int id = c[lane].id;
+                if (c[lane].kind == 0) {
+                    tw = face_proposal<true>(A, id, y0, y1, y2, rpT, rpT, dk, qx, qy, qz, dq, e0, e1);
+                } else if (c[lane].kind == 1) {
+                    tw = saddle_proposal<true>(A, id, y0, y1, y2, rpT, rpT, dk, qx, qy, qz, dq, e0, e1);
+                } else {  // a free triple point closer than r_p
+                    const P4<T> v = A.vq(id);
+                    const T dx = y0 - v.x, dy = y1 - v.y, dz = y2 - v.z;
+                    vnear = lt_sq<true>(dx * dx + dy * dy + dz * dz, rpT * rpT, rpT, dk) == 1;
+                }
+            }
+            bool und = false, mine = false;
+            if (__any_sync(0xffffffffu, vnear) ||
+                warp_test_proposals<true>(A, __ballot_sync(0xffffffffu, tw == 1), tw, qx, qy, qz, dq, e0, e1, rpT,
+                                          dk, und, mine) == 1)
+                r = 1;
+            else
+                r = warp_witness<true>(A, y0, y1, y2, rpT, rpT, dk, c[k].kind, c[k].id, um_prop, um_vert);
         } else {
-            r = -1;
+            r = -2;
         }
-        if (r < 0) {
+        if (r < 0) {  // FP64 at the exact root: the undecided items only, or the whole search
             double t64 = c[k].t64;
             if (t64 != t64) t64 = staged_exact_root(X, c[k].kind, c[k].id, s64, axis, rp, (double)c[k].t);
             double y[3] = {s64[0], s64[1], s64[2]};
             y[axis] += t64;
-            r = warp_witness<false>(X, y[0], y[1], y[2], rp, rp - 1e-11, 0.0, -1, -1);
+            if (r == -1)
+                r = warp_witness_retest(X, y[0], y[1], y[2], rp, rp - 1e-11, um_prop, um_vert);
+            else
+                r = warp_witness<false>(X, y[0], y[1], y[2], rp, rp - 1e-11, 0.0, -1, -1, um_prop, um_vert);
         }
         if (r == 0) {
             pick = k;

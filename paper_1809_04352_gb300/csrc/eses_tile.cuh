@@ -545,18 +545,20 @@ __device__ __forceinline__ int warp_free(const Acc &A, T qx, T qy, T qz, int e0,
 
 // Proposals held by the lanes in `mask`, tested one after the other by the
 // whole warp: 1 as soon as one is free and certainly within thr; else
-// und is set when one could be.
+// und is set when one could be, and `mine` on the lanes whose proposal could be.
 template <bool FILT, class Acc, class T>
 __device__ __forceinline__ int warp_test_proposals(const Acc &A, unsigned mask, int tw, T qx, T qy, T qz, T dq, int e0,
-                                                   int e1, T rp, T d0, bool &und)
+                                                   int e1, T rp, T d0, bool &und, bool &mine)
 {
     const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     while (mask) {
         const int b = __ffs(mask) - 1;
         mask &= mask - 1;
         const int btw = __shfl_sync(full, tw, b);
         if (btw == -2) {
             und = true;
+            if (lane == b) mine = true;
             continue;
         }
         const T bx = __shfl_sync(full, qx, b), by = __shfl_sync(full, qy, b), bz = __shfl_sync(full, qz, b);
@@ -564,7 +566,10 @@ __device__ __forceinline__ int warp_test_proposals(const Acc &A, unsigned mask, 
         const int b0 = __shfl_sync(full, e0, b), b1 = __shfl_sync(full, e1, b);
         const int f = warp_free<FILT>(A, bx, by, bz, b0, b1, rp, bd + d0);
         if (f == 1 && btw == 1) return 1;
-        if (f != 0) und = true;
+        if (f != 0) {
+            und = true;
+            if (lane == b) mine = true;
+        }
     }
     return 0;
 }
@@ -612,11 +617,18 @@ __device__ int classify_pt(const Acc &A, T x, T y, T z, T rp, T thr, T d0)
 
 // Warp-cooperative witness search at one point (all 32 lanes call it with the
 // same point): 1 if a free probe centre lies at distance < thr (certain),
-// 0 if none does (certain), -1 undecided.  Items (exclude_kind, exclude_id)
-// are skipped: kind 0 atom (convex witness), 1 pair, 2 vertex, -1 none.
+// 0 if none does (certain), -1 undecided with the undecided triple points and
+// proposals flagged (um_vert, um_prop: on the lane that holds the item, bit r
+// for item r * 32 + lane; proposals are numbered atoms first, then pairs),
+// -2 undecided whether the point lies in an expanded ball (nothing flagged).
+// Items (exclude_kind, exclude_id) are skipped: kind 0 atom (convex witness),
+// 1 pair, 2 vertex, -1 none.
 template <bool FILT, class Acc, class T>
-__device__ __noinline__ int warp_witness(const Acc &A, T x, T y, T z, T rp, T thr, T d0, int exclude_kind, int exclude_id)
+__device__ __noinline__ int warp_witness(const Acc &A, T x, T y, T z, T rp, T thr, T d0, int exclude_kind,
+                                         int exclude_id, unsigned &um_prop, unsigned &um_vert)
 {
+    um_prop = 0u;
+    um_vert = 0u;
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int na = A.na(), np = A.np(), nv = A.nv();
@@ -632,7 +644,7 @@ __device__ __noinline__ int warp_witness(const Acc &A, T x, T y, T z, T rp, T th
         else if (s < 0) sas_u = true;
     }
     if (__any_sync(full, vdw)) return 0;
-    if (!__any_sync(full, sas)) return __any_sync(full, sas_u) ? -1 : 1;
+    if (!__any_sync(full, sas)) return __any_sync(full, sas_u) ? -2 : 1;
     bool found = false, und = false;
     const T thr2 = thr * thr;
     for (int v = lane; v < nv; v += 32) {
@@ -641,7 +653,10 @@ __device__ __noinline__ int warp_witness(const Acc &A, T x, T y, T z, T rp, T th
         T dx = x - q.x, dy = y - q.y, dz = z - q.z;
         int t = lt_sq<FILT>(dx * dx + dy * dy + dz * dz, thr2, thr, d0);
         if (t == 1) found = true;
-        else if (t < 0) und = true;
+        else if (t < 0) {
+            und = true;
+            um_vert |= 1u << (v >> 5);
+        }
     }
     if (__any_sync(full, found)) return 1;
     und = __any_sync(full, und);
@@ -658,9 +673,47 @@ __device__ __noinline__ int warp_witness(const Acc &A, T x, T y, T z, T rp, T th
                 tw = saddle_proposal<FILT>(A, i - na, x, y, z, rp, thr, d0, qx, qy, qz, dq, e0, e1);
         }
         const unsigned m = __ballot_sync(full, tw != 0);
-        if (warp_test_proposals<FILT>(A, m, tw, qx, qy, qz, dq, e0, e1, rp, d0, und) == 1) return 1;
+        bool mine = false;
+        if (warp_test_proposals<FILT>(A, m, tw, qx, qy, qz, dq, e0, e1, rp, d0, und, mine) == 1) return 1;
+        if (mine) um_prop |= 1u << (i0 >> 5);
     }
     return und ? -1 : 0;
+}
+
+// FP64 re-test of the items that a warp_witness<true> pass at the same point
+// left undecided (um_prop, um_vert from that pass).  Its other items were
+// decided for every position within its error bound, the exact point among
+// them, so this gives the FP64 search's answer: 1 if a free probe centre lies
+// at distance < thr, else 0.
+template <class Acc>
+__device__ __noinline__ int warp_witness_retest(const Acc &X, double x, double y, double z, double rp, double thr,
+                                                unsigned um_prop, unsigned um_vert)
+{
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int na = X.na(), np = X.np(), nv = X.nv();
+    bool found = false;
+    for (int v = lane; v < nv; v += 32) {
+        if (!((um_vert >> (v >> 5)) & 1u)) continue;
+        const P4<double> q = X.vq(v);
+        const double dx = x - q.x, dy = y - q.y, dz = z - q.z;
+        if (dx * dx + dy * dy + dz * dz < thr * thr) found = true;
+    }
+    if (__any_sync(full, found)) return 1;
+    for (int i0 = 0; i0 < na + np; i0 += 32) {
+        const int i = i0 + lane;
+        double qx = 0.0, qy = 0.0, qz = 0.0, dq = 0.0;
+        int e0 = -1, e1 = -1, tw = 0;
+        if ((um_prop >> (i0 >> 5)) & 1u) {
+            if (i < na) tw = face_proposal<false>(X, i, x, y, z, rp, thr, 0.0, qx, qy, qz, dq, e0, e1);
+            else tw = saddle_proposal<false>(X, i - na, x, y, z, rp, thr, 0.0, qx, qy, qz, dq, e0, e1);
+        }
+        bool und = false, mine = false;
+        if (warp_test_proposals<false>(X, __ballot_sync(full, tw != 0), tw, qx, qy, qz, dq, e0, e1, rp, 0.0, und,
+                                       mine) == 1)
+            return 1;
+    }
+    return 0;
 }
 
 }  // namespace eses
