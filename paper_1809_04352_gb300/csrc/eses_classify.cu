@@ -17,8 +17,8 @@
 //   T = double, FILT = false is the plain FP64 form; T = float, FILT = true
 //   is the filtered form, whose undecided points get LABEL_BAND and are
 //   counted per tile.
-// k_band: re-labels the undecided points of the tiles that have any, in FP64,
-//   with the same per-point code over every staged item.
+// k_band: re-labels the undecided points of the tiles that have any, in FP64:
+//   one warp per point runs the witness search over every staged item.
 #include "eses_kernels.h"
 #include "eses_tile.cuh"
 
@@ -322,8 +322,19 @@ __global__ void __launch_bounds__(CLS_THREADS) k_band(Model M, Batch B, int8_t *
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileS<double> &S = *reinterpret_cast<TileS<double> *>(smem_raw);
     __shared__ Grid sG;
-    for (long long gt = blockIdx.x; gt < B.n_tiles; gt += gridDim.x) {
-        if (tile_band[gt] == 0) continue;  // uniform across the block
+    __shared__ int s_list[CLS_THREADS];
+    __shared__ short s_pts[TILE_PTS];
+    __shared__ int s_n, s_np;
+    // chunks of CLS_THREADS tiles: the threads pick out the tiles with
+    // undecided points, then the block re-labels them one after the other
+    for (long long c0 = (long long)blockIdx.x * CLS_THREADS; c0 < B.n_tiles; c0 += (long long)gridDim.x * CLS_THREADS) {
+      if (threadIdx.x == 0) s_n = 0;
+      __syncthreads();
+      if (c0 + threadIdx.x < B.n_tiles && tile_band[c0 + threadIdx.x] != 0) s_list[atomicAdd(&s_n, 1)] = threadIdx.x;
+      __syncthreads();
+      const int nband = s_n;
+      for (int q = 0; q < nband; ++q) {
+        const long long gt = c0 + s_list[q];
         const int mol = mol_of_tile(B, gt);
         load_grid(B, mol, sG);
         const Grid &G = sG;
@@ -335,24 +346,34 @@ __global__ void __launch_bounds__(CLS_THREADS) k_band(Model M, Batch B, int8_t *
         int t[3];
         tile_coords(G, tile, t);
         SmemAcc<double> A(S);
+        // the tile's undecided points, then one warp per point: the FP64
+        // witness search (a free probe centre closer than r_p: outside)
+        if (threadIdx.x == 0) s_np = 0;
+        __syncthreads();
         for (int p = threadIdx.x; p < TILE_PTS; p += CLS_THREADS) {
             int li = p >> 6, lj = (p >> 3) & 7, lk = p & 7;
             long long gi = (long long)TILE * t[0] + li, gj = (long long)TILE * t[1] + lj,
                       gk = (long long)TILE * t[2] + lk;
             if (gi >= G.dims[0] || gj >= G.dims[1] || gk >= G.dims[2]) continue;
-            long long idx = (gi * G.dims[1] + gj) * G.dims[2] + gk;
-            if (labels[idx] != LABEL_BAND) continue;
-            int lab = classify_pt<false>(A, (double)li * G.h, (double)lj * G.h, (double)lk * G.h, M.rp, M.rp, 0.0);
-            labels[idx] = (int8_t)lab;
+            if (labels[(gi * G.dims[1] + gj) * G.dims[2] + gk] == LABEL_BAND) s_pts[atomicAdd(&s_np, 1)] = (short)p;
         }
         __syncthreads();
+        const int npts = s_np;
+        for (int k = threadIdx.x >> 5; k < npts; k += CLS_THREADS / 32) {
+            const int p = s_pts[k];
+            const int li = p >> 6, lj = (p >> 3) & 7, lk = p & 7;
+            unsigned um_p, um_v;
+            const int r = warp_witness<false>(A, (double)li * G.h, (double)lj * G.h, (double)lk * G.h, M.rp, M.rp, 0.0,
+                                              -1, -1, um_p, um_v);
+            if ((threadIdx.x & 31) == 0) {
+                const long long gi = (long long)TILE * t[0] + li, gj = (long long)TILE * t[1] + lj,
+                                gk = (long long)TILE * t[2] + lk;
+                labels[(gi * G.dims[1] + gj) * G.dims[2] + gk] = r == 1 ? LABEL_OUT : LABEL_IN;
+            }
+        }
+        __syncthreads();
+      }
     }
-}
-
-static int grid_size(long long n_tiles)
-{
-    long long g = n_tiles < 1 ? 1 : n_tiles;
-    return (int)(g > 2147483647LL ? 2147483647LL : g);
 }
 
 template <class T>
@@ -361,12 +382,20 @@ static size_t cls_smem()
     return ((sizeof(TileS<T>) + 15) & ~(size_t)15) + sizeof(ClsSmem);
 }
 
-// dynamic shared memory limits (once per device, before any launch or capture)
+static long long g_band_grid = 1;  // resident k_band CTAs on the device
+
+// dynamic shared memory limits and the band kernel's grid (once per device,
+// before any launch or capture)
 void classify_init()
 {
     cudaFuncSetAttribute(k_classify<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cls_smem<double>());
     cudaFuncSetAttribute(k_classify<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cls_smem<float>());
     cudaFuncSetAttribute(k_band, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileS<double>));
+    int dev = 0, n_sm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_band, CLS_THREADS, sizeof(TileS<double>));
+    g_band_grid = (long long)(n_sm > 0 ? n_sm : 1) * (per_sm > 0 ? per_sm : 1);
 }
 
 int classify_ctas_per_sm(int precision)
@@ -396,8 +425,10 @@ int launch_classify(const Model &M, const Batch &B, int precision, const TileSch
 
 int launch_band(const Model &M, const Batch &B, int8_t *labels, const int *tile_band, int *err, cudaStream_t st)
 {
-    size_t sm = sizeof(TileS<double>);
-    k_band<<<grid_size(B.n_tiles), CLS_THREADS, sm, st>>>(M, B, labels, tile_band, err);
+    const size_t sm = sizeof(TileS<double>);
+    const long long chunks = (B.n_tiles + CLS_THREADS - 1) / CLS_THREADS;
+    const long long grid = chunks < 1 ? 1 : (chunks < g_band_grid ? chunks : g_band_grid);
+    k_band<<<(int)grid, CLS_THREADS, sm, st>>>(M, B, labels, tile_band, err);
     return 1;
 }
 

@@ -192,8 +192,10 @@ __device__ __forceinline__ void torus_coeffs(const double *o, const double *u, d
     co[0] = K * K - 4.0 * r2 * (P - z0 * z0);
 }
 
-// four FP64 Newton steps on the torus quartic from t0 (the FP32 root is within
-// 1e-3 A and the root simple, else the warp solve already took it in FP64)
+// FP64 Newton steps on the torus quartic from t0, at most four (the FP32 root
+// is within 1e-3 A and the root simple, else the warp solve already took it in
+// FP64): quadratic convergence, so the steps stop once one moves t by less
+// than 1e-13 A (the next would move it by about the square of that)
 __device__ __noinline__ double exact_root_torus(const double *o, const double *u, double rho, double rp,
                                                    const double *s, int axis, double t0)
 {
@@ -201,11 +203,13 @@ __device__ __noinline__ double exact_root_torus(const double *o, const double *u
     torus_coeffs(o, u, rho, rp, s, axis, co);
     double dc[4] = {co[1], 2.0 * co[2], 3.0 * co[3], 4.0};
     double t = t0;
-#pragma unroll
     for (int it = 0; it < 4; ++it) {
         double f = horner<double, 4>(co, t);
         double df = horner<double, 3>(dc, t);
-        if (df != 0.0) t -= f / df;
+        if (df == 0.0) break;
+        const double dt = f / df;
+        t -= dt;
+        if (fabs(dt) < 1e-13) break;
     }
     return t;
 }
@@ -835,19 +839,6 @@ __device__ int warp_select(const Model &M, const TileS<T> &S, const double *x0, 
     return status;
 }
 
-__device__ __forceinline__ int block_sum_int(int v, int *sh)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    int tot = 0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += sh[k];
-    __syncthreads();
-    return tot;
-}
-
 __device__ __forceinline__ double block_sum_double(double v, double *sh)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -861,47 +852,52 @@ __device__ __forceinline__ double block_sum_double(double v, double *sh)
     return tot;
 }
 
-__global__ void __launch_bounds__(EDGE_THREADS) k_edge_count(Batch B, const int8_t *__restrict__ labels_all,
-                                                             int *__restrict__ tile_edges,
-                                                             int *__restrict__ tile_inside)
+// Per tile and axis: crossing edges (end labels differ) and inside edges (both
+// ends inside) leaving the tile's points in + direction, and the tile's inside
+// points.  One warp per tile, 16 points per lane, warp sums (no block barrier).
+constexpr int COUNT_WARPS = 8;
+
+__global__ void __launch_bounds__(COUNT_WARPS * 32) k_edge_count(Batch B, const int8_t *__restrict__ labels_all,
+                                                                int *__restrict__ tile_edges,
+                                                                int *__restrict__ tile_inside)
 {
-    __shared__ int sh[EDGE_THREADS / 32];
-    __shared__ Grid sG;
+    const int lane = threadIdx.x & 31;
     const long long nt = B.n_tiles;
-    for (long long gt = blockIdx.x; gt < nt; gt += gridDim.x) {
-        load_grid(B, mol_of_tile(B, gt), sG);
-        const Grid &G = sG;
-        const long long tile = gt - G.tile0;
+    const long long nw = (long long)gridDim.x * COUNT_WARPS;
+    for (long long gt = (long long)blockIdx.x * COUNT_WARPS + (threadIdx.x >> 5); gt < nt; gt += nw) {
+        const Grid &G = B.grid[mol_of_tile(B, gt)];
+        const long long dims[3] = {G.dims[0], G.dims[1], G.dims[2]};
         const int8_t *__restrict__ labels = labels_all + G.lab0;
-        const long long st1 = G.dims[2], st0 = G.dims[1] * G.dims[2];
+        const long long st1 = dims[2], st0 = dims[1] * dims[2];
         int t[3];
-        tile_coords(G, tile, t);
+        tile_coords(G, gt - G.tile0, t);
         int ce[3] = {0, 0, 0}, ci[3] = {0, 0, 0}, npin = 0;
-        for (int p = threadIdx.x; p < TILE_PTS; p += EDGE_THREADS) {
-            long long g[3] = {(long long)TILE * t[0] + (p >> 6), (long long)TILE * t[1] + ((p >> 3) & 7),
-                              (long long)TILE * t[2] + (p & 7)};
-            if (g[0] >= G.dims[0] || g[1] >= G.dims[1] || g[2] >= G.dims[2]) continue;
-            long long idx = g[0] * st0 + g[1] * st1 + g[2];
-            int l0 = labels[idx];
+        for (int p = lane; p < TILE_PTS; p += 32) {
+            const long long g[3] = {(long long)TILE * t[0] + (p >> 6), (long long)TILE * t[1] + ((p >> 3) & 7),
+                                    (long long)TILE * t[2] + (p & 7)};
+            if (g[0] >= dims[0] || g[1] >= dims[1] || g[2] >= dims[2]) continue;
+            const long long idx = g[0] * st0 + g[1] * st1 + g[2];
+            const int l0 = labels[idx];
             npin += l0;
             const long long str[3] = {st0, st1, 1};
             for (int a = 0; a < 3; ++a) {
-                if (g[a] + 1 >= G.dims[a]) continue;
-                int l1 = labels[idx + str[a]];
+                if (g[a] + 1 >= dims[a]) continue;
+                const int l1 = labels[idx + str[a]];
                 if (l0 != l1) ++ce[a];
                 else if (l0) ++ci[a];
             }
         }
         for (int a = 0; a < 3; ++a) {
-            int e = block_sum_int(ce[a], sh);
-            int i = block_sum_int(ci[a], sh);
-            if (threadIdx.x == 0) {
-                tile_edges[a * nt + gt] = e;
-                tile_inside[a * nt + gt] = i;
-            }
+            ce[a] = __reduce_add_sync(0xffffffffu, ce[a]);
+            ci[a] = __reduce_add_sync(0xffffffffu, ci[a]);
         }
-        int pin = block_sum_int(npin, sh);
-        if (threadIdx.x == 0) tile_inside[3 * nt + gt] = pin;
+        npin = __reduce_add_sync(0xffffffffu, npin);
+        if (lane < 3) {
+            tile_edges[lane * nt + gt] = lane == 0 ? ce[0] : (lane == 1 ? ce[1] : ce[2]);
+            tile_inside[lane * nt + gt] = lane == 0 ? ci[0] : (lane == 1 ? ci[1] : ci[2]);
+        } else if (lane == 3) {
+            tile_inside[3 * nt + gt] = npin;
+        }
     }
 }
 
@@ -1203,7 +1199,18 @@ __global__ void __launch_bounds__(POLISH_THREADS) k_edge_polish(Model M, Batch B
         const float t32 = __int_as_float(code.x);
         const int kind = (code.y >> 29) & 3, lab_s = (code.y >> 28) & 1, failed = (code.y >> 27) & 1;
         const int mid = code.y & ((1 << 27) - 1);
-        const long long gi = idx / (G.dims[1] * G.dims[2]), gj = (idx / G.dims[2]) % G.dims[1], gk = idx % G.dims[2];
+        long long gi, gj, gk;
+        if (idx < (1LL << 32) && G.dims[1] * G.dims[2] < (1LL << 32)) {  // 32-bit division where it fits
+            const unsigned i32 = (unsigned)idx, d2 = (unsigned)G.dims[2], d1 = (unsigned)G.dims[1];
+            const unsigned q = i32 / d2;
+            gk = i32 - q * d2;
+            gj = q % d1;
+            gi = q / d1;
+        } else {
+            gi = idx / (G.dims[1] * G.dims[2]);
+            gj = (idx / G.dims[2]) % G.dims[1];
+            gk = idx % G.dims[2];
+        }
         const double s[3] = {G.lo[0] + h * (double)gi, G.lo[1] + h * (double)gj, G.lo[2] + h * (double)gk};
         double t = 0.5 * h, n[3] = {0.0, 0.0, 0.0};
         if (!failed) {
@@ -1338,7 +1345,8 @@ static int grid_tiles(long long n)
 
 int launch_edge_count(const Batch &B, const int8_t *labels, int *tile_edges, int *tile_inside, cudaStream_t st)
 {
-    k_edge_count<<<grid_tiles(B.n_tiles), EDGE_THREADS, 0, st>>>(B, labels, tile_edges, tile_inside);
+    k_edge_count<<<grid_tiles((B.n_tiles + COUNT_WARPS - 1) / COUNT_WARPS), COUNT_WARPS * 32, 0, st>>>(
+        B, labels, tile_edges, tile_inside);
     return 1;
 }
 

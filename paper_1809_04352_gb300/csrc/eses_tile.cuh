@@ -574,47 +574,6 @@ __device__ __forceinline__ int warp_test_proposals(const Acc &A, unsigned mask, 
     return 0;
 }
 
-// Label of the point (x,y,z) in the tile frame: 1 if no free probe centre lies
-// at distance < thr (thr = r_p for Eq. 2), 0 otherwise, 2 undecided (FP32).
-// Per thread, over all staged items.
-template <bool FILT, class Acc, class T>
-__device__ int classify_pt(const Acc &A, T x, T y, T z, T rp, T thr, T d0)
-{
-    const T thr2 = thr * thr;
-    bool in_sas = false, unsure_sas = false;
-    const int na = A.na(), np = A.np(), nv = A.nv();
-    for (int a = 0; a < na; ++a) {
-        P4<T> c = A.atom(a);
-        T dx = x - c.x, dy = y - c.y, dz = z - c.z;
-        T d2 = dx * dx + dy * dy + dz * dz;
-        T r = c.w, R = c.w + rp;
-        if (lt_sq<FILT>(d2, r * r, r, d0) == 1) return 1;  // inside a van der Waals ball
-        int s = lt_sq<FILT>(d2, R * R, R, d0);
-        if (s == 1) in_sas = true;
-        else if (s < 0) unsure_sas = true;
-    }
-    if (!in_sas) return unsure_sas ? 2 : 0;  // free point: dist 0
-    bool unsure = false;
-    for (int v = 0; v < nv; ++v) {
-        P4<T> q = A.vq(v);
-        T dx = x - q.x, dy = y - q.y, dz = z - q.z;
-        int t = lt_sq<FILT>(dx * dx + dy * dy + dz * dz, thr2, thr, d0);
-        if (t == 1) return 0;
-        if (t < 0) unsure = true;
-    }
-    for (int a = 0; a < na; ++a) {
-        int w = face_witness<FILT>(A, a, x, y, z, rp, thr, d0);
-        if (w == 1) return 0;
-        if (w < 0) unsure = true;
-    }
-    for (int p = 0; p < np; ++p) {
-        int w = saddle_witness<FILT>(A, p, x, y, z, rp, thr, d0);
-        if (w == 1) return 0;
-        if (w < 0) unsure = true;
-    }
-    return unsure ? 2 : 1;
-}
-
 // Warp-cooperative witness search at one point (all 32 lanes call it with the
 // same point): 1 if a free probe centre lies at distance < thr (certain),
 // 0 if none does (certain), -1 undecided with the undecided triple points and
