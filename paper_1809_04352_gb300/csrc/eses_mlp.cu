@@ -294,38 +294,42 @@ __device__ int certify_tile(const Model &M, const Grid &G, int mol, long long ti
     int tc[3];
     tile_coords(G, tile, tc);
     float th[3], tl[3];
-    double t[3];
+    int c0[3], c1[3];
+    const float delta = (float)(0.5 * (TILE - 1) * G.h * 1.7320508075688772);
+    const float slack = 1e-4f, rel_lo = 1.0f - 2e-6f, rel_hi = 1.0f + 2e-6f;
+    const float rp = (float)M.rp;
+    // every atom that can matter lies within delta + R_max of t: the cells that
+    // ball meets, indices in FP32 with 1e-2 A of room for their rounding (no
+    // FP64 division: a handful per tile would bound the whole kernel)
+    const float icell = 1.0f / (float)M.cell;
+    const float reach = (delta + (float)M.Rmax + 1e-2f) * icell;
     for (int a = 0; a < 3; ++a) {
         const double rel = G.h * ((double)(TILE * tc[a]) + 0.5 * (TILE - 1));
         th[a] = (float)rel;
         tl[a] = (float)(rel - (double)th[a]);
-        t[a] = G.lo[a] + rel;
+        const float u = ((float)(G.lo[a] - cg.clo[a]) + th[a]) * icell;  // centre in cell units
+        c0[a] = max((int)floorf(u - reach), 0);
+        c1[a] = min((int)floorf(u + reach), cg.cn[a] - 1);
     }
-    const float delta = (float)(0.5 * (TILE - 1) * G.h * sqrt(3.0));
-    const float slack = 1e-4f, rel_lo = 1.0f - 2e-6f, rel_hi = 1.0f + 2e-6f;
-    const float rp = (float)M.rp;
-    // every atom that can matter lies within delta + R_max of t
-    const int nc = (int)ceil(((double)delta + M.Rmax + 1e-3) / M.cell);
-    long long ci[3];
-    for (int a = 0; a < 3; ++a) ci[a] = floor_ll((t[a] - cg.clo[a]) / M.cell);
     bool not_out = false, in = false;
-    for (long long a = max(ci[0] - nc, 0LL); a <= min(ci[0] + nc, (long long)cg.cn[0] - 1); ++a)
-        for (long long b = max(ci[1] - nc, 0LL); b <= min(ci[1] + nc, (long long)cg.cn[1] - 1); ++b)
-            for (long long c = max(ci[2] - nc, 0LL); c <= min(ci[2] + nc, (long long)cg.cn[2] - 1); ++c) {
-                const int id = cg.coff + (int)((a * cg.cn[1] + b) * cg.cn[2] + c);
-                const int e = M.cell_start[id + 1];
-                for (int k = M.cell_start[id] + lane; k < e; k += 32) {
-                    const float4 hi = M.atom_hi[k], lo = M.atom_lo[k];
-                    const float dx = (hi.x - th[0]) + (lo.x - tl[0]);
-                    const float dy = (hi.y - th[1]) + (lo.y - tl[1]);
-                    const float dz = (hi.z - th[2]) + (lo.z - tl[2]);
-                    const float d2 = dx * dx + dy * dy + dz * dz;
-                    const float to = hi.w + rp + delta + slack;   // outside needs d >= R + delta
-                    if (d2 * rel_lo < to * to) not_out = true;
-                    const float ti = hi.w - delta - slack;        // inside needs d < r - delta
-                    if (ti > 0.0f && d2 * rel_hi < ti * ti) in = true;
-                }
+    // per (x, y) cell column, the atoms of its z cells are contiguous
+    for (int a = c0[0]; a <= c1[0]; ++a)
+        for (int b = c0[1]; b <= c1[1]; ++b) {
+            if (c0[2] > c1[2]) continue;
+            const int id0 = cg.coff + (a * cg.cn[1] + b) * cg.cn[2];
+            const int e = M.cell_start[id0 + c1[2] + 1];
+            for (int k = M.cell_start[id0 + c0[2]] + lane; k < e; k += 32) {
+                const float4 hi = M.atom_hi[k], lo = M.atom_lo[k];
+                const float dx = (hi.x - th[0]) + (lo.x - tl[0]);
+                const float dy = (hi.y - th[1]) + (lo.y - tl[1]);
+                const float dz = (hi.z - th[2]) + (lo.z - tl[2]);
+                const float d2 = dx * dx + dy * dy + dz * dz;
+                const float to = hi.w + rp + delta + slack;  // outside needs d >= R + delta
+                if (d2 * rel_lo < to * to) not_out = true;
+                const float ti = hi.w - delta - slack;  // inside needs d < r - delta
+                if (ti > 0.0f && d2 * rel_hi < ti * ti) in = true;
             }
+        }
     if (!__any_sync(0xffffffffu, not_out)) return 0;
     if (__any_sync(0xffffffffu, in)) return 1;
     return -1;
