@@ -119,12 +119,6 @@ struct ExactAcc {
     }
 };
 
-__device__ __forceinline__ int cell_coord_d(double v, double lo, double cell, int n)
-{
-    int k = (int)floor((v - lo) / cell);
-    return k < 0 ? 0 : (k >= n ? n - 1 : k);
-}
-
 __device__ __forceinline__ double box_dist2(double x, double y, double z, const double *b0, const double *b1)
 {
     double ex = x < b0[0] ? b0[0] - x : (x > b1[0] ? x - b1[0] : 0.0);
@@ -269,14 +263,19 @@ __device__ void stage_tile(const Model &M, const Grid &G, int mol, long long til
         const int a = threadIdx.x < 3 ? threadIdx.x : threadIdx.x - 3;
         const double rel = G.h * (double)(TILE * t[a]);  // region origin in the grid frame
         const double fx0 = G.lo[a] + rel, fx1 = fx0 + G.h * (double)TILE;
+        // cell range of the region plus halo: FP32 indices with 1e-2 A of room
+        // for their rounding (an FP64 division costs more than the rest)
+        const float icell = 1.0f / (float)M.cell, halo = (float)G.halo + 1e-2f;
         if (threadIdx.x < 3) {
             S.fx0[a] = fx0;
             S.fx1[a] = fx1;
             S.fh0[a] = (float)rel;
             S.fl0[a] = (float)(rel - (double)S.fh0[a]);
-            S.fc0[a] = cell_coord_d(fx0 - G.halo, CG.clo[a], M.cell, CG.cn[a]);
+            const int c = (int)floorf(((float)(fx0 - CG.clo[a]) - halo) * icell);
+            S.fc0[a] = c < 0 ? 0 : (c >= CG.cn[a] ? CG.cn[a] - 1 : c);
         } else {
-            S.fc1[a] = cell_coord_d(fx1 + G.halo, CG.clo[a], M.cell, CG.cn[a]);
+            const int c = (int)floorf(((float)(fx1 - CG.clo[a]) + halo) * icell);
+            S.fc1[a] = c < 0 ? 0 : (c >= CG.cn[a] ? CG.cn[a] - 1 : c);
         }
     }
     if (threadIdx.x == 32) {
@@ -417,7 +416,8 @@ __device__ __forceinline__ double axis_normal(const double *y, const double *u, 
     for (int a = 0; a < 3; ++a) w[a] -= zr * u[a];
     const double nw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
     if (nw > 1e-12 * (1.0 + sqrt(y[0] * y[0] + y[1] * y[1] + y[2] * y[2]))) {
-        for (int a = 0; a < 3; ++a) w[a] /= nw;
+        const double inw = 1.0 / nw;  // one FP64 division, not three
+        for (int a = 0; a < 3; ++a) w[a] *= inw;
         return nw;
     }
     const double ax = fabs(u[0]) > 0.6 ? 0.0 : 1.0, ay = fabs(u[0]) > 0.6 ? 1.0 : 0.0;
