@@ -275,7 +275,8 @@ struct EdgeSmem {
     int sh[EDGE_WARPS];
     // the current chunk of edges [c0, c0 + CHUNK): (edge, item) pairs that pass
     // the prefilter, then the roots they give (valid pieces only)
-    int npool, npool_t, nroot, next_c, next_e;
+    int npool, npool_t, nroot, next_c, next_e, nhard;
+    short hard[CHUNK];        // edges of the chunk left to the warp selection
     unsigned pool[POOL_MAX];  // (edge << 16) | item: spheres from the front, tori from the back
     WCand root[ROOT_MAX];
     short redge[ROOT_MAX];
@@ -933,6 +934,50 @@ __device__ __forceinline__ int block_excl_scan_e(int v, int *sh, int *total)
     return base + inc - v;
 }
 
+// Output of one crossing edge (one thread): lower index, and for the FP64
+// polish the FP32 root, kind, model index, end label and failure flag; a
+// failure (status 1) is logged with its candidates (cand, ncand), an overflow
+// (status 2) flagged.
+template <class T>
+__device__ void edge_out(const TileS<T> &S, const EdgeSmem &E, int e, const EdgeRef &R, const int *t, long long st0,
+                         long long st1, int mol, int status, float tr, int kind, int slot, EdgeOut &out,
+                         int *n_fail, int *err, long long *fail_log, const WCand *cand, int ncand)
+{
+    const int a = R.axis, q = R.p;
+    const int li = q >> 6, lj = (q >> 3) & 7, lk = q & 7;
+    int mid = 0;
+    if (status != 1) mid = kind == 0 ? S.agid[slot] : (kind == 1 ? S.pidx[slot] : S.vidx[slot]);
+    if (status != 0) {
+        atomicOr(err, status == 1 ? ERR_ROOT : ERR_CAP_CAND);
+        if (status == 1) {
+            int fs = atomicAdd(n_fail, 1);
+            if (fs < FAIL_LOG) {
+                long long *rec = fail_log + FAIL_REC * fs;
+                for (int z = 0; z < FAIL_REC; ++z) rec[z] = 0;
+                rec[0] = a;
+                rec[1] = (long long)TILE * t[0] + li;
+                rec[2] = (long long)TILE * t[1] + lj;
+                rec[3] = (long long)TILE * t[2] + lk;
+                rec[4] = R.lab;
+                rec[5] = S.na;
+                rec[6] = S.np;
+                rec[7] = S.nv;
+                rec[8] = ncand;
+                rec[23] = mol;
+                for (int z = 0; cand && z < 7 && z < ncand && z < WCAND; ++z) {
+                    rec[9 + z] = (long long)((double)cand[z].t * 1e9);
+                    rec[16 + z] = cand[z].kind;
+                }
+            }
+        }
+    }
+    const long long o = E.ebase[a] + (e - E.estart[a]);
+    out.idx[a][o] =
+        (long long)(TILE * t[0] + li) * st0 + (long long)(TILE * t[1] + lj) * st1 + (TILE * t[2] + lk);
+    // chosen piece for the FP64 polish: FP32 root, kind, model index, end label, failure
+    out.code[a][o] = make_int2(__float_as_int(tr), (kind << 29) | (R.lab << 28) | ((status == 1 ? 1 : 0) << 27) | mid);
+}
+
 template <class T, bool FILT>
 __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Batch B, TileSched Q, int chunk0,
                                                              const int8_t *__restrict__ labels_all,
@@ -1020,7 +1065,8 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Batch B, T
                 E.npool_t = 0;
                 E.nroot = 0;
                 E.next_c = 0;
-                E.next_e = c0;
+                E.next_e = 0;
+                E.nhard = 0;
             }
             for (int k = threadIdx.x; k < CHUNK; k += EDGE_THREADS) E.rfill[k] = 0;
             __syncthreads();
@@ -1108,12 +1154,47 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Batch B, T
             for (int r = threadIdx.x; r < nr; r += EDGE_THREADS)
                 E.rorder[atomicAdd(&E.rfill[E.redge[r] - c0], 1)] = (short)r;
             __syncthreads();
-            // 4. first root of every edge: one warp per edge, edges taken from the block's counter
+            // 4a. edges whose first root needs neither a witness test nor an FP64
+            //     tie break -- an inside end point, or a single candidate (the
+            //     last candidate needs no test) with no candidate the FP32
+            //     bounds cannot order: one thread each; the rest go to 4b
+            const bool ovf = nroot > ROOT_MAX || npool > POOL_MAX;
+            for (int e = c0 + threadIdx.x; e < c1; e += EDGE_THREADS) {
+                const int b = E.rstart[e - c0], n = E.rstart[e - c0 + 1] - b;
+                const EdgeRef R = edge_ref(E, e);
+                int k = -1;
+                if (!ovf && n >= 1 && n <= WCAND && (R.lab == LABEL_IN || n == 1)) {
+                    float tk = INFINITY;
+                    for (int j = 0; j < n; ++j) {  // smallest root, ties to the first (as warp_argmin)
+                        const float tj = E.root[E.rorder[b + j]].t;
+                        if (tj < tk) {
+                            tk = tj;
+                            k = j;
+                        }
+                    }
+                    const float ek = E.root[E.rorder[b + k]].err, tie = 1e-6f * (float)h;
+                    for (int j = 0; j < n && k >= 0; ++j) {
+                        const WCand &cj = E.root[E.rorder[b + j]];
+                        if (j != k && cj.t < INFINITY && cj.t - tk <= cj.err + ek + tie) k = -1;
+                    }
+                }
+                if (k >= 0) {
+                    const WCand &ck = E.root[E.rorder[b + k]];
+                    const float tr = ck.t64 == ck.t64 ? (float)ck.t64 : ck.t;
+                    edge_out(S, E, e, R, t, st0, st1, mol, 0, tr, ck.kind, ck.id, out, n_fail, err, fail_log, nullptr, 0);
+                } else {
+                    E.hard[atomicAdd(&E.nhard, 1)] = (short)e;
+                }
+            }
+            __syncthreads();
+            // 4b. the other edges: one warp per edge, taken from the block's counter
+            const int nhard = E.nhard;
             for (;;) {
-                int e = 0;
-                if (lane == 0) e = atomicAdd(&E.next_e, 1);
-                e = __shfl_sync(0xffffffffu, e, 0);
-                if (e >= c1) break;
+                int q = 0;
+                if (lane == 0) q = atomicAdd(&E.next_e, 1);
+                q = __shfl_sync(0xffffffffu, q, 0);
+                if (q >= nhard) break;
+                const int e = E.hard[q];
                 const int b = E.rstart[e - c0], n = E.rstart[e - c0 + 1] - b;
                 for (int k = lane; k < n && k < WCAND; k += 32) E.cand[warp][k] = E.root[E.rorder[b + k]];
                 if (lane == 0) E.ncand[warp] = n;
@@ -1121,44 +1202,10 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Batch B, T
                 float tr = 0.5f * (float)h;
                 int kind = 0, slot = 0;
                 int status = warp_select<T, FILT>(M, S, x0, E, warp, e, h, rp, d0, tr, kind, slot);
-                if (nroot > ROOT_MAX || npool > POOL_MAX) status = 2;  // single-edge overflow
-                if (lane == 0) {
-                    const EdgeRef R = edge_ref(E, e);
-                    const int a = R.axis, q = R.p;
-                    const int li = q >> 6, lj = (q >> 3) & 7, lk = q & 7;
-                    int mid = 0;
-                    if (status != 1) mid = kind == 0 ? S.agid[slot] : (kind == 1 ? S.pidx[slot] : S.vidx[slot]);
-                    if (status != 0) {
-                        atomicOr(err, status == 1 ? ERR_ROOT : ERR_CAP_CAND);
-                        if (status == 1) {
-                            int fs = atomicAdd(n_fail, 1);
-                            if (fs < FAIL_LOG) {
-                                long long *rec = fail_log + FAIL_REC * fs;
-                                for (int z = 0; z < FAIL_REC; ++z) rec[z] = 0;
-                                rec[0] = a;
-                                rec[1] = (long long)TILE * t[0] + li;
-                                rec[2] = (long long)TILE * t[1] + lj;
-                                rec[3] = (long long)TILE * t[2] + lk;
-                                rec[4] = R.lab;
-                                rec[5] = S.na;
-                                rec[6] = S.np;
-                                rec[7] = S.nv;
-                                rec[8] = E.ncand[warp];
-                                rec[23] = mol;
-                                for (int z = 0; z < 7 && z < E.ncand[warp] && z < WCAND; ++z) {
-                                    rec[9 + z] = (long long)((double)E.cand[warp][z].t * 1e9);
-                                    rec[16 + z] = E.cand[warp][z].kind;
-                                }
-                            }
-                        }
-                    }
-                    const long long o = E.ebase[a] + (e - E.estart[a]);
-                    out.idx[a][o] = (long long)(TILE * t[0] + li) * st0 + (long long)(TILE * t[1] + lj) * st1 +
-                                    (TILE * t[2] + lk);
-                    // chosen piece for the FP64 polish: FP32 root, kind, model index, end label, failure
-                    out.code[a][o] = make_int2(__float_as_int(tr), (kind << 29) | (R.lab << 28) |
-                                                                        ((status == 1 ? 1 : 0) << 27) | mid);
-                }
+                if (ovf) status = 2;  // single-edge overflow
+                if (lane == 0)
+                    edge_out(S, E, e, edge_ref(E, e), t, st0, st1, mol, status, tr, kind, slot, out, n_fail, err,
+                             fail_log, E.cand[warp], E.ncand[warp]);
                 __syncwarp();
             }
             __syncthreads();
