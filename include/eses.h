@@ -80,6 +80,12 @@ typedef struct eses_ctx eses_ctx;
 #define ESES_OPT_EDGE_CTAS 10  /* root-solve CTAs per SM (0 = occupancy limit, default) */
 #define ESES_OPT_EDGE_TILES 11 /* root-solve tiles per queue pop (default 4) */
 #define ESES_OPT_EDGE_CHUNK 12 /* root-solve edges per pooled chunk at most (0 = the maximum, 128; default) */
+#define ESES_OPT_EXTERIOR 13   /* 1: exterior-only surface -- outside points that no path of outside grid points
+                                  (6-neighbour steps) joins to the domain boundary lie in cavities and are labelled
+                                  inside before the crossing edges are found (default 0: every free probe position
+                                  is solvent, §1).  Its sweeps are synchronised from the host, so a run with this
+                                  option is never captured in a CUDA graph.  Timed in the "band" stage; the number
+                                  of filled points is eses_stats [13]. */
 
 #define ESES_PROPOSER_OFF 0      /* classify every tile (default) */
 #define ESES_PROPOSER_MLP 1      /* the MLP scores tiles; those scored far are certified and filled */
@@ -234,7 +240,9 @@ int eses_area_volume(const eses_ctx *ctx, double *area, double *volume);
  * with a free arc, [5] free triple points, [6] points re-evaluated in FP64
  * (filter band), [7] crossing edges (all axes), [8] edges with a reported
  * root failure, [9] inside points, [10] kernels launched by the run,
- * [11] tiles proposed far, [12] tiles certified far (eses_set_proposer). */
+ * [11] tiles proposed far, [12] tiles certified far (eses_set_proposer),
+ * [13] cavity points labelled inside (ESES_OPT_EXTERIOR), [14] flood-fill
+ * sweeps. */
 int eses_stats(const eses_ctx *ctx, int64_t *out, int n);
 
 /* Device time in milliseconds of every stage of the last eses_run, measured

@@ -86,6 +86,10 @@ def _load():
         lib.eo_flop_counts.restype = ctypes.c_int
         lib.eo_edge_flop_counts.argtypes = [P, P, i64, d, d, d, P, P, ctypes.c_int, P]
         lib.eo_edge_flop_counts.restype = ctypes.c_int
+        lib.eo_exterior_labels.argtypes = [P, P]
+        lib.eo_exterior_labels.restype = i64
+        lib.eo_result_exterior.argtypes = [P]
+        lib.eo_result_exterior.restype = i64
         _lib = lib
         return lib
 
@@ -141,8 +145,10 @@ class Result:
 
 
 def run(xyz, radii, r_p: float, h: float, margin: float, block_pts: int = 0, nthreads: int = 0,
-        brute: bool = False, block_ids=None) -> Result:
-    """Algorithm 1 over every block (or the blocks listed in block_ids)."""
+        brute: bool = False, block_ids=None, exterior: bool = False) -> Result:
+    """Algorithm 1 over every block (or the blocks listed in block_ids);
+    exterior: the exterior-only surface (cavities filled, reading X1; whole
+    grid only)."""
     lib = _load()
     xyz, radii = _atoms(xyz, radii)
     ids = None
@@ -155,6 +161,8 @@ def run(xyz, radii, r_p: float, h: float, margin: float, block_pts: int = 0, nth
     if not res:
         raise ValueError("invalid parameters")
     try:
+        if exterior and (block_ids is not None or lib.eo_result_exterior(res) < 0):
+            raise ValueError("the exterior-only surface needs the whole grid")
         dims = np.zeros(3, np.int64)
         lo = np.zeros(3, np.float64)
         lib.eo_result_grid(res, _ptr(dims), _ptr(lo))
@@ -177,6 +185,16 @@ def run(xyz, radii, r_p: float, h: float, margin: float, block_pts: int = 0, nth
     return Result(dims=dims, lo=lo, h=h, labels=labels, idx=idx, tau=tau, normal=nrm, ptype=pt,
                   area=float(st[0]), volume=float(st[1]), volume_count=float(st[2]),
                   near_ties=int(st[3]), slow_edges=int(st[4]), n_points=int(st[11]))
+
+
+def exterior_labels(labels) -> tuple:
+    """Flood fill of reading X1 on a label grid (int8, C order): returns
+    (labels with cavity points relabelled inside, number relabelled)."""
+    lib = _load()
+    lab = np.ascontiguousarray(labels, dtype=np.int8).copy()
+    dims = np.array(lab.shape, np.int64)
+    n = int(lib.eo_exterior_labels(_ptr(lab), _ptr(dims)))
+    return lab, n
 
 
 def run_blocks(xyz, radii, r_p: float, h: float, margin: float, block_pts: int, block_ids, nthreads: int = 0):

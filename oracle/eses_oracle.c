@@ -986,6 +986,98 @@ void eo_result_free(eo_result *res)
     free(res);
 }
 
+/* ------------------------------------------------------------------------ */
+/* exterior-only surface (cavities filled)                                    */
+/* ------------------------------------------------------------------------ */
+/* Reading X1.  §1 counts every free probe position as solvent (reading C4);
+ * the exterior-only variant keeps only the solvent that a probe can reach
+ * from outside the molecule.  On the grid: an outside point is exterior iff a
+ * path of outside points, each step between 6-neighbours, joins it to the
+ * domain boundary (whose points are all outside, reading C2).  Every other
+ * outside point lies in a cavity and becomes inside.  Plain breadth-first
+ * search from the boundary.  Returns the number of relabelled points. */
+int64_t eo_exterior_labels(int8_t *labels, const int64_t dims[3])
+{
+    const int64_t d0 = dims[0], d1 = dims[1], d2 = dims[2], n = d0 * d1 * d2;
+    if (n <= 0) return 0;
+    uint8_t *seen = (uint8_t *)calloc((size_t)n, 1);
+    int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t head = 0, tail = 0;
+    for (int64_t i = 0; i < d0; ++i)
+        for (int64_t j = 0; j < d1; ++j)
+            for (int64_t k = 0; k < d2; ++k) {
+                int on_face = i == 0 || j == 0 || k == 0 || i == d0 - 1 || j == d1 - 1 || k == d2 - 1;
+                int64_t p = (i * d1 + j) * d2 + k;
+                if (on_face && labels[p] == 0) { seen[p] = 1; queue[tail++] = p; }
+            }
+    while (head < tail) {
+        int64_t p = queue[head++];
+        int64_t g[3] = {p / (d1 * d2), (p / d2) % d1, p % d2};
+        for (int a = 0; a < 3; ++a)
+            for (int sgn = -1; sgn <= 1; sgn += 2) {
+                int64_t q[3] = {g[0], g[1], g[2]};
+                q[a] += sgn;
+                if (q[a] < 0 || q[a] >= dims[a]) continue;
+                int64_t pq = (q[0] * d1 + q[1]) * d2 + q[2];
+                if (labels[pq] == 0 && !seen[pq]) { seen[pq] = 1; queue[tail++] = pq; }
+            }
+    }
+    int64_t filled = 0;
+    for (int64_t p = 0; p < n; ++p)
+        if (labels[p] == 0 && !seen[p]) { labels[p] = 1; ++filled; }
+    free(seen);
+    free(queue);
+    return filled;
+}
+
+/* Exterior-only form of a whole-grid result: cavity points relabelled inside
+ * (eo_exterior_labels), the crossing edges that touch them dropped -- their
+ * other end is inside, since an outside neighbour would have joined the
+ * cavity to the exterior, so the edges left keep their first roots -- and the
+ * area and volume recomputed from what is left with the estimators of C9.
+ * Returns the number of relabelled points, -1 for a sparse result. */
+int64_t eo_result_exterior(eo_result *res)
+{
+    if (res->sparse) return -1;
+    const int64_t *dims = res->dims;
+    const double h = res->h;
+    int64_t filled = eo_exterior_labels(res->labels, dims);
+    const int64_t str[3] = {dims[1] * dims[2], dims[2], 1};
+    double area = 0.0, lines = 0.0;
+    for (int axis = 0; axis < 3; ++axis) {
+        int64_t keep = 0;
+        for (int64_t e = 0; e < res->idx[axis].n; ++e) {
+            int64_t p = res->idx[axis].v[e];
+            int ls = res->labels[p], lt = res->labels[p + str[axis]];
+            if (ls == lt) continue;
+            res->idx[axis].v[keep] = p;
+            res->tau[axis].v[keep] = res->tau[axis].v[e];
+            for (int a = 0; a < 3; ++a) res->nrm[axis].v[3 * keep + a] = res->nrm[axis].v[3 * e + a];
+            res->ptype[axis].v[keep] = res->ptype[axis].v[e];
+            double tau = res->tau[axis].v[e];
+            area += h * h * fabs(res->nrm[axis].v[3 * e + axis]);
+            lines += ls ? tau * h : (1.0 - tau) * h;
+            ++keep;
+        }
+        res->idx[axis].n = res->tau[axis].n = res->ptype[axis].n = keep;
+        res->nrm[axis].n = 3 * keep;
+    }
+    int64_t inside = 0;
+    for (int64_t i = 0; i < dims[0]; ++i)
+        for (int64_t j = 0; j < dims[1]; ++j)
+            for (int64_t k = 0; k < dims[2]; ++k) {
+                int64_t g[3] = {i, j, k}, p = (i * dims[1] + j) * dims[2] + k;
+                if (!res->labels[p]) continue;
+                ++inside;
+                for (int axis = 0; axis < 3; ++axis)
+                    if (g[axis] + 1 < dims[axis] && res->labels[p + str[axis]]) lines += h; /* edge inside */
+            }
+    res->area = area;
+    res->volume_lines = h * h * lines / 3.0;
+    res->volume_count = h * h * h * (double)inside;
+    return filled;
+}
+
 int eo_num_threads(void)
 {
 #ifdef _OPENMP

@@ -30,7 +30,7 @@ using namespace eses;
 static_assert(MLP_NPARAM == ESES_MLP_NPARAM, "proposer parameter count");
 
 // stages timed with CUDA events when ESES_OPT_PROFILE is set
-enum { NSTAT = 13 };
+enum { NSTAT = 15 };
 enum { ST_BIN = 0, ST_PAIRS, ST_ARCS, ST_CLASSIFY, ST_BAND, ST_EDGE_COUNT, ST_EDGE_SOLVE, ST_EDGE_POLISH, ST_REDUCE, NSTAGE };
 
 namespace {
@@ -142,6 +142,11 @@ struct eses_ctx {
     // launch shapes (eses_autotune, ESES_OPT_*)
     Shape cls, edge;
     bool use_queue = true;
+    // exterior-only surface (ESES_OPT_EXTERIOR)
+    bool exterior = false;
+    DBuf ext, ext_misc;
+    long long n_cavity = 0;
+    int ext_sweeps = 0;
     // learned tile proposer
     int proposer = 0;  // ESES_PROPOSER_*
     float z_far = 0.0f;
@@ -626,6 +631,30 @@ int run_device(eses_ctx *c)
                           c->precision == ESES_PREC_FP64 ? nullptr : tile_band, d_err, st);
     mark(c, ST_BAND);
     if (c->precision != ESES_PREC_FP64) nl += launch_band(M, B, labels, tile_band, d_err, st);
+    c->n_cavity = 0;
+    c->ext_sweeps = 0;
+    if (c->exterior) {  // cavities filled: sweeps until one reaches nothing new (never under capture)
+        if (g_capturing) throw std::string("the exterior-only surface is not captured in a graph");
+        uint8_t *ext = ensure<uint8_t>(c->ext, c->n_points);
+        unsigned long long *em = ensure<unsigned long long>(c->ext_misc, 2);  // [0] changed flag, [1] filled
+        ck(cudaMemsetAsync(em, 0, 2 * sizeof(unsigned long long), st), "memset");
+        nl += launch_ext_init(B, labels, ext, st);
+        const int sweep_grid = (int)std::min<long long>(std::max<long long>(nt, 1), 8LL * c->n_sm);
+        for (long long it = 0; it <= nt; ++it) {  // a sweep reaches at least one more tile, or nothing
+            ck(cudaMemsetAsync(em, 0, sizeof(unsigned long long), st), "memset");
+            nl += launch_ext_sweep(B, ext, reinterpret_cast<int *>(em), sweep_grid, st);
+            unsigned long long changed = 0;
+            ck(cudaMemcpyAsync(&changed, em, sizeof(changed), cudaMemcpyDeviceToHost, st), "read");
+            ck(cudaStreamSynchronize(st), "synchronize");
+            ++c->ext_sweeps;
+            if (!changed) break;
+        }
+        nl += launch_ext_apply(B, labels, ext, em + 1, st);
+        unsigned long long filled = 0;
+        ck(cudaMemcpyAsync(&filled, em + 1, sizeof(filled), cudaMemcpyDeviceToHost, st), "read");
+        ck(cudaStreamSynchronize(st), "synchronize");
+        c->n_cavity = (long long)filled;
+    }
 
     // 8. crossing edges, roots, area and volume
     int *tile_edges = ensure<int>(c->tile_edges, 3 * nt);
@@ -711,6 +740,8 @@ int finish(eses_ctx *c, int nl)
     c->stats[10] = nl;
     c->stats[11] = hprop[0];
     c->stats[12] = hprop[1];
+    c->stats[13] = c->n_cavity;
+    c->stats[14] = c->ext_sweeps;
     c->ran = true;
     int derr = hmisc[0];
     if (derr & (ERR_CAP_ATOMS | ERR_CAP_PAIRS | ERR_CAP_VERTS | ERR_CAP_CAND)) {
@@ -729,7 +760,7 @@ int run_impl(eses_ctx *c)
 {
     if (c->profile && !c->ev[0])
         for (int k = 0; k <= NSTAGE; ++k) ck(cudaEventCreate(&c->ev[k]), "cudaEventCreate");
-    const bool replay = c->graph_on && c->planned && c->plan_precision == c->precision;
+    const bool replay = c->graph_on && !c->exterior && c->planned && c->plan_precision == c->precision;
     if (!replay) {
         drop_graph(c);
         const int nl = run_device(c);
@@ -912,6 +943,14 @@ int eses_set_option(eses_ctx *c, int key, int64_t value)
         drop_graph(c);
         c->edge.chunk = (int)value;
         return ESES_OK;
+    case ESES_OPT_EXTERIOR:
+        if (value != 0 && value != 1) return fail(c, ESES_EINVAL, "exterior must be 0 or 1");
+        if ((value != 0) != c->exterior) {  // other list sizes: plan again (buffers may move)
+            drop_graph(c);
+            c->planned = false;
+        }
+        c->exterior = value != 0;
+        return ESES_OK;
     default:
         return fail(c, ESES_EINVAL, "unknown option key " + std::to_string(key));
     }
@@ -934,6 +973,7 @@ int eses_get_option(const eses_ctx *cc, int key, int64_t *value)
     case ESES_OPT_CLS_TILES: *value = c->cls.tiles_per_pop; return ESES_OK;
     case ESES_OPT_EDGE_TILES: *value = c->edge.tiles_per_pop; return ESES_OK;
     case ESES_OPT_EDGE_CHUNK: *value = c->edge.chunk; return ESES_OK;
+    case ESES_OPT_EXTERIOR: *value = c->exterior ? 1 : 0; return ESES_OK;
     default: return fail(c, ESES_EINVAL, "unknown option key " + std::to_string(key));
     }
 }

@@ -38,6 +38,7 @@ ESES_OPT_CLS_TILES = 9
 ESES_OPT_EDGE_CTAS = 10
 ESES_OPT_EDGE_TILES = 11
 ESES_OPT_EDGE_CHUNK = 12
+ESES_OPT_EXTERIOR = 13
 
 ESES_PROPOSER_OFF = 0
 ESES_PROPOSER_MLP = 1
@@ -49,7 +50,7 @@ ESES_PREC_FP32_FILTERED = 1
 
 STAT_NAMES = ["points", "tiles", "work_tiles", "circle_pairs", "free_arc_pairs", "free_vertices", "band_points",
               "crossing_edges", "root_failures", "inside_points", "kernel_launches", "tiles_proposed_far",
-              "tiles_certified"]
+              "tiles_certified", "cavity_points", "exterior_sweeps"]
 
 # every exported C symbol, as declared in include/eses.h
 SYMBOLS = ["eses_create", "eses_create_device", "eses_create_batch", "eses_run_batch", "eses_set_option",

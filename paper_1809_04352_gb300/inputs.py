@@ -108,6 +108,24 @@ def protein_like(n_atoms: int, seed: int, density: float | None = None):
     return np.ascontiguousarray(xyz), np.ascontiguousarray(radii)
 
 
+def hollow_shell(shell_radius: float = 8.0, spacing: float = 2.4, radius: float = 1.7, seed: int = 77,
+                 jitter: float = 0.05):
+    """A closed shell of atoms around an empty core: centres on a Fibonacci
+    sphere of the given radius, about `spacing` A apart, each moved by a seeded
+    uniform offset of at most `jitter` A per axis; all radii `radius`.  With
+    spacing < 2 (radius + r_p) sin 60 deg no probe passes between the atoms,
+    so the free space inside is a cavity.  Returns (xyz (n,3), radii (n,))."""
+    n = max(4, int(round(4.0 * math.pi * shell_radius ** 2 / (spacing ** 2 * math.sqrt(3.0) / 2.0))))
+    k = np.arange(n, dtype=np.float64) + 0.5
+    z = 1.0 - 2.0 * k / n
+    phi = math.pi * (3.0 - math.sqrt(5.0)) * k
+    rr = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    xyz = shell_radius * np.stack([rr * np.cos(phi), rr * np.sin(phi), z], axis=1)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    xyz = xyz + rng.uniform(-jitter, jitter, size=xyz.shape)
+    return np.ascontiguousarray(xyz), np.full(n, float(radius))
+
+
 def icosahedral_rotations() -> np.ndarray:
     """The 60 rotations of the icosahedral group, by closure of two generators."""
     phi = (1.0 + 5.0 ** 0.5) / 2.0
