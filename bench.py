@@ -17,6 +17,8 @@ point, crossing edges, roots and normals, area and volume.
   roofline   the dominant kernel (by event-timed duration; the other heavy
              kernel beside it) against the FP32 ALU peak, with the algorithmic
              flops of the oracle-counted flop model
+  exterior   the headline step with the exterior-only surface (cavities
+             filled by flood-fill sweeps; eager, host-synchronised sweeps)
   batch      the 256-molecule workload (log-uniform 300-20,000 atoms, h 0.5)
              in one batched context: persistent tile kernels with a device
              work queue, replayed as one CUDA graph, autotuned launch shapes
@@ -206,6 +208,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of the autotuner's")
     ap.add_argument("--no-graph", action="store_true", help="eager launches instead of CUDA-graph replay")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-molecule batched workload")
+    ap.add_argument("--no-exterior", action="store_true", help="skip the exterior-only surface step")
     ap.add_argument("--proposer", default="mlp", choices=["off", "mlp", "certify"],
                     help="tile proposer of the headline step (default: the trained MLP with the exact certificate)")
     ap.add_argument("--no-proposer-study", action="store_true",
@@ -406,6 +409,29 @@ def main():
         study["mlp_gain_vs_certify"] = study["certify"]["ms_per_step"] / study["mlp"]["ms_per_step"]
         eses.eses_destroy(sctx)
 
+    # ---- exterior-only surface on the headline molecule -----------------------
+    exterior = None
+    if not args.no_exterior:
+        xctx = eses.eses_create(xyz, rad, wl.r_p, wl.h, wl.margin)
+        eses.eses_set_option(xctx, eses.ESES_OPT_STREAM, stream.cuda_stream)
+        eses.eses_set_option(xctx, eses.ESES_OPT_PROFILE, 1)
+        set_prop(xctx, args.proposer)
+        eses.eses_set_option(xctx, eses.ESES_OPT_EXTERIOR, 1)
+        eses.eses_run(xctx)
+        torch.cuda.synchronize()
+        barrier()
+        xt, xs = timed_runs(xctx, max(3, min(args.steps, 5)))
+        torch.cuda.synchronize()
+        barrier()
+        xst = eses.eses_stats(xctx)
+        xav = eses.eses_area_volume(xctx)
+        exterior = {"ms_per_step": statistics.mean(xt), "points_per_s": npts / (statistics.mean(xt) / 1e3),
+                    "band_and_fill_ms": statistics.mean(v["band"] for v in xs),
+                    "cavity_points": int(xst["cavity_points"]), "sweeps": int(xst["exterior_sweeps"]),
+                    "crossing_edges": int(xst["crossing_edges"]), "area_A2": xav[0], "volume_A3": xav[1],
+                    "graph": False}
+        eses.eses_destroy(xctx)
+
     # ---- batched workload: 256 molecules in one context ---------------------
     batch = None
     if not args.no_batch:
@@ -464,6 +490,7 @@ def main():
                 "roofline_other_kernels": roofline_others,
                 "launch": {"cuda_graph": use_graph, "autotuned": tuned, "proposer": args.proposer},
                 "proposer_study": study,
+                "exterior": exterior,
                 "batch": batch,
                 "cpu_baseline": cpu,
                 "clocks": clk,

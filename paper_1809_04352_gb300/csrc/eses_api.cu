@@ -144,7 +144,7 @@ struct eses_ctx {
     bool use_queue = true;
     // exterior-only surface (ESES_OPT_EXTERIOR)
     bool exterior = false;
-    DBuf ext, ext_misc;
+    DBuf ext, ext_open, ext_misc;
     long long n_cavity = 0;
     int ext_sweeps = 0;
     // learned tile proposer
@@ -636,13 +636,14 @@ int run_device(eses_ctx *c)
     if (c->exterior) {  // cavities filled: sweeps until one reaches nothing new (never under capture)
         if (g_capturing) throw std::string("the exterior-only surface is not captured in a graph");
         uint8_t *ext = ensure<uint8_t>(c->ext, c->n_points);
+        uint8_t *open = ensure<uint8_t>(c->ext_open, nt);
         unsigned long long *em = ensure<unsigned long long>(c->ext_misc, 2);  // [0] changed flag, [1] filled
         ck(cudaMemsetAsync(em, 0, 2 * sizeof(unsigned long long), st), "memset");
-        nl += launch_ext_init(B, labels, ext, st);
+        nl += launch_ext_init(B, labels, ext, open, st);
         const int sweep_grid = (int)std::min<long long>(std::max<long long>(nt, 1), 8LL * c->n_sm);
         for (long long it = 0; it <= nt; ++it) {  // a sweep reaches at least one more tile, or nothing
             ck(cudaMemsetAsync(em, 0, sizeof(unsigned long long), st), "memset");
-            nl += launch_ext_sweep(B, ext, reinterpret_cast<int *>(em), sweep_grid, st);
+            nl += launch_ext_sweep(B, ext, open, reinterpret_cast<int *>(em), sweep_grid, st);
             unsigned long long changed = 0;
             ck(cudaMemcpyAsync(&changed, em, sizeof(changed), cudaMemcpyDeviceToHost, st), "read");
             ck(cudaStreamSynchronize(st), "synchronize");

@@ -10,10 +10,13 @@
 //
 // State per point (one byte): 0 inside, 1 outside not reached yet, 2 reached.
 //   k_ext_init:  boundary outside points reached, other outside points 1;
+//                a tile is open while it holds points in state 1;
 //   k_ext_sweep: per 8x8x8 tile with a one-point halo in shared memory, the
 //                reached set grows inside the tile until it stops (a bounded
 //                loop: a path inside the tile has fewer than 512 steps); the
-//                tile's new points are written back and a flag set.  The
+//                tile's new points are written back and a flag set; a
+//                tile left without state-1 points closes and is not read
+//                again.  The
 //                host repeats sweeps until one changes nothing (the reached
 //                set only grows, so neighbours read mid-sweep are either
 //                state and the fixed point is the same);
@@ -29,7 +32,8 @@ constexpr int HALO_W = TILE + 2;  // 10 points per axis
 
 // the tile's points: warp per tile, 16 points per lane
 __global__ void __launch_bounds__(EXT_WARPS * 32) k_ext_init(Batch B, const int8_t *__restrict__ labels_all,
-                                                            uint8_t *__restrict__ ext_all)
+                                                            uint8_t *__restrict__ ext_all,
+                                                            uint8_t *__restrict__ tile_open)
 {
     const int lane = threadIdx.x & 31;
     const long long nw = (long long)gridDim.x * EXT_WARPS;
@@ -38,6 +42,7 @@ __global__ void __launch_bounds__(EXT_WARPS * 32) k_ext_init(Batch B, const int8
         const long long d[3] = {G.dims[0], G.dims[1], G.dims[2]};
         int t[3];
         tile_coords(G, gt - G.tile0, t);
+        bool open = false;
         for (int p = lane; p < TILE_PTS; p += 32) {
             const long long g[3] = {(long long)TILE * t[0] + (p >> 6), (long long)TILE * t[1] + ((p >> 3) & 7),
                                     (long long)TILE * t[2] + (p & 7)};
@@ -45,17 +50,22 @@ __global__ void __launch_bounds__(EXT_WARPS * 32) k_ext_init(Batch B, const int8
             const long long idx = G.lab0 + (g[0] * d[1] + g[1]) * d[2] + g[2];
             const bool face = g[0] == 0 || g[1] == 0 || g[2] == 0 || g[0] == d[0] - 1 || g[1] == d[1] - 1 ||
                               g[2] == d[2] - 1;
-            ext_all[idx] = labels_all[idx] != 0 ? 0 : (face ? 2 : 1);
+            const uint8_t v = labels_all[idx] != 0 ? 0 : (face ? 2 : 1);
+            ext_all[idx] = v;
+            open = open || v == 1;
         }
+        open = __any_sync(0xffffffffu, open);
+        if (lane == 0) tile_open[gt] = open ? 1 : 0;
     }
 }
 
 __global__ void __launch_bounds__(EXT_THREADS) k_ext_sweep(Batch B, uint8_t *__restrict__ ext_all,
-                                                          int *__restrict__ changed)
+                                                          uint8_t *__restrict__ tile_open, int *__restrict__ changed)
 {
     __shared__ uint8_t s[HALO_W * HALO_W * HALO_W];
     __shared__ uint8_t s0[TILE_PTS];  // the tile's states before the sweep
     for (long long gt = blockIdx.x; gt < B.n_tiles; gt += gridDim.x) {
+        if (!tile_open[gt]) continue;  // uniform: every thread reads the same byte
         const Grid &G = B.grid[mol_of_tile(B, gt)];
         const long long d[3] = {G.dims[0], G.dims[1], G.dims[2]};
         int t[3];
@@ -77,7 +87,10 @@ __global__ void __launch_bounds__(EXT_THREADS) k_ext_sweep(Batch B, uint8_t *__r
                 if (v == 1) open = true;
             }
         }
-        if (!__syncthreads_or(open)) continue;  // nothing left to reach in this tile
+        if (!__syncthreads_or(open)) {  // nothing left to reach in this tile
+            if (threadIdx.x == 0) tile_open[gt] = 0;
+            continue;
+        }
         // grow the reached set inside the tile until it stops
         for (int it = 0; it < TILE_PTS; ++it) {
             bool grew = false;
@@ -93,10 +106,11 @@ __global__ void __launch_bounds__(EXT_THREADS) k_ext_sweep(Batch B, uint8_t *__r
             }
             if (!__syncthreads_or(grew)) break;
         }
-        bool any = false;
+        bool any = false, left = false;
         for (int p = threadIdx.x; p < TILE_PTS; p += EXT_THREADS) {
             const int li = p >> 6, lj = (p >> 3) & 7, lk = p & 7;
             const int q = ((li + 1) * HALO_W + (lj + 1)) * HALO_W + (lk + 1);
+            left = left || s[q] == 1;
             if (s[q] == 2 && s0[p] == 1) {
                 const long long g[3] = {(long long)TILE * t[0] + li, (long long)TILE * t[1] + lj,
                                         (long long)TILE * t[2] + lk};
@@ -104,7 +118,9 @@ __global__ void __launch_bounds__(EXT_THREADS) k_ext_sweep(Batch B, uint8_t *__r
                 any = true;
             }
         }
+        left = __syncthreads_or(left);
         if (__syncthreads_or(any) && threadIdx.x == 0) atomicExch(changed, 1);
+        if (!left && threadIdx.x == 0) tile_open[gt] = 0;
     }
 }
 
@@ -141,15 +157,15 @@ static int warp_grid(long long n_tiles)
     return (int)(g < 1 ? 1 : (g > 1048576 ? 1048576 : g));
 }
 
-int launch_ext_init(const Batch &B, const int8_t *labels, uint8_t *ext, cudaStream_t st)
+int launch_ext_init(const Batch &B, const int8_t *labels, uint8_t *ext, uint8_t *tile_open, cudaStream_t st)
 {
-    k_ext_init<<<warp_grid(B.n_tiles), EXT_WARPS * 32, 0, st>>>(B, labels, ext);
+    k_ext_init<<<warp_grid(B.n_tiles), EXT_WARPS * 32, 0, st>>>(B, labels, ext, tile_open);
     return 1;
 }
 
-int launch_ext_sweep(const Batch &B, uint8_t *ext, int *changed, int grid, cudaStream_t st)
+int launch_ext_sweep(const Batch &B, uint8_t *ext, uint8_t *tile_open, int *changed, int grid, cudaStream_t st)
 {
-    k_ext_sweep<<<grid < 1 ? 1 : grid, EXT_THREADS, 0, st>>>(B, ext, changed);
+    k_ext_sweep<<<grid < 1 ? 1 : grid, EXT_THREADS, 0, st>>>(B, ext, tile_open, changed);
     return 1;
 }
 
