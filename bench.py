@@ -22,6 +22,9 @@ point, crossing edges, roots and normals, area and volume.
   batch      the 256-molecule workload (log-uniform 300-20,000 atoms, h 0.5)
              in one batched context: persistent tile kernels with a device
              work queue, replayed as one CUDA graph, autotuned launch shapes
+  assembly   the 1,000,000-atom assembly (60 rotated 16,667-atom globules,
+             h 0.3, ~1.3e10 points) in one context: labels and intersections
+             stay in HBM (13 GB of labels), graph replay
   cpu_baseline  the FP64 CPU oracle on a seeded sample of blocks, all cores
 
 --impl reference times the oracle (the reference arm of this build) on the
@@ -209,6 +212,7 @@ def main():
     ap.add_argument("--no-graph", action="store_true", help="eager launches instead of CUDA-graph replay")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-molecule batched workload")
     ap.add_argument("--no-exterior", action="store_true", help="skip the exterior-only surface step")
+    ap.add_argument("--no-assembly", action="store_true", help="skip the 1,000,000-atom assembly")
     ap.add_argument("--proposer", default="mlp", choices=["off", "mlp", "certify"],
                     help="tile proposer of the headline step (default: the trained MLP with the exact certificate)")
     ap.add_argument("--no-proposer-study", action="store_true",
@@ -471,6 +475,40 @@ def main():
                  "graph": use_graph}
         eses.eses_destroy(bctx)
 
+    # ---- the 1,000,000-atom assembly in one context --------------------------
+    assembly = None
+    if not args.no_assembly:
+        awl = inputs.WORKLOADS[5]
+        axyz, arad = inputs.workload_atoms(5)
+        actx = eses.eses_create(axyz, arad, awl.r_p, awl.h, awl.margin)
+        eses.eses_set_option(actx, eses.ESES_OPT_STREAM, stream.cuda_stream)
+        eses.eses_set_option(actx, eses.ESES_OPT_GRAPH, 1 if use_graph else 0)
+        set_prop(actx, args.proposer)
+        for _ in range(2):  # planning run, then the graph capture
+            eses.eses_run(actx)
+        torch.cuda.synchronize()
+        barrier()
+        at = []
+        for _ in range(2):  # inputs and outputs far larger than L2
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            eses.eses_run(actx)
+            a1.record(stream)
+            a1.synchronize()
+            at.append(a0.elapsed_time(a1))
+        torch.cuda.synchronize()
+        barrier()
+        ast = eses.eses_stats(actx)
+        atot, apts_all = scaling.job_totals(sum(at) / 1e3, float(ast["points"]), "cuda")
+        assembly = {"workload": f"{awl.name}: 60 copies of a 16,667-atom globule on an icosahedral shell of radius "
+                                f"300 A ({axyz.shape[0]} atoms), r_p {awl.r_p} A, h {awl.h} A, margin {awl.margin} A",
+                    "value": scaling.throughput(apts_all, len(at), atot), "unit": UNIT,
+                    "ms_per_step": 1e3 * atot / len(at), "steps": len(at), "points": int(ast["points"]),
+                    "crossing_edges": int(ast["crossing_edges"]), "root_failures": int(ast["root_failures"]),
+                    "graph": use_graph, "proposer": args.proposer}
+        eses.eses_destroy(actx)
+
     # ---- CPU baseline (rank 0, N = 1) ---------------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -492,6 +530,7 @@ def main():
                 "proposer_study": study,
                 "exterior": exterior,
                 "batch": batch,
+                "assembly": assembly,
                 "cpu_baseline": cpu,
                 "clocks": clk,
                 "plain_fp64": {"value": all_pts / (plain_ms / 1e3), "unit": UNIT, "ms_per_step": plain_ms,
