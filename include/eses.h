@@ -186,6 +186,32 @@ int eses_mlp_grad(const float *X, const float *y, const float *w, int64_t n, con
                   float *loss, float *scratch, void *stream);
 int eses_mlp_adam(float *params, const float *grad, float *m, float *v, int step, float lr, void *stream);
 
+/* Triangle mesh of the surface from the last run's labels and intersections
+ * (one molecule; ESES_EINVAL on a batch context, ESES_ESTATE before a run).
+ * Cube by cube (lower corner in C order within 8x8x8 tiles, tiles in order),
+ * each cube's triangles from a 256-case table built by this rule: corner i of
+ * a cube sits at offset ((i >> 2) & 1, (i >> 1) & 1, i & 1); cube edge 4 a + j
+ * runs along axis a from the j-th corner (increasing corner number) with axis-a
+ * offset 0 and is cut when its labels differ; on each face two cut edges make
+ * one segment and four make two, each joining the edges at one inside corner;
+ * the segments close into loops, each started at its smallest edge, walked
+ * first to the smaller neighbour, reversed after its first vertex when its
+ * Newell normal (edge midpoints) points on the whole from outside corners to
+ * inside ones, and cut into the fan (v0, v_k, v_k+1).  The mesh is closed and
+ * its triangles face the solvent.  eses_mesh_count makes the mesh (device
+ * buffers owned by the context, kept until the next run) and returns the
+ * number of triangles (below 2^31).  eses_mesh copies it to host buffers,
+ * either may be NULL: keys (n * 3 int64: per vertex 3 * (linear index of the
+ * lower point of its edge) + axis) and xyz (n * 9 doubles: the three vertices,
+ * each its edge's intersection point).  eses_mesh_table (no device needed)
+ * writes the case table: tri[case * 3 * ESES_MESH_MAXT + 3 k + v] cube edges
+ * (-1 past the last triangle), ntri[case] triangles, for the 256 cases (bit i
+ * of the case: corner i inside). */
+#define ESES_MESH_MAXT 5
+int eses_mesh_count(eses_ctx *ctx, int64_t *n_tri);
+int eses_mesh(eses_ctx *ctx, int64_t *keys, double *xyz);
+int eses_mesh_table(int8_t *tri, uint8_t *ntri);
+
 /* Number of molecules of the context (host output). */
 int eses_num_molecules(const eses_ctx *ctx, int *n);
 

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libeses.so")
 SOURCES = ["eses_api.cu", "eses_scan.cu", "eses_model.cu", "eses_classify.cu", "eses_edges.cu", "eses_noalloc.cu",
-           "eses_mlp.cu", "eses_exterior.cu"]
+           "eses_mlp.cu", "eses_exterior.cu", "eses_mesh.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

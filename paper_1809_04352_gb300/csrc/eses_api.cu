@@ -145,6 +145,9 @@ struct eses_ctx {
     // exterior-only surface (ESES_OPT_EXTERIOR)
     bool exterior = false;
     DBuf ext, ext_open, ext_misc;
+    // triangle mesh of the last run (eses_mesh_count / eses_mesh)
+    DBuf mesh_mask, mesh_tile, mesh_off, mesh_keys, mesh_xyz, mesh_err;
+    long long n_tri = -1;  // -1: not made for the current results
     long long n_cavity = 0;
     int ext_sweeps = 0;
     // learned tile proposer
@@ -394,6 +397,7 @@ int create_common(const double *hxyz, const double *hr, const int64_t *counts, i
         classify_init();
         edges_init();
         mlp_init();
+        if (mesh_init() != 0) throw CudaError{cudaErrorInvalidValue, "mesh case table"};
         ck(cudaGetLastError(), "kernel attributes");
         ck(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking), "cudaStreamCreate");
         c->stream = c->own_stream;
@@ -797,6 +801,7 @@ int run_impl(eses_ctx *c)
 int run_guarded(eses_ctx *c)
 {
     c->ran = false;
+    c->n_tri = -1;
     try {
         ck(cudaSetDevice(c->device), "cudaSetDevice");
         return run_impl(c);
@@ -1374,6 +1379,70 @@ int eses_patch_data(const eses_ctx *cc, int32_t *pair_atoms, uint8_t *pair_free,
             vertices[3 * v + 1] = vq[v].y;
             vertices[3 * v + 2] = vq[v].z;
         }
+    return ESES_OK;
+}
+
+int eses_mesh_count(eses_ctx *c, int64_t *n_tri)
+{
+    if (!c || !n_tri) return fail(c, ESES_EINVAL, "NULL argument");
+    if (int rc = single(c)) return rc;
+    if (!c->ran) return fail(c, ESES_ESTATE, "no results: call eses_run first");
+    try {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        if (c->n_tri < 0) {
+            cudaStream_t st = c->stream;
+            const long long nt = c->n_tiles;
+            const Batch &B = c->B;
+            uint32_t *mask = ensure<uint32_t>(c->mesh_mask, (size_t)nt * 3 * (TILE_PTS / 32));
+            int *tile = ensure<int>(c->mesh_tile, nt);
+            int *off = ensure<int>(c->mesh_off, nt + 1);
+            int *derr = ensure<int>(c->mesh_err, 1);
+            launch_mesh_masks(B, (const int8_t *)c->labels.p, mask, st);
+            launch_mesh_count(B, (const int8_t *)c->labels.p, tile, st);
+            scan(c, tile, off, nt);
+            int tot = 0;
+            ck(cudaMemcpyAsync(&tot, off + nt, sizeof(int), cudaMemcpyDeviceToHost, st), "read");
+            ck(cudaStreamSynchronize(st), "synchronize");
+            EdgeOut eo{};
+            for (int a = 0; a < 3; ++a) eo.tau[a] = (double *)c->out_tau[a].p;
+            long long *keys = ensure<long long>(c->mesh_keys, 3 * (size_t)std::max(tot, 1));
+            double *xyz = ensure<double>(c->mesh_xyz, 9 * (size_t)std::max(tot, 1));
+            ck(cudaMemsetAsync(derr, 0, sizeof(int), st), "memset");
+            launch_mesh_emit(B, (const int8_t *)c->labels.p, mask, (const int *)c->edge_start.p, eo, off, keys, xyz,
+                             derr, st);
+            int herr = 0;
+            ck(cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st), "read");
+            ck(cudaStreamSynchronize(st), "synchronize");
+            ck(cudaGetLastError(), "mesh kernels");
+            if (herr) return fail(c, ESES_ESTATE, "a cut cube edge has no intersection in the run's output");
+            c->n_tri = tot;
+        }
+    } catch (const CudaError &e) {
+        return fail(c, ESES_ECUDA, std::string(e.what) + ": " + cudaGetErrorString(e.e));
+    } catch (const std::bad_alloc &) {
+        return fail(c, ESES_ENOMEM, "device allocation failed");
+    }
+    *n_tri = c->n_tri;
+    return ESES_OK;
+}
+
+int eses_mesh(eses_ctx *c, int64_t *keys, double *xyz)
+{
+    if (!c || (!keys && !xyz)) return fail(c, ESES_EINVAL, "NULL argument");
+    int64_t n = 0;
+    if (int rc = eses_mesh_count(c, &n)) return rc;
+    if (n == 0) return ESES_OK;
+    if (keys && cudaMemcpy(keys, c->mesh_keys.p, sizeof(int64_t) * 3 * (size_t)n, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(c, ESES_ECUDA, "copy mesh keys");
+    if (xyz && cudaMemcpy(xyz, c->mesh_xyz.p, sizeof(double) * 9 * (size_t)n, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(c, ESES_ECUDA, "copy mesh points");
+    return ESES_OK;
+}
+
+int eses_mesh_table(int8_t *tri, uint8_t *ntri)
+{
+    if (!tri || !ntri) return fail(nullptr, ESES_EINVAL, "NULL argument");
+    if (mesh_table_host(tri, ntri, ESES_MESH_MAXT) != 0) return fail(nullptr, ESES_EINVAL, "mesh case table");
     return ESES_OK;
 }
 

@@ -77,6 +77,15 @@ int launch_edge_solve(const Model &M, const Batch &B, int precision, const TileS
                       long long *fail_log, cudaStream_t st);
 int launch_edge_polish(const Model &M, const Batch &B, EdgeOut out, long long n_edges_total, const long long *medge,
                        double2 *term, cudaStream_t st);
+// triangle mesh of a one-molecule run (eses_mesh.cu): the case table to constant
+// memory (once per device), the host copy of it, crossing-edge masks per tile,
+// triangles per tile, and the triangles (keys and FP64 points)
+int mesh_init();
+int mesh_table_host(int8_t *tri, uint8_t *n, int max_tri);
+int launch_mesh_masks(const Batch &B, const int8_t *labels, uint32_t *mask, cudaStream_t st);
+int launch_mesh_count(const Batch &B, const int8_t *labels, int *tile_tri, cudaStream_t st);
+int launch_mesh_emit(const Batch &B, const int8_t *labels, const uint32_t *mask, const int *edge_start,
+                     const EdgeOut &out, const int *tile_off, long long *keys, double *xyz, int *err, cudaStream_t st);
 // part_d / part_i: reduce_scratch(n_mol) doubles / int64 each
 long long reduce_scratch(int n_mol);
 int launch_reduce(const Batch &B, const double2 *term, const long long *medge, const int *tile_inside, double *part_d,

@@ -61,7 +61,7 @@ SYMBOLS = ["eses_create", "eses_create_device", "eses_create_batch", "eses_run_b
            "eses_area_volume", "eses_stats", "eses_stage_times", "eses_root_failures", "eses_patch_counts",
            "eses_patch_data", "eses_crossing_edges_noalloc", "eses_set_proposer", "eses_num_tiles",
            "eses_tile_data", "eses_mlp_forward", "eses_mlp_forward_tc", "eses_mlp_grad_scratch", "eses_mlp_grad", "eses_mlp_adam",
-           "eses_last_error", "eses_destroy"]
+           "eses_mesh_count", "eses_mesh", "eses_mesh_table", "eses_last_error", "eses_destroy"]
 STAGE_NAMES = ["binning", "pairs", "arcs", "classify", "band", "edge_count", "edge_solve", "edge_polish", "reduce"]
 
 _lib = None
@@ -126,6 +126,9 @@ def load():
     lib.eses_patch_counts.argtypes = [P, P, P, P]
     lib.eses_patch_data.argtypes = [P, P, P, P, P]
     lib.eses_crossing_edges_noalloc.argtypes = [P, P, P, P, P, P, P, P]
+    lib.eses_mesh_count.argtypes = [P, P]
+    lib.eses_mesh.argtypes = [P, P, P]
+    lib.eses_mesh_table.argtypes = [P, P]
     lib.eses_last_error.argtypes = [P]
     lib.eses_last_error.restype = ctypes.c_char_p
     lib.eses_destroy.argtypes = [P]
@@ -356,6 +359,34 @@ def eses_labels(ctx, out=None):
         out = np.empty(tuple(int(v) for v in dims), np.int8)
     _check(load().eses_labels(ctx, _ptr(out)), ctx)
     return out
+
+
+ESES_MESH_MAXT = 5
+
+
+def eses_mesh_count(ctx) -> int:
+    """Make the triangle mesh of the last run (one molecule); its triangle count."""
+    n = np.zeros(1, np.int64)
+    _check(load().eses_mesh_count(ctx, _ptr(n)), ctx)
+    return int(n[0])
+
+
+def eses_mesh(ctx):
+    """(keys int64 (n, 3), xyz float64 (n, 3, 3)) of the mesh of the last run."""
+    n = eses_mesh_count(ctx)
+    keys = np.empty((n, 3), np.int64)
+    xyz = np.empty((n, 3, 3), np.float64)
+    if n:
+        _check(load().eses_mesh(ctx, _ptr(keys), _ptr(xyz)), ctx)
+    return keys, xyz
+
+
+def eses_mesh_table():
+    """The mesh's 256-case table: (tri int8 (256, ESES_MESH_MAXT, 3), ntri uint8 (256,))."""
+    tri = np.empty((256, ESES_MESH_MAXT, 3), np.int8)
+    ntri = np.empty(256, np.uint8)
+    _check(load().eses_mesh_table(_ptr(tri), _ptr(ntri)))
+    return tri, ntri
 
 
 def eses_labels_device(ctx) -> int:
