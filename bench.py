@@ -11,7 +11,8 @@ point, crossing edges, roots and normals, area and volume.
   e2e        points/s through the public C ABI with host buffers: create from
              pinned host atoms, run, copy labels and intersections back
   plain_fp64 the same step with every stage in FP64 and no proposer (the
-             plain GPU form)
+             plain GPU form), and the filtered step's labels, edges,
+             intersections and normals against its outputs
   proposer_study  the 50,000-atom globule (h 0.2) with the proposer off, the
              certificate on every tile, and the trained MLP + certificate
   roofline   the dominant kernel (by event-timed duration; the other heavy
@@ -309,11 +310,28 @@ def main():
     stage_ms = {k: statistics.mean(s[k] for s in stages) for k in stages[0]}
 
     # ---- plain FP64 form (same step, every stage FP64) ----------------------
+    lab32 = eses.eses_labels(ctx)
+    out32 = [eses.eses_intersections(ctx, a) for a in range(3)]
     eses.eses_set_option(ctx, eses.ESES_OPT_PRECISION, eses.ESES_PREC_FP64)
     set_prop(ctx, "off")
     eses.eses_run(ctx)
     t64, s64 = timed_runs(ctx, max(2, min(args.steps, 5)))
     plain_ms = statistics.mean(t64)
+    # the FP32-filtered step's outputs against the plain FP64 step's
+    out64 = [eses.eses_intersections(ctx, a) for a in range(3)]
+    same_edges = all(np.array_equal(np.sort(out32[a]["idx"]), np.sort(out64[a]["idx"])) for a in range(3))
+    dtau = dnrm = d32 = 0.0
+    if same_edges:
+        for a in range(3):
+            o1, o2 = np.argsort(out32[a]["idx"]), np.argsort(out64[a]["idx"])
+            if len(o1):
+                dtau = max(dtau, float(np.abs(out32[a]["tau"][o1] - out64[a]["tau"][o2]).max()) * wl.h)
+                dnrm = max(dnrm, float(np.abs(out32[a]["normal"][o1] - out64[a]["normal"][o2]).max()))
+                d32 = max(d32, float(np.abs(out32[a]["tau32"].astype(np.float64) - out32[a]["tau"]).max()) * wl.h)
+    precision_check = {"labels_equal": bool(np.array_equal(lab32, eses.eses_labels(ctx))),
+                       "edges_equal": bool(same_edges), "max_intersection_diff_A": dtau,
+                       "max_normal_diff": dnrm, "tau32_rounding_A": d32}
+    del lab32, out32, out64
     eses.eses_set_option(ctx, eses.ESES_OPT_PRECISION, eses.ESES_PREC_FP32_FILTERED)
     eses.eses_destroy(ctx)
 
@@ -534,7 +552,8 @@ def main():
                 "cpu_baseline": cpu,
                 "clocks": clk,
                 "plain_fp64": {"value": all_pts / (plain_ms / 1e3), "unit": UNIT, "ms_per_step": plain_ms,
-                               "stages_ms": {k: statistics.mean(s[k] for s in s64) for k in s64[0]}},
+                               "stages_ms": {k: statistics.mean(s[k] for s in s64) for k in s64[0]},
+                               "fp32_filtered_vs_fp64": precision_check},
                 "stages_ms": stage_ms,
                 "stats": {k: st[k] for k in ("crossing_edges", "inside_points", "circle_pairs", "free_vertices",
                                              "root_failures")},
