@@ -58,7 +58,7 @@ WORKLOAD = 2
 # ncu capture of the globule workload (profiles/k_<kernel>_globule-5000.md),
 # reported only while the kernel's sources are the ones that were captured
 TRAFFIC = {
-    "edge_solve": (53_811_200, {"eses_edges.cu": "7b6ba6d5a23b346f", "eses_tile.cuh": "52f021e2fa8f2849",
+    "edge_solve": (53_811_200, {"eses_edges.cu": "17a5061ebb563876", "eses_tile.cuh": "52f021e2fa8f2849",
                                 "eses_internal.cuh": "7ce4766849297923"}),
     "classify": (9_634_048, {"eses_classify.cu": "b213768c87a2c907", "eses_tile.cuh": "52f021e2fa8f2849",
                              "eses_internal.cuh": "7ce4766849297923"}),

@@ -5,25 +5,33 @@
 //   points whose end labels differ, and the edges with both ends inside.
 // (exclusive scan of the counts -> every tile's output offset per axis; the
 //   paper serialises this output step in a critical section, Algorithm 1)
-// k_edge_solve: per tile, stages the patches; one warp per crossing edge.
-//   The surface along an edge is made of pieces of van der Waals spheres
-//   (convex), tori around pair circles (saddle) and probe spheres around free
-//   triple points (concave).  Every root of every such piece in [0, h] whose
-//   witness (projection on the expanded sphere / nearest circle point / the
-//   triple point) is free, and whose witness distance crosses r_p in the
-//   direction that leaves the end point's side (falling from an inside end,
-//   rising from an outside end), is a candidate.  From an inside end point
-//   the first candidate is the first root; from an outside end point the
-//   first candidate that is not strictly outside M is.  Sphere roots come from
-//   the quadratic, torus roots from the quartic
-//     (|y-o|^2 + rho^2 - r_p^2)^2 = 4 rho^2 (|y-o|^2 - ((y-o).u)^2)
-//   isolated on the derivative chain (quadratic -> cubic -> quartic, monotone
-//   pieces) with safeguarded Newton-bisection, keeping the near branch
-//   (|w| - rho)^2 + z^2 = r_p^2.  The warp works in FP32 with an error bound
-//   on every root; a decision that the bound cannot make (grazing piece, root
-//   near an end point, near tie between candidates, witness near another
-//   sphere) is taken on the FP64 root.  The warp records the chosen piece and
-//   its FP32 root.
+// k_edge_solve: persistent CTAs take tiles from the work queue; per tile the
+//   patches are staged and the tile's crossing edges taken in chunks of at
+//   most 128.  The surface along an edge is made of pieces of van der Waals
+//   spheres (convex), tori around pair circles (saddle) and probe spheres
+//   around free triple points (concave).  Every root of every such piece in
+//   [0, h] whose witness (projection on the expanded sphere / nearest circle
+//   point / the triple point) is free, and whose witness distance crosses r_p
+//   in the direction that leaves the end point's side (falling from an inside
+//   end, rising from an outside end), is a candidate.  From an inside end
+//   point the first candidate is the first root; from an outside end point the
+//   first candidate that is not strictly outside M is.  Per chunk:
+//     1. (edge, piece) pairs that pass a prefilter go to a block pool (one
+//        warp per edge, lanes over the staged pieces);
+//     2. one thread per pair: sphere roots from the quadratic; torus roots of
+//          (|y-o|^2 + rho^2 - r_p^2)^2 = 4 rho^2 (|y-o|^2 - ((y-o).u)^2)
+//        on the near branch (|w| - rho)^2 + z^2 = r_p^2, isolated in FP32 on
+//        eight sub-intervals with certified exclusion and monotonicity tests
+//        and refined by Newton (undecided: the quartic on its derivative
+//        chain, then FP64); every FP32 root carries an error bound;
+//     3. the roots grouped by edge (counting sort);
+//     4. the first root per edge: one thread when the end point is inside or
+//        one candidate is left and the FP32 bounds order the candidates; else
+//        a warp: near ties broken on FP64 roots; at an outside end point each
+//        earlier candidate tested first against the later candidates'
+//        witnesses, then by the full witness search, whose undecided items
+//        are re-tested in FP64.
+//   The chosen piece and its FP32 root are recorded for the polish.
 // k_edge_polish: one thread per crossing edge (full warps of FP64 work): the
 //   FP64 root of the chosen piece next to the recorded one, the normal, the
 //   outputs and the area/volume terms.
