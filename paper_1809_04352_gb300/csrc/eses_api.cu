@@ -1513,7 +1513,8 @@ void eses_destroy(eses_ctx *c)
                     &c->tile_inside, &c->scan_tmp, &c->misc, &c->av, &c->counts, &c->red_d, &c->red_i, &c->fail_log, &c->atom_hi,
                     &c->atom_lo, &c->pair_hi, &c->pair_lo, &c->pair_u32, &c->vert_hi, &c->vert_lo,
                     &c->mlp_params, &c->need, &c->need_pos, &c->tile_list, &c->prop_counts, &c->features,
-                    &c->targets};
+                    &c->targets, &c->ext, &c->ext_open, &c->ext_misc, &c->mesh_mask, &c->mesh_tile, &c->mesh_off,
+                    &c->mesh_keys, &c->mesh_xyz, &c->mesh_err};
     if (c->own_stream) cudaStreamSynchronize(c->own_stream);
     drop_graph(c);
     for (DBuf *b : bufs) free_buf(*b);

@@ -77,3 +77,20 @@ def test_null_context_calls_fail_cleanly(lib):
     lib.eses_destroy(None)
     assert lib.eses_stats(None, None, 0) == eses.ESES_EINVAL
     assert isinstance(lib.eses_last_error(ctypes.c_void_p()), bytes)
+
+
+def test_destroy_frees_every_device_buffer():
+    """Every device buffer the context declares is released by eses_destroy
+    (a source check: a buffer added without its release leaks device memory)."""
+    src = open(os.path.join(ROOT, "paper_1809_04352_gb300", "csrc", "eses_api.cu")).read()
+    names = []
+    for decl in re.findall(r"^\s*DBuf ([^;]+);", src, flags=re.M):
+        names += [n.strip() for n in decl.split(",")]
+    assert len(names) > 60
+    body = src[src.index("void eses_destroy(eses_ctx *c)"):]
+    body = body[:body.index("\n}\n")]
+    for n in names:
+        if n.endswith("[3]"):
+            assert f"free_buf(c->{n[:-3]}[a])" in body, n
+        else:
+            assert f"&c->{n}" in body, n
