@@ -84,7 +84,7 @@ def test_destroy_frees_every_device_buffer():
     (a source check: a buffer added without its release leaks device memory)."""
     src = open(os.path.join(ROOT, "paper_1809_04352_gb300", "csrc", "eses_api.cu")).read()
     names = []
-    for decl in re.findall(r"^\s*DBuf ([^;]+);", src, flags=re.M):
+    for decl in re.findall(r"^\s*DBuf ([A-Za-z0-9_\[\], ]+);", src, flags=re.M):
         names += [n.strip() for n in decl.split(",")]
     assert len(names) > 60
     body = src[src.index("void eses_destroy(eses_ctx *c)"):]
