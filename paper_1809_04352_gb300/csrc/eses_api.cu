@@ -1399,10 +1399,15 @@ int eses_mesh_count(eses_ctx *c, int64_t *n_tri)
             int *derr = ensure<int>(c->mesh_err, 1);
             launch_mesh_masks(B, (const int8_t *)c->labels.p, mask, st);
             launch_mesh_count(B, (const int8_t *)c->labels.p, tile, st);
-            scan(c, tile, off, nt);
-            int tot = 0;
-            ck(cudaMemcpyAsync(&tot, off + nt, sizeof(int), cudaMemcpyDeviceToHost, st), "read");
+            // the total in 64 bits first: the offsets are 32-bit
+            std::vector<int> per_tile((size_t)nt);
+            ck(cudaMemcpyAsync(per_tile.data(), tile, sizeof(int) * (size_t)nt, cudaMemcpyDeviceToHost, st), "read");
             ck(cudaStreamSynchronize(st), "synchronize");
+            long long total = 0;
+            for (int v : per_tile) total += v;
+            if (total >= (1LL << 31)) return fail(c, ESES_EINVAL, "mesh of 2^31 triangles or more");
+            scan(c, tile, off, nt);
+            const int tot = (int)total;
             EdgeOut eo{};
             for (int a = 0; a < 3; ++a) eo.tau[a] = (double *)c->out_tau[a].p;
             long long *keys = ensure<long long>(c->mesh_keys, 3 * (size_t)std::max(tot, 1));
