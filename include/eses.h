@@ -230,7 +230,10 @@ int eses_mol_area_volume(const eses_ctx *ctx, int m, double *area, double *volum
 
 /* Run the whole path: cell binning, patch construction, classification,
  * crossing edges, root solve, area and volume.  Results stay in device memory
- * owned by the context until the next eses_run or eses_destroy. */
+ * owned by the context until the next eses_run or eses_destroy.  Limits of
+ * one context: fewer than 2^27 atoms, circle pairs and free triple points
+ * (ESES_EINVAL), and fewer than 2^31 crossing edges over all molecules (their
+ * offsets are 32-bit; 2^31 edges would take about 200 GB of outputs). */
 int eses_run(eses_ctx *ctx);
 
 /* Grid dimensions and origin (host outputs, 3 values each). */
