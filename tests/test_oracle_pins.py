@@ -83,6 +83,28 @@ def test_single_atom_tangent_edges():
     assert tangent >= 8
 
 
+def test_two_atom_torus_tangent_edge():
+    """Two atoms (r = 1, centres +-1.5 on z, r_p = 1.5): their expanded
+    spheres meet in the circle rho = 2 in z = 0 and the saddle surface passes
+    through (0.5, 0, 0), a grid point, at the middle of its arc.  Along y
+    the distance to the circle is sqrt(0.25 + y^2) - 2 in magnitude, r_p only
+    at y = 0: the grid line touches the surface there from the solvent side,
+    so the edge ending at the point has its (double) root at tau = 1, the
+    point is inside (the tie of C5) and the edge leaving it crosses at
+    tau = 0.  A double root is fixed by FP64 only to about sqrt(eps) of the
+    length scale: 1e-7 A here."""
+    res = oracle.run(np.array([[0.0, 0, -1.5], [0, 0, 1.5]]), np.array([1.0, 1.0]), 1.5, 0.25, 1.0)
+    assert np.allclose(res.lo, [-2.0, -2.0, -3.5])
+    d = res.dims
+    assert res.labels[10, 8, 14] == 1 and res.labels[10, 7, 14] == 0 and res.labels[10, 9, 14] == 0
+    for j, tau in ((7, 1.0), (8, 0.0)):
+        p = (10 * d[1] + j) * d[2] + 14
+        e = int(np.searchsorted(res.idx[1], p))
+        assert res.idx[1][e] == p and res.ptype[1][e] == oracle.TYPE_E
+        assert abs(res.tau[1][e] - tau) * 0.25 < 1e-7
+        assert np.abs(res.normal[1][e] - [1.0, 0.0, 0.0]).max() < 1e-6  # towards the circle point (2, 0, 0)
+
+
 @pytest.mark.parametrize("h,tol", [(0.2, 6e-3), (0.1, 2e-3)])
 def test_single_atom_area_volume_converge(h, tol):
     r = 1.8
