@@ -323,7 +323,9 @@ int eses_patch_data(const eses_ctx *ctx, int32_t *pair_atoms, uint8_t *pair_free
  * array sized for 131,072 tiles of 8x8x8 points (at most 67,108,864 grid
  * points, about 3 MiB, held by every GPU that loads the library until the
  * process exits).  Larger grids return ESES_EINVAL.  The first call on a
- * device looks up that array's address (make it before any stream capture).
+ * device looks up that array's address (make it before any stream capture)
+ * and keeps it for the life of the process: after cudaDeviceReset do not call
+ * this entry point again on that device.
  * Calls share the array: calls that overlap on the GPU race.  Returns
  * ESES_ECAPACITY when a count exceeds its capacity (the first capacity[a]
  * entries are written), ESES_EINVAL for NULL pointers or bad sizes,

@@ -12,7 +12,9 @@
 //
 // The first call on a device looks up that array's device address with
 // cudaGetSymbolAddress (with the device current) and caches it; make that
-// first call before any stream capture.  Every call reuses the same array and
+// first call before any stream capture.  The cached address belongs to the
+// device's current context: after cudaDeviceReset the process must not call
+// this entry point again on that device.  Every call reuses the same array and
 // leaves its contents behind; each call rewrites every entry it reads, so no
 // state carries over, but two calls that overlap on the GPU (different
 // streams, or one launched before the previous has finished on another
@@ -28,6 +30,9 @@ constexpr long long NAL_MAX_TILES = 1LL << 17;  // 131,072 tiles = 67,108,864 po
 constexpr int NAL_THREADS = 256;
 // layout: counts [3][NAL_MAX_TILES], offsets [3 * NAL_MAX_TILES + 1]
 constexpr long long NAL_SCRATCH_INTS = 6 * NAL_MAX_TILES + 1;
+// k_nal_write gives each thread points 2*tid and 2*tid+1, and nal_flag splits a local point index
+// into (p >> 6, (p >> 3) & 7, p & 7): both hold for 8x8x8 tiles only
+static_assert(TILE == 8 && TILE_PTS == 2 * NAL_THREADS, "noalloc kernels assume 8^3 tiles and 256 threads");
 
 static __device__ __align__(256) int g_nal_scratch[NAL_SCRATCH_INTS];
 
@@ -163,9 +168,11 @@ extern "C" int eses_crossing_edges_noalloc(const int8_t *labels, const int64_t d
     for (int a = 0; a < 3; ++a) {
         if (dims[a] < 1 || capacity[a] < 0) return ESES_EINVAL;
         G.dims[a] = dims[a];
-        G.tiles[a] = (int)((dims[a] + TILE - 1) / TILE);
-        if (G.tiles[a] > NAL_MAX_TILES) return ESES_EINVAL;
-        G.nt *= G.tiles[a];
+        // tile count in 64 bits, compared before it is narrowed (a wrapped int would pass the check)
+        const long long ta = (dims[a] - 1) / TILE + 1;
+        if (ta > NAL_MAX_TILES) return ESES_EINVAL;
+        G.tiles[a] = (int)ta;
+        G.nt *= ta;
         if (G.nt > NAL_MAX_TILES) return ESES_EINVAL;  // grid larger than the scratch array covers
     }
     int dev = 0;

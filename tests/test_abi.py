@@ -94,3 +94,20 @@ def test_destroy_frees_every_device_buffer():
             assert f"free_buf(c->{n[:-3]}[a])" in body, n
         else:
             assert f"&c->{n}" in body, n
+
+
+def test_noalloc_rejects_tile_counts_that_wrap_32_bits(lib):
+    """eses_crossing_edges_noalloc checks its size limit in 64 bits: an axis of
+    8 * (2^32 + 1) points has 2^32 + 1 tiles, which a 32-bit tile count would
+    wrap to 1 and let through.  The size check runs before any CUDA call, so
+    placeholder pointers never reach the device."""
+    import ctypes
+    fake = ctypes.c_void_p(16)
+    cap = np.zeros(3, np.int64)
+    counts = np.zeros(3, np.int64)
+    for dims in ([8 * (2 ** 32 + 1), 1, 1], [1, 8 * 2 ** 32, 1], [1, 1, 8 * (2 ** 31) + 8], [2 ** 62, 2, 2],
+                 [512, 512, 264]):
+        d = np.asarray(dims, np.int64)
+        rc = lib.eses_crossing_edges_noalloc(fake, d.ctypes.data, fake, fake, fake, cap.ctypes.data,
+                                             counts.ctypes.data, None)
+        assert rc == eses.ESES_EINVAL, dims
