@@ -6,14 +6,17 @@
 //      shared memory (tile frame) and lists, for every staged atom, the staged
 //      pairs it belongs to;
 //   2. splits the tile into 16 bricks of 2x4x4 points, one warp per brick:
-//      the lanes test the staged atoms against the brick's box and a ballot
-//      compacts the atoms whose expanded ball reaches the brick.  A warp with
-//      an empty list labels its 32 points outside at once; otherwise every
-//      lane tests its point against the short list: inside a van der Waals
-//      ball -> 1, in no expanded ball -> 0, else a shell point;
-//   3. shell points go to a per-tile queue and the whole CTA works through it:
-//      free triple points within r_p, convex witnesses of the containing
-//      balls, saddle witnesses of the pairs of the containing balls.
+//      the lanes test the staged atoms against the brick's box and ballots
+//      give the set of atoms whose expanded ball reaches the brick.  A warp
+//      with an empty set labels its 32 points outside at once; otherwise every
+//      lane tests its point against the set: inside a van der Waals ball -> 1,
+//      in no expanded ball -> 0, else a shell point;
+//   3. shell points go to a per-tile queue; when there are any, the block
+//      builds the staged atoms' neighbour sets (expanded spheres that meet)
+//      and works through the queue: free triple points within r_p, convex
+//      witnesses of the containing balls, saddle witnesses of the pairs of
+//      the containing balls, each witness tested for freeness against the
+//      neighbours of its atoms only.
 //   T = double, FILT = false is the plain FP64 form; T = float, FILT = true
 //   is the filtered form, whose undecided points get LABEL_BAND and are
 //   counted per tile.
@@ -26,17 +29,17 @@ namespace eses {
 
 constexpr int CLS_THREADS = 256;
 constexpr int NBRICK = 16;     // 2x4x4-point bricks per tile
-constexpr int HASH = 1024;     // staged-atom lookup (power of two > 2 A_MAX)
 constexpr int INC_MAX = 2 * P_MAX;
 
 struct ClsSmem {
-    int hkey[HASH];
-    short hval[HASH];
+    int hkey[SLOT_HASH];           // staged-atom lookup (pair_slots)
+    short hval[SLOT_HASH];
     short2 pslot[P_MAX];           // staged slots of each pair's atoms (-1: not staged)
     int inc_start[A_MAX + 1];      // incident pairs per staged atom (CSR)
     int inc_fill[A_MAX];
     short inc[INC_MAX];
-    short blist[NBRICK][A_MAX];    // per-brick atom lists
+    unsigned bmask[NBRICK][AW];    // per-brick sets of the atoms whose expanded ball reaches the brick
+    unsigned nbm[A_MAX * AW];      // neighbour set of every staged atom (build_neighbour_sets)
     int bcount[NBRICK];
     short queue[TILE_PTS];         // shell points
     int nq, band;
@@ -58,45 +61,17 @@ __device__ __forceinline__ T pt_coord(const Grid &G, int k)
     else return (double)k * G.h;
 }
 
-__device__ __forceinline__ unsigned hash_of(int key) { return ((unsigned)key * 2654435761u) & (HASH - 1); }
-
 // per-atom incident pair lists (whole block)
 template <class T>
 __device__ void build_incidence(const TileS<T> &S, ClsSmem &C)
 {
-    for (int k = threadIdx.x; k < HASH; k += blockDim.x) C.hkey[k] = -1;
     for (int a = threadIdx.x; a < A_MAX + 1; a += blockDim.x) C.inc_start[a] = 0;
-    __syncthreads();
-    for (int a = threadIdx.x; a < S.na; a += blockDim.x) {
-        int key = S.agid[a];
-        unsigned h = hash_of(key);
-        while (true) {
-            int prev = atomicCAS(&C.hkey[h], -1, key);
-            if (prev == -1 || prev == key) {
-                C.hval[h] = (short)a;
-                break;
-            }
-            h = (h + 1) & (HASH - 1);
-        }
-    }
-    __syncthreads();
+    pair_slots<T>(S, C.hkey, C.hval, C.pslot);
     for (int p = threadIdx.x; p < S.np; p += blockDim.x) {
-        int2 ij = S.pij[p];
-        short si = -1, sj = -1;
-        for (unsigned h = hash_of(ij.x);; h = (h + 1) & (HASH - 1)) {
-            int k = C.hkey[h];
-            if (k == ij.x) { si = C.hval[h]; break; }
-            if (k == -1) break;
-        }
-        for (unsigned h = hash_of(ij.y);; h = (h + 1) & (HASH - 1)) {
-            int k = C.hkey[h];
-            if (k == ij.y) { sj = C.hval[h]; break; }
-            if (k == -1) break;
-        }
-        C.pslot[p] = make_short2(si, sj);
-        if (si >= 0 && sj >= 0) {
-            atomicAdd(&C.inc_start[si + 1], 1);
-            atomicAdd(&C.inc_start[sj + 1], 1);
+        const short2 sl = C.pslot[p];
+        if (sl.x >= 0 && sl.y >= 0) {
+            atomicAdd(&C.inc_start[sl.x + 1], 1);
+            atomicAdd(&C.inc_start[sl.y + 1], 1);
         }
     }
     __syncthreads();
@@ -152,27 +127,33 @@ __device__ int shell_part(const TileS<T> &S, const ClsSmem &C, int brick, T x, T
         if (t == 1) return 0;
         if (t < 0) unsure = true;
     }
-    const int nb = C.bcount[brick];
+    const int nw = (S.na + 31) >> 5;
     int u = 0;  // candidate number
-    for (int m = 0; m < nb; ++m) {
-        int a = C.blist[brick][m];
+    for (int wd = 0; wd < nw; ++wd) {
+      unsigned bits = C.bmask[brick][wd];
+      while (bits) {
+        const int a = (wd << 5) + __ffs(bits) - 1;
+        bits &= bits - 1;
         P4<T> c = S.atom[a];
         T dx = x - c.x, dy = y - c.y, dz = z - c.z;
         T R = c.w + rp;
         if (lt_sq<FILT>(dx * dx + dy * dy + dz * dz, R * R, R, d0) == 0) continue;  // ball does not hold x
         if ((u & (G - 1)) == r) {
-            int w = face_witness<FILT>(A, a, x, y, z, rp, thr, d0);
+            int w = face_witness<FILT>(A, a, x, y, z, rp, thr, d0, C.nbm);
             if (w == 1) return 0;
             if (w < 0) unsure = true;
         }
         ++u;
         const int k0 = C.inc_start[a], k1 = C.inc_start[a + 1];
         for (int k = k0 + ((r - u) & (G - 1)); k < k1; k += G) {
-            int ws = saddle_witness<FILT>(A, (int)C.inc[k], x, y, z, rp, thr, d0);
+            const int p = (int)C.inc[k];
+            const short2 sl = C.pslot[p];
+            int ws = saddle_witness<FILT>(A, p, x, y, z, rp, thr, d0, C.nbm, (int)sl.x, (int)sl.y);
             if (ws == 1) return 0;
             if (ws < 0) unsure = true;
         }
         u += k1 - k0;
+      }
     }
     return unsure ? 2 : 1;
 }
@@ -244,7 +225,7 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Batch B, Tile
                     hit = ex * ex + ey * ey + ez * ez < reach * reach;
                 }
                 unsigned m = __ballot_sync(0xffffffffu, hit);
-                if (hit) C.blist[brick][cnt + __popc(m & ((1u << lane) - 1))] = (short)a;
+                if (lane == 0) C.bmask[brick][base >> 5] = m;
                 cnt += __popc(m);
             }
             if (lane == 0) C.bcount[brick] = cnt;
@@ -257,18 +238,24 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Batch B, Tile
             if (cnt > 0) {
                 T x = pt_coord<T>(G, li), y = pt_coord<T>(G, lj), z = pt_coord<T>(G, lk);
                 bool vdw = false, sas = false, sas_u = false;
-                for (int m2 = 0; m2 < cnt; ++m2) {
-                    P4<T> c = S.atom[C.blist[brick][m2]];
-                    T dx = x - c.x, dy = y - c.y, dz = z - c.z;
-                    T d2 = dx * dx + dy * dy + dz * dz;
-                    T r = c.w, R = c.w + rp;
-                    if (lt_sq<FILT>(d2, r * r, r, d0) == 1) {
-                        vdw = true;
-                        break;
+                const int nw = (S.na + 31) >> 5;
+                for (int wd = 0; wd < nw && !vdw; ++wd) {
+                    unsigned bits = C.bmask[brick][wd];
+                    while (bits) {
+                        const int a = (wd << 5) + __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        P4<T> c = S.atom[a];
+                        T dx = x - c.x, dy = y - c.y, dz = z - c.z;
+                        T d2 = dx * dx + dy * dy + dz * dz;
+                        T r = c.w, R = c.w + rp;
+                        if (lt_sq<FILT>(d2, r * r, r, d0) == 1) {
+                            vdw = true;
+                            break;
+                        }
+                        int s = lt_sq<FILT>(d2, R * R, R, d0);
+                        if (s == 1) sas = true;
+                        else if (s < 0) sas_u = true;
                     }
-                    int s = lt_sq<FILT>(d2, R * R, R, d0);
-                    if (s == 1) sas = true;
-                    else if (s < 0) sas_u = true;
                 }
                 if (vdw) lab = LABEL_IN;
                 else if (!sas) lab = sas_u ? LABEL_BAND : LABEL_OUT;
@@ -284,9 +271,13 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Batch B, Tile
             }
         }
         __syncthreads();
+        const int nq = C.nq;
+        if (nq > 0) {  // neighbour sets for the witnesses' freeness tests
+            build_neighbour_sets<T>(S, C.nbm, rp);
+            __syncthreads();
+        }
         // phase 2: shell points, the whole block; with few points, groups of
         // up to 32 lanes share one (so a tile's last point is not left to one lane)
-        const int nq = C.nq;
         int gs = 1;
         while (gs < 32 && nq * gs * 2 <= CLS_THREADS) gs <<= 1;
         const int r = lane & (gs - 1);

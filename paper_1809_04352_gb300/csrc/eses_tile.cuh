@@ -44,6 +44,7 @@ struct alignas(16) P4 {
 };
 
 constexpr int STAGE_CELLS = 128;  // cells staged with item-parallel scan (else one thread per cell)
+constexpr int AW = (A_MAX + 31) / 32;  // words of a set of staged atoms (bit k: staged slot k)
 
 template <class T>
 struct TileS {
@@ -403,6 +404,100 @@ __device__ __noinline__ int free_pt(const Acc &A, T qx, T qy, T qz, int e0, int 
     return res;
 }
 
+// Freeness of q against the staged atoms in the set m0 & m1 (m1 may be
+// null): 1 free, 0 covered, -1 undecided.  A witness q on the expanded
+// sphere of atom a (and, for a saddle, of atom b too) can only be covered by
+// an atom whose expanded sphere meets a's (and b's): |q - c_k| < R_k and
+// |q - c_a| = R_a give |c_a - c_k| < R_a + R_k.  So the neighbour sets of a
+// (and b) hold every atom that can cover q, and the answer is the one of
+// every staged atom but a and b; an atom outside the sets could only have
+// left an FP32 test undecided, never covered q.
+template <bool FILT, class Acc, class T>
+__device__ __noinline__ int free_set(const Acc &A, T qx, T qy, T qz, const unsigned *m0, const unsigned *m1, T rp,
+                                     T delta)
+{
+    int res = 1;
+    const int nw = (A.na() + 31) >> 5;
+    for (int w = 0; w < nw; ++w) {
+        unsigned bits = m1 ? (m0[w] & m1[w]) : m0[w];
+        while (bits) {
+            const int k = (w << 5) + __ffs(bits) - 1;
+            bits &= bits - 1;
+            const P4<T> c = A.atom(k);
+            const T dx = qx - c.x, dy = qy - c.y, dz = qz - c.z;
+            const T R = c.w + rp;
+            const int t = lt_sq<FILT>(dx * dx + dy * dy + dz * dz, R * R, R, delta);
+            if (t == 1) return 0;
+            if (t < 0) res = -1;
+        }
+    }
+    return res;
+}
+
+// Staged slots of every staged pair's two atoms (-1: atom not staged), by an
+// open-addressing hash of the staged atoms' model indices (hkey[SLOT_HASH],
+// hval[SLOT_HASH] scratch).  Whole block; ends with a barrier.
+constexpr int SLOT_HASH = 1024;  // power of two > 2 A_MAX
+__device__ __forceinline__ unsigned slot_hash(int key) { return ((unsigned)key * 2654435761u) & (SLOT_HASH - 1); }
+
+template <class T>
+__device__ void pair_slots(const TileS<T> &S, int *hkey, short *hval, short2 *pslot)
+{
+    for (int k = threadIdx.x; k < SLOT_HASH; k += blockDim.x) hkey[k] = -1;
+    __syncthreads();
+    for (int a = threadIdx.x; a < S.na; a += blockDim.x) {
+        const int key = S.agid[a];
+        for (unsigned h = slot_hash(key);; h = (h + 1) & (SLOT_HASH - 1)) {
+            const int prev = atomicCAS(&hkey[h], -1, key);
+            if (prev == -1 || prev == key) {
+                hval[h] = (short)a;
+                break;
+            }
+        }
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < S.np; p += blockDim.x) {
+        const int2 ij = S.pij[p];
+        short si = -1, sj = -1;
+        for (unsigned h = slot_hash(ij.x);; h = (h + 1) & (SLOT_HASH - 1)) {
+            const int k = hkey[h];
+            if (k == ij.x) { si = hval[h]; break; }
+            if (k == -1) break;
+        }
+        for (unsigned h = slot_hash(ij.y);; h = (h + 1) & (SLOT_HASH - 1)) {
+            const int k = hkey[h];
+            if (k == ij.y) { sj = hval[h]; break; }
+            if (k == -1) break;
+        }
+        pslot[p] = make_short2(si, sj);
+    }
+    __syncthreads();
+}
+
+// Neighbour sets of the staged atoms (whole block): bit b of nbm[a * AW + w]
+// (b = 32 w + bit) is set when the expanded spheres of staged atoms a != b
+// come within 1e-3 A of meeting (the margin covers the rounding of staged
+// FP32 positions, so no true neighbour is left out).
+template <class T>
+__device__ __forceinline__ void build_neighbour_sets(const TileS<T> &S, unsigned *nbm, T rp)
+{
+    const int na = S.na, nw = (na + 31) >> 5;
+    for (int it = threadIdx.x; it < na * nw; it += blockDim.x) {
+        const int a = it / nw, w = it - a * nw;
+        const P4<T> ca = S.atom[a];
+        const T Ra = ca.w + rp + T(1e-3);
+        unsigned bits = 0u;
+        const int b0 = w << 5, b1 = min(na, b0 + 32);
+        for (int b = b0; b < b1; ++b) {
+            const P4<T> cb = S.atom[b];
+            const T dx = ca.x - cb.x, dy = ca.y - cb.y, dz = ca.z - cb.z;
+            const T reach = Ra + cb.w + rp;
+            if (b != a && dx * dx + dy * dy + dz * dz < reach * reach) bits |= 1u << (b - b0);
+        }
+        nbm[a * AW + w] = bits;
+    }
+}
+
 // Direction from a circle's axis towards y (y relative to the centre, u the
 // unit axis): the part of y normal to u, with the rounding left along u
 // removed, so it is normal to u even next to the axis; on the axis (to 1e-12
@@ -493,31 +588,35 @@ __device__ __forceinline__ int saddle_proposal(const Acc &A, int p, T x, T y, T 
     return t;
 }
 
-// Convex witness of atom a at x: 1 free projection at distance < thr,
-// 0 none, -1 undecided.
+// Convex witness of staged atom a at x: 1 free projection at distance < thr,
+// 0 none, -1 undecided.  nbm: the staged atoms' neighbour sets; the
+// projection's freeness is tested against a's neighbours (free_set).
 template <bool FILT, class Acc, class T>
-__device__ __noinline__ int face_witness(const Acc &A, int a, T x, T y, T z, T rp, T thr, T d0)
+__device__ __noinline__ int face_witness(const Acc &A, int a, T x, T y, T z, T rp, T thr, T d0, const unsigned *nbm)
 {
     T qx, qy, qz, dq;
     int e0, e1;
     const int tw = face_proposal<FILT>(A, a, x, y, z, rp, thr, d0, qx, qy, qz, dq, e0, e1);
     if (tw == 0) return 0;
     if (tw == -2) return -1;
-    int f = free_pt<FILT>(A, qx, qy, qz, e0, e1, rp, dq + d0);
+    int f = free_set<FILT>(A, qx, qy, qz, nbm + a * AW, (const unsigned *)nullptr, rp, dq + d0);
     if (f == 1 && tw == 1) return 1;
     return f == 0 ? 0 : -1;
 }
 
-// Saddle witness of pair p at x: nearest point of its circle.
+// Saddle witness of pair p at x: nearest point of its circle; its freeness
+// is tested against the common neighbours of the pair's staged atoms (slots
+// sa, sb).
 template <bool FILT, class Acc, class T>
-__device__ __noinline__ int saddle_witness(const Acc &A, int p, T x, T y, T z, T rp, T thr, T d0)
+__device__ __noinline__ int saddle_witness(const Acc &A, int p, T x, T y, T z, T rp, T thr, T d0, const unsigned *nbm,
+                                           int sa, int sb)
 {
     T qx, qy, qz, dq;
     int e0, e1;
     const int t = saddle_proposal<FILT>(A, p, x, y, z, rp, thr, d0, qx, qy, qz, dq, e0, e1);
     if (t == 0) return 0;
     if (t == -2) return -1;
-    int f = free_pt<FILT>(A, qx, qy, qz, e0, e1, rp, dq + d0);
+    int f = free_set<FILT>(A, qx, qy, qz, nbm + sa * AW, nbm + sb * AW, rp, dq + d0);
     if (f == 1 && t == 1) return 1;
     return f == 0 ? 0 : -1;
 }
