@@ -78,6 +78,23 @@ def captured_traffic(kernel):
     return nbytes
 
 
+def measure_fma_peaks(stream_ptr=0):
+    """FP32 and FP64 FMA throughput of this device, measured by the package's
+    FMA microbenchmark (libpeaks.so, CUDA events, best of 5 launches)."""
+    import ctypes
+
+    from paper_1809_04352_gb300 import build as libbuild
+    lib = ctypes.CDLL(libbuild.PEAKS_LIB)
+    lib.peaks_fma.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]
+    lib.peaks_fma.restype = ctypes.c_int
+    out = (ctypes.c_double * 4)()
+    if lib.peaks_fma(5, ctypes.c_void_p(stream_ptr) if stream_ptr else None, out) != 0:
+        return None
+    return {"fp32_tflops": out[0], "fp32_kernel_ms": out[1], "fp64_tflops": out[2], "fp64_kernel_ms": out[3],
+            "how": "FMA microbenchmark: 8 independent FMA chains per thread, 8 blocks of 256 threads per SM, "
+                   "2 flops per FMA, best of 5 launches timed with CUDA events"}
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -147,22 +164,58 @@ def dist_setup():
     return rank_env()
 
 
-def cpu_sample(xyz, rad, wl, seed, n_blocks=None, block_pts=32):
-    """Oracle on a seeded sample of block_pts^3 blocks: (points, seconds, cores)."""
+def block_atom_counts(xyz, rad, wl, dims, lo, block_pts):
+    """Per block of the oracle's block layout (block_pts points, shared faces):
+    the number of atoms whose reach r + 2 r_p meets the block's box (a host
+    count used only to stratify the timing sample)."""
+    import numpy as np
+
+    import oracle
+    nb = [oracle.block_count(int(d), block_pts) for d in dims]
+    cells = block_pts - 1
+    edge = cells * wl.h
+    reach = rad + 2.0 * wl.r_p
+    b0 = np.clip(np.floor((xyz - reach[:, None] - lo) / edge).astype(np.int64), 0, np.array(nb) - 1)
+    b1 = np.clip(np.floor((xyz + reach[:, None] - lo) / edge).astype(np.int64), 0, np.array(nb) - 1)
+    cnt = np.zeros(nb, np.int64)
+    for i in range(xyz.shape[0]):
+        cnt[b0[i, 0]:b1[i, 0] + 1, b0[i, 1]:b1[i, 1] + 1, b0[i, 2]:b1[i, 2] + 1] += 1
+    return cnt.reshape(-1)
+
+
+def cpu_sample(xyz, rad, wl, seed, per_stratum=None, block_pts=32):
+    """The oracle's whole-grid time on the host cores, extrapolated from a
+    stratified sample: blocks (block_pts points) split into three strata by
+    the atoms that reach them (none; up to the median; more), per_stratum
+    seeded blocks of each timed on all cores, the whole grid's time taken as
+    the sum over strata of (blocks in the stratum) x (measured time per
+    block).  Returns (grid points, estimated seconds, cores, blocks timed,
+    measured seconds)."""
     import numpy as np
 
     import oracle
     cores = oracle.num_threads()
-    dims, _ = oracle.grid(xyz, rad, wl.h, wl.margin)
-    nb = [oracle.block_count(int(d), block_pts) for d in dims]
-    total = nb[0] * nb[1] * nb[2]
-    n_blocks = n_blocks or 2 * cores
+    dims, lo = oracle.grid(xyz, rad, wl.h, wl.margin)
+    cnt = block_atom_counts(np.asarray(xyz), np.asarray(rad), wl, dims, lo, block_pts)
+    nz = cnt[cnt > 0]
+    med = float(np.median(nz)) if len(nz) else 0.0
+    strata = [np.flatnonzero(cnt == 0), np.flatnonzero((cnt > 0) & (cnt <= med)), np.flatnonzero(cnt > med)]
+    per_stratum = per_stratum or cores
     rng = np.random.default_rng(seed)
-    ids = rng.choice(total, size=min(n_blocks, total), replace=False)
-    t0 = time.perf_counter()
-    res = oracle.run(xyz, rad, wl.r_p, wl.h, wl.margin, block_pts=block_pts, block_ids=ids, nthreads=cores)
-    dt = time.perf_counter() - t0
-    return res.n_points, dt, cores, len(ids)
+    est, measured, timed = 0.0, 0.0, 0
+    for ids in strata:
+        if len(ids) == 0:
+            continue
+        pick = np.sort(rng.choice(ids, size=min(per_stratum, len(ids)), replace=False))
+        t0 = time.perf_counter()
+        oracle.run(xyz, rad, wl.r_p, wl.h, wl.margin, block_pts=block_pts, block_ids=pick, nthreads=cores)
+        dt = time.perf_counter() - t0
+        # dt is the wall time of len(pick) blocks on min(len(pick), cores) threads
+        cpu_per_block = dt * min(len(pick), cores) / len(pick)
+        est += len(ids) * cpu_per_block / cores
+        measured += dt
+        timed += len(pick)
+    return int(np.prod(dims)), est, cores, timed, measured
 
 
 def run_reference(args):
@@ -173,19 +226,22 @@ def run_reference(args):
     wl = inputs.WORKLOADS[WORKLOAD]
     xyz, rad = inputs.workload_atoms(WORKLOAD)
     for w in range(args.warmup):
-        cpu_sample(xyz, rad, wl, seed=100 + w, n_blocks=args.ref_blocks)
-    pts, secs = 0, 0.0
+        cpu_sample(xyz, rad, wl, seed=100 + w, per_stratum=args.ref_blocks)
+    pts, secs, meas = 0, 0.0, 0.0
     cores = blocks = 0
     for k in range(args.steps):
-        p, dt, cores, blocks = cpu_sample(xyz, rad, wl, seed=200 + k, n_blocks=args.ref_blocks)
+        p, dt, cores, blocks, m = cpu_sample(xyz, rad, wl, seed=200 + k, per_stratum=args.ref_blocks)
         pts += p
         secs += dt
+        meas += m
     value = pts / secs
-    sample = f"{blocks} seeded 32^3-point blocks of {wl.name} per step, {args.steps} steps"
+    sample = (f"extrapolated: per step, a stratified sample of {blocks} seeded 32^3-point blocks of {wl.name} "
+              f"(three strata by the atoms reaching a block) timed on {cores} cores, the whole grid's time "
+              f"estimated from the time per block of each stratum; {args.steps} steps, {meas:.1f} s measured")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_of(wl, xyz, None),
+            "data": "synthetic", "config": config_of(wl, xyz, pts // max(args.steps, 1)),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -199,13 +255,56 @@ def config_of(wl, xyz, npts):
             "l2": "flushed between steps (256 MiB device write)"}
 
 
+def fp_compare(eses, ctx, n_mol, h, set_prop, prop_mode, k_steps, labels=True):
+    """The context's FP32-filtered results (already run) against its plain
+    FP64 form (every stage FP64, no proposer): labels, crossing edges, the
+    largest intersection and normal differences, and the FP64 form's step
+    time.  Restores the filtered precision and the proposer."""
+    import numpy as np
+
+    def grab():
+        return [[eses.eses_mol_intersections(ctx, m, a, fp32=False) for a in range(3)] for m in range(n_mol)]
+
+    a32 = grab()
+    lab32 = [eses.eses_mol_labels(ctx, m) for m in range(n_mol)] if labels else None
+    in32 = eses.eses_stats(ctx)["inside_points"]
+    eses.eses_set_option(ctx, eses.ESES_OPT_PRECISION, eses.ESES_PREC_FP64)
+    set_prop(ctx, "off")
+    eses.eses_run(ctx)
+    t = []
+    for _ in range(k_steps):
+        t0 = time.perf_counter()
+        eses.eses_run(ctx)
+        t.append(time.perf_counter() - t0)
+    a64 = grab()
+    same_lab = None
+    if labels:
+        same_lab = all(np.array_equal(lab32[m], eses.eses_mol_labels(ctx, m)) for m in range(n_mol))
+    in64 = eses.eses_stats(ctx)["inside_points"]
+    same_edges, dtau, dnrm = True, 0.0, 0.0
+    for m in range(n_mol):
+        for a in range(3):
+            x, y = a32[m][a], a64[m][a]
+            if not np.array_equal(x["idx"], y["idx"]):  # same tiles, same order when the edges agree
+                same_edges = False
+                continue
+            if len(x["idx"]):
+                dtau = max(dtau, float(np.abs(x["tau"] - y["tau"]).max()) * h)
+                dnrm = max(dnrm, float(np.abs(x["normal"] - y["normal"]).max()))
+    eses.eses_set_option(ctx, eses.ESES_OPT_PRECISION, eses.ESES_PREC_FP32_FILTERED)
+    set_prop(ctx, prop_mode)
+    return {"labels_equal": same_lab, "inside_points_equal": bool(in32 == in64), "edges_equal": same_edges,
+            "max_intersection_diff_A": dtau, "max_normal_diff": dnrm,
+            "fp64_form_ms_per_step": 1e3 * statistics.mean(t), "fp64_form_steps": k_steps}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--ref-blocks", type=int, default=None)
+    ap.add_argument("--ref-blocks", type=int, default=None, help="reference arm: blocks timed per stratum")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-only", action="store_true",
                     help="only the warm-up and device-resident steps (for ncu captures); prints stage times")
@@ -218,6 +317,11 @@ def main():
                     help="tile proposer of the headline step (default: the trained MLP with the exact certificate)")
     ap.add_argument("--no-proposer-study", action="store_true",
                     help="skip the proposer comparison on the 50,000-atom globule")
+    ap.add_argument("--no-density", action="store_true", help="skip the paper-density globule")
+    ap.add_argument("--no-precision-study", action="store_true",
+                    help="skip the FP32-filtered vs plain FP64 comparison on the larger workloads")
+    ap.add_argument("--no-stream", action="store_true",
+                    help="skip the assembly at h 0.1 streamed in slabs (3.1e11 points, beyond device memory)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -372,10 +476,15 @@ def main():
     # ---- roofline of the dominant kernel ------------------------------------
     peaks, psrc = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = N_SM * FP32_LANES * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    fma = measure_fma_peaks(stream.cuda_stream)
+    if fma is not None:
+        fp32_peak = fma["fp32_tflops"]
+        psrc_txt = "measured: " + fma["how"]
+    else:
+        fp32_peak = N_SM * FP32_LANES * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+        psrc_txt = f"derived: {N_SM} SMs x {FP32_LANES} FP32 lanes x 2 flops x {sm_max:.0f} MHz (sm_max_mhz {psrc})"
     with open(os.path.join(ROOT, "tests", "golden", "flop_model.json")) as f:
         fm = json.load(f)[wl.name]
-    psrc_txt = f"derived: {N_SM} SMs x {FP32_LANES} FP32 lanes x 2 flops x {sm_max:.0f} MHz (sm_max_mhz {psrc})"
     # algorithmic flops per launch (oracle-counted flop model) and the kernel's
     # mean event-timed duration over the timed steps
     kernels = {
@@ -429,6 +538,8 @@ def main():
         study["points"] = int(sst["points"])
         study["mlp_gain_vs_off"] = study["off"]["ms_per_step"] / study["mlp"]["ms_per_step"]
         study["mlp_gain_vs_certify"] = study["certify"]["ms_per_step"] / study["mlp"]["ms_per_step"]
+        if not args.no_precision_study:
+            study["fp32_filtered_vs_fp64"] = fp_compare(eses, sctx, 1, swl.h, set_prop, "mlp", 2)
         eses.eses_destroy(sctx)
 
     # ---- exterior-only surface on the headline molecule -----------------------
@@ -453,6 +564,33 @@ def main():
                     "crossing_edges": int(xst["crossing_edges"]), "area_A2": xav[0], "volume_A3": xav[1],
                     "graph": False}
         eses.eses_destroy(xctx)
+
+    # ---- the paper-density globule (0.1 atoms/A^3), h 0.25 and 0.4 ---------------
+    density = None
+    if not args.no_density:
+        dxyz, drad = inputs.paper_density(5000, 2200)
+        density = {"workload": "paper-density-5000: synthetic globule at 0.1 atoms/A^3 (eight atoms per residue), "
+                               f"{dxyz.shape[0]} atoms, r_p 1.4 A, margin 0.8 A"}
+        for dh in (0.25, 0.4):
+            dctx = eses.eses_create(dxyz, drad, 1.4, dh, 0.8)
+            eses.eses_set_option(dctx, eses.ESES_OPT_STREAM, stream.cuda_stream)
+            eses.eses_set_option(dctx, eses.ESES_OPT_PROFILE, 1)
+            eses.eses_set_option(dctx, eses.ESES_OPT_GRAPH, 1 if use_graph else 0)
+            set_prop(dctx, args.proposer)
+            for _ in range(args.warmup):
+                eses.eses_run(dctx)
+            torch.cuda.synchronize()
+            barrier()
+            dt, ds = timed_runs(dctx, max(3, min(args.steps, 10)))
+            dst = eses.eses_stats(dctx)
+            density[f"h{dh}"] = {"value": dst["points"] / (statistics.mean(dt) / 1e3), "unit": UNIT,
+                                 "ms_per_step": statistics.mean(dt), "points": int(dst["points"]),
+                                 "crossing_edges": int(dst["crossing_edges"]),
+                                 "root_failures": int(dst["root_failures"]),
+                                 "stages_ms": {k: statistics.mean(v[k] for v in ds) for k in ds[0]}}
+            if not args.no_precision_study:
+                density[f"h{dh}"]["fp32_filtered_vs_fp64"] = fp_compare(eses, dctx, 1, dh, set_prop, args.proposer, 2)
+            eses.eses_destroy(dctx)
 
     # ---- batched workload: 256 molecules in one context ---------------------
     batch = None
@@ -491,6 +629,8 @@ def main():
                  "points": int(bpts), "crossing_edges": int(bst["crossing_edges"]),
                  "root_failures": int(bst["root_failures"]), "kernel_launches_per_step": int(bst["kernel_launches"]),
                  "graph": use_graph}
+        if not args.no_precision_study:
+            batch["fp32_filtered_vs_fp64"] = fp_compare(eses, bctx, len(mols), bwl.h, lambda c, m: None, None, 1)
         eses.eses_destroy(bctx)
 
     # ---- the 1,000,000-atom assembly in one context --------------------------
@@ -525,14 +665,44 @@ def main():
                     "ms_per_step": 1e3 * atot / len(at), "steps": len(at), "points": int(ast["points"]),
                     "crossing_edges": int(ast["crossing_edges"]), "root_failures": int(ast["root_failures"]),
                     "graph": use_graph, "proposer": args.proposer}
+        if not args.no_precision_study:
+            assembly["fp32_filtered_vs_fp64"] = fp_compare(eses, actx, 1, awl.h, set_prop, args.proposer, 1,
+                                                           labels=False)
         eses.eses_destroy(actx)
+
+    # ---- the assembly at h 0.1 streamed in slabs (beyond device memory) -----
+    streamed = None
+    if not args.no_stream:
+        from paper_1809_04352_gb300 import stream as sstream
+        axyz, arad = inputs.workload_atoms(5)
+        free_b, total_b = torch.cuda.mem_get_info()
+        kept = {"slabs": 0}
+
+        def sink(k, part):
+            kept["slabs"] += 1
+
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tot = sstream.stream(axyz, arad, 1.4, 0.1, 0.8, sink, max_points=6 << 30, block_pts=128,
+                             proposer_params=params if args.proposer == "mlp" else None)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        streamed = {"workload": f"assembly-1M at h 0.1 A: {int(np.prod(tot['dims']))} points "
+                                f"({int(np.prod(tot['dims'])) / 1e9:.0f} GB of labels, device {total_b / 1e9:.0f} GB), "
+                                f"{tot['slabs']} slabs of at most {6 << 30} points, 2 contexts on 2 streams",
+                    "value": tot["points"] / wall, "unit": UNIT, "wall_s": wall, "points": int(tot["points"]),
+                    "crossing_edges": int(tot["crossing_edges"]), "area_A2": tot["area"], "volume_A3": tot["volume"],
+                    "timing": "host wall clock around the whole streamed run: model builds, every slab's run and "
+                              "its labels and intersections copied to host memory"}
 
     # ---- CPU baseline (rank 0, N = 1) ---------------------------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        pts, secs, cores, nblk = cpu_sample(xyz, rad, wl, seed=7)
+        pts, secs, cores, nblk, meas = cpu_sample(xyz, rad, wl, seed=7)
         cpu = {"value": pts / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{nblk} seeded 32^3-point blocks of {wl.name} ({pts} points, {secs:.1f} s)"}
+               "sample": f"extrapolated: a stratified sample of {nblk} seeded 32^3-point blocks of {wl.name} "
+                         f"(three strata by the atoms reaching a block, {meas:.1f} s measured on {cores} cores); "
+                         f"whole-grid time estimated as {secs:.1f} s for {pts} points"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -544,11 +714,15 @@ def main():
                 "gpu_launches": int(st["kernel_launches"]) * args.steps,
                 "roofline": roofline,
                 "roofline_other_kernels": roofline_others,
+                "peaks": {"fma": fma, "fp32_derived_tflops": N_SM * FP32_LANES * 2 * sm_max * 1e6 / 1e12,
+                          "hbm_gbs": peaks.get("hbm_gbs"), "hbm_source": psrc},
                 "launch": {"cuda_graph": use_graph, "autotuned": tuned, "proposer": args.proposer},
                 "proposer_study": study,
                 "exterior": exterior,
                 "batch": batch,
                 "assembly": assembly,
+                "assembly_streamed": streamed,
+                "paper_density": density,
                 "cpu_baseline": cpu,
                 "clocks": clk,
                 "plain_fp64": {"value": all_pts / (plain_ms / 1e3), "unit": UNIT, "ms_per_step": plain_ms,

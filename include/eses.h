@@ -32,9 +32,14 @@
  * lines (an edge with both ends inside counts h; a crossing edge counts the
  * part on the inside end's side of the root).
  *
- * Blocks (§2.3-2.5, Algorithm 1): work is grouped in cubic blocks of B
- * points per edge sharing faces (B-1 cells, ownership half-open per Eq. 5);
- * results do not depend on B.
+ * Blocks (§2.3-2.5, Algorithm 1): the paper splits the grid into cubic
+ * blocks computed independently, each with the atoms near it.  Here the
+ * blocks are the unit of eses_set_blocks (block selections for streaming or
+ * for sharding one molecule over processes): block b along an axis owns the
+ * points [b B, min((b+1) B, dims)) and the edges leaving them in +
+ * directions, B = ESES_OPT_BLOCK_PTS.  (The paper's blocks share their faces,
+ * B - 1 cells; these own B points each, so that a block is whole 8x8x8
+ * tiles.)  Results never depend on B or on the selection.
  *
  * Conventions for every function below:
  *   - return value 0 on success, a negative ESES_E* code on failure; on
@@ -61,12 +66,13 @@ typedef struct eses_ctx eses_ctx;
 #define ESES_ENOMEM (-2)    /* host or device allocation failed */
 #define ESES_ECUDA (-3)     /* a CUDA call failed */
 #define ESES_ETIMEOUT (-4)  /* a bounded device wait expired */
-#define ESES_ECAPACITY (-5) /* a per-tile list exceeded its capacity */
+#define ESES_ECAPACITY (-5) /* a per-tile list exceeded its capacity (even in global memory, see eses_stats [15]) */
 #define ESES_ESTATE (-6)    /* call out of order (e.g. results before eses_run) */
 #define ESES_EROOT (-7)     /* a crossing edge had no surface root (numerical failure) */
 
 /* option keys for eses_set_option */
-#define ESES_OPT_BLOCK_PTS 1   /* points per block edge, >= 9 (default 64) */
+#define ESES_OPT_BLOCK_PTS 1   /* B, points per block edge for eses_set_blocks: a multiple of 8 in [8, 2^20]
+                                  (default 64); changing it clears a block selection */
 #define ESES_OPT_PRECISION 2   /* ESES_PREC_* (default ESES_PREC_FP32_FILTERED) */
 #define ESES_OPT_STREAM 3      /* cudaStream_t cast to int64 (0 = the context's own stream) */
 #define ESES_OPT_SYNC 4        /* 1 (default): eses_run waits for the device; 0: returns after enqueueing */
@@ -86,6 +92,20 @@ typedef struct eses_ctx eses_ctx;
                                   is solvent, §1).  Its sweeps are synchronised from the host, so a run with this
                                   option is never captured in a CUDA graph.  Timed in the "band" stage; the number
                                   of filled points is eses_stats [13]. */
+#define ESES_OPT_TC_WAIT 14    /* for tests of the failure path: polls of each tensor-core wait of the proposer's
+                                  scoring (-1 = the default limit, 2^22).  A wait that runs out makes eses_run return
+                                  ESES_ETIMEOUT with exact labels (the tiles go to the exact classification); 0 makes
+                                  every scoring wait give up at once.  The wait before the tensor memory is freed
+                                  always uses the default limit, so no memory is freed under work in flight. */
+#define ESES_OPT_CULL 16       /* 1 (default): buried-patch pre-culling (the paper's proposed improvement, §5):
+                                  only the circles that keep a free arc, the expanded spheres that keep a free face
+                                  and the free triple points carry witnesses into the tiles; 0: every circle and
+                                  every face does (results are identical; for measuring what the culling saves) */
+#define ESES_OPT_FAIL_ALLOC 15 /* for tests of the failure path: N >= 1 makes the N-th device allocation that the
+                                  context's next eses_run, eses_autotune, eses_set_proposer or eses_mesh_count calls
+                                  attempt fail with ESES_ENOMEM before cudaMalloc is called (the count runs across
+                                  calls until it fires; 0 = never, the default).  The context stays valid: the next
+                                  run plans again, and eses_destroy releases every buffer. */
 
 #define ESES_PROPOSER_OFF 0      /* classify every tile (default) */
 #define ESES_PROPOSER_MLP 1      /* the MLP scores tiles; those scored far are certified and filled */
@@ -104,6 +124,18 @@ typedef struct eses_ctx eses_ctx;
  * same); atom indices reported by the library are input indices. */
 int eses_create(const double *xyz, const double *radii, int64_t n_atoms, double r_p, double h, double margin,
                 eses_ctx **out);
+
+/* As eses_create, for one molecule on a grid the caller gives instead of the
+ * grid of Eq. 2: point (i,j,k) at origin + h*(i,j,k), dims[a] points per axis
+ * (host, 3 values each; dims in [1, 2^30], at most 2^40 points).  The atoms
+ * need not lie inside the grid.  This is for the ranks of one molecule split
+ * over processes: each holds only the atoms near its blocks and all must use
+ * the molecule's own grid.  The labels and intersections of every point
+ * equal those of a context holding all atoms on the same grid as long as
+ * the atoms within r_i + 2 r_p (+ 1e-6 A) of the computed box (see
+ * eses_set_blocks) are present (§2.2: nothing farther can change a point). */
+int eses_create_on_grid(const double *xyz, const double *radii, int64_t n_atoms, double r_p, double h,
+                        const double origin[3], const int64_t dims[3], eses_ctx **out);
 
 /* As eses_create, with xyz and radii in device memory (copied on the device). */
 int eses_create_device(const double *xyz, const double *radii, int64_t n_atoms, double r_p, double h, double margin,
@@ -227,6 +259,7 @@ int eses_mol_intersections_device(const eses_ctx *ctx, int m, int axis, const in
                                   const double **tau, const double **normal, const float **tau32,
                                   const float **normal32);
 int eses_mol_area_volume(const eses_ctx *ctx, int m, double *area, double *volume);
+int eses_mol_intersection_patches(const eses_ctx *ctx, int m, int axis, int8_t *kind, int32_t *atoms);
 
 /* Run the whole path: cell binning, patch construction, classification,
  * crossing edges, root solve, area and volume.  Results stay in device memory
@@ -235,6 +268,28 @@ int eses_mol_area_volume(const eses_ctx *ctx, int m, double *area, double *volum
  * (ESES_EINVAL), and fewer than 2^31 crossing edges over all molecules (their
  * offsets are 32-bit; 2^31 edges would take about 200 GB of outputs). */
 int eses_run(eses_ctx *ctx);
+
+/* Block selections of a one-molecule context (§2.3-2.5, Algorithm 1 runs
+ * blocks one by one; here a selection is one run).  eses_num_blocks: blocks
+ * per axis, ceil(dims / B) (host output).  eses_set_blocks: the next runs
+ * compute only the blocks [block_lo[a], block_hi[a]) per axis (host, 3
+ * values each; 0 <= lo < hi <= eses_num_blocks); NULL, NULL restores the
+ * whole grid.  A selection owns the points of its blocks; the run also
+ * labels one 8-point layer of tiles beyond them in + directions (the other
+ * ends of the owned edges) but reports only owned points: eses_labels copies
+ * the owned box (eses_owned_box: its first point lo[3] and extent dims[3] in
+ * grid points), the intersections are the owned edges with lower indices of
+ * the full grid (eses_grid), in tile order within the selection, and area,
+ * volume and eses_stats [0] cover the owned part, so the results of disjoint
+ * selections add up to the whole grid's.  Device memory follows the
+ * selection's size: a grid larger than the device is run in selections.
+ * Under a selection eses_labels_device, eses_mesh_count and the
+ * exterior-only option return an error (they need the whole grid).  One run
+ * computes fewer than 2^29 tiles of 8x8x8 points (about 2.7e11 points);
+ * eses_run returns ESES_EINVAL for a larger grid without a selection. */
+int eses_num_blocks(const eses_ctx *ctx, int64_t nblocks[3]);
+int eses_set_blocks(eses_ctx *ctx, const int64_t block_lo[3], const int64_t block_hi[3]);
+int eses_owned_box(const eses_ctx *ctx, int64_t lo[3], int64_t dims[3]);
 
 /* Grid dimensions and origin (host outputs, 3 values each). */
 int eses_grid(const eses_ctx *ctx, int64_t dims[3], double origin[3]);
@@ -261,6 +316,19 @@ int eses_intersections(const eses_ctx *ctx, int axis, int64_t *lower_idx, double
 int eses_intersections_device(const eses_ctx *ctx, int axis, const int64_t **lower_idx, const double **tau,
                               const double **normal, const float **tau32, const float **normal32);
 
+/* The surface patch of every intersection of one axis and the atoms that
+ * generate it -- the "nearby atoms" of each surface point that the paper's
+ * chain colouring uses (§4.1).  Host outputs, caller-allocated for
+ * eses_num_intersections() records, in the order of eses_intersections, each
+ * may be NULL: kind (int8: 0 convex patch of a van der Waals sphere, 1 saddle
+ * patch of a pair torus, 2 concave patch of a probe sphere at a free triple
+ * point, -1 an edge with no root, see ESES_EROOT) and atoms (3 int32 per
+ * record: the input indices of the patch's one, two or three atoms in
+ * ascending order, padded with -1).  The patch is the one whose witness is
+ * the nearest free probe centre at the intersection; where two patches meet
+ * at an intersection (a crease, measure zero) either may be reported. */
+int eses_intersection_patches(const eses_ctx *ctx, int axis, int8_t *kind, int32_t *atoms);
+
 /* Surface area (A^2) and enclosed volume (A^3), host outputs. */
 int eses_area_volume(const eses_ctx *ctx, double *area, double *volume);
 
@@ -271,7 +339,10 @@ int eses_area_volume(const eses_ctx *ctx, double *area, double *volume);
  * root failure, [9] inside points, [10] kernels launched by the run,
  * [11] tiles proposed far, [12] tiles certified far (eses_set_proposer),
  * [13] cavity points labelled inside (ESES_OPT_EXTERIOR), [14] flood-fill
- * sweeps. */
+ * sweeps, [15] tile stagings that overflowed the shared-memory lists (320
+ * atoms, 512 free-arc pairs, 640 free triple points) and were redone with
+ * lists in global memory (1024, 2048, 2048; beyond those ESES_ECAPACITY),
+ * summed over the classification, the FP64 re-evaluation and the root solve. */
 int eses_stats(const eses_ctx *ctx, int64_t *out, int n);
 
 /* Device time in milliseconds of every stage of the last eses_run, measured
@@ -300,10 +371,12 @@ int eses_root_failures(const eses_ctx *ctx, int64_t *records, int max_records, i
 int eses_patch_counts(const eses_ctx *ctx, int64_t *n_pairs, int64_t *n_free_pairs, int64_t *n_vertices);
 
 /* Copy the patch model to host memory; every output may be NULL and is sized
- * from eses_patch_counts: pair_atoms (2 int32 per pair, original atom
- * indices, first < second in the library's sorted order), pair_free (1 per
- * pair), pair_circle (7 doubles per pair: centre, unit axis from the first
- * to the second atom, radius), vertices (3 doubles per free triple point). */
+ * from eses_patch_counts: pair_atoms (2 int32 per pair, input atom indices,
+ * first < second), pair_free (1 per pair), pair_circle (7 doubles per pair:
+ * centre, unit axis from the first to the second atom, radius), vertices (3
+ * doubles per free triple point).  A circle is always computed from its atom
+ * with the smaller input index, so its bits do not depend on the order in
+ * which the library sorts the atoms. */
 int eses_patch_data(const eses_ctx *ctx, int32_t *pair_atoms, uint8_t *pair_free, double *pair_circle,
                     double *vertices);
 

@@ -68,6 +68,7 @@ def _load():
         lib.eo_result_num_intersections.argtypes = [P, ctypes.c_int]
         lib.eo_result_num_intersections.restype = i64
         lib.eo_result_intersections.argtypes = [P, ctypes.c_int, P, P, P, P]
+        lib.eo_result_intersection_atoms.argtypes = [P, ctypes.c_int, P]
         lib.eo_result_stats.argtypes = [P, P]
         lib.eo_result_free.argtypes = [P]
         lib.eo_distance_points.argtypes = [P, P, i64, d, P, i64, d, ctypes.c_int, P, P, P, P, P]
@@ -78,6 +79,8 @@ def _load():
         lib.eo_model_stats.restype = ctypes.c_int
         lib.eo_num_threads.restype = ctypes.c_int
         lib.eo_run_sparse.argtypes = [P, P, i64, d, d, d, i64, ctypes.c_int, P, i64]
+        lib.eo_run_grid.argtypes = [P, P, P, i64, d, d, P, P, i64, ctypes.c_int]
+        lib.eo_run_grid.restype = P
         lib.eo_run_sparse.restype = ctypes.c_void_p
         lib.eo_result_block_region.argtypes = [ctypes.c_void_p, i64, P, P]
         lib.eo_result_block_region.restype = i64
@@ -136,6 +139,7 @@ class Result:
     tau: list                       # per axis: float64 in [0,1]
     normal: list                    # per axis: float64 (n,3), unit, into the solvent
     ptype: list                     # per axis: int32 patch type of the witness
+    atoms: list                     # per axis: int64 (n,3) input ids of the witness patch's atoms, -1 padded
     area: float
     volume: float                   # inside length along grid lines (mean of 3 axes)
     volume_count: float             # h^3 * number of inside points
@@ -160,29 +164,51 @@ def run(xyz, radii, r_p: float, h: float, margin: float, block_pts: int = 0, nth
                      1 if brute else 0, 0, _ptr(ids) if ids is not None else None, nids)
     if not res:
         raise ValueError("invalid parameters")
+    return _result(lib, res, h, exterior, block_ids is not None)
+
+
+def run_on_grid(xyz, radii, r_p: float, h: float, origin, dims, ids=None, block_pts: int = 0,
+                nthreads: int = 0) -> Result:
+    """Algorithm 1 on a caller-given grid (origin, dims) for atoms carrying
+    the caller's ids (reported as the patch atoms; default 0..n-1)."""
+    lib = _load()
+    xyz, radii = _atoms(xyz, radii)
+    o = np.ascontiguousarray(origin, dtype=np.float64).reshape(3)
+    dm = np.ascontiguousarray(dims, dtype=np.int64).reshape(3)
+    gid = None if ids is None else np.ascontiguousarray(ids, dtype=np.int64).reshape(-1)
+    res = lib.eo_run_grid(_ptr(xyz), _ptr(radii), _ptr(gid) if gid is not None else None, xyz.shape[0], r_p, h,
+                          _ptr(o), _ptr(dm), int(block_pts), int(nthreads))
+    if not res:
+        raise ValueError("invalid parameters")
+    return _result(lib, res, h, False, False)
+
+
+def _result(lib, res, h, exterior, sampled) -> Result:
     try:
-        if exterior and (block_ids is not None or lib.eo_result_exterior(res) < 0):
+        if exterior and (sampled or lib.eo_result_exterior(res) < 0):
             raise ValueError("the exterior-only surface needs the whole grid")
         dims = np.zeros(3, np.int64)
         lo = np.zeros(3, np.float64)
         lib.eo_result_grid(res, _ptr(dims), _ptr(lo))
         labels = np.empty(tuple(int(v) for v in dims), np.int8)
         lib.eo_result_labels(res, _ptr(labels))
-        idx, tau, nrm, pt = [], [], [], []
+        idx, tau, nrm, pt, at = [], [], [], [], []
         for a in range(3):
             ne = int(lib.eo_result_num_intersections(res, a))
             i = np.empty(ne, np.int64)
             t = np.empty(ne, np.float64)
             nn = np.empty((ne, 3), np.float64)
             p = np.empty(ne, np.int32)
+            w = np.empty((ne, 3), np.int64)
             if ne:
                 lib.eo_result_intersections(res, a, _ptr(i), _ptr(t), _ptr(nn), _ptr(p))
-            idx.append(i); tau.append(t); nrm.append(nn); pt.append(p)
+                lib.eo_result_intersection_atoms(res, a, _ptr(w))
+            idx.append(i); tau.append(t); nrm.append(nn); pt.append(p); at.append(w)
         st = np.zeros(16, np.float64)
         lib.eo_result_stats(res, _ptr(st))
     finally:
         lib.eo_result_free(res)
-    return Result(dims=dims, lo=lo, h=h, labels=labels, idx=idx, tau=tau, normal=nrm, ptype=pt,
+    return Result(dims=dims, lo=lo, h=h, labels=labels, idx=idx, tau=tau, normal=nrm, ptype=pt, atoms=at,
                   area=float(st[0]), volume=float(st[1]), volume_count=float(st[2]),
                   near_ties=int(st[3]), slow_edges=int(st[4]), n_points=int(st[11]))
 

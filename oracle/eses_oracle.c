@@ -597,6 +597,7 @@ typedef struct {
     ivec idx[3];
     dvec tau[3], nrm[3];
     ivec ptype[3];
+    ivec wid[3];               /* 3 per edge: the witness' generating atoms (-1 unused) */
     double area, volume_lines, volume_count;
     int64_t near_ties, slow_edges;
     /* instrumentation sums over the owned points / edges */
@@ -688,13 +689,15 @@ typedef struct {
     ivec idx[3];
     dvec tau[3], nrm[3];
     ivec ptype[3];
+    ivec wid[3];               /* 3 per edge: the witness' generating atoms (-1 unused) */
     double area, vol_lines, vol_count;
     int64_t near_ties, slow;
     int64_t sum_reach, sum_face, sum_face_tests, sum_arc, sum_vert, n_shell, n_points;
 } BlockOut;
 
-static void run_block(const double *xyz, const double *r, int64_t n, double rp, double h, const int64_t *dims,
-                      const double *lo, BlockOut *bo, int8_t *labels, int8_t *own_out, int brute, int instrument)
+static void run_block(const double *xyz, const double *r, const int64_t *gid, int64_t n, double rp, double h,
+                      const int64_t *dims, const double *lo, BlockOut *bo, int8_t *labels, int8_t *own_out, int brute,
+                      int instrument)
 {
     const double cap = rp + 2.0 * h; /* enough for the sphere tracing of a crossing edge */
     /* block box in space (computed points) */
@@ -723,6 +726,8 @@ static void run_block(const double *xyz, const double *r, int64_t n, double rp, 
         for (int a = 0; a < 3; ++a) bx[3 * k + a] = xyz[3 * sel[k] + a];
         br[k] = r[sel[k]];
     }
+    if (gid) /* the caller's atom ids (a subset of a larger input) */
+        for (int64_t k = 0; k < cnt; ++k) sel[k] = gid[sel[k]];
     Model m;
     model_build(&m, bx, br, sel, (int)cnt, rp, cap, brute);
 
@@ -787,6 +792,7 @@ static void run_block(const double *xyz, const double *r, int64_t n, double rp, 
                     dpush(&bo->tau[axis], tau);
                     for (int a = 0; a < 3; ++a) dpush(&bo->nrm[axis], nrm[a]);
                     ipush(&bo->ptype[axis], w.type);
+                    for (int q = 0; q < 3; ++q) ipush(&bo->wid[axis], w.type == EO_TYPE_NONE ? -1 : w.ids[q]);
                     /* C9 readings: area by the Crofton-type sum of |n_a|,
                      * volume by the inside length along grid lines */
                     bo->area += h * h * fabs(nrm[axis]);
@@ -809,12 +815,20 @@ static int cmp_i64(const void *a, const void *b)
  * points are left at -1).  nthreads <= 0: OpenMP default. */
 static eo_result *run_impl(const double *xyz, const double *r, int64_t n, double rp, double h, double margin,
                            int64_t block_pts, int nthreads, int brute, int instrument, const int64_t *block_ids,
-                           int64_t n_block_ids, int sparse)
+                           int64_t n_block_ids, int sparse, const int64_t *gid, const double *glo,
+                           const int64_t *gdims)
 {
     if (!(rp > 0.0)) return NULL; /* at r_p = 0 the closed set M is the whole space */
     if (sparse && !block_ids) return NULL;
     eo_result *res = (eo_result *)calloc(1, sizeof(eo_result));
-    if (eo_grid(xyz, r, n, h, margin, res->dims, res->lo) != 0) { free(res); return NULL; }
+    if (glo) { /* the caller's grid */
+        if (!(h > 0.0)) { free(res); return NULL; }
+        for (int a = 0; a < 3; ++a) {
+            if (gdims[a] < 1) { free(res); return NULL; }
+            res->dims[a] = gdims[a];
+            res->lo[a] = glo[a];
+        }
+    } else if (eo_grid(xyz, r, n, h, margin, res->dims, res->lo) != 0) { free(res); return NULL; }
     res->h = h; res->rp = rp;
     res->sparse = sparse;
     const int64_t *dims = res->dims;
@@ -865,7 +879,7 @@ static eo_result *run_impl(const double *xyz, const double *r, int64_t n, double
 #pragma omp parallel for schedule(dynamic, 1)
 #endif
     for (int64_t t = 0; t < nrun; ++t)
-        run_block(xyz, r, n, rp, h, dims, res->lo, &bos[t], res->labels,
+        run_block(xyz, r, gid, n, rp, h, dims, res->lo, &bos[t], res->labels,
                   sparse ? res->labels + res->blk_off[t] : NULL, brute, instrument);
     /* OutputInfo: concatenate in block order, then order edges by lower index */
     for (int64_t t = 0; t < nrun; ++t) {
@@ -876,8 +890,10 @@ static eo_result *run_impl(const double *xyz, const double *r, int64_t n, double
                 dpush(&res->tau[axis], bo->tau[axis].v[e]);
                 for (int a = 0; a < 3; ++a) dpush(&res->nrm[axis], bo->nrm[axis].v[3 * e + a]);
                 ipush(&res->ptype[axis], bo->ptype[axis].v[e]);
+                for (int q = 0; q < 3; ++q) ipush(&res->wid[axis], bo->wid[axis].v[3 * e + q]);
             }
             free(bo->idx[axis].v); free(bo->tau[axis].v); free(bo->nrm[axis].v); free(bo->ptype[axis].v);
+            free(bo->wid[axis].v);
         }
         res->area += bo->area;
         res->volume_lines += bo->vol_lines;
@@ -900,17 +916,21 @@ static eo_result *run_impl(const double *xyz, const double *r, int64_t n, double
         double *nt = (double *)malloc(sizeof(double) * (size_t)ne);
         double *nn = (double *)malloc(sizeof(double) * 3 * (size_t)ne);
         int64_t *np = (int64_t *)malloc(sizeof(int64_t) * (size_t)ne);
+        int64_t *nw = (int64_t *)malloc(sizeof(int64_t) * 3 * (size_t)ne);
         for (int64_t e = 0; e < ne; ++e) {
             int64_t src = key[2 * e + 1];
             ni[e] = res->idx[axis].v[src];
             nt[e] = res->tau[axis].v[src];
             for (int a = 0; a < 3; ++a) nn[3 * e + a] = res->nrm[axis].v[3 * src + a];
             np[e] = res->ptype[axis].v[src];
+            for (int q = 0; q < 3; ++q) nw[3 * e + q] = res->wid[axis].v[3 * src + q];
         }
         free(res->idx[axis].v); free(res->tau[axis].v); free(res->nrm[axis].v); free(res->ptype[axis].v);
+        free(res->wid[axis].v);
         res->idx[axis].v = ni; res->tau[axis].v = nt; res->nrm[axis].v = nn; res->ptype[axis].v = np;
+        res->wid[axis].v = nw;
         res->idx[axis].cap = res->tau[axis].cap = res->ptype[axis].cap = ne;
-        res->nrm[axis].cap = 3 * ne;
+        res->nrm[axis].cap = res->wid[axis].cap = 3 * ne;
         free(key);
     }
     /* C9: V = mean over the three axes of h^2 * (inside length along lines);
@@ -924,7 +944,8 @@ static eo_result *run_impl(const double *xyz, const double *r, int64_t n, double
 eo_result *eo_run(const double *xyz, const double *r, int64_t n, double rp, double h, double margin, int64_t block_pts,
                   int nthreads, int brute, int instrument, const int64_t *block_ids, int64_t n_block_ids)
 {
-    return run_impl(xyz, r, n, rp, h, margin, block_pts, nthreads, brute, instrument, block_ids, n_block_ids, 0);
+    return run_impl(xyz, r, n, rp, h, margin, block_pts, nthreads, brute, instrument, block_ids, n_block_ids, 0, NULL,
+                    NULL, NULL);
 }
 
 /* As eo_run over the listed blocks only, storing only their owned points'
@@ -932,7 +953,18 @@ eo_result *eo_run(const double *xyz, const double *r, int64_t n, double rp, doub
 eo_result *eo_run_sparse(const double *xyz, const double *r, int64_t n, double rp, double h, double margin,
                          int64_t block_pts, int nthreads, const int64_t *block_ids, int64_t n_block_ids)
 {
-    return run_impl(xyz, r, n, rp, h, margin, block_pts, nthreads, 0, 0, block_ids, n_block_ids, 1);
+    return run_impl(xyz, r, n, rp, h, margin, block_pts, nthreads, 0, 0, block_ids, n_block_ids, 1, NULL, NULL, NULL);
+}
+
+/* As eo_run on a grid given by the caller (point (i,j,k) at origin +
+ * h (i,j,k), dims points per axis) instead of the grid of Eq. 2, for atoms
+ * that carry the caller's ids (gid: one per atom, or NULL for 0..n-1): the
+ * oracle of one rank of a molecule split over processes, which holds only
+ * the atoms near its part of the grid. */
+eo_result *eo_run_grid(const double *xyz, const double *r, const int64_t *gid, int64_t n, double rp, double h,
+                       const double origin[3], const int64_t dims[3], int64_t block_pts, int nthreads)
+{
+    return run_impl(xyz, r, n, rp, h, h, block_pts, nthreads, 0, 0, NULL, 0, 0, gid, origin, dims);
 }
 
 /* sparse runs: owned region [lo, hi) of block t and its label count; labels of block t */
@@ -957,6 +989,13 @@ void eo_result_labels(const eo_result *res, int8_t *out)
     memcpy(out, res->labels, (size_t)(res->dims[0] * res->dims[1] * res->dims[2]));
 }
 int64_t eo_result_num_intersections(const eo_result *res, int axis) { return res->idx[axis].n; }
+/* the generating atoms of each intersection's witness patch (§4.1's "nearby
+ * atoms"): 3 input ids per edge -- one for a convex patch, the pair for a
+ * saddle, the triple for a concave patch -- padded with -1 */
+void eo_result_intersection_atoms(const eo_result *res, int axis, int64_t *ids)
+{
+    for (int64_t k = 0; k < res->wid[axis].n; ++k) ids[k] = res->wid[axis].v[k];
+}
 void eo_result_intersections(const eo_result *res, int axis, int64_t *idx, double *tau, double *normal, int32_t *ptype)
 {
     int64_t ne = res->idx[axis].n;
@@ -982,7 +1021,9 @@ void eo_result_free(eo_result *res)
     if (!res) return;
     free(res->labels);
     free(res->blk_lo); free(res->blk_hi); free(res->blk_off);
-    for (int a = 0; a < 3; ++a) { free(res->idx[a].v); free(res->tau[a].v); free(res->nrm[a].v); free(res->ptype[a].v); }
+    for (int a = 0; a < 3; ++a) {
+        free(res->idx[a].v); free(res->tau[a].v); free(res->nrm[a].v); free(res->ptype[a].v); free(res->wid[a].v);
+    }
     free(res);
 }
 
@@ -1054,13 +1095,14 @@ int64_t eo_result_exterior(eo_result *res)
             res->tau[axis].v[keep] = res->tau[axis].v[e];
             for (int a = 0; a < 3; ++a) res->nrm[axis].v[3 * keep + a] = res->nrm[axis].v[3 * e + a];
             res->ptype[axis].v[keep] = res->ptype[axis].v[e];
+            for (int q = 0; q < 3; ++q) res->wid[axis].v[3 * keep + q] = res->wid[axis].v[3 * e + q];
             double tau = res->tau[axis].v[e];
             area += h * h * fabs(res->nrm[axis].v[3 * e + axis]);
             lines += ls ? tau * h : (1.0 - tau) * h;
             ++keep;
         }
         res->idx[axis].n = res->tau[axis].n = res->ptype[axis].n = keep;
-        res->nrm[axis].n = 3 * keep;
+        res->nrm[axis].n = res->wid[axis].n = 3 * keep;
     }
     int64_t inside = 0;
     for (int64_t i = 0; i < dims[0]; ++i)

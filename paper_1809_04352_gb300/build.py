@@ -16,6 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libeses.so")
+PEAKS_LIB = os.path.join(HERE, "libpeaks.so")  # FMA-rate microbenchmark (measurement only, not part of libeses)
 SOURCES = ["eses_api.cu", "eses_scan.cu", "eses_model.cu", "eses_classify.cu", "eses_edges.cu", "eses_noalloc.cu",
            "eses_mlp.cu", "eses_exterior.cu", "eses_mesh.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
@@ -44,10 +45,13 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
-        return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(d) <= t for d in _deps())
+    for lib in (LIB, PEAKS_LIB):
+        if not os.path.exists(lib):
+            return False
+        t = os.path.getmtime(lib)
+        if not all(os.path.getmtime(d) <= t for d in _deps()):
+            return False
+    return True
 
 
 def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False) -> str:
@@ -68,8 +72,18 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
             print(r.stdout + r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    def build_peaks():
+        tmp = PEAKS_LIB + f".tmp{os.getpid()}"
+        cmd = [nvcc] + _flags() + ["-shared", os.path.join(CSRC, "peaks.cu"), "-o", tmp]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for peaks.cu:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, PEAKS_LIB)
+
+    with cf.ThreadPoolExecutor(max_workers=len(SOURCES) + 1) as ex:
+        peaks = ex.submit(build_peaks)
         objs = list(ex.map(compile_one, SOURCES))
+        peaks.result()
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc, ARCH, "-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)

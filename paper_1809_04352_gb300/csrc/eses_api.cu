@@ -30,7 +30,7 @@ using namespace eses;
 static_assert(MLP_NPARAM == ESES_MLP_NPARAM, "proposer parameter count");
 
 // stages timed with CUDA events when ESES_OPT_PROFILE is set
-enum { NSTAT = 15 };
+enum { NSTAT = 16 };
 enum { ST_BIN = 0, ST_PAIRS, ST_ARCS, ST_CLASSIFY, ST_BAND, ST_EDGE_COUNT, ST_EDGE_SOLVE, ST_EDGE_POLISH, ST_REDUCE, NSTAGE };
 
 namespace {
@@ -53,6 +53,10 @@ void ck(cudaError_t e, const char *what)
 struct CaptureGrow {};  // a buffer would have to grow during graph capture
 
 thread_local bool g_capturing = false;
+// allocation-failure injection (ESES_OPT_FAIL_ALLOC): the calling context's
+// countdown while one of its entry points runs; the allocation that brings it
+// to zero fails before cudaMalloc is called
+thread_local long long *g_fail_countdown = nullptr;
 
 template <class T>
 T *ensure(DBuf &b, size_t count)
@@ -64,6 +68,7 @@ T *ensure(DBuf &b, size_t count)
         b.p = nullptr;
         b.cap = 0;
         size_t want = bytes + bytes / 4;
+        if (g_fail_countdown && *g_fail_countdown > 0 && --*g_fail_countdown == 0) throw std::bad_alloc();
         cudaError_t e = cudaMalloc(&b.p, want);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -105,6 +110,7 @@ struct eses_ctx {
     int n_mol = 1;
     long long n_atoms = 0;  // all molecules, coincident repeats dropped
     std::vector<int64_t> kept;  // input index of every atom of the model
+    std::vector<int64_t> in_off;  // first input index of every molecule (n_mol + 1)
     double rp = 0, h = 0, margin = 0;
     double rmax = 0, Rmax = 0;
     std::vector<MolInfo> mol;
@@ -119,13 +125,14 @@ struct eses_ctx {
     DBuf cell_id, cell_count, cell_start, cursor, atom_orig, atom;
     DBuf nb_count, nb_start, nb_list, circle_count, contained, face;
     DBuf pair_count, pair_start, pair_o, pair_u, pair_ij, pair_free;
-    DBuf vert_count, vert_start, vert;
+    DBuf vert_count, vert_start, vert, vert_atoms;
     DBuf pbin_count, pbin_start, pbin_cursor, pbin_cell, pbin_list;
     DBuf vbin_count, vbin_start, vbin_cursor, vbin_cell, vbin_list;
     DBuf labels, tile_band, tile_edges, edge_start, tile_inside;
     DBuf out_idx[3], out_tau[3], out_nrm[3], out_tau32[3], out_nrm32[3], out_code[3];
     DBuf scan_tmp, misc, av, counts, red_d, red_i;  // misc: err, n_fail
     DBuf fail_log;
+    DBuf ovf, big;  // tiles that overflow the shared-memory staging, and the global-memory tier's scratch
     DBuf atom_hi, atom_lo, pair_hi, pair_lo, pair_u32, vert_hi, vert_lo;
     // plan: list sizes of the first run (the inputs never change)
     bool planned = false;
@@ -159,6 +166,18 @@ struct eses_ctx {
     bool graph_on = false;
     cudaGraphExec_t gexec = nullptr;
     int graph_launches = 0;  // kernels in the graph
+    // block selection (eses_set_blocks): blocks [sel_lo, sel_hi) of block_pts points per axis
+    bool sel = false;
+    long long sel_lo[3] = {0, 0, 0}, sel_hi[3] = {0, 0, 0};
+    // grid given by the caller (eses_create_on_grid)
+    bool grid_given = false;
+    double given_lo[3] = {0, 0, 0};
+    long long given_dims[3] = {0, 0, 0};
+    // buried-patch pre-culling (ESES_OPT_CULL)
+    bool cull = true;
+    // failure injection for tests (ESES_OPT_TC_WAIT, ESES_OPT_FAIL_ALLOC)
+    long long tc_wait = -1;      // polls of each tensor-core scoring wait (-1: the default limit)
+    long long fail_alloc = 0;    // countdown to the device allocation that fails (0: none)
     // stage timing (ESES_OPT_PROFILE)
     bool profile = false;
     cudaEvent_t ev[NSTAGE + 1] = {};
@@ -243,6 +262,10 @@ int setup(eses_ctx *c, const double *xyz, const double *r, const int64_t *counts
             }
             I.lo[a] = mn - c->margin;
             I.dims[a] = (long long)ceil((mx + c->margin - I.lo[a]) / c->h) + 1;
+            if (c->grid_given) {  // one molecule on the caller's grid
+                I.lo[a] = c->given_lo[a];
+                I.dims[a] = c->given_dims[a];
+            }
         }
         I.rmax = 0.0;
         for (long long i = 0; i < I.n_atoms; ++i) I.rmax = std::max(I.rmax, R[i]);
@@ -291,6 +314,9 @@ int setup(eses_ctx *c, const double *xyz, const double *r, const int64_t *counts
         for (int a = 0; a < 3; ++a) {
             G.lo[a] = I.lo[a];
             G.dims[a] = I.dims[a];
+            G.own[a] = I.dims[a];
+            G.full[a] = I.dims[a];
+            G.toff[a] = 0;
             G.tiles[a] = (int)ceil_div_ll(I.dims[a], TILE);
         }
         G.h = c->h;
@@ -313,12 +339,12 @@ int setup(eses_ctx *c, const double *xyz, const double *r, const int64_t *counts
     }
     c->n_tiles = c->tile_off[nm];
     c->n_points = lab0;
-    if (c->n_tiles >= (1LL << 31) / 4) return fail(c, ESES_EINVAL, "too many tiles");
     return ESES_OK;
 }
 
 int create_common(const double *hxyz, const double *hr, const int64_t *counts, int n_mol, double rp, double h,
-                  double margin, const double *dxyz, const double *dr, eses_ctx **out)
+                  double margin, const double *dxyz, const double *dr, eses_ctx **out,
+                  const double *grid_lo = nullptr, const int64_t *grid_dims = nullptr)
 {
     if (!out) return fail(nullptr, ESES_EINVAL, "out is NULL");
     *out = nullptr;
@@ -334,6 +360,8 @@ int create_common(const double *hxyz, const double *hr, const int64_t *counts, i
     // Coincident atoms (the same centre and radius, within one molecule) are
     // one ball: the union of balls (§1) does not change without the repeats,
     // and keeping them would let each sphere "cover" the other's surface.
+    std::vector<int64_t> in_off((size_t)n_mol + 1, 0);  // first input index of every molecule
+    for (int m = 0; m < n_mol; ++m) in_off[(size_t)m + 1] = in_off[(size_t)m] + counts[m];
     std::vector<int64_t> kept;  // input index of every atom the model uses
     std::vector<int64_t> kcounts(counts, counts + n_mol);
     {
@@ -386,11 +414,19 @@ int create_common(const double *hxyz, const double *hr, const int64_t *counts, i
     eses_ctx *c = new (std::nothrow) eses_ctx();
     if (!c) return fail(nullptr, ESES_ENOMEM, "host allocation failed");
     c->kept = std::move(kept);
+    c->in_off = std::move(in_off);
     c->n_atoms = total;
     c->n_mol = n_mol;
     c->rp = rp;
     c->h = h;
     c->margin = margin;
+    if (grid_lo) {
+        c->grid_given = true;
+        for (int a = 0; a < 3; ++a) {
+            c->given_lo[a] = grid_lo[a];
+            c->given_dims[a] = grid_dims[a];
+        }
+    }
     try {
         ck(cudaGetDevice(&c->device), "cudaGetDevice");
         ck(cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device), "device attribute");
@@ -570,7 +606,8 @@ int run_device(eses_ctx *c)
     M.n_verts = nv;
     double4 *vert = ensure<double4>(c->vert, std::max(nv, 1));
     int *vert_mol = ensure<int>(c->vert_mol, std::max(nv, 1));
-    nl += launch_arcs_emit(M, vert_start, vert, vert_mol, st);
+    int4 *vert_atoms = ensure<int4>(c->vert_atoms, std::max(nv, 1));
+    nl += launch_arcs_emit(M, vert_start, vert, vert_mol, vert_atoms, st);
     M.vert = vert;
     M.vert_mol = vert_mol;
 
@@ -579,6 +616,7 @@ int run_device(eses_ctx *c)
     // 5. free faces
     uint8_t *face = ensure<uint8_t>(c->face, n);
     nl += launch_faces(M, circle_count, contained, face, st);
+    if (!c->cull) ck(cudaMemsetAsync(face, 1, n, st), "memset");  // every face a witness carrier
     M.atom_face = face;
 
     // 6. patch bins
@@ -589,7 +627,7 @@ int run_device(eses_ctx *c)
     int *plist = ensure<int>(c->pbin_list, std::max(np, 1));
     ck(cudaMemsetAsync(pcnt, 0, sizeof(int) * ncell, st), "memset");
     ck(cudaMemsetAsync(pcur, 0, sizeof(int) * ncell, st), "memset");
-    nl += launch_bin_count(M, 0, pcnt, pcell, st);
+    nl += launch_bin_count(M, 0, c->cull, pcnt, pcell, st);
     nl += scan(c, pcnt, pstart, ncell);
     nl += launch_bin_scatter(M, 0, pcell, pstart, pcur, plist, st);
     int *vcnt = ensure<int>(c->vbin_count, ncell);
@@ -599,7 +637,7 @@ int run_device(eses_ctx *c)
     int *vlist = ensure<int>(c->vbin_list, std::max(nv, 1));
     ck(cudaMemsetAsync(vcnt, 0, sizeof(int) * ncell, st), "memset");
     ck(cudaMemsetAsync(vcur, 0, sizeof(int) * ncell, st), "memset");
-    nl += launch_bin_count(M, 1, vcnt, vcell, st);
+    nl += launch_bin_count(M, 1, true, vcnt, vcell, st);
     nl += scan(c, vcnt, vstart, ncell);
     nl += launch_bin_scatter(M, 1, vcell, vstart, vcur, vlist, st);
     M.pcell_start = pstart;
@@ -625,16 +663,20 @@ int run_device(eses_ctx *c)
         int *pos = ensure<int>(c->need_pos, nt + 1);
         int *list = ensure<int>(c->tile_list, nt);
         nl += launch_propose(M, B, c->proposer, (const float *)c->mlp_params.p, c->z_far, labels,
-                             c->precision == ESES_PREC_FP64 ? nullptr : tile_band, need, prop_counts, d_err, st);
+                             c->precision == ESES_PREC_FP64 ? nullptr : tile_band, need, prop_counts, d_err,
+                             c->tc_wait, st);
         nl += scan(c, need, pos, nt);
         nl += launch_compact(nt, need, pos, list, st);
         cq.list = list;
         cq.list_n = pos + nt;
     }
+    int *ovf = ensure<int>(c->ovf, (size_t)nt + 2);
+    ck(cudaMemsetAsync(ovf, 0, sizeof(int), st), "memset");
+    unsigned char *big = ensure<unsigned char>(c->big, std::max(classify_big_bytes(), edges_big_bytes()));
     nl += launch_classify(M, B, c->precision, cq, grid_of(c, c->cls, classify_ctas_per_sm(c->precision)), labels,
-                          c->precision == ESES_PREC_FP64 ? nullptr : tile_band, d_err, st);
+                          c->precision == ESES_PREC_FP64 ? nullptr : tile_band, d_err, ovf, big, st);
     mark(c, ST_BAND);
-    if (c->precision != ESES_PREC_FP64) nl += launch_band(M, B, labels, tile_band, d_err, st);
+    if (c->precision != ESES_PREC_FP64) nl += launch_band(M, B, labels, tile_band, d_err, ovf, big, st);
     c->n_cavity = 0;
     c->ext_sweeps = 0;
     if (c->exterior) {  // cavities filled: sweeps until one reaches nothing new (never under capture)
@@ -697,7 +739,7 @@ int run_device(eses_ctx *c)
     const int chunk = c->edge.chunk > 0 ? c->edge.chunk : edge_chunk_max();
     nl += launch_edge_solve(M, B, c->precision, sched_of(c, c->edge, 1),
                             grid_of(c, c->edge, edge_ctas_per_sm(c->precision)), chunk, labels, edge_start, eo, d_fail,
-                            d_err, fail_log, st);
+                            d_err, fail_log, ovf, big, st);
     mark(c, ST_EDGE_POLISH);
     nl += launch_edge_polish(M, B, eo, ne_all, medge, term, st);
     mark(c, ST_REDUCE);
@@ -721,6 +763,8 @@ int finish(eses_ctx *c, int nl)
     ck(cudaMemcpyAsync(hmisc, c->misc.p, sizeof(hmisc), cudaMemcpyDeviceToHost, st), "read results");
     int hprop[4] = {0, 0, 0, 0};
     ck(cudaMemcpyAsync(hprop, c->prop_counts.p, sizeof(hprop), cudaMemcpyDeviceToHost, st), "read results");
+    int hovf = 0;  // tiles the global-memory staging tier took
+    ck(cudaMemcpyAsync(&hovf, c->ovf.p, sizeof(int), cudaMemcpyDeviceToHost, st), "read results");
     ck(cudaMemcpyAsync(c->medge_h.data(), c->medge.p, sizeof(long long) * c->medge_h.size(), cudaMemcpyDeviceToHost, st),
        "read results");
     ck(cudaMemcpyAsync(c->av_h.data(), c->av.p, sizeof(double) * c->av_h.size(), cudaMemcpyDeviceToHost, st),
@@ -732,7 +776,7 @@ int finish(eses_ctx *c, int nl)
         for (int k = 0; k < NSTAGE; ++k) ck(cudaEventElapsedTime(&c->stage_ms[k], c->ev[k], c->ev[k + 1]), "elapsed");
     long long inside = 0;
     for (int m = 0; m < nm; ++m) inside += c->cnt_h[2 * m];
-    c->stats[0] = c->n_points;
+    c->stats[0] = c->sel ? c->grids[0].own[0] * c->grids[0].own[1] * c->grids[0].own[2] : c->n_points;
     c->stats[1] = c->n_tiles;
     c->stats[2] = 0;
     c->stats[3] = c->n_pairs;
@@ -747,6 +791,7 @@ int finish(eses_ctx *c, int nl)
     c->stats[12] = hprop[1];
     c->stats[13] = c->n_cavity;
     c->stats[14] = c->ext_sweeps;
+    c->stats[15] = hovf;
     c->ran = true;
     int derr = hmisc[0];
     if (derr & (ERR_CAP_ATOMS | ERR_CAP_PAIRS | ERR_CAP_VERTS | ERR_CAP_CAND)) {
@@ -798,16 +843,76 @@ int run_impl(eses_ctx *c)
     return finish(c, c->graph_launches);
 }
 
+// The box that the next runs of a one-molecule context compute: the whole
+// grid, or the tiles of a block selection plus one tile layer in + directions
+// (the neighbours of the owned points' edges), clipped to the grid.  Sets the
+// grid, the tile layout and their device copies; the next run plans again.
+void apply_box(eses_ctx *c)
+{
+    Grid &G = c->grids[0];
+    const MolInfo &I = c->mol[0];
+    long long nt = 1, np = 1;
+    for (int a = 0; a < 3; ++a) {
+        const long long full = I.dims[a], ftiles = ceil_div_ll(full, TILE);
+        G.full[a] = full;
+        if (!c->sel) {
+            G.toff[a] = 0;
+            G.dims[a] = G.own[a] = full;
+            G.tiles[a] = (int)ftiles;
+        } else {
+            const long long B = c->block_pts;
+            const long long lo = c->sel_lo[a] * B, hi = std::min(c->sel_hi[a] * B, full);
+            const long long tend = std::min(ceil_div_ll(hi, TILE) + 1, ftiles);
+            G.toff[a] = (int)(lo / TILE);
+            G.tiles[a] = (int)(tend - lo / TILE);
+            G.dims[a] = std::min(tend * TILE, full) - lo;
+            G.own[a] = hi - lo;
+        }
+        nt *= G.tiles[a];
+        np *= G.dims[a];
+    }
+    G.n_tiles = nt;
+    G.tile0 = 0;
+    G.lab0 = 0;
+    c->tile_off.assign(2, 0);
+    c->tile_off[1] = nt;
+    c->n_tiles = nt;
+    c->n_points = np;
+    c->B.n_tiles = nt;
+    ck(cudaMemcpyAsync(c->grid_d.p, &G, sizeof(Grid), cudaMemcpyHostToDevice, c->stream), "copy grid");
+    ck(cudaMemcpyAsync(c->tile_off_d.p, c->tile_off.data(), 2 * sizeof(long long), cudaMemcpyHostToDevice, c->stream),
+       "copy tile offsets");
+    ck(cudaStreamSynchronize(c->stream), "synchronize");
+    drop_graph(c);
+    c->planned = false;
+    c->ran = false;
+}
+
+// points the allocation-failure countdown at the context for one entry point
+struct AllocScope {
+    explicit AllocScope(eses_ctx *c) { g_fail_countdown = &c->fail_alloc; }
+    ~AllocScope() { g_fail_countdown = nullptr; }
+};
+
 int run_guarded(eses_ctx *c)
 {
     c->ran = false;
     c->n_tri = -1;
+    if (c->sel && c->exterior)
+        return fail(c, ESES_EINVAL, "the exterior-only surface needs the whole grid (no block selection)");
+    // per-tile arrays are indexed in 32 bits (4 ints per tile): a larger grid runs in block selections
+    if (c->n_tiles >= (1LL << 31) / 4)
+        return fail(c, ESES_EINVAL, "too many tiles in one run: select blocks (eses_set_blocks)");
+    AllocScope scope(c);
     try {
         ck(cudaSetDevice(c->device), "cudaSetDevice");
         return run_impl(c);
     } catch (const CudaError &e) {
         return fail(c, ESES_ECUDA, std::string(e.what) + ": " + cudaGetErrorString(e.e));
     } catch (const std::bad_alloc &) {
+        // buffers may be half sized: the next run plans again
+        drop_graph(c);
+        c->planned = false;
         return fail(c, ESES_ENOMEM, "device allocation failed");
     } catch (const CaptureGrow &) {
         // a buffer the plan did not size: plan again (eagerly), capture next time
@@ -851,6 +956,20 @@ int eses_create(const double *xyz, const double *radii, int64_t n_atoms, double 
     if (!xyz || !radii) return fail(nullptr, ESES_EINVAL, "xyz or radii is NULL");
     if (n_atoms < 1 || n_atoms > (int64_t)1 << 30) return fail(nullptr, ESES_EINVAL, "n_atoms must be in [1, 2^30]");
     return create_common(xyz, radii, &n_atoms, 1, r_p, h, margin, nullptr, nullptr, out);
+}
+
+int eses_create_on_grid(const double *xyz, const double *radii, int64_t n_atoms, double r_p, double h,
+                        const double origin[3], const int64_t dims[3], eses_ctx **out)
+{
+    if (!xyz || !radii || !origin || !dims) return fail(nullptr, ESES_EINVAL, "NULL argument");
+    if (n_atoms < 1 || n_atoms > (int64_t)1 << 30) return fail(nullptr, ESES_EINVAL, "n_atoms must be in [1, 2^30]");
+    for (int a = 0; a < 3; ++a) {
+        if (!isfinite(origin[a])) return fail(nullptr, ESES_EINVAL, "origin must be finite");
+        if (dims[a] < 1 || dims[a] > (1LL << 30)) return fail(nullptr, ESES_EINVAL, "dims must be in [1, 2^30]");
+    }
+    if (dims[0] * dims[1] * dims[2] > (1LL << 40)) return fail(nullptr, ESES_EINVAL, "grid too large");
+    // margin = h passes the argument check; the caller's grid replaces the one it would give
+    return create_common(xyz, radii, &n_atoms, 1, r_p, h, h, nullptr, nullptr, out, origin, dims);
 }
 
 int eses_create_device(const double *xyz, const double *radii, int64_t n_atoms, double r_p, double h, double margin,
@@ -905,7 +1024,16 @@ int eses_set_option(eses_ctx *c, int key, int64_t value)
     if (!c) return fail(nullptr, ESES_EINVAL, "ctx is NULL");
     switch (key) {
     case ESES_OPT_BLOCK_PTS:
-        if (value < 9 || value > (1 << 20)) return fail(c, ESES_EINVAL, "block points must be in [9, 2^20]");
+        if (value < TILE || value > (1 << 20) || value % TILE)
+            return fail(c, ESES_EINVAL, "block points must be a multiple of 8 in [8, 2^20]");
+        if (value != c->block_pts && c->sel) {  // the selection was in blocks of the old size: whole grid again
+            c->sel = false;
+            try {
+                apply_box(c);
+            } catch (const CudaError &e) {
+                return fail(c, ESES_ECUDA, std::string(e.what) + ": " + cudaGetErrorString(e.e));
+            }
+        }
         c->block_pts = (int)value;
         return ESES_OK;
     case ESES_OPT_PRECISION:
@@ -949,8 +1077,26 @@ int eses_set_option(eses_ctx *c, int key, int64_t value)
         drop_graph(c);
         c->edge.chunk = (int)value;
         return ESES_OK;
+    case ESES_OPT_CULL:
+        if (value != 0 && value != 1) return fail(c, ESES_EINVAL, "cull must be 0 or 1");
+        if ((value != 0) != c->cull) {  // other staging lists: plan again
+            drop_graph(c);
+            c->planned = false;
+        }
+        c->cull = value != 0;
+        return ESES_OK;
+    case ESES_OPT_TC_WAIT:
+        if (value < -1) return fail(c, ESES_EINVAL, "wait limit must be >= -1");
+        drop_graph(c);
+        c->tc_wait = value;
+        return ESES_OK;
+    case ESES_OPT_FAIL_ALLOC:
+        if (value < 0) return fail(c, ESES_EINVAL, "allocation countdown must be >= 0");
+        c->fail_alloc = value;
+        return ESES_OK;
     case ESES_OPT_EXTERIOR:
         if (value != 0 && value != 1) return fail(c, ESES_EINVAL, "exterior must be 0 or 1");
+        if (value && c->sel) return fail(c, ESES_EINVAL, "the exterior-only surface needs the whole grid");
         if ((value != 0) != c->exterior) {  // other list sizes: plan again (buffers may move)
             drop_graph(c);
             c->planned = false;
@@ -972,6 +1118,9 @@ int eses_get_option(const eses_ctx *cc, int key, int64_t *value)
     case ESES_OPT_STREAM: *value = (int64_t)(intptr_t)c->stream; return ESES_OK;
     case ESES_OPT_SYNC: *value = c->sync ? 1 : 0; return ESES_OK;
     case ESES_OPT_PROFILE: *value = c->profile ? 1 : 0; return ESES_OK;
+    case ESES_OPT_TC_WAIT: *value = c->tc_wait; return ESES_OK;
+    case ESES_OPT_CULL: *value = c->cull ? 1 : 0; return ESES_OK;
+    case ESES_OPT_FAIL_ALLOC: *value = c->fail_alloc; return ESES_OK;
     case ESES_OPT_GRAPH: *value = c->graph_on ? 1 : 0; return ESES_OK;
     case ESES_OPT_QUEUE: *value = c->use_queue ? 1 : 0; return ESES_OK;
     case ESES_OPT_CLS_CTAS: *value = c->cls.ctas_per_sm; return ESES_OK;
@@ -1002,6 +1151,7 @@ int eses_autotune(eses_ctx *c, int reps, double *ms_out)
         c->graph_on = graph;
         return rc;
     }
+    AllocScope scope(c);
     try {
         cudaStream_t st = c->stream;
         cudaEvent_t e0, e1;
@@ -1034,11 +1184,13 @@ int eses_autotune(eses_ctx *c, int reps, double *ms_out)
                 float ms = time_it([&] {
                     ck(cudaMemsetAsync(c->queue.p, 0, 4 * sizeof(unsigned long long), st), "memset");
                     launch_classify(M, B, c->precision, sched_of(c, s, 0), grid_of(c, s, cls_max), labels,
-                                    c->precision == ESES_PREC_FP64 ? nullptr : tile_band, misc, st);
+                                    c->precision == ESES_PREC_FP64 ? nullptr : tile_band, misc, (int *)c->ovf.p,
+                                    (unsigned char *)c->big.p, st);
                 });
                 if (ms < best_cls_ms) best_cls_ms = ms, best_cls = s;
             }
-        if (c->precision != ESES_PREC_FP64) launch_band(M, B, labels, tile_band, misc, st);
+        if (c->precision != ESES_PREC_FP64)
+            launch_band(M, B, labels, tile_band, misc, (int *)c->ovf.p, (unsigned char *)c->big.p, st);
         // root solve: CTAs per SM x tiles per pop x chunk
         Shape best_edge = c->edge;
         float best_edge_ms = INFINITY;
@@ -1062,7 +1214,7 @@ int eses_autotune(eses_ctx *c, int reps, double *ms_out)
                         ck(cudaMemsetAsync(c->queue.p, 0, 4 * sizeof(unsigned long long), st), "memset");
                         launch_edge_solve(M, B, c->precision, sched_of(c, s, 1), grid_of(c, s, edge_max), chunk,
                                           labels, (const int *)c->edge_start.p, eo, misc + 1, misc,
-                                          (long long *)c->fail_log.p, st);
+                                          (long long *)c->fail_log.p, (int *)c->ovf.p, (unsigned char *)c->big.p, st);
                     });
                     if (ms < best_edge_ms) best_edge_ms = ms, best_edge = s;
                 }
@@ -1092,6 +1244,7 @@ int eses_set_proposer(eses_ctx *c, int mode, const float *params, double p_far)
         if (!(p_far > 0.0 && p_far < 1.0)) return fail(c, ESES_EINVAL, "p_far must be in (0, 1)");
         if (!params && !c->have_params) return fail(c, ESES_EINVAL, "the MLP proposer needs parameters");
     }
+    AllocScope scope(c);
     try {
         if (params) {
             for (int k = 0; k < MLP_NPARAM; ++k)
@@ -1158,11 +1311,19 @@ int eses_mol_labels(const eses_ctx *cc, int m, int8_t *out)
     eses_ctx *c = const_cast<eses_ctx *>(cc);
     if (!mol_ok(c, m) || !out) return fail(c, ESES_EINVAL, "bad argument");
     if (!c->ran) return fail(c, ESES_ESTATE, "no results: call eses_run first");
-    const size_t n = (size_t)mol_points(c, m);
-    if (cudaMemcpyAsync(out, (const int8_t *)c->labels.p + c->grids[m].lab0, n, cudaMemcpyDeviceToHost, c->stream) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(c->stream) != cudaSuccess)
-        return fail(c, ESES_ECUDA, "label copy failed");
+    const Grid &G = c->grids[m];
+    const int8_t *src = (const int8_t *)c->labels.p + G.lab0;
+    bool ok = true;
+    if (!c->sel) {
+        const size_t n = (size_t)mol_points(c, m);
+        ok = cudaMemcpyAsync(out, src, n, cudaMemcpyDeviceToHost, c->stream) == cudaSuccess;
+    } else {  // the owned box out of the computed box, one plane at a time
+        for (long long i = 0; i < G.own[0] && ok; ++i)
+            ok = cudaMemcpy2DAsync(out + i * G.own[1] * G.own[2], (size_t)G.own[2], src + i * G.dims[1] * G.dims[2],
+                                   (size_t)G.dims[2], (size_t)G.own[2], (size_t)G.own[1], cudaMemcpyDeviceToHost,
+                                   c->stream) == cudaSuccess;
+    }
+    if (!ok || cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(c, ESES_ECUDA, "label copy failed");
     return ESES_OK;
 }
 
@@ -1171,6 +1332,7 @@ int eses_mol_labels_device(const eses_ctx *cc, int m, const int8_t **dptr)
     eses_ctx *c = const_cast<eses_ctx *>(cc);
     if (!mol_ok(c, m) || !dptr) return fail(c, ESES_EINVAL, "bad argument");
     if (!c->ran) return fail(c, ESES_ESTATE, "no results: call eses_run first");
+    if (c->sel) return fail(c, ESES_ESTATE, "a block selection's labels are read with eses_labels");
     *dptr = (const int8_t *)c->labels.p + c->grids[m].lab0;
     return ESES_OK;
 }
@@ -1234,6 +1396,53 @@ int eses_mol_intersections_device(const eses_ctx *cc, int m, int axis, const int
     return ESES_OK;
 }
 
+int eses_mol_intersection_patches(const eses_ctx *cc, int m, int axis, int8_t *kind, int32_t *atoms)
+{
+    eses_ctx *c = const_cast<eses_ctx *>(cc);
+    if (!mol_ok(c, m) || axis < 0 || axis > 2) return fail(c, ESES_EINVAL, "bad argument");
+    if (!c->ran) return fail(c, ESES_ESTATE, "no results: call eses_run first");
+    long long off, n;
+    mol_range(c, m, axis, off, n);
+    if (n == 0) return ESES_OK;
+    if (!kind && !atoms) return ESES_OK;
+    const int na = c->M.n_atoms, np = c->M.n_pairs, nv = c->M.n_verts;
+    std::vector<int2> code((size_t)n);
+    std::vector<int> orig((size_t)na);
+    std::vector<int2> ij((size_t)std::max(np, 1));
+    std::vector<int4> va((size_t)std::max(nv, 1));
+    bool ok = cudaMemcpy(code.data(), (const int2 *)c->out_code[axis].p + off, sizeof(int2) * (size_t)n,
+                         cudaMemcpyDeviceToHost) == cudaSuccess;
+    ok &= cudaMemcpy(orig.data(), c->atom_orig.p, sizeof(int) * (size_t)na, cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (np > 0) ok &= cudaMemcpy(ij.data(), c->pair_ij.p, sizeof(int2) * np, cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (nv > 0) ok &= cudaMemcpy(va.data(), c->vert_atoms.p, sizeof(int4) * nv, cudaMemcpyDeviceToHost) == cudaSuccess;
+    if (!ok) return fail(c, ESES_ECUDA, "patch id copy failed");
+    const int64_t base = c->in_off[(size_t)m];
+    auto input_id = [&](int sorted) { return (int32_t)(c->kept[(size_t)orig[(size_t)sorted]] - base); };
+    for (long long e = 0; e < n; ++e) {
+        const int y = code[(size_t)e].y;
+        const int k = (y >> 29) & 3, failed = (y >> 27) & 1, mid = y & ((1 << 27) - 1);
+        int32_t id[3] = {-1, -1, -1};
+        int nid = 0;
+        if (!failed) {
+            if (k == 0) {
+                id[nid++] = input_id(mid);
+            } else if (k == 1) {
+                id[nid++] = input_id(ij[(size_t)mid].x);
+                id[nid++] = input_id(ij[(size_t)mid].y);
+            } else {
+                id[nid++] = input_id(va[(size_t)mid].x);
+                id[nid++] = input_id(va[(size_t)mid].y);
+                id[nid++] = input_id(va[(size_t)mid].z);
+            }
+            std::sort(id, id + nid);
+        }
+        if (kind) kind[e] = failed ? (int8_t)-1 : (int8_t)k;
+        if (atoms)
+            for (int q = 0; q < 3; ++q) atoms[3 * e + q] = id[q];
+    }
+    return ESES_OK;
+}
+
 int eses_mol_area_volume(const eses_ctx *cc, int m, double *area, double *volume)
 {
     eses_ctx *c = const_cast<eses_ctx *>(cc);
@@ -1241,6 +1450,55 @@ int eses_mol_area_volume(const eses_ctx *cc, int m, double *area, double *volume
     if (!c->ran) return fail(c, ESES_ESTATE, "no results: call eses_run first");
     *area = c->av_h[2 * m];
     *volume = c->av_h[2 * m + 1];
+    return ESES_OK;
+}
+
+int eses_num_blocks(const eses_ctx *cc, int64_t nblocks[3])
+{
+    eses_ctx *c = const_cast<eses_ctx *>(cc);
+    if (!c || !nblocks) return fail(c, ESES_EINVAL, "NULL argument");
+    if (int rc = single(c)) return rc;
+    for (int a = 0; a < 3; ++a) nblocks[a] = ceil_div_ll(c->mol[0].dims[a], c->block_pts);
+    return ESES_OK;
+}
+
+int eses_set_blocks(eses_ctx *c, const int64_t block_lo[3], const int64_t block_hi[3])
+{
+    if (!c) return fail(nullptr, ESES_EINVAL, "ctx is NULL");
+    if (int rc = single(c)) return rc;
+    if ((block_lo == nullptr) != (block_hi == nullptr)) return fail(c, ESES_EINVAL, "give both block bounds or neither");
+    if (block_lo) {
+        if (c->exterior) return fail(c, ESES_EINVAL, "the exterior-only surface needs the whole grid");
+        for (int a = 0; a < 3; ++a) {
+            const long long nb = ceil_div_ll(c->mol[0].dims[a], c->block_pts);
+            if (block_lo[a] < 0 || block_hi[a] <= block_lo[a] || block_hi[a] > nb)
+                return fail(c, ESES_EINVAL, "block range must satisfy 0 <= lo < hi <= eses_num_blocks");
+        }
+    }
+    c->sel = block_lo != nullptr;
+    for (int a = 0; a < 3; ++a) {
+        c->sel_lo[a] = c->sel ? block_lo[a] : 0;
+        c->sel_hi[a] = c->sel ? block_hi[a] : 0;
+    }
+    try {
+        ck(cudaSetDevice(c->device), "cudaSetDevice");
+        apply_box(c);
+    } catch (const CudaError &e) {
+        return fail(c, ESES_ECUDA, std::string(e.what) + ": " + cudaGetErrorString(e.e));
+    }
+    return ESES_OK;
+}
+
+int eses_owned_box(const eses_ctx *cc, int64_t lo[3], int64_t dims[3])
+{
+    eses_ctx *c = const_cast<eses_ctx *>(cc);
+    if (!c || !lo || !dims) return fail(c, ESES_EINVAL, "NULL argument");
+    if (int rc = single(c)) return rc;
+    const Grid &G = c->grids[0];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = (int64_t)TILE * G.toff[a];
+        dims[a] = G.own[a];
+    }
     return ESES_OK;
 }
 
@@ -1292,6 +1550,14 @@ int eses_intersections_device(const eses_ctx *cc, int axis, const int64_t **lowe
     if (!c || axis < 0 || axis > 2) return fail(c, ESES_EINVAL, "bad argument");
     if (int rc = single(c)) return rc;
     return eses_mol_intersections_device(c, 0, axis, lower_idx, tau, normal, tau32, normal32);
+}
+
+int eses_intersection_patches(const eses_ctx *cc, int axis, int8_t *kind, int32_t *atoms)
+{
+    eses_ctx *c = const_cast<eses_ctx *>(cc);
+    if (!c) return fail(c, ESES_EINVAL, "NULL argument");
+    if (int rc = single(c)) return rc;
+    return eses_mol_intersection_patches(c, 0, axis, kind, atoms);
 }
 
 int eses_area_volume(const eses_ctx *cc, double *area, double *volume)
@@ -1363,8 +1629,9 @@ int eses_patch_data(const eses_ctx *cc, int32_t *pair_atoms, uint8_t *pair_free,
     if (!ok) return fail(c, ESES_ECUDA, "patch copy failed");
     for (int p = 0; p < np; ++p) {
         if (pair_atoms) {
-            pair_atoms[2 * p] = (int32_t)c->kept[(size_t)orig[ij[p].x]];
-            pair_atoms[2 * p + 1] = (int32_t)c->kept[(size_t)orig[ij[p].y]];
+            const int32_t a = (int32_t)c->kept[(size_t)orig[ij[p].x]], b = (int32_t)c->kept[(size_t)orig[ij[p].y]];
+            pair_atoms[2 * p] = std::min(a, b);  // the circle's axis points from this atom to the other
+            pair_atoms[2 * p + 1] = std::max(a, b);
         }
         if (pair_circle) {
             double *o = pair_circle + 7 * p;
@@ -1387,6 +1654,8 @@ int eses_mesh_count(eses_ctx *c, int64_t *n_tri)
     if (!c || !n_tri) return fail(c, ESES_EINVAL, "NULL argument");
     if (int rc = single(c)) return rc;
     if (!c->ran) return fail(c, ESES_ESTATE, "no results: call eses_run first");
+    if (c->sel) return fail(c, ESES_ESTATE, "the mesh needs the whole grid (no block selection)");
+    AllocScope scope(c);
     try {
         ck(cudaSetDevice(c->device), "cudaSetDevice");
         if (c->n_tri < 0) {
@@ -1512,10 +1781,10 @@ void eses_destroy(eses_ctx *c)
                     &c->medge, &c->term, &c->queue, &c->cell_id, &c->cell_count, &c->cell_start, &c->cursor,
                     &c->atom_orig, &c->atom, &c->nb_count, &c->nb_start, &c->nb_list, &c->circle_count,
                     &c->contained, &c->face, &c->pair_count, &c->pair_start, &c->pair_o, &c->pair_u, &c->pair_ij,
-                    &c->pair_free, &c->vert_count, &c->vert_start, &c->vert, &c->pbin_count, &c->pbin_start,
+                    &c->pair_free, &c->vert_count, &c->vert_start, &c->vert, &c->vert_atoms, &c->pbin_count, &c->pbin_start,
                     &c->pbin_cursor, &c->pbin_cell, &c->pbin_list, &c->vbin_count, &c->vbin_start, &c->vbin_cursor,
                     &c->vbin_cell, &c->vbin_list, &c->labels, &c->tile_band, &c->tile_edges, &c->edge_start,
-                    &c->tile_inside, &c->scan_tmp, &c->misc, &c->av, &c->counts, &c->red_d, &c->red_i, &c->fail_log, &c->atom_hi,
+                    &c->tile_inside, &c->scan_tmp, &c->misc, &c->av, &c->counts, &c->red_d, &c->red_i, &c->fail_log, &c->ovf, &c->big, &c->atom_hi,
                     &c->atom_lo, &c->pair_hi, &c->pair_lo, &c->pair_u32, &c->vert_hi, &c->vert_lo,
                     &c->mlp_params, &c->need, &c->need_pos, &c->tile_list, &c->prop_counts, &c->features,
                     &c->targets, &c->ext, &c->ext_open, &c->ext_misc, &c->mesh_mask, &c->mesh_tile, &c->mesh_off,

@@ -29,21 +29,32 @@ namespace eses {
 
 constexpr int CLS_THREADS = 256;
 constexpr int NBRICK = 16;     // 2x4x4-point bricks per tile
-constexpr int INC_MAX = 2 * P_MAX;
 
+template <class CP>
 struct ClsSmem {
-    int hkey[SLOT_HASH];           // staged-atom lookup (pair_slots)
-    short hval[SLOT_HASH];
-    short2 pslot[P_MAX];           // staged slots of each pair's atoms (-1: not staged)
-    int inc_start[A_MAX + 1];      // incident pairs per staged atom (CSR)
-    int inc_fill[A_MAX];
-    short inc[INC_MAX];
-    unsigned bmask[NBRICK][AW];    // per-brick sets of the atoms whose expanded ball reaches the brick
-    unsigned nbm[A_MAX * AW];      // neighbour set of every staged atom (build_neighbour_sets)
+    static constexpr int HS = slot_hash_size<CP>(), AWC = atom_words<CP>();
+    int hkey[HS];                  // staged-atom lookup (pair_slots)
+    short hval[HS];
+    short2 pslot[CP::P];           // staged slots of each pair's atoms (-1: not staged)
+    int inc_start[CP::A + 1];      // incident pairs per staged atom (CSR)
+    int inc_fill[CP::A];
+    short inc[2 * CP::P];
+    unsigned bmask[NBRICK][AWC];   // per-brick sets of the atoms whose expanded ball reaches the brick
+    unsigned nbm[CP::A * AWC];     // neighbour set of every staged atom (build_neighbour_sets)
     int bcount[NBRICK];
     short queue[TILE_PTS];         // shell points
     int nq, band;
 };
+
+// a tile that overflowed the shared-memory staging goes to the list of the
+// global-memory tier: ovf[0] counts such tiles over the run, ovf[1] is the
+// stage's list length, ovf[2..] the global tiles
+__device__ __forceinline__ void ovf_push(int *ovf, long long gt)
+{
+    atomicAdd(&ovf[0], 1);
+    const int k = atomicAdd(&ovf[1], 1);
+    ovf[2 + k] = (int)gt;
+}
 
 __device__ __forceinline__ void brick_point(int brick, int lane, int &li, int &lj, int &lk)
 {
@@ -62,10 +73,11 @@ __device__ __forceinline__ T pt_coord(const Grid &G, int k)
 }
 
 // per-atom incident pair lists (whole block)
-template <class T>
-__device__ void build_incidence(const TileS<T> &S, ClsSmem &C)
+template <class T, class CP>
+__device__ void build_incidence(const TileS<T, CP> &S, ClsSmem<CP> &C)
 {
-    for (int a = threadIdx.x; a < A_MAX + 1; a += blockDim.x) C.inc_start[a] = 0;
+    constexpr int A_CAP = CP::A;
+    for (int a = threadIdx.x; a < A_CAP + 1; a += blockDim.x) C.inc_start[a] = 0;
     pair_slots<T>(S, C.hkey, C.hval, C.pslot);
     for (int p = threadIdx.x; p < S.np; p += blockDim.x) {
         const short2 sl = C.pslot[p];
@@ -75,13 +87,13 @@ __device__ void build_incidence(const TileS<T> &S, ClsSmem &C)
         }
     }
     __syncthreads();
-    if (threadIdx.x < 32) {  // inclusive scan of inc_start[1..A_MAX] by one warp
+    if (threadIdx.x < 32) {  // inclusive scan of inc_start[1..A_CAP] by one warp
         const int lane = threadIdx.x;
-        const int per = (A_MAX + 31) / 32;
+        const int per = (A_CAP + 31) / 32;
         const int base = 1 + lane * per;
         int s = 0;
         for (int k = 0; k < per; ++k)
-            if (base + k <= A_MAX) s += C.inc_start[base + k];
+            if (base + k <= A_CAP) s += C.inc_start[base + k];
         int inc = s;
         for (int o = 1; o < 32; o <<= 1) {
             int t = __shfl_up_sync(0xffffffffu, inc, o);
@@ -89,13 +101,13 @@ __device__ void build_incidence(const TileS<T> &S, ClsSmem &C)
         }
         int run = inc - s;
         for (int k = 0; k < per; ++k)
-            if (base + k <= A_MAX) {
+            if (base + k <= A_CAP) {
                 run += C.inc_start[base + k];
                 C.inc_start[base + k] = run;
             }
     }
     __syncthreads();
-    for (int a = threadIdx.x; a < A_MAX; a += blockDim.x) C.inc_fill[a] = C.inc_start[a];
+    for (int a = threadIdx.x; a < A_CAP; a += blockDim.x) C.inc_fill[a] = C.inc_start[a];
     __syncthreads();
     for (int p = threadIdx.x; p < S.np; p += blockDim.x) {
         short2 sl = C.pslot[p];
@@ -114,10 +126,12 @@ __device__ void build_incidence(const TileS<T> &S, ClsSmem &C)
 // Returns this lane's part: 0 a free witness within r_p (certain), 2 one is
 // undecided, 1 none; the group's label is 0 if any part is 0, else 2 if any
 // part is 2, else 1 -- the label of one lane testing every candidate.
-template <bool FILT, class T>
-__device__ int shell_part(const TileS<T> &S, const ClsSmem &C, int brick, T x, T y, T z, T rp, T d0, int r, int G)
+template <bool FILT, class T, class CP>
+__device__ int shell_part(const TileS<T, CP> &S, const ClsSmem<CP> &C, int brick, T x, T y, T z, T rp, T d0, int r,
+                          int G)
 {
-    SmemAcc<T> A(S);
+    SmemAcc<T, CP> A(S);
+    constexpr int aw = ClsSmem<CP>::AWC;
     bool unsure = false;
     const T thr = rp, thr2 = rp * rp;
     for (int v = r; v < S.nv; v += G) {
@@ -139,7 +153,7 @@ __device__ int shell_part(const TileS<T> &S, const ClsSmem &C, int brick, T x, T
         T R = c.w + rp;
         if (lt_sq<FILT>(dx * dx + dy * dy + dz * dz, R * R, R, d0) == 0) continue;  // ball does not hold x
         if ((u & (G - 1)) == r) {
-            int w = face_witness<FILT>(A, a, x, y, z, rp, thr, d0, C.nbm);
+            int w = face_witness<FILT>(A, a, x, y, z, rp, thr, d0, C.nbm, aw);
             if (w == 1) return 0;
             if (w < 0) unsure = true;
         }
@@ -148,7 +162,7 @@ __device__ int shell_part(const TileS<T> &S, const ClsSmem &C, int brick, T x, T
         for (int k = k0 + ((r - u) & (G - 1)); k < k1; k += G) {
             const int p = (int)C.inc[k];
             const short2 sl = C.pslot[p];
-            int ws = saddle_witness<FILT>(A, p, x, y, z, rp, thr, d0, C.nbm, (int)sl.x, (int)sl.y);
+            int ws = saddle_witness<FILT>(A, p, x, y, z, rp, thr, d0, C.nbm, aw, (int)sl.x, (int)sl.y);
             if (ws == 1) return 0;
             if (ws < 0) unsure = true;
         }
@@ -158,13 +172,27 @@ __device__ int shell_part(const TileS<T> &S, const ClsSmem &C, int brick, T x, T
     return unsure ? 2 : 1;
 }
 
-template <class T, bool FILT>
+// bytes of a CTA's staging (TileS, then ClsSmem 16-byte aligned), rounded up to
+// 256 so that consecutive slices of the global-memory tier stay aligned
+template <class T, class CP>
+__host__ __device__ constexpr size_t cls_bytes()
+{
+    return (((sizeof(TileS<T, CP>) + 15) & ~(size_t)15) + sizeof(ClsSmem<CP>) + 255) & ~(size_t)255;
+}
+
+// CP = CapSmall: the staged lists in shared memory; a tile that overflows
+// them goes to ovf.  CP = CapBig (BIG): the tiles listed in ovf, with the
+// staged lists in this CTA's slice of the global scratch `big`; overflowing
+// that too is a capacity error.
+template <class T, bool FILT, class CP, bool BIG>
 __global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Batch B, TileSched Q, int8_t *__restrict__ labels_all,
-                                                          int *__restrict__ tile_band, int *__restrict__ err)
+                                                          int *__restrict__ tile_band, int *__restrict__ err,
+                                                          int *__restrict__ ovf, unsigned char *__restrict__ big)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    TileS<T> &S = *reinterpret_cast<TileS<T> *>(smem_raw);
-    ClsSmem &C = *reinterpret_cast<ClsSmem *>(smem_raw + ((sizeof(TileS<T>) + 15) & ~(size_t)15));
+    unsigned char *store = BIG ? big + (size_t)blockIdx.x * cls_bytes<T, CP>() : smem_raw;
+    TileS<T, CP> &S = *reinterpret_cast<TileS<T, CP> *>(store);
+    ClsSmem<CP> &C = *reinterpret_cast<ClsSmem<CP> *>(store + ((sizeof(TileS<T, CP>) + 15) & ~(size_t)15));
     __shared__ long long q_base;
     __shared__ Grid sG;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -186,6 +214,14 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Batch B, Tile
         const T h = (T)G.h;
         double x0[3];
         stage_tile<T>(M, G, mol, tile, S, x0);
+        if (S.flags & ERR_CAP_ANY) {  // uniform: set before stage_tile's last barrier
+            if (threadIdx.x == 0) {
+                if (BIG) atomicOr(err, S.flags);
+                else ovf_push(ovf, gt);
+            }
+            __syncthreads();
+            continue;
+        }
         if (threadIdx.x == 0) {
             C.nq = 0;
             C.band = 0;
@@ -205,7 +241,7 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Batch B, Tile
             __syncthreads();
             continue;
         }
-        build_incidence<T>(S, C);
+        build_incidence<T, CP>(S, C);
         // phase 1: bricks
         for (int brick = warp; brick < NBRICK; brick += CLS_THREADS / 32) {
             int li, lj, lk;
@@ -273,7 +309,7 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Batch B, Tile
         __syncthreads();
         const int nq = C.nq;
         if (nq > 0) {  // neighbour sets for the witnesses' freeness tests
-            build_neighbour_sets<T>(S, C.nbm, rp);
+            build_neighbour_sets<T, CP>(S, C.nbm, rp);
             __syncthreads();
         }
         // phase 2: shell points, the whole block; with few points, groups of
@@ -287,7 +323,7 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Batch B, Tile
             int brick = (code >> 9) & 15;
             int li = (code >> 6) & 7, lj = (code >> 3) & 7, lk = code & 7;
             T x = pt_coord<T>(G, li), y = pt_coord<T>(G, lj), z = pt_coord<T>(G, lk);
-            int part = shell_part<FILT>(S, C, brick, x, y, z, rp, d0, r, gs);
+            int part = shell_part<FILT, T, CP>(S, C, brick, x, y, z, rp, d0, r, gs);
             // group label: 0 if any part found a witness, else 2 if any is undecided, else 1
             for (int o = 1; o < gs; o <<= 1) {
                 const int q = __shfl_xor_sync(gmask, part, o);
@@ -307,86 +343,128 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Batch B, Tile
     }
 }
 
+// The undecided points of global tile gt re-labelled in FP64 (whole block):
+// one warp per point runs the witness search over every staged item.  A tile
+// that overflows the staging goes to ovf (or, in the global-memory tier, is a
+// capacity error).
+template <class CP>
+__device__ void band_tile(const Model &M, const Batch &B, long long gt, int8_t *__restrict__ labels_all,
+                          TileS<double, CP> &S, Grid &sG, short *s_pts, int &s_np, int *err, int *ovf, bool big)
+{
+    const int mol = mol_of_tile(B, gt);
+    load_grid(B, mol, sG);
+    const Grid &G = sG;
+    const long long tile = gt - G.tile0;
+    int8_t *__restrict__ labels = labels_all + G.lab0;
+    double x0[3];
+    stage_tile<double>(M, G, mol, tile, S, x0);
+    if (S.flags & ERR_CAP_ANY) {
+        if (threadIdx.x == 0) {
+            if (big) atomicOr(err, S.flags);
+            else ovf_push(ovf, gt);
+        }
+        __syncthreads();
+        return;
+    }
+    if (threadIdx.x == 0 && S.flags) atomicOr(err, S.flags);
+    int t[3];
+    tile_coords(G, tile, t);
+    SmemAcc<double, CP> A(S);
+    // the tile's undecided points, then one warp per point: the FP64
+    // witness search (a free probe centre closer than r_p: outside)
+    if (threadIdx.x == 0) s_np = 0;
+    __syncthreads();
+    for (int p = threadIdx.x; p < TILE_PTS; p += CLS_THREADS) {
+        int li = p >> 6, lj = (p >> 3) & 7, lk = p & 7;
+        long long gi = (long long)TILE * t[0] + li, gj = (long long)TILE * t[1] + lj, gk = (long long)TILE * t[2] + lk;
+        if (gi >= G.dims[0] || gj >= G.dims[1] || gk >= G.dims[2]) continue;
+        if (labels[(gi * G.dims[1] + gj) * G.dims[2] + gk] == LABEL_BAND) s_pts[atomicAdd(&s_np, 1)] = (short)p;
+    }
+    __syncthreads();
+    const int npts = s_np;
+    for (int k = threadIdx.x >> 5; k < npts; k += CLS_THREADS / 32) {
+        const int p = s_pts[k];
+        const int li = p >> 6, lj = (p >> 3) & 7, lk = p & 7;
+        unsigned um_p, um_v;
+        const int r = warp_witness<false>(A, (double)li * G.h, (double)lj * G.h, (double)lk * G.h, M.rp, M.rp, 0.0, -1,
+                                          -1, um_p, um_v);
+        if ((threadIdx.x & 31) == 0) {
+            const long long gi = (long long)TILE * t[0] + li, gj = (long long)TILE * t[1] + lj,
+                            gk = (long long)TILE * t[2] + lk;
+            labels[(gi * G.dims[1] + gj) * G.dims[2] + gk] = r == 1 ? LABEL_OUT : LABEL_IN;
+        }
+    }
+    __syncthreads();
+}
+
+template <class CP>
+__host__ __device__ constexpr size_t band_bytes()
+{
+    return (sizeof(TileS<double, CP>) + 255) & ~(size_t)255;
+}
+
+// CapSmall: chunks of CLS_THREADS tiles, the threads pick out the tiles with
+// undecided points, then the block re-labels them one after the other.
+// CapBig (BIG): the tiles listed in ovf, staged in global memory.
+template <class CP, bool BIG>
 __global__ void __launch_bounds__(CLS_THREADS) k_band(Model M, Batch B, int8_t *__restrict__ labels_all,
-                                                      const int *__restrict__ tile_band, int *__restrict__ err)
+                                                      const int *__restrict__ tile_band, int *__restrict__ err,
+                                                      int *__restrict__ ovf, unsigned char *__restrict__ big)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    TileS<double> &S = *reinterpret_cast<TileS<double> *>(smem_raw);
+    unsigned char *store = BIG ? big + (size_t)blockIdx.x * band_bytes<CP>() : smem_raw;
+    TileS<double, CP> &S = *reinterpret_cast<TileS<double, CP> *>(store);
     __shared__ Grid sG;
     __shared__ int s_list[CLS_THREADS];
     __shared__ short s_pts[TILE_PTS];
     __shared__ int s_n, s_np;
-    // chunks of CLS_THREADS tiles: the threads pick out the tiles with
-    // undecided points, then the block re-labels them one after the other
+    if (BIG) {
+        const int n = ovf[1];
+        for (int k = blockIdx.x; k < n; k += gridDim.x) band_tile<CP>(M, B, ovf[2 + k], labels_all, S, sG, s_pts, s_np,
+                                                                     err, ovf, true);
+        return;
+    }
     for (long long c0 = (long long)blockIdx.x * CLS_THREADS; c0 < B.n_tiles; c0 += (long long)gridDim.x * CLS_THREADS) {
-      if (threadIdx.x == 0) s_n = 0;
-      __syncthreads();
-      if (c0 + threadIdx.x < B.n_tiles && tile_band[c0 + threadIdx.x] != 0) s_list[atomicAdd(&s_n, 1)] = threadIdx.x;
-      __syncthreads();
-      const int nband = s_n;
-      for (int q = 0; q < nband; ++q) {
-        const long long gt = c0 + s_list[q];
-        const int mol = mol_of_tile(B, gt);
-        load_grid(B, mol, sG);
-        const Grid &G = sG;
-        const long long tile = gt - G.tile0;
-        int8_t *__restrict__ labels = labels_all + G.lab0;
-        double x0[3];
-        stage_tile<double>(M, G, mol, tile, S, x0);
-        if (threadIdx.x == 0 && S.flags) atomicOr(err, S.flags);
-        int t[3];
-        tile_coords(G, tile, t);
-        SmemAcc<double> A(S);
-        // the tile's undecided points, then one warp per point: the FP64
-        // witness search (a free probe centre closer than r_p: outside)
-        if (threadIdx.x == 0) s_np = 0;
+        if (threadIdx.x == 0) s_n = 0;
         __syncthreads();
-        for (int p = threadIdx.x; p < TILE_PTS; p += CLS_THREADS) {
-            int li = p >> 6, lj = (p >> 3) & 7, lk = p & 7;
-            long long gi = (long long)TILE * t[0] + li, gj = (long long)TILE * t[1] + lj,
-                      gk = (long long)TILE * t[2] + lk;
-            if (gi >= G.dims[0] || gj >= G.dims[1] || gk >= G.dims[2]) continue;
-            if (labels[(gi * G.dims[1] + gj) * G.dims[2] + gk] == LABEL_BAND) s_pts[atomicAdd(&s_np, 1)] = (short)p;
-        }
+        if (c0 + threadIdx.x < B.n_tiles && tile_band[c0 + threadIdx.x] != 0) s_list[atomicAdd(&s_n, 1)] = threadIdx.x;
         __syncthreads();
-        const int npts = s_np;
-        for (int k = threadIdx.x >> 5; k < npts; k += CLS_THREADS / 32) {
-            const int p = s_pts[k];
-            const int li = p >> 6, lj = (p >> 3) & 7, lk = p & 7;
-            unsigned um_p, um_v;
-            const int r = warp_witness<false>(A, (double)li * G.h, (double)lj * G.h, (double)lk * G.h, M.rp, M.rp, 0.0,
-                                              -1, -1, um_p, um_v);
-            if ((threadIdx.x & 31) == 0) {
-                const long long gi = (long long)TILE * t[0] + li, gj = (long long)TILE * t[1] + lj,
-                                gk = (long long)TILE * t[2] + lk;
-                labels[(gi * G.dims[1] + gj) * G.dims[2] + gk] = r == 1 ? LABEL_OUT : LABEL_IN;
-            }
-        }
-        __syncthreads();
-      }
+        const int nband = s_n;
+        for (int q = 0; q < nband; ++q)
+            band_tile<CP>(M, B, c0 + s_list[q], labels_all, S, sG, s_pts, s_np, err, ovf, false);
     }
 }
 
-template <class T>
-static size_t cls_smem()
-{
-    return ((sizeof(TileS<T>) + 15) & ~(size_t)15) + sizeof(ClsSmem);
-}
-
 static long long g_band_grid = 1;  // resident k_band CTAs on the device
+static int g_n_sm = 1;              // SMs: the grid of the global-memory tier
 
 // dynamic shared memory limits and the band kernel's grid (once per device,
 // before any launch or capture)
 void classify_init()
 {
-    cudaFuncSetAttribute(k_classify<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cls_smem<double>());
-    cudaFuncSetAttribute(k_classify<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cls_smem<float>());
-    cudaFuncSetAttribute(k_band, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TileS<double>));
+    cudaFuncSetAttribute(k_classify<double, false, CapSmall, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)cls_bytes<double, CapSmall>());
+    cudaFuncSetAttribute(k_classify<float, true, CapSmall, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)cls_bytes<float, CapSmall>());
+    cudaFuncSetAttribute(k_band<CapSmall, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)band_bytes<CapSmall>());
     int dev = 0, n_sm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_band, CLS_THREADS, sizeof(TileS<double>));
-    g_band_grid = (long long)(n_sm > 0 ? n_sm : 1) * (per_sm > 0 ? per_sm : 1);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_band<CapSmall, false>, CLS_THREADS,
+                                                  band_bytes<CapSmall>());
+    g_n_sm = n_sm > 0 ? n_sm : 1;
+    g_band_grid = (long long)g_n_sm * (per_sm > 0 ? per_sm : 1);
+}
+
+// bytes of global scratch the global-memory tier of the classification and
+// the band re-labelling need (one slice per CTA, one CTA per SM)
+size_t classify_big_bytes()
+{
+    size_t per = cls_bytes<double, CapBig>();
+    if (cls_bytes<float, CapBig>() > per) per = cls_bytes<float, CapBig>();
+    if (band_bytes<CapBig>() > per) per = band_bytes<CapBig>();
+    return per * (size_t)g_n_sm;
 }
 
 int classify_ctas_per_sm(int precision)
@@ -394,33 +472,46 @@ int classify_ctas_per_sm(int precision)
     int dev = 0, n = 0;
     cudaGetDevice(&dev);
     if (precision == 0)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_classify<double, false>, CLS_THREADS, cls_smem<double>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_classify<double, false, CapSmall, false>, CLS_THREADS,
+                                                      cls_bytes<double, CapSmall>());
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_classify<float, true>, CLS_THREADS, cls_smem<float>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_classify<float, true, CapSmall, false>, CLS_THREADS,
+                                                      cls_bytes<float, CapSmall>());
     return n > 0 ? n : 1;
 }
 
+// the shared-memory tier over the scheduled tiles, then the global-memory
+// tier over the tiles that overflowed it (ovf: count, then tiles)
 int launch_classify(const Model &M, const Batch &B, int precision, const TileSched &Q, int grid, int8_t *labels,
-                    int *tile_band, int *err, cudaStream_t st)
+                    int *tile_band, int *err, int *ovf, unsigned char *big, cudaStream_t st)
 {
     if (grid < 1) grid = 1;
+    cudaMemsetAsync(ovf + 1, 0, sizeof(int), st);
+    TileSched QB{nullptr, 1, ovf + 2, ovf + 1};
     if (precision == 0) {
-        size_t sm = cls_smem<double>();
-        k_classify<double, false><<<grid, CLS_THREADS, sm, st>>>(M, B, Q, labels, tile_band, err);
+        k_classify<double, false, CapSmall, false><<<grid, CLS_THREADS, cls_bytes<double, CapSmall>(), st>>>(
+            M, B, Q, labels, tile_band, err, ovf, nullptr);
+        k_classify<double, false, CapBig, true><<<g_n_sm, CLS_THREADS, 0, st>>>(M, B, QB, labels, tile_band, err, ovf,
+                                                                               big);
     } else {
-        size_t sm = cls_smem<float>();
-        k_classify<float, true><<<grid, CLS_THREADS, sm, st>>>(M, B, Q, labels, tile_band, err);
+        k_classify<float, true, CapSmall, false><<<grid, CLS_THREADS, cls_bytes<float, CapSmall>(), st>>>(
+            M, B, Q, labels, tile_band, err, ovf, nullptr);
+        k_classify<float, true, CapBig, true><<<g_n_sm, CLS_THREADS, 0, st>>>(M, B, QB, labels, tile_band, err, ovf,
+                                                                             big);
     }
-    return 1;
+    return 2;
 }
 
-int launch_band(const Model &M, const Batch &B, int8_t *labels, const int *tile_band, int *err, cudaStream_t st)
+int launch_band(const Model &M, const Batch &B, int8_t *labels, const int *tile_band, int *err, int *ovf,
+                unsigned char *big, cudaStream_t st)
 {
-    const size_t sm = sizeof(TileS<double>);
     const long long chunks = (B.n_tiles + CLS_THREADS - 1) / CLS_THREADS;
     const long long grid = chunks < 1 ? 1 : (chunks < g_band_grid ? chunks : g_band_grid);
-    k_band<<<(int)grid, CLS_THREADS, sm, st>>>(M, B, labels, tile_band, err);
-    return 1;
+    cudaMemsetAsync(ovf + 1, 0, sizeof(int), st);
+    k_band<CapSmall, false><<<(int)grid, CLS_THREADS, band_bytes<CapSmall>(), st>>>(M, B, labels, tile_band, err, ovf,
+                                                                                 nullptr);
+    k_band<CapBig, true><<<g_n_sm, CLS_THREADS, 0, st>>>(M, B, labels, tile_band, err, ovf, big);
+    return 2;
 }
 
 }  // namespace eses

@@ -245,8 +245,8 @@ __device__ __forceinline__ void exact_normal(int kind, const double *c, const do
 }
 
 // exact root of a staged piece (tile frame, FP64 data from HBM) near t0
-template <class TS>
-__device__ __noinline__ double staged_exact_root(const ExactAcc<TS> &X, int kind, int slot, const double *s,
+template <class XA>
+__device__ __noinline__ double staged_exact_root(const XA &X, int kind, int slot, const double *s,
                                                     int axis, double rp, double t0)
 {
     if (kind == 0) {
@@ -521,8 +521,8 @@ __device__ __noinline__ void torus_piece_exact(const Acc &X, EdgeSmem &E, int e,
 // to the segment takes the value rad (its minimum and maximum over the
 // segment bracket rad); tori: the 1-Lipschitz distance to the circle is
 // within h/2 of r_p at the edge's midpoint.  mg widens both for FP32.
-template <class T>
-__device__ __forceinline__ bool cand_test(const TileS<T> &S, const T *s, int axis, int it, T hT, T rpT, T mg)
+template <class T, class CP>
+__device__ __forceinline__ bool cand_test(const TileS<T, CP> &S, const T *s, int axis, int it, T hT, T rpT, T mg)
 {
     const int na = S.na, nv = S.nv;
     if (it < na + nv) {
@@ -554,16 +554,16 @@ __device__ __forceinline__ bool cand_test(const TileS<T> &S, const T *s, int axi
 // direction that leaves the end point's side (falling from an inside end,
 // rising from an outside end) and whose witness is free.  FP32 roots carry
 // an error bound; a decision the bound cannot make goes to FP64.
-template <class T, bool FILT>
-__device__ void cand_roots(const Model &M, const TileS<T> &S, const double *x0, EdgeSmem &E, int e, int it, double h,
+template <class T, bool FILT, class CP>
+__device__ void cand_roots(const Model &M, const TileS<T, CP> &S, const double *x0, EdgeSmem &E, int e, int it, double h,
                            double rp, T d0)
 {
     const EdgeRef R = edge_ref(E, e);
     const int axis = R.axis;
     const double s64[3] = {E.hd[R.p >> 6], E.hd[(R.p >> 3) & 7], E.hd[R.p & 7]};
     const T s[3] = {(T)s64[0], (T)s64[1], (T)s64[2]};
-    SmemAcc<T> A(S);
-    ExactAcc<T> X(S, M, x0);
+    SmemAcc<T, CP> A(S);
+    ExactAcc<T, CP> X(S, M, x0);
     const int na = S.na, nv = S.nv;
     const T hT = (T)h, rpT = (T)rp;
     const T lo = FILT ? T(-1e-4) : T(0), hi = hT + (FILT ? T(1e-4) : T(0));
@@ -717,8 +717,8 @@ __device__ void cand_roots(const Model &M, const TileS<T> &S, const double *x0, 
 // warp).  Returns 0 with the chosen piece (kind, staged slot) and its root, 1
 // when no root is found, 2 when the candidates overflowed the buffer (the
 // first WCAND are used).
-template <class T, bool FILT>
-__device__ int warp_select(const Model &M, const TileS<T> &S, const double *x0, EdgeSmem &E, int warp, int e,
+template <class T, bool FILT, class CP>
+__device__ int warp_select(const Model &M, const TileS<T, CP> &S, const double *x0, EdgeSmem &E, int warp, int e,
                            double h, double rp, T d0, float &t_out, int &kind_out, int &slot_out)
 {
     const int lane = threadIdx.x & 31;
@@ -726,8 +726,8 @@ __device__ int warp_select(const Model &M, const TileS<T> &S, const double *x0, 
     const int axis = R.axis;
     const double s64[3] = {E.hd[R.p >> 6], E.hd[(R.p >> 3) & 7], E.hd[R.p & 7]};
     const T s[3] = {(T)s64[0], (T)s64[1], (T)s64[2]};
-    SmemAcc<T> A(S);
-    ExactAcc<T> X(S, M, x0);
+    SmemAcc<T, CP> A(S);
+    ExactAcc<T, CP> X(S, M, x0);
     const T rpT = (T)rp;
     const float tie = 1e-6f * (float)h;  // FP32 rounding of a root
     const bool inside = R.lab == LABEL_IN;
@@ -876,6 +876,7 @@ __global__ void __launch_bounds__(COUNT_WARPS * 32) k_edge_count(Batch B, const 
     for (long long gt = (long long)blockIdx.x * COUNT_WARPS + (threadIdx.x >> 5); gt < nt; gt += nw) {
         const Grid &G = B.grid[mol_of_tile(B, gt)];
         const long long dims[3] = {G.dims[0], G.dims[1], G.dims[2]};
+        const long long own[3] = {G.own[0], G.own[1], G.own[2]};
         const int8_t *__restrict__ labels = labels_all + G.lab0;
         const long long st1 = dims[2], st0 = dims[1] * dims[2];
         int t[3];
@@ -884,7 +885,7 @@ __global__ void __launch_bounds__(COUNT_WARPS * 32) k_edge_count(Batch B, const 
         for (int p = lane; p < TILE_PTS; p += 32) {
             const long long g[3] = {(long long)TILE * t[0] + (p >> 6), (long long)TILE * t[1] + ((p >> 3) & 7),
                                     (long long)TILE * t[2] + (p & 7)};
-            if (g[0] >= dims[0] || g[1] >= dims[1] || g[2] >= dims[2]) continue;
+            if (g[0] >= own[0] || g[1] >= own[1] || g[2] >= own[2]) continue;  // not owned (or not in the grid)
             const long long idx = g[0] * st0 + g[1] * st1 + g[2];
             const int l0 = labels[idx];
             npin += l0;
@@ -946,9 +947,9 @@ __device__ __forceinline__ int block_excl_scan_e(int v, int *sh, int *total)
 // polish the FP32 root, kind, model index, end label and failure flag; a
 // failure (status 1) is logged with its candidates (cand, ncand), an overflow
 // (status 2) flagged.
-template <class T>
-__device__ void edge_out(const TileS<T> &S, const EdgeSmem &E, int e, const EdgeRef &R, const int *t, long long st0,
-                         long long st1, int mol, int status, float tr, int kind, int slot, EdgeOut &out,
+template <class T, class CP>
+__device__ void edge_out(const TileS<T, CP> &S, const EdgeSmem &E, int e, const EdgeRef &R, const int *t, const int *toff,
+                         long long st0, long long st1, int mol, int status, float tr, int kind, int slot, EdgeOut &out,
                          int *n_fail, int *err, long long *fail_log, const WCand *cand, int ncand)
 {
     const int a = R.axis, q = R.p;
@@ -980,22 +981,35 @@ __device__ void edge_out(const TileS<T> &S, const EdgeSmem &E, int e, const Edge
         }
     }
     const long long o = E.ebase[a] + (e - E.estart[a]);
-    out.idx[a][o] =
-        (long long)(TILE * t[0] + li) * st0 + (long long)(TILE * t[1] + lj) * st1 + (TILE * t[2] + lk);
+    // full-grid index of the lower point (st0, st1: the full grid's strides)
+    out.idx[a][o] = (long long)(TILE * (t[0] + toff[0]) + li) * st0 + (long long)(TILE * (t[1] + toff[1]) + lj) * st1 +
+                    (TILE * (t[2] + toff[2]) + lk);
     // chosen piece for the FP64 polish: FP32 root, kind, model index, end label, failure
     out.code[a][o] = make_int2(__float_as_int(tr), (kind << 29) | (R.lab << 28) | ((status == 1 ? 1 : 0) << 27) | mid);
 }
 
-template <class T, bool FILT>
+template <class T, class CP>
+__host__ __device__ constexpr size_t edge_tile_bytes()  // rounded to 256: aligned slices in global memory
+{
+    return (sizeof(TileS<T, CP>) + 255) & ~(size_t)255;
+}
+
+// CP = CapSmall: the staged lists in shared memory (with EdgeSmem); a tile
+// that overflows them goes to ovf.  CP = CapBig (BIG): the tiles listed in ovf
+// (Q.list), the staged lists in this CTA's slice of the global scratch `big`,
+// EdgeSmem in shared memory; overflowing that too is a capacity error.
+template <class T, bool FILT, class CP, bool BIG>
 __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Batch B, TileSched Q, int chunk0,
                                                              const int8_t *__restrict__ labels_all,
                                                              const int *__restrict__ edge_start, EdgeOut out,
                                                              int *__restrict__ n_fail, int *__restrict__ err,
-                                                             long long *__restrict__ fail_log)
+                                                             long long *__restrict__ fail_log, int *__restrict__ ovf,
+                                                             unsigned char *__restrict__ big)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    TileS<T> &S = *reinterpret_cast<TileS<T> *>(smem_raw);
-    EdgeSmem &E = *reinterpret_cast<EdgeSmem *>(smem_raw + ((sizeof(TileS<T>) + 15) & ~(size_t)15));
+    TileS<T, CP> &S = *reinterpret_cast<TileS<T, CP> *>(BIG ? big + (size_t)blockIdx.x * edge_tile_bytes<T, CP>()
+                                                             : smem_raw);
+    EdgeSmem &E = *reinterpret_cast<EdgeSmem *>(BIG ? smem_raw : smem_raw + edge_tile_bytes<T, CP>());
     __shared__ long long q_base;
     __shared__ Grid sG;
     const long long nt = B.n_tiles;
@@ -1003,11 +1017,13 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Batch B, T
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const T rpT = (T)rp, mg = FILT ? T(2e-3) : T(0);
     long long iter = 0;
+    const long long npos = sched_count(Q, nt);
     for (;;) {
       const long long base = next_tiles(Q, iter, &q_base);
-      if (base >= nt) break;
-      const long long bend = min(base + (long long)Q.per, nt);
-      for (long long gt = base; gt < bend; ++gt) {
+      if (base >= npos) break;
+      const long long bend = min(base + (long long)Q.per, npos);
+      for (long long pos = base; pos < bend; ++pos) {
+        const long long gt = sched_tile(Q, pos);
         int tot = 0;
         for (int a = 0; a < 3; ++a) tot += edge_start[a * nt + gt + 1] - edge_start[a * nt + gt];
         if (tot == 0) continue;
@@ -1017,11 +1033,24 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Batch B, T
         const long long tile = gt - G.tile0;
         const int8_t *__restrict__ labels = labels_all + G.lab0;
         const long long st1 = G.dims[2], st0 = G.dims[1] * G.dims[2];
+        const long long fst1 = G.full[2], fst0 = G.full[1] * G.full[2];  // strides of the output indices
         const double h = G.h;
         const T d0 = FILT ? (T)G.d0 : T(0);
         const T hT = (T)h;
         double x0[3];
         stage_tile<T>(M, G, mol, tile, S, x0);
+        if (S.flags & ERR_CAP_ANY) {  // uniform: set before stage_tile's last barrier
+            if (threadIdx.x == 0) {
+                if (BIG) atomicOr(err, S.flags);
+                else {  // to the global-memory tier (ovf: run total, stage count, tiles)
+                    atomicAdd(&ovf[0], 1);
+                    const int k = atomicAdd(&ovf[1], 1);
+                    ovf[2 + k] = (int)gt;
+                }
+            }
+            __syncthreads();
+            continue;
+        }
         if (threadIdx.x == 0 && S.flags) atomicOr(err, S.flags);
         int t[3];
         tile_coords(G, tile, t);
@@ -1042,10 +1071,12 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Batch B, T
             for (int k = 0; k < 2; ++k) {
                 int q = 2 * threadIdx.x + k;
                 int l[3] = {q >> 6, (q >> 3) & 7, q & 7};
+                const bool owned = TILE * t[0] + l[0] < G.own[0] && TILE * t[1] + l[1] < G.own[1] &&
+                                   TILE * t[2] + l[2] < G.own[2];
                 int8_t l0 = E.lab[(l[0] * 9 + l[1]) * 9 + l[2]];
                 l[a] += 1;
                 int8_t l1 = E.lab[(l[0] * 9 + l[1]) * 9 + l[2]];
-                flag[k] = (l0 >= 0 && l1 >= 0 && l0 != l1) ? 1 : 0;
+                flag[k] = (owned && l0 >= 0 && l1 >= 0 && l0 != l1) ? 1 : 0;
             }
             int tsum;
             int rank = block_excl_scan_e(flag[0] + flag[1], E.sh, &tsum);
@@ -1085,7 +1116,7 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Batch B, T
                 const int nsph = S.na + S.nv;
                 for (int i0 = 0; i0 < nitem; i0 += 32) {
                     const int it = i0 + lane;
-                    const bool hit = it < nitem && cand_test<T>(S, s, R.axis, it, hT, rpT, mg);
+                    const bool hit = it < nitem && cand_test<T, CP>(S, s, R.axis, it, hT, rpT, mg);
                     // spheres and tori in separate runs, so a warp of the root phase does one kind
                     const bool tor = it >= nsph;
                     const unsigned ms = __ballot_sync(0xffffffffu, hit && !tor);
@@ -1123,7 +1154,7 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Batch B, T
                     const int k = base + lane;
                     if (k < ns + nt_) {
                         const unsigned v = k < ns ? E.pool[k] : E.pool[POOL_MAX - 1 - (k - ns)];
-                        cand_roots<T, FILT>(M, S, x0, E, (int)(v >> 16), (int)(v & 0xffffu), h, rp, d0);
+                        cand_roots<T, FILT, CP>(M, S, x0, E, (int)(v >> 16), (int)(v & 0xffffu), h, rp, d0);
                     }
                 }
             }
@@ -1189,7 +1220,8 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Batch B, T
                 if (k >= 0) {
                     const WCand &ck = E.root[E.rorder[b + k]];
                     const float tr = ck.t64 == ck.t64 ? (float)ck.t64 : ck.t;
-                    edge_out(S, E, e, R, t, st0, st1, mol, 0, tr, ck.kind, ck.id, out, n_fail, err, fail_log, nullptr, 0);
+                    edge_out(S, E, e, R, t, G.toff, fst0, fst1, mol, 0, tr, ck.kind, ck.id, out, n_fail, err, fail_log,
+                             nullptr, 0);
                 } else {
                     E.hard[atomicAdd(&E.nhard, 1)] = (short)e;
                 }
@@ -1209,11 +1241,11 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Batch B, T
                 __syncwarp();
                 float tr = 0.5f * (float)h;
                 int kind = 0, slot = 0;
-                int status = warp_select<T, FILT>(M, S, x0, E, warp, e, h, rp, d0, tr, kind, slot);
+                int status = warp_select<T, FILT, CP>(M, S, x0, E, warp, e, h, rp, d0, tr, kind, slot);
                 if (ovf) status = 2;  // single-edge overflow
                 if (lane == 0)
-                    edge_out(S, E, e, edge_ref(E, e), t, st0, st1, mol, status, tr, kind, slot, out, n_fail, err,
-                             fail_log, E.cand[warp], E.ncand[warp]);
+                    edge_out(S, E, e, edge_ref(E, e), t, G.toff, fst0, fst1, mol, status, tr, kind, slot, out, n_fail,
+                             err, fail_log, E.cand[warp], E.ncand[warp]);
                 __syncwarp();
             }
             __syncthreads();
@@ -1254,17 +1286,17 @@ __global__ void __launch_bounds__(POLISH_THREADS) k_edge_polish(Model M, Batch B
         const float t32 = __int_as_float(code.x);
         const int kind = (code.y >> 29) & 3, lab_s = (code.y >> 28) & 1, failed = (code.y >> 27) & 1;
         const int mid = code.y & ((1 << 27) - 1);
-        long long gi, gj, gk;
-        if (idx < (1LL << 32) && G.dims[1] * G.dims[2] < (1LL << 32)) {  // 32-bit division where it fits
-            const unsigned i32 = (unsigned)idx, d2 = (unsigned)G.dims[2], d1 = (unsigned)G.dims[1];
+        long long gi, gj, gk;  // full-grid point of the lower index
+        if (idx < (1LL << 32) && G.full[1] * G.full[2] < (1LL << 32)) {  // 32-bit division where it fits
+            const unsigned i32 = (unsigned)idx, d2 = (unsigned)G.full[2], d1 = (unsigned)G.full[1];
             const unsigned q = i32 / d2;
             gk = i32 - q * d2;
             gj = q % d1;
             gi = q / d1;
         } else {
-            gi = idx / (G.dims[1] * G.dims[2]);
-            gj = (idx / G.dims[2]) % G.dims[1];
-            gk = idx % G.dims[2];
+            gi = idx / (G.full[1] * G.full[2]);
+            gj = (idx / G.full[2]) % G.full[1];
+            gk = idx % G.full[2];
         }
         const double s[3] = {G.lo[0] + h * (double)gi, G.lo[1] + h * (double)gj, G.lo[2] + h * (double)gk};
         double t = 0.5 * h, n[3] = {0.0, 0.0, 0.0};
@@ -1412,30 +1444,48 @@ int launch_mol_edges(const Batch &B, const int *edge_start, long long *medge, cu
     return 1;
 }
 
-template <class T, bool FILT>
+template <class T>
 static size_t edge_smem()
 {
-    return ((sizeof(TileS<T>) + 15) & ~(size_t)15) + sizeof(EdgeSmem);
+    return edge_tile_bytes<T, CapSmall>() + sizeof(EdgeSmem);
 }
+
+static int g_edge_n_sm = 1;  // SMs: the grid of the global-memory tier
 
 // dynamic shared memory limits (once per device, before any launch or capture)
 void edges_init()
 {
-    cudaFuncSetAttribute(k_edge_solve<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)edge_smem<double, false>());
-    cudaFuncSetAttribute(k_edge_solve<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)edge_smem<float, true>());
+    cudaFuncSetAttribute(k_edge_solve<double, false, CapSmall, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)edge_smem<double>());
+    cudaFuncSetAttribute(k_edge_solve<float, true, CapSmall, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)edge_smem<float>());
+    cudaFuncSetAttribute(k_edge_solve<double, false, CapBig, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(EdgeSmem));
+    cudaFuncSetAttribute(k_edge_solve<float, true, CapBig, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(EdgeSmem));
+    int dev = 0, n_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    g_edge_n_sm = n_sm > 0 ? n_sm : 1;
+}
+
+// bytes of global scratch the root solve's global-memory tier needs
+size_t edges_big_bytes()
+{
+    size_t per = edge_tile_bytes<double, CapBig>();
+    if (edge_tile_bytes<float, CapBig>() > per) per = edge_tile_bytes<float, CapBig>();
+    return per * (size_t)g_edge_n_sm;
 }
 
 int edge_ctas_per_sm(int precision)
 {
     int n = 0;
     if (precision == 0)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_edge_solve<double, false>, EDGE_THREADS,
-                                                      edge_smem<double, false>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_edge_solve<double, false, CapSmall, false>, EDGE_THREADS,
+                                                      edge_smem<double>());
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_edge_solve<float, true>, EDGE_THREADS,
-                                                      edge_smem<float, true>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_edge_solve<float, true, CapSmall, false>, EDGE_THREADS,
+                                                      edge_smem<float>());
     return n > 0 ? n : 1;
 }
 
@@ -1444,26 +1494,31 @@ int edge_chunk_max() { return CHUNK; }
 template <class T, bool FILT>
 static void edge_solve_launch(const Model &M, const Batch &B, const TileSched &Q, int grid, int chunk,
                               const int8_t *labels, const int *edge_start, EdgeOut out, int *n_fail, int *err,
-                              long long *fail_log, cudaStream_t st)
+                              long long *fail_log, int *ovf, unsigned char *big, cudaStream_t st)
 {
-    size_t sm = edge_smem<T, FILT>();
-    k_edge_solve<T, FILT><<<grid, EDGE_THREADS, sm, st>>>(M, B, Q, chunk, labels, edge_start, out, n_fail, err,
-                                                           fail_log);
+    cudaMemsetAsync(ovf + 1, 0, sizeof(int), st);
+    k_edge_solve<T, FILT, CapSmall, false><<<grid, EDGE_THREADS, edge_smem<T>(), st>>>(
+        M, B, Q, chunk, labels, edge_start, out, n_fail, err, fail_log, ovf, nullptr);
+    TileSched QB{nullptr, 1, ovf + 2, ovf + 1};
+    k_edge_solve<T, FILT, CapBig, true><<<g_edge_n_sm, EDGE_THREADS, sizeof(EdgeSmem), st>>>(
+        M, B, QB, chunk, labels, edge_start, out, n_fail, err, fail_log, ovf, big);
 }
 
 long long polish_blocks(long long n_edges) { return n_edges > 0 ? ceil_div_ll(n_edges, POLISH_THREADS) : 0; }
 
 int launch_edge_solve(const Model &M, const Batch &B, int precision, const TileSched &Q, int grid, int chunk,
                       const int8_t *labels, const int *edge_start, EdgeOut out, int *n_fail, int *err,
-                      long long *fail_log, cudaStream_t st)
+                      long long *fail_log, int *ovf, unsigned char *big, cudaStream_t st)
 {
     if (grid < 1) grid = 1;
     chunk = chunk < 1 ? 1 : (chunk > CHUNK ? CHUNK : chunk);
     if (precision == 0)
-        edge_solve_launch<double, false>(M, B, Q, grid, chunk, labels, edge_start, out, n_fail, err, fail_log, st);
+        edge_solve_launch<double, false>(M, B, Q, grid, chunk, labels, edge_start, out, n_fail, err, fail_log, ovf,
+                                         big, st);
     else
-        edge_solve_launch<float, true>(M, B, Q, grid, chunk, labels, edge_start, out, n_fail, err, fail_log, st);
-    return 1;
+        edge_solve_launch<float, true>(M, B, Q, grid, chunk, labels, edge_start, out, n_fail, err, fail_log, ovf, big,
+                                       st);
+    return 2;
 }
 
 int launch_edge_polish(const Model &M, const Batch &B, EdgeOut out, long long n_edges_total,

@@ -23,10 +23,19 @@ namespace eses {
 constexpr int TILE = 8;          // points per tile edge
 constexpr int TILE_PTS = TILE * TILE * TILE;
 
-// per-tile staging capacities (shared memory lists)
-constexpr int A_MAX = 320;
-constexpr int P_MAX = 512;
-constexpr int V_MAX = 640;
+// Per-tile staging capacities: the shared-memory tier every tile uses, and
+// the larger tier in global memory for the tiles that overflow it (very
+// dense atom sets); only a tile that overflows both is an error.
+struct CapSmall {
+    static constexpr int A = 320, P = 512, V = 640;
+};
+struct CapBig {
+    static constexpr int A = 1024, P = 2048, V = 2048;
+};
+constexpr int A_MAX = CapSmall::A;
+constexpr int P_MAX = CapSmall::P;
+constexpr int V_MAX = CapSmall::V;
+constexpr int ERR_CAP_ANY = 1 | 2 | 4;  // ERR_CAP_ATOMS | ERR_CAP_PAIRS | ERR_CAP_VERTS
 
 // device error bits (OR-ed into ctx->d_err)
 enum : int {
@@ -76,7 +85,7 @@ struct Model {
     const int *pcell_start;       // free-arc pairs binned by o
     const int *pcell_list;
     int n_verts;
-    const double4 *vert;          // free triple points (xyz, 0)
+    const double4 *vert;          // free triple points (xyz, third atom of the triple as a double)
     const int *vert_mol;          // molecule of each triple point
     const int *vcell_start;
     const int *vcell_list;
@@ -92,11 +101,20 @@ struct Model {
     const float4 *vert_lo;
 };
 
-// The grid of one molecule (Eq. 2 with the origin of its reading).
+// The grid of one molecule (Eq. 2 with the origin of its reading), or the box
+// of it that a block selection computes: the box starts at tile toff of the
+// molecule's full grid (point 8 toff), holds dims points (its labels, C
+// order), and owns the first own[a] points along each axis -- only owned
+// points give edges, intersections and area/volume terms; the rest of the
+// box is the layer of neighbours the owned edges need.  Without a selection
+// toff = 0 and own = dims = full.
 struct Grid {
-    double lo[3];
+    double lo[3];                 // origin of the full grid
     double h;
-    long long dims[3];
+    long long dims[3];            // points of the computed box
+    long long own[3];             // owned points from the box origin
+    long long full[3];            // points of the full grid (output lower indices index it)
+    int toff[3];                  // first tile of the box in the full grid
     int tiles[3];
     long long n_tiles;
     long long tile0;              // index of its first tile in the batch

@@ -28,9 +28,10 @@ int launch_pair_count(const Model &M, int *pair_count, cudaStream_t st);
 int launch_pair_fill(const Model &M, const int *pair_start, double4 *pair_o, double4 *pair_u, int2 *pair_ij,
                       cudaStream_t st);
 int launch_arcs(const Model &M, uint8_t *pair_free, int *vert_count, cudaStream_t st);
-int launch_arcs_emit(const Model &M, const int *vert_start, double4 *vert, int *vert_mol, cudaStream_t st);
+int launch_arcs_emit(const Model &M, const int *vert_start, double4 *vert, int *vert_mol, int4 *vert_atoms,
+                     cudaStream_t st);
 int launch_faces(const Model &M, const int *circle_count, const uint8_t *contained, uint8_t *face, cudaStream_t st);
-int launch_bin_count(const Model &M, int which, int *count, int *item_cell, cudaStream_t st);
+int launch_bin_count(const Model &M, int which, bool cull, int *count, int *item_cell, cudaStream_t st);
 // FP32 double-float copies: which 0 atoms (hi, lo), 1 circles (hi, lo, axis), 2 triple points (hi, lo)
 int launch_model_f32(const Model &M, int which, const Grid *grids, float4 *hi, float4 *lo_, float4 *u32,
                      cudaStream_t st);
@@ -41,9 +42,14 @@ int launch_bin_scatter(const Model &M, int which, const int *item_cell, const in
 // persistent: `grid` CTAs take tiles in the order of Q (labels of the whole batch)
 void classify_init();
 int classify_ctas_per_sm(int precision);
+// ovf: int[2 + tiles] scratch (tiles sent to the global-memory tier over the
+// run, the stage's count, then the tiles that overflowed the shared-memory
+// staging); big: classify_big_bytes() of global scratch for that tier
 int launch_classify(const Model &M, const Batch &B, int precision, const TileSched &Q, int grid, int8_t *labels,
-                    int *tile_band, int *err, cudaStream_t st);
-int launch_band(const Model &M, const Batch &B, int8_t *labels, const int *tile_band, int *err, cudaStream_t st);
+                    int *tile_band, int *err, int *ovf, unsigned char *big, cudaStream_t st);
+size_t classify_big_bytes();
+int launch_band(const Model &M, const Batch &B, int8_t *labels, const int *tile_band, int *err, int *ovf,
+                unsigned char *big, cudaStream_t st);
 // exterior-only surface (eses_exterior.cu): state init, one sweep (sets *changed
 // when it reached new points), cavity points relabelled inside (counted)
 int launch_ext_init(const Batch &B, const int8_t *labels, uint8_t *ext, uint8_t *tile_open, cudaStream_t st);
@@ -74,7 +80,8 @@ int edge_chunk_max();
 // persistent: `grid` CTAs take tiles in the order of Q; `chunk` edges per pooled chunk
 int launch_edge_solve(const Model &M, const Batch &B, int precision, const TileSched &Q, int grid, int chunk,
                       const int8_t *labels, const int *edge_start, EdgeOut out, int *n_fail, int *err,
-                      long long *fail_log, cudaStream_t st);
+                      long long *fail_log, int *ovf, unsigned char *big, cudaStream_t st);
+size_t edges_big_bytes();
 int launch_edge_polish(const Model &M, const Batch &B, EdgeOut out, long long n_edges_total, const long long *medge,
                        double2 *term, cudaStream_t st);
 // triangle mesh of a one-molecule run (eses_mesh.cu): the case table to constant
@@ -111,9 +118,10 @@ int launch_adam(float *P, const float *g, float *m, float *v, int step, float lr
 int launch_tile_features(const Model &M, const Batch &B, float *feat, cudaStream_t st);
 int launch_tile_targets(const Batch &B, const int8_t *labels, uint8_t *target, cudaStream_t st);
 // mode 1: MLP + certificate, 2: certificate on every tile; need[t] = 1 for
-// tiles left to the exact classification; counts[0..1] += proposed, certified
+// tiles left to the exact classification; counts[0..1] += proposed, certified;
+// wait_limit: polls of each tensor-core wait (< 0: the default limit)
 int launch_propose(const Model &M, const Batch &B, int mode, const float *P, float z_far, int8_t *labels,
-                   int *tile_band, int *need, int *counts, int *err, cudaStream_t st);
+                   int *tile_band, int *need, int *counts, int *err, long long wait_limit, cudaStream_t st);
 // the proposer's tensor-core MLP on n rows of features (err |= ERR_TIMEOUT on a wait that ran out)
 int launch_mlp_forward_tc(const float *X, int n, const float *P, float *z, int *err, cudaStream_t st);
 int launch_compact(long long n, const int *need, const int *pos, int *list, cudaStream_t st);

@@ -206,7 +206,7 @@ __device__ __forceinline__ void tile_centre(const Grid &G, long long tile, doubl
 {
     int tc[3];
     tile_coords(G, tile, tc);
-    for (int a = 0; a < 3; ++a) t[a] = G.lo[a] + G.h * ((double)(TILE * tc[a]) + 0.5 * (TILE - 1));
+    for (int a = 0; a < 3; ++a) t[a] = G.lo[a] + G.h * ((double)(TILE * (tc[a] + G.toff[a])) + 0.5 * (TILE - 1));
 }
 
 __device__ __forceinline__ long long floor_ll(double v) { return (long long)floor(v); }
@@ -304,7 +304,7 @@ __device__ int certify_tile(const Model &M, const Grid &G, int mol, long long ti
     const float icell = 1.0f / (float)M.cell;
     const float reach = (delta + (float)M.Rmax + 1e-2f) * icell;
     for (int a = 0; a < 3; ++a) {
-        const double rel = G.h * ((double)(TILE * tc[a]) + 0.5 * (TILE - 1));
+        const double rel = G.h * ((double)(TILE * (tc[a] + G.toff[a])) + 0.5 * (TILE - 1));
         th[a] = (float)rel;
         tl[a] = (float)(rel - (double)th[a]);
         const float u = ((float)(G.lo[a] - cg.clo[a]) + th[a]) * icell;  // centre in cell units
@@ -342,7 +342,8 @@ __device__ int certify_tile(const Model &M, const Grid &G, int mol, long long ti
 __global__ void __launch_bounds__(PROP_THREADS) k_propose(Model M, Batch B, int mode, const float *__restrict__ Pg,
                                                           float z_far, int8_t *__restrict__ labels_all,
                                                           int *__restrict__ tile_band, int *__restrict__ need,
-                                                          int *__restrict__ counts, int *__restrict__ err)
+                                                          int *__restrict__ counts, int *__restrict__ err,
+                                                          long long wait_limit)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TcSmem &T = *reinterpret_cast<TcSmem *>(smem_raw);
@@ -350,7 +351,7 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propose(Model M, Batch B, int 
     __shared__ int n_far;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t phase = 0;
-    if (mode == 1) tc_setup(T, Pg);
+    if (mode == 1) tc_setup(T, Pg, wait_limit);
     for (long long base = (long long)blockIdx.x * PROP_THREADS; base < B.n_tiles;
          base += (long long)gridDim.x * PROP_THREADS) {
         if (threadIdx.x == 0) n_far = 0;
@@ -497,10 +498,10 @@ static int tc_grid(long long rows)
 }
 
 int launch_propose(const Model &M, const Batch &B, int mode, const float *P, float z_far, int8_t *labels,
-                   int *tile_band, int *need, int *counts, int *err, cudaStream_t st)
+                   int *tile_band, int *need, int *counts, int *err, long long wait_limit, cudaStream_t st)
 {
     k_propose<<<tc_grid(B.n_tiles), PROP_THREADS, sizeof(TcSmem), st>>>(M, B, mode, P, z_far, labels, tile_band, need,
-                                                                       counts, err);
+                                                                       counts, err, wait_limit);
     return 1;
 }
 

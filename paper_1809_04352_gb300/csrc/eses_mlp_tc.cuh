@@ -36,6 +36,7 @@ struct TcSmem {
     alignas(8) unsigned long long mbar;
     uint32_t tmem;
     int dead;  // a wait ran out: no further tensor-core work in this CTA
+    long long wait_limit;  // iterations of each scoring wait (tc_teardown always waits TC_WAIT_LIMIT)
 };
 
 // byte offset of element (r, k) of a K-major matrix with K columns (canonical, no swizzle)
@@ -82,11 +83,12 @@ __device__ __forceinline__ void mbar_init(unsigned long long *mbar, int count)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
 }
 
-// bounded wait for the phase with the given parity; false when the limit ran out
-__device__ __forceinline__ bool mbar_wait(unsigned long long *mbar, uint32_t parity)
+// bounded wait for the phase with the given parity (at most `limit` polls);
+// false when the limit ran out
+__device__ __forceinline__ bool mbar_wait(unsigned long long *mbar, uint32_t parity, long long limit = TC_WAIT_LIMIT)
 {
     const uint32_t a = smem_u32(mbar);
-    for (long long it = 0; it < TC_WAIT_LIMIT; ++it) {
+    for (long long it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -132,8 +134,10 @@ __device__ __forceinline__ void tmem_free(uint32_t taddr)
 }
 
 // weights into shared memory (BF16, transposed to N x K, K-major) and biases;
-// TMEM allocation and mbarrier set-up.  Whole CTA (128 threads); ends with a barrier.
-__device__ void tc_setup(TcSmem &T, const float *__restrict__ P)
+// TMEM allocation and mbarrier set-up.  wait_limit: polls of each scoring wait
+// (< 0: TC_WAIT_LIMIT; 0 makes every scoring wait give up at once, which only
+// a test of the fallback wants).  Whole CTA (128 threads); ends with a barrier.
+__device__ void tc_setup(TcSmem &T, const float *__restrict__ P, long long wait_limit = -1)
 {
     for (int e = threadIdx.x; e < MLP_H * MLP_IN; e += blockDim.x) {
         const int n = e / MLP_IN, k = e % MLP_IN;
@@ -151,6 +155,7 @@ __device__ void tc_setup(TcSmem &T, const float *__restrict__ P)
     if (threadIdx.x == 0) {
         T.b3 = P[P_B3];
         T.dead = 0;
+        T.wait_limit = wait_limit < 0 ? TC_WAIT_LIMIT : wait_limit;
         mbar_init(&T.mbar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -202,7 +207,7 @@ __device__ float tc_score(TcSmem &T, const float *x, bool valid, uint32_t &phase
                    s > 0);
         tc_commit(&T.mbar);
     }
-    bool ok = __all_sync(0xffffffffu, mbar_wait(&T.mbar, phase));
+    bool ok = __all_sync(0xffffffffu, mbar_wait(&T.mbar, phase, T.wait_limit));
     tc_fence_after();
     const uint32_t lane_base = (uint32_t)((t >> 5) * 32) << 16;
     // layer 1 epilogue: bias, ReLU, BF16 into row t of A2
@@ -241,7 +246,7 @@ __device__ float tc_score(TcSmem &T, const float *x, bool valid, uint32_t &phase
                    s > 0);
         tc_commit(&T.mbar);
     }
-    ok = __all_sync(0xffffffffu, mbar_wait(&T.mbar, phase));
+    ok = __all_sync(0xffffffffu, mbar_wait(&T.mbar, phase, T.wait_limit));
     tc_fence_after();
     float z = T.b3;
     if (ok) {

@@ -136,8 +136,12 @@ __device__ __forceinline__ void warp_neighbour_cells(const Model &M, int mol, do
 
 constexpr int NB_WARPS = 4;  // warps (atoms) per block of the neighbour and pair kernels
 
-// the circle where expanded spheres (ci, Ri) and (cj, Rj) meet, if any
-__device__ __forceinline__ bool circle_of(double4 ci, double Ri, double4 cj, double Rj, double3 &o, double3 &u,
+// the circle where expanded spheres (ci, Ri) and (cj, Rj) meet, if any.  Kept
+// out of line, like frame_of and cover_of, so that every kernel and every
+// path computes a circle or a triple point with the same instructions (the
+// same rounding and contraction): counts and fills agree, and the bits do not
+// depend on which path a model took.
+__device__ __noinline__ bool circle_of(double4 ci, double Ri, double4 cj, double Rj, double3 &o, double3 &u,
                                           double &rho)
 {
     double dx = cj.x - ci.x, dy = cj.y - ci.y, dz = cj.z - ci.z;
@@ -153,6 +157,17 @@ __device__ __forceinline__ bool circle_of(double4 ci, double Ri, double4 cj, dou
     o = make_double3(ci.x + a * u.x, ci.y + a * u.y, ci.z + a * u.z);
     rho = sqrt(rho2);
     return true;
+}
+
+// The circle of atoms i and j, computed from the one with the smaller input
+// index (axis from it to the other): the same bits whatever the atoms' places
+// in the cell sort, so any model holding both atoms -- a subset of the atoms
+// on the same grid included -- has the same circle.
+__device__ __forceinline__ bool circle_canon(const Model &M, int i, int j, const double4 &ci, double Ri,
+                                             const double4 &cj, double Rj, double3 &o, double3 &u, double &rho)
+{
+    const bool sw = M.atom_orig[i] > M.atom_orig[j];
+    return circle_of(sw ? cj : ci, sw ? Rj : Ri, sw ? ci : cj, sw ? Ri : Rj, o, u, rho);
 }
 
 // One warp per atom: neighbours (expanded spheres that overlap), circles, and
@@ -178,7 +193,7 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_nb_count(Model M, int *__rest
             ++nb;
             double3 o, u;
             double rho;
-            if (circle_of(ci, Ri, cj, Rj, o, u, rho)) ++nc;
+            if (circle_canon(M, i, j, ci, Ri, cj, Rj, o, u, rho)) ++nc;
             else if (Rj >= Ri && sqrt(D2) <= Rj - Ri) inside = true;  // ball i inside ball j
         }
     });
@@ -247,7 +262,7 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_pair_count(Model M, int *__re
         const double4 cj = M.atom[j];
         double3 o, u;
         double rho;
-        if (circle_of(ci, Ri, cj, cj.w + M.rp, o, u, rho)) ++c;
+        if (circle_canon(M, i, j, ci, Ri, cj, cj.w + M.rp, o, u, rho)) ++c;
     }
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if ((threadIdx.x & 31) == 0) pair_count[i] = c;
@@ -282,7 +297,7 @@ __global__ void __launch_bounds__(NB_WARPS * 32) k_pair_fill(Model M, const int 
             j = M.nb_list[t];
             if (j > i) {
                 const double4 cj = M.atom[j];
-                keep = circle_of(ci, Ri, cj, cj.w + M.rp, o, u, rho);
+                keep = circle_canon(M, i, j, ci, Ri, cj, cj.w + M.rp, o, u, rho);
             }
         }
         const unsigned m = __ballot_sync(0xffffffffu, keep);
@@ -313,7 +328,7 @@ struct CircleFrame {
     double rho;
 };
 
-__device__ __forceinline__ CircleFrame frame_of(double4 po, double4 pu)
+__device__ __noinline__ CircleFrame frame_of(double4 po, double4 pu)
 {
     CircleFrame f;
     f.o = make_double3(po.x, po.y, po.z);
@@ -331,7 +346,7 @@ __device__ __forceinline__ CircleFrame frame_of(double4 po, double4 pu)
 
 // Coverage of the circle by ball (ck, Rk): 0 none, 1 partial (end points
 // qa, qb returned), 2 the whole circle.
-__device__ __forceinline__ int cover_of(const CircleFrame &f, double4 ck, double Rk, double3 &qa, double3 &qb)
+__device__ __noinline__ int cover_of(const CircleFrame &f, double4 ck, double Rk, double3 &qa, double3 &qb)
 {
     double dx = ck.x - f.o.x, dy = ck.y - f.o.y, dz = ck.z - f.o.z;
     double d1 = dx * f.v1.x + dy * f.v1.y + dz * f.v1.z;
@@ -404,13 +419,15 @@ __device__ void arcs_of_pair(const Model &M, int p, uint8_t *pair_free, int *ver
             bool fa = endpoint_free(M, i, j, k, cj, Rj, qa);
             bool fb = endpoint_free(M, i, j, k, cj, Rj, qb);
             n_free_end += (int)fa + (int)fb;
-            if (k > j) {  // triple i < j < k: emitted once, from the circle (i, j)
+            // each triple point is emitted once: from the circle of the triple's two
+            // atoms with the smaller input indices (any cell order gives the same bits)
+            if (M.atom_orig[k] > M.atom_orig[i] && M.atom_orig[k] > M.atom_orig[j]) {
                 if (fa) {
-                    if (EMIT) vert[w + n_emit] = make_double4(qa.x, qa.y, qa.z, 0.0);
+                    if (EMIT) vert[w + n_emit] = make_double4(qa.x, qa.y, qa.z, (double)k);
                     ++n_emit;
                 }
                 if (fb) {
-                    if (EMIT) vert[w + n_emit] = make_double4(qb.x, qb.y, qb.z, 0.0);
+                    if (EMIT) vert[w + n_emit] = make_double4(qb.x, qb.y, qb.z, (double)k);
                     ++n_emit;
                 }
             }
@@ -611,7 +628,9 @@ __device__ void arcs_of_pair_warp(const Model &M, int p, ArcWarp &W, uint8_t *pa
         full = full || __any_sync(full_mask, status == 2);
         if (full) break;  // uniform
         int np_ = status == 1 ? 1 : 0, nf_ = (int)fr[0] + (int)fr[1];
-        const bool emits = status == 1 && a < n && W.nbk[a] > j;  // triple i < j < k: emitted once, here
+        // emitted once: from the circle of the two atoms with the smaller input indices
+        const bool emits = status == 1 && a < n && M.atom_orig[W.nbk[a]] > M.atom_orig[i] &&
+                           M.atom_orig[W.nbk[a]] > M.atom_orig[j];
         int ne_ = emits ? nf_ : 0;
         // inclusive scan of ne_ over the lanes (the serial order a = 0, 1, ...)
         int inc = ne_;
@@ -630,8 +649,9 @@ __device__ void arcs_of_pair_warp(const Model &M, int p, ArcWarp &W, uint8_t *pa
                 cover_of(f, ck, ck.w + M.rp, qe[0], qe[1]);
             }
             int wpos = w0 + n_emit_total + inc - ne_;
+            const double kw = (double)W.nbk[a];  // the triple's third atom
             for (int e = 0; e < 2; ++e)
-                if (fr[e]) vert[wpos++] = make_double4(qe[e].x, qe[e].y, qe[e].z, 0.0);
+                if (fr[e]) vert[wpos++] = make_double4(qe[e].x, qe[e].y, qe[e].z, kw);
         }
         n_emit_total += tot;
         for (int o = 16; o > 0; o >>= 1) {
@@ -659,8 +679,11 @@ __global__ void __launch_bounds__(ARC_WARPS * 32) k_arcs(Model M, uint8_t *__res
     arcs_of_pair_warp<false>(M, p, W[warp], pair_free, vert_count, nullptr, nullptr);
 }
 
+// emits the free triple points of circle p (xyz, third atom in w), their
+// molecule and their three atoms (i, j of the circle, k; sorted indices)
 __global__ void __launch_bounds__(ARC_WARPS * 32) k_arcs_emit(Model M, const int *__restrict__ vert_start,
-                                                              double4 *__restrict__ vert, int *__restrict__ vert_mol)
+                                                              double4 *__restrict__ vert, int *__restrict__ vert_mol,
+                                                              int4 *__restrict__ vert_atoms)
 {
     __shared__ ArcWarp W[ARC_WARPS];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -668,8 +691,13 @@ __global__ void __launch_bounds__(ARC_WARPS * 32) k_arcs_emit(Model M, const int
     if (p >= M.n_pairs) return;
     if (vert_start[p + 1] == vert_start[p]) return;
     arcs_of_pair_warp<true>(M, p, W[warp], nullptr, nullptr, vert_start, vert);
-    const int mol = M.atom_mol[M.pair_ij[p].x];
-    for (int k = vert_start[p] + lane; k < vert_start[p + 1]; k += 32) vert_mol[k] = mol;
+    __syncwarp();
+    const int2 ij = M.pair_ij[p];
+    const int mol = M.atom_mol[ij.x];
+    for (int k = vert_start[p] + lane; k < vert_start[p + 1]; k += 32) {
+        vert_mol[k] = mol;
+        vert_atoms[k] = make_int4(ij.x, ij.y, (int)vert[k].w, 0);
+    }
 }
 
 int launch_arcs(const Model &M, uint8_t *pair_free, int *vert_count, cudaStream_t st)
@@ -679,10 +707,12 @@ int launch_arcs(const Model &M, uint8_t *pair_free, int *vert_count, cudaStream_
     return 1;
 }
 
-int launch_arcs_emit(const Model &M, const int *vert_start, double4 *vert, int *vert_mol, cudaStream_t st)
+int launch_arcs_emit(const Model &M, const int *vert_start, double4 *vert, int *vert_mol, int4 *vert_atoms,
+                     cudaStream_t st)
 {
     if (M.n_pairs <= 0) return 0;
-    k_arcs_emit<<<(M.n_pairs + ARC_WARPS - 1) / ARC_WARPS, ARC_WARPS * 32, 0, st>>>(M, vert_start, vert, vert_mol);
+    k_arcs_emit<<<(M.n_pairs + ARC_WARPS - 1) / ARC_WARPS, ARC_WARPS * 32, 0, st>>>(M, vert_start, vert, vert_mol,
+                                                                                  vert_atoms);
     return 1;
 }
 
@@ -714,7 +744,9 @@ int launch_faces(const Model &M, const int *circle_count, const uint8_t *contain
 }
 
 // which = 0: free-arc pairs by circle centre; which = 1: free triple points
-__global__ void k_bin_count(Model M, int which, int *__restrict__ count, int *__restrict__ item_cell)
+// cull: bin only the circles that keep a free arc (buried saddle patches are
+// culled before the classification); without it every circle is binned
+__global__ void k_bin_count(Model M, int which, bool cull, int *__restrict__ count, int *__restrict__ item_cell)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     int n = which == 0 ? M.n_pairs : M.n_verts;
@@ -722,7 +754,7 @@ __global__ void k_bin_count(Model M, int which, int *__restrict__ count, int *__
     double x, y, z;
     int mol;
     if (which == 0) {
-        if (!M.pair_free[p]) {
+        if (cull && !M.pair_free[p]) {
             item_cell[p] = -1;
             return;
         }
@@ -810,11 +842,11 @@ int launch_model_f32(const Model &M, int which, const Grid *grids, float4 *hi, f
     return 1;
 }
 
-int launch_bin_count(const Model &M, int which, int *count, int *item_cell, cudaStream_t st)
+int launch_bin_count(const Model &M, int which, bool cull, int *count, int *item_cell, cudaStream_t st)
 {
     int n = which == 0 ? M.n_pairs : M.n_verts;
     if (n <= 0) return 0;
-    k_bin_count<<<(n + 255) / 256, 256, 0, st>>>(M, which, count, item_cell);
+    k_bin_count<<<(n + 255) / 256, 256, 0, st>>>(M, which, cull, count, item_cell);
     return 1;
 }
 

@@ -44,19 +44,22 @@ struct alignas(16) P4 {
 };
 
 constexpr int STAGE_CELLS = 128;  // cells staged with item-parallel scan (else one thread per cell)
-constexpr int AW = (A_MAX + 31) / 32;  // words of a set of staged atoms (bit k: staged slot k)
+// words of a set of staged atoms (bit k: staged slot k) for capacity C
+template <class C>
+__host__ __device__ constexpr int atom_words() { return (C::A + 31) / 32; }
+constexpr int AW = atom_words<CapSmall>();
 
-template <class T>
+template <class T, class C = CapSmall>
 struct TileS {
-    P4<T> atom[A_MAX];      // centre (tile frame), vdW radius
-    P4<T> po[P_MAX];        // circle centre (tile frame), rho
-    P4<T> pu[P_MAX];        // circle axis
-    P4<T> vq[V_MAX];        // free triple point (tile frame)
-    int agid[A_MAX];        // sorted atom index
-    int2 pij[P_MAX];        // sorted atom indices of the pair
-    int pidx[P_MAX];        // pair index in the model
-    int vidx[V_MAX];        // triple point index in the model
-    uint8_t aface[A_MAX];   // expanded sphere keeps a free face
+    P4<T> atom[C::A];       // centre (tile frame), vdW radius
+    P4<T> po[C::P];         // circle centre (tile frame), rho
+    P4<T> pu[C::P];         // circle axis
+    P4<T> vq[C::V];         // free triple point (tile frame)
+    int agid[C::A];         // sorted atom index
+    int2 pij[C::P];         // sorted atom indices of the pair
+    int pidx[C::P];         // pair index in the model
+    int vidx[C::V];         // triple point index in the model
+    uint8_t aface[C::A];    // expanded sphere keeps a free face
     int cid[STAGE_CELLS];           // cells of the staging range
     int cs[3][STAGE_CELLS + 1];     // prefix of their atoms / pairs / vertices
     double fx0[3], fx1[3];          // tile region (absolute), computed once per tile
@@ -68,11 +71,11 @@ struct TileS {
 // ---------------------------------------------------------------------------
 // accessors: staged (shared memory) or exact (FP64 from HBM, same tile frame)
 // ---------------------------------------------------------------------------
-template <class T>
+template <class T, class C = CapSmall>
 struct SmemAcc {
     using real = T;
-    const TileS<T> &S;
-    __device__ SmemAcc(const TileS<T> &s) : S(s) {}
+    const TileS<T, C> &S;
+    __device__ SmemAcc(const TileS<T, C> &s) : S(s) {}
     __device__ int na() const { return S.na; }
     __device__ int np() const { return S.np; }
     __device__ int nv() const { return S.nv; }
@@ -85,13 +88,14 @@ struct SmemAcc {
     __device__ P4<T> vq(int v) const { return S.vq[v]; }
 };
 
-template <class TS>
+template <class TS, class C = CapSmall>
 struct ExactAcc {
     using real = double;
-    const TileS<TS> &S;
+    const TileS<TS, C> &S;
     const Model &M;
     double x0, y0, z0;
-    __device__ ExactAcc(const TileS<TS> &s, const Model &m, const double *o) : S(s), M(m), x0(o[0]), y0(o[1]), z0(o[2]) {}
+    __device__ ExactAcc(const TileS<TS, C> &s, const Model &m, const double *o)
+        : S(s), M(m), x0(o[0]), y0(o[1]), z0(o[2]) {}
     __device__ int na() const { return S.na; }
     __device__ int np() const { return S.np; }
     __device__ int nv() const { return S.nv; }
@@ -158,8 +162,8 @@ __device__ __forceinline__ float box_dist2f(float x, float y, float z, const flo
     return ex * ex + ey * ey + ez * ez;
 }
 
-template <class T>
-__device__ __forceinline__ void stage_item(const Model &M, TileS<T> &S, int list, int k, const StageFrame &F)
+template <class T, class C>
+__device__ __forceinline__ void stage_item(const Model &M, TileS<T, C> &S, int list, int k, const StageFrame &F)
 {
     const double rp = M.rp;
     if constexpr (sizeof(T) == sizeof(float)) {
@@ -254,15 +258,15 @@ __device__ __forceinline__ void stage_item(const Model &M, TileS<T> &S, int list
 // least 96 threads).
 // The items of every cell in range are numbered by a prefix over the cells
 // and tested one per thread, so all threads share the work.
-template <class T>
-__device__ void stage_tile(const Model &M, const Grid &G, int mol, long long tile, TileS<T> &S, double x0[3])
+template <class T, class C>
+__device__ void stage_tile(const Model &M, const Grid &G, int mol, long long tile, TileS<T, C> &S, double x0[3])
 {
     const CellGrid &CG = M.cg[mol];
     if (threadIdx.x < 6) {  // the tile frame, once per tile: one thread per axis and end
         int t[3];
         tile_coords(G, tile, t);
         const int a = threadIdx.x < 3 ? threadIdx.x : threadIdx.x - 3;
-        const double rel = G.h * (double)(TILE * t[a]);  // region origin in the grid frame
+        const double rel = G.h * (double)(TILE * (t[a] + G.toff[a]));  // region origin in the grid frame
         const double fx0 = G.lo[a] + rel, fx1 = fx0 + G.h * (double)TILE;
         // cell range of the region plus halo: FP32 indices with 1e-2 A of room
         // for their rounding (an FP64 division costs more than the rest)
@@ -355,9 +359,9 @@ __device__ void stage_tile(const Model &M, const Grid &G, int mol, long long til
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        if (S.na > A_MAX) { S.flags |= ERR_CAP_ATOMS; S.na = A_MAX; }
-        if (S.np > P_MAX) { S.flags |= ERR_CAP_PAIRS; S.np = P_MAX; }
-        if (S.nv > V_MAX) { S.flags |= ERR_CAP_VERTS; S.nv = V_MAX; }
+        if (S.na > C::A) { S.flags |= ERR_CAP_ATOMS; S.na = C::A; }
+        if (S.np > C::P) { S.flags |= ERR_CAP_PAIRS; S.np = C::P; }
+        if (S.nv > C::V) { S.flags |= ERR_CAP_VERTS; S.nv = C::V; }
     }
     __syncthreads();
 }
@@ -435,19 +439,27 @@ __device__ __noinline__ int free_set(const Acc &A, T qx, T qy, T qz, const unsig
 }
 
 // Staged slots of every staged pair's two atoms (-1: atom not staged), by an
-// open-addressing hash of the staged atoms' model indices (hkey[SLOT_HASH],
-// hval[SLOT_HASH] scratch).  Whole block; ends with a barrier.
-constexpr int SLOT_HASH = 1024;  // power of two > 2 A_MAX
-__device__ __forceinline__ unsigned slot_hash(int key) { return ((unsigned)key * 2654435761u) & (SLOT_HASH - 1); }
-
-template <class T>
-__device__ void pair_slots(const TileS<T> &S, int *hkey, short *hval, short2 *pslot)
+// open-addressing hash of the staged atoms' model indices (hkey[slot_hash_size],
+// hval[slot_hash_size] scratch).  Whole block; ends with a barrier.
+template <class C>
+__host__ __device__ constexpr int slot_hash_size()  // a power of two > 2 C::A
 {
-    for (int k = threadIdx.x; k < SLOT_HASH; k += blockDim.x) hkey[k] = -1;
+    int n = 1;
+    while (n <= 2 * C::A) n <<= 1;
+    return n;
+}
+constexpr int SLOT_HASH = slot_hash_size<CapSmall>();
+
+template <class T, class C>
+__device__ void pair_slots(const TileS<T, C> &S, int *hkey, short *hval, short2 *pslot)
+{
+    constexpr int HS = slot_hash_size<C>();
+    auto slot_hash = [](int key) { return ((unsigned)key * 2654435761u) & (unsigned)(HS - 1); };
+    for (int k = threadIdx.x; k < HS; k += blockDim.x) hkey[k] = -1;
     __syncthreads();
     for (int a = threadIdx.x; a < S.na; a += blockDim.x) {
         const int key = S.agid[a];
-        for (unsigned h = slot_hash(key);; h = (h + 1) & (SLOT_HASH - 1)) {
+        for (unsigned h = slot_hash(key);; h = (h + 1) & (HS - 1)) {
             const int prev = atomicCAS(&hkey[h], -1, key);
             if (prev == -1 || prev == key) {
                 hval[h] = (short)a;
@@ -459,12 +471,12 @@ __device__ void pair_slots(const TileS<T> &S, int *hkey, short *hval, short2 *ps
     for (int p = threadIdx.x; p < S.np; p += blockDim.x) {
         const int2 ij = S.pij[p];
         short si = -1, sj = -1;
-        for (unsigned h = slot_hash(ij.x);; h = (h + 1) & (SLOT_HASH - 1)) {
+        for (unsigned h = slot_hash(ij.x);; h = (h + 1) & (HS - 1)) {
             const int k = hkey[h];
             if (k == ij.x) { si = hval[h]; break; }
             if (k == -1) break;
         }
-        for (unsigned h = slot_hash(ij.y);; h = (h + 1) & (SLOT_HASH - 1)) {
+        for (unsigned h = slot_hash(ij.y);; h = (h + 1) & (HS - 1)) {
             const int k = hkey[h];
             if (k == ij.y) { sj = hval[h]; break; }
             if (k == -1) break;
@@ -474,13 +486,14 @@ __device__ void pair_slots(const TileS<T> &S, int *hkey, short *hval, short2 *ps
     __syncthreads();
 }
 
-// Neighbour sets of the staged atoms (whole block): bit b of nbm[a * AW + w]
+// Neighbour sets of the staged atoms (whole block): bit b of nbm[a * aw + w]
 // (b = 32 w + bit) is set when the expanded spheres of staged atoms a != b
 // come within 1e-3 A of meeting (the margin covers the rounding of staged
 // FP32 positions, so no true neighbour is left out).
-template <class T>
-__device__ __forceinline__ void build_neighbour_sets(const TileS<T> &S, unsigned *nbm, T rp)
+template <class T, class C>
+__device__ __forceinline__ void build_neighbour_sets(const TileS<T, C> &S, unsigned *nbm, T rp)
 {
+    constexpr int aw = atom_words<C>();
     const int na = S.na, nw = (na + 31) >> 5;
     for (int it = threadIdx.x; it < na * nw; it += blockDim.x) {
         const int a = it / nw, w = it - a * nw;
@@ -494,7 +507,7 @@ __device__ __forceinline__ void build_neighbour_sets(const TileS<T> &S, unsigned
             const T reach = Ra + cb.w + rp;
             if (b != a && dx * dx + dy * dy + dz * dz < reach * reach) bits |= 1u << (b - b0);
         }
-        nbm[a * AW + w] = bits;
+        nbm[a * aw + w] = bits;
     }
 }
 
@@ -592,14 +605,15 @@ __device__ __forceinline__ int saddle_proposal(const Acc &A, int p, T x, T y, T 
 // 0 none, -1 undecided.  nbm: the staged atoms' neighbour sets; the
 // projection's freeness is tested against a's neighbours (free_set).
 template <bool FILT, class Acc, class T>
-__device__ __noinline__ int face_witness(const Acc &A, int a, T x, T y, T z, T rp, T thr, T d0, const unsigned *nbm)
+__device__ __noinline__ int face_witness(const Acc &A, int a, T x, T y, T z, T rp, T thr, T d0, const unsigned *nbm,
+                                         int aw)
 {
     T qx, qy, qz, dq;
     int e0, e1;
     const int tw = face_proposal<FILT>(A, a, x, y, z, rp, thr, d0, qx, qy, qz, dq, e0, e1);
     if (tw == 0) return 0;
     if (tw == -2) return -1;
-    int f = free_set<FILT>(A, qx, qy, qz, nbm + a * AW, (const unsigned *)nullptr, rp, dq + d0);
+    int f = free_set<FILT>(A, qx, qy, qz, nbm + a * aw, (const unsigned *)nullptr, rp, dq + d0);
     if (f == 1 && tw == 1) return 1;
     return f == 0 ? 0 : -1;
 }
@@ -609,14 +623,14 @@ __device__ __noinline__ int face_witness(const Acc &A, int a, T x, T y, T z, T r
 // sa, sb).
 template <bool FILT, class Acc, class T>
 __device__ __noinline__ int saddle_witness(const Acc &A, int p, T x, T y, T z, T rp, T thr, T d0, const unsigned *nbm,
-                                           int sa, int sb)
+                                           int aw, int sa, int sb)
 {
     T qx, qy, qz, dq;
     int e0, e1;
     const int t = saddle_proposal<FILT>(A, p, x, y, z, rp, thr, d0, qx, qy, qz, dq, e0, e1);
     if (t == 0) return 0;
     if (t == -2) return -1;
-    int f = free_set<FILT>(A, qx, qy, qz, nbm + sa * AW, nbm + sb * AW, rp, dq + d0);
+    int f = free_set<FILT>(A, qx, qy, qz, nbm + sa * aw, nbm + sb * aw, rp, dq + d0);
     if (f == 1 && t == 1) return 1;
     return f == 0 ? 0 : -1;
 }
@@ -713,7 +727,8 @@ __device__ __noinline__ int warp_witness(const Acc &A, T x, T y, T z, T rp, T th
         if (t == 1) found = true;
         else if (t < 0) {
             und = true;
-            um_vert |= 1u << (v >> 5);
+            if ((v >> 5) < 32) um_vert |= 1u << (v >> 5);
+            else um_vert = ~0u, um_prop = ~0u;  // beyond the masks: the retest takes every item
         }
     }
     if (__any_sync(full, found)) return 1;
@@ -733,7 +748,10 @@ __device__ __noinline__ int warp_witness(const Acc &A, T x, T y, T z, T rp, T th
         const unsigned m = __ballot_sync(full, tw != 0);
         bool mine = false;
         if (warp_test_proposals<FILT>(A, m, tw, qx, qy, qz, dq, e0, e1, rp, d0, und, mine) == 1) return 1;
-        if (mine) um_prop |= 1u << (i0 >> 5);
+        if (mine) {
+            if ((i0 >> 5) < 32) um_prop |= 1u << (i0 >> 5);
+            else um_vert = ~0u, um_prop = ~0u;  // beyond the masks: the retest takes every item
+        }
     }
     return und ? -1 : 0;
 }
@@ -751,8 +769,11 @@ __device__ __noinline__ int warp_witness_retest(const Acc &X, double x, double y
     const int lane = threadIdx.x & 31;
     const int na = X.na(), np = X.np(), nv = X.nv();
     bool found = false;
+    // items past the masks' 32 words are retested when the lane's masks are
+    // the "every item" mark that warp_witness leaves for them
+    const bool all = um_vert == ~0u && um_prop == ~0u;
     for (int v = lane; v < nv; v += 32) {
-        if (!((um_vert >> (v >> 5)) & 1u)) continue;
+        if (!((v >> 5) < 32 ? ((um_vert >> (v >> 5)) & 1u) : all)) continue;
         const P4<double> q = X.vq(v);
         const double dx = x - q.x, dy = y - q.y, dz = z - q.z;
         if (dx * dx + dy * dy + dz * dz < thr * thr) found = true;
@@ -762,7 +783,7 @@ __device__ __noinline__ int warp_witness_retest(const Acc &X, double x, double y
         const int i = i0 + lane;
         double qx = 0.0, qy = 0.0, qz = 0.0, dq = 0.0;
         int e0 = -1, e1 = -1, tw = 0;
-        if ((um_prop >> (i0 >> 5)) & 1u) {
+        if (i < na + np && ((i0 >> 5) < 32 ? ((um_prop >> (i0 >> 5)) & 1u) : all)) {
             if (i < na) tw = face_proposal<false>(X, i, x, y, z, rp, thr, 0.0, qx, qy, qz, dq, e0, e1);
             else tw = saddle_proposal<false>(X, i - na, x, y, z, rp, thr, 0.0, qx, qy, qz, dq, e0, e1);
         }

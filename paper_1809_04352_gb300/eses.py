@@ -39,6 +39,9 @@ ESES_OPT_EDGE_CTAS = 10
 ESES_OPT_EDGE_TILES = 11
 ESES_OPT_EDGE_CHUNK = 12
 ESES_OPT_EXTERIOR = 13
+ESES_OPT_TC_WAIT = 14
+ESES_OPT_FAIL_ALLOC = 15
+ESES_OPT_CULL = 16
 
 ESES_PROPOSER_OFF = 0
 ESES_PROPOSER_MLP = 1
@@ -50,7 +53,7 @@ ESES_PREC_FP32_FILTERED = 1
 
 STAT_NAMES = ["points", "tiles", "work_tiles", "circle_pairs", "free_arc_pairs", "free_vertices", "band_points",
               "crossing_edges", "root_failures", "inside_points", "kernel_launches", "tiles_proposed_far",
-              "tiles_certified", "cavity_points", "exterior_sweeps"]
+              "tiles_certified", "cavity_points", "exterior_sweeps", "big_tier_tiles"]
 
 # every exported C symbol, as declared in include/eses.h
 SYMBOLS = ["eses_create", "eses_create_device", "eses_create_batch", "eses_run_batch", "eses_set_option",
@@ -61,7 +64,9 @@ SYMBOLS = ["eses_create", "eses_create_device", "eses_create_batch", "eses_run_b
            "eses_area_volume", "eses_stats", "eses_stage_times", "eses_root_failures", "eses_patch_counts",
            "eses_patch_data", "eses_crossing_edges_noalloc", "eses_set_proposer", "eses_num_tiles",
            "eses_tile_data", "eses_mlp_forward", "eses_mlp_forward_tc", "eses_mlp_grad_scratch", "eses_mlp_grad", "eses_mlp_adam",
-           "eses_mesh_count", "eses_mesh", "eses_mesh_table", "eses_last_error", "eses_destroy"]
+           "eses_mesh_count", "eses_mesh", "eses_mesh_table", "eses_intersection_patches", "eses_create_on_grid",
+           "eses_num_blocks", "eses_set_blocks", "eses_owned_box",
+           "eses_mol_intersection_patches", "eses_last_error", "eses_destroy"]
 STAGE_NAMES = ["binning", "pairs", "arcs", "classify", "band", "edge_count", "edge_solve", "edge_polish", "reduce"]
 
 _lib = None
@@ -126,6 +131,12 @@ def load():
     lib.eses_patch_counts.argtypes = [P, P, P, P]
     lib.eses_patch_data.argtypes = [P, P, P, P, P]
     lib.eses_crossing_edges_noalloc.argtypes = [P, P, P, P, P, P, P, P]
+    lib.eses_intersection_patches.argtypes = [P, ci, P, P]
+    lib.eses_create_on_grid.argtypes = [P, P, i64, d, d, P, P, PP]
+    lib.eses_num_blocks.argtypes = [P, P]
+    lib.eses_set_blocks.argtypes = [P, P, P]
+    lib.eses_owned_box.argtypes = [P, P, P]
+    lib.eses_mol_intersection_patches.argtypes = [P, ci, ci, P, P]
     lib.eses_mesh_count.argtypes = [P, P]
     lib.eses_mesh.argtypes = [P, P, P]
     lib.eses_mesh_table.argtypes = [P, P]
@@ -171,6 +182,44 @@ def eses_create(xyz, radii, r_p: float, h: float, margin: float):
     out = ctypes.c_void_p()
     _check(lib.eses_create(_ptr(xyz), _ptr(radii), xyz.shape[0], r_p, h, margin, ctypes.byref(out)))
     return out
+
+
+def eses_create_on_grid(xyz, radii, r_p: float, h: float, origin, dims):
+    """Host atoms on a caller-given grid (origin float64[3], dims int64[3]) -> context handle."""
+    lib = load()
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+    radii = np.ascontiguousarray(radii, dtype=np.float64).reshape(-1)
+    if xyz.shape[0] != radii.shape[0]:
+        raise ValueError("xyz and radii disagree in length")
+    o = np.ascontiguousarray(origin, dtype=np.float64).reshape(3)
+    dm = np.ascontiguousarray(dims, dtype=np.int64).reshape(3)
+    out = ctypes.c_void_p()
+    _check(lib.eses_create_on_grid(_ptr(xyz), _ptr(radii), xyz.shape[0], r_p, h, _ptr(o), _ptr(dm),
+                                   ctypes.byref(out)))
+    return out
+
+
+def eses_num_blocks(ctx):
+    nb = np.zeros(3, np.int64)
+    _check(load().eses_num_blocks(ctx, _ptr(nb)), ctx)
+    return nb
+
+
+def eses_set_blocks(ctx, block_lo=None, block_hi=None):
+    """Restrict the next runs to blocks [block_lo, block_hi) per axis (None, None: the whole grid)."""
+    if block_lo is None:
+        _check(load().eses_set_blocks(ctx, None, None), ctx)
+        return
+    lo = np.ascontiguousarray(block_lo, dtype=np.int64).reshape(3)
+    hi = np.ascontiguousarray(block_hi, dtype=np.int64).reshape(3)
+    _check(load().eses_set_blocks(ctx, _ptr(lo), _ptr(hi)), ctx)
+
+
+def eses_owned_box(ctx):
+    lo = np.zeros(3, np.int64)
+    dims = np.zeros(3, np.int64)
+    _check(load().eses_owned_box(ctx, _ptr(lo), _ptr(dims)), ctx)
+    return lo, dims
 
 
 def eses_create_device(xyz, radii, n_atoms: int, r_p: float, h: float, margin: float):
@@ -354,7 +403,8 @@ def eses_grid(ctx):
 
 
 def eses_labels(ctx, out=None):
-    dims, _ = eses_grid(ctx)
+    """Host copy of the labels: the whole grid, or the owned box of a block selection."""
+    _, dims = eses_owned_box(ctx)
     if out is None:
         out = np.empty(tuple(int(v) for v in dims), np.int8)
     _check(load().eses_labels(ctx, _ptr(out)), ctx)
@@ -416,6 +466,26 @@ def eses_intersections(ctx, axis: int, fp32: bool = True):
         out["tau32"] = t32
         out["normal32"] = n32
     return out
+
+
+def eses_intersection_patches(ctx, axis: int):
+    """Patch kind (int8 (n,)) and generating input atoms (int32 (n, 3), ascending,
+    -1 padded) of one axis' intersections, in the order of eses_intersections."""
+    n = eses_num_intersections(ctx, axis)
+    kind = np.empty(n, np.int8)
+    atoms = np.empty((n, 3), np.int32)
+    if n:
+        _check(load().eses_intersection_patches(ctx, axis, _ptr(kind), _ptr(atoms)), ctx)
+    return kind, atoms
+
+
+def eses_mol_intersection_patches(ctx, m: int, axis: int):
+    n = eses_mol_num_intersections(ctx, m, axis)
+    kind = np.empty(n, np.int8)
+    atoms = np.empty((n, 3), np.int32)
+    if n:
+        _check(load().eses_mol_intersection_patches(ctx, int(m), axis, _ptr(kind), _ptr(atoms)), ctx)
+    return kind, atoms
 
 
 def eses_intersections_device(ctx, axis: int):

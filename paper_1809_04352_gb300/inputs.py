@@ -17,6 +17,15 @@ Recipe:
 * "compacted" walks reject C-alpha steps that leave the sphere of radius
   (3N / (4 pi rho))^(1/3) - 2.5 A, giving a globule of density rho atoms/A^3;
 * random numbers from numpy's PCG64, seeded per workload and molecule.
+
+Paper-density variant (``paper_density``): the appendix table of the paper
+implies about 0.1 atoms per cubic Angstrom of enclosed volume, eight times the
+globules above.  A 3.0 A self-avoiding C-alpha walk with three side atoms per
+residue cannot reach that density (the walk traps itself), so the variant
+keeps the walk and fills the rest with side atoms: eight atoms per residue
+(the C-alpha and seven side atoms at 1.5-2.5 A, about the heavy-atom count of
+a real residue), the C-alpha walk confined to the sphere for rho = 0.1, and a
+trapped step backs the walk up four residues instead of restarting the chain.
 """
 from __future__ import annotations
 
@@ -31,6 +40,9 @@ STEP = 3.8
 MIN_CA = 3.0
 SIDE_MIN, SIDE_MAX = 1.5, 2.5
 PROTEIN_DENSITY = 0.0125  # atoms / A^3 of the compacted globules
+PAPER_DENSITY = 0.1       # atoms / A^3 of the paper-density variant
+DENSE_RESIDUE_ATOMS = 8   # C-alpha + 7 side atoms per residue in that variant
+DENSE_BACKTRACK = 4       # residues a trapped walk backs up
 
 
 def _unit_vectors(rng: np.random.Generator, n: int) -> np.ndarray:
@@ -80,6 +92,48 @@ def _ca_walk(rng: np.random.Generator, n_res: int, confine: float | None) -> np.
                 break
         if ok:
             return pts
+
+
+def _ca_walk_backtrack(rng: np.random.Generator, n_res: int, confine: float, back: int = DENSE_BACKTRACK,
+                       max_traps: int = 1_000_000) -> np.ndarray:
+    """Self-avoiding C-alpha walk (min spacing 3.0 A) confined to a sphere; a
+    step whose 100 tries all fail backs the walk up `back` residues."""
+    pts = np.zeros((n_res, 3))
+    k, traps = 1, 0
+    while k < n_res:
+        cand = pts[k - 1] + STEP * _unit_vectors(rng, 100)
+        ok = np.einsum("ij,ij->i", cand, cand) <= confine * confine
+        d = cand[:, None, :] - pts[None, :k, :]
+        ok &= (np.einsum("ijk,ijk->ij", d, d) >= MIN_CA * MIN_CA).all(axis=1)
+        hit = np.flatnonzero(ok)
+        if len(hit):
+            pts[k] = cand[hit[0]]
+            k += 1
+        else:
+            traps += 1
+            if traps > max_traps:
+                raise RuntimeError("confined walk did not finish")
+            k = max(1, k - back)
+    return pts
+
+
+def paper_density(n_atoms: int, seed: int, density: float = PAPER_DENSITY):
+    """Return (xyz, radii) of a globule at the paper's packing density: eight
+    atoms per residue, a confined C-alpha walk that backtracks when trapped
+    (recipe in the module docstring)."""
+    if n_atoms < 1:
+        raise ValueError("n_atoms must be >= 1")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    side = DENSE_RESIDUE_ATOMS - 1
+    n_res = (n_atoms + DENSE_RESIDUE_ATOMS - 1) // DENSE_RESIDUE_ATOMS
+    confine = max((3.0 * n_atoms / (4.0 * math.pi * density)) ** (1.0 / 3.0) - 2.5, STEP)
+    ca = _ca_walk_backtrack(rng, n_res, confine)
+    side_dir = _unit_vectors(rng, side * n_res).reshape(n_res, side, 3)
+    side_len = rng.uniform(SIDE_MIN, SIDE_MAX, size=(n_res, side, 1))
+    xyz = np.concatenate([ca[:, None, :], ca[:, None, :] + side_dir * side_len], axis=1).reshape(-1, 3)[:n_atoms]
+    types = rng.choice(4, size=xyz.shape[0], p=FREQS)
+    xyz = xyz - xyz.mean(axis=0, keepdims=True)
+    return np.ascontiguousarray(xyz), np.ascontiguousarray(RADII[types])
 
 
 def protein_like(n_atoms: int, seed: int, density: float | None = None):

@@ -149,3 +149,47 @@ class SampledFree:
         free = np.all(d2 >= self.R[None, :] ** 2, axis=1)
         d, _ = self.tree.query(x)
         return np.where(free, 0.0, d)
+
+
+def circle_of_spheres(ci, Ri, cj, Rj):
+    """Intersection circle of two spheres: centre, unit axis, radius (closed form)."""
+    d = cj - ci
+    D = np.linalg.norm(d)
+    u = d / D
+    a = (D * D + Ri * Ri - Rj * Rj) / (2.0 * D)
+    return ci + a * u, u, math.sqrt(max(Ri * Ri - a * a, 0.0))
+
+
+def trilaterate(c, R):
+    """The two points at distance R[k] from c[k], k = 0..2 (closed form)."""
+    ex = (c[1] - c[0]) / np.linalg.norm(c[1] - c[0])
+    i = ex @ (c[2] - c[0])
+    ey = c[2] - c[0] - i * ex
+    ey /= np.linalg.norm(ey)
+    ez = np.cross(ex, ey)
+    d = np.linalg.norm(c[1] - c[0])
+    j = ey @ (c[2] - c[0])
+    x = (R[0] ** 2 - R[1] ** 2 + d * d) / (2 * d)
+    y = (R[0] ** 2 - R[2] ** 2 + i * i + j * j) / (2 * j) - i * x / j
+    z = math.sqrt(max(R[0] ** 2 - x * x - y * y, 0.0))
+    base = c[0] + x * ex + y * ey
+    return base + z * ez, base - z * ez
+
+
+def patch_offset(xyz, rad, rp, p, kind, ids):
+    """|distance from p to the patch (kind, ids) - its radius|, by closed forms:
+    0 the van der Waals sphere of ids[0], 1 the torus of radius r_p around the
+    intersection circle of the pair's expanded spheres, 2 the probe sphere at
+    the nearer-fitting of the triple's two meeting points (inf for a bad kind)."""
+    R = np.asarray(rad) + rp
+    if kind == 0:
+        return abs(np.linalg.norm(p - xyz[ids[0]]) - rad[ids[0]])
+    if kind == 1:
+        o, u, rho = circle_of_spheres(xyz[ids[0]], R[ids[0]], xyz[ids[1]], R[ids[1]])
+        w = p - o
+        z = w @ u
+        return abs(math.hypot(math.sqrt(max(w @ w - z * z, 0.0)) - rho, z) - rp)
+    if kind == 2:
+        q1, q2 = trilaterate(xyz[list(ids[:3])], R[list(ids[:3])])
+        return min(abs(np.linalg.norm(p - q1) - rp), abs(np.linalg.norm(p - q2) - rp))
+    return math.inf

@@ -95,7 +95,7 @@ def _check(eses, g, o, h, xyz, rad):
         assert np.array_equal(ga["idx"][order], o.idx[a])
         if len(order):
             assert np.abs(ga["tau"][order] - o.tau[a]).max() * h < TAU_TOL_A
-            en = normal_error(xyz, rad, RP, ga["idx"][order], ga["tau"][order], ga["normal"][order], o.normal[a],
+            en, _ = normal_error(xyz, rad, RP, ga["idx"][order], ga["tau"][order], ga["normal"][order], o.normal[a],
                               o.dims, o.lo, h, a)
             assert en.max() < 1e-6
     assert abs(g["area"] - o.area) <= 1e-9 * max(o.area, 1.0)

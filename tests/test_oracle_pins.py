@@ -21,7 +21,7 @@ import numpy as np
 import pytest
 
 import oracle
-from tests.exact_geometry import SampledFree, TwoAtoms, sphere_first_root
+from tests.exact_geometry import SampledFree, TwoAtoms, circle_of_spheres, sphere_first_root, trilaterate
 from paper_1809_04352_gb300 import inputs
 
 RP = 1.4
@@ -389,3 +389,42 @@ def test_coincident_atoms_are_one_ball():
     for a in range(3):
         assert np.array_equal(one.idx[a], rep.idx[a]) and np.array_equal(one.tau[a], rep.tau[a])
     assert one.area == rep.area and one.volume == rep.volume
+
+
+# ------------------------------------------------- patch atoms of each root
+def test_intersection_patch_atoms_generate_the_surface_point():
+    """Every intersection's reported patch atoms (§4.1's nearby atoms) carry
+    the surface there, checked by closed forms that do not use the oracle:
+    a convex patch's point lies on the atom's van der Waals sphere; a saddle
+    patch's point lies at distance r_p from the intersection circle of the
+    pair's expanded spheres; a concave patch's point at distance r_p from one
+    of the two points where the triple's expanded spheres meet.  A wrong atom
+    index, or a type that does not match the ids, fails."""
+    xyz, rad = inputs.protein_like(80, 17, inputs.PROTEIN_DENSITY)
+    res = oracle.run(xyz, rad, RP, 0.35, 0.8)
+    R = rad + RP
+    seen = set()
+    for a in range(3):
+        s = _grid_points(res, res.idx[a])
+        for e in range(len(s)):
+            p = s[e].copy()
+            p[a] += res.tau[a][e] * res.h
+            t, ids = int(res.ptype[a][e]), res.atoms[a][e]
+            n_ids = int((ids >= 0).sum())
+            assert n_ids == t + 1 and np.all(ids[:n_ids] >= 0) and np.all(ids[n_ids:] == -1), (t, ids)
+            seen.add(t)
+            if t == 0:
+                i = ids[0]
+                assert abs(np.linalg.norm(p - xyz[i]) - rad[i]) < 1e-7
+            elif t == 1:
+                i, j = ids[0], ids[1]
+                o, u, rho = circle_of_spheres(xyz[i], R[i], xyz[j], R[j])
+                w = p - o
+                z = w @ u
+                dist = math.hypot(math.sqrt(max(w @ w - z * z, 0.0)) - rho, z)
+                assert abs(dist - RP) < 1e-7
+            else:
+                q1, q2 = trilaterate(xyz[ids], R[ids])
+                off = min(abs(np.linalg.norm(p - q1) - RP), abs(np.linalg.norm(p - q2) - RP))
+                assert off < 1e-7
+    assert seen == {0, 1, 2}
