@@ -439,6 +439,31 @@ def main():
     eses.eses_set_option(ctx, eses.ESES_OPT_PRECISION, eses.ESES_PREC_FP32_FILTERED)
     eses.eses_destroy(ctx)
 
+    # ---- buried-patch pre-culling on the headline molecule -------------------
+    culling = None
+    if not args.no_density:
+        cctx = eses.eses_create(xyz, rad, wl.r_p, wl.h, wl.margin)
+        eses.eses_set_option(cctx, eses.ESES_OPT_STREAM, stream.cuda_stream)
+        eses.eses_set_option(cctx, eses.ESES_OPT_PROFILE, 1)
+        set_prop(cctx, args.proposer)
+        culling = {}
+        labs = {}
+        for cull in (1, 0):
+            eses.eses_set_option(cctx, eses.ESES_OPT_CULL, cull)
+            for _ in range(2):
+                eses.eses_run(cctx)
+            ct, cs = timed_runs(cctx, max(3, min(args.steps, 5)))
+            labs[cull] = eses.eses_labels(cctx)
+            culling["culled" if cull else "unculled"] = {
+                "ms_per_step": statistics.mean(ct), "stages_ms": {k: statistics.mean(v[k] for v in cs) for k in cs[0]},
+                "big_tier_tiles": int(eses.eses_stats(cctx)["big_tier_tiles"])}
+        npair, nfree, nvert = eses.eses_patch_counts(cctx)
+        culling.update(workload=wl.name, circle_pairs=npair, free_arc_pairs=nfree, free_vertices=nvert,
+                       labels_equal=bool(np.array_equal(labs[0], labs[1])), graph=False,
+                       gain=culling["unculled"]["ms_per_step"] / culling["culled"]["ms_per_step"])
+        del labs
+        eses.eses_destroy(cctx)
+
     # ---- end to end through the C ABI with host buffers ---------------------
     xyz_pin = torch.from_numpy(np.ascontiguousarray(xyz)).pin_memory()
     rad_pin = torch.from_numpy(np.ascontiguousarray(rad)).pin_memory()
@@ -590,6 +615,16 @@ def main():
                                  "stages_ms": {k: statistics.mean(v[k] for v in ds) for k in ds[0]}}
             if not args.no_precision_study:
                 density[f"h{dh}"]["fp32_filtered_vs_fp64"] = fp_compare(eses, dctx, 1, dh, set_prop, args.proposer, 2)
+            # buried-patch pre-culling (§5 of the paper): the same step with every circle and face staged
+            npair, nfree, nvert = eses.eses_patch_counts(dctx)
+            eses.eses_set_option(dctx, eses.ESES_OPT_CULL, 0)
+            try:
+                eses.eses_run(dctx)
+                unculled = "runs"
+            except eses.EsesError as e:
+                unculled = f"fails: {e}"
+            density[f"h{dh}"]["culling"] = {"circle_pairs": npair, "free_arc_pairs": nfree, "free_vertices": nvert,
+                                            "without_culling": unculled}
             eses.eses_destroy(dctx)
 
     # ---- batched workload: 256 molecules in one context ---------------------
@@ -723,6 +758,7 @@ def main():
                 "assembly": assembly,
                 "assembly_streamed": streamed,
                 "paper_density": density,
+                "culling": culling,
                 "cpu_baseline": cpu,
                 "clocks": clk,
                 "plain_fp64": {"value": all_pts / (plain_ms / 1e3), "unit": UNIT, "ms_per_step": plain_ms,

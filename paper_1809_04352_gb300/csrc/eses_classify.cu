@@ -214,14 +214,14 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Batch B, Tile
         const T h = (T)G.h;
         double x0[3];
         stage_tile<T>(M, G, mol, tile, S, x0);
-        if (S.flags & ERR_CAP_ANY) {  // uniform: set before stage_tile's last barrier
-            if (threadIdx.x == 0) {
-                if (BIG) atomicOr(err, S.flags);
-                else ovf_push(ovf, gt);
-            }
+        if (!BIG && (S.flags & ERR_CAP_ANY)) {  // uniform: set before stage_tile's last barrier
+            if (threadIdx.x == 0) ovf_push(ovf, gt);
             __syncthreads();
             continue;
         }
+        // (the global-memory tier classifies even a tile that overflows it,
+        // with its lists cut at capacity, so every label is written; the
+        // error bit makes the run report ESES_ECAPACITY)
         if (threadIdx.x == 0) {
             C.nq = 0;
             C.band = 0;
@@ -358,18 +358,15 @@ __device__ void band_tile(const Model &M, const Batch &B, long long gt, int8_t *
     int8_t *__restrict__ labels = labels_all + G.lab0;
     double x0[3];
     stage_tile<double>(M, G, mol, tile, S, x0);
-    if (S.flags & ERR_CAP_ANY) {
-        if (threadIdx.x == 0) {
-            if (big) atomicOr(err, S.flags);
-            else ovf_push(ovf, gt);
-        }
+    if (!big && (S.flags & ERR_CAP_ANY)) {  // the global-memory tier relabels even an overflowing tile
+        if (threadIdx.x == 0) ovf_push(ovf, gt);
         __syncthreads();
         return;
     }
     if (threadIdx.x == 0 && S.flags) atomicOr(err, S.flags);
     int t[3];
     tile_coords(G, tile, t);
-    SmemAcc<double, CP> A(S);
+    SmemAcc<double, CP> A(S, &M);
     // the tile's undecided points, then one warp per point: the FP64
     // witness search (a free probe centre closer than r_p: outside)
     if (threadIdx.x == 0) s_np = 0;

@@ -32,9 +32,6 @@ struct CapSmall {
 struct CapBig {
     static constexpr int A = 1024, P = 2048, V = 2048;
 };
-constexpr int A_MAX = CapSmall::A;
-constexpr int P_MAX = CapSmall::P;
-constexpr int V_MAX = CapSmall::V;
 constexpr int ERR_CAP_ANY = 1 | 2 | 4;  // ERR_CAP_ATOMS | ERR_CAP_PAIRS | ERR_CAP_VERTS
 
 // device error bits (OR-ed into ctx->d_err)

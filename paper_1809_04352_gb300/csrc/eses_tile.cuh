@@ -47,7 +47,6 @@ constexpr int STAGE_CELLS = 128;  // cells staged with item-parallel scan (else 
 // words of a set of staged atoms (bit k: staged slot k) for capacity C
 template <class C>
 __host__ __device__ constexpr int atom_words() { return (C::A + 31) / 32; }
-constexpr int AW = atom_words<CapSmall>();
 
 template <class T, class C = CapSmall>
 struct TileS {
@@ -75,7 +74,22 @@ template <class T, class C = CapSmall>
 struct SmemAcc {
     using real = T;
     const TileS<T, C> &S;
-    __device__ SmemAcc(const TileS<T, C> &s) : S(s) {}
+    const Model *mp;  // optional: the model, for freeness tests against its neighbour lists
+    __device__ SmemAcc(const TileS<T, C> &s, const Model *m = nullptr) : S(s), mp(m) {}
+    __device__ const Model *model() const { return mp; }
+    // tile-frame position of model atom k, with the staging's arithmetic
+    // (the staged value bit for bit when k is staged)
+    __device__ P4<T> atom_g(int k) const
+    {
+        if constexpr (sizeof(T) == sizeof(float)) {
+            const float4 a = mp->atom_hi[k], l = mp->atom_lo[k];
+            return P4<T>{(a.x - S.fh0[0]) + (l.x - S.fl0[0]), (a.y - S.fh0[1]) + (l.y - S.fl0[1]),
+                         (a.z - S.fh0[2]) + (l.z - S.fl0[2]), a.w};
+        } else {
+            const double4 a = mp->atom[k];
+            return P4<T>{(T)(a.x - S.fx0[0]), (T)(a.y - S.fx0[1]), (T)(a.z - S.fx0[2]), (T)a.w};
+        }
+    }
     __device__ int na() const { return S.na; }
     __device__ int np() const { return S.np; }
     __device__ int nv() const { return S.nv; }
@@ -99,6 +113,12 @@ struct ExactAcc {
     __device__ int na() const { return S.na; }
     __device__ int np() const { return S.np; }
     __device__ int nv() const { return S.nv; }
+    __device__ const Model *model() const { return &M; }
+    __device__ P4<double> atom_g(int k) const
+    {
+        double4 g = M.atom[k];
+        return P4<double>{g.x - x0, g.y - y0, g.z - z0, g.w};
+    }
     __device__ P4<double> atom(int a) const
     {
         double4 g = M.atom[S.agid[a]];
@@ -173,7 +193,7 @@ __device__ __forceinline__ void stage_item(const Model &M, TileS<T, C> &S, int l
             float reach = a.w + 2.0f * rpf + tol;
             if (box_dist2f(a.x, a.y, a.z, F.b0, F.b1) < reach * reach) {
                 int s = atomicAdd(&S.na, 1);
-                if (s < A_MAX) {
+                if (s < C::A) {
                     float4 l = M.atom_lo[k];
                     S.atom[s] = P4<T>{(a.x - F.h0[0]) + (l.x - F.l0[0]), (a.y - F.h0[1]) + (l.y - F.l0[1]),
                                       (a.z - F.h0[2]) + (l.z - F.l0[2]), a.w};
@@ -187,7 +207,7 @@ __device__ __forceinline__ void stage_item(const Model &M, TileS<T, C> &S, int l
             float reach = o.w + rpf + tol;
             if (box_dist2f(o.x, o.y, o.z, F.b0, F.b1) < reach * reach) {
                 int s = atomicAdd(&S.np, 1);
-                if (s < P_MAX) {
+                if (s < C::P) {
                     float4 l = M.pair_lo[p];
                     float4 u = M.pair_u32[p];
                     S.po[s] = P4<T>{(o.x - F.h0[0]) + (l.x - F.l0[0]), (o.y - F.h0[1]) + (l.y - F.l0[1]),
@@ -203,7 +223,7 @@ __device__ __forceinline__ void stage_item(const Model &M, TileS<T, C> &S, int l
             float reach = rpf + tol;
             if (box_dist2f(q.x, q.y, q.z, F.b0, F.b1) < reach * reach) {
                 int s = atomicAdd(&S.nv, 1);
-                if (s < V_MAX) {
+                if (s < C::V) {
                     float4 l = M.vert_lo[v];
                     S.vq[s] = P4<T>{(q.x - F.h0[0]) + (l.x - F.l0[0]), (q.y - F.h0[1]) + (l.y - F.l0[1]),
                                     (q.z - F.h0[2]) + (l.z - F.l0[2]), 0.0f};
@@ -219,7 +239,7 @@ __device__ __forceinline__ void stage_item(const Model &M, TileS<T, C> &S, int l
             double reach = a.w + 2.0 * rp + tol;
             if (box_dist2(a.x, a.y, a.z, x0, x1) < reach * reach) {
                 int s = atomicAdd(&S.na, 1);
-                if (s < A_MAX) {
+                if (s < C::A) {
                     S.atom[s] = P4<T>{(T)(a.x - x0[0]), (T)(a.y - x0[1]), (T)(a.z - x0[2]), (T)a.w};
                     S.agid[s] = k;
                     S.aface[s] = M.atom_face[k];
@@ -231,7 +251,7 @@ __device__ __forceinline__ void stage_item(const Model &M, TileS<T, C> &S, int l
             double reach = o.w + rp + tol;
             if (box_dist2(o.x, o.y, o.z, x0, x1) < reach * reach) {
                 int s = atomicAdd(&S.np, 1);
-                if (s < P_MAX) {
+                if (s < C::P) {
                     double4 u = M.pair_u[p];
                     S.po[s] = P4<T>{(T)(o.x - x0[0]), (T)(o.y - x0[1]), (T)(o.z - x0[2]), (T)o.w};
                     S.pu[s] = P4<T>{(T)u.x, (T)u.y, (T)u.z, (T)0};
@@ -245,7 +265,7 @@ __device__ __forceinline__ void stage_item(const Model &M, TileS<T, C> &S, int l
             double reach = rp + tol;
             if (box_dist2(q.x, q.y, q.z, x0, x1) < reach * reach) {
                 int s = atomicAdd(&S.nv, 1);
-                if (s < V_MAX) {
+                if (s < C::V) {
                     S.vq[s] = P4<T>{(T)(q.x - x0[0]), (T)(q.y - x0[1]), (T)(q.z - x0[2]), (T)0};
                     S.vidx[s] = v;
                 }
@@ -408,6 +428,50 @@ __device__ __noinline__ int free_pt(const Acc &A, T qx, T qy, T qz, int e0, int 
     return res;
 }
 
+// Freeness of a witness q on the expanded sphere of atom e0 (and, for a
+// saddle, of e1 too) against the model's neighbours of e0 -- the atoms whose
+// expanded spheres meet e0's, which hold every atom that can cover q (see
+// free_set) -- read from the neighbour list in global memory.  1 free, 0
+// covered, -1 undecided.  free_nb32: positions in the tile frame from the
+// double-float copies, with the staging's arithmetic (the staged values, bit
+// for bit), FP32 filtered; free_nb64: FP64 positions relative to the tile
+// origin x0, exact.
+template <class T, class C>
+__device__ __noinline__ int free_nb32(const Model &M, const TileS<T, C> &S, float qx, float qy, float qz, int e0,
+                                      int e1, float rp, float delta)
+{
+    int res = 1;
+    const float h0 = S.fh0[0], h1 = S.fh0[1], h2 = S.fh0[2], l0 = S.fl0[0], l1 = S.fl0[1], l2 = S.fl0[2];
+    const int t1 = M.nb_start[e0 + 1];
+    for (int t = M.nb_start[e0]; t < t1; ++t) {
+        const int k = M.nb_list[t];
+        if (k == e1) continue;
+        const float4 a = M.atom_hi[k], l = M.atom_lo[k];
+        const float cx = (a.x - h0) + (l.x - l0), cy = (a.y - h1) + (l.y - l1), cz = (a.z - h2) + (l.z - l2);
+        const float dx = qx - cx, dy = qy - cy, dz = qz - cz;
+        const float R = a.w + rp;
+        const int r = lt_sq<true>(dx * dx + dy * dy + dz * dz, R * R, R, delta);
+        if (r == 1) return 0;
+        if (r < 0) res = -1;
+    }
+    return res;
+}
+
+static __device__ __noinline__ int free_nb64(const Model &M, const double *x0, double qx, double qy, double qz, int e0,
+                                      int e1, double rp)
+{
+    const int t1 = M.nb_start[e0 + 1];
+    for (int t = M.nb_start[e0]; t < t1; ++t) {
+        const int k = M.nb_list[t];
+        if (k == e1) continue;
+        const double4 a = M.atom[k];
+        const double dx = qx - (a.x - x0[0]), dy = qy - (a.y - x0[1]), dz = qz - (a.z - x0[2]);
+        const double R = a.w + rp;
+        if (dx * dx + dy * dy + dz * dz < R * R) return 0;
+    }
+    return 1;
+}
+
 // Freeness of q against the staged atoms in the set m0 & m1 (m1 may be
 // null): 1 free, 0 covered, -1 undecided.  A witness q on the expanded
 // sphere of atom a (and, for a saddle, of atom b too) can only be covered by
@@ -448,7 +512,6 @@ __host__ __device__ constexpr int slot_hash_size()  // a power of two > 2 C::A
     while (n <= 2 * C::A) n <<= 1;
     return n;
 }
-constexpr int SLOT_HASH = slot_hash_size<CapSmall>();
 
 template <class T, class C>
 __device__ void pair_slots(const TileS<T, C> &S, int *hkey, short *hval, short2 *pslot)
@@ -642,15 +705,30 @@ __device__ __forceinline__ int warp_free(const Acc &A, T qx, T qy, T qz, int e0,
 {
     const unsigned full = 0xffffffffu;
     bool cov = false, und = false;
-    for (int k = threadIdx.x & 31; k < A.na(); k += 32) {
-        int g = A.agid(k);
-        if (g == e0 || g == e1) continue;
-        P4<T> c = A.atom(k);
-        T dx = qx - c.x, dy = qy - c.y, dz = qz - c.z;
-        T R = c.w + rp;
-        int t = lt_sq<FILT>(dx * dx + dy * dy + dz * dz, R * R, R, delta);
-        if (t == 1) cov = true;
-        else if (t < 0) und = true;
+    const Model *M = A.model();
+    if (M && e0 >= 0) {  // the neighbours of e0 hold every atom that can cover q (see free_set)
+        const int t1 = M->nb_start[e0 + 1];
+        for (int t = M->nb_start[e0] + (threadIdx.x & 31); t < t1; t += 32) {
+            const int k = M->nb_list[t];
+            if (k == e1) continue;
+            const P4<T> c = A.atom_g(k);
+            T dx = qx - c.x, dy = qy - c.y, dz = qz - c.z;
+            T R = c.w + rp;
+            int r = lt_sq<FILT>(dx * dx + dy * dy + dz * dz, R * R, R, delta);
+            if (r == 1) cov = true;
+            else if (r < 0) und = true;
+        }
+    } else {
+        for (int k = threadIdx.x & 31; k < A.na(); k += 32) {
+            int g = A.agid(k);
+            if (g == e0 || g == e1) continue;
+            P4<T> c = A.atom(k);
+            T dx = qx - c.x, dy = qy - c.y, dz = qz - c.z;
+            T R = c.w + rp;
+            int t = lt_sq<FILT>(dx * dx + dy * dy + dz * dz, R * R, R, delta);
+            if (t == 1) cov = true;
+            else if (t < 0) und = true;
+        }
     }
     if (__any_sync(full, cov)) return 0;
     return __any_sync(full, und) ? -1 : 1;

@@ -142,8 +142,10 @@ def test_overflowing_tiles_take_the_global_memory_tier_and_match_oracle(precisio
 def test_buried_patch_culling_changes_nothing_but_the_work(precision):
     """Without the pre-culling every circle and every face carries witnesses
     into the tiles; the witnesses of buried patches are never free, so the
-    labels, edges and intersections must be identical, bit for bit."""
-    xyz, rad = inputs.paper_density(700, 2300)
+    labels, edges and intersections must be identical, bit for bit.  (A
+    globule at 0.0125 atoms/A^3: at the paper's density the unculled circles
+    overflow even the global-memory staging, which the next test checks.)"""
+    xyz, rad = inputs.protein_like(1500, 2301, inputs.PROTEIN_DENSITY)
     out = {}
     for cull in (1, 0):
         ctx = eses.eses_create(xyz, rad, 1.4, 0.4, 0.8)
@@ -163,3 +165,22 @@ def test_buried_patch_culling_changes_nothing_but_the_work(precision):
         assert np.array_equal(x["normal"], y["normal"])
     n_pairs, n_free, _ = out[1][2]
     assert n_free < n_pairs  # the culling does remove buried circles here
+
+
+def test_without_culling_the_paper_density_overflows_and_reports_it():
+    """At 0.1 atoms/A^3 a tile meets thousands of circles, most of them buried:
+    without the pre-culling its staging overflows even the global-memory tier,
+    and the run reports ESES_ECAPACITY (with every output written, so the
+    context stays usable); with the culling the same molecule runs."""
+    xyz, rad = inputs.paper_density(700, 2300)
+    ctx = eses.eses_create(xyz, rad, 1.4, 0.4, 0.8)
+    try:
+        eses.eses_set_option(ctx, eses.ESES_OPT_CULL, 0)
+        with pytest.raises(eses.EsesError) as ei:
+            eses.eses_run(ctx)
+        assert ei.value.code == eses.ESES_ECAPACITY
+        eses.eses_set_option(ctx, eses.ESES_OPT_CULL, 1)
+        eses.eses_run(ctx)
+        assert eses.eses_stats(ctx)["root_failures"] == 0
+    finally:
+        eses.eses_destroy(ctx)
