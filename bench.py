@@ -308,6 +308,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-only", action="store_true",
                     help="only the warm-up and device-resident steps (for ncu captures); prints stage times")
+    ap.add_argument("--profile-workload", default="globule", choices=["globule", "paper-density"],
+                    help="with --profile-only: the headline globule, or the paper-density globule at h 0.25")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of the autotuner's")
     ap.add_argument("--no-graph", action="store_true", help="eager launches instead of CUDA-graph replay")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-molecule batched workload")
@@ -351,6 +353,8 @@ def main():
     eses.load()
     wl = inputs.WORKLOADS[WORKLOAD]
     xyz, rad = inputs.workload_atoms(WORKLOAD, molecule=rank)
+    if args.profile_only and args.profile_workload == "paper-density":
+        xyz, rad = inputs.paper_density(5000, 2200)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 

@@ -683,24 +683,34 @@ int run_device(eses_ctx *c)
         if (g_capturing) throw std::string("the exterior-only surface is not captured in a graph");
         uint8_t *ext = ensure<uint8_t>(c->ext, c->n_points);
         uint8_t *open = ensure<uint8_t>(c->ext_open, nt);
-        unsigned long long *em = ensure<unsigned long long>(c->ext_misc, 2);  // [0] changed flag, [1] filled
-        ck(cudaMemsetAsync(em, 0, 2 * sizeof(unsigned long long), st), "memset");
+        // em[0..1]: four ints (three sweep flags, the sweep count), em[2]: filled points
+        unsigned long long *em = ensure<unsigned long long>(c->ext_misc, 3);
+        int *flags = reinterpret_cast<int *>(em);
+        ck(cudaMemsetAsync(em, 0, 3 * sizeof(unsigned long long), st), "memset");
         nl += launch_ext_init(B, labels, ext, open, st);
-        const int sweep_grid = (int)std::min<long long>(std::max<long long>(nt, 1), 8LL * c->n_sm);
-        for (long long it = 0; it <= nt; ++it) {  // a sweep reaches at least one more tile, or nothing
-            ck(cudaMemsetAsync(em, 0, sizeof(unsigned long long), st), "memset");
-            nl += launch_ext_sweep(B, ext, open, reinterpret_cast<int *>(em), sweep_grid, st);
-            unsigned long long changed = 0;
-            ck(cudaMemcpyAsync(&changed, em, sizeof(changed), cudaMemcpyDeviceToHost, st), "read");
-            ck(cudaStreamSynchronize(st), "synchronize");
-            ++c->ext_sweeps;
-            if (!changed) break;
+        // a sweep reaches at least one more tile, or nothing: at most nt + 1 sweeps
+        const int coop = launch_ext_fill(B, ext, open, flags, nt + 1, st);
+        if (coop < 0) throw CudaError{cudaGetLastError(), "cooperative launch"};
+        if (coop == 1) {  // one launch for every sweep
+            ++nl;
+        } else {  // no cooperative launch on this device: one launch per sweep, driven from the host
+            const int sweep_grid = (int)std::min<long long>(std::max<long long>(nt, 1), 8LL * c->n_sm);
+            for (long long it = 0; it <= nt; ++it) {
+                ck(cudaMemsetAsync(flags, 0, sizeof(int), st), "memset");
+                nl += launch_ext_sweep(B, ext, open, flags, sweep_grid, st);
+                int changed = 0;
+                ck(cudaMemcpyAsync(&changed, flags, sizeof(changed), cudaMemcpyDeviceToHost, st), "read");
+                ck(cudaStreamSynchronize(st), "synchronize");
+                ++c->ext_sweeps;
+                if (!changed) break;
+            }
         }
-        nl += launch_ext_apply(B, labels, ext, em + 1, st);
-        unsigned long long filled = 0;
-        ck(cudaMemcpyAsync(&filled, em + 1, sizeof(filled), cudaMemcpyDeviceToHost, st), "read");
+        nl += launch_ext_apply(B, labels, ext, em + 2, st);
+        unsigned long long misc[3] = {0, 0, 0};
+        ck(cudaMemcpyAsync(misc, em, sizeof(misc), cudaMemcpyDeviceToHost, st), "read");
         ck(cudaStreamSynchronize(st), "synchronize");
-        c->n_cavity = (long long)filled;
+        if (coop == 1) c->ext_sweeps = reinterpret_cast<const int *>(misc)[3];
+        c->n_cavity = (long long)misc[2];
     }
 
     // 8. crossing edges, roots, area and volume

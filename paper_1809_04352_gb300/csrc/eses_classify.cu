@@ -366,7 +366,7 @@ __device__ void band_tile(const Model &M, const Batch &B, long long gt, int8_t *
     if (threadIdx.x == 0 && S.flags) atomicOr(err, S.flags);
     int t[3];
     tile_coords(G, tile, t);
-    SmemAcc<double, CP> A(S, &M);
+    SmemAcc<double, CP> A(S);
     // the tile's undecided points, then one warp per point: the FP64
     // witness search (a free probe centre closer than r_p: outside)
     if (threadIdx.x == 0) s_np = 0;

@@ -497,8 +497,8 @@ __device__ __noinline__ void torus_root_exact(const Acc &X, EdgeSmem &E, int e, 
     const double rate = fabs(rd) <= 1e-9 ? 0.0 : rd;
     if (inside ? rate > 0.0 : rate < 0.0) return;
     const int2 ij = X.pij(pi);
-    const double xo[3] = {X.x0, X.y0, X.z0};
-    const int f = free_nb64(X.M, xo, oo[0] + oe.w * wd[0], oo[1] + oe.w * wd[1], oo[2] + oe.w * wd[2], ij.x, ij.y, rp);
+    const int f = free_pt<false>(X, oo[0] + oe.w * wd[0], oo[1] + oe.w * wd[1], oo[2] + oe.w * wd[2], ij.x, ij.y, rp,
+                                 0.0);
     if (f == 1) pool_push(E, e, (float)t64, 0.0f, t64, 1, pi);
 }
 
@@ -622,8 +622,8 @@ __device__ void cand_roots(const Model &M, const TileS<T, CP> &S, const double *
                 int f = -1;
                 if (FILT) {
                     T delta = d0 + terr * (T(1) + sc) + T(2e-6);
-                    f = free_nb32(M, S, c.x + sc * v32[0], c.y + sc * v32[1], c.z + sc * v32[2], S.agid[slot], -1,
-                                  rpT, delta);
+                    f = free_pt<true>(A, c.x + sc * v32[0], c.y + sc * v32[1], c.z + sc * v32[2], S.agid[slot], -1,
+                                      rpT, delta);
                 }
                 if (f < 0) {
                     P4<double> ce = X.atom(slot);
@@ -633,8 +633,8 @@ __device__ void cand_roots(const Model &M, const TileS<T, CP> &S, const double *
                     v[axis] += t64;
                     double nv64 = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
                     double R64 = ce.w + rp;
-                    f = free_nb64(M, x0, cc[0] + R64 * v[0] / nv64, cc[1] + R64 * v[1] / nv64,
-                                  cc[2] + R64 * v[2] / nv64, S.agid[slot], -1, rp);
+                    f = free_pt<false>(X, cc[0] + R64 * v[0] / nv64, cc[1] + R64 * v[1] / nv64,
+                                       cc[2] + R64 * v[2] / nv64, S.agid[slot], -1, rp, 0.0);
                 }
                 if (f != 1) continue;
             }
@@ -645,7 +645,7 @@ __device__ void cand_roots(const Model &M, const TileS<T, CP> &S, const double *
     // saddle: torus around a free-arc circle
     const int pi = it - na - nv;
     if constexpr (!FILT) {
-        torus_piece_exact(X, E, e, pi, s64, axis, h, rp, inside);
+        torus_piece_exact(A, E, e, pi, s64, axis, h, rp, inside);
     } else {
         const P4<T> o = S.po[pi];
         const P4<T> u = S.pu[pi];
@@ -698,7 +698,8 @@ __device__ void cand_roots(const Model &M, const TileS<T, CP> &S, const double *
             if (inside ? rate > 0.0f : rate < 0.0f) continue;
             const float kk = o.w / nw;
             const float delta = d0 + terr * (1.0f + 2.0f * o.w / nw) + 2e-6f;
-            const int f = free_nb32(M, S, o.x + kk * wv[0], o.y + kk * wv[1], o.z + kk * wv[2], ij.x, ij.y, rpT, delta);
+            const int f =
+                free_pt<true>(A, o.x + kk * wv[0], o.y + kk * wv[1], o.z + kk * wv[2], ij.x, ij.y, rpT, delta);
             if (f == 1) {
                 pool_push(E, e, t, terr, NaN, 1, pi);
             } else if (f < 0) {
@@ -725,7 +726,7 @@ __device__ int warp_select(const Model &M, const TileS<T, CP> &S, const double *
     const int axis = R.axis;
     const double s64[3] = {E.hd[R.p >> 6], E.hd[(R.p >> 3) & 7], E.hd[R.p & 7]};
     const T s[3] = {(T)s64[0], (T)s64[1], (T)s64[2]};
-    SmemAcc<T, CP> A(S, &M);
+    SmemAcc<T, CP> A(S);
     ExactAcc<T, CP> X(S, M, x0);
     const T rpT = (T)rp;
     const float tie = 1e-6f * (float)h;  // FP32 rounding of a root

@@ -16,11 +16,15 @@
 //                loop: a path inside the tile has fewer than 512 steps); the
 //                tile's new points are written back and a flag set; a
 //                tile left without state-1 points closes and is not read
-//                again.  The
-//                host repeats sweeps until one changes nothing (the reached
-//                set only grows, so neighbours read mid-sweep are either
-//                state and the fixed point is the same);
+//                again.  Sweeps repeat until one changes nothing (the
+//                reached set only grows, so neighbours read mid-sweep are
+//                either state and the fixed point is the same): k_ext_fill
+//                runs them all in one cooperative launch with a grid-wide
+//                barrier after each sweep (k_ext_sweep, one sweep per launch
+//                driven from the host, where cooperative launch is missing);
 //   k_ext_apply: points still 1 are cavity points: label 1, counted.
+#include <cooperative_groups.h>
+
 #include "eses_kernels.h"
 #include "eses_tile.cuh"
 
@@ -59,11 +63,10 @@ __global__ void __launch_bounds__(EXT_WARPS * 32) k_ext_init(Batch B, const int8
     }
 }
 
-__global__ void __launch_bounds__(EXT_THREADS) k_ext_sweep(Batch B, uint8_t *__restrict__ ext_all,
-                                                          uint8_t *__restrict__ tile_open, int *__restrict__ changed)
+// one sweep over the block's tiles gt = blockIdx.x, + gridDim.x, ... (whole block)
+__device__ void sweep_tiles(const Batch &B, uint8_t *__restrict__ ext_all, uint8_t *__restrict__ tile_open,
+                            int *__restrict__ changed, uint8_t *s, uint8_t *s0)
 {
-    __shared__ uint8_t s[HALO_W * HALO_W * HALO_W];
-    __shared__ uint8_t s0[TILE_PTS];  // the tile's states before the sweep
     for (long long gt = blockIdx.x; gt < B.n_tiles; gt += gridDim.x) {
         if (!tile_open[gt]) continue;  // uniform: every thread reads the same byte
         const Grid &G = B.grid[mol_of_tile(B, gt)];
@@ -124,6 +127,37 @@ __global__ void __launch_bounds__(EXT_THREADS) k_ext_sweep(Batch B, uint8_t *__r
     }
 }
 
+__global__ void __launch_bounds__(EXT_THREADS) k_ext_sweep(Batch B, uint8_t *__restrict__ ext_all,
+                                                          uint8_t *__restrict__ tile_open, int *__restrict__ changed)
+{
+    __shared__ uint8_t s[HALO_W * HALO_W * HALO_W];
+    __shared__ uint8_t s0[TILE_PTS];  // the tile's states before the sweep
+    sweep_tiles(B, ext_all, tile_open, changed, s, s0);
+}
+
+// Every sweep in one cooperative launch (all blocks resident): after each
+// sweep a grid-wide barrier, then every block reads that sweep's changed flag
+// and all stop together when it is clear.  Three flags rotate: block 0 clears
+// the next sweep's flag, which every block last read before the previous
+// barrier.  At most max_sweeps sweeps (the host loop's bound); flags[3]
+// receives the number of sweeps run.
+__global__ void __launch_bounds__(EXT_THREADS) k_ext_fill(Batch B, uint8_t *__restrict__ ext_all,
+                                                         uint8_t *__restrict__ tile_open, int *__restrict__ flags,
+                                                         long long max_sweeps)
+{
+    __shared__ uint8_t s[HALO_W * HALO_W * HALO_W];
+    __shared__ uint8_t s0[TILE_PTS];
+    cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+    long long it = 0;
+    for (; it < max_sweeps; ++it) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) flags[(it + 1) % 3] = 0;
+        sweep_tiles(B, ext_all, tile_open, &flags[it % 3], s, s0);
+        grid.sync();
+        if (*(volatile int *)&flags[it % 3] == 0) break;  // the same value in every block
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) flags[3] = (int)(it < max_sweeps ? it + 1 : it);
+}
+
 __global__ void __launch_bounds__(EXT_WARPS * 32) k_ext_apply(Batch B, int8_t *__restrict__ labels_all,
                                                              const uint8_t *__restrict__ ext_all,
                                                              unsigned long long *__restrict__ filled)
@@ -166,6 +200,28 @@ int launch_ext_init(const Batch &B, const int8_t *labels, uint8_t *ext, uint8_t 
 int launch_ext_sweep(const Batch &B, uint8_t *ext, uint8_t *tile_open, int *changed, int grid, cudaStream_t st)
 {
     k_ext_sweep<<<grid < 1 ? 1 : grid, EXT_THREADS, 0, st>>>(B, ext, tile_open, changed);
+    return 1;
+}
+
+// all sweeps in one cooperative launch; returns 0 when the device cannot
+// launch cooperatively (the caller then drives k_ext_sweep from the host)
+int launch_ext_fill(const Batch &B, uint8_t *ext, uint8_t *tile_open, int *flags, long long max_sweeps,
+                    cudaStream_t st)
+{
+    int dev = 0, coop = 0, n_sm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (!coop) return 0;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ext_fill, EXT_THREADS, 0);
+    if (per_sm < 1) return 0;
+    long long grid = (long long)per_sm * n_sm;
+    if (grid > B.n_tiles) grid = B.n_tiles < 1 ? 1 : B.n_tiles;
+    Batch b = B;
+    void *args[] = {&b, &ext, &tile_open, &flags, &max_sweeps};
+    if (cudaLaunchCooperativeKernel((void *)k_ext_fill, dim3((unsigned)grid), dim3(EXT_THREADS), args, 0, st) !=
+        cudaSuccess)
+        return -1;
     return 1;
 }
 

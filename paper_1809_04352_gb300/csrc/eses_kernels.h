@@ -54,6 +54,8 @@ int launch_band(const Model &M, const Batch &B, int8_t *labels, const int *tile_
 // when it reached new points), cavity points relabelled inside (counted)
 int launch_ext_init(const Batch &B, const int8_t *labels, uint8_t *ext, uint8_t *tile_open, cudaStream_t st);
 int launch_ext_sweep(const Batch &B, uint8_t *ext, uint8_t *tile_open, int *changed, int grid, cudaStream_t st);
+int launch_ext_fill(const Batch &B, uint8_t *ext, uint8_t *tile_open, int *flags, long long max_sweeps,
+                    cudaStream_t st);
 int launch_ext_apply(const Batch &B, int8_t *labels, const uint8_t *ext, unsigned long long *filled, cudaStream_t st);
 
 // ---- crossing edges, roots, area/volume (eses_edges.cu) ------------------

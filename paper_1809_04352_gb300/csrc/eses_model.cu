@@ -136,26 +136,28 @@ __device__ __forceinline__ void warp_neighbour_cells(const Model &M, int mol, do
 
 constexpr int NB_WARPS = 4;  // warps (atoms) per block of the neighbour and pair kernels
 
-// the circle where expanded spheres (ci, Ri) and (cj, Rj) meet, if any.  Kept
-// out of line, like frame_of and cover_of, so that every kernel and every
-// path computes a circle or a triple point with the same instructions (the
-// same rounding and contraction): counts and fills agree, and the bits do not
-// depend on which path a model took.
-__device__ __noinline__ bool circle_of(double4 ci, double Ri, double4 cj, double Rj, double3 &o, double3 &u,
+// the circle where expanded spheres (ci, Ri) and (cj, Rj) meet, if any.  Every
+// operation is an explicit round-to-nearest intrinsic, so no multiply-add is
+// contracted and every inlined copy (count and fill kernels, any path)
+// computes the same bits: counts and fills agree, and a circle's bits do not
+// depend on where it was computed.  frame_of and cover_of are kept out of
+// line for the same reason.
+__device__ __forceinline__ bool circle_of(double4 ci, double Ri, double4 cj, double Rj, double3 &o, double3 &u,
                                           double &rho)
 {
-    double dx = cj.x - ci.x, dy = cj.y - ci.y, dz = cj.z - ci.z;
-    double D2 = dx * dx + dy * dy + dz * dz;
-    double S = Ri + Rj;
-    if (!(D2 < S * S)) return false;
-    double D = sqrt(D2);
-    if (!(D > fabs(Ri - Rj))) return false;
-    double a = (D2 + Ri * Ri - Rj * Rj) / (2.0 * D);
-    double rho2 = Ri * Ri - a * a;
+    const double dx = __dsub_rn(cj.x, ci.x), dy = __dsub_rn(cj.y, ci.y), dz = __dsub_rn(cj.z, ci.z);
+    const double D2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    const double S = __dadd_rn(Ri, Rj);
+    if (!(D2 < __dmul_rn(S, S))) return false;
+    const double D = __dsqrt_rn(D2);
+    if (!(D > fabs(__dsub_rn(Ri, Rj)))) return false;
+    const double a = __ddiv_rn(__dsub_rn(__dadd_rn(D2, __dmul_rn(Ri, Ri)), __dmul_rn(Rj, Rj)), __dmul_rn(2.0, D));
+    const double rho2 = __dsub_rn(__dmul_rn(Ri, Ri), __dmul_rn(a, a));
     if (!(rho2 > 0.0)) return false;
-    u = make_double3(dx / D, dy / D, dz / D);
-    o = make_double3(ci.x + a * u.x, ci.y + a * u.y, ci.z + a * u.z);
-    rho = sqrt(rho2);
+    u = make_double3(__ddiv_rn(dx, D), __ddiv_rn(dy, D), __ddiv_rn(dz, D));
+    o = make_double3(__dadd_rn(ci.x, __dmul_rn(a, u.x)), __dadd_rn(ci.y, __dmul_rn(a, u.y)),
+                     __dadd_rn(ci.z, __dmul_rn(a, u.z)));
+    rho = __dsqrt_rn(rho2);
     return true;
 }
 
@@ -447,7 +449,7 @@ __device__ void arcs_of_pair(const Model &M, int p, uint8_t *pair_free, int *ver
 // FP64 otherwise, so the decisions are those of the FP64 form.  FP32 end
 // points carry a propagated error bound (the FP64 end point is used when that
 // bound exceeds 2e-4 A); emitted triple points are always computed in FP64.
-constexpr int ARC_MAXN = 128;
+constexpr int ARC_MAXN = 256;
 
 // 1: d2 < t^2 certain, 0: d2 >= t^2 certain, -1 undecided (delta: error of the vector)
 __device__ __forceinline__ int arc_lt(float d2, float t, float delta)
@@ -529,11 +531,50 @@ __device__ void arcs_of_pair_warp(const Model &M, int p, ArcWarp &W, uint8_t *pa
         __syncwarp();
         return;
     }
-    // 2-3. candidates a = lane + 32 r
     CircleFrame f;
     bool have64 = false;
-    int n_partial = 0, n_free_end = 0, n_emit_total = 0;
+    // 2. a candidate that covers the whole circle ends the work before any
+    //    end point is tested (at protein packing most circles are buried
+    //    this way): the same cover decisions as below, FP64 when undecided
     bool full = false;
+    for (int r = 0; r * 32 < n && !full; ++r) {
+        const int a = r * 32 + lane;
+        bool whole = false;
+        if (a < n) {
+            const float4 c = W.nb[a];
+            const float d1 = c.x * v1x + c.y * v1y + c.z * v1z;
+            const float d2 = c.x * v2x + c.y * v2y + c.z * v2z;
+            const float dd = c.x * c.x + c.y * c.y + c.z * c.z;
+            const float A = sqrtf(d1 * d1 + d2 * d2);
+            const float num = rho * rho + dd - c.w * c.w, den = 2.0f * rho * A;
+            const float dk = sqrtf(dd);
+            const float en = 2.0f * dk * dlt + 2e-6f * (rho * rho + dd + c.w * c.w);
+            const float ed = 2.0f * rho * (dlt + 3e-7f * dk) + 2e-6f * den;
+            const float err = 2.0f * (en + ed);
+            if (num < -den - err) {
+                whole = true;
+            } else if (num < -den + err) {  // undecided near a whole cover: FP64
+                if (!have64) {
+                    f = frame_of(M.pair_o[p], M.pair_u[p]);
+                    have64 = true;
+                }
+                const double4 ck = M.atom[W.nbk[a]];
+                double3 qa, qb;
+                whole = cover_of(f, ck, ck.w + M.rp, qa, qb) == 2;
+            }
+        }
+        full = __any_sync(full_mask, whole);
+    }
+    if (full) {
+        if (!EMIT && lane == 0) {
+            pair_free[p] = 0;
+            vert_count[p] = 0;
+        }
+        __syncwarp();
+        return;
+    }
+    // 3. candidates a = lane + 32 r: covers, end points and their freeness
+    int n_partial = 0, n_free_end = 0, n_emit_total = 0;
     const int w0 = EMIT ? vert_start[p] : 0;
     for (int r = 0; r * 32 < n; ++r) {
         const int a = r * 32 + lane;

@@ -74,22 +74,7 @@ template <class T, class C = CapSmall>
 struct SmemAcc {
     using real = T;
     const TileS<T, C> &S;
-    const Model *mp;  // optional: the model, for freeness tests against its neighbour lists
-    __device__ SmemAcc(const TileS<T, C> &s, const Model *m = nullptr) : S(s), mp(m) {}
-    __device__ const Model *model() const { return mp; }
-    // tile-frame position of model atom k, with the staging's arithmetic
-    // (the staged value bit for bit when k is staged)
-    __device__ P4<T> atom_g(int k) const
-    {
-        if constexpr (sizeof(T) == sizeof(float)) {
-            const float4 a = mp->atom_hi[k], l = mp->atom_lo[k];
-            return P4<T>{(a.x - S.fh0[0]) + (l.x - S.fl0[0]), (a.y - S.fh0[1]) + (l.y - S.fl0[1]),
-                         (a.z - S.fh0[2]) + (l.z - S.fl0[2]), a.w};
-        } else {
-            const double4 a = mp->atom[k];
-            return P4<T>{(T)(a.x - S.fx0[0]), (T)(a.y - S.fx0[1]), (T)(a.z - S.fx0[2]), (T)a.w};
-        }
-    }
+    __device__ SmemAcc(const TileS<T, C> &s) : S(s) {}
     __device__ int na() const { return S.na; }
     __device__ int np() const { return S.np; }
     __device__ int nv() const { return S.nv; }
@@ -113,12 +98,6 @@ struct ExactAcc {
     __device__ int na() const { return S.na; }
     __device__ int np() const { return S.np; }
     __device__ int nv() const { return S.nv; }
-    __device__ const Model *model() const { return &M; }
-    __device__ P4<double> atom_g(int k) const
-    {
-        double4 g = M.atom[k];
-        return P4<double>{g.x - x0, g.y - y0, g.z - z0, g.w};
-    }
     __device__ P4<double> atom(int a) const
     {
         double4 g = M.atom[S.agid[a]];
@@ -428,50 +407,6 @@ __device__ __noinline__ int free_pt(const Acc &A, T qx, T qy, T qz, int e0, int 
     return res;
 }
 
-// Freeness of a witness q on the expanded sphere of atom e0 (and, for a
-// saddle, of e1 too) against the model's neighbours of e0 -- the atoms whose
-// expanded spheres meet e0's, which hold every atom that can cover q (see
-// free_set) -- read from the neighbour list in global memory.  1 free, 0
-// covered, -1 undecided.  free_nb32: positions in the tile frame from the
-// double-float copies, with the staging's arithmetic (the staged values, bit
-// for bit), FP32 filtered; free_nb64: FP64 positions relative to the tile
-// origin x0, exact.
-template <class T, class C>
-__device__ __noinline__ int free_nb32(const Model &M, const TileS<T, C> &S, float qx, float qy, float qz, int e0,
-                                      int e1, float rp, float delta)
-{
-    int res = 1;
-    const float h0 = S.fh0[0], h1 = S.fh0[1], h2 = S.fh0[2], l0 = S.fl0[0], l1 = S.fl0[1], l2 = S.fl0[2];
-    const int t1 = M.nb_start[e0 + 1];
-    for (int t = M.nb_start[e0]; t < t1; ++t) {
-        const int k = M.nb_list[t];
-        if (k == e1) continue;
-        const float4 a = M.atom_hi[k], l = M.atom_lo[k];
-        const float cx = (a.x - h0) + (l.x - l0), cy = (a.y - h1) + (l.y - l1), cz = (a.z - h2) + (l.z - l2);
-        const float dx = qx - cx, dy = qy - cy, dz = qz - cz;
-        const float R = a.w + rp;
-        const int r = lt_sq<true>(dx * dx + dy * dy + dz * dz, R * R, R, delta);
-        if (r == 1) return 0;
-        if (r < 0) res = -1;
-    }
-    return res;
-}
-
-static __device__ __noinline__ int free_nb64(const Model &M, const double *x0, double qx, double qy, double qz, int e0,
-                                      int e1, double rp)
-{
-    const int t1 = M.nb_start[e0 + 1];
-    for (int t = M.nb_start[e0]; t < t1; ++t) {
-        const int k = M.nb_list[t];
-        if (k == e1) continue;
-        const double4 a = M.atom[k];
-        const double dx = qx - (a.x - x0[0]), dy = qy - (a.y - x0[1]), dz = qz - (a.z - x0[2]);
-        const double R = a.w + rp;
-        if (dx * dx + dy * dy + dz * dz < R * R) return 0;
-    }
-    return 1;
-}
-
 // Freeness of q against the staged atoms in the set m0 & m1 (m1 may be
 // null): 1 free, 0 covered, -1 undecided.  A witness q on the expanded
 // sphere of atom a (and, for a saddle, of atom b too) can only be covered by
@@ -705,30 +640,15 @@ __device__ __forceinline__ int warp_free(const Acc &A, T qx, T qy, T qz, int e0,
 {
     const unsigned full = 0xffffffffu;
     bool cov = false, und = false;
-    const Model *M = A.model();
-    if (M && e0 >= 0) {  // the neighbours of e0 hold every atom that can cover q (see free_set)
-        const int t1 = M->nb_start[e0 + 1];
-        for (int t = M->nb_start[e0] + (threadIdx.x & 31); t < t1; t += 32) {
-            const int k = M->nb_list[t];
-            if (k == e1) continue;
-            const P4<T> c = A.atom_g(k);
-            T dx = qx - c.x, dy = qy - c.y, dz = qz - c.z;
-            T R = c.w + rp;
-            int r = lt_sq<FILT>(dx * dx + dy * dy + dz * dz, R * R, R, delta);
-            if (r == 1) cov = true;
-            else if (r < 0) und = true;
-        }
-    } else {
-        for (int k = threadIdx.x & 31; k < A.na(); k += 32) {
-            int g = A.agid(k);
-            if (g == e0 || g == e1) continue;
-            P4<T> c = A.atom(k);
-            T dx = qx - c.x, dy = qy - c.y, dz = qz - c.z;
-            T R = c.w + rp;
-            int t = lt_sq<FILT>(dx * dx + dy * dy + dz * dz, R * R, R, delta);
-            if (t == 1) cov = true;
-            else if (t < 0) und = true;
-        }
+    for (int k = threadIdx.x & 31; k < A.na(); k += 32) {
+        int g = A.agid(k);
+        if (g == e0 || g == e1) continue;
+        P4<T> c = A.atom(k);
+        T dx = qx - c.x, dy = qy - c.y, dz = qz - c.z;
+        T R = c.w + rp;
+        int t = lt_sq<FILT>(dx * dx + dy * dy + dz * dz, R * R, R, delta);
+        if (t == 1) cov = true;
+        else if (t < 0) und = true;
     }
     if (__any_sync(full, cov)) return 0;
     return __any_sync(full, und) ? -1 : 1;
