@@ -43,7 +43,7 @@ struct ClsSmem {
     unsigned nbm[CP::A * AWC];     // neighbour set of every staged atom (build_neighbour_sets)
     int bcount[NBRICK];
     short queue[TILE_PTS];         // shell points
-    int nq, band;
+    int nq, band, next;            // queue length, band points, next queue position to take
 };
 
 // a tile that overflowed the shared-memory staging goes to the list of the
@@ -225,6 +225,7 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Batch B, Tile
         if (threadIdx.x == 0) {
             C.nq = 0;
             C.band = 0;
+            C.next = 0;
             if (S.flags) atomicOr(err, S.flags);
         }
         int t[3];
@@ -313,12 +314,18 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Batch B, Tile
             __syncthreads();
         }
         // phase 2: shell points, the whole block; with few points, groups of
-        // up to 32 lanes share one (so a tile's last point is not left to one lane)
+        // up to 32 lanes share one (so a tile's last point is not left to one
+        // lane).  A thread (or group) takes the next point from a block counter
+        // when it is done, so the slow points do not pile up on a few threads.
         int gs = 1;
         while (gs < 32 && nq * gs * 2 <= CLS_THREADS) gs <<= 1;
         const int r = lane & (gs - 1);
         const unsigned gmask = (gs == 32 ? 0xffffffffu : ((1u << gs) - 1u)) << (lane & ~(gs - 1));
-        for (int k = threadIdx.x / gs; k < nq; k += CLS_THREADS / gs) {
+        for (;;) {
+            int k = 0;
+            if (r == 0) k = atomicAdd(&C.next, 1);
+            k = __shfl_sync(gmask, k, lane & ~(gs - 1));
+            if (k >= nq) break;
             int code = C.queue[k];
             int brick = (code >> 9) & 15;
             int li = (code >> 6) & 7, lj = (code >> 3) & 7, lk = code & 7;
