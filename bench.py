@@ -393,7 +393,7 @@ def main():
         tuned = {k: eses.eses_get_option(ctx, v) for k, v in (
             ("cls_ctas_per_sm", eses.ESES_OPT_CLS_CTAS), ("cls_tiles_per_pop", eses.ESES_OPT_CLS_TILES),
             ("edge_ctas_per_sm", eses.ESES_OPT_EDGE_CTAS), ("edge_tiles_per_pop", eses.ESES_OPT_EDGE_TILES),
-            ("edge_chunk", eses.ESES_OPT_EDGE_CHUNK))}
+            ("root_threads", eses.ESES_OPT_ROOT_THREADS))}
     for _ in range(args.warmup):
         eses.eses_run(ctx)
     dims, _ = eses.eses_grid(ctx)

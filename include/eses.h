@@ -83,9 +83,10 @@ typedef struct eses_ctx eses_ctx;
                                   0: fixed grid-stride order */
 #define ESES_OPT_CLS_CTAS 8    /* classification CTAs per SM (0 = occupancy limit, default) */
 #define ESES_OPT_CLS_TILES 9   /* classification tiles per queue pop (default 4) */
-#define ESES_OPT_EDGE_CTAS 10  /* root-solve CTAs per SM (0 = occupancy limit, default) */
-#define ESES_OPT_EDGE_TILES 11 /* root-solve tiles per queue pop (default 4) */
-#define ESES_OPT_EDGE_CHUNK 12 /* root-solve edges per pooled chunk at most (0 = the maximum, 128; default) */
+#define ESES_OPT_EDGE_CTAS 10  /* root-solve staging pass: CTAs per SM (0 = occupancy limit, default) */
+#define ESES_OPT_EDGE_TILES 11 /* root-solve staging pass: tiles per queue pop (default 4) */
+#define ESES_OPT_ROOT_THREADS 12 /* root solve: threads per block of the per-candidate root kernels
+                                    (0 = 256, default; 64, 128 or 256) */
 #define ESES_OPT_EXTERIOR 13   /* 1: exterior-only surface -- outside points that no path of outside grid points
                                   (6-neighbour steps) joins to the domain boundary lie in cavities and are labelled
                                   inside before the crossing edges are found (default 0: every free probe position
@@ -168,7 +169,8 @@ int eses_get_option(const eses_ctx *ctx, int key, int64_t *value);
 
 /* Autotuner: runs the context once, then times the persistent kernels
  * (classification; root solve) over their launch shapes -- CTAs per SM from 1
- * to the occupancy limit, tiles per queue pop, root-solve chunk size -- on
+ * to the occupancy limit, tiles per queue pop, threads per block of the
+ * root kernels -- on
  * the context's own workload, `reps` timed launches each (1..100), keeps the
  * fastest (readable with eses_get_option) and runs once more with it.
  * ms_out (host, 2 doubles, may be NULL): mean milliseconds of the chosen

@@ -94,7 +94,7 @@ struct MolInfo {
 struct Shape {
     int ctas_per_sm = 0;  // 0: the occupancy limit
     int tiles_per_pop = 4;
-    int chunk = 0;        // root solve: edges per pooled chunk (0: the maximum)
+    int threads = 0;      // root solve: threads per block of the per-candidate root kernels (0: 256)
 };
 
 }  // namespace
@@ -133,6 +133,9 @@ struct eses_ctx {
     DBuf scan_tmp, misc, av, counts, red_d, red_i;  // misc: err, n_fail
     DBuf fail_log;
     DBuf ovf, big;  // tiles that overflow the shared-memory staging, and the global-memory tier's scratch
+    // phased root solve: edge records, candidates, their roots, staged tiles (slabs), counters, hard edges
+    DBuf r_einfo, r_ecnt, r_csph, r_ctor, r_nsph, r_ntor, r_rsph, r_rtor, r_slab, r_ctr, r_hard;
+    long long cap_sph = 0, cap_tor = 0, cap_slab = 0;  // planned capacities
     DBuf atom_hi, atom_lo, pair_hi, pair_lo, pair_u32, vert_hi, vert_lo;
     // plan: list sizes of the first run (the inputs never change)
     bool planned = false;
@@ -515,6 +518,38 @@ TileSched sched_of(eses_ctx *c, const Shape &s, int which)
     return q;
 }
 
+// Buffers of the phased root solve.  Planning: capacities from a first
+// estimate per crossing edge (grown by run_device when the staging pass needs
+// more); capturing: the planned capacities.
+constexpr long long SLAB_CAP_MAX = 16LL * 2147483647LL;  // slab offsets are 16-byte units in an int
+RootWork root_work(eses_ctx *c, long long ne_all)
+{
+    const long long ne = std::max(ne_all, 1LL);
+    if (!g_capturing) {
+        c->cap_sph = std::max(c->cap_sph, 3 * ne + 1024);
+        c->cap_tor = std::max(c->cap_tor, 4 * ne + 1024);
+        c->cap_slab = std::max(c->cap_slab, 96 * ne + (1LL << 20));
+        c->cap_slab = std::min(c->cap_slab, SLAB_CAP_MAX);
+    }
+    RootWork W;
+    W.einfo = ensure<int4>(c->r_einfo, (size_t)ne);
+    W.ecnt = ensure<int>(c->r_ecnt, (size_t)ne);
+    W.hard = ensure<int>(c->r_hard, (size_t)ne);
+    W.csph = ensure<int2>(c->r_csph, (size_t)c->cap_sph);
+    W.nsph = ensure<uint8_t>(c->r_nsph, (size_t)c->cap_sph);
+    W.rsph = ensure<RootRec>(c->r_rsph, 2 * (size_t)c->cap_sph);
+    W.ctor = ensure<int2>(c->r_ctor, (size_t)c->cap_tor);
+    W.ntor = ensure<uint8_t>(c->r_ntor, (size_t)c->cap_tor);
+    W.rtor = ensure<RootRec>(c->r_rtor, 4 * (size_t)c->cap_tor);
+    W.slab = ensure<unsigned char>(c->r_slab, (size_t)c->cap_slab);
+    W.ctr = ensure<unsigned long long>(c->r_ctr, 4);
+    W.cap_slab = c->cap_slab;
+    W.cap_sph = c->cap_sph;
+    W.cap_tor = c->cap_tor;
+    W.n_edges = ne_all;
+    return W;
+}
+
 // The device path of one run.  Planning (not capturing): reads list totals
 // and sizes every buffer; capturing: uses the planned sizes and touches no
 // host memory.  Returns the number of kernels launched.
@@ -746,10 +781,29 @@ int run_device(eses_ctx *c)
     long long *cnt = ensure<long long>(c->counts, 2 * (size_t)c->n_mol);
     long long *fail_log = ensure<long long>(c->fail_log, FAIL_LOG * FAIL_REC);
     mark(c, ST_EDGE_SOLVE);
-    const int chunk = c->edge.chunk > 0 ? c->edge.chunk : edge_chunk_max();
-    nl += launch_edge_solve(M, B, c->precision, sched_of(c, c->edge, 1),
-                            grid_of(c, c->edge, edge_ctas_per_sm(c->precision)), chunk, labels, edge_start, eo, d_fail,
-                            d_err, fail_log, ovf, big, st);
+    RootWork W = root_work(c, ne_all);
+    const TileSched eq = sched_of(c, c->edge, 1);
+    const int eg = grid_of(c, c->edge, edge_ctas_per_sm(c->precision));
+    nl += launch_edge_stage(M, B, c->precision, eq, eg, labels, edge_start, eo, d_err, ovf, big, W, st);
+    if (!g_capturing) {  // planning: the totals the staging pass needed; a full buffer is grown and the pass rerun
+        unsigned long long need[3] = {0, 0, 0};
+        int ov[2] = {0, 0};
+        ck(cudaMemcpyAsync(need, W.ctr, sizeof(need), cudaMemcpyDeviceToHost, st), "read");
+        ck(cudaMemcpyAsync(ov, ovf, sizeof(ov), cudaMemcpyDeviceToHost, st), "read");
+        ck(cudaStreamSynchronize(st), "synchronize");
+        if ((long long)need[0] > W.cap_slab || (long long)need[1] > W.cap_sph || (long long)need[2] > W.cap_tor) {
+            c->cap_slab = std::max(c->cap_slab, (long long)(need[0] + need[0] / 8));
+            c->cap_sph = std::max(c->cap_sph, (long long)(need[1] + need[1] / 8));
+            c->cap_tor = std::max(c->cap_tor, (long long)(need[2] + need[2] / 8));
+            W = root_work(c, ne_all);
+            // the tiles the first pass gave the global-memory tier are counted again
+            const int run_total = ov[0] - ov[1];
+            ck(cudaMemcpyAsync(ovf, &run_total, sizeof(int), cudaMemcpyHostToDevice, st), "write");
+            nl += launch_edge_stage(M, B, c->precision, eq, eg, labels, edge_start, eo, d_err, ovf, big, W, st);
+        }
+    }
+    nl += launch_edge_roots(M, B, c->precision, c->edge.threads, eo, edge_start, ne_all, d_fail, d_err, fail_log, W,
+                            st);
     mark(c, ST_EDGE_POLISH);
     nl += launch_edge_polish(M, B, eo, ne_all, medge, term, st);
     mark(c, ST_REDUCE);
@@ -1081,11 +1135,11 @@ int eses_set_option(eses_ctx *c, int key, int64_t value)
         drop_graph(c);
         (key == ESES_OPT_CLS_TILES ? c->cls : c->edge).tiles_per_pop = (int)value;
         return ESES_OK;
-    case ESES_OPT_EDGE_CHUNK:
-        if (value < 0 || value > edge_chunk_max())
-            return fail(c, ESES_EINVAL, "edge chunk must be in [0, " + std::to_string(edge_chunk_max()) + "]");
+    case ESES_OPT_ROOT_THREADS:
+        if (value < 0 || value > 256 || !root_threads_valid((int)value))
+            return fail(c, ESES_EINVAL, "root threads must be 0, 64, 128 or 256");
         drop_graph(c);
-        c->edge.chunk = (int)value;
+        c->edge.threads = (int)value;
         return ESES_OK;
     case ESES_OPT_CULL:
         if (value != 0 && value != 1) return fail(c, ESES_EINVAL, "cull must be 0 or 1");
@@ -1137,7 +1191,7 @@ int eses_get_option(const eses_ctx *cc, int key, int64_t *value)
     case ESES_OPT_EDGE_CTAS: *value = c->edge.ctas_per_sm; return ESES_OK;
     case ESES_OPT_CLS_TILES: *value = c->cls.tiles_per_pop; return ESES_OK;
     case ESES_OPT_EDGE_TILES: *value = c->edge.tiles_per_pop; return ESES_OK;
-    case ESES_OPT_EDGE_CHUNK: *value = c->edge.chunk; return ESES_OK;
+    case ESES_OPT_ROOT_THREADS: *value = c->edge.threads; return ESES_OK;
     case ESES_OPT_EXTERIOR: *value = c->exterior ? 1 : 0; return ESES_OK;
     default: return fail(c, ESES_EINVAL, "unknown option key " + std::to_string(key));
     }
@@ -1201,7 +1255,7 @@ int eses_autotune(eses_ctx *c, int reps, double *ms_out)
             }
         if (c->precision != ESES_PREC_FP64)
             launch_band(M, B, labels, tile_band, misc, (int *)c->ovf.p, (unsigned char *)c->big.p, st);
-        // root solve: CTAs per SM x tiles per pop x chunk
+        // root solve: staging CTAs per SM x tiles per pop x root-kernel threads per block
         Shape best_edge = c->edge;
         float best_edge_ms = INFINITY;
         EdgeOut eo;
@@ -1213,18 +1267,36 @@ int eses_autotune(eses_ctx *c, int reps, double *ms_out)
             eo.nrm32[a] = (float *)c->out_nrm32[a].p;
             eo.code[a] = (int2 *)c->out_code[a].p;
         }
+        RootWork W;  // the planned buffers of the run above
+        W.einfo = (int4 *)c->r_einfo.p;
+        W.ecnt = (int *)c->r_ecnt.p;
+        W.hard = (int *)c->r_hard.p;
+        W.csph = (int2 *)c->r_csph.p;
+        W.nsph = (uint8_t *)c->r_nsph.p;
+        W.rsph = (RootRec *)c->r_rsph.p;
+        W.ctor = (int2 *)c->r_ctor.p;
+        W.ntor = (uint8_t *)c->r_ntor.p;
+        W.rtor = (RootRec *)c->r_rtor.p;
+        W.slab = (unsigned char *)c->r_slab.p;
+        W.ctr = (unsigned long long *)c->r_ctr.p;
+        W.cap_slab = c->cap_slab;
+        W.cap_sph = c->cap_sph;
+        W.cap_tor = c->cap_tor;
+        const long long ne_all = c->n_edges[0] + c->n_edges[1] + c->n_edges[2];
+        W.n_edges = ne_all;
         for (int k = 1; k <= edge_max; ++k)
             for (int per : {1, 4})
-                for (int chunk : {32, 64, edge_chunk_max()}) {
+                for (int threads : {128, 256}) {
                     Shape s;
                     s.ctas_per_sm = k;
                     s.tiles_per_pop = per;
-                    s.chunk = chunk;
+                    s.threads = threads;
                     float ms = time_it([&] {
-                        ck(cudaMemsetAsync(c->queue.p, 0, 4 * sizeof(unsigned long long), st), "memset");
-                        launch_edge_solve(M, B, c->precision, sched_of(c, s, 1), grid_of(c, s, edge_max), chunk,
-                                          labels, (const int *)c->edge_start.p, eo, misc + 1, misc,
-                                          (long long *)c->fail_log.p, (int *)c->ovf.p, (unsigned char *)c->big.p, st);
+                        launch_edge_stage(M, B, c->precision, sched_of(c, s, 1), grid_of(c, s, edge_max), labels,
+                                          (const int *)c->edge_start.p, eo, misc, (int *)c->ovf.p,
+                                          (unsigned char *)c->big.p, W, st);
+                        launch_edge_roots(M, B, c->precision, threads, eo, (const int *)c->edge_start.p, ne_all,
+                                          misc + 1, misc, (long long *)c->fail_log.p, W, st);
                     });
                     if (ms < best_edge_ms) best_edge_ms = ms, best_edge = s;
                 }
@@ -1794,7 +1866,9 @@ void eses_destroy(eses_ctx *c)
                     &c->pair_free, &c->vert_count, &c->vert_start, &c->vert, &c->vert_atoms, &c->pbin_count, &c->pbin_start,
                     &c->pbin_cursor, &c->pbin_cell, &c->pbin_list, &c->vbin_count, &c->vbin_start, &c->vbin_cursor,
                     &c->vbin_cell, &c->vbin_list, &c->labels, &c->tile_band, &c->tile_edges, &c->edge_start,
-                    &c->tile_inside, &c->scan_tmp, &c->misc, &c->av, &c->counts, &c->red_d, &c->red_i, &c->fail_log, &c->ovf, &c->big, &c->atom_hi,
+                    &c->tile_inside, &c->scan_tmp, &c->misc, &c->av, &c->counts, &c->red_d, &c->red_i, &c->fail_log,
+                    &c->ovf, &c->big, &c->r_einfo, &c->r_ecnt, &c->r_csph, &c->r_ctor, &c->r_nsph, &c->r_ntor,
+                    &c->r_rsph, &c->r_rtor, &c->r_slab, &c->r_ctr, &c->r_hard, &c->atom_hi,
                     &c->atom_lo, &c->pair_hi, &c->pair_lo, &c->pair_u32, &c->vert_hi, &c->vert_lo,
                     &c->mlp_params, &c->need, &c->need_pos, &c->tile_list, &c->prop_counts, &c->features,
                     &c->targets, &c->ext, &c->ext_open, &c->ext_misc, &c->mesh_mask, &c->mesh_tile, &c->mesh_off,

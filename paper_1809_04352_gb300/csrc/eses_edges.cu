@@ -5,32 +5,37 @@
 //   points whose end labels differ, and the edges with both ends inside.
 // (exclusive scan of the counts -> every tile's output offset per axis; the
 //   paper serialises this output step in a critical section, Algorithm 1)
-// k_edge_solve: persistent CTAs take tiles from the work queue; per tile the
-//   patches are staged and the tile's crossing edges taken in chunks of at
-//   most 128.  The surface along an edge is made of pieces of van der Waals
-//   spheres (convex), tori around pair circles (saddle) and probe spheres
-//   around free triple points (concave).  Every root of every such piece in
-//   [0, h] whose witness (projection on the expanded sphere / nearest circle
-//   point / the triple point) is free, and whose witness distance crosses r_p
-//   in the direction that leaves the end point's side (falling from an inside
-//   end, rising from an outside end), is a candidate.  From an inside end
-//   point the first candidate is the first root; from an outside end point the
-//   first candidate that is not strictly outside M is.  Per chunk:
-//     1. (edge, piece) pairs that pass a prefilter go to a block pool (one
-//        warp per edge, lanes over the staged pieces);
-//     2. one thread per pair: sphere roots from the quadratic; torus roots of
+// The root solve: the surface along an edge is made of pieces of van der
+//   Waals spheres (convex), tori around pair circles (saddle) and probe
+//   spheres around free triple points (concave).  Every root of every such
+//   piece in [0, h] whose witness (projection on the expanded sphere /
+//   nearest circle point / the triple point) is free, and whose witness
+//   distance crosses r_p in the direction that leaves the end point's side
+//   (falling from an inside end, rising from an outside end), is a candidate.
+//   From an inside end point the first candidate is the first root; from an
+//   outside end point the first candidate that is not strictly outside M is.
+//   Five launches linked by lists in HBM:
+//   k_edge_stage: persistent CTAs take tiles from the work queue; per tile
+//     the pieces are staged (shared memory, or the global-memory tier for a
+//     tile that overflows it), the crossing edges listed, and written out:
+//     the staged lists (the tile's slab), an edge record per edge, and the
+//     (edge, piece) pairs that pass a prefilter (one warp per edge, lanes over
+//     the staged pieces), spheres and tori in separate lists;
+//   k_roots_sphere / k_roots_torus: one thread per pair, no block barrier:
+//     sphere roots from the quadratic; torus roots of
 //          (|y-o|^2 + rho^2 - r_p^2)^2 = 4 rho^2 (|y-o|^2 - ((y-o).u)^2)
-//        on the near branch (|w| - rho)^2 + z^2 = r_p^2, isolated in FP32 on
-//        eight sub-intervals with certified exclusion and monotonicity tests
-//        and refined by Newton (undecided: the quartic on its derivative
-//        chain, then FP64); every FP32 root carries an error bound;
-//     3. the roots grouped by edge (counting sort);
-//     4. the first root per edge: one thread when the end point is inside or
-//        one candidate is left and the FP32 bounds order the candidates; else
-//        a warp: near ties broken on FP64 roots; at an outside end point each
-//        earlier candidate tested first against the later candidates'
-//        witnesses, then by the full witness search, whose undecided items
-//        are re-tested in FP64.
+//     on the near branch (|w| - rho)^2 + z^2 = r_p^2, isolated in FP32 on
+//     eight sub-intervals with certified exclusion and monotonicity tests and
+//     refined by Newton (undecided: the quartic on its derivative chain, then
+//     FP64); every FP32 root carries an error bound; the accepted roots go to
+//     the pair's slots;
+//   k_edge_pick: one thread per edge: the first root when the end point is
+//     inside or one candidate is left and the FP32 bounds order the
+//     candidates; the other edges are listed;
+//   k_edge_hard: one warp per listed edge: near ties broken on FP64 roots; at
+//     an outside end point each earlier candidate tested first against the
+//     later candidates' witnesses, then by the full witness search, whose
+//     undecided items are re-tested in FP64.
 //   The chosen piece and its FP32 root are recorded for the polish.
 // k_edge_polish: one thread per crossing edge (full warps of FP64 work): the
 //   FP64 root of the chosen piece next to the recorded one, the normal, the
@@ -40,6 +45,8 @@
 // Every tile kernel runs over the tiles of all molecules of a batch.
 #include <math.h>
 
+#include <algorithm>
+
 #include "eses_kernels.h"
 #include "eses_tile.cuh"
 
@@ -48,9 +55,9 @@ namespace eses {
 constexpr int EDGE_THREADS = 256;
 constexpr int EDGE_WARPS = EDGE_THREADS / 32;
 constexpr int WCAND = 64;        // candidate roots of one edge in the selection buffer
-constexpr int CHUNK = 128;       // edges per chunk of the pooled root solve (at most)
-constexpr int POOL_MAX = 2048;   // (edge, item) pairs of a chunk that pass the prefilter
-constexpr int ROOT_MAX = 512;    // valid roots of a chunk
+constexpr int ROOT_THREADS_MAX = 256;  // per-candidate root kernels: threads per block (at most, the default)
+constexpr int PICK_THREADS = 256;
+constexpr int HARD_THREADS = 256;
 constexpr int POLISH_THREADS = 256;
 
 // --------------------------------------------------------------------------
@@ -266,55 +273,193 @@ __device__ __noinline__ double staged_exact_root(const XA &X, int kind, int slot
 }
 
 // --------------------------------------------------------------------------
-// root candidates of a tile's crossing edges, pooled over the block
+// the phased root solve: data between the launches
 // --------------------------------------------------------------------------
+// A candidate root of one crossing edge during the selection.
 struct WCand {
     double t64;    // exact root once computed (NaN before)
     float t, err;  // FP32 root and its error bound (A)
     int kind, id;  // kind 0: van der Waals sphere (atom slot), 1: torus (pair slot), 2: probe sphere (vertex slot)
 };
 
-struct EdgeSmem {
+// Accepted roots of one (edge, piece) candidate, written to the candidate's
+// slots in HBM (at most SPH_SLOTS for a sphere, whose two roots cross in
+// opposite directions; at most TOR_SLOTS, the quartic's degree, for a torus).
+constexpr int SPH_SLOTS = 2;
+constexpr int TOR_SLOTS = 4;
+struct RootSink {
+    RootRec *r;
+    int n, cap;
+    __device__ __forceinline__ void push(float t, float err, double t64)
+    {
+        if (n < cap) {
+            RootRec q;
+            q.t64 = t64;
+            q.t = t;
+            q.err = err;
+            r[n] = q;
+        }
+        ++n;
+    }
+};
+
+// einfo[].y: lower point (local index), axis, end label, dropped (a buffer of
+// the staging pass was full)
+__host__ __device__ constexpr int edge_pack(int p, int axis, int lab, int dropped)
+{
+    return p | (axis << 9) | (lab << 11) | (dropped << 12);
+}
+__device__ __forceinline__ int pk_point(int pk) { return pk & 511; }
+__device__ __forceinline__ int pk_axis(int pk) { return (pk >> 9) & 3; }
+__device__ __forceinline__ int pk_label(int pk) { return (pk >> 11) & 1; }
+__device__ __forceinline__ bool pk_dropped(int pk) { return ((pk >> 12) & 1) != 0; }
+
+// A staged tile in HBM (its slab): this header, then the staged lists in the
+// tile frame, each segment 16-byte aligned.  Written once by the staging pass
+// and read (through L1/L2) by every root and selection thread of the tile.
+struct alignas(16) SlabHdr {
+    int na, np, nv, mol;
+    double x0[3];  // tile frame origin (absolute)
+    int t[3];      // tile coordinates in the run's grid
+    int gt;        // batch tile
+};
+
+__host__ __device__ constexpr long long align16(long long b) { return (b + 15) & ~15LL; }
+
+template <class T>
+struct SlabLayout {
+    long long atom, po, pu, vq, agid, pij, pidx, vidx, face, bytes;
+    __host__ __device__ SlabLayout(int na, int np, int nv)
+    {
+        const long long P = (long long)sizeof(P4<T>);
+        atom = (long long)sizeof(SlabHdr);
+        po = atom + na * P;
+        pu = po + np * P;
+        vq = pu + np * P;
+        agid = vq + nv * P;
+        pij = align16(agid + 4LL * na);
+        pidx = align16(pij + 8LL * np);
+        vidx = align16(pidx + 4LL * np);
+        face = align16(vidx + 4LL * nv);
+        bytes = align16(face + na);
+    }
+};
+
+__device__ __forceinline__ P4<float> ldg4(const P4<float> *p)
+{
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    return P4<float>{v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ P4<double> ldg4(const P4<double> *p)
+{
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    return P4<double>{a.x, a.y, b.x, b.y};
+}
+
+// the staged lists of a slab (same interface as SmemAcc)
+template <class T>
+struct SlabAcc {
+    using real = T;
+    const P4<T> *a_, *po_, *pu_, *vq_;
+    const int *agid_, *pidx_, *vidx_;
+    const int2 *pij_;
+    const uint8_t *face_;
+    int na_, np_, nv_;
+    __device__ explicit SlabAcc(const unsigned char *s)
+    {
+        const int4 h = __ldg(reinterpret_cast<const int4 *>(s));
+        na_ = h.x;
+        np_ = h.y;
+        nv_ = h.z;
+        const SlabLayout<T> L(na_, np_, nv_);
+        a_ = reinterpret_cast<const P4<T> *>(s + L.atom);
+        po_ = reinterpret_cast<const P4<T> *>(s + L.po);
+        pu_ = reinterpret_cast<const P4<T> *>(s + L.pu);
+        vq_ = reinterpret_cast<const P4<T> *>(s + L.vq);
+        agid_ = reinterpret_cast<const int *>(s + L.agid);
+        pij_ = reinterpret_cast<const int2 *>(s + L.pij);
+        pidx_ = reinterpret_cast<const int *>(s + L.pidx);
+        vidx_ = reinterpret_cast<const int *>(s + L.vidx);
+        face_ = reinterpret_cast<const uint8_t *>(s + L.face);
+    }
+    __device__ int na() const { return na_; }
+    __device__ int np() const { return np_; }
+    __device__ int nv() const { return nv_; }
+    __device__ P4<T> atom(int a) const { return ldg4(a_ + a); }
+    __device__ int agid(int a) const { return __ldg(agid_ + a); }
+    __device__ bool face(int a) const { return __ldg(face_ + a) != 0; }
+    __device__ P4<T> po(int p) const { return ldg4(po_ + p); }
+    __device__ P4<T> pu(int p) const { return ldg4(pu_ + p); }
+    __device__ int2 pij(int p) const { return __ldg(pij_ + p); }
+    __device__ P4<T> vq(int v) const { return ldg4(vq_ + v); }
+    __device__ int pidx(int p) const { return __ldg(pidx_ + p); }
+    __device__ int vidx(int v) const { return __ldg(vidx_ + v); }
+    // model index of a staged piece (kind as in WCand)
+    __device__ int model_index(int kind, int slot) const
+    {
+        return kind == 0 ? agid(slot) : (kind == 1 ? pidx(slot) : vidx(slot));
+    }
+};
+
+// FP64 data of a slab's pieces from HBM, in the same tile frame (as ExactAcc)
+template <class T>
+struct SlabExact {
+    using real = double;
+    const SlabAcc<T> &S;
+    const Model &M;
+    double x0, y0, z0;
+    __device__ SlabExact(const SlabAcc<T> &s, const Model &m, const double *o)
+        : S(s), M(m), x0(o[0]), y0(o[1]), z0(o[2]) {}
+    __device__ int na() const { return S.na(); }
+    __device__ int np() const { return S.np(); }
+    __device__ int nv() const { return S.nv(); }
+    __device__ P4<double> atom(int a) const
+    {
+        const double4 g = M.atom[S.agid(a)];
+        return P4<double>{g.x - x0, g.y - y0, g.z - z0, g.w};
+    }
+    __device__ int agid(int a) const { return S.agid(a); }
+    __device__ bool face(int a) const { return S.face(a); }
+    __device__ P4<double> po(int p) const
+    {
+        const double4 g = M.pair_o[S.pidx(p)];
+        return P4<double>{g.x - x0, g.y - y0, g.z - z0, g.w};
+    }
+    __device__ P4<double> pu(int p) const
+    {
+        const double4 g = M.pair_u[S.pidx(p)];
+        return P4<double>{g.x, g.y, g.z, 0.0};
+    }
+    __device__ int2 pij(int p) const { return S.pij(p); }
+    __device__ P4<double> vq(int v) const
+    {
+        const double4 g = M.vert[S.vidx(v)];
+        return P4<double>{g.x - x0, g.y - y0, g.z - z0, 0.0};
+    }
+};
+
+// shared memory of the staging pass (beside the staged tile)
+struct StageSmem {
     double hd[TILE + 1];  // k * h, k = 0..8
     int8_t lab[9 * 9 * 9];
     short eptr[3 * TILE_PTS];  // crossing edges of the tile (local point), grouped by axis
+    int cs[3 * TILE_PTS + 1];  // per edge: sphere candidates, then their offset in the tile's run
+    int ct[3 * TILE_PTS + 1];  // the same for tori
     int estart[4];
-    long long ebase[3];
-    int sh[EDGE_WARPS];
-    // the current chunk of edges [c0, c0 + CHUNK): (edge, item) pairs that pass
-    // the prefilter, then the roots they give (valid pieces only)
-    int npool, npool_t, nroot, next_c, next_e, nhard;
-    short hard[CHUNK];        // edges of the chunk left to the warp selection
-    unsigned pool[POOL_MAX];  // (edge << 16) | item: spheres from the front, tori from the back
-    WCand root[ROOT_MAX];
-    short redge[ROOT_MAX];
-    short rorder[ROOT_MAX];   // roots grouped by edge
-    int rstart[CHUNK + 1];
-    int rfill[CHUNK];
-    // per-warp selection buffer
-    WCand cand[EDGE_WARPS][WCAND];
-    int ncand[EDGE_WARPS];
+    int gbase[3];  // global id of the tile's first edge per axis (all axes numbered in one run)
+    int abase[3];  // its index in the axis' output
+    int sh[EDGE_WARPS], sh2[EDGE_WARPS];
+    long long slab;    // slab offset (16-byte units), -1 when the slab buffer is full
+    long long sb, tb;  // the tile's first sphere / torus candidate, -1 when a buffer is full
+    long long sb0, tb0;  // the same as reserved (also when a buffer is full)
 };
-
-__device__ __forceinline__ void pool_push(EdgeSmem &E, int e, float t, float err, double t64, int kind, int id)
-{
-    int slot = atomicAdd(&E.nroot, 1);
-    if (slot < ROOT_MAX) {
-        WCand &c = E.root[slot];
-        c.t = t;
-        c.err = err;
-        c.t64 = t64;
-        c.kind = kind;
-        c.id = id;
-        E.redge[slot] = (short)e;
-    }
-}
 
 // axis, lower point (local index) and its label of crossing edge e of the tile
 struct EdgeRef {
     int axis, p, lab;
 };
-__device__ __forceinline__ EdgeRef edge_ref(const EdgeSmem &E, int e)
+__device__ __forceinline__ EdgeRef edge_ref(const StageSmem &E, int e)
 {
     EdgeRef r;
     r.axis = e < E.estart[1] ? 0 : (e < E.estart[2] ? 1 : 2);
@@ -478,7 +623,7 @@ __device__ __noinline__ bool torus_roots32(const float *q0, const float *u, floa
 // [0, h], its witness distance crosses r_p in the direction that leaves the
 // end point's side, and its witness (nearest circle point) is free.
 template <class Acc>
-__device__ __noinline__ void torus_root_exact(const Acc &X, EdgeSmem &E, int e, int pi, const double *s64, int axis,
+__device__ __noinline__ void torus_root_exact(const Acc &X, RootSink &out, int pi, const double *s64, int axis,
                                               double h, double rp, bool inside, double t64)
 {
     if (!(t64 >= 0.0 && t64 <= h)) return;
@@ -499,12 +644,12 @@ __device__ __noinline__ void torus_root_exact(const Acc &X, EdgeSmem &E, int e, 
     const int2 ij = X.pij(pi);
     const int f = free_pt<false>(X, oo[0] + oe.w * wd[0], oo[1] + oe.w * wd[1], oo[2] + oe.w * wd[2], ij.x, ij.y, rp,
                                  0.0);
-    if (f == 1) pool_push(E, e, (float)t64, 0.0f, t64, 1, pi);
+    if (f == 1) out.push((float)t64, 0.0f, t64);
 }
 
 // Every root of a torus piece in [0, h] from the quartic, each decided in FP64.
 template <class Acc>
-__device__ __noinline__ void torus_piece_exact(const Acc &X, EdgeSmem &E, int e, int pi, const double *s64, int axis,
+__device__ __noinline__ void torus_piece_exact(const Acc &X, RootSink &out, int pi, const double *s64, int axis,
                                                double h, double rp, bool inside)
 {
     const P4<double> oe = X.po(pi);
@@ -513,7 +658,7 @@ __device__ __noinline__ void torus_piece_exact(const Acc &X, EdgeSmem &E, int e,
     double co[5], r64[4];
     torus_coeffs(oo, u64, oe.w, rp, s64, axis, co);
     const int n = PolyRoots<double, 4>::run(co, 0.0, h, r64);
-    for (int k = 0; k < n; ++k) torus_root_exact(X, E, e, pi, s64, axis, h, rp, inside, r64[k]);
+    for (int k = 0; k < n; ++k) torus_root_exact(X, out, pi, s64, axis, h, rp, inside, r64[k]);
 }
 
 // Can item `it` (staged atom, vertex or pair, in that order) put a root on the
@@ -549,106 +694,115 @@ __device__ __forceinline__ bool cand_test(const TileS<T, CP> &S, const T *s, int
     return fabs(gm) <= T(0.5) * hT + mg;
 }
 
-// Roots of one (edge, item) pair that can be the surface on that edge: every
-// root in [0, h] of the piece whose witness distance crosses r_p in the
+// Roots of one (edge, piece) candidate that can be the surface on that edge:
+// every root in [0, h] of the piece whose witness distance crosses r_p in the
 // direction that leaves the end point's side (falling from an inside end,
-// rising from an outside end) and whose witness is free.  FP32 roots carry
-// an error bound; a decision the bound cannot make goes to FP64.
-template <class T, bool FILT, class CP>
-__device__ void cand_roots(const Model &M, const TileS<T, CP> &S, const double *x0, EdgeSmem &E, int e, int it, double h,
-                           double rp, T d0)
+// rising from an outside end) and whose witness is free.  FP32 roots carry an
+// error bound; a decision the bound cannot make goes to FP64.  A: the staged
+// lists (tile frame), X: the same pieces in FP64; s64 the edge's lower point
+// in the tile frame.
+//
+// Spheres (item < na: van der Waals sphere of staged atom `item`, convex,
+// witness = projection on the expanded sphere; else the probe sphere of staged
+// triple point item - na, concave, witness = the triple point).
+template <class T, bool FILT, class AccT, class AccX>
+__device__ void sphere_roots(const AccT &A, const AccX &X, int item, const double *s64, int axis, bool inside,
+                             double h, double rp, T d0, RootSink &out)
 {
-    const EdgeRef R = edge_ref(E, e);
-    const int axis = R.axis;
-    const double s64[3] = {E.hd[R.p >> 6], E.hd[(R.p >> 3) & 7], E.hd[R.p & 7]};
     const T s[3] = {(T)s64[0], (T)s64[1], (T)s64[2]};
-    SmemAcc<T, CP> A(S);
-    ExactAcc<T, CP> X(S, M, x0);
-    const int na = S.na, nv = S.nv;
+    const int na = A.na();
     const T hT = (T)h, rpT = (T)rp;
     const T lo = FILT ? T(-1e-4) : T(0), hi = hT + (FILT ? T(1e-4) : T(0));
     const T tmax = T(1e-3);  // FP32 root error beyond which FP64 decides (grazing pieces)
-    const bool inside = R.lab == LABEL_IN;
     const double NaN = __longlong_as_double(0x7ff8000000000000LL);
-    if (it < na + nv) {  // spheres: convex (van der Waals, witness = projection) or concave (probe)
-        const bool vdw = it < na;
-        const int slot = vdw ? it : it - na;
-        P4<T> c = vdw ? S.atom[slot] : S.vq[slot];
-        const T rad = vdw ? c.w : rpT;
-        T d[3] = {s[0] - c.x, s[1] - c.y, s[2] - c.z};
-        T dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-        T b = d[axis], disc = b * b - (dd - rad * rad);
-        T co32[3] = {dd - rad * rad, T(2) * b, T(1)};
-        T rt32[2];
-        int nr = PolyRoots<T, 2>::run(co32, lo, hi, rt32);
-        if (FILT && nr == 0 && disc < T(2e-3)) {  // grazing: let FP64 decide
-            rt32[0] = -b;
-            nr = (-b >= lo && -b <= hi) ? 1 : 0;
-        }
-        for (int k = 0; k < nr; ++k) {
-            T t = rt32[k];
-            T vA = d[axis] + t;  // +-sqrt(disc) at a root: the rate of |y - c|
-            T terr = T(0);
-            if (FILT) {
-                T derr = T(2) * (fabs(b) + sqrt(dd)) * d0 + T(2e-6) * (dd + rad * rad);
-                terr = d0 + derr / (T(2) * fmax(fabs(vA), T(1e-20)));
-            }
-            double t64 = NaN;
-            bool exact = FILT && (terr > tmax || t < terr + T(1e-6) || t > hT - terr - T(1e-6));
-            if (exact) {
-                P4<double> ce = vdw ? X.atom(slot) : X.vq(slot);
-                double cc[3] = {ce.x, ce.y, ce.z};
-                double r64 = vdw ? ce.w : rp;
-                t64 = exact_root_sphere(cc, r64, s64, axis, (double)t);
-                double dv[3] = {s64[0] - cc[0], s64[1] - cc[1], s64[2] - cc[2]};
-                dv[axis] += t64;
-                double f = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2] - r64 * r64;
-                if (!(t64 >= 0.0 && t64 <= h) || fabs(f) > 1e-9 * r64) continue;
-                vA = (T)dv[axis];
-                if (fabs(dv[axis]) <= 1e-9 * r64) vA = T(0);  // tangent: either way
-                t = (T)t64;
-                terr = T(0);
-            }
-            // witness distance: R - |y - c| (convex) falls iff vA > 0; |y - v| (concave) rises iff vA > 0
-            const bool rises = vdw ? (vA < T(0)) : (vA > T(0));
-            const bool falls = vdw ? (vA > T(0)) : (vA < T(0));
-            if (inside ? rises : falls) continue;
-            if (vdw) {
-                T v32[3] = {d[0], d[1], d[2]};
-                v32[axis] += t;
-                T nvv = sqrt(v32[0] * v32[0] + v32[1] * v32[1] + v32[2] * v32[2]);
-                T Rr = c.w + rpT;
-                T sc = Rr / nvv;
-                int f = -1;
-                if (FILT) {
-                    T delta = d0 + terr * (T(1) + sc) + T(2e-6);
-                    f = free_pt<true>(A, c.x + sc * v32[0], c.y + sc * v32[1], c.z + sc * v32[2], S.agid[slot], -1,
-                                      rpT, delta);
-                }
-                if (f < 0) {
-                    P4<double> ce = X.atom(slot);
-                    double cc[3] = {ce.x, ce.y, ce.z};
-                    if (t64 != t64) t64 = exact_root_sphere(cc, ce.w, s64, axis, (double)t);
-                    double v[3] = {s64[0] - cc[0], s64[1] - cc[1], s64[2] - cc[2]};
-                    v[axis] += t64;
-                    double nv64 = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-                    double R64 = ce.w + rp;
-                    f = free_pt<false>(X, cc[0] + R64 * v[0] / nv64, cc[1] + R64 * v[1] / nv64,
-                                       cc[2] + R64 * v[2] / nv64, S.agid[slot], -1, rp, 0.0);
-                }
-                if (f != 1) continue;
-            }
-            pool_push(E, e, (float)t, (float)terr, t64, vdw ? 0 : 2, slot);
-        }
-        return;
+    const bool vdw = item < na;
+    const int slot = vdw ? item : item - na;
+    const P4<T> c = vdw ? A.atom(slot) : A.vq(slot);
+    const T rad = vdw ? c.w : rpT;
+    const T d[3] = {s[0] - c.x, s[1] - c.y, s[2] - c.z};
+    const T dd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const T b = d[axis], disc = b * b - (dd - rad * rad);
+    const T co32[3] = {dd - rad * rad, T(2) * b, T(1)};
+    T rt32[2];
+    int nr = PolyRoots<T, 2>::run(co32, lo, hi, rt32);
+    if (FILT && nr == 0 && disc < T(2e-3)) {  // grazing: let FP64 decide
+        rt32[0] = -b;
+        nr = (-b >= lo && -b <= hi) ? 1 : 0;
     }
-    // saddle: torus around a free-arc circle
-    const int pi = it - na - nv;
+    for (int k = 0; k < nr; ++k) {
+        T t = rt32[k];
+        T vA = d[axis] + t;  // +-sqrt(disc) at a root: the rate of |y - c|
+        T terr = T(0);
+        if (FILT) {
+            const T derr = T(2) * (fabs(b) + sqrt(dd)) * d0 + T(2e-6) * (dd + rad * rad);
+            terr = d0 + derr / (T(2) * fmax(fabs(vA), T(1e-20)));
+        }
+        double t64 = NaN;
+        const bool exact = FILT && (terr > tmax || t < terr + T(1e-6) || t > hT - terr - T(1e-6));
+        if (exact) {
+            const P4<double> ce = vdw ? X.atom(slot) : X.vq(slot);
+            const double cc[3] = {ce.x, ce.y, ce.z};
+            const double r64 = vdw ? ce.w : rp;
+            t64 = exact_root_sphere(cc, r64, s64, axis, (double)t);
+            double dv[3] = {s64[0] - cc[0], s64[1] - cc[1], s64[2] - cc[2]};
+            dv[axis] += t64;
+            const double f = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2] - r64 * r64;
+            if (!(t64 >= 0.0 && t64 <= h) || fabs(f) > 1e-9 * r64) continue;
+            vA = (T)dv[axis];
+            if (fabs(dv[axis]) <= 1e-9 * r64) vA = T(0);  // tangent: either way
+            t = (T)t64;
+            terr = T(0);
+        }
+        // witness distance: R - |y - c| (convex) falls iff vA > 0; |y - v| (concave) rises iff vA > 0
+        const bool rises = vdw ? (vA < T(0)) : (vA > T(0));
+        const bool falls = vdw ? (vA > T(0)) : (vA < T(0));
+        if (inside ? rises : falls) continue;
+        if (vdw) {
+            T v32[3] = {d[0], d[1], d[2]};
+            v32[axis] += t;
+            const T nvv = sqrt(v32[0] * v32[0] + v32[1] * v32[1] + v32[2] * v32[2]);
+            const T Rr = c.w + rpT;
+            const T sc = Rr / nvv;
+            int f = -1;
+            if (FILT) {
+                const T delta = d0 + terr * (T(1) + sc) + T(2e-6);
+                f = free_pt<true>(A, c.x + sc * v32[0], c.y + sc * v32[1], c.z + sc * v32[2], A.agid(slot), -1, rpT,
+                                  delta);
+            }
+            if (f < 0) {
+                const P4<double> ce = X.atom(slot);
+                const double cc[3] = {ce.x, ce.y, ce.z};
+                if (t64 != t64) t64 = exact_root_sphere(cc, ce.w, s64, axis, (double)t);
+                double v[3] = {s64[0] - cc[0], s64[1] - cc[1], s64[2] - cc[2]};
+                v[axis] += t64;
+                const double nv64 = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+                const double R64 = ce.w + rp;
+                f = free_pt<false>(X, cc[0] + R64 * v[0] / nv64, cc[1] + R64 * v[1] / nv64, cc[2] + R64 * v[2] / nv64,
+                                   A.agid(slot), -1, rp, 0.0);
+            }
+            if (f != 1) continue;
+        }
+        out.push((float)t, (float)terr, t64);
+    }
+}
+
+// Tori (saddle pieces) around the free-arc circle of staged pair pi: roots on
+// the near branch, isolated in FP32 (certified) with the quartic on its
+// derivative chain and FP64 where that cannot decide.
+template <class T, bool FILT, class AccT, class AccX>
+__device__ void torus_roots(const AccT &A, const AccX &X, int pi, const double *s64, int axis, bool inside, double h,
+                            double rp, T d0, RootSink &out)
+{
     if constexpr (!FILT) {
-        torus_piece_exact(A, E, e, pi, s64, axis, h, rp, inside);
+        torus_piece_exact(A, out, pi, s64, axis, h, rp, inside);
     } else {
-        const P4<T> o = S.po[pi];
-        const P4<T> u = S.pu[pi];
+        const T s[3] = {(T)s64[0], (T)s64[1], (T)s64[2]};
+        const T hT = (T)h, rpT = (T)rp;
+        const T lo = T(-1e-4), hi = hT + T(1e-4);
+        const T tmax = T(1e-3);
+        const double NaN = __longlong_as_double(0x7ff8000000000000LL);
+        const P4<T> o = A.po(pi);
+        const P4<T> u = A.pu(pi);
         const float q0[3] = {s[0] - o.x, s[1] - o.y, s[2] - o.z};
         const float uu[3] = {u.x, u.y, u.z};
         float rt[4];
@@ -674,11 +828,11 @@ __device__ void cand_roots(const Model &M, const TileS<T, CP> &S, const double *
                 else if (Ay > 0.0f && nr >= 0) rt[nr++] = rq[k];
             }
             if (nr < 0) {
-                torus_piece_exact(X, E, e, pi, s64, axis, h, rp, inside);
+                torus_piece_exact(X, out, pi, s64, axis, h, rp, inside);
                 return;
             }
         }
-        const int2 ij = S.pij[pi];
+        const int2 ij = A.pij(pi);
         for (int k = 0; k < nr; ++k) {
             const float t = rt[k];
             float D, rate, nw, yy, zy, wv[3];
@@ -692,7 +846,7 @@ __device__ void cand_roots(const Model &M, const TileS<T, CP> &S, const double *
                 const P4<double> ue = X.pu(pi);
                 const double oo[3] = {oe.x, oe.y, oe.z}, u64[3] = {ue.x, ue.y, ue.z};
                 const double t64 = exact_root_torus(oo, u64, oe.w, rp, s64, axis, (double)t);
-                torus_root_exact(X, E, e, pi, s64, axis, h, rp, inside, t64);
+                torus_root_exact(X, out, pi, s64, axis, h, rp, inside, t64);
                 continue;
             }
             if (inside ? rate > 0.0f : rate < 0.0f) continue;
@@ -701,40 +855,32 @@ __device__ void cand_roots(const Model &M, const TileS<T, CP> &S, const double *
             const int f =
                 free_pt<true>(A, o.x + kk * wv[0], o.y + kk * wv[1], o.z + kk * wv[2], ij.x, ij.y, rpT, delta);
             if (f == 1) {
-                pool_push(E, e, t, terr, NaN, 1, pi);
+                out.push(t, terr, NaN);
             } else if (f < 0) {
                 const P4<double> oe = X.po(pi);
                 const P4<double> ue = X.pu(pi);
                 const double oo[3] = {oe.x, oe.y, oe.z}, u64[3] = {ue.x, ue.y, ue.z};
                 const double t64 = exact_root_torus(oo, u64, oe.w, rp, s64, axis, (double)t);
-                torus_root_exact(X, E, e, pi, s64, axis, h, rp, inside, t64);
+                torus_root_exact(X, out, pi, s64, axis, h, rp, inside, t64);
             }
         }
     }
 }
 
-// First root of one crossing edge from its candidates in E.cand[warp] (whole
-// warp).  Returns 0 with the chosen piece (kind, staged slot) and its root, 1
-// when no root is found, 2 when the candidates overflowed the buffer (the
-// first WCAND are used).
-template <class T, bool FILT, class CP>
-__device__ int warp_select(const Model &M, const TileS<T, CP> &S, const double *x0, EdgeSmem &E, int warp, int e,
+// First root of one crossing edge from its candidates c[0, n) (whole warp; c
+// in shared memory, updated in place).  Returns 0 with the chosen piece (kind,
+// staged slot) and its root, 1 when no root is found, 2 when the candidates
+// overflowed the buffer (the first WCAND are used).
+template <class T, bool FILT, class AccT, class AccX>
+__device__ int warp_select(const AccT &A, const AccX &X, WCand *c, int n, const double *s64, int axis, bool inside,
                            double h, double rp, T d0, float &t_out, int &kind_out, int &slot_out)
 {
     const int lane = threadIdx.x & 31;
-    const EdgeRef R = edge_ref(E, e);
-    const int axis = R.axis;
-    const double s64[3] = {E.hd[R.p >> 6], E.hd[(R.p >> 3) & 7], E.hd[R.p & 7]};
     const T s[3] = {(T)s64[0], (T)s64[1], (T)s64[2]};
-    SmemAcc<T, CP> A(S);
-    ExactAcc<T, CP> X(S, M, x0);
     const T rpT = (T)rp;
     const float tie = 1e-6f * (float)h;  // FP32 rounding of a root
-    const bool inside = R.lab == LABEL_IN;
-    int n = E.ncand[warp];
     int status = n > WCAND ? 2 : 0;
     if (n > WCAND) n = WCAND;
-    WCand *c = E.cand[warp];
     int pick = -1;
     for (int iter = 0; iter <= n; ++iter) {
         int k = warp_argmin(c, n);
@@ -943,79 +1089,88 @@ __device__ __forceinline__ int block_excl_scan_e(int v, int *sh, int *total)
     return base + inc - v;
 }
 
-// Output of one crossing edge (one thread): lower index, and for the FP64
-// polish the FP32 root, kind, model index, end label and failure flag; a
-// failure (status 1) is logged with its candidates (cand, ncand), an overflow
-// (status 2) flagged.
-template <class T, class CP>
-__device__ void edge_out(const TileS<T, CP> &S, const EdgeSmem &E, int e, const EdgeRef &R, const int *t, const int *toff,
-                         long long st0, long long st1, int mol, int status, float tr, int kind, int slot, EdgeOut &out,
-                         int *n_fail, int *err, long long *fail_log, const WCand *cand, int ncand)
-{
-    const int a = R.axis, q = R.p;
-    const int li = q >> 6, lj = (q >> 3) & 7, lk = q & 7;
-    int mid = 0;
-    if (status != 1) mid = kind == 0 ? S.agid[slot] : (kind == 1 ? S.pidx[slot] : S.vidx[slot]);
-    if (status != 0) {
-        atomicOr(err, status == 1 ? ERR_ROOT : ERR_CAP_CAND);
-        if (status == 1) {
-            int fs = atomicAdd(n_fail, 1);
-            if (fs < FAIL_LOG) {
-                long long *rec = fail_log + FAIL_REC * fs;
-                for (int z = 0; z < FAIL_REC; ++z) rec[z] = 0;
-                rec[0] = a;
-                rec[1] = (long long)TILE * t[0] + li;
-                rec[2] = (long long)TILE * t[1] + lj;
-                rec[3] = (long long)TILE * t[2] + lk;
-                rec[4] = R.lab;
-                rec[5] = S.na;
-                rec[6] = S.np;
-                rec[7] = S.nv;
-                rec[8] = ncand;
-                rec[23] = mol;
-                for (int z = 0; cand && z < 7 && z < ncand && z < WCAND; ++z) {
-                    rec[9 + z] = (long long)((double)cand[z].t * 1e9);
-                    rec[16 + z] = cand[z].kind;
-                }
-            }
-        }
-    }
-    const long long o = E.ebase[a] + (e - E.estart[a]);
-    // full-grid index of the lower point (st0, st1: the full grid's strides)
-    out.idx[a][o] = (long long)(TILE * (t[0] + toff[0]) + li) * st0 + (long long)(TILE * (t[1] + toff[1]) + lj) * st1 +
-                    (TILE * (t[2] + toff[2]) + lk);
-    // chosen piece for the FP64 polish: FP32 root, kind, model index, end label, failure
-    out.code[a][o] = make_int2(__float_as_int(tr), (kind << 29) | (R.lab << 28) | ((status == 1 ? 1 : 0) << 27) | mid);
-}
-
 template <class T, class CP>
 __host__ __device__ constexpr size_t edge_tile_bytes()  // rounded to 256: aligned slices in global memory
 {
     return (sizeof(TileS<T, CP>) + 255) & ~(size_t)255;
 }
 
-// CP = CapSmall: the staged lists in shared memory (with EdgeSmem); a tile
-// that overflows them goes to ovf.  CP = CapBig (BIG): the tiles listed in ovf
-// (Q.list), the staged lists in this CTA's slice of the global scratch `big`,
-// EdgeSmem in shared memory; overflowing that too is a capacity error.
+// exclusive prefix sums of v[0..n) and w[0..n) in place (whole block), the
+// totals at v[n] and w[n]; each thread sums a contiguous run of entries
+__device__ __forceinline__ void block_scan_runs(int *v, int *w, int n, int *sh, int *sh2)
+{
+    const int per = (n + EDGE_THREADS - 1) / EDGE_THREADS;
+    const int b = threadIdx.x * per, e = min(n, b + per);
+    int sv = 0, sw = 0;
+    for (int k = b; k < e; ++k) {
+        sv += v[k];
+        sw += w[k];
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int iv = sv, iw = sw;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(0xffffffffu, iv, o);
+        const int c = __shfl_up_sync(0xffffffffu, iw, o);
+        if (lane >= o) {
+            iv += a;
+            iw += c;
+        }
+    }
+    if (lane == 31) {
+        sh[wid] = iv;
+        sh2[wid] = iw;
+    }
+    __syncthreads();
+    int bv = 0, bw = 0, tv = 0, tw = 0;
+    for (int k = 0; k < EDGE_WARPS; ++k) {
+        if (k < wid) {
+            bv += sh[k];
+            bw += sh2[k];
+        }
+        tv += sh[k];
+        tw += sh2[k];
+    }
+    int rv = bv + iv - sv, rw = bw + iw - sw;
+    for (int k = b; k < e; ++k) {
+        const int a = v[k], c = w[k];
+        v[k] = rv;
+        w[k] = rw;
+        rv += a;
+        rw += c;
+    }
+    if (threadIdx.x == 0) {
+        v[n] = tv;
+        w[n] = tw;
+    }
+    __syncthreads();
+}
+
+// 1. Staging pass.  Persistent CTAs take tiles from the work queue.  Per tile
+// with crossing edges: the pieces are staged (CP = CapSmall: in shared memory,
+// a tile that overflows it goes to ovf; CP = CapBig (BIG): the tiles listed in
+// ovf, staged in this CTA's slice of the global scratch `big`, lists cut at
+// capacity with the error bit set), the crossing edges listed per axis in
+// point order, and written to HBM: the staged lists (the tile's slab), per
+// edge its output point index and its record (einfo, ecnt), and the (edge,
+// piece) pairs that pass the prefilter, spheres and tori in separate lists,
+// each edge's run in item order.  A buffer that is full drops the tile's
+// edges (flagged); the counters still add up what was needed.
 template <class T, bool FILT, class CP, bool BIG>
-__global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Batch B, TileSched Q, int chunk0,
+__global__ void __launch_bounds__(EDGE_THREADS) k_edge_stage(Model M, Batch B, TileSched Q,
                                                              const int8_t *__restrict__ labels_all,
                                                              const int *__restrict__ edge_start, EdgeOut out,
-                                                             int *__restrict__ n_fail, int *__restrict__ err,
-                                                             long long *__restrict__ fail_log, int *__restrict__ ovf,
-                                                             unsigned char *__restrict__ big)
+                                                             int *__restrict__ err, int *__restrict__ ovf,
+                                                             unsigned char *__restrict__ big, RootWork W)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileS<T, CP> &S = *reinterpret_cast<TileS<T, CP> *>(BIG ? big + (size_t)blockIdx.x * edge_tile_bytes<T, CP>()
                                                              : smem_raw);
-    EdgeSmem &E = *reinterpret_cast<EdgeSmem *>(BIG ? smem_raw : smem_raw + edge_tile_bytes<T, CP>());
+    StageSmem &E = *reinterpret_cast<StageSmem *>(BIG ? smem_raw : smem_raw + edge_tile_bytes<T, CP>());
     __shared__ long long q_base;
     __shared__ Grid sG;
     const long long nt = B.n_tiles;
-    const double rp = M.rp;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const T rpT = (T)rp, mg = FILT ? T(2e-3) : T(0);
+    const T rpT = (T)M.rp, mg = FILT ? T(2e-3) : T(0);
     long long iter = 0;
     const long long npos = sched_count(Q, nt);
     for (;;) {
@@ -1035,7 +1190,6 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Batch B, T
         const long long st1 = G.dims[2], st0 = G.dims[1] * G.dims[2];
         const long long fst1 = G.full[2], fst0 = G.full[1] * G.full[2];  // strides of the output indices
         const double h = G.h;
-        const T d0 = FILT ? (T)G.d0 : T(0);
         const T hT = (T)h;
         double x0[3];
         stage_tile<T>(M, G, mol, tile, S, x0);
@@ -1048,9 +1202,6 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Batch B, T
             __syncthreads();
             continue;
         }
-        // (the global-memory tier solves even a tile that overflows it, with
-        // its lists cut at capacity, so every output record is written; the
-        // error bit makes the run report ESES_ECAPACITY)
         if (threadIdx.x == 0 && S.flags) atomicOr(err, S.flags);
         int t[3];
         tile_coords(G, tile, t);
@@ -1080,180 +1231,429 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_solve(Model M, Batch B, T
             }
             int tsum;
             int rank = block_excl_scan_e(flag[0] + flag[1], E.sh, &tsum);
-            const int base = E.estart[a];
+            const int eb = E.estart[a];
             for (int k = 0; k < 2; ++k)
-                if (flag[k]) E.eptr[base + rank++] = (short)(2 * threadIdx.x + k);
+                if (flag[k]) E.eptr[eb + rank++] = (short)(2 * threadIdx.x + k);
             if (threadIdx.x == 0) {
-                E.estart[a + 1] = base + tsum;
-                E.ebase[a] = (long long)edge_start[a * nt + gt] - edge_start[a * nt];
+                E.estart[a + 1] = eb + tsum;
+                E.gbase[a] = edge_start[a * nt + gt];
+                E.abase[a] = edge_start[a * nt + gt] - edge_start[a * nt];
             }
             __syncthreads();
         }
         const int ne = E.estart[3];
-        const int nitem = S.na + S.nv + S.np;
-        // chunks of edges; a chunk whose candidates or roots overflow the pools
-        // is retried at half the size
-        // chunks of equal size (at most chunk0 edges), so no small last chunk
-        const int nch = (ne + chunk0 - 1) / chunk0;
-        const int cbal = nch > 0 ? (ne + nch - 1) / nch : chunk0;
-        int c0 = 0, csz = cbal;
-        while (c0 < ne) {
-            const int c1 = min(ne, c0 + csz);
-            if (threadIdx.x == 0) {
-                E.npool = 0;
-                E.npool_t = 0;
-                E.nroot = 0;
-                E.next_c = 0;
-                E.next_e = 0;
-                E.nhard = 0;
+        const int na = S.na, np = S.np, nv = S.nv, nsph = na + nv, nitem = nsph + np;
+        if (threadIdx.x == 0) {  // the tile's slab
+            const unsigned long long bytes = (unsigned long long)SlabLayout<T>(na, np, nv).bytes;
+            const unsigned long long off = atomicAdd(W.ctr, bytes);
+            E.slab = off + bytes <= (unsigned long long)W.cap_slab ? (long long)(off >> 4) : -1LL;
+        }
+        // output point index of every edge (full grid)
+        for (int e = threadIdx.x; e < ne; e += EDGE_THREADS) {
+            const EdgeRef R = edge_ref(E, e);
+            const int li = R.p >> 6, lj = (R.p >> 3) & 7, lk = R.p & 7;
+            out.idx[R.axis][E.abase[R.axis] + (e - E.estart[R.axis])] =
+                (long long)(TILE * (t[0] + G.toff[0]) + li) * fst0 + (long long)(TILE * (t[1] + G.toff[1]) + lj) * fst1 +
+                (TILE * (t[2] + G.toff[2]) + lk);
+        }
+        // (edge, item) pairs that pass the prefilter, counted: one warp per edge, lanes over items
+        for (int e = warp; e < ne; e += EDGE_WARPS) {
+            const EdgeRef R = edge_ref(E, e);
+            const T s[3] = {(T)E.hd[R.p >> 6], (T)E.hd[(R.p >> 3) & 7], (T)E.hd[R.p & 7]};
+            int cs = 0, ct = 0;
+            for (int i0 = 0; i0 < nitem; i0 += 32) {
+                const int it = i0 + lane;
+                const bool hit = it < nitem && cand_test<T, CP>(S, s, R.axis, it, hT, rpT, mg);
+                cs += __popc(__ballot_sync(0xffffffffu, hit && it < nsph));
+                ct += __popc(__ballot_sync(0xffffffffu, hit && it >= nsph));
             }
-            for (int k = threadIdx.x; k < CHUNK; k += EDGE_THREADS) E.rfill[k] = 0;
-            __syncthreads();
-            // 1. (edge, item) pairs that pass the prefilter: one warp per edge, lanes over items
-            for (int e = c0 + warp; e < c1; e += EDGE_WARPS) {
+            if (lane == 0) {
+                E.cs[e] = cs;
+                E.ct[e] = ct;
+            }
+        }
+        __syncthreads();
+        block_scan_runs(E.cs, E.ct, ne, E.sh, E.sh2);
+        if (threadIdx.x == 0) {
+            const unsigned long long ns = (unsigned long long)E.cs[ne], nq = (unsigned long long)E.ct[ne];
+            const unsigned long long sb = atomicAdd(W.ctr + 1, ns);
+            const unsigned long long tb = atomicAdd(W.ctr + 2, nq);
+            const bool ok = E.slab >= 0 && sb + ns <= (unsigned long long)W.cap_sph &&
+                            tb + nq <= (unsigned long long)W.cap_tor;
+            E.sb = ok ? (long long)sb : -1LL;
+            E.tb = ok ? (long long)tb : -1LL;
+            E.sb0 = (long long)sb;
+            E.tb0 = (long long)tb;
+        }
+        __syncthreads();
+        const bool ok = E.sb >= 0;
+        if (ok) {  // the slab: header and staged lists
+            unsigned char *sl = W.slab + ((size_t)E.slab << 4);
+            const SlabLayout<T> L(na, np, nv);
+            if (threadIdx.x == 0) {
+                SlabHdr hd;
+                hd.na = na;
+                hd.np = np;
+                hd.nv = nv;
+                hd.mol = mol;
+                for (int a = 0; a < 3; ++a) {
+                    hd.x0[a] = x0[a];
+                    hd.t[a] = t[a];
+                }
+                hd.gt = (int)gt;
+                *reinterpret_cast<SlabHdr *>(sl) = hd;
+            }
+            P4<T> *pa = reinterpret_cast<P4<T> *>(sl + L.atom);
+            P4<T> *po = reinterpret_cast<P4<T> *>(sl + L.po);
+            P4<T> *pu = reinterpret_cast<P4<T> *>(sl + L.pu);
+            P4<T> *pv = reinterpret_cast<P4<T> *>(sl + L.vq);
+            int *ag = reinterpret_cast<int *>(sl + L.agid);
+            int2 *pj = reinterpret_cast<int2 *>(sl + L.pij);
+            int *px = reinterpret_cast<int *>(sl + L.pidx);
+            int *vx = reinterpret_cast<int *>(sl + L.vidx);
+            uint8_t *fc = reinterpret_cast<uint8_t *>(sl + L.face);
+            for (int k = threadIdx.x; k < na; k += EDGE_THREADS) {
+                pa[k] = S.atom[k];
+                ag[k] = S.agid[k];
+                fc[k] = S.aface[k];
+            }
+            for (int k = threadIdx.x; k < np; k += EDGE_THREADS) {
+                po[k] = S.po[k];
+                pu[k] = S.pu[k];
+                pj[k] = S.pij[k];
+                px[k] = S.pidx[k];
+            }
+            for (int k = threadIdx.x; k < nv; k += EDGE_THREADS) {
+                pv[k] = S.vq[k];
+                vx[k] = S.vidx[k];
+            }
+        }
+        // edge records
+        for (int e = threadIdx.x; e < ne; e += EDGE_THREADS) {
+            const EdgeRef R = edge_ref(E, e);
+            const long long g = (long long)E.gbase[R.axis] + (e - E.estart[R.axis]);
+            W.einfo[g] = make_int4(ok ? (int)E.slab : 0, edge_pack(R.p, R.axis, R.lab, ok ? 0 : 1),
+                                   ok ? (int)(E.sb + E.cs[e]) : 0, ok ? (int)(E.tb + E.ct[e]) : 0);
+            W.ecnt[g] = ok ? ((E.cs[e + 1] - E.cs[e]) | ((E.ct[e + 1] - E.ct[e]) << 16)) : 0;
+        }
+        // the pairs themselves, in item order.  Every slot of the reserved runs
+        // below the capacities is written: a slot no pair fills (a dropped tile,
+        // or a second prefilter pass that disagreed with the count) gets a dead
+        // record (edge -1), so the root kernels never read an unwritten slot.
+        if (ok) {
+            for (int e = warp; e < ne; e += EDGE_WARPS) {
                 const EdgeRef R = edge_ref(E, e);
+                const int g = E.gbase[R.axis] + (e - E.estart[R.axis]);
                 const T s[3] = {(T)E.hd[R.p >> 6], (T)E.hd[(R.p >> 3) & 7], (T)E.hd[R.p & 7]};
-                const int nsph = S.na + S.nv;
+                long long ps = E.sb + E.cs[e], pt = E.tb + E.ct[e];
+                const long long ps1 = E.sb + E.cs[e + 1], pt1 = E.tb + E.ct[e + 1];
+                const unsigned below = (1u << lane) - 1;
                 for (int i0 = 0; i0 < nitem; i0 += 32) {
                     const int it = i0 + lane;
                     const bool hit = it < nitem && cand_test<T, CP>(S, s, R.axis, it, hT, rpT, mg);
-                    // spheres and tori in separate runs, so a warp of the root phase does one kind
-                    const bool tor = it >= nsph;
-                    const unsigned ms = __ballot_sync(0xffffffffu, hit && !tor);
-                    const unsigned mt = __ballot_sync(0xffffffffu, hit && tor);
-                    int bs = 0, bt = 0;
-                    if (lane == 0) {
-                        if (ms) bs = atomicAdd(&E.npool, __popc(ms));
-                        if (mt) bt = atomicAdd(&E.npool_t, __popc(mt));
-                    }
-                    bs = __shfl_sync(0xffffffffu, bs, 0);
-                    bt = __shfl_sync(0xffffffffu, bt, 0);
-                    const unsigned below = (1u << lane) - 1;
-                    const int pos = tor ? POOL_MAX - 1 - (bt + __popc(mt & below)) : bs + __popc(ms & below);
-                    const int used = tor ? bt + __popc(mt & below) : bs + __popc(ms & below);
-                    if (hit && used < POOL_MAX) E.pool[pos] = ((unsigned)e << 16) | (unsigned)it;
+                    const unsigned ms = __ballot_sync(0xffffffffu, hit && it < nsph);
+                    const unsigned mt = __ballot_sync(0xffffffffu, hit && it >= nsph);
+                    const long long qs = ps + __popc(ms & below), qt = pt + __popc(mt & below);
+                    if (hit && it < nsph && qs < ps1) W.csph[qs] = make_int2(g, it);
+                    if (hit && it >= nsph && qt < pt1) W.ctor[qt] = make_int2(g, it - nsph);
+                    ps += __popc(ms);
+                    pt += __popc(mt);
                 }
+                for (long long q = ps + lane; q < ps1; q += 32) W.csph[q] = make_int2(-1, 0);
+                for (long long q = pt + lane; q < pt1; q += 32) W.ctor[q] = make_int2(-1, 0);
             }
-            __syncthreads();
-            const int npool_s = E.npool, npool_t = E.npool_t;
-            const int npool = npool_s + npool_t;
-            if (npool > POOL_MAX && csz > 1) {
-                csz = (csz + 1) / 2;
-                __syncthreads();
-                continue;
-            }
-            // 2. roots of every pair, one thread each; warps take 32 pairs at a
-            //    time from the block's counter (spheres first, then tori)
-            {
-                const int ns = min(npool_s, POOL_MAX), nt_ = min(npool_t, POOL_MAX - ns);
-                for (;;) {
-                    int base = 0;
-                    if (lane == 0) base = atomicAdd(&E.next_c, 32);
-                    base = __shfl_sync(0xffffffffu, base, 0);
-                    if (base >= ns + nt_) break;
-                    const int k = base + lane;
-                    if (k < ns + nt_) {
-                        const unsigned v = k < ns ? E.pool[k] : E.pool[POOL_MAX - 1 - (k - ns)];
-                        cand_roots<T, FILT, CP>(M, S, x0, E, (int)(v >> 16), (int)(v & 0xffffu), h, rp, d0);
-                    }
-                }
-            }
-            __syncthreads();
-            const int nroot = E.nroot;
-            if (nroot > ROOT_MAX && csz > 1) {
-                csz = (csz + 1) / 2;
-                __syncthreads();
-                continue;
-            }
-            const int nr = min(nroot, ROOT_MAX);
-            // 3. roots grouped by edge (counting sort)
-            for (int r = threadIdx.x; r < nr; r += EDGE_THREADS) atomicAdd(&E.rfill[E.redge[r] - c0], 1);
-            __syncthreads();
-            if (warp == 0) {
-                constexpr int PER = CHUNK / 32;
-                int v[PER], s = 0;
-                for (int k = 0; k < PER; ++k) {
-                    v[k] = E.rfill[lane * PER + k];
-                    s += v[k];
-                }
-                int inc = s;
-                for (int o = 1; o < 32; o <<= 1) {
-                    int u = __shfl_up_sync(0xffffffffu, inc, o);
-                    if (lane >= o) inc += u;
-                }
-                int run = inc - s;
-                for (int k = 0; k < PER; ++k) {
-                    E.rstart[lane * PER + k] = run;
-                    E.rfill[lane * PER + k] = run;
-                    run += v[k];
-                }
-                if (lane == 31) E.rstart[CHUNK] = run;
-            }
-            __syncthreads();
-            for (int r = threadIdx.x; r < nr; r += EDGE_THREADS)
-                E.rorder[atomicAdd(&E.rfill[E.redge[r] - c0], 1)] = (short)r;
-            __syncthreads();
-            // 4a. edges whose first root needs neither a witness test nor an FP64
-            //     tie break -- an inside end point, or a single candidate (the
-            //     last candidate needs no test) with no candidate the FP32
-            //     bounds cannot order: one thread each; the rest go to 4b
-            const bool ovf = nroot > ROOT_MAX || npool > POOL_MAX;
-            for (int e = c0 + threadIdx.x; e < c1; e += EDGE_THREADS) {
-                const int b = E.rstart[e - c0], n = E.rstart[e - c0 + 1] - b;
-                const EdgeRef R = edge_ref(E, e);
-                int k = -1;
-                if (!ovf && n >= 1 && n <= WCAND && (R.lab == LABEL_IN || n == 1)) {
-                    float tk = INFINITY;
-                    for (int j = 0; j < n; ++j) {  // smallest root, ties to the first (as warp_argmin)
-                        const float tj = E.root[E.rorder[b + j]].t;
-                        if (tj < tk) {
-                            tk = tj;
-                            k = j;
-                        }
-                    }
-                    const float ek = E.root[E.rorder[b + k]].err, tie = 1e-6f * (float)h;
-                    for (int j = 0; j < n && k >= 0; ++j) {
-                        const WCand &cj = E.root[E.rorder[b + j]];
-                        if (j != k && cj.t < INFINITY && cj.t - tk <= cj.err + ek + tie) k = -1;
-                    }
-                }
-                if (k >= 0) {
-                    const WCand &ck = E.root[E.rorder[b + k]];
-                    const float tr = ck.t64 == ck.t64 ? (float)ck.t64 : ck.t;
-                    edge_out(S, E, e, R, t, G.toff, fst0, fst1, mol, 0, tr, ck.kind, ck.id, out, n_fail, err, fail_log,
-                             nullptr, 0);
-                } else {
-                    E.hard[atomicAdd(&E.nhard, 1)] = (short)e;
-                }
-            }
-            __syncthreads();
-            // 4b. the other edges: one warp per edge, taken from the block's counter
-            const int nhard = E.nhard;
-            for (;;) {
-                int q = 0;
-                if (lane == 0) q = atomicAdd(&E.next_e, 1);
-                q = __shfl_sync(0xffffffffu, q, 0);
-                if (q >= nhard) break;
-                const int e = E.hard[q];
-                const int b = E.rstart[e - c0], n = E.rstart[e - c0 + 1] - b;
-                for (int k = lane; k < n && k < WCAND; k += 32) E.cand[warp][k] = E.root[E.rorder[b + k]];
-                if (lane == 0) E.ncand[warp] = n;
-                __syncwarp();
-                float tr = 0.5f * (float)h;
-                int kind = 0, slot = 0;
-                int status = warp_select<T, FILT, CP>(M, S, x0, E, warp, e, h, rp, d0, tr, kind, slot);
-                if (ovf) status = 2;  // single-edge overflow
-                if (lane == 0)
-                    edge_out(S, E, e, edge_ref(E, e), t, G.toff, fst0, fst1, mol, status, tr, kind, slot, out, n_fail,
-                             err, fail_log, E.cand[warp], E.ncand[warp]);
-                __syncwarp();
-            }
-            __syncthreads();
-            c0 = c1;
-            csz = cbal;
+        } else {
+            const long long s1 = min(E.sb0 + E.cs[ne], W.cap_sph), t1 = min(E.tb0 + E.ct[ne], W.cap_tor);
+            for (long long q = E.sb0 + threadIdx.x; q < s1; q += EDGE_THREADS) W.csph[q] = make_int2(-1, 0);
+            for (long long q = E.tb0 + threadIdx.x; q < t1; q += EDGE_THREADS) W.ctor[q] = make_int2(-1, 0);
         }
         __syncthreads();
       }
+    }
+}
+
+// slab, grid and edge geometry of global edge g's record
+struct EdgeView {
+    const unsigned char *slab;
+    int axis, p, lab;
+    double s64[3];  // lower point in the tile frame
+};
+
+// 2. Roots of the sphere candidates, one thread each (grid-stride).
+template <class T, bool FILT>
+__global__ void __launch_bounds__(ROOT_THREADS_MAX) k_roots_sphere(Model M, Batch B, RootWork W,
+                                                                   int *__restrict__ err)
+{
+    const long long n = min((long long)W.ctr[1], W.cap_sph);
+    const double rp = M.rp;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int2 c = W.csph[k];
+        if (c.x < 0 || c.x >= W.n_edges) {  // dead record
+            W.nsph[k] = 0;
+            continue;
+        }
+        const int4 inf = W.einfo[c.x];
+        const unsigned char *sl = W.slab + ((size_t)(unsigned)inf.x << 4);
+        const SlabHdr *hd = reinterpret_cast<const SlabHdr *>(sl);
+        const int mol = __ldg(&hd->mol);
+        const double x0[3] = {__ldg(&hd->x0[0]), __ldg(&hd->x0[1]), __ldg(&hd->x0[2])};
+        const double h = B.grid[mol].h;
+        const T d0 = FILT ? (T)B.grid[mol].d0 : T(0);
+        const int pk = inf.y, p = pk_point(pk);
+        const double s64[3] = {(double)(p >> 6) * h, (double)((p >> 3) & 7) * h, (double)(p & 7) * h};
+        const SlabAcc<T> A(sl);
+        const SlabExact<T> X(A, M, x0);
+        RootSink out{W.rsph + (size_t)SPH_SLOTS * k, 0, SPH_SLOTS};
+        sphere_roots<T, FILT>(A, X, c.y, s64, pk_axis(pk), pk_label(pk) == LABEL_IN, h, rp, d0, out);
+        if (out.n > SPH_SLOTS) atomicOr(err, ERR_CAP_CAND);
+        W.nsph[k] = (uint8_t)min(out.n, SPH_SLOTS);
+    }
+}
+
+// 3. Roots of the torus candidates, one thread each (grid-stride).
+template <class T, bool FILT>
+__global__ void __launch_bounds__(ROOT_THREADS_MAX) k_roots_torus(Model M, Batch B, RootWork W,
+                                                                  int *__restrict__ err)
+{
+    const long long n = min((long long)W.ctr[2], W.cap_tor);
+    const double rp = M.rp;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int2 c = W.ctor[k];
+        if (c.x < 0 || c.x >= W.n_edges) {  // dead record
+            W.ntor[k] = 0;
+            continue;
+        }
+        const int4 inf = W.einfo[c.x];
+        const unsigned char *sl = W.slab + ((size_t)(unsigned)inf.x << 4);
+        const SlabHdr *hd = reinterpret_cast<const SlabHdr *>(sl);
+        const int mol = __ldg(&hd->mol);
+        const double x0[3] = {__ldg(&hd->x0[0]), __ldg(&hd->x0[1]), __ldg(&hd->x0[2])};
+        const double h = B.grid[mol].h;
+        const T d0 = FILT ? (T)B.grid[mol].d0 : T(0);
+        const int pk = inf.y, p = pk_point(pk);
+        const double s64[3] = {(double)(p >> 6) * h, (double)((p >> 3) & 7) * h, (double)(p & 7) * h};
+        const SlabAcc<T> A(sl);
+        const SlabExact<T> X(A, M, x0);
+        RootSink out{W.rtor + (size_t)TOR_SLOTS * k, 0, TOR_SLOTS};
+        torus_roots<T, FILT>(A, X, c.y, s64, pk_axis(pk), pk_label(pk) == LABEL_IN, h, rp, d0, out);
+        if (out.n > TOR_SLOTS) atomicOr(err, ERR_CAP_CAND);
+        W.ntor[k] = (uint8_t)min(out.n, TOR_SLOTS);
+    }
+}
+
+// chosen piece of an edge for the FP64 polish: FP32 root, kind, model index,
+// end label, failure
+__device__ __forceinline__ void code_out(EdgeOut &out, int axis, long long o, int failed, float tr, int kind, int mid,
+                                         int lab)
+{
+    out.code[axis][o] = make_int2(__float_as_int(tr), (kind << 29) | (lab << 28) | (failed << 27) | mid);
+}
+
+// 4. The first root of every edge whose choice needs neither a witness test
+// nor an FP64 tie break -- an inside end point, or a single candidate (the
+// last candidate needs no test) -- with no candidate the FP32 bounds cannot
+// order: one thread per edge, candidates in order (spheres by item, then
+// tori); the other edges are listed for the warp selection.  A dropped edge
+// is recorded as failed (and the run as over capacity).
+template <class T>
+__global__ void __launch_bounds__(PICK_THREADS) k_edge_pick(Batch B, RootWork W, const int *__restrict__ edge_start,
+                                                            long long ne_all, EdgeOut out, int *__restrict__ err)
+{
+    const long long nt = B.n_tiles;
+    const int lane = threadIdx.x & 31;
+    const long long nwarp = (long long)gridDim.x * (PICK_THREADS / 32);
+    for (long long w0 = ((long long)blockIdx.x * (PICK_THREADS / 32) + (threadIdx.x >> 5)) * 32; w0 < ne_all;
+         w0 += nwarp * 32) {
+        const long long g = w0 + lane;
+        bool hard = false;
+        if (g < ne_all) {
+            const int4 inf = W.einfo[g];
+            const int cnt = W.ecnt[g];
+            const int ns = cnt & 0xffff, nq = (cnt >> 16) & 0xffff;
+            // the axis from the edge's place in the output (all axes in one run)
+            const int axis = g < edge_start[nt] ? 0 : (g < edge_start[2 * nt] ? 1 : 2);
+            const int pk = inf.y, lab = pk_label(pk);
+            const long long o = g - edge_start[axis * nt];
+            // a record that is not the staging pass's (never expected) counts as dropped
+            const bool bad = pk_axis(pk) != axis || inf.x < 0 || 16LL * inf.x >= W.cap_slab || inf.z < 0 ||
+                             inf.w < 0 || (long long)inf.z + ns > W.cap_sph || (long long)inf.w + nq > W.cap_tor;
+            if (pk_dropped(pk) || bad) {
+                atomicOr(err, ERR_CAP_CAND);
+                code_out(out, axis, o, 1, 0.0f, 0, 0, lab);
+            } else {
+                const unsigned char *sl = W.slab + ((size_t)(unsigned)inf.x << 4);
+                const SlabHdr *hd = reinterpret_cast<const SlabHdr *>(sl);
+                const int na = __ldg(&hd->na);
+                // smallest FP32 root (ties to the first), its record, and the count
+                int n = 0, kind = -1, slot = 0, kn = -1;
+                float tk = INFINITY, ek = 0.0f;
+                double t64k = 0.0;
+                for (int j = 0; j < ns; ++j) {
+                    const int nr = W.nsph[inf.z + j];
+                    for (int r = 0; r < nr; ++r, ++n) {
+                        const RootRec q = W.rsph[(size_t)SPH_SLOTS * (inf.z + j) + r];
+                        if (q.t < tk) {
+                            const int it = W.csph[inf.z + j].y;
+                            tk = q.t;
+                            ek = q.err;
+                            t64k = q.t64;
+                            kind = it < na ? 0 : 2;
+                            slot = it < na ? it : it - na;
+                            kn = n;
+                        }
+                    }
+                }
+                for (int j = 0; j < nq; ++j) {
+                    const int nr = W.ntor[inf.w + j];
+                    for (int r = 0; r < nr; ++r, ++n) {
+                        const RootRec q = W.rtor[(size_t)TOR_SLOTS * (inf.w + j) + r];
+                        if (q.t < tk) {
+                            tk = q.t;
+                            ek = q.err;
+                            t64k = q.t64;
+                            kind = 1;
+                            slot = W.ctor[inf.w + j].y;
+                            kn = n;
+                        }
+                    }
+                }
+                hard = !(n >= 1 && n <= WCAND && (lab == LABEL_IN || n == 1) && kn >= 0);
+                if (!hard) {  // every other candidate ordered after it by the FP32 bounds
+                    const float tie = 1e-6f * (float)B.grid[__ldg(&hd->mol)].h;
+                    int m = 0;
+                    for (int j = 0; j < ns && !hard; ++j) {
+                        const int nr = W.nsph[inf.z + j];
+                        for (int r = 0; r < nr; ++r, ++m) {
+                            const RootRec q = W.rsph[(size_t)SPH_SLOTS * (inf.z + j) + r];
+                            if (m != kn && q.t < INFINITY && q.t - tk <= q.err + ek + tie) hard = true;
+                        }
+                    }
+                    for (int j = 0; j < nq && !hard; ++j) {
+                        const int nr = W.ntor[inf.w + j];
+                        for (int r = 0; r < nr; ++r, ++m) {
+                            const RootRec q = W.rtor[(size_t)TOR_SLOTS * (inf.w + j) + r];
+                            if (m != kn && q.t < INFINITY && q.t - tk <= q.err + ek + tie) hard = true;
+                        }
+                    }
+                }
+                if (!hard) {
+                    const SlabAcc<T> A(sl);
+                    const float tr = t64k == t64k ? (float)t64k : tk;
+                    code_out(out, axis, o, 0, tr, kind, A.model_index(kind, slot), lab);
+                }
+            }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, hard);
+        int base = 0;
+        if (lane == 0 && m) base = (int)atomicAdd(W.ctr + 3, (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (hard) W.hard[base + __popc(m & ((1u << lane) - 1))] = (int)g;
+    }
+}
+
+// 5. The listed edges: one warp per edge (grid-stride over the list).  The
+// edge's accepted roots are gathered in candidate order into the warp's
+// buffer in shared memory (at most WCAND; more is a capacity error), then
+// chosen by warp_select.  A failure is logged with its candidates.
+template <class T, bool FILT>
+__global__ void __launch_bounds__(HARD_THREADS) k_edge_hard(Model M, Batch B, RootWork W,
+                                                            const int *__restrict__ edge_start, EdgeOut out,
+                                                            int *__restrict__ n_fail, int *__restrict__ err,
+                                                            long long *__restrict__ fail_log)
+{
+    __shared__ WCand cand[HARD_THREADS / 32][WCAND];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long nt = B.n_tiles;
+    const long long nh = (long long)W.ctr[3];
+    const double rp = M.rp;
+    WCand *c = cand[warp];
+    for (long long q = (long long)blockIdx.x * (HARD_THREADS / 32) + warp; q < nh;
+         q += (long long)gridDim.x * (HARD_THREADS / 32)) {
+        const int g = W.hard[q];
+        const int4 inf = W.einfo[g];
+        const int cnt = W.ecnt[g];
+        const int ns = cnt & 0xffff, nq = (cnt >> 16) & 0xffff;
+        const int pk = inf.y, axis = pk_axis(pk), lab = pk_label(pk), p = pk_point(pk);
+        const long long o = (long long)g - edge_start[axis * nt];
+        const unsigned char *sl = W.slab + ((size_t)(unsigned)inf.x << 4);
+        const SlabHdr *hd = reinterpret_cast<const SlabHdr *>(sl);
+        const int mol = __ldg(&hd->mol);
+        const double x0[3] = {__ldg(&hd->x0[0]), __ldg(&hd->x0[1]), __ldg(&hd->x0[2])};
+        const double h = B.grid[mol].h;
+        const T d0 = FILT ? (T)B.grid[mol].d0 : T(0);
+        const double s64[3] = {(double)(p >> 6) * h, (double)((p >> 3) & 7) * h, (double)(p & 7) * h};
+        const SlabAcc<T> A(sl);
+        const SlabExact<T> X(A, M, x0);
+        const int na = A.na();
+        // gather: lanes over candidates, each lane's roots at its prefix of the counts
+        int n = 0;
+        for (int j0 = 0; j0 < ns + nq; j0 += 32) {
+            const int j = j0 + lane;
+            const bool sph = j < ns;
+            int nr = 0;
+            if (j < ns + nq) nr = sph ? W.nsph[inf.z + j] : W.ntor[inf.w + (j - ns)];
+            int inc = nr;
+            for (int d = 1; d < 32; d <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, inc, d);
+                if (lane >= d) inc += u;
+            }
+            const int at = n + inc - nr;
+            if (nr > 0) {
+                int kind, slot;
+                if (sph) {
+                    const int it = W.csph[inf.z + j].y;
+                    kind = it < na ? 0 : 2;
+                    slot = it < na ? it : it - na;
+                } else {
+                    kind = 1;
+                    slot = W.ctor[inf.w + (j - ns)].y;
+                }
+                for (int r = 0; r < nr; ++r) {
+                    if (at + r >= WCAND) break;
+                    const RootRec qr = sph ? W.rsph[(size_t)SPH_SLOTS * (inf.z + j) + r]
+                                           : W.rtor[(size_t)TOR_SLOTS * (inf.w + (j - ns)) + r];
+                    WCand &w = c[at + r];
+                    w.t64 = qr.t64;
+                    w.t = qr.t;
+                    w.err = qr.err;
+                    w.kind = kind;
+                    w.id = slot;
+                }
+            }
+            n += __shfl_sync(0xffffffffu, inc, 31);
+        }
+        __syncwarp();
+        float tr = 0.5f * (float)h;
+        int kind = 0, slot = 0;
+        int status = pk_dropped(pk) ? 2 : warp_select<T, FILT>(A, X, c, n, s64, axis, lab == LABEL_IN, h, rp, d0, tr,
+                                                               kind, slot);
+        if (lane == 0) {
+            const int mid = status == 1 || pk_dropped(pk) ? 0 : A.model_index(kind, slot);
+            if (status != 0) atomicOr(err, status == 1 ? ERR_ROOT : ERR_CAP_CAND);
+            if (status == 1) {
+                const int fs = atomicAdd(n_fail, 1);
+                if (fs < FAIL_LOG) {
+                    long long *rec = fail_log + FAIL_REC * fs;
+                    for (int z = 0; z < FAIL_REC; ++z) rec[z] = 0;
+                    rec[0] = axis;
+                    rec[1] = (long long)TILE * __ldg(&hd->t[0]) + (p >> 6);
+                    rec[2] = (long long)TILE * __ldg(&hd->t[1]) + ((p >> 3) & 7);
+                    rec[3] = (long long)TILE * __ldg(&hd->t[2]) + (p & 7);
+                    rec[4] = lab;
+                    rec[5] = na;
+                    rec[6] = A.np();
+                    rec[7] = A.nv();
+                    rec[8] = n;
+                    for (int z = 0; z < 7 && z < n && z < WCAND; ++z) {
+                        rec[9 + z] = (long long)((double)c[z].t * 1e9);
+                        rec[16 + z] = c[z].kind;
+                    }
+                    rec[23] = mol;
+                }
+            }
+            code_out(out, axis, o, status == 1 || pk_dropped(pk) ? 1 : 0, tr, kind, mid, lab);
+        }
+        __syncwarp();
     }
 }
 
@@ -1448,31 +1848,45 @@ int launch_mol_edges(const Batch &B, const int *edge_start, long long *medge, cu
 }
 
 template <class T>
-static size_t edge_smem()
+static size_t stage_smem()
 {
-    return edge_tile_bytes<T, CapSmall>() + sizeof(EdgeSmem);
+    return edge_tile_bytes<T, CapSmall>() + sizeof(StageSmem);
 }
 
-static int g_edge_n_sm = 1;  // SMs: the grid of the global-memory tier
+static int g_edge_n_sm = 1;  // SMs: the grid of the global-memory tier and of the persistent root kernels
+// resident blocks per SM: [FP64, FP32][sphere roots, torus roots][64, 128, 256 threads]; hard selection
+static int g_occ_roots[2][2][3];
+static int g_occ_hard[2];
 
-// dynamic shared memory limits (once per device, before any launch or capture)
+static int threads_slot(int threads) { return threads <= 64 ? 0 : (threads <= 128 ? 1 : 2); }
+
+// dynamic shared memory limits and occupancies (once per device, before any launch or capture)
 void edges_init()
 {
-    cudaFuncSetAttribute(k_edge_solve<double, false, CapSmall, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)edge_smem<double>());
-    cudaFuncSetAttribute(k_edge_solve<float, true, CapSmall, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)edge_smem<float>());
-    cudaFuncSetAttribute(k_edge_solve<double, false, CapBig, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(EdgeSmem));
-    cudaFuncSetAttribute(k_edge_solve<float, true, CapBig, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sizeof(EdgeSmem));
+    cudaFuncSetAttribute(k_edge_stage<double, false, CapSmall, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)stage_smem<double>());
+    cudaFuncSetAttribute(k_edge_stage<float, true, CapSmall, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)stage_smem<float>());
+    cudaFuncSetAttribute(k_edge_stage<double, false, CapBig, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(StageSmem));
+    cudaFuncSetAttribute(k_edge_stage<float, true, CapBig, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(StageSmem));
     int dev = 0, n_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     g_edge_n_sm = n_sm > 0 ? n_sm : 1;
+    const int tb[3] = {64, 128, 256};
+    for (int k = 0; k < 3; ++k) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ_roots[0][0][k], k_roots_sphere<double, false>, tb[k], 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ_roots[0][1][k], k_roots_torus<double, false>, tb[k], 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ_roots[1][0][k], k_roots_sphere<float, true>, tb[k], 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ_roots[1][1][k], k_roots_torus<float, true>, tb[k], 0);
+    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ_hard[0], k_edge_hard<double, false>, HARD_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ_hard[1], k_edge_hard<float, true>, HARD_THREADS, 0);
 }
 
-// bytes of global scratch the root solve's global-memory tier needs
+// bytes of global scratch the staging pass's global-memory tier needs
 size_t edges_big_bytes()
 {
     size_t per = edge_tile_bytes<double, CapBig>();
@@ -1484,45 +1898,79 @@ int edge_ctas_per_sm(int precision)
 {
     int n = 0;
     if (precision == 0)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_edge_solve<double, false, CapSmall, false>, EDGE_THREADS,
-                                                      edge_smem<double>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_edge_stage<double, false, CapSmall, false>, EDGE_THREADS,
+                                                      stage_smem<double>());
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_edge_solve<float, true, CapSmall, false>, EDGE_THREADS,
-                                                      edge_smem<float>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_edge_stage<float, true, CapSmall, false>, EDGE_THREADS,
+                                                      stage_smem<float>());
     return n > 0 ? n : 1;
 }
 
-int edge_chunk_max() { return CHUNK; }
+bool root_threads_valid(int threads) { return threads == 0 || threads == 64 || threads == 128 || threads == 256; }
+
+long long slab_bytes_max(int precision)
+{
+    return precision == 0 ? SlabLayout<double>(CapBig::A, CapBig::P, CapBig::V).bytes
+                          : SlabLayout<float>(CapBig::A, CapBig::P, CapBig::V).bytes;
+}
 
 template <class T, bool FILT>
-static void edge_solve_launch(const Model &M, const Batch &B, const TileSched &Q, int grid, int chunk,
-                              const int8_t *labels, const int *edge_start, EdgeOut out, int *n_fail, int *err,
-                              long long *fail_log, int *ovf, unsigned char *big, cudaStream_t st)
+static void stage_launch(const Model &M, const Batch &B, const TileSched &Q, int grid, const int8_t *labels,
+                         const int *edge_start, EdgeOut out, int *err, int *ovf, unsigned char *big,
+                         const RootWork &W, cudaStream_t st)
 {
+    cudaMemsetAsync(W.ctr, 0, 4 * sizeof(unsigned long long), st);
+    if (Q.head) cudaMemsetAsync(Q.head, 0, sizeof(unsigned long long), st);
     cudaMemsetAsync(ovf + 1, 0, sizeof(int), st);
-    k_edge_solve<T, FILT, CapSmall, false><<<grid, EDGE_THREADS, edge_smem<T>(), st>>>(
-        M, B, Q, chunk, labels, edge_start, out, n_fail, err, fail_log, ovf, nullptr);
+    k_edge_stage<T, FILT, CapSmall, false><<<grid, EDGE_THREADS, stage_smem<T>(), st>>>(M, B, Q, labels, edge_start,
+                                                                                       out, err, ovf, nullptr, W);
     TileSched QB{nullptr, 1, ovf + 2, ovf + 1};
-    k_edge_solve<T, FILT, CapBig, true><<<g_edge_n_sm, EDGE_THREADS, sizeof(EdgeSmem), st>>>(
-        M, B, QB, chunk, labels, edge_start, out, n_fail, err, fail_log, ovf, big);
+    k_edge_stage<T, FILT, CapBig, true><<<g_edge_n_sm, EDGE_THREADS, sizeof(StageSmem), st>>>(
+        M, B, QB, labels, edge_start, out, err, ovf, big, W);
+}
+
+template <class T, bool FILT>
+static void roots_launch(const Model &M, const Batch &B, int threads, EdgeOut out, const int *edge_start,
+                         long long ne_all, int *n_fail, int *err, long long *fail_log, const RootWork &W,
+                         cudaStream_t st)
+{
+    const int P = FILT ? 1 : 0, ts = threads_slot(threads), tb = 64 << ts;
+    const int gs = std::max(g_occ_roots[P][0][ts], 1) * g_edge_n_sm;
+    const int gq = std::max(g_occ_roots[P][1][ts], 1) * g_edge_n_sm;
+    k_roots_sphere<T, FILT><<<gs, tb, 0, st>>>(M, B, W, err);
+    k_roots_torus<T, FILT><<<gq, tb, 0, st>>>(M, B, W, err);
+    const long long pb = std::min<long long>(std::max<long long>(ceil_div_ll(ne_all, PICK_THREADS), 1),
+                                             8LL * g_edge_n_sm);
+    k_edge_pick<T><<<(unsigned)pb, PICK_THREADS, 0, st>>>(B, W, edge_start, ne_all, out, err);
+    k_edge_hard<T, FILT><<<std::max(g_occ_hard[P], 1) * g_edge_n_sm, HARD_THREADS, 0, st>>>(
+        M, B, W, edge_start, out, n_fail, err, fail_log);
+}
+
+int launch_edge_stage(const Model &M, const Batch &B, int precision, const TileSched &Q, int grid,
+                      const int8_t *labels, const int *edge_start, EdgeOut out, int *err, int *ovf,
+                      unsigned char *big, const RootWork &W, cudaStream_t st)
+{
+    if (grid < 1) grid = 1;
+    if (precision == 0)
+        stage_launch<double, false>(M, B, Q, grid, labels, edge_start, out, err, ovf, big, W, st);
+    else
+        stage_launch<float, true>(M, B, Q, grid, labels, edge_start, out, err, ovf, big, W, st);
+    return 2;
+}
+
+int launch_edge_roots(const Model &M, const Batch &B, int precision, int threads, EdgeOut out,
+                      const int *edge_start, long long ne_all, int *n_fail, int *err, long long *fail_log,
+                      const RootWork &W, cudaStream_t st)
+{
+    if (!root_threads_valid(threads) || threads == 0) threads = ROOT_THREADS_MAX;
+    if (precision == 0)
+        roots_launch<double, false>(M, B, threads, out, edge_start, ne_all, n_fail, err, fail_log, W, st);
+    else
+        roots_launch<float, true>(M, B, threads, out, edge_start, ne_all, n_fail, err, fail_log, W, st);
+    return 4;
 }
 
 long long polish_blocks(long long n_edges) { return n_edges > 0 ? ceil_div_ll(n_edges, POLISH_THREADS) : 0; }
-
-int launch_edge_solve(const Model &M, const Batch &B, int precision, const TileSched &Q, int grid, int chunk,
-                      const int8_t *labels, const int *edge_start, EdgeOut out, int *n_fail, int *err,
-                      long long *fail_log, int *ovf, unsigned char *big, cudaStream_t st)
-{
-    if (grid < 1) grid = 1;
-    chunk = chunk < 1 ? 1 : (chunk > CHUNK ? CHUNK : chunk);
-    if (precision == 0)
-        edge_solve_launch<double, false>(M, B, Q, grid, chunk, labels, edge_start, out, n_fail, err, fail_log, ovf,
-                                         big, st);
-    else
-        edge_solve_launch<float, true>(M, B, Q, grid, chunk, labels, edge_start, out, n_fail, err, fail_log, ovf, big,
-                                       st);
-    return 2;
-}
 
 int launch_edge_polish(const Model &M, const Batch &B, EdgeOut out, long long n_edges_total,
                        const long long *medge, double2 *term, cudaStream_t st)

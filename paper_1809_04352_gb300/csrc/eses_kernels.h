@@ -76,13 +76,43 @@ struct EdgeOut {
 constexpr int FAIL_LOG = 8;
 constexpr int FAIL_REC = 24;
 long long polish_blocks(long long n_edges);
+// The root solve runs in phases linked by lists in HBM (eses_edges.cu):
+// staging (per tile: staged lists, edge records, prefiltered (edge, piece)
+// candidates), roots per sphere and per torus candidate, the easy picks, the
+// warp selections.  RootRec: one accepted root of a candidate.
+struct RootRec {
+    double t64;    // exact root once computed (NaN before)
+    float t, err;  // FP32 root and its error bound (A)
+};
+// buffers of the phased root solve; the capacities are planned by the caller
+// from the totals the staging pass adds up in ctr ([0] slab bytes, [1] sphere
+// and [2] torus candidates; [3] edges listed for the warp selection)
+struct RootWork {
+    int4 *einfo;            // per crossing edge: slab (16-byte units), packed point/axis/label/dropped,
+                            // first sphere and first torus candidate
+    int *ecnt;              // per crossing edge: sphere candidates | torus candidates << 16
+    int2 *csph, *ctor;      // candidates: (edge, staged item) and (edge, staged pair)
+    uint8_t *nsph, *ntor;   // accepted roots per candidate
+    RootRec *rsph, *rtor;   // their roots: 2 slots per sphere candidate, 4 per torus candidate
+    unsigned char *slab;    // staged tiles
+    unsigned long long *ctr;
+    int *hard;              // edges listed for the warp selection (at most one per edge)
+    long long cap_slab, cap_sph, cap_tor;
+    long long n_edges;      // crossing edges of the run (all axes)
+};
 void edges_init();
 int edge_ctas_per_sm(int precision);
-int edge_chunk_max();
-// persistent: `grid` CTAs take tiles in the order of Q; `chunk` edges per pooled chunk
-int launch_edge_solve(const Model &M, const Batch &B, int precision, const TileSched &Q, int grid, int chunk,
-                      const int8_t *labels, const int *edge_start, EdgeOut out, int *n_fail, int *err,
-                      long long *fail_log, int *ovf, unsigned char *big, cudaStream_t st);
+bool root_threads_valid(int threads);  // 0 (the default, 256), 64, 128 or 256
+long long slab_bytes_max(int precision);  // one tile's slab at the global tier's capacities
+// staging pass: persistent, `grid` CTAs take tiles in the order of Q (its head
+// and W.ctr are reset first); then the global-memory tier over the tiles ovf lists
+int launch_edge_stage(const Model &M, const Batch &B, int precision, const TileSched &Q, int grid,
+                      const int8_t *labels, const int *edge_start, EdgeOut out, int *err, int *ovf,
+                      unsigned char *big, const RootWork &W, cudaStream_t st);
+// roots of the candidates, picks and warp selections (`threads` per block of the root kernels)
+int launch_edge_roots(const Model &M, const Batch &B, int precision, int threads, EdgeOut out,
+                      const int *edge_start, long long ne_all, int *n_fail, int *err, long long *fail_log,
+                      const RootWork &W, cudaStream_t st);
 size_t edges_big_bytes();
 int launch_edge_polish(const Model &M, const Batch &B, EdgeOut out, long long n_edges_total, const long long *medge,
                        double2 *term, cudaStream_t st);

@@ -37,7 +37,7 @@ ESES_OPT_CLS_CTAS = 8
 ESES_OPT_CLS_TILES = 9
 ESES_OPT_EDGE_CTAS = 10
 ESES_OPT_EDGE_TILES = 11
-ESES_OPT_EDGE_CHUNK = 12
+ESES_OPT_ROOT_THREADS = 12
 ESES_OPT_EXTERIOR = 13
 ESES_OPT_TC_WAIT = 14
 ESES_OPT_FAIL_ALLOC = 15

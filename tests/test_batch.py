@@ -113,7 +113,7 @@ def test_graph_replay_and_queue_modes_give_identical_results():
         eses.eses_set_option(ctx, eses.ESES_OPT_QUEUE, 0)
         eses.eses_set_option(ctx, eses.ESES_OPT_CLS_CTAS, 1)
         eses.eses_set_option(ctx, eses.ESES_OPT_EDGE_TILES, 3)
-        eses.eses_set_option(ctx, eses.ESES_OPT_EDGE_CHUNK, 8)
+        eses.eses_set_option(ctx, eses.ESES_OPT_ROOT_THREADS, 128)
         eses.eses_run(ctx)
         eses.eses_run(ctx)
         for m in range(len(mols)):
@@ -148,7 +148,7 @@ def test_autotune_picks_a_shape_and_keeps_results():
         assert ms[0] > 0.0 and ms[1] > 0.0
         assert eses.eses_get_option(ctx, eses.ESES_OPT_CLS_CTAS) >= 1
         assert eses.eses_get_option(ctx, eses.ESES_OPT_EDGE_CTAS) >= 1
-        assert eses.eses_get_option(ctx, eses.ESES_OPT_EDGE_CHUNK) >= 1
+        assert eses.eses_get_option(ctx, eses.ESES_OPT_ROOT_THREADS) in (128, 256)
         for m in range(len(mols)):
             same_result(mol_result(ctx, m), base[m], h, tau_tol=0.0)
     finally:
