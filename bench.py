@@ -247,6 +247,38 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def profile_batch(args, eses, inputs, torch):
+    """--profile-only on the 256-molecule batch: one context, W + K runs (the
+    first plans, the rest replay its graph), one JSON line with the mean step
+    and stage times of the last K."""
+    bwl = inputs.WORKLOADS[3]
+    mols = [inputs.workload_atoms(3, molecule=m) for m in range(len(inputs.batch_sizes()))]
+    stream = torch.cuda.current_stream()
+    ctx = eses.eses_create_batch(mols, bwl.r_p, bwl.h, bwl.margin)
+    try:
+        eses.eses_set_option(ctx, eses.ESES_OPT_STREAM, stream.cuda_stream)
+        eses.eses_set_option(ctx, eses.ESES_OPT_GRAPH, 0 if args.no_graph else 1)
+        eses.eses_set_option(ctx, eses.ESES_OPT_PROFILE, 1)
+        times, stages = [], []
+        for k in range(args.warmup + args.steps):
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            eses.eses_run(ctx)
+            s1.record(stream)
+            s1.synchronize()
+            if k >= args.warmup:
+                times.append(s0.elapsed_time(s1))
+                stages.append(eses.eses_stage_times(ctx))
+        st = eses.eses_stats(ctx)
+        print(json.dumps({"profile_only": True, "workload": bwl.name, "ms_per_step": statistics.mean(times),
+                          "stages_ms": {k: statistics.mean(x[k] for x in stages) for k in stages[0]},
+                          "kernel_launches_per_step": st["kernel_launches"], "points": st["points"],
+                          "crossing_edges": st["crossing_edges"]}))
+    finally:
+        eses.eses_destroy(ctx)
+
+
 def config_of(wl, xyz, npts):
     return {"workload": f"{wl.name}: synthetic C-alpha-walk globule, {xyz.shape[0]} atoms, "
                         f"r_p {wl.r_p} A, h {wl.h} A, margin {wl.margin} A",
@@ -308,8 +340,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-only", action="store_true",
                     help="only the warm-up and device-resident steps (for ncu captures); prints stage times")
-    ap.add_argument("--profile-workload", default="globule", choices=["globule", "paper-density"],
-                    help="with --profile-only: the headline globule, or the paper-density globule at h 0.25")
+    ap.add_argument("--profile-workload", default="globule", choices=["globule", "paper-density", "batch-256"],
+                    help="with --profile-only: the headline globule, the paper-density globule at h 0.25, or the "
+                         "256-molecule batch (h 0.5, one context)")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shapes instead of the autotuner's")
     ap.add_argument("--no-graph", action="store_true", help="eager launches instead of CUDA-graph replay")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-molecule batched workload")
@@ -351,6 +384,9 @@ def main():
     barrier()
     libbuild.build()
     eses.load()
+    if args.profile_only and args.profile_workload == "batch-256":
+        profile_batch(args, eses, inputs, torch)
+        return
     wl = inputs.WORKLOADS[WORKLOAD]
     xyz, rad = inputs.workload_atoms(WORKLOAD, molecule=rank)
     if args.profile_only and args.profile_workload == "paper-density":
@@ -520,7 +556,8 @@ def main():
         "classify": ("k_classify<float,true> (FP32-filtered classification, every grid point)",
                      fm["model_flops"], stage_ms["classify"],
                      {"flops_per_point": fm["flops_per_point"]}),
-        "edge_solve": ("k_edge_solve<float,true> (first root and its patch of every crossing edge, pooled per tile)",
+        "edge_solve": ("root solve: k_edge_stage, k_roots_sphere, k_roots_torus, k_edge_pick, k_edge_hard "
+                       "<float,true> (first root and its patch of every crossing edge)",
                        fm["edge_counts"]["model_flops"], stage_ms["edge_solve"],
                        {"flops_per_edge": fm["edge_flops_per_edge"], "edges": fm["edge_counts"]["edges"]}),
     }

@@ -344,7 +344,12 @@ int eses_area_volume(const eses_ctx *ctx, double *area, double *volume);
  * sweeps, [15] tile stagings that overflowed the shared-memory lists (320
  * atoms, 512 free-arc pairs, 640 free triple points) and were redone with
  * lists in global memory (1024, 2048, 2048; beyond those ESES_ECAPACITY),
- * summed over the classification, the FP64 re-evaluation and the root solve. */
+ * summed over the classification, the FP64 re-evaluation and the root solve;
+ * [16] atom tests of the classification's witness freeness checks (each
+ * convex or saddle witness of a shell point is tested against the staged
+ * atoms whose expanded spheres meet its atoms' ones, one test per atom);
+ * [17] (edge, sphere) and [18] (edge, torus) candidates of the root solve's
+ * prefilter, [19] crossing edges that took the warp selection. */
 int eses_stats(const eses_ctx *ctx, int64_t *out, int n);
 
 /* Device time in milliseconds of every stage of the last eses_run, measured

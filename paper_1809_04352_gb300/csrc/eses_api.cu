@@ -30,7 +30,7 @@ using namespace eses;
 static_assert(MLP_NPARAM == ESES_MLP_NPARAM, "proposer parameter count");
 
 // stages timed with CUDA events when ESES_OPT_PROFILE is set
-enum { NSTAT = 16 };
+enum { NSTAT = 20 };
 enum { ST_BIN = 0, ST_PAIRS, ST_ARCS, ST_CLASSIFY, ST_BAND, ST_EDGE_COUNT, ST_EDGE_SOLVE, ST_EDGE_POLISH, ST_REDUCE, NSTAGE };
 
 namespace {
@@ -134,8 +134,8 @@ struct eses_ctx {
     DBuf fail_log;
     DBuf ovf, big;  // tiles that overflow the shared-memory staging, and the global-memory tier's scratch
     // phased root solve: edge records, candidates, their roots, staged tiles (slabs), counters, hard edges
-    DBuf r_einfo, r_ecnt, r_csph, r_ctor, r_nsph, r_ntor, r_rsph, r_rtor, r_slab, r_ctr, r_hard;
-    long long cap_sph = 0, cap_tor = 0, cap_slab = 0;  // planned capacities
+    DBuf r_einfo, r_ecnt, r_csph, r_ctor, r_nsph, r_ntor, r_rsph, r_rtor, r_slab, r_ctr, r_hard, r_jobs;
+    long long cap_sph = 0, cap_tor = 0, cap_slab = 0, cap_jobs = 0;  // planned capacities
     DBuf atom_hi, atom_lo, pair_hi, pair_lo, pair_u32, vert_hi, vert_lo;
     // plan: list sizes of the first run (the inputs never change)
     bool planned = false;
@@ -530,6 +530,7 @@ RootWork root_work(eses_ctx *c, long long ne_all)
         c->cap_tor = std::max(c->cap_tor, 4 * ne + 1024);
         c->cap_slab = std::max(c->cap_slab, 96 * ne + (1LL << 20));
         c->cap_slab = std::min(c->cap_slab, SLAB_CAP_MAX);
+        c->cap_jobs = std::max(c->cap_jobs, c->cap_tor / 4 + 4096);
     }
     RootWork W;
     W.einfo = ensure<int4>(c->r_einfo, (size_t)ne);
@@ -542,10 +543,12 @@ RootWork root_work(eses_ctx *c, long long ne_all)
     W.ntor = ensure<uint8_t>(c->r_ntor, (size_t)c->cap_tor);
     W.rtor = ensure<RootRec>(c->r_rtor, 4 * (size_t)c->cap_tor);
     W.slab = ensure<unsigned char>(c->r_slab, (size_t)c->cap_slab);
-    W.ctr = ensure<unsigned long long>(c->r_ctr, 4);
+    W.ctr = ensure<unsigned long long>(c->r_ctr, 8);
+    W.jobs = ensure<int2>(c->r_jobs, (size_t)c->cap_jobs);
     W.cap_slab = c->cap_slab;
     W.cap_sph = c->cap_sph;
     W.cap_tor = c->cap_tor;
+    W.cap_jobs = c->cap_jobs;
     W.n_edges = ne_all;
     return W;
 }
@@ -564,6 +567,7 @@ int run_device(eses_ctx *c)
     const long long nt = c->n_tiles;
     int *misc = ensure<int>(c->misc, 64);
     int *d_err = misc, *d_fail = misc + 1;
+    unsigned long long *d_tests = reinterpret_cast<unsigned long long *>(misc + 8);  // classification atom tests
     unsigned long long *queue = ensure<unsigned long long>(c->queue, 4);
     ck(cudaMemsetAsync(misc, 0, 64 * sizeof(int), st), "memset");
     ck(cudaMemsetAsync(queue, 0, 4 * sizeof(unsigned long long), st), "memset");
@@ -709,7 +713,7 @@ int run_device(eses_ctx *c)
     ck(cudaMemsetAsync(ovf, 0, sizeof(int), st), "memset");
     unsigned char *big = ensure<unsigned char>(c->big, std::max(classify_big_bytes(), edges_big_bytes()));
     nl += launch_classify(M, B, c->precision, cq, grid_of(c, c->cls, classify_ctas_per_sm(c->precision)), labels,
-                          c->precision == ESES_PREC_FP64 ? nullptr : tile_band, d_err, ovf, big, st);
+                          c->precision == ESES_PREC_FP64 ? nullptr : tile_band, d_err, ovf, big, d_tests, st);
     mark(c, ST_BAND);
     if (c->precision != ESES_PREC_FP64) nl += launch_band(M, B, labels, tile_band, d_err, ovf, big, st);
     c->n_cavity = 0;
@@ -804,6 +808,17 @@ int run_device(eses_ctx *c)
     }
     nl += launch_edge_roots(M, B, c->precision, c->edge.threads, eo, edge_start, ne_all, d_fail, d_err, fail_log, W,
                             st);
+    if (!g_capturing) {  // planning: a full FP64 job list is grown and the root launches rerun
+        unsigned long long jobs = 0;
+        ck(cudaMemcpyAsync(&jobs, W.ctr + 4, sizeof(jobs), cudaMemcpyDeviceToHost, st), "read");
+        ck(cudaStreamSynchronize(st), "synchronize");
+        if ((long long)jobs > W.cap_jobs) {
+            c->cap_jobs = (long long)(jobs + jobs / 8);
+            W = root_work(c, ne_all);
+            nl += launch_edge_roots(M, B, c->precision, c->edge.threads, eo, edge_start, ne_all, d_fail, d_err,
+                                    fail_log, W, st);
+        }
+    }
     mark(c, ST_EDGE_POLISH);
     nl += launch_edge_polish(M, B, eo, ne_all, medge, term, st);
     mark(c, ST_REDUCE);
@@ -829,6 +844,9 @@ int finish(eses_ctx *c, int nl)
     ck(cudaMemcpyAsync(hprop, c->prop_counts.p, sizeof(hprop), cudaMemcpyDeviceToHost, st), "read results");
     int hovf = 0;  // tiles the global-memory staging tier took
     ck(cudaMemcpyAsync(&hovf, c->ovf.p, sizeof(int), cudaMemcpyDeviceToHost, st), "read results");
+    // root solve: slab bytes, sphere and torus candidates, hard edges, torus candidates with FP64 work
+    unsigned long long rctr[5] = {0, 0, 0, 0, 0};
+    if (c->r_ctr.p) ck(cudaMemcpyAsync(rctr, c->r_ctr.p, sizeof(rctr), cudaMemcpyDeviceToHost, st), "read results");
     ck(cudaMemcpyAsync(c->medge_h.data(), c->medge.p, sizeof(long long) * c->medge_h.size(), cudaMemcpyDeviceToHost, st),
        "read results");
     ck(cudaMemcpyAsync(c->av_h.data(), c->av.p, sizeof(double) * c->av_h.size(), cudaMemcpyDeviceToHost, st),
@@ -856,8 +874,15 @@ int finish(eses_ctx *c, int nl)
     c->stats[13] = c->n_cavity;
     c->stats[14] = c->ext_sweeps;
     c->stats[15] = hovf;
+    unsigned long long tests = 0;
+    memcpy(&tests, hmisc + 8, sizeof(tests));
+    c->stats[16] = (long long)tests;
+    c->stats[17] = (long long)rctr[1];
+    c->stats[18] = (long long)rctr[2];
+    c->stats[19] = (long long)rctr[3];
     c->ran = true;
     int derr = hmisc[0];
+    if ((long long)rctr[4] > c->cap_jobs) derr |= ERR_CAP_CAND;  // the FP64 job list was full (never planned so)
     if (derr & (ERR_CAP_ATOMS | ERR_CAP_PAIRS | ERR_CAP_VERTS | ERR_CAP_CAND)) {
         c->ran = false;
         return fail(c, ESES_ECAPACITY, (derr & ERR_CAP_CAND) ? "an edge had more candidate roots than its buffer holds"
@@ -1249,7 +1274,7 @@ int eses_autotune(eses_ctx *c, int reps, double *ms_out)
                     ck(cudaMemsetAsync(c->queue.p, 0, 4 * sizeof(unsigned long long), st), "memset");
                     launch_classify(M, B, c->precision, sched_of(c, s, 0), grid_of(c, s, cls_max), labels,
                                     c->precision == ESES_PREC_FP64 ? nullptr : tile_band, misc, (int *)c->ovf.p,
-                                    (unsigned char *)c->big.p, st);
+                                    (unsigned char *)c->big.p, nullptr, st);
                 });
                 if (ms < best_cls_ms) best_cls_ms = ms, best_cls = s;
             }
@@ -1279,6 +1304,8 @@ int eses_autotune(eses_ctx *c, int reps, double *ms_out)
         W.rtor = (RootRec *)c->r_rtor.p;
         W.slab = (unsigned char *)c->r_slab.p;
         W.ctr = (unsigned long long *)c->r_ctr.p;
+        W.jobs = (int2 *)c->r_jobs.p;
+        W.cap_jobs = c->cap_jobs;
         W.cap_slab = c->cap_slab;
         W.cap_sph = c->cap_sph;
         W.cap_tor = c->cap_tor;
@@ -1868,7 +1895,7 @@ void eses_destroy(eses_ctx *c)
                     &c->vbin_cell, &c->vbin_list, &c->labels, &c->tile_band, &c->tile_edges, &c->edge_start,
                     &c->tile_inside, &c->scan_tmp, &c->misc, &c->av, &c->counts, &c->red_d, &c->red_i, &c->fail_log,
                     &c->ovf, &c->big, &c->r_einfo, &c->r_ecnt, &c->r_csph, &c->r_ctor, &c->r_nsph, &c->r_ntor,
-                    &c->r_rsph, &c->r_rtor, &c->r_slab, &c->r_ctr, &c->r_hard, &c->atom_hi,
+                    &c->r_rsph, &c->r_rtor, &c->r_slab, &c->r_ctr, &c->r_hard, &c->r_jobs, &c->atom_hi,
                     &c->atom_lo, &c->pair_hi, &c->pair_lo, &c->pair_u32, &c->vert_hi, &c->vert_lo,
                     &c->mlp_params, &c->need, &c->need_pos, &c->tile_list, &c->prop_counts, &c->features,
                     &c->targets, &c->ext, &c->ext_open, &c->ext_misc, &c->mesh_mask, &c->mesh_tile, &c->mesh_off,

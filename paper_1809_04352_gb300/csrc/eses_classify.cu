@@ -125,10 +125,11 @@ __device__ void build_incidence(const TileS<T, CP> &S, ClsSmem<CP> &C)
 // pairs) are numbered and lane r of the group tests those numbered r mod G.
 // Returns this lane's part: 0 a free witness within r_p (certain), 2 one is
 // undecided, 1 none; the group's label is 0 if any part is 0, else 2 if any
-// part is 2, else 1 -- the label of one lane testing every candidate.
+// part is 2, else 1 -- the label of one lane testing every candidate.  nt
+// counts the atom tests of the witnesses' freeness.
 template <bool FILT, class T, class CP>
 __device__ int shell_part(const TileS<T, CP> &S, const ClsSmem<CP> &C, int brick, T x, T y, T z, T rp, T d0, int r,
-                          int G)
+                          int G, int &nt)
 {
     SmemAcc<T, CP> A(S);
     constexpr int aw = ClsSmem<CP>::AWC;
@@ -153,7 +154,7 @@ __device__ int shell_part(const TileS<T, CP> &S, const ClsSmem<CP> &C, int brick
         T R = c.w + rp;
         if (lt_sq<FILT>(dx * dx + dy * dy + dz * dz, R * R, R, d0) == 0) continue;  // ball does not hold x
         if ((u & (G - 1)) == r) {
-            int w = face_witness<FILT>(A, a, x, y, z, rp, thr, d0, C.nbm, aw);
+            int w = face_witness<FILT>(A, a, x, y, z, rp, thr, d0, C.nbm, aw, nt);
             if (w == 1) return 0;
             if (w < 0) unsure = true;
         }
@@ -162,7 +163,7 @@ __device__ int shell_part(const TileS<T, CP> &S, const ClsSmem<CP> &C, int brick
         for (int k = k0 + ((r - u) & (G - 1)); k < k1; k += G) {
             const int p = (int)C.inc[k];
             const short2 sl = C.pslot[p];
-            int ws = saddle_witness<FILT>(A, p, x, y, z, rp, thr, d0, C.nbm, aw, (int)sl.x, (int)sl.y);
+            int ws = saddle_witness<FILT>(A, p, x, y, z, rp, thr, d0, C.nbm, aw, (int)sl.x, (int)sl.y, nt);
             if (ws == 1) return 0;
             if (ws < 0) unsure = true;
         }
@@ -187,7 +188,8 @@ __host__ __device__ constexpr size_t cls_bytes()
 template <class T, bool FILT, class CP, bool BIG>
 __global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Batch B, TileSched Q, int8_t *__restrict__ labels_all,
                                                           int *__restrict__ tile_band, int *__restrict__ err,
-                                                          int *__restrict__ ovf, unsigned char *__restrict__ big)
+                                                          int *__restrict__ ovf, unsigned char *__restrict__ big,
+                                                          unsigned long long *__restrict__ n_tests)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *store = BIG ? big + (size_t)blockIdx.x * cls_bytes<T, CP>() : smem_raw;
@@ -198,6 +200,7 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Batch B, Tile
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const T rp = (T)M.rp;
     long long iter = 0;
+    int ntests = 0;  // this thread's atom tests (witness freeness)
     const long long npos = sched_count(Q, B.n_tiles);
     for (;;) {
       const long long base = next_tiles(Q, iter, &q_base);
@@ -330,7 +333,7 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Batch B, Tile
             int brick = (code >> 9) & 15;
             int li = (code >> 6) & 7, lj = (code >> 3) & 7, lk = code & 7;
             T x = pt_coord<T>(G, li), y = pt_coord<T>(G, lj), z = pt_coord<T>(G, lk);
-            int part = shell_part<FILT, T, CP>(S, C, brick, x, y, z, rp, d0, r, gs);
+            int part = shell_part<FILT, T, CP>(S, C, brick, x, y, z, rp, d0, r, gs, ntests);
             // group label: 0 if any part found a witness, else 2 if any is undecided, else 1
             for (int o = 1; o < gs; o <<= 1) {
                 const int q = __shfl_xor_sync(gmask, part, o);
@@ -348,6 +351,9 @@ __global__ void __launch_bounds__(CLS_THREADS) k_classify(Model M, Batch B, Tile
         __syncthreads();
       }
     }
+    unsigned long long nw = (unsigned long long)ntests;
+    for (int o = 16; o > 0; o >>= 1) nw += __shfl_down_sync(0xffffffffu, nw, o);
+    if (lane == 0 && nw && n_tests) atomicAdd(n_tests, nw);
 }
 
 // The undecided points of global tile gt re-labelled in FP64 (whole block):
@@ -487,21 +493,22 @@ int classify_ctas_per_sm(int precision)
 // the shared-memory tier over the scheduled tiles, then the global-memory
 // tier over the tiles that overflowed it (ovf: count, then tiles)
 int launch_classify(const Model &M, const Batch &B, int precision, const TileSched &Q, int grid, int8_t *labels,
-                    int *tile_band, int *err, int *ovf, unsigned char *big, cudaStream_t st)
+                    int *tile_band, int *err, int *ovf, unsigned char *big, unsigned long long *n_tests,
+                    cudaStream_t st)
 {
     if (grid < 1) grid = 1;
     cudaMemsetAsync(ovf + 1, 0, sizeof(int), st);
     TileSched QB{nullptr, 1, ovf + 2, ovf + 1};
     if (precision == 0) {
         k_classify<double, false, CapSmall, false><<<grid, CLS_THREADS, cls_bytes<double, CapSmall>(), st>>>(
-            M, B, Q, labels, tile_band, err, ovf, nullptr);
+            M, B, Q, labels, tile_band, err, ovf, nullptr, n_tests);
         k_classify<double, false, CapBig, true><<<g_n_sm, CLS_THREADS, 0, st>>>(M, B, QB, labels, tile_band, err, ovf,
-                                                                               big);
+                                                                               big, n_tests);
     } else {
         k_classify<float, true, CapSmall, false><<<grid, CLS_THREADS, cls_bytes<float, CapSmall>(), st>>>(
-            M, B, Q, labels, tile_band, err, ovf, nullptr);
+            M, B, Q, labels, tile_band, err, ovf, nullptr, n_tests);
         k_classify<float, true, CapBig, true><<<g_n_sm, CLS_THREADS, 0, st>>>(M, B, QB, labels, tile_band, err, ovf,
-                                                                             big);
+                                                                             big, n_tests);
     }
     return 2;
 }

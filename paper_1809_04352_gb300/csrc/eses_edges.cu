@@ -58,6 +58,7 @@ constexpr int WCAND = 64;        // candidate roots of one edge in the selection
 constexpr int ROOT_THREADS_MAX = 256;  // per-candidate root kernels: threads per block (at most, the default)
 constexpr int PICK_THREADS = 256;
 constexpr int HARD_THREADS = 256;
+constexpr int HMASK_WORDS = 2048;  // prefilter hit masks kept between the staging pass's two sweeps
 constexpr int POLISH_THREADS = 256;
 
 // --------------------------------------------------------------------------
@@ -301,7 +302,19 @@ struct RootSink {
         }
         ++n;
     }
+    // a slot kept for a root whose decision needs FP64 (err < 0: pending; the
+    // FP32 root kept in t), settled by k_roots_torus_exact
+    __device__ __forceinline__ void pend(float t) { push(t, -1.0f, __longlong_as_double(0x7ff8000000000000LL)); }
 };
+// a settled slot whose root was rejected
+__device__ __forceinline__ RootRec no_root()
+{
+    RootRec q;
+    q.t64 = __longlong_as_double(0x7ff8000000000000LL);
+    q.t = INFINITY;
+    q.err = 0.0f;
+    return q;
+}
 
 // einfo[].y: lower point (local index), axis, end label, dropped (a buffer of
 // the staging pass was full)
@@ -328,9 +341,10 @@ __host__ __device__ constexpr long long align16(long long b) { return (b + 15) &
 
 template <class T>
 struct SlabLayout {
-    long long atom, po, pu, vq, agid, pij, pidx, vidx, face, bytes;
+    long long atom, po, pu, vq, agid, pij, pidx, vidx, face, nbm, pslot, bytes;
     __host__ __device__ SlabLayout(int na, int np, int nv)
     {
+        const long long nw = (na + 31) / 32;  // words of a set of staged atoms
         const long long P = (long long)sizeof(P4<T>);
         atom = (long long)sizeof(SlabHdr);
         po = atom + na * P;
@@ -341,7 +355,9 @@ struct SlabLayout {
         pidx = align16(pij + 8LL * np);
         vidx = align16(pidx + 4LL * np);
         face = align16(vidx + 4LL * nv);
-        bytes = align16(face + na);
+        nbm = align16(face + na);
+        pslot = align16(nbm + 4LL * na * nw);
+        bytes = align16(pslot + 4LL * np);
     }
 };
 
@@ -365,7 +381,9 @@ struct SlabAcc {
     const int *agid_, *pidx_, *vidx_;
     const int2 *pij_;
     const uint8_t *face_;
-    int na_, np_, nv_;
+    const unsigned *nbm_;
+    const short2 *pslot_;
+    int na_, np_, nv_, nw_;
     __device__ explicit SlabAcc(const unsigned char *s)
     {
         const int4 h = __ldg(reinterpret_cast<const int4 *>(s));
@@ -382,6 +400,9 @@ struct SlabAcc {
         pidx_ = reinterpret_cast<const int *>(s + L.pidx);
         vidx_ = reinterpret_cast<const int *>(s + L.vidx);
         face_ = reinterpret_cast<const uint8_t *>(s + L.face);
+        nbm_ = reinterpret_cast<const unsigned *>(s + L.nbm);
+        pslot_ = reinterpret_cast<const short2 *>(s + L.pslot);
+        nw_ = (na_ + 31) >> 5;
     }
     __device__ int na() const { return na_; }
     __device__ int np() const { return np_; }
@@ -395,6 +416,11 @@ struct SlabAcc {
     __device__ P4<T> vq(int v) const { return ldg4(vq_ + v); }
     __device__ int pidx(int p) const { return __ldg(pidx_ + p); }
     __device__ int vidx(int v) const { return __ldg(vidx_ + v); }
+    // neighbour set of staged atom a (staged atoms whose expanded spheres
+    // come within 1e-3 A of meeting a's), ceil(na / 32) words
+    __device__ const unsigned *nb(int a) const { return nbm_ + (size_t)a * nw_; }
+    // staged slots of pair p's atoms (-1: not staged)
+    __device__ short2 pslot(int p) const { return __ldg(pslot_ + p); }
     // model index of a staged piece (kind as in WCand)
     __device__ int model_index(int kind, int slot) const
     {
@@ -437,7 +463,24 @@ struct SlabExact {
         const double4 g = M.vert[S.vidx(v)];
         return P4<double>{g.x - x0, g.y - y0, g.z - z0, 0.0};
     }
+    __device__ const unsigned *nb(int a) const { return S.nb(a); }
+    __device__ short2 pslot(int p) const { return S.pslot(p); }
 };
+
+// Freeness of a witness on the expanded sphere of staged atom a (and, for a
+// saddle witness, of staged atom b too): only the atoms whose expanded
+// spheres meet a's (and b's) can cover it, so the neighbour sets decide the
+// same as a test against every staged atom but a and b (free_set).  A pair
+// whose atoms are not both staged is tested against every staged atom.
+template <bool FILT, class Acc, class T>
+__device__ __forceinline__ int free_witness(const Acc &A, T qx, T qy, T qz, int sa, int sb, int ga, int gb, T rp,
+                                            T delta)
+{
+    int nt = 0;
+    if (sa >= 0 && (gb < 0 || sb >= 0))
+        return free_set<FILT>(A, qx, qy, qz, A.nb(sa), gb < 0 ? (const unsigned *)nullptr : A.nb(sb), rp, delta, nt);
+    return free_pt<FILT>(A, qx, qy, qz, ga, gb, rp, delta);
+}
 
 // shared memory of the staging pass (beside the staged tile)
 struct StageSmem {
@@ -453,7 +496,15 @@ struct StageSmem {
     long long slab;    // slab offset (16-byte units), -1 when the slab buffer is full
     long long sb, tb;  // the tile's first sphere / torus candidate, -1 when a buffer is full
     long long sb0, tb0;  // the same as reserved (also when a buffer is full)
+    unsigned hmask[HMASK_WORDS];  // prefilter hits, ceil(items / 32) words per edge (when they fit)
 };
+
+// items [0, nsph) are spheres: the bits of 32-item word w that are spheres
+__device__ __forceinline__ unsigned sphere_bits(int w, int nsph)
+{
+    const int r = nsph - 32 * w;
+    return r >= 32 ? 0xffffffffu : (r <= 0 ? 0u : (1u << r) - 1u);
+}
 
 // axis, lower point (local index) and its label of crossing edge e of the tile
 struct EdgeRef {
@@ -642,8 +693,9 @@ __device__ __noinline__ void torus_root_exact(const Acc &X, RootSink &out, int p
     const double rate = fabs(rd) <= 1e-9 ? 0.0 : rd;
     if (inside ? rate > 0.0 : rate < 0.0) return;
     const int2 ij = X.pij(pi);
-    const int f = free_pt<false>(X, oo[0] + oe.w * wd[0], oo[1] + oe.w * wd[1], oo[2] + oe.w * wd[2], ij.x, ij.y, rp,
-                                 0.0);
+    const short2 sl = X.pslot(pi);
+    const int f = free_witness<false>(X, oo[0] + oe.w * wd[0], oo[1] + oe.w * wd[1], oo[2] + oe.w * wd[2], (int)sl.x,
+                                      (int)sl.y, ij.x, ij.y, rp, 0.0);
     if (f == 1) out.push((float)t64, 0.0f, t64);
 }
 
@@ -766,8 +818,8 @@ __device__ void sphere_roots(const AccT &A, const AccX &X, int item, const doubl
             int f = -1;
             if (FILT) {
                 const T delta = d0 + terr * (T(1) + sc) + T(2e-6);
-                f = free_pt<true>(A, c.x + sc * v32[0], c.y + sc * v32[1], c.z + sc * v32[2], A.agid(slot), -1, rpT,
-                                  delta);
+                f = free_witness<true>(A, c.x + sc * v32[0], c.y + sc * v32[1], c.z + sc * v32[2], slot, -1,
+                                       A.agid(slot), -1, rpT, delta);
             }
             if (f < 0) {
                 const P4<double> ce = X.atom(slot);
@@ -777,8 +829,8 @@ __device__ void sphere_roots(const AccT &A, const AccX &X, int item, const doubl
                 v[axis] += t64;
                 const double nv64 = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
                 const double R64 = ce.w + rp;
-                f = free_pt<false>(X, cc[0] + R64 * v[0] / nv64, cc[1] + R64 * v[1] / nv64, cc[2] + R64 * v[2] / nv64,
-                                   A.agid(slot), -1, rp, 0.0);
+                f = free_witness<false>(X, cc[0] + R64 * v[0] / nv64, cc[1] + R64 * v[1] / nv64,
+                                        cc[2] + R64 * v[2] / nv64, slot, -1, A.agid(slot), -1, rp, 0.0);
             }
             if (f != 1) continue;
         }
@@ -833,6 +885,7 @@ __device__ void torus_roots(const AccT &A, const AccX &X, int pi, const double *
             }
         }
         const int2 ij = A.pij(pi);
+        const short2 sl = A.pslot(pi);
         for (int k = 0; k < nr; ++k) {
             const float t = rt[k];
             float D, rate, nw, yy, zy, wv[3];
@@ -852,8 +905,8 @@ __device__ void torus_roots(const AccT &A, const AccX &X, int pi, const double *
             if (inside ? rate > 0.0f : rate < 0.0f) continue;
             const float kk = o.w / nw;
             const float delta = d0 + terr * (1.0f + 2.0f * o.w / nw) + 2e-6f;
-            const int f =
-                free_pt<true>(A, o.x + kk * wv[0], o.y + kk * wv[1], o.z + kk * wv[2], ij.x, ij.y, rpT, delta);
+            const int f = free_witness<true>(A, o.x + kk * wv[0], o.y + kk * wv[1], o.z + kk * wv[2], (int)sl.x,
+                                             (int)sl.y, ij.x, ij.y, rpT, delta);
             if (f == 1) {
                 out.push(t, terr, NaN);
             } else if (f < 0) {
@@ -1256,7 +1309,10 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_stage(Model M, Batch B, T
                 (long long)(TILE * (t[0] + G.toff[0]) + li) * fst0 + (long long)(TILE * (t[1] + G.toff[1]) + lj) * fst1 +
                 (TILE * (t[2] + G.toff[2]) + lk);
         }
-        // (edge, item) pairs that pass the prefilter, counted: one warp per edge, lanes over items
+        // (edge, item) pairs that pass the prefilter, counted: one warp per edge,
+        // lanes over items; the hit masks kept when they fit
+        const int nwd = (nitem + 31) >> 5;
+        const bool keep = (long long)ne * nwd <= HMASK_WORDS;
         for (int e = warp; e < ne; e += EDGE_WARPS) {
             const EdgeRef R = edge_ref(E, e);
             const T s[3] = {(T)E.hd[R.p >> 6], (T)E.hd[(R.p >> 3) & 7], (T)E.hd[R.p & 7]};
@@ -1264,8 +1320,10 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_stage(Model M, Batch B, T
             for (int i0 = 0; i0 < nitem; i0 += 32) {
                 const int it = i0 + lane;
                 const bool hit = it < nitem && cand_test<T, CP>(S, s, R.axis, it, hT, rpT, mg);
-                cs += __popc(__ballot_sync(0xffffffffu, hit && it < nsph));
-                ct += __popc(__ballot_sync(0xffffffffu, hit && it >= nsph));
+                const unsigned m = __ballot_sync(0xffffffffu, hit), sm = sphere_bits(i0 >> 5, nsph);
+                cs += __popc(m & sm);
+                ct += __popc(m & ~sm);
+                if (keep && lane == 0) E.hmask[e * nwd + (i0 >> 5)] = m;
             }
             if (lane == 0) {
                 E.cs[e] = cs;
@@ -1327,6 +1385,36 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_stage(Model M, Batch B, T
                 pv[k] = S.vq[k];
                 vx[k] = S.vidx[k];
             }
+            // neighbour sets (expanded spheres within 1e-3 A of meeting; the
+            // margin covers the rounding of the staged FP32 positions)
+            unsigned *nbm = reinterpret_cast<unsigned *>(sl + L.nbm);
+            const int nw = (na + 31) >> 5;
+            for (int it = threadIdx.x; it < na * nw; it += EDGE_THREADS) {
+                const int a = it / nw, w = it - a * nw;
+                const P4<T> ca = S.atom[a];
+                const T Ra = ca.w + rpT + T(1e-3);
+                unsigned bits = 0u;
+                const int b0 = w << 5, b1 = min(na, b0 + 32);
+                for (int b = b0; b < b1; ++b) {
+                    const P4<T> cb = S.atom[b];
+                    const T dx = ca.x - cb.x, dy = ca.y - cb.y, dz = ca.z - cb.z;
+                    const T reach = Ra + cb.w + rpT;
+                    if (b != a && dx * dx + dy * dy + dz * dz < reach * reach) bits |= 1u << (b - b0);
+                }
+                nbm[it] = bits;
+            }
+            // staged slots of every pair's atoms
+            short2 *ps = reinterpret_cast<short2 *>(sl + L.pslot);
+            for (int k = threadIdx.x; k < np; k += EDGE_THREADS) {
+                const int2 ij = S.pij[k];
+                int si = -1, sj = -1;
+                for (int a = 0; a < na; ++a) {
+                    const int g = S.agid[a];
+                    si = g == ij.x ? a : si;
+                    sj = g == ij.y ? a : sj;
+                }
+                ps[k] = make_short2((short)si, (short)sj);
+            }
         }
         // edge records
         for (int e = threadIdx.x; e < ne; e += EDGE_THREADS) {
@@ -1350,9 +1438,11 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_stage(Model M, Batch B, T
                 const unsigned below = (1u << lane) - 1;
                 for (int i0 = 0; i0 < nitem; i0 += 32) {
                     const int it = i0 + lane;
-                    const bool hit = it < nitem && cand_test<T, CP>(S, s, R.axis, it, hT, rpT, mg);
-                    const unsigned ms = __ballot_sync(0xffffffffu, hit && it < nsph);
-                    const unsigned mt = __ballot_sync(0xffffffffu, hit && it >= nsph);
+                    const unsigned m =
+                        keep ? E.hmask[e * nwd + (i0 >> 5)]
+                             : __ballot_sync(0xffffffffu, it < nitem && cand_test<T, CP>(S, s, R.axis, it, hT, rpT, mg));
+                    const bool hit = (m >> lane) & 1u;
+                    const unsigned sm = sphere_bits(i0 >> 5, nsph), ms = m & sm, mt = m & ~sm;
                     const long long qs = ps + __popc(ms & below), qt = pt + __popc(mt & below);
                     if (hit && it < nsph && qs < ps1) W.csph[qs] = make_int2(g, it);
                     if (hit && it >= nsph && qt < pt1) W.ctor[qt] = make_int2(g, it - nsph);
@@ -1410,19 +1500,74 @@ __global__ void __launch_bounds__(ROOT_THREADS_MAX) k_roots_sphere(Model M, Batc
     }
 }
 
-// 3. Roots of the torus candidates, one thread each (grid-stride).
+// The FP32 part of torus_roots (FILT): the certified isolation and, per
+// root, the FP32 decisions.  A root whose decision needs FP64 keeps a pending
+// slot; a candidate whose isolation is undecided is left whole to the exact
+// kernel.  Returns 0 (done), 1 (pending slots) or 2 (whole candidate).
+template <class AccT>
+__device__ int torus_roots_fp32(const AccT &A, int pi, const double *s64, int axis, bool inside, double h, double rp,
+                                float d0, RootSink &out)
+{
+    const float s[3] = {(float)s64[0], (float)s64[1], (float)s64[2]};
+    const float hT = (float)h, rpT = (float)rp;
+    const float lo = -1e-4f, hi = hT + 1e-4f;
+    const float tmax = 1e-3f;
+    const double NaN = __longlong_as_double(0x7ff8000000000000LL);
+    const P4<float> o = A.po(pi);
+    const P4<float> u = A.pu(pi);
+    const float q0[3] = {s[0] - o.x, s[1] - o.y, s[2] - o.z};
+    const float uu[3] = {u.x, u.y, u.z};
+    float rt[4];
+    int nr = 0;
+    if (!torus_roots32(q0, uu, o.w, rpT, axis, lo, hi, d0, rt, nr)) return 2;
+    int job = 0;
+    const int2 ij = A.pij(pi);
+    const short2 sl = A.pslot(pi);
+    for (int k = 0; k < nr; ++k) {
+        const float t = rt[k];
+        float D, rate, nw, yy, zy, wv[3];
+        circle_dist32(q0, uu, o.w, axis, t, D, rate, nw, yy, zy, wv);
+        const float terr = (fabsf(D - rpT) + circle_dist_err(d0, yy, nw, o.w, rpT)) / fmax(fabs(rate), 1e-20f) + d0;
+        if (terr > tmax || t < terr + 1e-6f || t > hT - terr - 1e-6f || fabs(rate) < 1e-3f || nw < 1e-3f) {
+            out.pend(t);  // grazing or at an end point: the FP64 root decides
+            job = 1;
+            continue;
+        }
+        if (inside ? rate > 0.0f : rate < 0.0f) continue;
+        const float kk = o.w / nw;
+        const float delta = d0 + terr * (1.0f + 2.0f * o.w / nw) + 2e-6f;
+        const int f = free_witness<true>(A, o.x + kk * wv[0], o.y + kk * wv[1], o.z + kk * wv[2], (int)sl.x,
+                                         (int)sl.y, ij.x, ij.y, rpT, delta);
+        if (f == 1) {
+            out.push(t, terr, NaN);
+        } else if (f < 0) {
+            out.pend(t);
+            job = 1;
+        }
+    }
+    return job;
+}
+
+// 3. Roots of the torus candidates, one thread each (grid-stride, the lanes
+// of a warp together).  FP32 form: torus_roots_fp32, and the candidates with
+// FP64 work listed for k_roots_torus_exact (one warp-aggregated append per
+// iteration); FP64 form: every root in FP64 here.
 template <class T, bool FILT>
 __global__ void __launch_bounds__(ROOT_THREADS_MAX) k_roots_torus(Model M, Batch B, RootWork W,
                                                                   int *__restrict__ err)
 {
     const long long n = min((long long)W.ctr[2], W.cap_tor);
     const double rp = M.rp;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); k0 < n; k0 += stride) {
+        const long long k = k0 + lane;
+        int job = 0;
+        if (k < n) {
         const int2 c = W.ctor[k];
         if (c.x < 0 || c.x >= W.n_edges) {  // dead record
             W.ntor[k] = 0;
-            continue;
-        }
+        } else {
         const int4 inf = W.einfo[c.x];
         const unsigned char *sl = W.slab + ((size_t)(unsigned)inf.x << 4);
         const SlabHdr *hd = reinterpret_cast<const SlabHdr *>(sl);
@@ -1435,9 +1580,77 @@ __global__ void __launch_bounds__(ROOT_THREADS_MAX) k_roots_torus(Model M, Batch
         const SlabAcc<T> A(sl);
         const SlabExact<T> X(A, M, x0);
         RootSink out{W.rtor + (size_t)TOR_SLOTS * k, 0, TOR_SLOTS};
-        torus_roots<T, FILT>(A, X, c.y, s64, pk_axis(pk), pk_label(pk) == LABEL_IN, h, rp, d0, out);
+        if constexpr (FILT) {
+            job = torus_roots_fp32(A, c.y, s64, pk_axis(pk), pk_label(pk) == LABEL_IN, h, rp, (float)d0, out);
+        } else {
+            torus_roots<T, FILT>(A, X, c.y, s64, pk_axis(pk), pk_label(pk) == LABEL_IN, h, rp, d0, out);
+        }
         if (out.n > TOR_SLOTS) atomicOr(err, ERR_CAP_CAND);
         W.ntor[k] = (uint8_t)min(out.n, TOR_SLOTS);
+        }
+        }
+        if constexpr (FILT) {  // list the candidates with FP64 work: (candidate, whole)
+            const unsigned m = __ballot_sync(0xffffffffu, job != 0);
+            if (m) {
+                unsigned long long b = 0;
+                if (lane == 0) b = atomicAdd(W.ctr + 4, (unsigned long long)__popc(m));
+                b = __shfl_sync(0xffffffffu, b, 0);
+                if (job != 0) {
+                    const unsigned long long q = b + __popc(m & ((1u << lane) - 1));
+                    // (a full list is reported by the run from the count)
+                    if (q < (unsigned long long)W.cap_jobs) W.jobs[q] = make_int2((int)k, job);
+                }
+            }
+        }
+    }
+}
+
+// 3b. The listed torus candidates' FP64 work, one thread each (FP32 form
+// only): job 1 settles the pending slots (the FP64 root next to the FP32 one,
+// kept or rejected as torus_roots does), job 2 solves the whole candidate
+// with torus_roots (the quartic on its derivative chain, FP64 where needed).
+template <class T, bool FILT>
+__global__ void __launch_bounds__(ROOT_THREADS_MAX) k_roots_torus_exact(Model M, Batch B, RootWork W,
+                                                                        int *__restrict__ err)
+{
+    const long long n = min((long long)W.ctr[4], W.cap_jobs);
+    const double rp = M.rp;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const int2 jb = W.jobs[q];
+        const long long k = jb.x;
+        const int2 c = W.ctor[k];
+        const int4 inf = W.einfo[c.x];
+        const unsigned char *sl = W.slab + ((size_t)(unsigned)inf.x << 4);
+        const SlabHdr *hd = reinterpret_cast<const SlabHdr *>(sl);
+        const int mol = __ldg(&hd->mol);
+        const double x0[3] = {__ldg(&hd->x0[0]), __ldg(&hd->x0[1]), __ldg(&hd->x0[2])};
+        const double h = B.grid[mol].h;
+        const T d0 = FILT ? (T)B.grid[mol].d0 : T(0);
+        const int pk = inf.y, p = pk_point(pk), axis = pk_axis(pk);
+        const bool inside = pk_label(pk) == LABEL_IN;
+        const double s64[3] = {(double)(p >> 6) * h, (double)((p >> 3) & 7) * h, (double)(p & 7) * h};
+        const SlabAcc<T> A(sl);
+        const SlabExact<T> X(A, M, x0);
+        RootRec *slots = W.rtor + (size_t)TOR_SLOTS * k;
+        if (jb.y == 2) {
+            RootSink out{slots, 0, TOR_SLOTS};
+            torus_roots<T, FILT>(A, X, c.y, s64, axis, inside, h, rp, d0, out);
+            if (out.n > TOR_SLOTS) atomicOr(err, ERR_CAP_CAND);
+            W.ntor[k] = (uint8_t)min(out.n, TOR_SLOTS);
+        } else {
+            const P4<double> oe = X.po(c.y);
+            const P4<double> ue = X.pu(c.y);
+            const double oo[3] = {oe.x, oe.y, oe.z}, u64[3] = {ue.x, ue.y, ue.z};
+            const int nr = W.ntor[k];
+            for (int j = 0; j < nr; ++j) {
+                const RootRec r = slots[j];
+                if (!(r.err < 0.0f)) continue;
+                const double t64 = exact_root_torus(oo, u64, oe.w, rp, s64, axis, (double)r.t);
+                RootSink one{slots + j, 0, 1};
+                torus_root_exact(X, one, c.y, s64, axis, h, rp, inside, t64);
+                if (one.n == 0) slots[j] = no_root();
+            }
+        }
     }
 }
 
@@ -1490,8 +1703,9 @@ __global__ void __launch_bounds__(PICK_THREADS) k_edge_pick(Batch B, RootWork W,
                 double t64k = 0.0;
                 for (int j = 0; j < ns; ++j) {
                     const int nr = W.nsph[inf.z + j];
-                    for (int r = 0; r < nr; ++r, ++n) {
+                    for (int r = 0; r < nr; ++r) {
                         const RootRec q = W.rsph[(size_t)SPH_SLOTS * (inf.z + j) + r];
+                        if (!(q.t < INFINITY)) continue;
                         if (q.t < tk) {
                             const int it = W.csph[inf.z + j].y;
                             tk = q.t;
@@ -1501,12 +1715,14 @@ __global__ void __launch_bounds__(PICK_THREADS) k_edge_pick(Batch B, RootWork W,
                             slot = it < na ? it : it - na;
                             kn = n;
                         }
+                        ++n;
                     }
                 }
                 for (int j = 0; j < nq; ++j) {
                     const int nr = W.ntor[inf.w + j];
-                    for (int r = 0; r < nr; ++r, ++n) {
+                    for (int r = 0; r < nr; ++r) {
                         const RootRec q = W.rtor[(size_t)TOR_SLOTS * (inf.w + j) + r];
+                        if (!(q.t < INFINITY) || q.err < 0.0f) continue;  // rejected (or never settled)
                         if (q.t < tk) {
                             tk = q.t;
                             ek = q.err;
@@ -1515,6 +1731,7 @@ __global__ void __launch_bounds__(PICK_THREADS) k_edge_pick(Batch B, RootWork W,
                             slot = W.ctor[inf.w + j].y;
                             kn = n;
                         }
+                        ++n;
                     }
                 }
                 hard = !(n >= 1 && n <= WCAND && (lab == LABEL_IN || n == 1) && kn >= 0);
@@ -1523,16 +1740,20 @@ __global__ void __launch_bounds__(PICK_THREADS) k_edge_pick(Batch B, RootWork W,
                     int m = 0;
                     for (int j = 0; j < ns && !hard; ++j) {
                         const int nr = W.nsph[inf.z + j];
-                        for (int r = 0; r < nr; ++r, ++m) {
+                        for (int r = 0; r < nr; ++r) {
                             const RootRec q = W.rsph[(size_t)SPH_SLOTS * (inf.z + j) + r];
-                            if (m != kn && q.t < INFINITY && q.t - tk <= q.err + ek + tie) hard = true;
+                            if (!(q.t < INFINITY)) continue;
+                            if (m != kn && q.t - tk <= q.err + ek + tie) hard = true;
+                            ++m;
                         }
                     }
                     for (int j = 0; j < nq && !hard; ++j) {
                         const int nr = W.ntor[inf.w + j];
-                        for (int r = 0; r < nr; ++r, ++m) {
+                        for (int r = 0; r < nr; ++r) {
                             const RootRec q = W.rtor[(size_t)TOR_SLOTS * (inf.w + j) + r];
-                            if (m != kn && q.t < INFINITY && q.t - tk <= q.err + ek + tie) hard = true;
+                            if (!(q.t < INFINITY) || q.err < 0.0f) continue;
+                            if (m != kn && q.t - tk <= q.err + ek + tie) hard = true;
+                            ++m;
                         }
                     }
                 }
@@ -1614,7 +1835,7 @@ __global__ void __launch_bounds__(HARD_THREADS) k_edge_hard(Model M, Batch B, Ro
                                            : W.rtor[(size_t)TOR_SLOTS * (inf.w + (j - ns)) + r];
                     WCand &w = c[at + r];
                     w.t64 = qr.t64;
-                    w.t = qr.t;
+                    w.t = qr.err < 0.0f ? INFINITY : qr.t;  // a rejected (or unsettled) slot: no candidate
                     w.err = qr.err;
                     w.kind = kind;
                     w.id = slot;
@@ -1857,6 +2078,7 @@ static int g_edge_n_sm = 1;  // SMs: the grid of the global-memory tier and of t
 // resident blocks per SM: [FP64, FP32][sphere roots, torus roots][64, 128, 256 threads]; hard selection
 static int g_occ_roots[2][2][3];
 static int g_occ_hard[2];
+static int g_occ_exact[2];
 
 static int threads_slot(int threads) { return threads <= 64 ? 0 : (threads <= 128 ? 1 : 2); }
 
@@ -1882,6 +2104,7 @@ void edges_init()
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ_roots[1][0][k], k_roots_sphere<float, true>, tb[k], 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ_roots[1][1][k], k_roots_torus<float, true>, tb[k], 0);
     }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ_exact[1], k_roots_torus_exact<float, true>, 256, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ_hard[0], k_edge_hard<double, false>, HARD_THREADS, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_occ_hard[1], k_edge_hard<float, true>, HARD_THREADS, 0);
 }
@@ -1919,7 +2142,7 @@ static void stage_launch(const Model &M, const Batch &B, const TileSched &Q, int
                          const int *edge_start, EdgeOut out, int *err, int *ovf, unsigned char *big,
                          const RootWork &W, cudaStream_t st)
 {
-    cudaMemsetAsync(W.ctr, 0, 4 * sizeof(unsigned long long), st);
+    cudaMemsetAsync(W.ctr, 0, 8 * sizeof(unsigned long long), st);
     if (Q.head) cudaMemsetAsync(Q.head, 0, sizeof(unsigned long long), st);
     cudaMemsetAsync(ovf + 1, 0, sizeof(int), st);
     k_edge_stage<T, FILT, CapSmall, false><<<grid, EDGE_THREADS, stage_smem<T>(), st>>>(M, B, Q, labels, edge_start,
@@ -1938,7 +2161,10 @@ static void roots_launch(const Model &M, const Batch &B, int threads, EdgeOut ou
     const int gs = std::max(g_occ_roots[P][0][ts], 1) * g_edge_n_sm;
     const int gq = std::max(g_occ_roots[P][1][ts], 1) * g_edge_n_sm;
     k_roots_sphere<T, FILT><<<gs, tb, 0, st>>>(M, B, W, err);
+    cudaMemsetAsync(W.ctr + 3, 0, 2 * sizeof(unsigned long long), st);  // hard edges, FP64 jobs
     k_roots_torus<T, FILT><<<gq, tb, 0, st>>>(M, B, W, err);
+    if (FILT)
+        k_roots_torus_exact<T, FILT><<<std::max(g_occ_exact[P], 1) * g_edge_n_sm, tb, 0, st>>>(M, B, W, err);
     const long long pb = std::min<long long>(std::max<long long>(ceil_div_ll(ne_all, PICK_THREADS), 1),
                                              8LL * g_edge_n_sm);
     k_edge_pick<T><<<(unsigned)pb, PICK_THREADS, 0, st>>>(B, W, edge_start, ne_all, out, err);
@@ -1967,7 +2193,7 @@ int launch_edge_roots(const Model &M, const Batch &B, int precision, int threads
         roots_launch<double, false>(M, B, threads, out, edge_start, ne_all, n_fail, err, fail_log, W, st);
     else
         roots_launch<float, true>(M, B, threads, out, edge_start, ne_all, n_fail, err, fail_log, W, st);
-    return 4;
+    return precision == 0 ? 4 : 5;
 }
 
 long long polish_blocks(long long n_edges) { return n_edges > 0 ? ceil_div_ll(n_edges, POLISH_THREADS) : 0; }

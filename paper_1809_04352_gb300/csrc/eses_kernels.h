@@ -45,8 +45,10 @@ int classify_ctas_per_sm(int precision);
 // ovf: int[2 + tiles] scratch (tiles sent to the global-memory tier over the
 // run, the stage's count, then the tiles that overflowed the shared-memory
 // staging); big: classify_big_bytes() of global scratch for that tier
+// n_tests (may be null): adds up the atom tests of the shell points' witness freeness
 int launch_classify(const Model &M, const Batch &B, int precision, const TileSched &Q, int grid, int8_t *labels,
-                    int *tile_band, int *err, int *ovf, unsigned char *big, cudaStream_t st);
+                    int *tile_band, int *err, int *ovf, unsigned char *big, unsigned long long *n_tests,
+                    cudaStream_t st);
 size_t classify_big_bytes();
 int launch_band(const Model &M, const Batch &B, int8_t *labels, const int *tile_band, int *err, int *ovf,
                 unsigned char *big, cudaStream_t st);
@@ -86,7 +88,8 @@ struct RootRec {
 };
 // buffers of the phased root solve; the capacities are planned by the caller
 // from the totals the staging pass adds up in ctr ([0] slab bytes, [1] sphere
-// and [2] torus candidates; [3] edges listed for the warp selection)
+// and [2] torus candidates; [3] edges listed for the warp selection; [4] torus
+// candidates listed for FP64 work)
 struct RootWork {
     int4 *einfo;            // per crossing edge: slab (16-byte units), packed point/axis/label/dropped,
                             // first sphere and first torus candidate
@@ -95,9 +98,10 @@ struct RootWork {
     uint8_t *nsph, *ntor;   // accepted roots per candidate
     RootRec *rsph, *rtor;   // their roots: 2 slots per sphere candidate, 4 per torus candidate
     unsigned char *slab;    // staged tiles
-    unsigned long long *ctr;
+    unsigned long long *ctr;  // 8 counters, [4] the torus candidates listed for FP64 work
     int *hard;              // edges listed for the warp selection (at most one per edge)
-    long long cap_slab, cap_sph, cap_tor;
+    int2 *jobs;             // torus candidates with FP64 work: (candidate, 1 pending slots / 2 whole)
+    long long cap_slab, cap_sph, cap_tor, cap_jobs;
     long long n_edges;      // crossing edges of the run (all axes)
 };
 void edges_init();

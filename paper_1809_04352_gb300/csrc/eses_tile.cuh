@@ -414,10 +414,10 @@ __device__ __noinline__ int free_pt(const Acc &A, T qx, T qy, T qz, int e0, int 
 // |q - c_a| = R_a give |c_a - c_k| < R_a + R_k.  So the neighbour sets of a
 // (and b) hold every atom that can cover q, and the answer is the one of
 // every staged atom but a and b; an atom outside the sets could only have
-// left an FP32 test undecided, never covered q.
+// left an FP32 test undecided, never covered q.  nt counts the atom tests.
 template <bool FILT, class Acc, class T>
 __device__ __noinline__ int free_set(const Acc &A, T qx, T qy, T qz, const unsigned *m0, const unsigned *m1, T rp,
-                                     T delta)
+                                     T delta, int &nt)
 {
     int res = 1;
     const int nw = (A.na() + 31) >> 5;
@@ -426,6 +426,7 @@ __device__ __noinline__ int free_set(const Acc &A, T qx, T qy, T qz, const unsig
         while (bits) {
             const int k = (w << 5) + __ffs(bits) - 1;
             bits &= bits - 1;
+            ++nt;
             const P4<T> c = A.atom(k);
             const T dx = qx - c.x, dy = qy - c.y, dz = qz - c.z;
             const T R = c.w + rp;
@@ -604,14 +605,14 @@ __device__ __forceinline__ int saddle_proposal(const Acc &A, int p, T x, T y, T 
 // projection's freeness is tested against a's neighbours (free_set).
 template <bool FILT, class Acc, class T>
 __device__ __noinline__ int face_witness(const Acc &A, int a, T x, T y, T z, T rp, T thr, T d0, const unsigned *nbm,
-                                         int aw)
+                                         int aw, int &nt)
 {
     T qx, qy, qz, dq;
     int e0, e1;
     const int tw = face_proposal<FILT>(A, a, x, y, z, rp, thr, d0, qx, qy, qz, dq, e0, e1);
     if (tw == 0) return 0;
     if (tw == -2) return -1;
-    int f = free_set<FILT>(A, qx, qy, qz, nbm + a * aw, (const unsigned *)nullptr, rp, dq + d0);
+    int f = free_set<FILT>(A, qx, qy, qz, nbm + a * aw, (const unsigned *)nullptr, rp, dq + d0, nt);
     if (f == 1 && tw == 1) return 1;
     return f == 0 ? 0 : -1;
 }
@@ -621,14 +622,14 @@ __device__ __noinline__ int face_witness(const Acc &A, int a, T x, T y, T z, T r
 // sa, sb).
 template <bool FILT, class Acc, class T>
 __device__ __noinline__ int saddle_witness(const Acc &A, int p, T x, T y, T z, T rp, T thr, T d0, const unsigned *nbm,
-                                           int aw, int sa, int sb)
+                                           int aw, int sa, int sb, int &nt)
 {
     T qx, qy, qz, dq;
     int e0, e1;
     const int t = saddle_proposal<FILT>(A, p, x, y, z, rp, thr, d0, qx, qy, qz, dq, e0, e1);
     if (t == 0) return 0;
     if (t == -2) return -1;
-    int f = free_set<FILT>(A, qx, qy, qz, nbm + sa * aw, nbm + sb * aw, rp, dq + d0);
+    int f = free_set<FILT>(A, qx, qy, qz, nbm + sa * aw, nbm + sb * aw, rp, dq + d0, nt);
     if (f == 1 && t == 1) return 1;
     return f == 0 ? 0 : -1;
 }

@@ -53,7 +53,8 @@ ESES_PREC_FP32_FILTERED = 1
 
 STAT_NAMES = ["points", "tiles", "work_tiles", "circle_pairs", "free_arc_pairs", "free_vertices", "band_points",
               "crossing_edges", "root_failures", "inside_points", "kernel_launches", "tiles_proposed_far",
-              "tiles_certified", "cavity_points", "exterior_sweeps", "big_tier_tiles"]
+              "tiles_certified", "cavity_points", "exterior_sweeps", "big_tier_tiles", "witness_atom_tests",
+              "sphere_candidates", "torus_candidates", "hard_edges"]
 
 # every exported C symbol, as declared in include/eses.h
 SYMBOLS = ["eses_create", "eses_create_device", "eses_create_batch", "eses_run_batch", "eses_set_option",

@@ -282,6 +282,37 @@ def test_repeated_runs_are_deterministic():
         eses.eses_destroy(ctx)
 
 
+def test_witness_atom_tests_counted():
+    """eses_stats' witness_atom_tests: the atom tests of the shell points'
+    witness freeness.  A lone atom has no neighbour, so its witnesses need no
+    test at all; two overlapping atoms need some, on every run, graph replays
+    included.  (The count depends on the order in which a tile's atoms are
+    staged, which is not fixed, so runs of a larger molecule may differ a
+    little; its labels do not.)"""
+    one = (np.zeros((1, 3)), np.array([1.7]))
+    two = (np.array([[0.0, 0.0, 0.0], [2.0, 0.3, -0.2]]), np.array([1.7, 1.5]))
+    for name, (xyz, rad) in {"one": one, "two": two}.items():
+        ctx = eses.eses_create(xyz, rad, 1.4, 0.2, 0.8)
+        try:
+            eses.eses_set_option(ctx, eses.ESES_OPT_GRAPH, 1)
+            for _ in range(3):  # plan, capture, replay
+                eses.eses_run(ctx)
+                n = eses.eses_stats(ctx)["witness_atom_tests"]
+                assert (n == 0) if name == "one" else (n > 0), (name, n)
+        finally:
+            eses.eses_destroy(ctx)
+    xyz, rad = inputs.protein_like(300, 17, inputs.PROTEIN_DENSITY)
+    ctx = eses.eses_create(xyz, rad, 1.4, 0.3, 0.8)
+    try:
+        eses.eses_run(ctx)
+        n0 = eses.eses_stats(ctx)["witness_atom_tests"]
+        eses.eses_run(ctx)
+        n1 = eses.eses_stats(ctx)["witness_atom_tests"]
+        assert n0 > 0 and abs(n1 - n0) <= 0.1 * n0
+    finally:
+        eses.eses_destroy(ctx)
+
+
 def test_stage_times_reported():
     xyz, rad = inputs.protein_like(100, 9)
     g = gpu_run(xyz, rad, 1.4, 0.5, 1.0, profile=True)
