@@ -163,6 +163,16 @@ __device__ int shell_part(const TileS<T, CP> &S, const ClsSmem<CP> &C, int brick
         for (int k = k0 + ((r - u) & (G - 1)); k < k1; k += G) {
             const int p = (int)C.inc[k];
             const short2 sl = C.pslot[p];
+            // a pair whose other ball holds x too is tested once, under the
+            // lower slot (the balls are taken in slot order; the same test
+            // decides whether that ball is taken)
+            const int b = sl.x == a ? sl.y : sl.x;
+            if (b >= 0 && b < a && ((C.bmask[brick][b >> 5] >> (b & 31)) & 1u)) {
+                const P4<T> cb = S.atom[b];
+                const T ex = x - cb.x, ey = y - cb.y, ez = z - cb.z;
+                const T Rb = cb.w + rp;
+                if (lt_sq<FILT>(ex * ex + ey * ey + ez * ez, Rb * Rb, Rb, d0) != 0) continue;
+            }
             int ws = saddle_witness<FILT>(A, p, x, y, z, rp, thr, d0, C.nbm, aw, (int)sl.x, (int)sl.y, nt);
             if (ws == 1) return 0;
             if (ws < 0) unsure = true;
