@@ -316,6 +316,25 @@ __device__ __forceinline__ RootRec no_root()
     return q;
 }
 
+// Lower point p (local index) of an edge in the tile frame, and the spacing,
+// in T: for FP32 the molecule's table of k * h rounded to FP32 (the same
+// values as rounding the FP64 products), so no FP64 arithmetic is spent.
+template <class T>
+__device__ __forceinline__ void edge_point(const Grid &G, int p, T *s, T &hT)
+{
+    if constexpr (sizeof(T) == sizeof(float)) {
+        s[0] = G.hl[p >> 6];
+        s[1] = G.hl[(p >> 3) & 7];
+        s[2] = G.hl[p & 7];
+        hT = G.hl[1];
+    } else {
+        s[0] = (double)(p >> 6) * G.h;
+        s[1] = (double)((p >> 3) & 7) * G.h;
+        s[2] = (double)(p & 7) * G.h;
+        hT = G.h;
+    }
+}
+
 // einfo[].y: lower point (local index), axis, end label, dropped (a buffer of
 // the staging pass was full)
 __host__ __device__ constexpr int edge_pack(int p, int axis, int lab, int dropped)
@@ -484,7 +503,6 @@ __device__ __forceinline__ int free_witness(const Acc &A, T qx, T qy, T qz, int 
 
 // shared memory of the staging pass (beside the staged tile)
 struct StageSmem {
-    double hd[TILE + 1];  // k * h, k = 0..8
     int8_t lab[9 * 9 * 9];
     short eptr[3 * TILE_PTS];  // crossing edges of the tile (local point), grouped by axis
     int cs[3 * TILE_PTS + 1];  // per edge: sphere candidates, then their offset in the tile's run
@@ -758,12 +776,10 @@ __device__ __forceinline__ bool cand_test(const TileS<T, CP> &S, const T *s, int
 // witness = projection on the expanded sphere; else the probe sphere of staged
 // triple point item - na, concave, witness = the triple point).
 template <class T, bool FILT, class AccT, class AccX>
-__device__ void sphere_roots(const AccT &A, const AccX &X, int item, const double *s64, int axis, bool inside,
-                             double h, double rp, T d0, RootSink &out)
+__device__ void sphere_roots(const AccT &A, const AccX &X, int item, const T *s, const double *s64, int axis,
+                             bool inside, T hT, T rpT, double h, double rp, T d0, RootSink &out)
 {
-    const T s[3] = {(T)s64[0], (T)s64[1], (T)s64[2]};
     const int na = A.na();
-    const T hT = (T)h, rpT = (T)rp;
     const T lo = FILT ? T(-1e-4) : T(0), hi = hT + (FILT ? T(1e-4) : T(0));
     const T tmax = T(1e-3);  // FP32 root error beyond which FP64 decides (grazing pieces)
     const double NaN = __longlong_as_double(0x7ff8000000000000LL);
@@ -925,13 +941,11 @@ __device__ void torus_roots(const AccT &A, const AccX &X, int pi, const double *
 // staged slot) and its root, 1 when no root is found, 2 when the candidates
 // overflowed the buffer (the first WCAND are used).
 template <class T, bool FILT, class AccT, class AccX>
-__device__ int warp_select(const AccT &A, const AccX &X, WCand *c, int n, const double *s64, int axis, bool inside,
-                           double h, double rp, T d0, float &t_out, int &kind_out, int &slot_out)
+__device__ int warp_select(const AccT &A, const AccX &X, WCand *c, int n, const T *s, const double *s64, int axis,
+                           bool inside, float hf, T rpT, double rp, T d0, float &t_out, int &kind_out, int &slot_out)
 {
     const int lane = threadIdx.x & 31;
-    const T s[3] = {(T)s64[0], (T)s64[1], (T)s64[2]};
-    const T rpT = (T)rp;
-    const float tie = 1e-6f * (float)h;  // FP32 rounding of a root
+    const float tie = 1e-6f * hf;  // FP32 rounding of a root
     int status = n > WCAND ? 2 : 0;
     if (n > WCAND) n = WCAND;
     int pick = -1;
@@ -1267,7 +1281,6 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_stage(Model M, Batch B, T
             E.lab[q] = v;
         }
         if (threadIdx.x == 0) E.estart[0] = 0;
-        if (threadIdx.x <= TILE) E.hd[threadIdx.x] = (double)threadIdx.x * h;
         __syncthreads();
         // the tile's crossing edges, axis by axis, in point order
         for (int a = 0; a < 3; ++a) {
@@ -1315,7 +1328,8 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_stage(Model M, Batch B, T
         const bool keep = (long long)ne * nwd <= HMASK_WORDS;
         for (int e = warp; e < ne; e += EDGE_WARPS) {
             const EdgeRef R = edge_ref(E, e);
-            const T s[3] = {(T)E.hd[R.p >> 6], (T)E.hd[(R.p >> 3) & 7], (T)E.hd[R.p & 7]};
+            T s[3], hs;
+            edge_point<T>(G, R.p, s, hs);
             int cs = 0, ct = 0;
             for (int i0 = 0; i0 < nitem; i0 += 32) {
                 const int it = i0 + lane;
@@ -1432,7 +1446,8 @@ __global__ void __launch_bounds__(EDGE_THREADS) k_edge_stage(Model M, Batch B, T
             for (int e = warp; e < ne; e += EDGE_WARPS) {
                 const EdgeRef R = edge_ref(E, e);
                 const int g = E.gbase[R.axis] + (e - E.estart[R.axis]);
-                const T s[3] = {(T)E.hd[R.p >> 6], (T)E.hd[(R.p >> 3) & 7], (T)E.hd[R.p & 7]};
+                T s[3], hs;
+            edge_point<T>(G, R.p, s, hs);
                 long long ps = E.sb + E.cs[e], pt = E.tb + E.ct[e];
                 const long long ps1 = E.sb + E.cs[e + 1], pt1 = E.tb + E.ct[e + 1];
                 const unsigned below = (1u << lane) - 1;
@@ -1476,6 +1491,7 @@ __global__ void __launch_bounds__(ROOT_THREADS_MAX) k_roots_sphere(Model M, Batc
 {
     const long long n = min((long long)W.ctr[1], W.cap_sph);
     const double rp = M.rp;
+    const T rpT = (T)rp;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
         const int2 c = W.csph[k];
         if (c.x < 0 || c.x >= W.n_edges) {  // dead record
@@ -1491,10 +1507,12 @@ __global__ void __launch_bounds__(ROOT_THREADS_MAX) k_roots_sphere(Model M, Batc
         const T d0 = FILT ? (T)B.grid[mol].d0 : T(0);
         const int pk = inf.y, p = pk_point(pk);
         const double s64[3] = {(double)(p >> 6) * h, (double)((p >> 3) & 7) * h, (double)(p & 7) * h};
+        T s[3], hT;
+        edge_point<T>(B.grid[mol], p, s, hT);
         const SlabAcc<T> A(sl);
         const SlabExact<T> X(A, M, x0);
         RootSink out{W.rsph + (size_t)SPH_SLOTS * k, 0, SPH_SLOTS};
-        sphere_roots<T, FILT>(A, X, c.y, s64, pk_axis(pk), pk_label(pk) == LABEL_IN, h, rp, d0, out);
+        sphere_roots<T, FILT>(A, X, c.y, s, s64, pk_axis(pk), pk_label(pk) == LABEL_IN, hT, rpT, h, rp, d0, out);
         if (out.n > SPH_SLOTS) atomicOr(err, ERR_CAP_CAND);
         W.nsph[k] = (uint8_t)min(out.n, SPH_SLOTS);
     }
@@ -1505,11 +1523,9 @@ __global__ void __launch_bounds__(ROOT_THREADS_MAX) k_roots_sphere(Model M, Batc
 // slot; a candidate whose isolation is undecided is left whole to the exact
 // kernel.  Returns 0 (done), 1 (pending slots) or 2 (whole candidate).
 template <class AccT>
-__device__ int torus_roots_fp32(const AccT &A, int pi, const double *s64, int axis, bool inside, double h, double rp,
+__device__ int torus_roots_fp32(const AccT &A, int pi, const float *s, int axis, bool inside, float hT, float rpT,
                                 float d0, RootSink &out)
 {
-    const float s[3] = {(float)s64[0], (float)s64[1], (float)s64[2]};
-    const float hT = (float)h, rpT = (float)rp;
     const float lo = -1e-4f, hi = hT + 1e-4f;
     const float tmax = 1e-3f;
     const double NaN = __longlong_as_double(0x7ff8000000000000LL);
@@ -1558,6 +1574,7 @@ __global__ void __launch_bounds__(ROOT_THREADS_MAX) k_roots_torus(Model M, Batch
 {
     const long long n = min((long long)W.ctr[2], W.cap_tor);
     const double rp = M.rp;
+    const float rpf = (float)rp;
     const int lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long k0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); k0 < n; k0 += stride) {
@@ -1576,13 +1593,15 @@ __global__ void __launch_bounds__(ROOT_THREADS_MAX) k_roots_torus(Model M, Batch
         const double h = B.grid[mol].h;
         const T d0 = FILT ? (T)B.grid[mol].d0 : T(0);
         const int pk = inf.y, p = pk_point(pk);
-        const double s64[3] = {(double)(p >> 6) * h, (double)((p >> 3) & 7) * h, (double)(p & 7) * h};
         const SlabAcc<T> A(sl);
-        const SlabExact<T> X(A, M, x0);
         RootSink out{W.rtor + (size_t)TOR_SLOTS * k, 0, TOR_SLOTS};
         if constexpr (FILT) {
-            job = torus_roots_fp32(A, c.y, s64, pk_axis(pk), pk_label(pk) == LABEL_IN, h, rp, (float)d0, out);
+            float s[3], hT;
+            edge_point<float>(B.grid[mol], p, s, hT);
+            job = torus_roots_fp32(A, c.y, s, pk_axis(pk), pk_label(pk) == LABEL_IN, hT, rpf, (float)d0, out);
         } else {
+            const double s64[3] = {(double)(p >> 6) * h, (double)((p >> 3) & 7) * h, (double)(p & 7) * h};
+            const SlabExact<T> X(A, M, x0);
             torus_roots<T, FILT>(A, X, c.y, s64, pk_axis(pk), pk_label(pk) == LABEL_IN, h, rp, d0, out);
         }
         if (out.n > TOR_SLOTS) atomicOr(err, ERR_CAP_CAND);
@@ -1736,7 +1755,7 @@ __global__ void __launch_bounds__(PICK_THREADS) k_edge_pick(Batch B, RootWork W,
                 }
                 hard = !(n >= 1 && n <= WCAND && (lab == LABEL_IN || n == 1) && kn >= 0);
                 if (!hard) {  // every other candidate ordered after it by the FP32 bounds
-                    const float tie = 1e-6f * (float)B.grid[__ldg(&hd->mol)].h;
+                    const float tie = 1e-6f * B.grid[__ldg(&hd->mol)].hl[1];
                     int m = 0;
                     for (int j = 0; j < ns && !hard; ++j) {
                         const int nr = W.nsph[inf.z + j];
@@ -1787,6 +1806,7 @@ __global__ void __launch_bounds__(HARD_THREADS) k_edge_hard(Model M, Batch B, Ro
     const long long nt = B.n_tiles;
     const long long nh = (long long)W.ctr[3];
     const double rp = M.rp;
+    const T rpT = (T)rp;
     WCand *c = cand[warp];
     for (long long q = (long long)blockIdx.x * (HARD_THREADS / 32) + warp; q < nh;
          q += (long long)gridDim.x * (HARD_THREADS / 32)) {
@@ -1803,6 +1823,8 @@ __global__ void __launch_bounds__(HARD_THREADS) k_edge_hard(Model M, Batch B, Ro
         const double h = B.grid[mol].h;
         const T d0 = FILT ? (T)B.grid[mol].d0 : T(0);
         const double s64[3] = {(double)(p >> 6) * h, (double)((p >> 3) & 7) * h, (double)(p & 7) * h};
+        T s[3], hT;
+        edge_point<T>(B.grid[mol], p, s, hT);
         const SlabAcc<T> A(sl);
         const SlabExact<T> X(A, M, x0);
         const int na = A.na();
@@ -1846,7 +1868,7 @@ __global__ void __launch_bounds__(HARD_THREADS) k_edge_hard(Model M, Batch B, Ro
         __syncwarp();
         float tr = 0.5f * (float)h;
         int kind = 0, slot = 0;
-        int status = pk_dropped(pk) ? 2 : warp_select<T, FILT>(A, X, c, n, s64, axis, lab == LABEL_IN, h, rp, d0, tr,
+        int status = pk_dropped(pk) ? 2 : warp_select<T, FILT>(A, X, c, n, s, s64, axis, lab == LABEL_IN, (float)hT, rpT, rp, d0, tr,
                                                                kind, slot);
         if (lane == 0) {
             const int mid = status == 1 || pk_dropped(pk) ? 0 : A.model_index(kind, slot);
