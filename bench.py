@@ -54,14 +54,16 @@ FP32_LANES = 128  # FP32 FMA lanes per SM
 WORKLOAD = 2
 
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
-# ncu capture of the globule workload (profiles/k_<kernel>_globule-5000.md),
-# reported only while the kernel's sources are the ones that were captured
+# DRAM bytes per step (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of the globule workload: the root solve's six launches summed
+# (profiles/root-solve_globule-5000.md), the classification's two tiers
+# (profiles/k_classify_globule-5000.md); reported only while the kernels'
+# sources are the ones that were captured
 TRAFFIC = {
-    "edge_solve": (53_811_200, {"eses_edges.cu": "17a5061ebb563876", "eses_tile.cuh": "52f021e2fa8f2849",
-                                "eses_internal.cuh": "7ce4766849297923"}),
-    "classify": (9_634_048, {"eses_classify.cu": "b213768c87a2c907", "eses_tile.cuh": "52f021e2fa8f2849",
-                             "eses_internal.cuh": "7ce4766849297923"}),
+    "edge_solve": (741_614_080, {"eses_edges.cu": "b562f215d515fa73", "eses_tile.cuh": "0665160bfe8f347d",
+                                 "eses_internal.cuh": "9f7abbfab2b48180"}),
+    "classify": (10_066_432, {"eses_classify.cu": "c4f589a46300dc44", "eses_tile.cuh": "0665160bfe8f347d",
+                              "eses_internal.cuh": "9f7abbfab2b48180"}),
 }
 
 
