@@ -558,7 +558,8 @@ def main():
         "classify": ("k_classify<float,true> (FP32-filtered classification, every grid point)",
                      fm["model_flops"], stage_ms["classify"],
                      {"flops_per_point": fm["flops_per_point"]}),
-        "edge_solve": ("root solve: k_edge_stage, k_roots_sphere, k_roots_torus, k_edge_pick, k_edge_hard "
+        "edge_solve": ("root solve: k_edge_stage, k_roots_sphere, k_roots_torus, k_roots_torus_exact, k_edge_pick, "
+                       "k_edge_hard "
                        "<float,true> (first root and its patch of every crossing edge)",
                        fm["edge_counts"]["model_flops"], stage_ms["edge_solve"],
                        {"flops_per_edge": fm["edge_flops_per_edge"], "edges": fm["edge_counts"]["edges"]}),
