@@ -60,7 +60,7 @@ WORKLOAD = 2
 # (profiles/k_classify_globule-5000.md); reported only while the kernels'
 # sources are the ones that were captured
 TRAFFIC = {
-    "edge_solve": (741_614_080, {"eses_edges.cu": "b562f215d515fa73", "eses_tile.cuh": "0665160bfe8f347d",
+    "edge_solve": (741_614_080, {"eses_edges.cu": "31f790f16209e362", "eses_tile.cuh": "0665160bfe8f347d",
                                  "eses_internal.cuh": "9f7abbfab2b48180"}),
     "classify": (10_066_432, {"eses_classify.cu": "c4f589a46300dc44", "eses_tile.cuh": "0665160bfe8f347d",
                               "eses_internal.cuh": "9f7abbfab2b48180"}),

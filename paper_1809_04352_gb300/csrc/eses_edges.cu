@@ -1061,19 +1061,6 @@ __device__ int warp_select(const AccT &A, const AccX &X, WCand *c, int n, const 
     return status;
 }
 
-__device__ __forceinline__ double block_sum_double(double v, double *sh)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    double tot = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += sh[k];  // fixed order: deterministic
-    __syncthreads();
-    return tot;
-}
-
 // Per tile and axis: crossing edges (end labels differ) and inside edges (both
 // ends inside) leaving the tile's points in + direction, and the tile's inside
 // points.  One warp per tile, 16 points per lane, warp sums (no block barrier).
