@@ -191,7 +191,7 @@ __host__ __device__ constexpr size_t cls_bytes()
     return (((sizeof(TileS<T, CP>) + 15) & ~(size_t)15) + sizeof(ClsSmem<CP>) + 255) & ~(size_t)255;
 }
 
-// CP = CapSmall: the staged lists in shared memory; a tile that overflows
+// CP = CapMid: the staged lists in shared memory; a tile that overflows
 // them goes to ovf.  CP = CapBig (BIG): the tiles listed in ovf, with the
 // staged lists in this CTA's slice of the global scratch `big`; overflowing
 // that too is a capacity error.
@@ -462,10 +462,10 @@ static int g_n_sm = 1;              // SMs: the grid of the global-memory tier
 // before any launch or capture)
 void classify_init()
 {
-    cudaFuncSetAttribute(k_classify<double, false, CapSmall, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)cls_bytes<double, CapSmall>());
-    cudaFuncSetAttribute(k_classify<float, true, CapSmall, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)cls_bytes<float, CapSmall>());
+    cudaFuncSetAttribute(k_classify<double, false, CapMid, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)cls_bytes<double, CapMid>());
+    cudaFuncSetAttribute(k_classify<float, true, CapMid, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)cls_bytes<float, CapMid>());
     cudaFuncSetAttribute(k_band<CapSmall, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)band_bytes<CapSmall>());
     int dev = 0, n_sm = 0, per_sm = 0;
@@ -492,11 +492,11 @@ int classify_ctas_per_sm(int precision)
     int dev = 0, n = 0;
     cudaGetDevice(&dev);
     if (precision == 0)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_classify<double, false, CapSmall, false>, CLS_THREADS,
-                                                      cls_bytes<double, CapSmall>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_classify<double, false, CapMid, false>, CLS_THREADS,
+                                                      cls_bytes<double, CapMid>());
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_classify<float, true, CapSmall, false>, CLS_THREADS,
-                                                      cls_bytes<float, CapSmall>());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_classify<float, true, CapMid, false>, CLS_THREADS,
+                                                      cls_bytes<float, CapMid>());
     return n > 0 ? n : 1;
 }
 
@@ -510,12 +510,12 @@ int launch_classify(const Model &M, const Batch &B, int precision, const TileSch
     cudaMemsetAsync(ovf + 1, 0, sizeof(int), st);
     TileSched QB{nullptr, 1, ovf + 2, ovf + 1};
     if (precision == 0) {
-        k_classify<double, false, CapSmall, false><<<grid, CLS_THREADS, cls_bytes<double, CapSmall>(), st>>>(
+        k_classify<double, false, CapMid, false><<<grid, CLS_THREADS, cls_bytes<double, CapMid>(), st>>>(
             M, B, Q, labels, tile_band, err, ovf, nullptr, n_tests);
         k_classify<double, false, CapBig, true><<<g_n_sm, CLS_THREADS, 0, st>>>(M, B, QB, labels, tile_band, err, ovf,
                                                                                big, n_tests);
     } else {
-        k_classify<float, true, CapSmall, false><<<grid, CLS_THREADS, cls_bytes<float, CapSmall>(), st>>>(
+        k_classify<float, true, CapMid, false><<<grid, CLS_THREADS, cls_bytes<float, CapMid>(), st>>>(
             M, B, Q, labels, tile_band, err, ovf, nullptr, n_tests);
         k_classify<float, true, CapBig, true><<<g_n_sm, CLS_THREADS, 0, st>>>(M, B, QB, labels, tile_band, err, ovf,
                                                                              big, n_tests);

@@ -32,6 +32,12 @@ struct CapSmall {
 struct CapBig {
     static constexpr int A = 1024, P = 2048, V = 2048;
 };
+// the shared-memory tier of the classification and of the root solve's
+// staging pass: lists sized so that four CTAs fit an SM (the tiles past them
+// take the global-memory tier)
+struct CapMid {
+    static constexpr int A = 256, P = 384, V = 384;
+};
 constexpr int ERR_CAP_ANY = 1 | 2 | 4;  // ERR_CAP_ATOMS | ERR_CAP_PAIRS | ERR_CAP_VERTS
 
 // device error bits (OR-ed into ctx->d_err)
