@@ -58,7 +58,7 @@ constexpr int WCAND = 64;        // candidate roots of one edge in the selection
 constexpr int ROOT_THREADS_MAX = 256;  // per-candidate root kernels: threads per block (at most, the default)
 constexpr int PICK_THREADS = 256;
 constexpr int HARD_THREADS = 256;
-constexpr int HMASK_WORDS = 2048;  // prefilter hit masks kept between the staging pass's two sweeps
+constexpr int HMASK_WORDS = 1536;  // prefilter hit masks kept between the staging pass's two sweeps
 constexpr int POLISH_THREADS = 256;
 
 // --------------------------------------------------------------------------
@@ -1200,7 +1200,7 @@ __device__ __forceinline__ void block_scan_runs(int *v, int *w, int n, int *sh, 
 }
 
 // 1. Staging pass.  Persistent CTAs take tiles from the work queue.  Per tile
-// with crossing edges: the pieces are staged (CP = CapSmall: in shared memory,
+// with crossing edges: the pieces are staged (CP = CapMid: in shared memory,
 // a tile that overflows it goes to ovf; CP = CapBig (BIG): the tiles listed in
 // ovf, staged in this CTA's slice of the global scratch `big`, lists cut at
 // capacity with the error bit set), the crossing edges listed per axis in
@@ -2080,7 +2080,7 @@ int launch_mol_edges(const Batch &B, const int *edge_start, long long *medge, cu
 template <class T>
 static size_t stage_smem()
 {
-    return edge_tile_bytes<T, CapSmall>() + sizeof(StageSmem);
+    return edge_tile_bytes<T, CapMid>() + sizeof(StageSmem);
 }
 
 static int g_edge_n_sm = 1;  // SMs: the grid of the global-memory tier and of the persistent root kernels
@@ -2094,9 +2094,9 @@ static int threads_slot(int threads) { return threads <= 64 ? 0 : (threads <= 12
 // dynamic shared memory limits and occupancies (once per device, before any launch or capture)
 void edges_init()
 {
-    cudaFuncSetAttribute(k_edge_stage<double, false, CapSmall, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_edge_stage<double, false, CapMid, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)stage_smem<double>());
-    cudaFuncSetAttribute(k_edge_stage<float, true, CapSmall, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_edge_stage<float, true, CapMid, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)stage_smem<float>());
     cudaFuncSetAttribute(k_edge_stage<double, false, CapBig, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(StageSmem));
@@ -2130,10 +2130,10 @@ int edge_ctas_per_sm(int precision)
 {
     int n = 0;
     if (precision == 0)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_edge_stage<double, false, CapSmall, false>, EDGE_THREADS,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_edge_stage<double, false, CapMid, false>, EDGE_THREADS,
                                                       stage_smem<double>());
     else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_edge_stage<float, true, CapSmall, false>, EDGE_THREADS,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_edge_stage<float, true, CapMid, false>, EDGE_THREADS,
                                                       stage_smem<float>());
     return n > 0 ? n : 1;
 }
@@ -2154,7 +2154,7 @@ static void stage_launch(const Model &M, const Batch &B, const TileSched &Q, int
     cudaMemsetAsync(W.ctr, 0, 8 * sizeof(unsigned long long), st);
     if (Q.head) cudaMemsetAsync(Q.head, 0, sizeof(unsigned long long), st);
     cudaMemsetAsync(ovf + 1, 0, sizeof(int), st);
-    k_edge_stage<T, FILT, CapSmall, false><<<grid, EDGE_THREADS, stage_smem<T>(), st>>>(M, B, Q, labels, edge_start,
+    k_edge_stage<T, FILT, CapMid, false><<<grid, EDGE_THREADS, stage_smem<T>(), st>>>(M, B, Q, labels, edge_start,
                                                                                        out, err, ovf, nullptr, W);
     TileSched QB{nullptr, 1, ovf + 2, ovf + 1};
     k_edge_stage<T, FILT, CapBig, true><<<g_edge_n_sm, EDGE_THREADS, sizeof(StageSmem), st>>>(
