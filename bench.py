@@ -60,10 +60,10 @@ WORKLOAD = 2
 # (profiles/k_classify_globule-5000.md); reported only while the kernels'
 # sources are the ones that were captured
 TRAFFIC = {
-    "edge_solve": (741_614_080, {"eses_edges.cu": "31f790f16209e362", "eses_tile.cuh": "0665160bfe8f347d",
-                                 "eses_internal.cuh": "9f7abbfab2b48180"}),
-    "classify": (10_066_432, {"eses_classify.cu": "c4f589a46300dc44", "eses_tile.cuh": "0665160bfe8f347d",
-                              "eses_internal.cuh": "9f7abbfab2b48180"}),
+    "edge_solve": (739_858_432, {"eses_edges.cu": "caf97df99fe6129f", "eses_tile.cuh": "0665160bfe8f347d",
+                                 "eses_internal.cuh": "9c0bf5106d8efdeb"}),
+    "classify": (10_196_736, {"eses_classify.cu": "71fc2607bb299d7e", "eses_tile.cuh": "0665160bfe8f347d",
+                              "eses_internal.cuh": "9c0bf5106d8efdeb"}),
 }
 
 
