@@ -341,9 +341,11 @@ int eses_area_volume(const eses_ctx *ctx, double *area, double *volume);
  * root failure, [9] inside points, [10] kernels launched by the run,
  * [11] tiles proposed far, [12] tiles certified far (eses_set_proposer),
  * [13] cavity points labelled inside (ESES_OPT_EXTERIOR), [14] flood-fill
- * sweeps, [15] tile stagings that overflowed the shared-memory lists (320
- * atoms, 512 free-arc pairs, 640 free triple points) and were redone with
- * lists in global memory (1024, 2048, 2048; beyond those ESES_ECAPACITY),
+ * sweeps, [15] tile stagings that overflowed the shared-memory lists (256
+ * atoms, 384 free-arc pairs, 384 free triple points in the classification
+ * and the root solve's staging pass; 320, 512, 640 in the FP64
+ * re-evaluation) and were redone with lists in global memory (1024, 2048,
+ * 2048; beyond those ESES_ECAPACITY),
  * summed over the classification, the FP64 re-evaluation and the root solve;
  * [16] atom tests of the classification's witness freeness checks (each
  * convex or saddle witness of a shell point is tested against the staged
